@@ -1,0 +1,269 @@
+"""ctypes wrapper of the FP64 CPU oracle (oracle.cpp).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the package smoke check and
+the benchmark's CPU-baseline leg. The product path never imports this module.
+"""
+import ctypes as ct
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.cpp")
+
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+class Config(ct.Structure):
+    _fields_ = [
+        ("solver", ct.c_int), ("restart", ct.c_int), ("tol", ct.c_double),
+        ("maxiter", ct.c_int), ("precond", ct.c_int), ("pmode", ct.c_int),
+        ("matching_rounds", ct.c_int), ("agg_passes", ct.c_int),
+        ("jacobi_omega", ct.c_double), ("nu1", ct.c_int), ("nu2", ct.c_int),
+        ("coarse_size", ct.c_int), ("max_levels", ct.c_int),
+        ("max_coarsen_ratio", ct.c_double), ("p_omega", ct.c_double),
+        ("coarse_dense_max", ct.c_int), ("coarse_sweeps", ct.c_int),
+    ]
+
+
+class Result(ct.Structure):
+    _fields_ = [("status", ct.c_int), ("iters", ct.c_int), ("restarts", ct.c_int),
+                ("rel_res_initial", ct.c_double), ("rel_res_final", ct.c_double),
+                ("levels", ct.c_int)]
+
+
+def build(force=False):
+    """Compile liboracle.so (plain C++17, no implicit FMA contraction)."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        return _SO
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-o", _SO, _SRC]
+    subprocess.check_call(cmd)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ct.CDLL(_SO)
+        L.or_config_default.argtypes = [ct.POINTER(Config)]
+        L.or_ldu_check.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p]
+        L.or_ldu_structure.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p]
+        L.or_ldu_values.argtypes = [ct.c_int, ct.c_int, ct.c_int, _i32p, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
+        L.or_bsr_to_ldu.argtypes = [ct.c_int, ct.c_int, ct.c_int, _i32p, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
+        L.or_bsr_spmv.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, _f64p, _f64p]
+        L.or_dense_inverse.argtypes = [ct.c_int, _f64p, _f64p]
+        L.or_block_norms.argtypes = [ct.c_int, ct.c_int, _f64p, _f64p]
+        L.or_aggregate.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, ct.POINTER(Config), _i32p]
+        L.or_amg_setup.restype = ct.c_void_p
+        L.or_amg_setup.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, ct.POINTER(Config), ct.POINTER(ct.c_int)]
+        L.or_amg_resetup.argtypes = [ct.c_void_p, _f64p]
+        L.or_amg_free.argtypes = [ct.c_void_p]
+        L.or_amg_levels.argtypes = [ct.c_void_p]
+        L.or_amg_level_info.argtypes = [ct.c_void_p, ct.c_int] + [ct.POINTER(ct.c_int)] * 4
+        L.or_amg_get_A.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p]
+        L.or_amg_get_P.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]
+        L.or_amg_get_dinv.argtypes = [ct.c_void_p, ct.c_int, _f64p]
+        L.or_amg_get_coarse_inverse.argtypes = [ct.c_void_p, _f64p]
+        L.or_amg_vcycle.argtypes = [ct.c_void_p, _f64p, _f64p]
+        L.or_solve.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, ct.c_void_p, ct.POINTER(Config),
+                               _f64p, _f64p, ct.POINTER(Result), ct.c_void_p, ct.c_int]
+        L.or_fgmres_arnoldi.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, ct.c_void_p,
+                                        ct.POINTER(Config), _f64p, ct.c_int, _f64p, _f64p, _f64p]
+        _lib = L
+    return _lib
+
+
+def config(**kw):
+    c = Config()
+    lib().or_config_default(ct.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+def ldu_check(C, owner, neighbour):
+    owner = np.ascontiguousarray(owner, np.int32)
+    neighbour = np.ascontiguousarray(neighbour, np.int32)
+    return lib().or_ldu_check(C, owner.size, owner, neighbour)
+
+
+def ldu_to_bsr(sys):
+    """Block-CSR structure and values of an LDU system (dict from synth)."""
+    C, F, n = sys["n_cells"], sys["n_faces"], sys["n"]
+    owner = np.ascontiguousarray(sys["owner"], np.int32)
+    nb = np.ascontiguousarray(sys["neighbour"], np.int32)
+    rp = np.zeros(C + 1, np.int32)
+    col = np.zeros(C + 2 * F, np.int32)
+    pd = np.zeros(C, np.int32)
+    pu = np.zeros(F, np.int32)
+    pl = np.zeros(F, np.int32)
+    st = lib().or_ldu_structure(C, F, owner, nb, rp, col, pd, pu, pl)
+    if st:
+        raise ValueError("invalid LDU addressing")
+    val = np.zeros((C + 2 * F) * n * n)
+    lib().or_ldu_values(C, F, n, pd, pu, pl, sys["diag"].ravel(), sys["upper"].ravel(),
+                        sys["lower"].ravel(), val)
+    return dict(rows=C, n=n, row_ptr=rp, col=col, val=val.reshape(-1, n, n),
+                pos_diag=pd, pos_up=pu, pos_lo=pl)
+
+
+def bsr_to_ldu(bsr, F):
+    C, n = bsr["rows"], bsr["n"]
+    d = np.zeros(C * n * n)
+    u = np.zeros(F * n * n)
+    lo = np.zeros(F * n * n)
+    lib().or_bsr_to_ldu(C, F, n, bsr["pos_diag"], bsr["pos_up"], bsr["pos_lo"],
+                        np.ascontiguousarray(bsr["val"]).ravel(), d, u, lo)
+    return d.reshape(C, n, n), u.reshape(F, n, n), lo.reshape(F, n, n)
+
+
+def spmv(bsr, x):
+    rows, n = bsr["rows"], bsr["n"]
+    y = np.zeros(rows * n)
+    lib().or_bsr_spmv(rows, n, bsr["row_ptr"], bsr["col"], np.ascontiguousarray(bsr["val"]).ravel(),
+                      np.ascontiguousarray(x, np.float64).ravel(), y)
+    return y.reshape(rows, n)
+
+
+def dense_inverse(A):
+    A = np.ascontiguousarray(A, np.float64)
+    N = A.shape[0]
+    out = np.zeros((N, N))
+    if lib().or_dense_inverse(N, A.ravel(), out.ravel()):
+        raise np.linalg.LinAlgError("zero pivot")
+    return out
+
+
+def block_norms(val):
+    val = np.ascontiguousarray(val, np.float64)
+    nb, n = val.shape[0], val.shape[1]
+    out = np.zeros(nb)
+    lib().or_block_norms(nb, n, val.ravel(), out)
+    return out
+
+
+def aggregate(bsr, cfg=None):
+    cfg = cfg or config()
+    agg = np.zeros(bsr["rows"], np.int32)
+    na = lib().or_aggregate(bsr["rows"], bsr["n"], bsr["row_ptr"], bsr["col"],
+                            np.ascontiguousarray(bsr["val"]).ravel(), ct.byref(cfg), agg)
+    return agg, na
+
+
+class Amg:
+    """AMG hierarchy built by the oracle (full setup at construction)."""
+
+    def __init__(self, bsr, cfg=None):
+        self.cfg = cfg or config()
+        self.n = bsr["n"]
+        self.rows = bsr["rows"]
+        self._bsr = bsr
+        st = ct.c_int(0)
+        self.h = lib().or_amg_setup(bsr["rows"], bsr["n"], bsr["row_ptr"], bsr["col"],
+                                    np.ascontiguousarray(bsr["val"]).ravel(), ct.byref(self.cfg), ct.byref(st))
+        self.status = st.value
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_amg_free(self.h)
+            self.h = None
+
+    def resetup(self, val):
+        return lib().or_amg_resetup(self.h, np.ascontiguousarray(val, np.float64).ravel())
+
+    @property
+    def levels(self):
+        return lib().or_amg_levels(self.h)
+
+    def info(self, l):
+        r, nz, pn, k = ct.c_int(), ct.c_int(), ct.c_int(), ct.c_int()
+        lib().or_amg_level_info(self.h, l, ct.byref(r), ct.byref(nz), ct.byref(pn), ct.byref(k))
+        return dict(rows=r.value, nnz=nz.value, p_nnz=pn.value, coarse_kind=k.value)
+
+    def A(self, l):
+        i = self.info(l)
+        n = self.n
+        rp = np.zeros(i["rows"] + 1, np.int32)
+        ci = np.zeros(i["nnz"], np.int32)
+        v = np.zeros(i["nnz"] * n * n)
+        lib().or_amg_get_A(self.h, l, _p(rp), _p(ci), _p(v))
+        return dict(rows=i["rows"], n=n, row_ptr=rp, col=ci, val=v.reshape(-1, n, n))
+
+    def P(self, l):
+        i = self.info(l)
+        n = self.n
+        rp = np.zeros(i["rows"] + 1, np.int32)
+        ci = np.zeros(i["p_nnz"], np.int32)
+        v = np.zeros(i["p_nnz"] * n * n)
+        agg = np.zeros(i["rows"], np.int32)
+        om = ct.c_double(0)
+        lib().or_amg_get_P(self.h, l, _p(rp), _p(ci), _p(v), _p(agg), ct.byref(om))
+        cols = self.info(l + 1)["rows"]
+        return dict(rows=i["rows"], cols=cols, n=n, row_ptr=rp, col=ci, val=v.reshape(-1, n, n),
+                    agg=agg, omega=om.value)
+
+    def dinv(self, l):
+        i = self.info(l)
+        out = np.zeros(i["rows"] * self.n * self.n)
+        lib().or_amg_get_dinv(self.h, l, out)
+        return out.reshape(-1, self.n, self.n)
+
+    def coarse_inverse(self):
+        i = self.info(self.levels - 1)
+        N = i["rows"] * self.n
+        out = np.zeros(N * N)
+        lib().or_amg_get_coarse_inverse(self.h, out)
+        return out.reshape(N, N)
+
+    def vcycle(self, v):
+        v = np.ascontiguousarray(v, np.float64).ravel()
+        z = np.zeros_like(v)
+        lib().or_amg_vcycle(self.h, v, z)
+        return z.reshape(-1, self.n)
+
+
+def solve(bsr, b, x0=None, cfg=None, amg=None, hist_len=0):
+    """Krylov solve with the oracle; returns (x, result dict, history)."""
+    cfg = cfg or config()
+    n, rows = bsr["n"], bsr["rows"]
+    if cfg.precond == 0 and amg is None:
+        amg = Amg(bsr, cfg)
+        if amg.status:
+            return None, dict(status=amg.status), None
+    x = np.zeros(rows * n) if x0 is None else np.ascontiguousarray(x0, np.float64).ravel().copy()
+    res = Result()
+    hist = np.zeros(max(hist_len, 1))
+    lib().or_solve(rows, n, bsr["row_ptr"], bsr["col"], np.ascontiguousarray(bsr["val"]).ravel(),
+                   amg.h if amg is not None else None, ct.byref(cfg),
+                   np.ascontiguousarray(b, np.float64).ravel(), x, ct.byref(res),
+                   _p(hist) if hist_len else None, hist_len)
+    out = {k: getattr(res, k) for k, _ in Result._fields_}
+    return x.reshape(rows, n), out, hist[:min(hist_len, res.iters)] if hist_len else None
+
+
+def arnoldi(bsr, b, j_steps, cfg=None, amg=None):
+    cfg = cfg or config()
+    n, rows = bsr["n"], bsr["rows"]
+    N = rows * n
+    V = np.zeros((j_steps + 1) * N)
+    Z = np.zeros(j_steps * N)
+    H = np.zeros((j_steps + 1) * j_steps)
+    done = lib().or_fgmres_arnoldi(rows, n, bsr["row_ptr"], bsr["col"], np.ascontiguousarray(bsr["val"]).ravel(),
+                                   amg.h if amg is not None else None, ct.byref(cfg),
+                                   np.ascontiguousarray(b, np.float64).ravel(), j_steps, V, Z, H)
+    return done, V.reshape(j_steps + 1, N), Z.reshape(j_steps, N), H.reshape(j_steps + 1, j_steps)

@@ -1,0 +1,145 @@
+/*
+ * FP64 CPU oracle for the block-coupled linear solve.
+ *
+ * TEST INFRASTRUCTURE ONLY. This is a plain, slow, single-threaded reference
+ * written from the paper's statement of the problem; it shares no code with
+ * the CUDA library. Only the tests, the package's smoke() check and the
+ * benchmark's CPU-baseline leg may load it. The product path never calls it.
+ *
+ * What it follows:
+ *   Eq. 1 (Sec. 2)        A_ii U_i + sum_N A_ij U_j = b_i with dense n x n
+ *                         blocks; LDU face addressing (Sec. 2.3): upper[f] is
+ *                         the block at (owner, neighbour), lower[f] the block
+ *                         at (neighbour, owner).
+ *   Sec. 2.3, Alg. 1      block AoS storage (row-major n x n blocks,
+ *                         concatenated) and the LDU -> block-CSR permutation;
+ *                         first-iteration setup vs. values-only replacement.
+ *   Sec. 2.3              aggregation AMG for block systems built by graph
+ *                         matching, smoothers, Krylov solvers (GMRES, BiCGStab).
+ *   Sec. 2 (ref. Saad & Schultz)  GMRES.
+ * The paper leaves the AMG and Krylov details unspecified; the readings used
+ * here (matching rule, smoothed prolongation, block-Jacobi smoother, CGS2,
+ * stopping rule, coarse solve) are written out beside each function.
+ *
+ * Parity status: every function below is pinned by the CPU tests against
+ * closed forms, invariants, dense/library special cases or brute force, except
+ * where a header comment says "parity unpinned".
+ */
+#ifndef BCS_ORACLE_H
+#define BCS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Solver settings read by the oracle. Field meaning matches the library's
+ * configuration; the two structs are deliberately separate definitions. */
+typedef struct {
+  int solver;            /* 0 = FGMRES(restart), 1 = BiCGStab */
+  int restart;           /* FGMRES restart length m */
+  double tol;            /* relative residual target ||b - A x|| / ||b|| */
+  int maxiter;           /* total Krylov iterations allowed */
+  int precond;           /* 0 = AMG V-cycle, 1 = none, 2 = block Jacobi (one sweep) */
+  int pmode;             /* 0 = smoothed prolongation, 1 = tentative (default) */
+  int matching_rounds;   /* synchronous handshake rounds per matching pass */
+  int agg_passes;        /* matching passes per level (2 gives aggregates of ~4) */
+  double jacobi_omega;   /* damped block-Jacobi weight */
+  int nu1, nu2;          /* pre / post smoothing sweeps */
+  int coarse_size;       /* stop coarsening when rows <= coarse_size */
+  int max_levels;        /* hierarchy depth limit */
+  double max_coarsen_ratio; /* stop if C_{l+1} > ratio * C_l */
+  double p_omega;        /* prolongation smoothing numerator: omega_P = p_omega / rho */
+  int coarse_dense_max;  /* dense inverse at the coarsest level if rows*n <= this */
+  int coarse_sweeps;     /* otherwise this many block-Jacobi sweeps */
+} or_config;
+
+typedef struct {
+  int status;            /* 0 ok, 4 not converged, 5 breakdown, 6 singular block */
+  int iters;
+  int restarts;
+  double rel_res_initial;
+  double rel_res_final;  /* true residual, recomputed */
+  int levels;
+} or_result;
+
+void or_config_default(or_config* cfg);
+
+/* LDU addressing check: returns 0 when valid; 1 when C < 1, F < 0, an index is
+ * out of range, owner == neighbour, or a face (as an unordered pair) repeats. */
+int or_ldu_check(int C, int F, const int32_t* owner, const int32_t* neighbour);
+
+/* Block-CSR structure of the LDU matrix (Sec. 2.3). Rows hold the diagonal and
+ * one block per face touching the row, columns strictly ascending.
+ * row_ptr[C+1], col[C+2F], pos_diag[C], pos_up[F], pos_lo[F]. Returns the
+ * result of or_ldu_check. */
+int or_ldu_structure(int C, int F, const int32_t* owner, const int32_t* neighbour,
+                     int32_t* row_ptr, int32_t* col, int32_t* pos_diag,
+                     int32_t* pos_up, int32_t* pos_lo);
+
+/* BSR values from LDU block arrays (Alg. 1, LDU -> block CSR permutation). */
+void or_ldu_values(int C, int F, int n, const int32_t* pos_diag, const int32_t* pos_up,
+                   const int32_t* pos_lo, const double* diag, const double* upper,
+                   const double* lower, double* val);
+
+/* Inverse of or_ldu_values: BSR values back to LDU block arrays. */
+void or_bsr_to_ldu(int C, int F, int n, const int32_t* pos_diag, const int32_t* pos_up,
+                   const int32_t* pos_lo, const double* val, double* diag, double* upper,
+                   double* lower);
+
+/* y = A x for a BSR matrix with `rows` block rows (Eq. 1 left-hand side). */
+void or_bsr_spmv(int rows, int n, const int32_t* row_ptr, const int32_t* col,
+                 const double* val, const double* x, double* y);
+
+/* Gauss-Jordan inverse with implicit partial pivoting of an N x N row-major
+ * matrix. Returns 0, or 1 when a pivot is exactly zero. */
+int or_dense_inverse(int N, const double* A, double* Ainv);
+
+/* Frobenius norm of each n x n block (fma accumulation, row-major order). */
+void or_block_norms(int nblocks, int n, const double* val, double* nrm);
+
+/* One aggregation level: matching passes + leftovers + canonical numbering.
+ * agg[rows] receives aggregate ids; returns the number of aggregates. */
+int or_aggregate(int rows, int n, const int32_t* row_ptr, const int32_t* col,
+                 const double* val, const or_config* cfg, int32_t* agg);
+
+/* ---- AMG hierarchy ---------------------------------------------------- */
+typedef struct or_amg or_amg;
+
+/* Full setup from a fine BSR matrix (values copied). *status: 0 ok,
+ * 6 singular block. */
+or_amg* or_amg_setup(int rows, int n, const int32_t* row_ptr, const int32_t* col,
+                     const double* val, const or_config* cfg, int* status);
+/* Values-only resetup: same aggregates and sparsity, new fine values. */
+int or_amg_resetup(or_amg* h, const double* val);
+void or_amg_free(or_amg* h);
+int or_amg_levels(const or_amg* h);
+/* Sizes of level l: block rows, nnz blocks of A_l, nnz blocks of P_l (0 at
+ * the coarsest level), coarse_kind (0 dense inverse, 1 smoother sweeps,
+ * -1 not the coarsest). */
+void or_amg_level_info(const or_amg* h, int l, int* rows, int* nnz, int* p_nnz,
+                       int* coarse_kind);
+/* Copies of level-l data; any pointer may be NULL. */
+void or_amg_get_A(const or_amg* h, int l, int32_t* row_ptr, int32_t* col, double* val);
+void or_amg_get_P(const or_amg* h, int l, int32_t* row_ptr, int32_t* col, double* val,
+                  int32_t* agg, double* omega_p);
+void or_amg_get_dinv(const or_amg* h, int l, double* dinv);
+void or_amg_get_coarse_inverse(const or_amg* h, double* inv);
+/* z = M^{-1} v: one V-cycle from a zero initial guess. */
+void or_amg_vcycle(const or_amg* h, const double* v, double* z);
+
+/* Solve A x = b (x holds x0 on entry). h may be NULL when cfg->precond != 0. */
+int or_solve(int rows, int n, const int32_t* row_ptr, const int32_t* col,
+             const double* val, const or_amg* h, const or_config* cfg,
+             const double* b, double* x, or_result* res, double* hist, int hist_len);
+
+/* Arnoldi check hook: runs j_steps of FGMRES's Arnoldi process from x0 = 0 and
+ * returns V (j+1 vectors) and Z (j vectors), H ((j+1) x j, row-major). */
+int or_fgmres_arnoldi(int rows, int n, const int32_t* row_ptr, const int32_t* col,
+                      const double* val, const or_amg* h, const or_config* cfg,
+                      const double* b, int j_steps, double* V, double* Z, double* H);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
