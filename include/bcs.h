@@ -1,0 +1,204 @@
+/*
+ * bcs.h - block-coupled sparse solver for one B300 GPU (C ABI).
+ *
+ * Solves A x = b where A is the block-coupled matrix of Eq. 1 (Sec. 2):
+ *     A_ii U_i + sum_{j in N(i)} A_ij U_j = b_i,
+ * every A_ij a dense n x n block (n = 5 for the density-based solver of
+ * Sec. 2.1, n = 4 for the pressure-based solver of Sec. 2.2; any 1 <= n <= 8
+ * is accepted). The matrix arrives in OpenFOAM's LDU face form (Sec. 2.3):
+ * per internal face f an owner cell owner[f] and a neighbour cell
+ * neighbour[f]; upper[f] is the block at (row owner, column neighbour),
+ * lower[f] the block at (row neighbour, column owner); diag[i] is A_ii. Blocks
+ * are stored "block AoS" (Sec. 2.3): each block row-major, blocks
+ * concatenated; vectors are cell-major, component-minor ([cell][n]).
+ *
+ * The calls follow the paper's per-iteration procedure (Alg. 1): create a
+ * solver once; upload the face addressing on the first iteration or after a
+ * topology change (bcs_set_structure); upload coefficients every iteration
+ * (bcs_set_values: the first upload after a structure change runs the full
+ * AMG setup, later ones replace values on the fixed sparsity); solve b -> x to
+ * a relative tolerance (bcs_solve); read iterations and residuals
+ * (bcs_result); destroy on the final iteration. The solver is a Krylov method
+ * (FGMRES or BiCGStab, Sec. 2.3) preconditioned with aggregation AMG.
+ *
+ * Memory: every pointer argument is either host memory (mem = BCS_MEM_HOST)
+ * or device memory of the solver's device (mem = BCS_MEM_DEVICE), as the
+ * argument's comment says. The caller owns every array it passes; the library
+ * copies what it keeps, so inputs may be freed once the call returns. Every
+ * call below synchronises the solver's stream before returning.
+ *
+ * Errors: every call returns a bcs_status; no call aborts the process. The
+ * message of the last failure is available from bcs_last_error(). After
+ * BCS_ECUDA the solver should be destroyed.
+ */
+#ifndef BCS_H
+#define BCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bcs_status {
+  BCS_OK = 0,
+  BCS_EINVAL = 1,          /* invalid argument or addressing */
+  BCS_ENOMEM = 2,          /* device allocation failed */
+  BCS_ECUDA = 3,           /* CUDA runtime error */
+  BCS_NOT_CONVERGED = 4,   /* maxiter reached above the tolerance */
+  BCS_BREAKDOWN = 5,       /* NaN/Inf or a Krylov breakdown */
+  BCS_SINGULAR_BLOCK = 6,  /* a diagonal block (or the coarse matrix) is singular */
+  BCS_TIMEOUT = 7,         /* a bounded device wait gave up */
+  BCS_REJECTED = 8,        /* serving: request does not fit the memory budget */
+  BCS_ESTATE = 9           /* call out of order (e.g. solve before set_values) */
+} bcs_status;
+
+enum { BCS_MEM_HOST = 0, BCS_MEM_DEVICE = 1 };
+enum { BCS_FGMRES = 0, BCS_BICGSTAB = 1 };
+enum { BCS_PC_AMG = 0, BCS_PC_NONE = 1, BCS_PC_JACOBI = 2 };
+enum { BCS_P_SMOOTHED = 0, BCS_P_TENTATIVE = 1 };
+enum { BCS_PREC_FP64 = 0, BCS_PREC_FP32 = 1, BCS_PREC_BF16 = 2 };
+
+/* Solver options (Alg. 1: "initialize with linear solver options"). Fill with
+ * bcs_config_default(), then override fields. */
+typedef struct bcs_config {
+  int solver;              /* BCS_FGMRES (default) or BCS_BICGSTAB */
+  int restart;             /* FGMRES restart length m (default 30, 1..64) */
+  double tol;              /* stop when ||b - A x||_2 / ||b||_2 <= tol (1e-8) */
+  int maxiter;             /* Krylov iteration cap (1000) */
+  int precond;             /* BCS_PC_AMG (default), BCS_PC_NONE, BCS_PC_JACOBI */
+  int pmode;               /* BCS_P_TENTATIVE (default) or BCS_P_SMOOTHED */
+  int matching_rounds;     /* handshake rounds per matching pass (4) */
+  int agg_passes;          /* matching passes per level (2: aggregates of ~4) */
+  double jacobi_omega;     /* damped block-Jacobi weight (0.8) */
+  int nu1, nu2;            /* pre / post smoothing sweeps (2, 2) */
+  int coarse_size;         /* stop coarsening at <= this many block rows (128) */
+  int max_levels;          /* hierarchy depth cap (20) */
+  double max_coarsen_ratio;/* stop when C_{l+1} > ratio * C_l (0.8) */
+  double p_omega;          /* smoothed P: omega_P = p_omega / rho_hat (4/3) */
+  int coarse_dense_max;    /* dense inverse at the coarsest level when rows*n <= this (1024) */
+  int coarse_sweeps;       /* else this many block-Jacobi sweeps there (8) */
+  int precision;           /* AMG storage: BCS_PREC_FP64, BCS_PREC_FP32 (default), BCS_PREC_BF16 */
+  int profile;             /* 1: time kernels with CUDA events (bcs_get_stats) */
+} bcs_config;
+
+typedef struct bcs_result {
+  int status;              /* bcs_status of the solve */
+  int iters;               /* Krylov iterations (BiCGStab: one per two V-cycles) */
+  int restarts;            /* FGMRES restarts / BiCGStab restarts */
+  int levels;              /* AMG levels */
+  double rel_res_initial;  /* ||b - A x0|| / ||b|| */
+  double rel_res_final;    /* true residual ||b - A x|| / ||b|| recomputed in FP64 */
+  double setup_ms;         /* last set_values (conversion + AMG setup), wall time */
+  double solve_ms;         /* this solve, wall time */
+} bcs_result;
+
+/* Per-kernel-kind statistics since creation or the last bcs_reset_stats. */
+#define BCS_NUM_KERNEL_KINDS 16
+typedef struct bcs_stats {
+  long long launches;                         /* kernels launched by this solver */
+  long long kind_launches[BCS_NUM_KERNEL_KINDS];
+  double kind_ms[BCS_NUM_KERNEL_KINDS];       /* CUDA-event time (profile = 1 only) */
+  double kind_bytes[BCS_NUM_KERNEL_KINDS];    /* algorithmic bytes moved */
+  double kind_flops[BCS_NUM_KERNEL_KINDS];    /* algorithmic flops */
+} bcs_stats;
+
+typedef struct bcs_solver bcs_solver;
+
+/* Fill cfg with defaults. Returns BCS_EINVAL when cfg is NULL. */
+bcs_status bcs_config_default(bcs_config* cfg);
+
+/* Create a solver for n x n blocks (1 <= n <= 8) on the current CUDA device.
+ * stream: a cudaStream_t the solver launches on (NULL = legacy default
+ * stream). cfg may be NULL (defaults). *out receives the handle.
+ * BCS_EINVAL for a bad n or an option out of range. */
+bcs_status bcs_create(bcs_solver** out, int n, const bcs_config* cfg, void* stream);
+
+/* Destroy the solver and free its device memory. NULL is accepted. */
+bcs_status bcs_destroy(bcs_solver* s);
+
+/* Replace the options. A change of any AMG field (or the precision) drops the
+ * hierarchy, so the next set_values runs a full setup. */
+bcs_status bcs_set_config(bcs_solver* s, const bcs_config* cfg);
+
+/* Upload the LDU face addressing (Alg. 1, first iteration / topology change):
+ * n_cells C >= 1, n_faces F >= 0, owner[F] and neighbour[F] int32 cell ids
+ * (host or device per mem). Builds the block-CSR structure on the device:
+ * per row the diagonal plus one block per face, columns ascending.
+ * owner > neighbour is accepted (upper is still the (owner, neighbour) block).
+ * BCS_EINVAL: C < 1, F < 0, an id out of range, owner == neighbour, or a
+ * repeated face (unordered pair); the solver then has no structure. Drops any
+ * AMG hierarchy and values. */
+bcs_status bcs_set_structure(bcs_solver* s, int32_t n_cells, int32_t n_faces,
+                             const int32_t* owner, const int32_t* neighbour, int mem);
+
+/* Upload coefficients (Alg. 1, every iteration): diag[C][n][n],
+ * upper[F][n][n] (block (owner, neighbour)), lower[F][n][n] (block
+ * (neighbour, owner)), FP64 row-major, host or device per mem. Permutes them
+ * into block-CSR order (Alg. 1, LDU -> block CSR) and then runs the full AMG
+ * setup if no hierarchy exists, else a values-only resetup that keeps the
+ * aggregates and every sparsity pattern. BCS_ESTATE before set_structure;
+ * BCS_SINGULAR_BLOCK when a diagonal block or the coarsest matrix is
+ * singular (the hierarchy is then dropped). */
+bcs_status bcs_set_values(bcs_solver* s, const double* diag, const double* upper,
+                          const double* lower, int mem);
+
+/* Forget the hierarchy: the next set_values runs a full setup (new
+ * aggregates). */
+bcs_status bcs_invalidate_hierarchy(bcs_solver* s);
+
+/* Solve A x = b: b[C][n] FP64; x[C][n] FP64 holds the initial guess on entry
+ * and the solution on exit (both host or both device per mem). res may be
+ * NULL. Returns BCS_OK when the true relative residual is <= tol,
+ * BCS_NOT_CONVERGED at maxiter, BCS_BREAKDOWN on NaN/Inf or breakdown;
+ * x holds the last iterate in every case. b = 0 gives x = 0 and BCS_OK.
+ * BCS_ESTATE before set_values. */
+bcs_status bcs_solve(bcs_solver* s, const double* b, double* x, int mem, bcs_result* res);
+
+/* y = A x with the fine matrix in FP64 (Eq. 1 left-hand side); x, y [C][n]
+ * host or device per mem. BCS_ESTATE before set_values. */
+bcs_status bcs_spmv(bcs_solver* s, const double* x, double* y, int mem);
+
+/* z = M^{-1} v: one application of the configured preconditioner (one AMG
+ * V-cycle from zero) in the configured precision, returned in FP64. */
+bcs_status bcs_precond_apply(bcs_solver* s, const double* v, double* z, int mem);
+
+/* Test hooks: copies of internal state to HOST arrays (any may be NULL).
+ * bcs_get_bsr: row_ptr[C+1], col[nnz], val[nnz][n][n] of the fine matrix and
+ * the LDU -> BSR maps pos_diag[C], pos_up[F], pos_lo[F]. */
+bcs_status bcs_get_bsr(bcs_solver* s, int32_t* row_ptr, int32_t* col, double* val,
+                       int32_t* pos_diag, int32_t* pos_up, int32_t* pos_lo);
+/* Number of AMG levels (0 without a hierarchy). */
+int bcs_num_levels(const bcs_solver* s);
+/* Sizes of level l: block rows, nnz blocks of A_l, nnz blocks of P_l (0 at
+ * the coarsest level or in tentative mode), coarse_kind (-1 not coarsest,
+ * 0 dense inverse, 1 smoother sweeps). */
+bcs_status bcs_get_level_info(const bcs_solver* s, int l, int* rows, int* nnz, int* p_nnz,
+                              int* coarse_kind);
+/* FP64 level data: A_l (row_ptr, col, val), aggregate map agg[rows] (not at
+ * the coarsest level), block inverses dinv[rows][n][n]. */
+bcs_status bcs_get_level(bcs_solver* s, int l, int32_t* row_ptr, int32_t* col, double* val,
+                         int32_t* agg, double* dinv);
+/* Smoothed prolongation of level l (pmode smoothed only) and omega_P. */
+bcs_status bcs_get_prolongation(bcs_solver* s, int l, int32_t* row_ptr, int32_t* col,
+                                double* val, double* omega_p);
+/* Dense inverse of the coarsest matrix, [N][N] with N = rows * n. */
+bcs_status bcs_get_coarse_inverse(bcs_solver* s, double* inv);
+
+/* Statistics (launch counts always; times only with cfg.profile = 1). */
+bcs_status bcs_get_stats(bcs_solver* s, bcs_stats* st);
+bcs_status bcs_reset_stats(bcs_solver* s);
+/* Name of kernel kind k (0 <= k < BCS_NUM_KERNEL_KINDS), "" if unused. */
+const char* bcs_kernel_kind_name(int k);
+
+/* Message for the last failed call on s (never NULL). */
+const char* bcs_last_error(const bcs_solver* s);
+
+/* Device bytes currently held by the solver. */
+size_t bcs_device_bytes(const bcs_solver* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BCS_H */

@@ -1,0 +1,427 @@
+// Block-CSR row kernels (SpMV, residual, damped block-Jacobi sweep), the
+// outer FP64 SpMV (Eq. 1's left-hand side y_i = sum_j A_ij x_j), the
+// inter-grid transfers and the AMG V-cycle built from them.
+//
+// Row mapping: a warp serves floor(32 / n) block rows; lane l handles scalar
+// row r = l % n of block row l / n. The n lanes of a block row sit in one warp
+// and exchange residual components by shuffle for the D^-1 epilogue. Each lane
+// reads its row of every block (n contiguous values) and the matching x
+// block, one fma per matrix entry.
+//
+// V-cycle (reading of the paper's unparameterised "AMG preconditioner"):
+// per level, nu1 damped block-Jacobi sweeps x <- x + w D^-1 (b - A x) (the
+// first from x = 0 is x = w D^-1 b), residual, restriction R = P^T,
+// recursion, prolongation-correction, nu2 sweeps; the coarsest level applies
+// its dense FP64 inverse (or smoother sweeps when too large for one).
+#include "internal.h"
+
+namespace bcs {
+
+namespace {
+
+template <class AT, class T> __device__ __forceinline__ AT lda(const T* p);
+template <> __device__ __forceinline__ double lda<double, double>(const double* p) { return __ldg(p); }
+template <> __device__ __forceinline__ double lda<double, float>(const float* p) { return (double)__ldg(p); }
+template <> __device__ __forceinline__ float lda<float, float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float lda<float, bf16>(const bf16* p) { return __bfloat162float(__ldg(p)); }
+
+template <int N>
+struct RowMap {
+  static constexpr int RPW = 32 / N;  // block rows per warp
+  int rw, r, i;
+  bool active;
+  __device__ explicit RowMap(int rows) {
+    const int lane = threadIdx.x & 31;
+    rw = lane / N;
+    r = lane - rw * N;
+    const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    i = warp * RPW + rw;
+    active = rw < RPW && i < rows;
+  }
+};
+
+template <int N, class AT, class TV, class TX>
+__device__ __forceinline__ AT row_dot(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                      const TV* __restrict__ val, const TX* __restrict__ x, int i, int r) {
+  AT acc = 0;
+  const int kb = __ldg(rp + i), ke = __ldg(rp + i + 1);
+#pragma unroll 2
+  for (int k = kb; k < ke; ++k) {
+    const int j = __ldg(ci + k);
+    const TV* a = val + (size_t)k * (N * N) + r * N;
+    const TX* xj = x + (size_t)j * N;
+#pragma unroll
+    for (int c = 0; c < N; ++c) acc = fma(lda<AT>(a + c), lda<AT>(xj + c), acc);
+  }
+  return acc;
+}
+
+// y = A x (M_SPMV), y += A x (M_ADD), y = b - A x (M_RESID).
+template <int N, class AT, class TV, class TX, class TY, int MODE>
+__global__ void __launch_bounds__(128) k_rows(int rows, const int32_t* __restrict__ rp,
+                                              const int32_t* __restrict__ ci, const TV* __restrict__ val,
+                                              const TX* __restrict__ x, TY* __restrict__ y,
+                                              const TY* __restrict__ b) {
+  RowMap<N> m(rows);
+  if (!m.active) return;
+  const AT acc = row_dot<N, AT>(rp, ci, val, x, m.i, m.r);
+  const size_t o = (size_t)m.i * N + m.r;
+  if (MODE == M_SPMV) y[o] = (TY)acc;
+  else if (MODE == M_ADD) y[o] = (TY)((AT)y[o] + acc);
+  else y[o] = (TY)((AT)b[o] - acc);
+}
+
+// y = x + omega D^-1 (b - A x)
+template <int N, class AT, class TV, class TD, class TC>
+__global__ void __launch_bounds__(128) k_jacobi(int rows, const int32_t* __restrict__ rp,
+                                                const int32_t* __restrict__ ci, const TV* __restrict__ val,
+                                                const TD* __restrict__ dinv, const TC* __restrict__ x,
+                                                const TC* __restrict__ b, TC* __restrict__ y, AT omega) {
+  RowMap<N> m(rows);
+  AT res = 0;
+  if (m.active) res = (AT)b[(size_t)m.i * N + m.r] - row_dot<N, AT>(rp, ci, val, x, m.i, m.r);
+  AT t = 0;
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    const AT rc = __shfl_sync(0xffffffffu, res, (m.rw * N + c) & 31);
+    if (m.active) t = fma((AT)dinv[((size_t)m.i * N + m.r) * N + c], rc, t);
+  }
+  if (m.active) {
+    const size_t o = (size_t)m.i * N + m.r;
+    y[o] = (TC)((AT)x[o] + omega * t);
+  }
+}
+
+// y = omega D^-1 b (first sweep from a zero guess)
+template <int N, class AT, class TD, class TC>
+__global__ void k_jacobi0(int rows, const TD* __restrict__ dinv, const TC* __restrict__ b, TC* __restrict__ y,
+                          AT omega) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)rows * N) return;
+  const size_t i = t / N;
+  const int r = (int)(t - i * N);
+  AT acc = 0;
+#pragma unroll
+  for (int c = 0; c < N; ++c) acc = fma((AT)dinv[(i * N + r) * N + c], (AT)b[i * N + c], acc);
+  y[t] = (TC)(omega * acc);
+}
+
+// Tentative transfers: restriction b_c[I] = sum of r over I's members
+// (ascending), prolongation-correction x[i] += x_c[agg[i]].
+template <int N, class AT, class TC>
+__global__ void k_restrict_tent(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
+                                const TC* __restrict__ r, TC* __restrict__ bc) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)nagg * N) return;
+  const size_t I = t / N;
+  const int c = (int)(t - I * N);
+  AT acc = 0;
+  for (int q = mptr[I]; q < mptr[I + 1]; ++q) acc += (AT)r[(size_t)mem[q] * N + c];
+  bc[t] = (TC)acc;
+}
+
+template <int N, class TC>
+__global__ void k_prolong_tent(int rows, const int32_t* __restrict__ agg, const TC* __restrict__ xc,
+                               TC* __restrict__ x) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)rows * N) return;
+  const size_t i = t / N;
+  const int c = (int)(t - i * N);
+  x[t] = x[t] + xc[(size_t)agg[i] * N + c];
+}
+
+// Coarsest level: x = Ainv b with the dense FP64 inverse, warp per row.
+template <class TC>
+__global__ void k_coarse_gemv(int Nc, const double* __restrict__ inv, const TC* __restrict__ b,
+                              TC* __restrict__ x) {
+  const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= Nc) return;
+  double acc = 0.0;
+  for (int c = lane; c < Nc; c += 32) acc = fma(inv[(size_t)row * Nc + c], (double)b[c], acc);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+  if (lane == 0) x[row] = (TC)acc;
+}
+
+template <class TI, class TO>
+__global__ void k_cast(size_t n, const TI* __restrict__ in, TO* __restrict__ out) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    out[t] = (TO)in[t];
+}
+
+__global__ void k_cast_bf16(size_t n, const double* __restrict__ in, bf16* __restrict__ out) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    out[t] = __double2bfloat16(in[t]);
+}
+
+unsigned rows_grid(int rows, int n) {
+  const int rpw = 32 / n;
+  const size_t warps = ((size_t)rows + rpw - 1) / rpw;
+  return grid_for(warps * 32, 128);
+}
+
+}  // namespace
+
+template <class TI, class TO>
+bcs_status cast_vec(Solver* s, const TI* in, TO* out, size_t N) {
+  unsigned g = grid_for(N, 256);
+  if (g > 148u * 16u) g = 148u * 16u;
+  if constexpr (std::is_same<TO, bf16>::value) {
+    BCS_LAUNCH(s, K_CAST, (double)N * (sizeof(TI) + sizeof(TO)), 0, k_cast_bf16, g, 256, 0, N, in, out);
+  } else {
+    BCS_LAUNCH(s, K_CAST, (double)N * (sizeof(TI) + sizeof(TO)), 0, (k_cast<TI, TO>), g, 256, 0, N, in, out);
+  }
+  return BCS_OK;
+}
+template bcs_status cast_vec<double, float>(Solver*, const double*, float*, size_t);
+template bcs_status cast_vec<float, double>(Solver*, const float*, double*, size_t);
+template bcs_status cast_vec<double, double>(Solver*, const double*, double*, size_t);
+template bcs_status cast_vec<double, bf16>(Solver*, const double*, bf16*, size_t);
+
+bool cycle_is_float(const Solver* s) {
+  return s->setup_cfg.precond == BCS_PC_AMG && s->setup_cfg.precision != BCS_PREC_FP64;
+}
+
+// ------------------------------------------------------------ outer FP64 SpMV
+bcs_status spmv64(Solver* s, const Bsr& A, const void* x, bool x_is_float, double* y, const double* b,
+                  int kind) {
+  const int rows = A.rows;
+  return with_n(s->n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    const double bytes = (double)A.nnz * (N * N * 8 + 4) + 4.0 * (rows + 1) +
+                         (double)rows * N * ((x_is_float ? 4 : 8) + 8 + (b ? 8 : 0));
+    const double flops = 2.0 * A.nnz * N * N;
+    const unsigned g = rows_grid(rows, N);
+    if (x_is_float) {
+      if (b)
+        BCS_LAUNCH(s, kind, bytes, flops, (k_rows<N, double, double, float, double, M_RESID>), g, 128, 0, rows,
+                   A.rp.p, A.ci.p, A.v.p, (const float*)x, y, b);
+      else
+        BCS_LAUNCH(s, kind, bytes, flops, (k_rows<N, double, double, float, double, M_SPMV>), g, 128, 0, rows,
+                   A.rp.p, A.ci.p, A.v.p, (const float*)x, y, b);
+    } else {
+      if (b)
+        BCS_LAUNCH(s, kind, bytes, flops, (k_rows<N, double, double, double, double, M_RESID>), g, 128, 0, rows,
+                   A.rp.p, A.ci.p, A.v.p, (const double*)x, y, b);
+      else
+        BCS_LAUNCH(s, kind, bytes, flops, (k_rows<N, double, double, double, double, M_SPMV>), g, 128, 0, rows,
+                   A.rp.p, A.ci.p, A.v.p, (const double*)x, y, b);
+    }
+    return BCS_OK;
+  });
+}
+
+// ------------------------------------------------------------------- V-cycle
+namespace {
+
+// Typed views of a cycle with matrix storage TV, inverse storage TD, vector
+// type TC and accumulator AT.
+template <class TV, class TD, class TC, class AT>
+struct Cycle {
+  Solver* s;
+  static const TV* mat(const Level& L);
+  static const TD* dinv(const Level& L);
+  static const TV* pmat(const Level& L);
+  static const TV* rmat(const Level& L);
+
+  template <int N>
+  bcs_status sweep0(const Level& L, const TC* b, TC* y) {
+    const int rows = L.A.rows;
+    const AT om = (AT)s->setup_cfg.jacobi_omega;
+    BCS_LAUNCH(s, K_SWEEP, (double)rows * N * (N * sizeof(TD) + 2 * sizeof(TC)), 2.0 * rows * N * N,
+               (k_jacobi0<N, AT, TD, TC>), grid_for((size_t)rows * N, 256), 256, 0, rows, dinv(L), b, y, om);
+    return BCS_OK;
+  }
+  template <int N>
+  bcs_status sweep(const Level& L, const TC* x, const TC* b, TC* y) {
+    const int rows = L.A.rows;
+    const AT om = (AT)s->setup_cfg.jacobi_omega;
+    const double bytes = (double)L.A.nnz * (N * N * sizeof(TV) + 4) + 4.0 * (rows + 1) +
+                         (double)rows * N * (N * sizeof(TD) + 3 * sizeof(TC));
+    BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_jacobi<N, AT, TV, TD, TC>),
+               rows_grid(rows, N), 128, 0, rows, L.A.rp.p, L.A.ci.p, mat(L), dinv(L), x, b, y, om);
+    return BCS_OK;
+  }
+  template <int N>
+  bcs_status resid(const Level& L, const TC* x, const TC* b, TC* r) {
+    const int rows = L.A.rows;
+    const double bytes = (double)L.A.nnz * (N * N * sizeof(TV) + 4) + 4.0 * (rows + 1) +
+                         (double)rows * N * 3 * sizeof(TC);
+    BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_rows<N, AT, TV, TC, TC, M_RESID>), rows_grid(rows, N),
+               128, 0, rows, L.A.rp.p, L.A.ci.p, mat(L), x, r, b);
+    return BCS_OK;
+  }
+  template <int N>
+  bcs_status restrict_(const Level& L, const TC* r, TC* bc) {
+    if (s->setup_cfg.pmode == BCS_P_TENTATIVE) {
+      BCS_LAUNCH(s, K_TRANSFER, (double)(L.A.rows + L.nagg) * N * sizeof(TC) + 4.0 * L.A.rows, 0,
+                 (k_restrict_tent<N, AT, TC>), grid_for((size_t)L.nagg * N, 256), 256, 0, L.nagg, L.mptr.p,
+                 L.mem.p, r, bc);
+    } else {
+      const Bsr& R = L.R;
+      BCS_LAUNCH(s, K_TRANSFER, (double)R.nnz * (N * N * sizeof(TV) + 4), 2.0 * R.nnz * N * N,
+                 (k_rows<N, AT, TV, TC, TC, M_SPMV>), rows_grid(R.rows, N), 128, 0, R.rows, R.rp.p, R.ci.p,
+                 rmat(L), r, bc, (const TC*)nullptr);
+    }
+    return BCS_OK;
+  }
+  template <int N>
+  bcs_status prolong(const Level& L, const TC* xc, TC* x) {
+    if (s->setup_cfg.pmode == BCS_P_TENTATIVE) {
+      BCS_LAUNCH(s, K_TRANSFER, (double)L.A.rows * N * 3 * sizeof(TC) + 4.0 * L.A.rows, 0,
+                 (k_prolong_tent<N, TC>), grid_for((size_t)L.A.rows * N, 256), 256, 0, L.A.rows, L.agg.p, xc, x);
+    } else {
+      const Bsr& P = L.P;
+      BCS_LAUNCH(s, K_TRANSFER, (double)P.nnz * (N * N * sizeof(TV) + 4), 2.0 * P.nnz * N * N,
+                 (k_rows<N, AT, TV, TC, TC, M_ADD>), rows_grid(P.rows, N), 128, 0, P.rows, P.rp.p, P.ci.p,
+                 pmat(L), xc, x, (const TC*)nullptr);
+    }
+    return BCS_OK;
+  }
+
+  // count >= 1 sweeps from zero; the start buffer is chosen so the last
+  // sweep lands in x.
+  template <int N>
+  bcs_status sweeps_from_zero(const Level& L, int count, const TC* b, TC* x, TC* tmp) {
+    TC* cur = ((count - 1) % 2 == 0) ? x : tmp;
+    TC* alt = cur == x ? tmp : x;
+    BCS_OKR(sweep0<N>(L, b, cur));
+    for (int k = 1; k < count; ++k) {
+      BCS_OKR(sweep<N>(L, cur, b, alt));
+      std::swap(cur, alt);
+    }
+    return BCS_OK;
+  }
+
+  template <int N>
+  bcs_status run(int l, const TC* b, TC* x) {
+    Level& L = s->lv[l];
+    const int nu1 = s->setup_cfg.nu1, nu2 = s->setup_cfg.nu2;
+    TC* tmp = (TC*)L.vt.p;
+    if (L.coarse_kind == 0) {
+      BCS_LAUNCH(s, K_COARSE, 8.0 * s->cN * s->cN, 2.0 * s->cN * s->cN, k_coarse_gemv<TC>,
+                 grid_for((size_t)s->cN * 32, 256), 256, 0, s->cN, s->cinv.p, b, x);
+      return BCS_OK;
+    }
+    if (L.coarse_kind == 1) return sweeps_from_zero<N>(L, s->setup_cfg.coarse_sweeps, b, x, tmp);
+    const int swaps = (nu1 > 1 ? nu1 - 1 : 0) + nu2;
+    TC* cur = swaps % 2 == 0 ? x : tmp;
+    TC* alt = cur == x ? tmp : x;
+    if (nu1 >= 1) {
+      BCS_OKR(sweep0<N>(L, b, cur));
+      for (int k = 1; k < nu1; ++k) {
+        BCS_OKR(sweep<N>(L, cur, b, alt));
+        std::swap(cur, alt);
+      }
+    } else {
+      BCS_CU(s, cudaMemsetAsync(cur, 0, (size_t)L.A.rows * N * sizeof(TC), s->stream));
+    }
+    Level& Lc = s->lv[l + 1];
+    TC* r = (TC*)L.vr.p;
+    BCS_OKR(resid<N>(L, cur, b, r));
+    BCS_OKR(restrict_<N>(L, r, (TC*)Lc.vb.p));
+    BCS_OKR(run<N>(l + 1, (const TC*)Lc.vb.p, (TC*)Lc.vx.p));
+    BCS_OKR(prolong<N>(L, (const TC*)Lc.vx.p, cur));
+    for (int k = 0; k < nu2; ++k) {
+      BCS_OKR(sweep<N>(L, cur, b, alt));
+      std::swap(cur, alt);
+    }
+    return BCS_OK;
+  }
+};
+
+template <> const double* Cycle<double, double, double, double>::mat(const Level& L) { return L.A.v.p; }
+template <> const double* Cycle<double, double, double, double>::dinv(const Level& L) { return L.dinv.p; }
+template <> const double* Cycle<double, double, double, double>::pmat(const Level& L) { return L.P.v.p; }
+template <> const double* Cycle<double, double, double, double>::rmat(const Level& L) { return L.R.v.p; }
+template <> const float* Cycle<float, float, float, float>::mat(const Level& L) { return L.v32.p; }
+template <> const float* Cycle<float, float, float, float>::dinv(const Level& L) { return L.dinv32.p; }
+template <> const float* Cycle<float, float, float, float>::pmat(const Level& L) { return L.P32.p; }
+template <> const float* Cycle<float, float, float, float>::rmat(const Level& L) { return L.R32.p; }
+template <> const bf16* Cycle<bf16, float, float, float>::mat(const Level& L) { return L.v16.p; }
+template <> const float* Cycle<bf16, float, float, float>::dinv(const Level& L) { return L.dinv32.p; }
+template <> const bf16* Cycle<bf16, float, float, float>::pmat(const Level& L) { return L.P16.p; }
+template <> const bf16* Cycle<bf16, float, float, float>::rmat(const Level& L) { return L.R16.p; }
+
+template <class TV, class TD, class TC, class AT>
+bcs_status run_cycle(Solver* s, const TC* b, TC* x) {
+  Cycle<TV, TD, TC, AT> c{s};
+  return with_n(s->n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    return c.template run<N>(0, b, x);
+  });
+}
+
+}  // namespace
+
+// Cycle vectors and storage copies of the hierarchy in the configured
+// precision (after every setup / resetup).
+bcs_status cycle_prepare(Solver* s) {
+  const int prec = s->setup_cfg.precision;
+  const size_t vsz = prec == BCS_PREC_FP64 ? sizeof(double) : sizeof(float);
+  const int n = s->n, nn = n * n;
+  for (size_t l = 0; l < s->lv.size(); ++l) {
+    Level& L = s->lv[l];
+    const size_t N = (size_t)L.A.rows * n;
+    BCS_ALLOC(s, L.vx, N * vsz);
+    BCS_ALLOC(s, L.vb, N * vsz);
+    BCS_ALLOC(s, L.vr, N * vsz);
+    BCS_ALLOC(s, L.vt, N * vsz);
+    if (prec == BCS_PREC_FP64 || s->setup_cfg.precond != BCS_PC_AMG) continue;
+    BCS_ALLOC(s, L.dinv32, (size_t)L.A.rows * nn);
+    BCS_OKR(cast_vec<double, float>(s, L.dinv.p, L.dinv32.p, (size_t)L.A.rows * nn));
+    const size_t an = (size_t)L.A.nnz * nn;
+    const bool smoothed = L.coarse_kind < 0 && s->setup_cfg.pmode == BCS_P_SMOOTHED;
+    if (prec == BCS_PREC_FP32) {
+      BCS_ALLOC(s, L.v32, an);
+      BCS_OKR(cast_vec<double, float>(s, L.A.v.p, L.v32.p, an));
+      if (smoothed) {
+        BCS_ALLOC(s, L.P32, (size_t)L.P.nnz * nn);
+        BCS_ALLOC(s, L.R32, (size_t)L.R.nnz * nn);
+        BCS_OKR(cast_vec<double, float>(s, L.P.v.p, L.P32.p, (size_t)L.P.nnz * nn));
+        BCS_OKR(cast_vec<double, float>(s, L.R.v.p, L.R32.p, (size_t)L.R.nnz * nn));
+      }
+    } else {
+      BCS_ALLOC(s, L.v16, an);
+      BCS_OKR(cast_vec<double, bf16>(s, L.A.v.p, L.v16.p, an));
+      if (smoothed) {
+        BCS_ALLOC(s, L.P16, (size_t)L.P.nnz * nn);
+        BCS_ALLOC(s, L.R16, (size_t)L.R.nnz * nn);
+        BCS_OKR(cast_vec<double, bf16>(s, L.P.v.p, L.P16.p, (size_t)L.P.nnz * nn));
+        BCS_OKR(cast_vec<double, bf16>(s, L.R.v.p, L.R16.p, (size_t)L.R.nnz * nn));
+      }
+    }
+  }
+  return BCS_OK;
+}
+
+// z = M^{-1} v in the cycle precision; v is FP64 (a Krylov vector).
+bcs_status precond_apply(Solver* s, const double* v, void* z) {
+  Level& L0 = s->lv[0];
+  const size_t N = (size_t)L0.A.rows * s->n;
+  switch (s->setup_cfg.precision) {
+    case BCS_PREC_FP64:
+      return run_cycle<double, double, double, double>(s, v, (double*)z);
+    case BCS_PREC_FP32:
+      BCS_OKR(cast_vec<double, float>(s, v, (float*)L0.vb.p, N));
+      return run_cycle<float, float, float, float>(s, (const float*)L0.vb.p, (float*)z);
+    default:
+      BCS_OKR(cast_vec<double, float>(s, v, (float*)L0.vb.p, N));
+      return run_cycle<bf16, float, float, float>(s, (const float*)L0.vb.p, (float*)z);
+  }
+}
+
+// Block-Jacobi preconditioner (one undamped block solve): z = D^-1 v.
+bcs_status jacobi_apply(Solver* s, const double* v, double* z) {
+  Level& L0 = s->lv[0];
+  return with_n(s->n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    const int rows = L0.A.rows;
+    BCS_LAUNCH(s, K_SWEEP, (double)rows * N * (N * 8 + 16), 2.0 * rows * N * N, (k_jacobi0<N, double, double, double>),
+               grid_for((size_t)rows * N, 256), 256, 0, rows, L0.dinv.p, v, z, 1.0);
+    return BCS_OK;
+  });
+}
+
+}  // namespace bcs

@@ -1,0 +1,265 @@
+// Internal declarations of the block-coupled solver library (not installed).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <utility>
+#include <vector>
+
+#include "../../include/bcs.h"
+
+namespace bcs {
+
+using bf16 = __nv_bfloat16;
+
+// Kernel kinds for launch counting and event timing.
+enum Kind {
+  K_CONVERT = 0,    // LDU -> BSR structure / value permutation
+  K_SPMV64 = 1,     // FP64 outer SpMV / true residual
+  K_SWEEP = 2,      // block-Jacobi sweep (SpMV + D^-1 epilogue)
+  K_RESID = 3,      // V-cycle residual
+  K_TRANSFER = 4,   // restriction / prolongation
+  K_COARSE = 5,     // coarsest-level solve
+  K_BLAS = 6,       // dots, norms, axpy, Gram-Schmidt
+  K_SETUP_AGG = 7,  // strength, matching, numbering
+  K_SETUP_GAL = 8,  // Galerkin products, prolongation
+  K_SETUP_INV = 9,  // block inverses, coarse inverse
+  K_CAST = 10,      // precision casts
+  K_MISC = 11,      // scans, sorts
+  K_NKINDS = 12
+};
+const char* kind_name(int k);
+
+// ------------------------------------------------------------ device memory
+// Stream-ordered allocations (cudaMallocAsync) on the solver's stream.
+struct Alloc {
+  cudaStream_t stream = nullptr;
+  size_t live = 0;
+  void* get(size_t bytes);
+  void put(void* p, size_t bytes);
+};
+
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  Alloc* a = nullptr;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept { *this = std::move(o); }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p;
+      n = o.n;
+      a = o.a;
+      o.p = nullptr;
+      o.n = 0;
+    }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void release() {
+    if (p && a) a->put(p, n * sizeof(T));
+    p = nullptr;
+    n = 0;
+  }
+  // (Re)allocates when the size differs; contents undefined. False on OOM.
+  bool resize(Alloc* al, size_t count) {
+    if (count == n && (p || count == 0)) return true;
+    release();
+    a = al;
+    if (count == 0) return true;
+    p = static_cast<T*>(al->get(count * sizeof(T)));
+    if (!p) return false;
+    n = count;
+    return true;
+  }
+};
+
+// ----------------------------------------------------------- data structures
+// Block-CSR matrix on the device; values FP64 (setup precision).
+struct Bsr {
+  int rows = 0, cols = 0, nnz = 0;
+  DBuf<int32_t> rp, ci;
+  DBuf<double> v;
+};
+
+struct Level {
+  Bsr A;                     // FP64 operator of this level
+  DBuf<int32_t> dpos;        // diagonal block position per row
+  DBuf<double> dinv;         // FP64 diagonal block inverses
+  DBuf<float> v32, dinv32;   // storage copies for the V-cycle
+  DBuf<bf16> v16;
+  // transfer to level l+1 (absent at the coarsest level)
+  int nagg = 0;
+  DBuf<int32_t> agg;         // aggregate of each row
+  DBuf<int32_t> mptr, mem;   // aggregate member lists (members ascending)
+  Bsr P, R, AP;              // smoothed mode only (FP64)
+  DBuf<int32_t> Prow, Rrow, AProw, Crow;  // row of every nonzero of P, R, AP, A_{l+1}
+  DBuf<float> P32, R32;
+  DBuf<bf16> P16, R16;
+  double omega_p = 0.0;
+  int coarse_kind = -1;      // -1 not coarsest, 0 dense inverse, 1 sweeps
+  DBuf<char> vx, vb, vr, vt; // V-cycle vectors (cycle precision)
+};
+
+struct Timer {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+struct Solver {
+  int n = 0;
+  bcs_config cfg{};
+  bcs_config setup_cfg{};        // options the hierarchy was built with
+  cudaStream_t stream = nullptr;
+  Alloc alloc;
+  std::string err;
+  // structure
+  int C = 0, F = 0, nnz = 0;
+  bool have_structure = false, have_values = false, have_hierarchy = false;
+  DBuf<int32_t> src;             // BSR position -> LDU source code
+  DBuf<int32_t> pos_diag, pos_up, pos_lo;
+  DBuf<double> stage_d, stage_u, stage_l;  // host-input staging
+  DBuf<int32_t> stage_o, stage_n;
+  // hierarchy
+  std::vector<Level> lv;
+  DBuf<double> cinv;             // coarsest dense inverse (FP64)
+  int cN = 0;
+  // Krylov work space
+  DBuf<double> kv;               // FGMRES V (m+1 vectors) / BiCGStab vectors
+  DBuf<char> kz;                 // FGMRES Z (m vectors, cycle precision)
+  DBuf<double> kw, kr, kx, kb;
+  DBuf<double> red;              // reduction partials
+  DBuf<double> scal;             // device scalars
+  double* hscal = nullptr;       // pinned host mirror of scal
+  DBuf<int32_t> flag;            // device status flags
+  // statistics
+  long long launches = 0;
+  long long kind_launches[BCS_NUM_KERNEL_KINDS] = {};
+  double kind_bytes[BCS_NUM_KERNEL_KINDS] = {};
+  double kind_flops[BCS_NUM_KERNEL_KINDS] = {};
+  double kind_ms[BCS_NUM_KERNEL_KINDS] = {};
+  std::vector<Timer> timers;
+  std::vector<cudaEvent_t> event_pool;
+  size_t event_next = 0;
+  double last_setup_ms = 0.0;
+
+  bcs_status fail(bcs_status st, const std::string& m) {
+    err = m;
+    return st;
+  }
+  void pre(int kind);
+  bcs_status post(int kind, const char* what, double bytes, double flops);
+  void flush_timers();
+};
+
+#define BCS_CU(S, call)                                                                \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return (S)->fail(BCS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define BCS_OKR(...)                \
+  do {                              \
+    bcs_status st_ = (__VA_ARGS__); \
+    if (st_ != BCS_OK) return st_;  \
+  } while (0)
+#define BCS_ALLOC(S, buf, count)                                                        \
+  do {                                                                                  \
+    if (!(buf).resize(&(S)->alloc, (count)))                                            \
+      return (S)->fail(BCS_ENOMEM, std::string("device allocation failed: ") + #buf);   \
+  } while (0)
+
+// Launch kernel<<<grid, block, smem, s->stream>>>(args...) with bookkeeping.
+#define BCS_LAUNCH(S, KIND, BYTES, FLOPS, kernel, grid, block, smem, ...)  \
+  do {                                                                    \
+    (S)->pre(KIND);                                                       \
+    kernel<<<(grid), (block), (smem), (S)->stream>>>(__VA_ARGS__);         \
+    bcs_status st_ = (S)->post(KIND, #kernel, (BYTES), (FLOPS));          \
+    if (st_ != BCS_OK) return st_;                                        \
+  } while (0)
+
+inline unsigned grid_for(size_t work, int block) {
+  size_t g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// Block-size dispatch: calls f(std::integral_constant<int, N>) for n = 1..8.
+template <class F>
+bcs_status with_n(int n, F&& f) {
+  switch (n) {
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 3: return f(std::integral_constant<int, 3>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 5: return f(std::integral_constant<int, 5>{});
+    case 6: return f(std::integral_constant<int, 6>{});
+    case 7: return f(std::integral_constant<int, 7>{});
+    case 8: return f(std::integral_constant<int, 8>{});
+    default: return BCS_EINVAL;
+  }
+}
+
+// ------------------------------------------------------------------ format.cu
+bcs_status build_structure(Solver* s, const int32_t* owner_d, const int32_t* nb_d);
+bcs_status permute_values(Solver* s, const double* diag_d, const double* upper_d,
+                          const double* lower_d);
+
+// -------------------------------------------------------------------- scan.cu
+// out[0..n] = exclusive prefix sums of in[0..n-1]; out[n] = total. Device.
+bcs_status exclusive_scan(Solver* s, const int32_t* in, int32_t* out, int n);
+// Per-segment sort + unique of int keys: seg_ptr[rows+1] delimits segments of
+// keys; on return count[r] holds the unique count of segment r and the
+// segment starts with its sorted unique keys. max_len bounds the segments.
+bcs_status segmented_sort_unique(Solver* s, const int32_t* seg_ptr, int32_t* keys,
+                                 int32_t* count, int rows, int max_len);
+
+// -------------------------------------------------------------------- blas.cu
+// Deterministic FP64 reductions into s->scal[slot...].
+bcs_status dot(Solver* s, const double* x, const double* y, size_t N, int slot);
+bcs_status multidot(Solver* s, const double* V, size_t ldv, int k, const double* w, size_t N,
+                    int slot);
+bcs_status fetch_scalars(Solver* s, int count);  // scal[0..count) -> hscal, synchronises
+bcs_status axpby(Solver* s, double a, const double* x, double b, double* y, size_t N);
+bcs_status scale_copy(Solver* s, double a, const double* x, double* y, size_t N);
+bcs_status gs_update(Solver* s, const double* V, size_t ldv, int k, const double* hdev, double* w,
+                     size_t N);
+bcs_status add_combination(Solver* s, const void* Z, bool z_float, size_t ldz, int k,
+                           const double* ydev, double* x, size_t N);
+bcs_status bicg_p_update(Solver* s, double beta, double omega, const double* r, const double* v,
+                         double* p, size_t N);
+bcs_status bicg_x_update(Solver* s, double alpha, const double* ph, double omega, const double* sh,
+                         double* x, size_t N);
+
+// ------------------------------------------------------------------- cycle.cu
+enum Mode { M_SPMV = 0, M_ADD = 1, M_RESID = 2 };
+// y = A x (b == nullptr) or y = b - A x with the FP64 matrix; x double or float.
+bcs_status spmv64(Solver* s, const Bsr& A, const void* x, bool x_is_float, double* y,
+                  const double* b, int kind);
+bcs_status cycle_prepare(Solver* s);
+bcs_status precond_apply(Solver* s, const double* v, void* z);  // z in cycle precision
+bcs_status jacobi_apply(Solver* s, const double* v, double* z);
+bool cycle_is_float(const Solver* s);
+template <class TI, class TO>
+bcs_status cast_vec(Solver* s, const TI* in, TO* out, size_t N);
+
+// ------------------------------------------------------------------- setup.cu
+bcs_status amg_setup(Solver* s, bool full);
+
+// ------------------------------------------------------------------ krylov.cu
+bcs_status solve(Solver* s, const double* b_d, double* x_d, bcs_result* res);
+
+}  // namespace bcs
+
+struct bcs_solver {
+  bcs::Solver impl;
+};

@@ -1,0 +1,210 @@
+// Device prefix sums and per-segment sort/unique used by the structure and
+// setup phases (row pointers, sparsity patterns of Galerkin products).
+#include <climits>
+
+#include "internal.h"
+
+namespace bcs {
+
+namespace {
+
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Block-local exclusive scan of one tile; writes the tile total.
+__global__ void k_scan_tile(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                            int32_t* __restrict__ tile_sum, int n) {
+  __shared__ int32_t warp_tot[SCAN_THREADS / 32];
+  const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  int32_t v[SCAN_ITEMS];
+  int32_t local = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int i = base + k;
+    v[k] = i < n ? in[i] : 0;
+    local += v[k];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t incl = local;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int32_t w = lane < SCAN_THREADS / 32 ? warp_tot[lane] : 0;
+    int32_t wi = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t t = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) wi += t;
+    }
+    if (lane < SCAN_THREADS / 32) warp_tot[lane] = wi - w;  // exclusive warp offsets
+    if (lane == SCAN_THREADS / 32 - 1) tile_sum[blockIdx.x] = wi;
+  }
+  __syncthreads();
+  int32_t run = warp_tot[warp] + incl - local;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int i = base + k;
+    if (i < n) out[i] = run;
+    run += v[k];
+  }
+}
+
+__global__ void k_scan_add(int32_t* __restrict__ out, const int32_t* __restrict__ tile_off, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += tile_off[i / SCAN_TILE];
+}
+
+__global__ void k_scan_total(const int32_t* __restrict__ in, int32_t* __restrict__ out, int n) {
+  out[n] = out[n - 1] + in[n - 1];
+}
+
+}  // namespace
+
+bcs_status exclusive_scan(Solver* s, const int32_t* in, int32_t* out, int n) {
+  if (n <= 0) {
+    BCS_CU(s, cudaMemsetAsync(out, 0, sizeof(int32_t), s->stream));
+    return BCS_OK;
+  }
+  const int tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  DBuf<int32_t> sums, offs;
+  BCS_ALLOC(s, sums, tiles);
+  BCS_ALLOC(s, offs, tiles + 1);
+  BCS_LAUNCH(s, K_MISC, 8.0 * n, 0, k_scan_tile, tiles, SCAN_THREADS, 0, in, out, sums.p, n);
+  if (tiles > 1) {
+    BCS_OKR(exclusive_scan(s, sums.p, offs.p, tiles));
+    BCS_LAUNCH(s, K_MISC, 8.0 * n, 0, k_scan_add, grid_for(n, 256), 256, 0, out, offs.p, n);
+  }
+  BCS_LAUNCH(s, K_MISC, 0, 0, k_scan_total, 1, 1, 0, in, out, n);
+  return BCS_OK;
+}
+
+// ------------------------------------------------------------------ sort/unique
+namespace {
+
+constexpr int WARP_SEG_MAX = 256;  // segments up to this length: one warp
+constexpr int WARPS_PER_BLOCK = 4;
+constexpr int BLOCK_SEG_MAX = 16384;
+
+__global__ void k_seg_sort_warp(const int32_t* __restrict__ seg_ptr, int32_t* __restrict__ keys,
+                                int32_t* __restrict__ count, int32_t* __restrict__ long_rows,
+                                int32_t* __restrict__ n_long, int rows) {
+  __shared__ int32_t sm[WARPS_PER_BLOCK][WARP_SEG_MAX];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * WARPS_PER_BLOCK + warp;
+  if (r >= rows) return;
+  const int b = seg_ptr[r], len = seg_ptr[r + 1] - b;
+  if (len > WARP_SEG_MAX) {
+    if (lane == 0) long_rows[atomicAdd(n_long, 1)] = r;
+    return;
+  }
+  int32_t* a = sm[warp];
+  int S = 32;
+  while (S < len) S <<= 1;
+  for (int i = lane; i < S; i += 32) a[i] = i < len ? keys[b + i] : INT_MAX;
+  __syncwarp();
+  for (int k = 2; k <= S; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < S; i += 32) {
+        const int l = i ^ j;
+        if (l > i) {
+          const int32_t x = a[i], y = a[l];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  int outpos = 0;
+  for (int i0 = 0; i0 < len; i0 += 32) {
+    const int i = i0 + lane;
+    const bool keep = i < len && (i == 0 || a[i] != a[i - 1]);
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) keys[b + outpos + __popc(m & ((1u << lane) - 1u))] = a[i];
+    outpos += __popc(m);
+  }
+  if (lane == 0) count[r] = outpos;
+}
+
+__global__ void k_seg_sort_block(const int32_t* __restrict__ seg_ptr, int32_t* __restrict__ keys,
+                                 int32_t* __restrict__ count, const int32_t* __restrict__ long_rows) {
+  extern __shared__ int32_t a[];
+  __shared__ int32_t wsum[32];
+  const int r = long_rows[blockIdx.x];
+  const int b = seg_ptr[r], len = seg_ptr[r + 1] - b;
+  int S = 32;
+  while (S < len) S <<= 1;
+  for (int i = threadIdx.x; i < S; i += blockDim.x) a[i] = i < len ? keys[b + i] : INT_MAX;
+  __syncthreads();
+  for (int k = 2; k <= S; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < S; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const int32_t x = a[i], y = a[l];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int base = 0;
+  for (int i0 = 0; i0 < len; i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    const bool keep = i < len && (i == 0 || a[i] != a[i - 1]);
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wsum[warp] = __popc(m);
+    __syncthreads();
+    int off = base, tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) off += wsum[w];
+      tot += wsum[w];
+    }
+    if (keep) keys[b + off + __popc(m & ((1u << lane) - 1u))] = a[i];
+    base += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) count[r] = base;
+}
+
+}  // namespace
+
+bcs_status segmented_sort_unique(Solver* s, const int32_t* seg_ptr, int32_t* keys, int32_t* count,
+                                 int rows, int max_len) {
+  if (rows <= 0) return BCS_OK;
+  if (max_len > BLOCK_SEG_MAX)
+    return s->fail(BCS_EINVAL, "a sparsity-pattern row has more than 16384 candidate entries");
+  DBuf<int32_t> long_rows, aux;
+  BCS_ALLOC(s, long_rows, rows);
+  BCS_ALLOC(s, aux, 1);
+  BCS_CU(s, cudaMemsetAsync(aux.p, 0, sizeof(int32_t), s->stream));
+  BCS_LAUNCH(s, K_MISC, 0, 0, k_seg_sort_warp, grid_for(rows, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, 0,
+             seg_ptr, keys, count, long_rows.p, aux.p, rows);
+  if (max_len > WARP_SEG_MAX) {
+    int32_t h = 0;
+    BCS_CU(s, cudaMemcpyAsync(&h, aux.p, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    BCS_CU(s, cudaStreamSynchronize(s->stream));
+    if (h > 0) {
+      int S = 32;
+      while (S < max_len) S <<= 1;
+      const size_t smem = (size_t)S * sizeof(int32_t);
+      BCS_CU(s, cudaFuncSetAttribute(k_seg_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      BCS_LAUNCH(s, K_MISC, 0, 0, k_seg_sort_block, h, 512, smem, seg_ptr, keys, count, long_rows.p);
+    }
+  }
+  return BCS_OK;
+}
+
+}  // namespace bcs

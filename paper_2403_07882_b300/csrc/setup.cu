@@ -1,0 +1,964 @@
+// Aggregation AMG setup for block-coupled systems (Sec. 2.3: aggregation
+// AMG built by graph matching; block smoothers). All setup arithmetic is FP64
+// and every value is produced by one thread in a fixed operation order with
+// explicit fma, so the hierarchy is identical bit for bit across runs and
+// equal to the CPU reference's.
+//
+// Reading of the unstated rules (the paper names graph matching only):
+//  * strength: w_ij = (N(A_ij) + N(A_ji)) / (2 max(N(A_ii), N(A_jj))),
+//    N = Frobenius norm (fma sum of squares in row-major order, then sqrt);
+//  * synchronous handshake matching rounds: each unmatched row picks the
+//    unmatched neighbour of largest positive weight (smaller index on ties),
+//    mutual picks pair up;
+//  * unmatched rows join the aggregate of their strongest matched neighbour,
+//    if any; aggregates are numbered by ascending smallest member;
+//  * a second pass repeats this on the aggregate graph (block sums), giving
+//    aggregates of about four rows;
+//  * Galerkin coarse operator R A P with R = P^T; P tentative (identity
+//    blocks, the default) or smoothed (I - omega_P D^-1 A) P_tent with
+//    omega_P = p_omega / max_i sum_j ||D_i^-1 A_ij||_inf;
+//  * block inverses by Gauss-Jordan with implicit partial pivoting;
+//  * coarsest level: dense Gauss-Jordan inverse (FP64), applied as a GEMV.
+#include <cooperative_groups.h>
+
+#include <climits>
+
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace bcs {
+
+namespace {
+
+__device__ __forceinline__ int find_col(const int32_t* __restrict__ ci, int b, int e, int j) {
+  while (b < e) {
+    const int m = (b + e) >> 1;
+    const int c = ci[m];
+    if (c == j) return m;
+    if (c < j) b = m + 1;
+    else e = m;
+  }
+  return -1;
+}
+
+__global__ void k_diag_pos(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           int32_t* __restrict__ dpos, int32_t* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const int p = find_col(ci, rp[i], rp[i + 1], i);
+  dpos[i] = p;
+  if (p < 0) atomicOr(err, 4);
+}
+
+// Gauss-Jordan inverse of one N x N block per thread: implicit partial
+// pivoting (largest |M[r][k]| among unused rows, first on ties), deferred
+// normalisation, updates M[r][j] = fma(-l, M[p][j], M[r][j]) for j >= k.
+template <int N>
+__global__ void k_block_inverse(int rows, const int32_t* __restrict__ dpos, const double* __restrict__ val,
+                                double* __restrict__ dinv, int32_t* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const int dp = dpos[i];
+  if (dp < 0) return;
+  double M[N][2 * N];
+  const double* a = val + (size_t)dp * N * N;
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      M[r][c] = a[r * N + c];
+      M[r][N + c] = r == c ? 1.0 : 0.0;
+    }
+  bool used[N];
+  int prow[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) used[r] = false;
+  for (int k = 0; k < N; ++k) {
+    int p = 0;
+    double best = -1.0;
+    for (int r = 0; r < N; ++r) {
+      if (used[r]) continue;
+      const double v = fabs(M[r][k]);
+      if (v > best) {
+        best = v;
+        p = r;
+      }
+    }
+    const double piv = M[p][k];
+    if (piv == 0.0) {
+      atomicOr(err, 8);
+      return;
+    }
+    used[p] = true;
+    prow[k] = p;
+    for (int r = 0; r < N; ++r) {
+      if (r == p) continue;
+      const double l = M[r][k] / piv;
+      for (int j = k; j < 2 * N; ++j) M[r][j] = fma(-l, M[p][j], M[r][j]);
+    }
+  }
+  double* o = dinv + (size_t)i * N * N;
+  for (int k = 0; k < N; ++k) {
+    const int p = prow[k];
+    const double d = M[p][k];
+    for (int j = 0; j < N; ++j) o[k * N + j] = M[p][N + j] / d;
+  }
+}
+
+template <int NN>
+__global__ void k_block_norms(int nnz, const double* __restrict__ val, double* __restrict__ nrm) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnz) return;
+  const double* a = val + (size_t)k * NN;
+  double acc = 0.0;
+#pragma unroll
+  for (int e = 0; e < NN; ++e) acc = fma(a[e], a[e], acc);
+  nrm[k] = sqrt(acc);
+}
+
+__global__ void k_row_index(int rows, const int32_t* __restrict__ rp, int32_t* __restrict__ ridx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) ridx[k] = i;
+}
+
+__global__ void k_weights(int nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const int32_t* __restrict__ ridx, const int32_t* __restrict__ dpos,
+                          const double* __restrict__ nrm, double* __restrict__ w) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnz) return;
+  const int i = ridx[k], j = ci[k];
+  if (i == j) {
+    w[k] = 0.0;
+    return;
+  }
+  const int kt = find_col(ci, rp[j], rp[j + 1], i);
+  const double s = nrm[k] + (kt >= 0 ? nrm[kt] : 0.0);
+  const double di = dpos[i] >= 0 ? nrm[dpos[i]] : 0.0;
+  const double dj = dpos[j] >= 0 ? nrm[dpos[j]] : 0.0;
+  const double d = 2.0 * (di < dj ? dj : di);
+  w[k] = d > 0.0 ? s / d : 0.0;
+}
+
+__global__ void k_choose(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const double* __restrict__ w, const int32_t* __restrict__ mate,
+                         int32_t* __restrict__ choice) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  int best = -1;
+  if (mate[i] < 0) {
+    double bw = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const int j = ci[k];
+      if (j == i || mate[j] >= 0) continue;
+      if (w[k] > bw) {
+        bw = w[k];
+        best = j;
+      }
+    }
+  }
+  choice[i] = best;
+}
+
+__global__ void k_pair(int rows, const int32_t* __restrict__ choice, int32_t* __restrict__ mate) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const int c = choice[i];
+  if (mate[i] < 0 && c >= 0 && choice[c] == i) mate[i] = c;
+}
+
+__global__ void k_root(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                       const double* __restrict__ w, const int32_t* __restrict__ mate,
+                       int32_t* __restrict__ root, int32_t* __restrict__ amin) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  int r;
+  if (mate[i] >= 0) {
+    r = min(i, mate[i]);
+  } else {
+    int best = -1;
+    double bw = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const int j = ci[k];
+      if (j == i || mate[j] < 0) continue;
+      if (w[k] > bw) {
+        bw = w[k];
+        best = j;
+      }
+    }
+    r = best >= 0 ? min(best, mate[best]) : i;
+  }
+  root[i] = r;
+  atomicMin(&amin[r], i);
+}
+
+__global__ void k_is_min(int rows, const int32_t* __restrict__ root, const int32_t* __restrict__ amin,
+                         int32_t* __restrict__ flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < rows) flag[i] = amin[root[i]] == i ? 1 : 0;
+}
+
+__global__ void k_assign(int rows, const int32_t* __restrict__ root, const int32_t* __restrict__ amin,
+                         const int32_t* __restrict__ id, int32_t* __restrict__ agg) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < rows) agg[i] = id[amin[root[i]]];
+}
+
+__global__ void k_compose(int rows, const int32_t* __restrict__ a2, int32_t* __restrict__ agg) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < rows) agg[i] = a2[agg[i]];
+}
+
+__global__ void k_fill_int(int32_t* __restrict__ a, int n, int v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+__global__ void k_count_by(int m, const int32_t* __restrict__ key, int32_t* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) atomicAdd(&cnt[key[i]], 1);
+}
+
+// out[ptr[key[q]] + slot] = val ? val[q] : q
+__global__ void k_place_by(int m, const int32_t* __restrict__ key, const int32_t* __restrict__ val,
+                           const int32_t* __restrict__ ptr, int32_t* __restrict__ cursor,
+                           int32_t* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < m) out[ptr[key[q]] + atomicAdd(&cursor[key[q]], 1)] = val ? val[q] : q;
+}
+
+__global__ void k_max_int(int n, const int32_t* __restrict__ a, int32_t* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicMax(out, a[i]);
+}
+
+__global__ void k_compact(int rows, const int32_t* __restrict__ cptr, const int32_t* __restrict__ cand,
+                          const int32_t* __restrict__ rp, int32_t* __restrict__ ci) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const int b = cptr[i], o = rp[i], len = rp[i + 1] - rp[i];
+  for (int q = 0; q < len; ++q) ci[o + q] = cand[b + q];
+}
+
+// Candidates of the tentative Galerkin pattern: row I gathers agg(col) over
+// the rows of its members.
+__global__ void k_cand_count_tent(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
+                                  const int32_t* __restrict__ rp, int32_t* __restrict__ cnt) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nagg) return;
+  int c = 0;
+  for (int q = mptr[I]; q < mptr[I + 1]; ++q) c += rp[mem[q] + 1] - rp[mem[q]];
+  cnt[I] = c;
+}
+
+__global__ void k_cand_fill_tent(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
+                                 const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                 const int32_t* __restrict__ agg, const int32_t* __restrict__ cptr,
+                                 int32_t* __restrict__ cand) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nagg) return;
+  int o = cptr[I];
+  for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
+    const int i = mem[q];
+    for (int k = rp[i]; k < rp[i + 1]; ++k) cand[o++] = agg[ci[k]];
+  }
+}
+
+// R A P with tentative P: block (I, J) = sum over members i of I
+// (ascending) of [sum over row i's blocks k (ascending) with agg(col k) = J
+// of A_k], each sum a plain left-to-right FP64 add from +0. (This is the
+// general product with identity blocks: fma(a, 1, acc) = acc + a and
+// fma(a, 0, acc) = acc.)
+template <int NN>
+__global__ void k_gal_tent_values(int cnnz, const int32_t* __restrict__ crow, const int32_t* __restrict__ cci,
+                                  const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
+                                  const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                  const double* __restrict__ val, const int32_t* __restrict__ agg,
+                                  double* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= cnnz) return;
+  const int I = crow[q], J = cci[q];
+  double acc[NN];
+#pragma unroll
+  for (int e = 0; e < NN; ++e) acc[e] = 0.0;
+  for (int m = mptr[I]; m < mptr[I + 1]; ++m) {
+    const int i = mem[m];
+    double t[NN];
+#pragma unroll
+    for (int e = 0; e < NN; ++e) t[e] = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      if (agg[ci[k]] != J) continue;
+      const double* a = val + (size_t)k * NN;
+#pragma unroll
+      for (int e = 0; e < NN; ++e) t[e] = t[e] + a[e];
+    }
+#pragma unroll
+    for (int e = 0; e < NN; ++e) acc[e] = acc[e] + t[e];
+  }
+  double* o = out + (size_t)q * NN;
+#pragma unroll
+  for (int e = 0; e < NN; ++e) o[e] = acc[e];
+}
+
+// ----------------------------------------------------- smoothed prolongation
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+template <int N>
+__global__ void k_rho(int rows, const int32_t* __restrict__ rp, const double* __restrict__ val,
+                      const double* __restrict__ dinv, double* __restrict__ rho) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const double* D = dinv + (size_t)i * N * N;
+  double s = 0.0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) {
+    const double* a = val + (size_t)k * N * N;
+    double mx = 0.0;
+    for (int r = 0; r < N; ++r) {
+      double rs = 0.0;
+      for (int c = 0; c < N; ++c) {
+        double t = 0.0;
+        for (int m = 0; m < N; ++m) t = fma(D[r * N + m], a[m * N + c], t);
+        rs = rs + fabs(t);
+      }
+      if (rs > mx) mx = rs;
+    }
+    s = s + mx;
+  }
+  atomic_max_nonneg(rho, s);
+}
+
+__global__ void k_cand_count_p(int rows, const int32_t* __restrict__ rp, int32_t* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < rows) cnt[i] = rp[i + 1] - rp[i];
+}
+
+__global__ void k_cand_fill_p(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                              const int32_t* __restrict__ agg, int32_t* __restrict__ cand) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) cand[k] = agg[ci[k]];
+}
+
+// P block (i, J) = fma(-omega, D_i^-1 S_iJ, delta), S_iJ = sum (row order) of
+// A_ik over neighbours k in aggregate J.
+template <int N>
+__global__ void k_p_values(int pnnz, const int32_t* __restrict__ prow, const int32_t* __restrict__ pci,
+                           const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ val, const double* __restrict__ dinv,
+                           const int32_t* __restrict__ agg, double omega, double* __restrict__ pv) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= pnnz) return;
+  const int i = prow[q], J = pci[q];
+  double S[N * N];
+#pragma unroll
+  for (int e = 0; e < N * N; ++e) S[e] = 0.0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) {
+    if (agg[ci[k]] != J) continue;
+    const double* a = val + (size_t)k * N * N;
+#pragma unroll
+    for (int e = 0; e < N * N; ++e) S[e] = S[e] + a[e];
+  }
+  const double* D = dinv + (size_t)i * N * N;
+  const bool own = agg[i] == J;
+  double* o = pv + (size_t)q * N * N;
+  for (int r = 0; r < N; ++r)
+    for (int c = 0; c < N; ++c) {
+      double t = 0.0;
+#pragma unroll
+      for (int m = 0; m < N; ++m) t = fma(D[r * N + m], S[m * N + c], t);
+      o[r * N + c] = fma(-omega, t, (own && r == c) ? 1.0 : 0.0);
+    }
+}
+
+// R block (J, i) = P block (i, J)^T.
+template <int N>
+__global__ void k_transpose_values(int rnnz, const int32_t* __restrict__ rrow, const int32_t* __restrict__ rci,
+                                   const int32_t* __restrict__ prp, const int32_t* __restrict__ pci,
+                                   const double* __restrict__ pv, double* __restrict__ rv) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= rnnz) return;
+  const int J = rrow[q], i = rci[q];
+  const int kk = find_col(pci, prp[i], prp[i + 1], J);
+  const double* a = pv + (size_t)kk * N * N;
+  double* o = rv + (size_t)q * N * N;
+  for (int r = 0; r < N; ++r)
+    for (int c = 0; c < N; ++c) o[r * N + c] = a[c * N + r];
+}
+
+// General block SpGEMM C = A B.
+__global__ void k_cand_count_gemm(int rows, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                                  const int32_t* __restrict__ brp, int32_t* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  int c = 0;
+  for (int k = arp[i]; k < arp[i + 1]; ++k) c += brp[aci[k] + 1] - brp[aci[k]];
+  cnt[i] = c;
+}
+
+__global__ void k_cand_fill_gemm(int rows, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                                 const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
+                                 const int32_t* __restrict__ cptr, int32_t* __restrict__ cand) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  int o = cptr[i];
+  for (int k = arp[i]; k < arp[i + 1]; ++k) {
+    const int j = aci[k];
+    for (int kk = brp[j]; kk < brp[j + 1]; ++kk) cand[o++] = bci[kk];
+  }
+}
+
+// C_iJ[r][c] = over k of A's row i (ascending), then m ascending,
+// fma(A_ik[r][m], B_kJ[m][c], acc), from +0.
+template <int N>
+__global__ void k_gemm_values(int cnnz, const int32_t* __restrict__ crow, const int32_t* __restrict__ cci,
+                              const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                              const double* __restrict__ av, const int32_t* __restrict__ brp,
+                              const int32_t* __restrict__ bci, const double* __restrict__ bv,
+                              double* __restrict__ cv) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= cnnz) return;
+  const int i = crow[q], J = cci[q];
+  double acc[N * N];
+#pragma unroll
+  for (int e = 0; e < N * N; ++e) acc[e] = 0.0;
+  for (int k = arp[i]; k < arp[i + 1]; ++k) {
+    const int j = aci[k];
+    const int kk = find_col(bci, brp[j], brp[j + 1], J);
+    if (kk < 0) continue;
+    const double* a = av + (size_t)k * N * N;
+    const double* b = bv + (size_t)kk * N * N;
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+      for (int c = 0; c < N; ++c)
+#pragma unroll
+        for (int m = 0; m < N; ++m) acc[r * N + c] = fma(a[r * N + m], b[m * N + c], acc[r * N + c]);
+  }
+  double* o = cv + (size_t)q * N * N;
+#pragma unroll
+  for (int e = 0; e < N * N; ++e) o[e] = acc[e];
+}
+
+// ------------------------------------------------------------ coarse inverse
+__global__ void k_dense_from_bsr(int rows, int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                 const double* __restrict__ val, double* __restrict__ M, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const size_t W = 2 * (size_t)N;
+  for (int r = 0; r < n; ++r) {
+    double* row = M + (size_t)(i * n + r) * W;
+    for (size_t j = 0; j < W; ++j) row[j] = 0.0;
+    row[N + i * n + r] = 1.0;
+  }
+  for (int k = rp[i]; k < rp[i + 1]; ++k)
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c)
+        M[(size_t)(i * n + r) * W + ci[k] * n + c] = val[(size_t)k * n * n + r * n + c];
+}
+
+// Gauss-Jordan on [A | I] (N x 2N) over a cooperative grid, one grid barrier
+// per pivot step. Step k: every block finds the same pivot among the unused
+// rows from colbuf[k & 1] (column k as it stood after step k-1); each block
+// updates its own rows i != p for columns j >= k and records their column
+// k+1 in colbuf[(k + 1) & 1]; the pivot row is only read in step k.
+__global__ void k_gauss_jordan(int N, double* __restrict__ M, double* __restrict__ colbuf,
+                               int32_t* __restrict__ prow_out, int32_t* __restrict__ err) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ unsigned char used[];  // N flags
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_p;
+  __shared__ double s_l;
+  const size_t W = 2 * (size_t)N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) used[i] = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+    colbuf[i] = M[(size_t)i * W];
+  grid.sync();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = 0; k < N; ++k) {
+    const double* col = colbuf + (size_t)(k & 1) * N;
+    double bv = -1.0;
+    int bi = INT_MAX;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      if (used[i]) continue;
+      const double v = fabs(col[i]);
+      if (v > bv || (v == bv && i < bi)) {
+        bv = v;
+        bi = i;
+      }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, bv, d);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, d);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      red_v[warp] = bv;
+      red_i[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = red_v[0];
+      int p = red_i[0];
+      for (int w = 1; w < nw; ++w)
+        if (red_v[w] > v || (red_v[w] == v && red_i[w] < p)) {
+          v = red_v[w];
+          p = red_i[w];
+        }
+      s_p = p;
+      used[p] = 1;
+      if (blockIdx.x == 0) prow_out[k] = p;
+    }
+    __syncthreads();
+    const int p = s_p;
+    const double* prow = M + (size_t)p * W;
+    const double piv = prow[k];
+    if (piv == 0.0) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 16);
+      return;  // every block sees the same pivot and leaves before the next barrier
+    }
+    double* nxt = colbuf + (size_t)((k + 1) & 1) * N;
+    for (int i = blockIdx.x; i < N; i += gridDim.x) {
+      if (i == p) {
+        if (threadIdx.x == 0 && k + 1 < N) nxt[i] = prow[k + 1];
+        continue;
+      }
+      double* row = M + (size_t)i * W;
+      if (threadIdx.x == 0) s_l = row[k] / piv;
+      __syncthreads();
+      const double l = s_l;
+      for (size_t j = k + threadIdx.x; j < W; j += blockDim.x) row[j] = fma(-l, prow[j], row[j]);
+      __syncthreads();
+      if (threadIdx.x == 0 && k + 1 < N) nxt[i] = row[k + 1];
+    }
+    grid.sync();
+  }
+}
+
+__global__ void k_gj_finish(int N, const double* __restrict__ M, const int32_t* __restrict__ prow,
+                            double* __restrict__ inv) {
+  const size_t W = 2 * (size_t)N;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)N * N;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t / N), j = (int)(t % N);
+    const int p = prow[k];
+    inv[t] = M[(size_t)p * W + N + j] / M[(size_t)p * W + k];
+  }
+}
+
+}  // namespace
+
+// ======================================================================= host
+namespace {
+
+bcs_status read_int(Solver* s, const int32_t* d, int32_t* h) {
+  BCS_CU(s, cudaMemcpyAsync(h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  return BCS_OK;
+}
+
+bcs_status max_of(Solver* s, const int32_t* a, int n, int32_t* out) {
+  DBuf<int32_t> m;
+  BCS_ALLOC(s, m, 1);
+  BCS_CU(s, cudaMemsetAsync(m.p, 0, sizeof(int32_t), s->stream));
+  if (n > 0) BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_max_int, grid_for(n, 256), 256, 0, n, a, m.p);
+  return read_int(s, m.p, out);
+}
+
+// Sorted unique pattern from per-row candidate segments. cnt[rows] holds the
+// candidate counts on entry; fills out.rp / ci / nnz and crow (row of each
+// nonzero).
+template <class FillFn>
+bcs_status pattern_from_candidates(Solver* s, int rows, DBuf<int32_t>& cnt, FillFn fill, Bsr& out,
+                                   DBuf<int32_t>& crow) {
+  DBuf<int32_t> cptr, cand;
+  BCS_ALLOC(s, cptr, rows + 1);
+  BCS_OKR(exclusive_scan(s, cnt.p, cptr.p, rows));
+  int32_t total = 0, mx = 0;
+  BCS_OKR(read_int(s, cptr.p + rows, &total));
+  BCS_ALLOC(s, cand, total > 0 ? total : 1);
+  BCS_OKR(fill(cptr.p, cand.p));
+  BCS_OKR(max_of(s, cnt.p, rows, &mx));
+  BCS_OKR(segmented_sort_unique(s, cptr.p, cand.p, cnt.p, rows, mx));
+  BCS_ALLOC(s, out.rp, rows + 1);
+  BCS_OKR(exclusive_scan(s, cnt.p, out.rp.p, rows));
+  int32_t nnz = 0;
+  BCS_OKR(read_int(s, out.rp.p + rows, &nnz));
+  out.rows = rows;
+  out.nnz = nnz;
+  BCS_ALLOC(s, out.ci, nnz > 0 ? nnz : 1);
+  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_compact, grid_for(rows, 256), 256, 0, rows, cptr.p, cand.p, out.rp.p,
+             out.ci.p);
+  BCS_ALLOC(s, crow, nnz > 0 ? nnz : 1);
+  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_row_index, grid_for(rows, 256), 256, 0, rows, out.rp.p, crow.p);
+  return BCS_OK;
+}
+
+// One matching pass on A (rows x rows): agg[rows]; returns the count.
+bcs_status match_pass(Solver* s, const Bsr& A, DBuf<int32_t>& agg, int* nagg) {
+  const int rows = A.rows, nnz = A.nnz;
+  DBuf<double> nrm, w;
+  DBuf<int32_t> ridx, dpos, mate, choice, root, amin, flag, id;
+  BCS_ALLOC(s, nrm, nnz);
+  BCS_ALLOC(s, w, nnz);
+  BCS_ALLOC(s, ridx, nnz);
+  BCS_ALLOC(s, dpos, rows);
+  BCS_ALLOC(s, mate, rows);
+  BCS_ALLOC(s, choice, rows);
+  BCS_ALLOC(s, root, rows);
+  BCS_ALLOC(s, amin, rows);
+  BCS_ALLOC(s, flag, rows);
+  BCS_ALLOC(s, id, rows + 1);
+  BCS_ALLOC(s, agg, rows);
+  const unsigned gr = grid_for(rows, 256), gn = grid_for(nnz, 256);
+  BCS_OKR(with_n(s->n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    BCS_LAUNCH(s, K_SETUP_AGG, 8.0 * nnz * (N * N + 1), 2.0 * nnz * N * N, k_block_norms<N * N>, gn, 256, 0, nnz,
+               A.v.p, nrm.p);
+    return BCS_OK;
+  }));
+  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_row_index, gr, 256, 0, rows, A.rp.p, ridx.p);
+  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_diag_pos, gr, 256, 0, rows, A.rp.p, A.ci.p, dpos.p, s->flag.p);
+  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_weights, gn, 256, 0, nnz, A.rp.p, A.ci.p, ridx.p, dpos.p, nrm.p, w.p);
+  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_fill_int, gr, 256, 0, mate.p, rows, -1);
+  // A round that pairs nobody leaves the state unchanged, so running every
+  // round equals stopping at the first idle one.
+  for (int round = 0; round < s->setup_cfg.matching_rounds; ++round) {
+    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_choose, gr, 256, 0, rows, A.rp.p, A.ci.p, w.p, mate.p, choice.p);
+    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_pair, gr, 256, 0, rows, choice.p, mate.p);
+  }
+  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_fill_int, gr, 256, 0, amin.p, rows, INT_MAX);
+  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_root, gr, 256, 0, rows, A.rp.p, A.ci.p, w.p, mate.p, root.p, amin.p);
+  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_is_min, gr, 256, 0, rows, root.p, amin.p, flag.p);
+  BCS_OKR(exclusive_scan(s, flag.p, id.p, rows));
+  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_assign, gr, 256, 0, rows, root.p, amin.p, id.p, agg.p);
+  int32_t na = 0;
+  BCS_OKR(read_int(s, id.p + rows, &na));
+  *nagg = na;
+  return BCS_OK;
+}
+
+// Member lists of an aggregation: mptr[nagg+1], mem (members ascending).
+bcs_status members(Solver* s, int rows, int nagg, const int32_t* agg, DBuf<int32_t>& mptr,
+                   DBuf<int32_t>& mem) {
+  DBuf<int32_t> cnt, cursor;
+  BCS_ALLOC(s, cnt, nagg);
+  BCS_ALLOC(s, cursor, nagg);
+  BCS_ALLOC(s, mptr, nagg + 1);
+  BCS_ALLOC(s, mem, rows);
+  BCS_CU(s, cudaMemsetAsync(cnt.p, 0, nagg * sizeof(int32_t), s->stream));
+  BCS_CU(s, cudaMemsetAsync(cursor.p, 0, nagg * sizeof(int32_t), s->stream));
+  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_count_by, grid_for(rows, 256), 256, 0, rows, agg, cnt.p);
+  BCS_OKR(exclusive_scan(s, cnt.p, mptr.p, nagg));
+  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_place_by, grid_for(rows, 256), 256, 0, rows, agg, (const int32_t*)nullptr,
+             mptr.p, cursor.p, mem.p);
+  int32_t mx = 0;
+  BCS_OKR(max_of(s, cnt.p, nagg, &mx));
+  // members are distinct: sort/unique keeps the counts and sorts each list
+  return segmented_sort_unique(s, mptr.p, mem.p, cnt.p, nagg, mx);
+}
+
+bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, const int32_t* mptr,
+                        const int32_t* mem, Bsr& Ac, DBuf<int32_t>& crow) {
+  DBuf<int32_t> cnt;
+  BCS_ALLOC(s, cnt, nagg);
+  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p,
+             cnt.p);
+  auto fill = [&](const int32_t* cptr, int32_t* cand) -> bcs_status {
+    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_fill_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p,
+               A.ci.p, agg, cptr, cand);
+    return BCS_OK;
+  };
+  BCS_OKR(pattern_from_candidates(s, nagg, cnt, fill, Ac, crow));
+  Ac.cols = nagg;
+  return BCS_OK;
+}
+
+bcs_status tent_values(Solver* s, const Bsr& A, const int32_t* agg, const int32_t* mptr, const int32_t* mem,
+                       Bsr& Ac, const int32_t* crow) {
+  const int n = s->n;
+  BCS_ALLOC(s, Ac.v, (size_t)Ac.nnz * n * n);
+  return with_n(n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + Ac.nnz) * N * N, 1.0 * A.nnz * N * N, k_gal_tent_values<N * N>,
+               grid_for(Ac.nnz, 128), 128, 0, Ac.nnz, crow, Ac.ci.p, mptr, mem, A.rp.p, A.ci.p, A.v.p, agg,
+               Ac.v.p);
+    return BCS_OK;
+  });
+}
+
+// Aggregation with agg_passes matching passes; fills L.agg / L.nagg.
+bcs_status aggregate_level(Solver* s, Level& L) {
+  int nagg = 0;
+  BCS_OKR(match_pass(s, L.A, L.agg, &nagg));
+  DBuf<int32_t> cur_agg;
+  BCS_ALLOC(s, cur_agg, L.A.rows);
+  BCS_CU(s, cudaMemcpyAsync(cur_agg.p, L.agg.p, L.A.rows * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                            s->stream));
+  Bsr G;  // current aggregate graph (passes >= 2)
+  const Bsr* cur = &L.A;
+  for (int pass = 1; pass < s->setup_cfg.agg_passes; ++pass) {
+    DBuf<int32_t> mptr, mem, crow;
+    BCS_OKR(members(s, cur->rows, nagg, cur_agg.p, mptr, mem));
+    Bsr Abar;
+    BCS_OKR(tent_pattern(s, *cur, nagg, cur_agg.p, mptr.p, mem.p, Abar, crow));
+    BCS_OKR(tent_values(s, *cur, cur_agg.p, mptr.p, mem.p, Abar, crow.p));
+    DBuf<int32_t> a2;
+    int n2 = 0;
+    BCS_OKR(match_pass(s, Abar, a2, &n2));
+    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_compose, grid_for(L.A.rows, 256), 256, 0, L.A.rows, a2.p, L.agg.p);
+    cur_agg = std::move(a2);
+    const bool stalled = n2 == nagg;
+    nagg = n2;
+    G = std::move(Abar);
+    cur = &G;
+    if (stalled) break;
+  }
+  L.nagg = nagg;
+  return BCS_OK;
+}
+
+bcs_status block_inverses(Solver* s, Level& L, bool full) {
+  const int rows = L.A.rows, n = s->n;
+  if (full || !L.dpos.p) {
+    BCS_ALLOC(s, L.dpos, rows);
+    BCS_LAUNCH(s, K_SETUP_INV, 0, 0, k_diag_pos, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, L.A.ci.p,
+               L.dpos.p, s->flag.p);
+  }
+  BCS_ALLOC(s, L.dinv, (size_t)rows * n * n);
+  return with_n(n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    BCS_LAUNCH(s, K_SETUP_INV, 16.0 * rows * N * N, 4.0 * rows * N * N * N, k_block_inverse<N>,
+               grid_for(rows, 64), 64, 0, rows, L.dpos.p, L.A.v.p, L.dinv.p, s->flag.p);
+    return BCS_OK;
+  });
+}
+
+bcs_status coarse_inverse(Solver* s, Level& L) {
+  const int N = L.A.rows * s->n;
+  s->cN = N;
+  DBuf<double> M, colbuf;
+  DBuf<int32_t> prow;
+  BCS_ALLOC(s, M, (size_t)N * 2 * N);
+  BCS_ALLOC(s, colbuf, 2 * (size_t)N);
+  BCS_ALLOC(s, prow, N);
+  BCS_ALLOC(s, s->cinv, (size_t)N * N);
+  BCS_LAUNCH(s, K_SETUP_INV, 0, 0, k_dense_from_bsr, grid_for(L.A.rows, 64), 64, 0, L.A.rows, s->n, L.A.rp.p,
+             L.A.ci.p, L.A.v.p, M.p, N);
+  int dev = 0, sms = 0, per_sm = 0;
+  BCS_CU(s, cudaGetDevice(&dev));
+  BCS_CU(s, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int threads = 256;
+  const size_t smem = (size_t)N;
+  BCS_CU(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gauss_jordan, threads, smem));
+  if (per_sm < 1) return s->fail(BCS_ECUDA, "coarse inverse kernel cannot be resident");
+  int blocks = sms * per_sm;
+  if (blocks > N) blocks = N;
+  int Nn = N;
+  double* Mp = M.p;
+  double* cb = colbuf.p;
+  int32_t* pr = prow.p;
+  int32_t* fl = s->flag.p;
+  void* args[] = {&Nn, &Mp, &cb, &pr, &fl};
+  s->pre(K_SETUP_INV);
+  BCS_CU(s, cudaLaunchCooperativeKernel((void*)k_gauss_jordan, blocks, threads, args, smem, s->stream));
+  BCS_OKR(s->post(K_SETUP_INV, "k_gauss_jordan", 24.0 * N * N * N, 3.0 * N * N * N));
+  BCS_LAUNCH(s, K_SETUP_INV, 0, 0, k_gj_finish, grid_for((size_t)N * N, 256), 256, 0, N, M.p, prow.p,
+             s->cinv.p);
+  return BCS_OK;
+}
+
+// R = P^T: structure (full) and values.
+bcs_status transpose_P(Solver* s, Level& L, bool full) {
+  Bsr& P = L.P;
+  Bsr& R = L.R;
+  const int rows = L.A.rows;
+  if (full) {
+    DBuf<int32_t> rcnt, cursor;
+    R.rows = L.nagg;
+    R.cols = rows;
+    R.nnz = P.nnz;
+    BCS_ALLOC(s, rcnt, L.nagg);
+    BCS_ALLOC(s, cursor, L.nagg);
+    BCS_ALLOC(s, R.rp, L.nagg + 1);
+    BCS_ALLOC(s, R.ci, R.nnz);
+    BCS_CU(s, cudaMemsetAsync(rcnt.p, 0, L.nagg * sizeof(int32_t), s->stream));
+    BCS_CU(s, cudaMemsetAsync(cursor.p, 0, L.nagg * sizeof(int32_t), s->stream));
+    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_count_by, grid_for(P.nnz, 256), 256, 0, P.nnz, P.ci.p, rcnt.p);
+    BCS_OKR(exclusive_scan(s, rcnt.p, R.rp.p, L.nagg));
+    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_place_by, grid_for(P.nnz, 256), 256, 0, P.nnz, P.ci.p, L.Prow.p, R.rp.p,
+               cursor.p, R.ci.p);
+    int32_t mx = 0;
+    BCS_OKR(max_of(s, rcnt.p, L.nagg, &mx));
+    BCS_OKR(segmented_sort_unique(s, R.rp.p, R.ci.p, rcnt.p, L.nagg, mx));
+    BCS_ALLOC(s, L.Rrow, R.nnz);
+    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_row_index, grid_for(L.nagg, 256), 256, 0, L.nagg, R.rp.p, L.Rrow.p);
+  }
+  const int n = s->n;
+  BCS_ALLOC(s, R.v, (size_t)R.nnz * n * n);
+  return with_n(n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    BCS_LAUNCH(s, K_SETUP_GAL, 16.0 * R.nnz * N * N, 0, k_transpose_values<N>, grid_for(R.nnz, 128), 128, 0,
+               R.nnz, L.Rrow.p, R.ci.p, P.rp.p, P.ci.p, P.v.p, R.v.p);
+    return BCS_OK;
+  });
+}
+
+// Smoothed prolongation of level L: omega_P, pattern (full), values, R.
+bcs_status smoothed_prolongation(Solver* s, Level& L, bool full) {
+  const int rows = L.A.rows, n = s->n;
+  DBuf<double> rho;
+  BCS_ALLOC(s, rho, 1);
+  BCS_CU(s, cudaMemsetAsync(rho.p, 0, sizeof(double), s->stream));
+  BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * L.A.nnz * N * N, 2.0 * L.A.nnz * N * N * N, k_rho<N>, grid_for(rows, 128),
+               128, 0, rows, L.A.rp.p, L.A.v.p, L.dinv.p, rho.p);
+    return BCS_OK;
+  }));
+  double h_rho = 0.0;
+  BCS_CU(s, cudaMemcpyAsync(&h_rho, rho.p, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  L.omega_p = s->setup_cfg.p_omega / h_rho;
+  if (full) {
+    DBuf<int32_t> cnt;
+    BCS_ALLOC(s, cnt, rows);
+    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_p, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, cnt.p);
+    auto fill = [&](const int32_t*, int32_t* cand) -> bcs_status {
+      // candidate segments coincide with A's rows
+      BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_fill_p, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, L.A.ci.p,
+                 L.agg.p, cand);
+      return BCS_OK;
+    };
+    BCS_OKR(pattern_from_candidates(s, rows, cnt, fill, L.P, L.Prow));
+    L.P.cols = L.nagg;
+  }
+  BCS_ALLOC(s, L.P.v, (size_t)L.P.nnz * n * n);
+  const double om = L.omega_p;
+  BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (L.A.nnz + L.P.nnz) * N * N, 2.0 * L.P.nnz * N * N * N, k_p_values<N>,
+               grid_for(L.P.nnz, 128), 128, 0, L.P.nnz, L.Prow.p, L.P.ci.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.dinv.p,
+               L.agg.p, om, L.P.v.p);
+    return BCS_OK;
+  }));
+  return transpose_P(s, L, full);
+}
+
+// C = A B (block SpGEMM): pattern when full, values always.
+bcs_status spgemm(Solver* s, const Bsr& A, const Bsr& B, Bsr& Cm, DBuf<int32_t>& crow, bool full) {
+  const int rows = A.rows, n = s->n;
+  if (full) {
+    DBuf<int32_t> cnt;
+    BCS_ALLOC(s, cnt, rows);
+    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_gemm, grid_for(rows, 256), 256, 0, rows, A.rp.p, A.ci.p, B.rp.p,
+               cnt.p);
+    auto fill = [&](const int32_t* cptr, int32_t* cand) -> bcs_status {
+      BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_fill_gemm, grid_for(rows, 256), 256, 0, rows, A.rp.p, A.ci.p,
+                 B.rp.p, B.ci.p, cptr, cand);
+      return BCS_OK;
+    };
+    BCS_OKR(pattern_from_candidates(s, rows, cnt, fill, Cm, crow));
+    Cm.cols = B.cols;
+  }
+  BCS_ALLOC(s, Cm.v, (size_t)Cm.nnz * n * n);
+  return with_n(n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + Cm.nnz) * N * N, 0, k_gemm_values<N>, grid_for(Cm.nnz, 64), 64, 0,
+               Cm.nnz, crow.p, Cm.ci.p, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, Cm.v.p);
+    return BCS_OK;
+  });
+}
+
+bcs_status check_flags(Solver* s, bool* singular) {
+  int32_t h = 0;
+  BCS_OKR(read_int(s, s->flag.p, &h));
+  *singular = false;
+  if (h & 4) return s->fail(BCS_EINVAL, "a block row has no diagonal block");
+  if (h & (8 | 16)) *singular = true;
+  return BCS_OK;
+}
+
+// Transfer operators and coarse matrix for level l -> l+1.
+bcs_status build_transfer(Solver* s, int l, bool full) {
+  if ((int)s->lv.size() <= l + 1) s->lv.emplace_back();
+  Level& L = s->lv[l];
+  Level& Lc = s->lv[l + 1];
+  if (full) BCS_OKR(members(s, L.A.rows, L.nagg, L.agg.p, L.mptr, L.mem));
+  if (s->setup_cfg.pmode == BCS_P_TENTATIVE) {
+    if (full) BCS_OKR(tent_pattern(s, L.A, L.nagg, L.agg.p, L.mptr.p, L.mem.p, Lc.A, L.Crow));
+    BCS_OKR(tent_values(s, L.A, L.agg.p, L.mptr.p, L.mem.p, Lc.A, L.Crow.p));
+  } else {
+    BCS_OKR(smoothed_prolongation(s, L, full));
+    BCS_OKR(spgemm(s, L.A, L.P, L.AP, L.AProw, full));
+    BCS_OKR(spgemm(s, L.R, L.AP, Lc.A, L.Crow, full));
+  }
+  Lc.A.cols = Lc.A.rows;
+  return BCS_OK;
+}
+
+}  // namespace
+
+bcs_status amg_setup(Solver* s, bool full) {
+  const bcs_config& cfg = s->setup_cfg;
+  if (full) {
+    s->lv.resize(1);
+    Level& L0 = s->lv[0];
+    L0.agg.release();
+    L0.nagg = 0;
+    L0.coarse_kind = -1;
+  }
+  BCS_CU(s, cudaMemsetAsync(s->flag.p, 0, 4 * sizeof(int32_t), s->stream));
+  for (int l = 0;; ++l) {
+    Level& L = s->lv[l];
+    BCS_OKR(block_inverses(s, L, full));
+    bool singular = false;
+    BCS_OKR(check_flags(s, &singular));
+    if (singular) return s->fail(BCS_SINGULAR_BLOCK, "singular diagonal block at level " + std::to_string(l));
+    bool last;
+    if (full) {
+      const int C = L.A.rows;
+      last = C <= cfg.coarse_size || l == cfg.max_levels - 1 || cfg.precond != BCS_PC_AMG;
+      if (!last) {
+        BCS_OKR(aggregate_level(s, L));
+        if (L.nagg >= C || (double)L.nagg > cfg.max_coarsen_ratio * C) {
+          last = true;
+          L.agg.release();
+          L.nagg = 0;
+        }
+      }
+    } else {
+      last = L.coarse_kind >= 0;
+    }
+    if (last) {
+      s->lv.resize(l + 1);
+      Level& Lf = s->lv[l];
+      if (cfg.precond != BCS_PC_AMG) {
+        Lf.coarse_kind = 1;
+      } else if ((long long)Lf.A.rows * s->n <= cfg.coarse_dense_max) {
+        Lf.coarse_kind = 0;
+        BCS_OKR(coarse_inverse(s, Lf));
+        bool sing = false;
+        BCS_OKR(check_flags(s, &sing));
+        if (sing) return s->fail(BCS_SINGULAR_BLOCK, "singular coarsest-level matrix");
+      } else {
+        Lf.coarse_kind = 1;
+        s->cinv.release();
+        s->cN = 0;
+      }
+      break;
+    }
+    L.coarse_kind = -1;
+    BCS_OKR(build_transfer(s, l, full));
+  }
+  return BCS_OK;
+}
+
+}  // namespace bcs
