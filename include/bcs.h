@@ -37,6 +37,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define BCS_API __attribute__((visibility("default")))
+#else
+#define BCS_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -107,20 +113,20 @@ typedef struct bcs_stats {
 typedef struct bcs_solver bcs_solver;
 
 /* Fill cfg with defaults. Returns BCS_EINVAL when cfg is NULL. */
-bcs_status bcs_config_default(bcs_config* cfg);
+BCS_API bcs_status bcs_config_default(bcs_config* cfg);
 
 /* Create a solver for n x n blocks (1 <= n <= 8) on the current CUDA device.
  * stream: a cudaStream_t the solver launches on (NULL = legacy default
  * stream). cfg may be NULL (defaults). *out receives the handle.
  * BCS_EINVAL for a bad n or an option out of range. */
-bcs_status bcs_create(bcs_solver** out, int n, const bcs_config* cfg, void* stream);
+BCS_API bcs_status bcs_create(bcs_solver** out, int n, const bcs_config* cfg, void* stream);
 
 /* Destroy the solver and free its device memory. NULL is accepted. */
-bcs_status bcs_destroy(bcs_solver* s);
+BCS_API bcs_status bcs_destroy(bcs_solver* s);
 
 /* Replace the options. A change of any AMG field (or the precision) drops the
  * hierarchy, so the next set_values runs a full setup. */
-bcs_status bcs_set_config(bcs_solver* s, const bcs_config* cfg);
+BCS_API bcs_status bcs_set_config(bcs_solver* s, const bcs_config* cfg);
 
 /* Upload the LDU face addressing (Alg. 1, first iteration / topology change):
  * n_cells C >= 1, n_faces F >= 0, owner[F] and neighbour[F] int32 cell ids
@@ -130,7 +136,7 @@ bcs_status bcs_set_config(bcs_solver* s, const bcs_config* cfg);
  * BCS_EINVAL: C < 1, F < 0, an id out of range, owner == neighbour, or a
  * repeated face (unordered pair); the solver then has no structure. Drops any
  * AMG hierarchy and values. */
-bcs_status bcs_set_structure(bcs_solver* s, int32_t n_cells, int32_t n_faces,
+BCS_API bcs_status bcs_set_structure(bcs_solver* s, int32_t n_cells, int32_t n_faces,
                              const int32_t* owner, const int32_t* neighbour, int mem);
 
 /* Upload coefficients (Alg. 1, every iteration): diag[C][n][n],
@@ -141,12 +147,12 @@ bcs_status bcs_set_structure(bcs_solver* s, int32_t n_cells, int32_t n_faces,
  * aggregates and every sparsity pattern. BCS_ESTATE before set_structure;
  * BCS_SINGULAR_BLOCK when a diagonal block or the coarsest matrix is
  * singular (the hierarchy is then dropped). */
-bcs_status bcs_set_values(bcs_solver* s, const double* diag, const double* upper,
+BCS_API bcs_status bcs_set_values(bcs_solver* s, const double* diag, const double* upper,
                           const double* lower, int mem);
 
 /* Forget the hierarchy: the next set_values runs a full setup (new
  * aggregates). */
-bcs_status bcs_invalidate_hierarchy(bcs_solver* s);
+BCS_API bcs_status bcs_invalidate_hierarchy(bcs_solver* s);
 
 /* Solve A x = b: b[C][n] FP64; x[C][n] FP64 holds the initial guess on entry
  * and the solution on exit (both host or both device per mem). res may be
@@ -154,49 +160,49 @@ bcs_status bcs_invalidate_hierarchy(bcs_solver* s);
  * BCS_NOT_CONVERGED at maxiter, BCS_BREAKDOWN on NaN/Inf or breakdown;
  * x holds the last iterate in every case. b = 0 gives x = 0 and BCS_OK.
  * BCS_ESTATE before set_values. */
-bcs_status bcs_solve(bcs_solver* s, const double* b, double* x, int mem, bcs_result* res);
+BCS_API bcs_status bcs_solve(bcs_solver* s, const double* b, double* x, int mem, bcs_result* res);
 
 /* y = A x with the fine matrix in FP64 (Eq. 1 left-hand side); x, y [C][n]
  * host or device per mem. BCS_ESTATE before set_values. */
-bcs_status bcs_spmv(bcs_solver* s, const double* x, double* y, int mem);
+BCS_API bcs_status bcs_spmv(bcs_solver* s, const double* x, double* y, int mem);
 
 /* z = M^{-1} v: one application of the configured preconditioner (one AMG
  * V-cycle from zero) in the configured precision, returned in FP64. */
-bcs_status bcs_precond_apply(bcs_solver* s, const double* v, double* z, int mem);
+BCS_API bcs_status bcs_precond_apply(bcs_solver* s, const double* v, double* z, int mem);
 
 /* Test hooks: copies of internal state to HOST arrays (any may be NULL).
  * bcs_get_bsr: row_ptr[C+1], col[nnz], val[nnz][n][n] of the fine matrix and
  * the LDU -> BSR maps pos_diag[C], pos_up[F], pos_lo[F]. */
-bcs_status bcs_get_bsr(bcs_solver* s, int32_t* row_ptr, int32_t* col, double* val,
+BCS_API bcs_status bcs_get_bsr(bcs_solver* s, int32_t* row_ptr, int32_t* col, double* val,
                        int32_t* pos_diag, int32_t* pos_up, int32_t* pos_lo);
 /* Number of AMG levels (0 without a hierarchy). */
-int bcs_num_levels(const bcs_solver* s);
+BCS_API int bcs_num_levels(const bcs_solver* s);
 /* Sizes of level l: block rows, nnz blocks of A_l, nnz blocks of P_l (0 at
  * the coarsest level or in tentative mode), coarse_kind (-1 not coarsest,
  * 0 dense inverse, 1 smoother sweeps). */
-bcs_status bcs_get_level_info(const bcs_solver* s, int l, int* rows, int* nnz, int* p_nnz,
+BCS_API bcs_status bcs_get_level_info(const bcs_solver* s, int l, int* rows, int* nnz, int* p_nnz,
                               int* coarse_kind);
 /* FP64 level data: A_l (row_ptr, col, val), aggregate map agg[rows] (not at
  * the coarsest level), block inverses dinv[rows][n][n]. */
-bcs_status bcs_get_level(bcs_solver* s, int l, int32_t* row_ptr, int32_t* col, double* val,
+BCS_API bcs_status bcs_get_level(bcs_solver* s, int l, int32_t* row_ptr, int32_t* col, double* val,
                          int32_t* agg, double* dinv);
 /* Smoothed prolongation of level l (pmode smoothed only) and omega_P. */
-bcs_status bcs_get_prolongation(bcs_solver* s, int l, int32_t* row_ptr, int32_t* col,
+BCS_API bcs_status bcs_get_prolongation(bcs_solver* s, int l, int32_t* row_ptr, int32_t* col,
                                 double* val, double* omega_p);
 /* Dense inverse of the coarsest matrix, [N][N] with N = rows * n. */
-bcs_status bcs_get_coarse_inverse(bcs_solver* s, double* inv);
+BCS_API bcs_status bcs_get_coarse_inverse(bcs_solver* s, double* inv);
 
 /* Statistics (launch counts always; times only with cfg.profile = 1). */
-bcs_status bcs_get_stats(bcs_solver* s, bcs_stats* st);
-bcs_status bcs_reset_stats(bcs_solver* s);
+BCS_API bcs_status bcs_get_stats(bcs_solver* s, bcs_stats* st);
+BCS_API bcs_status bcs_reset_stats(bcs_solver* s);
 /* Name of kernel kind k (0 <= k < BCS_NUM_KERNEL_KINDS), "" if unused. */
-const char* bcs_kernel_kind_name(int k);
+BCS_API const char* bcs_kernel_kind_name(int k);
 
 /* Message for the last failed call on s (never NULL). */
-const char* bcs_last_error(const bcs_solver* s);
+BCS_API const char* bcs_last_error(const bcs_solver* s);
 
 /* Device bytes currently held by the solver. */
-size_t bcs_device_bytes(const bcs_solver* s);
+BCS_API size_t bcs_device_bytes(const bcs_solver* s);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,379 @@
+"""Python binding of the C ABI in include/bcs.h (argument marshalling only).
+
+Every function named bcs_* here calls the library function of the same name.
+Arrays may be numpy arrays (host memory, BCS_MEM_HOST) or CUDA torch tensors
+(device memory, BCS_MEM_DEVICE); all arrays of one call must live in the same
+place. There is no fallback: without the built CUDA library (libbcs.so) every
+call raises.
+"""
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbcs.so")
+
+BCS_OK, BCS_EINVAL, BCS_ENOMEM, BCS_ECUDA, BCS_NOT_CONVERGED, BCS_BREAKDOWN, \
+    BCS_SINGULAR_BLOCK, BCS_TIMEOUT, BCS_REJECTED, BCS_ESTATE = range(10)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "NOT_CONVERGED", "BREAKDOWN",
+                "SINGULAR_BLOCK", "TIMEOUT", "REJECTED", "ESTATE"]
+BCS_MEM_HOST, BCS_MEM_DEVICE = 0, 1
+BCS_FGMRES, BCS_BICGSTAB = 0, 1
+BCS_PC_AMG, BCS_PC_NONE, BCS_PC_JACOBI = 0, 1, 2
+BCS_P_SMOOTHED, BCS_P_TENTATIVE = 0, 1
+BCS_PREC_FP64, BCS_PREC_FP32, BCS_PREC_BF16 = 0, 1, 2
+NUM_KERNEL_KINDS = 16
+
+
+class bcs_config(ct.Structure):
+    _fields_ = [
+        ("solver", ct.c_int), ("restart", ct.c_int), ("tol", ct.c_double), ("maxiter", ct.c_int),
+        ("precond", ct.c_int), ("pmode", ct.c_int), ("matching_rounds", ct.c_int),
+        ("agg_passes", ct.c_int), ("jacobi_omega", ct.c_double), ("nu1", ct.c_int), ("nu2", ct.c_int),
+        ("coarse_size", ct.c_int), ("max_levels", ct.c_int), ("max_coarsen_ratio", ct.c_double),
+        ("p_omega", ct.c_double), ("coarse_dense_max", ct.c_int), ("coarse_sweeps", ct.c_int),
+        ("precision", ct.c_int), ("profile", ct.c_int),
+    ]
+
+
+class bcs_result(ct.Structure):
+    _fields_ = [("status", ct.c_int), ("iters", ct.c_int), ("restarts", ct.c_int), ("levels", ct.c_int),
+                ("rel_res_initial", ct.c_double), ("rel_res_final", ct.c_double),
+                ("setup_ms", ct.c_double), ("solve_ms", ct.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class bcs_stats(ct.Structure):
+    _fields_ = [("launches", ct.c_longlong), ("kind_launches", ct.c_longlong * NUM_KERNEL_KINDS),
+                ("kind_ms", ct.c_double * NUM_KERNEL_KINDS), ("kind_bytes", ct.c_double * NUM_KERNEL_KINDS),
+                ("kind_flops", ct.c_double * NUM_KERNEL_KINDS)]
+
+
+class BcsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 10 else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_vp = ct.c_void_p
+
+
+def lib():
+    """The loaded CUDA library; raises when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run __graft_entry__.build() or python -m paper_2403_07882_b300.build)")
+        L = ct.CDLL(LIB_PATH)
+        sig = {
+            "bcs_config_default": (ct.c_int, [ct.POINTER(bcs_config)]),
+            "bcs_create": (ct.c_int, [ct.POINTER(_vp), ct.c_int, ct.POINTER(bcs_config), _vp]),
+            "bcs_destroy": (ct.c_int, [_vp]),
+            "bcs_set_config": (ct.c_int, [_vp, ct.POINTER(bcs_config)]),
+            "bcs_set_structure": (ct.c_int, [_vp, ct.c_int32, ct.c_int32, _vp, _vp, ct.c_int]),
+            "bcs_set_values": (ct.c_int, [_vp, _vp, _vp, _vp, ct.c_int]),
+            "bcs_invalidate_hierarchy": (ct.c_int, [_vp]),
+            "bcs_solve": (ct.c_int, [_vp, _vp, _vp, ct.c_int, ct.POINTER(bcs_result)]),
+            "bcs_spmv": (ct.c_int, [_vp, _vp, _vp, ct.c_int]),
+            "bcs_precond_apply": (ct.c_int, [_vp, _vp, _vp, ct.c_int]),
+            "bcs_get_bsr": (ct.c_int, [_vp] + [_vp] * 6),
+            "bcs_num_levels": (ct.c_int, [_vp]),
+            "bcs_get_level_info": (ct.c_int, [_vp, ct.c_int] + [ct.POINTER(ct.c_int)] * 4),
+            "bcs_get_level": (ct.c_int, [_vp, ct.c_int] + [_vp] * 5),
+            "bcs_get_prolongation": (ct.c_int, [_vp, ct.c_int] + [_vp] * 3 + [ct.POINTER(ct.c_double)]),
+            "bcs_get_coarse_inverse": (ct.c_int, [_vp, _vp]),
+            "bcs_get_stats": (ct.c_int, [_vp, ct.POINTER(bcs_stats)]),
+            "bcs_reset_stats": (ct.c_int, [_vp]),
+            "bcs_kernel_kind_name": (ct.c_char_p, [ct.c_int]),
+            "bcs_last_error": (ct.c_char_p, [_vp]),
+            "bcs_device_bytes": (ct.c_size_t, [_vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_names():
+    return ["bcs_config_default", "bcs_create", "bcs_destroy", "bcs_set_config", "bcs_set_structure",
+            "bcs_set_values", "bcs_invalidate_hierarchy", "bcs_solve", "bcs_spmv", "bcs_precond_apply",
+            "bcs_get_bsr", "bcs_num_levels", "bcs_get_level_info", "bcs_get_level", "bcs_get_prolongation",
+            "bcs_get_coarse_inverse", "bcs_get_stats", "bcs_reset_stats", "bcs_kernel_kind_name",
+            "bcs_last_error", "bcs_device_bytes"]
+
+
+# ------------------------------------------------------------ marshalling
+def _ptr_mem(*arrays):
+    """Pointers and the memory kind of a group of arrays (all host or all device)."""
+    mems = set()
+    ptrs = []
+    for a in arrays:
+        if a is None:
+            ptrs.append(None)
+            continue
+        if isinstance(a, np.ndarray):
+            if not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("arrays must be C-contiguous")
+            ptrs.append(a.ctypes.data)
+            mems.add(BCS_MEM_HOST)
+        else:  # torch tensor
+            if not a.is_contiguous():
+                raise ValueError("tensors must be contiguous")
+            ptrs.append(a.data_ptr())
+            mems.add(BCS_MEM_DEVICE if a.is_cuda else BCS_MEM_HOST)
+    if len(mems) > 1:
+        raise ValueError("mix of host and device arrays in one call")
+    return ptrs, (mems.pop() if mems else BCS_MEM_HOST)
+
+
+def _check(status, handle=None):
+    if status != BCS_OK:
+        msg = lib().bcs_last_error(handle).decode() if handle else ""
+        raise BcsError(status, msg)
+    return status
+
+
+def bcs_config_default(**overrides):
+    c = bcs_config()
+    _check(lib().bcs_config_default(ct.byref(c)))
+    for k, v in overrides.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def bcs_create(n, cfg=None, stream=None):
+    h = _vp()
+    st = lib().bcs_create(ct.byref(h), n, ct.byref(cfg) if cfg is not None else None,
+                          stream if stream is not None else _current_stream())
+    _check(st)
+    return h
+
+
+def bcs_destroy(h):
+    return lib().bcs_destroy(h)
+
+
+def bcs_set_config(h, cfg):
+    return _check(lib().bcs_set_config(h, ct.byref(cfg)), h)
+
+
+def bcs_set_structure(h, n_cells, owner, neighbour):
+    (po, pn), mem = _ptr_mem(owner, neighbour)
+    return _check(lib().bcs_set_structure(h, n_cells, len(owner), po, pn, mem), h)
+
+
+def bcs_set_values(h, diag, upper, lower):
+    (pd, pu, pl), mem = _ptr_mem(diag, upper, lower)
+    return _check(lib().bcs_set_values(h, pd, pu, pl, mem), h)
+
+
+def bcs_invalidate_hierarchy(h):
+    return _check(lib().bcs_invalidate_hierarchy(h), h)
+
+
+def bcs_solve(h, b, x, check=False):
+    """Solve in place into x; returns (status, result dict)."""
+    (pb, px), mem = _ptr_mem(b, x)
+    res = bcs_result()
+    st = lib().bcs_solve(h, pb, px, mem, ct.byref(res))
+    if st in (BCS_EINVAL, BCS_ENOMEM, BCS_ECUDA, BCS_ESTATE) or (check and st != BCS_OK):
+        _check(st, h)
+    return st, res.as_dict()
+
+
+def bcs_spmv(h, x, y):
+    (px, py), mem = _ptr_mem(x, y)
+    return _check(lib().bcs_spmv(h, px, py, mem), h)
+
+
+def bcs_precond_apply(h, v, z):
+    (pv, pz), mem = _ptr_mem(v, z)
+    return _check(lib().bcs_precond_apply(h, pv, pz, mem), h)
+
+
+def bcs_get_bsr(h, C, F, n, nnz, values=True):
+    rp = np.zeros(C + 1, np.int32)
+    col = np.zeros(nnz, np.int32)
+    val = np.zeros((nnz, n, n)) if values else None
+    pd = np.zeros(C, np.int32)
+    pu = np.zeros(max(F, 1), np.int32)
+    pl = np.zeros(max(F, 1), np.int32)
+    _check(lib().bcs_get_bsr(h, rp.ctypes.data, col.ctypes.data, val.ctypes.data if values else None,
+                             pd.ctypes.data, pu.ctypes.data, pl.ctypes.data), h)
+    return dict(rows=C, n=n, row_ptr=rp, col=col, val=val, pos_diag=pd, pos_up=pu[:F], pos_lo=pl[:F])
+
+
+def bcs_num_levels(h):
+    return lib().bcs_num_levels(h)
+
+
+def bcs_get_level_info(h, l):
+    r, nz, pn, k = ct.c_int(), ct.c_int(), ct.c_int(), ct.c_int()
+    _check(lib().bcs_get_level_info(h, l, ct.byref(r), ct.byref(nz), ct.byref(pn), ct.byref(k)), h)
+    return dict(rows=r.value, nnz=nz.value, p_nnz=pn.value, coarse_kind=k.value)
+
+
+def bcs_get_level(h, l, n):
+    i = bcs_get_level_info(h, l)
+    rp = np.zeros(i["rows"] + 1, np.int32)
+    col = np.zeros(i["nnz"], np.int32)
+    val = np.zeros((i["nnz"], n, n))
+    agg = np.full(i["rows"], -1, np.int32)
+    dinv = np.zeros((i["rows"], n, n))
+    _check(lib().bcs_get_level(h, l, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
+                               agg.ctypes.data if i["coarse_kind"] < 0 else None, dinv.ctypes.data), h)
+    return dict(rows=i["rows"], n=n, row_ptr=rp, col=col, val=val, agg=agg, dinv=dinv,
+                coarse_kind=i["coarse_kind"])
+
+
+def bcs_get_prolongation(h, l, n):
+    i = bcs_get_level_info(h, l)
+    rp = np.zeros(i["rows"] + 1, np.int32)
+    col = np.zeros(i["p_nnz"], np.int32)
+    val = np.zeros((i["p_nnz"], n, n))
+    om = ct.c_double()
+    _check(lib().bcs_get_prolongation(h, l, rp.ctypes.data, col.ctypes.data, val.ctypes.data, ct.byref(om)), h)
+    return dict(rows=i["rows"], n=n, row_ptr=rp, col=col, val=val, omega=om.value)
+
+
+def bcs_get_coarse_inverse(h, N):
+    out = np.zeros((N, N))
+    _check(lib().bcs_get_coarse_inverse(h, out.ctypes.data), h)
+    return out
+
+
+def bcs_get_stats(h):
+    st = bcs_stats()
+    _check(lib().bcs_get_stats(h, ct.byref(st)), h)
+    kinds = {}
+    for k in range(NUM_KERNEL_KINDS):
+        name = lib().bcs_kernel_kind_name(k).decode()
+        if name:
+            kinds[name] = dict(launches=st.kind_launches[k], ms=st.kind_ms[k], bytes=st.kind_bytes[k],
+                               flops=st.kind_flops[k])
+    return dict(launches=st.launches, kinds=kinds)
+
+
+def bcs_reset_stats(h):
+    return _check(lib().bcs_reset_stats(h), h)
+
+
+def bcs_kernel_kind_name(k):
+    return lib().bcs_kernel_kind_name(k).decode()
+
+
+def bcs_last_error(h):
+    return lib().bcs_last_error(h).decode()
+
+
+def bcs_device_bytes(h):
+    return lib().bcs_device_bytes(h)
+
+
+class Solver:
+    """Owning wrapper: a solver handle for n x n blocks."""
+
+    def __init__(self, n, **cfg):
+        self.n = n
+        self.cfg = bcs_config_default(**cfg)
+        self.h = bcs_create(n, self.cfg)
+        self.C = self.F = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            bcs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_config(self, **cfg):
+        for k, v in cfg.items():
+            setattr(self.cfg, k, v)
+        bcs_set_config(self.h, self.cfg)
+
+    def set_structure(self, n_cells, owner, neighbour):
+        self.C, self.F = int(n_cells), len(owner)
+        bcs_set_structure(self.h, n_cells, owner, neighbour)
+
+    def set_values(self, diag, upper, lower):
+        bcs_set_values(self.h, diag, upper, lower)
+
+    def load(self, system, device=None):
+        """Structure + values of a synth system dict (numpy; device=torch device copies first)."""
+        keys = ("owner", "neighbour", "diag", "upper", "lower")
+        arr = {k: system[k] for k in keys}
+        if device is not None:
+            import torch
+            arr = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in arr.items()}
+        self.set_structure(system["n_cells"], arr["owner"], arr["neighbour"])
+        self.set_values(arr["diag"], arr["upper"], arr["lower"])
+
+    def solve(self, b, x=None):
+        if x is None:
+            x = np.zeros_like(b) if isinstance(b, np.ndarray) else b.new_zeros(b.shape)
+        st, res = bcs_solve(self.h, b, x)
+        return x, st, res
+
+    def spmv(self, x, y=None):
+        if y is None:
+            y = np.zeros_like(x) if isinstance(x, np.ndarray) else x.new_zeros(x.shape)
+        bcs_spmv(self.h, x, y)
+        return y
+
+    def precond(self, v, z=None):
+        if z is None:
+            z = np.zeros_like(v) if isinstance(v, np.ndarray) else v.new_zeros(v.shape)
+        bcs_precond_apply(self.h, v, z)
+        return z
+
+    def bsr(self, values=True):
+        return bcs_get_bsr(self.h, self.C, self.F, self.n, self.C + 2 * self.F, values)
+
+    @property
+    def levels(self):
+        return bcs_num_levels(self.h)
+
+    def level(self, l):
+        return bcs_get_level(self.h, l, self.n)
+
+    def level_info(self, l):
+        return bcs_get_level_info(self.h, l)
+
+    def prolongation(self, l):
+        return bcs_get_prolongation(self.h, l, self.n)
+
+    def coarse_inverse(self):
+        info = self.level_info(self.levels - 1)
+        return bcs_get_coarse_inverse(self.h, info["rows"] * self.n)
+
+    def stats(self):
+        return bcs_get_stats(self.h)
+
+    def reset_stats(self):
+        bcs_reset_stats(self.h)

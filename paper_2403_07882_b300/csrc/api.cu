@@ -1,0 +1,457 @@
+// C ABI of the block-coupled solver (bcs.h). Argument checks, host/device
+// staging, the Alg. 1 call sequence (structure once, values every
+// iteration with full setup or values-only resetup, solve), statistics.
+#include <chrono>
+#include <cmath>
+#include <new>
+
+#include "internal.h"
+
+namespace bcs {
+
+const char* kind_name(int k) {
+  static const char* names[K_NKINDS] = {"ldu_to_bsr", "spmv_fp64",   "jacobi_sweep", "residual",
+                                        "transfer",   "coarse_solve", "blas1",       "setup_aggregation",
+                                        "setup_galerkin", "setup_inverse", "cast",   "scan_sort"};
+  return (k >= 0 && k < K_NKINDS) ? names[k] : "";
+}
+
+void* Alloc::get(size_t bytes) {
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  live += bytes;
+  return p;
+}
+
+void Alloc::put(void* p, size_t bytes) {
+  if (!p) return;
+  (void)cudaFreeAsync(p, stream);
+  live -= bytes;
+}
+
+void Solver::pre(int kind) {
+  if (!cfg.profile) return;
+  if (event_next + 2 > event_pool.size()) {
+    for (int q = 0; q < 64; ++q) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      event_pool.push_back(e);
+    }
+  }
+  Timer t{kind, event_pool[event_next], event_pool[event_next + 1]};
+  event_next += 2;
+  cudaEventRecord(t.a, stream);
+  timers.push_back(t);
+}
+
+bcs_status Solver::post(int kind, const char* what, double bytes, double flops) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(BCS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  ++launches;
+  kind_launches[kind]++;
+  kind_bytes[kind] += bytes;
+  kind_flops[kind] += flops;
+  if (cfg.profile && !timers.empty() && timers.back().kind == kind) cudaEventRecord(timers.back().b, stream);
+  return BCS_OK;
+}
+
+void Solver::flush_timers() {
+  if (timers.empty()) return;
+  cudaStreamSynchronize(stream);
+  for (const Timer& t : timers) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) kind_ms[t.kind] += ms;
+  }
+  timers.clear();
+  event_next = 0;
+}
+
+}  // namespace bcs
+
+using namespace bcs;
+
+namespace {
+
+bcs_status check_config(const bcs_config* c) {
+  if (c->solver != BCS_FGMRES && c->solver != BCS_BICGSTAB) return BCS_EINVAL;
+  if (c->restart < 1 || c->restart > 64) return BCS_EINVAL;
+  if (!(c->tol > 0.0) || c->maxiter < 1) return BCS_EINVAL;
+  if (c->precond < BCS_PC_AMG || c->precond > BCS_PC_JACOBI) return BCS_EINVAL;
+  if (c->pmode != BCS_P_SMOOTHED && c->pmode != BCS_P_TENTATIVE) return BCS_EINVAL;
+  if (c->matching_rounds < 1 || c->agg_passes < 1 || c->agg_passes > 4) return BCS_EINVAL;
+  if (c->nu1 < 0 || c->nu2 < 0 || c->nu1 + c->nu2 < 1) return BCS_EINVAL;
+  if (c->coarse_size < 1 || c->max_levels < 1 || c->coarse_sweeps < 1) return BCS_EINVAL;
+  if (c->coarse_dense_max < 1 || c->coarse_dense_max > 8192) return BCS_EINVAL;
+  if (c->precision < BCS_PREC_FP64 || c->precision > BCS_PREC_BF16) return BCS_EINVAL;
+  if (!(c->max_coarsen_ratio > 0.0) || !(c->p_omega > 0.0) || !(c->jacobi_omega > 0.0)) return BCS_EINVAL;
+  return BCS_OK;
+}
+
+bool same_hierarchy_options(const bcs_config& a, const bcs_config& b) {
+  return a.precond == b.precond && a.pmode == b.pmode && a.matching_rounds == b.matching_rounds &&
+         a.agg_passes == b.agg_passes && a.jacobi_omega == b.jacobi_omega && a.nu1 == b.nu1 && a.nu2 == b.nu2 &&
+         a.coarse_size == b.coarse_size && a.max_levels == b.max_levels &&
+         a.max_coarsen_ratio == b.max_coarsen_ratio && a.p_omega == b.p_omega &&
+         a.coarse_dense_max == b.coarse_dense_max && a.coarse_sweeps == b.coarse_sweeps &&
+         a.precision == b.precision;
+}
+
+// Copy a host array into a device staging buffer (or pass a device pointer).
+template <class T>
+bcs_status stage(Solver* s, const T* src, size_t count, int mem, DBuf<T>& buf, const T** out) {
+  if (mem == BCS_MEM_DEVICE || count == 0) {
+    *out = src;
+    if (count == 0 && !src) *out = nullptr;
+    return BCS_OK;
+  }
+  BCS_ALLOC(s, buf, count);
+  BCS_CU(s, cudaMemcpyAsync(buf.p, src, count * sizeof(T), cudaMemcpyHostToDevice, s->stream));
+  *out = buf.p;
+  return BCS_OK;
+}
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+bcs_status to_host(Solver* s, void* dst, const void* src, size_t bytes) {
+  if (!dst || bytes == 0) return BCS_OK;
+  BCS_CU(s, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->stream));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  return BCS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bcs_status bcs_config_default(bcs_config* c) {
+  if (!c) return BCS_EINVAL;
+  std::memset(c, 0, sizeof(*c));
+  c->solver = BCS_FGMRES;
+  c->restart = 30;
+  c->tol = 1e-8;
+  c->maxiter = 1000;
+  c->precond = BCS_PC_AMG;
+  c->pmode = BCS_P_TENTATIVE;
+  c->matching_rounds = 4;
+  c->agg_passes = 2;
+  c->jacobi_omega = 0.8;
+  c->nu1 = 2;
+  c->nu2 = 2;
+  c->coarse_size = 128;
+  c->max_levels = 20;
+  c->max_coarsen_ratio = 0.8;
+  c->p_omega = 4.0 / 3.0;
+  c->coarse_dense_max = 1024;
+  c->coarse_sweeps = 8;
+  c->precision = BCS_PREC_FP32;
+  c->profile = 0;
+  return BCS_OK;
+}
+
+bcs_status bcs_create(bcs_solver** out, int n, const bcs_config* cfg, void* stream) {
+  if (!out) return BCS_EINVAL;
+  *out = nullptr;
+  if (n < 1 || n > 8) return BCS_EINVAL;
+  bcs_config c;
+  if (cfg) c = *cfg;
+  else bcs_config_default(&c);
+  if (check_config(&c) != BCS_OK) return BCS_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return BCS_ECUDA;
+  }
+  // Keep freed blocks in the stream-ordered pool instead of returning them
+  // at every synchronisation (setup allocates and frees temporaries).
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  bcs_solver* h = new (std::nothrow) bcs_solver();
+  if (!h) return BCS_ENOMEM;
+  Solver* s = &h->impl;
+  s->n = n;
+  s->cfg = c;
+  s->setup_cfg = c;
+  s->stream = (cudaStream_t)stream;
+  s->alloc.stream = s->stream;
+  if (!s->flag.resize(&s->alloc, 4) || !s->scal.resize(&s->alloc, 160) ||
+      cudaMallocHost(&s->hscal, 160 * sizeof(double)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete h;
+    return BCS_ENOMEM;
+  }
+  if (cudaMemsetAsync(s->flag.p, 0, 4 * sizeof(int32_t), s->stream) != cudaSuccess) {
+    delete h;
+    return BCS_ECUDA;
+  }
+  *out = h;
+  return BCS_OK;
+}
+
+bcs_status bcs_destroy(bcs_solver* h) {
+  if (!h) return BCS_OK;
+  Solver* s = &h->impl;
+  cudaStreamSynchronize(s->stream);
+  for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
+  if (s->hscal) cudaFreeHost(s->hscal);
+  cudaStream_t st = s->stream;
+  delete h;  // frees device buffers (stream-ordered)
+  cudaStreamSynchronize(st);
+  return BCS_OK;
+}
+
+bcs_status bcs_set_config(bcs_solver* h, const bcs_config* cfg) {
+  if (!h || !cfg) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  if (check_config(cfg) != BCS_OK) return s->fail(BCS_EINVAL, "invalid configuration");
+  if (!same_hierarchy_options(*cfg, s->setup_cfg)) s->have_hierarchy = false;
+  s->cfg = *cfg;
+  return BCS_OK;
+}
+
+bcs_status bcs_set_structure(bcs_solver* h, int32_t C, int32_t F, const int32_t* owner, const int32_t* nb,
+                             int mem) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  s->have_structure = s->have_values = s->have_hierarchy = false;
+  if (C < 1 || F < 0 || (F > 0 && (!owner || !nb)) || (mem != BCS_MEM_HOST && mem != BCS_MEM_DEVICE))
+    return s->fail(BCS_EINVAL, "invalid structure arguments");
+  s->C = C;
+  s->F = F;
+  const int32_t *o = nullptr, *m = nullptr;
+  BCS_OKR(stage(s, owner, (size_t)F, mem, s->stage_o, &o));
+  BCS_OKR(stage(s, nb, (size_t)F, mem, s->stage_n, &m));
+  bcs_status st = build_structure(s, o, m);
+  s->stage_o.release();
+  s->stage_n.release();
+  if (st != BCS_OK) return st;
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  s->have_structure = true;
+  return BCS_OK;
+}
+
+bcs_status bcs_set_values(bcs_solver* h, const double* diag, const double* upper, const double* lower, int mem) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  if (!s->have_structure) return s->fail(BCS_ESTATE, "set_values before set_structure");
+  if (!diag || (s->F > 0 && (!upper || !lower)) || (mem != BCS_MEM_HOST && mem != BCS_MEM_DEVICE))
+    return s->fail(BCS_EINVAL, "invalid value arguments");
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t nn = (size_t)s->n * s->n;
+  const double *d = nullptr, *u = nullptr, *l = nullptr;
+  BCS_OKR(stage(s, diag, s->C * nn, mem, s->stage_d, &d));
+  BCS_OKR(stage(s, upper, s->F * nn, mem, s->stage_u, &u));
+  BCS_OKR(stage(s, lower, s->F * nn, mem, s->stage_l, &l));
+  BCS_OKR(permute_values(s, d, u, l));
+  s->have_values = true;
+  const bool full = !s->have_hierarchy;
+  if (full) s->setup_cfg = s->cfg;
+  s->have_hierarchy = false;
+  BCS_OKR(amg_setup(s, full));
+  BCS_OKR(cycle_prepare(s));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  s->have_hierarchy = true;
+  s->last_setup_ms = ms_since(t0);
+  return BCS_OK;
+}
+
+bcs_status bcs_invalidate_hierarchy(bcs_solver* h) {
+  if (!h) return BCS_EINVAL;
+  h->impl.have_hierarchy = false;
+  return BCS_OK;
+}
+
+bcs_status bcs_solve(bcs_solver* h, const double* b, double* x, int mem, bcs_result* res) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  bcs_result local{};
+  if (!res) res = &local;
+  std::memset(res, 0, sizeof(*res));
+  if (!s->have_hierarchy) return s->fail(BCS_ESTATE, "solve before set_values");
+  if (!b || !x || (mem != BCS_MEM_HOST && mem != BCS_MEM_DEVICE)) return s->fail(BCS_EINVAL, "invalid solve arguments");
+  if (!same_hierarchy_options(s->cfg, s->setup_cfg))
+    return s->fail(BCS_ESTATE, "options changed since the last set_values");
+  const size_t N = (size_t)s->C * s->n;
+  const double* bd = b;
+  double* xd = x;
+  if (mem == BCS_MEM_HOST) {
+    BCS_ALLOC(s, s->kb, N);
+    BCS_ALLOC(s, s->kx, N);
+    BCS_CU(s, cudaMemcpyAsync(s->kb.p, b, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    BCS_CU(s, cudaMemcpyAsync(s->kx.p, x, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    bd = s->kb.p;
+    xd = s->kx.p;
+  }
+  bcs_status st = solve(s, bd, xd, res);
+  if (st == BCS_ECUDA || st == BCS_ENOMEM || st == BCS_EINVAL) return st;
+  if (mem == BCS_MEM_HOST) BCS_OKR(to_host(s, x, xd, N * sizeof(double)));
+  return st;
+}
+
+bcs_status bcs_spmv(bcs_solver* h, const double* x, double* y, int mem) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  if (!s->have_values) return s->fail(BCS_ESTATE, "spmv before set_values");
+  if (!x || !y) return s->fail(BCS_EINVAL, "null vector");
+  const size_t N = (size_t)s->C * s->n;
+  const double* xd = x;
+  double* yd = y;
+  if (mem == BCS_MEM_HOST) {
+    BCS_ALLOC(s, s->kb, N);
+    BCS_ALLOC(s, s->kx, N);
+    BCS_CU(s, cudaMemcpyAsync(s->kb.p, x, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    xd = s->kb.p;
+    yd = s->kx.p;
+  }
+  BCS_OKR(spmv64(s, s->lv[0].A, xd, false, yd, nullptr, K_SPMV64));
+  if (mem == BCS_MEM_HOST) BCS_OKR(to_host(s, y, yd, N * sizeof(double)));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  return BCS_OK;
+}
+
+bcs_status bcs_precond_apply(bcs_solver* h, const double* v, double* z, int mem) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  if (!s->have_hierarchy) return s->fail(BCS_ESTATE, "precond_apply before set_values");
+  if (!v || !z) return s->fail(BCS_EINVAL, "null vector");
+  const size_t N = (size_t)s->C * s->n;
+  BCS_ALLOC(s, s->kb, N);
+  BCS_ALLOC(s, s->kx, N);
+  DBuf<char> zt;
+  BCS_ALLOC(s, zt, N * sizeof(double));
+  const double* vd = v;
+  if (mem == BCS_MEM_HOST) {
+    BCS_CU(s, cudaMemcpyAsync(s->kb.p, v, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    vd = s->kb.p;
+  }
+  double* zd = mem == BCS_MEM_HOST ? s->kx.p : z;
+  switch (s->setup_cfg.precond) {
+    case BCS_PC_AMG:
+      BCS_OKR(precond_apply(s, vd, zt.p));
+      if (cycle_is_float(s)) BCS_OKR(cast_vec<float, double>(s, (const float*)zt.p, zd, N));
+      else BCS_CU(s, cudaMemcpyAsync(zd, zt.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+      break;
+    case BCS_PC_JACOBI:
+      BCS_OKR(jacobi_apply(s, vd, zd));
+      break;
+    default:
+      BCS_CU(s, cudaMemcpyAsync(zd, vd, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  }
+  if (mem == BCS_MEM_HOST) BCS_OKR(to_host(s, z, zd, N * sizeof(double)));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  return BCS_OK;
+}
+
+bcs_status bcs_get_bsr(bcs_solver* h, int32_t* rp, int32_t* col, double* val, int32_t* pd, int32_t* pu,
+                       int32_t* pl) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  if (!s->have_structure) return s->fail(BCS_ESTATE, "no structure");
+  const Bsr& A = s->lv[0].A;
+  BCS_OKR(to_host(s, rp, A.rp.p, (A.rows + 1) * sizeof(int32_t)));
+  BCS_OKR(to_host(s, col, A.ci.p, (size_t)A.nnz * sizeof(int32_t)));
+  if (val) {
+    if (!s->have_values) return s->fail(BCS_ESTATE, "no values");
+    BCS_OKR(to_host(s, val, A.v.p, (size_t)A.nnz * s->n * s->n * sizeof(double)));
+  }
+  BCS_OKR(to_host(s, pd, s->pos_diag.p, (size_t)s->C * sizeof(int32_t)));
+  BCS_OKR(to_host(s, pu, s->pos_up.p, (size_t)s->F * sizeof(int32_t)));
+  BCS_OKR(to_host(s, pl, s->pos_lo.p, (size_t)s->F * sizeof(int32_t)));
+  return BCS_OK;
+}
+
+int bcs_num_levels(const bcs_solver* h) {
+  if (!h || !h->impl.have_hierarchy) return 0;
+  return (int)h->impl.lv.size();
+}
+
+bcs_status bcs_get_level_info(const bcs_solver* h, int l, int* rows, int* nnz, int* p_nnz, int* kind) {
+  if (!h) return BCS_EINVAL;
+  const Solver* s = &h->impl;
+  if (!s->have_hierarchy || l < 0 || l >= (int)s->lv.size()) return BCS_EINVAL;
+  const Level& L = s->lv[l];
+  if (rows) *rows = L.A.rows;
+  if (nnz) *nnz = L.A.nnz;
+  if (p_nnz) *p_nnz = (L.coarse_kind < 0 && s->setup_cfg.pmode == BCS_P_SMOOTHED) ? L.P.nnz : 0;
+  if (kind) *kind = L.coarse_kind;
+  return BCS_OK;
+}
+
+bcs_status bcs_get_level(bcs_solver* h, int l, int32_t* rp, int32_t* col, double* val, int32_t* agg,
+                         double* dinv) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  if (!s->have_hierarchy || l < 0 || l >= (int)s->lv.size()) return s->fail(BCS_EINVAL, "no such level");
+  const Level& L = s->lv[l];
+  const size_t nn = (size_t)s->n * s->n;
+  BCS_OKR(to_host(s, rp, L.A.rp.p, (L.A.rows + 1) * sizeof(int32_t)));
+  BCS_OKR(to_host(s, col, L.A.ci.p, (size_t)L.A.nnz * sizeof(int32_t)));
+  BCS_OKR(to_host(s, val, L.A.v.p, (size_t)L.A.nnz * nn * sizeof(double)));
+  if (agg && L.coarse_kind < 0) BCS_OKR(to_host(s, agg, L.agg.p, (size_t)L.A.rows * sizeof(int32_t)));
+  BCS_OKR(to_host(s, dinv, L.dinv.p, (size_t)L.A.rows * nn * sizeof(double)));
+  return BCS_OK;
+}
+
+bcs_status bcs_get_prolongation(bcs_solver* h, int l, int32_t* rp, int32_t* col, double* val, double* omega) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  if (!s->have_hierarchy || l < 0 || l + 1 >= (int)s->lv.size() || s->setup_cfg.pmode != BCS_P_SMOOTHED)
+    return s->fail(BCS_EINVAL, "no smoothed prolongation at this level");
+  const Level& L = s->lv[l];
+  BCS_OKR(to_host(s, rp, L.P.rp.p, (L.P.rows + 1) * sizeof(int32_t)));
+  BCS_OKR(to_host(s, col, L.P.ci.p, (size_t)L.P.nnz * sizeof(int32_t)));
+  BCS_OKR(to_host(s, val, L.P.v.p, (size_t)L.P.nnz * s->n * s->n * sizeof(double)));
+  if (omega) *omega = L.omega_p;
+  return BCS_OK;
+}
+
+bcs_status bcs_get_coarse_inverse(bcs_solver* h, double* inv) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  if (!s->have_hierarchy || s->lv.back().coarse_kind != 0) return s->fail(BCS_EINVAL, "no dense coarse inverse");
+  return to_host(s, inv, s->cinv.p, (size_t)s->cN * s->cN * sizeof(double));
+}
+
+bcs_status bcs_get_stats(bcs_solver* h, bcs_stats* st) {
+  if (!h || !st) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  s->flush_timers();
+  std::memset(st, 0, sizeof(*st));
+  st->launches = s->launches;
+  for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {
+    st->kind_launches[k] = s->kind_launches[k];
+    st->kind_ms[k] = s->kind_ms[k];
+    st->kind_bytes[k] = s->kind_bytes[k];
+    st->kind_flops[k] = s->kind_flops[k];
+  }
+  return BCS_OK;
+}
+
+bcs_status bcs_reset_stats(bcs_solver* h) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  s->flush_timers();
+  s->launches = 0;
+  for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {
+    s->kind_launches[k] = 0;
+    s->kind_ms[k] = 0.0;
+    s->kind_bytes[k] = 0.0;
+    s->kind_flops[k] = 0.0;
+  }
+  return BCS_OK;
+}
+
+const char* bcs_kernel_kind_name(int k) { return kind_name(k); }
+
+const char* bcs_last_error(const bcs_solver* h) { return h ? h->impl.err.c_str() : "null solver"; }
+
+size_t bcs_device_bytes(const bcs_solver* h) { return h ? h->impl.alloc.live : 0; }
+
+}  // extern "C"

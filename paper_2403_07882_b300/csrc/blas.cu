@@ -1,0 +1,176 @@
+// FP64 vector kernels of the Krylov solvers: deterministic multi-dot
+// products (a fixed grid and a fixed reduction tree, so results do not depend
+// on timing), classical Gram-Schmidt updates, and the axpy family.
+#include "internal.h"
+
+namespace bcs {
+
+namespace {
+
+constexpr int RED_BLOCKS = 296;  // 2 x 148 SMs; fixed for reproducibility
+constexpr int RED_THREADS = 256;
+constexpr int MD_CHUNK = 8;      // vectors per multidot block row
+
+// partial[q * RED_BLOCKS + block] = sum over this block's share of i of
+// V[q][i] * w[i], for q in this chunk.
+__global__ void __launch_bounds__(RED_THREADS) k_multidot(const double* __restrict__ V, size_t ldv, int k,
+                                                          const double* __restrict__ w, size_t N,
+                                                          double* __restrict__ partial) {
+  __shared__ double sm[MD_CHUNK][RED_THREADS / 32];
+  const int q0 = blockIdx.y * MD_CHUNK;
+  const int nq = min(MD_CHUNK, k - q0);
+  double acc[MD_CHUNK];
+#pragma unroll
+  for (int q = 0; q < MD_CHUNK; ++q) acc[q] = 0.0;
+  const size_t stride = (size_t)RED_BLOCKS * RED_THREADS;
+  for (size_t i = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; i < N; i += stride) {
+    const double wi = __ldg(w + i);
+#pragma unroll
+    for (int q = 0; q < MD_CHUNK; ++q)
+      if (q < nq) acc[q] = fma(__ldg(V + (size_t)(q0 + q) * ldv + i), wi, acc[q]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < MD_CHUNK; ++q) {
+    double v = acc[q];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    if (lane == 0) sm[q][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nq) {
+    double v = 0.0;
+    for (int wv = 0; wv < RED_THREADS / 32; ++wv) v += sm[threadIdx.x][wv];
+    partial[(size_t)(q0 + threadIdx.x) * RED_BLOCKS + blockIdx.x] = v;
+  }
+}
+
+// out[q] = sum of the RED_BLOCKS partials of vector q (fixed tree).
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_partials(const double* __restrict__ partial,
+                                                                 double* __restrict__ out) {
+  __shared__ double sm[RED_THREADS / 32];
+  const int q = blockIdx.x;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < RED_BLOCKS; b += RED_THREADS) v += partial[(size_t)q * RED_BLOCKS + b];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int wv = 0; wv < RED_THREADS / 32; ++wv) t += sm[wv];
+    out[q] = t;
+  }
+}
+
+// w[i] -= sum_q h[q] V[q][i]
+__global__ void k_gs_update(const double* __restrict__ V, size_t ldv, int k, const double* __restrict__ h,
+                            double* __restrict__ w, size_t N) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    double t = w[i];
+    for (int q = 0; q < k; ++q) t = fma(-__ldg(h + q), __ldg(V + (size_t)q * ldv + i), t);
+    w[i] = t;
+  }
+}
+
+struct Coefs {
+  double c[72];
+};
+
+// x[i] += sum_q y[q] Z[q][i]
+template <class TZ>
+__global__ void k_add_combination(const TZ* __restrict__ Z, size_t ldz, int k, Coefs y, double* __restrict__ x,
+                                  size_t N) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    double t = x[i];
+    for (int q = 0; q < k; ++q) t = fma(y.c[q], (double)Z[(size_t)q * ldz + i], t);
+    x[i] = t;
+  }
+}
+
+// y = a x + b y
+__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, size_t N) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+// y = a x
+__global__ void k_scale(double a, const double* x, double* y, size_t N) {  // may run in place
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+// p = r + beta (p - omega v)
+__global__ void k_bicg_p(double beta, double omega, const double* __restrict__ r, const double* __restrict__ v,
+                         double* __restrict__ p, size_t N) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = r[i] + beta * (p[i] - omega * v[i]);
+}
+
+unsigned vgrid(size_t N) {
+  unsigned g = grid_for(N, 256);
+  return g > 148u * 16u ? 148u * 16u : g;
+}
+
+}  // namespace
+
+bcs_status multidot(Solver* s, const double* V, size_t ldv, int k, const double* w, size_t N, int slot) {
+  if (k <= 0) return BCS_OK;
+  const int chunks = (k + MD_CHUNK - 1) / MD_CHUNK;
+  BCS_ALLOC(s, s->red, (size_t)72 * RED_BLOCKS);
+  if (k > 72) return s->fail(BCS_EINVAL, "too many vectors in one multidot");
+  const dim3 grid(RED_BLOCKS, chunks);
+  BCS_LAUNCH(s, K_BLAS, 8.0 * N * (k + chunks), 2.0 * N * k, k_multidot, grid, RED_THREADS, 0, V, ldv, k, w, N,
+             s->red.p);
+  BCS_LAUNCH(s, K_BLAS, 8.0 * k * RED_BLOCKS, 0, k_reduce_partials, k, RED_THREADS, 0, s->red.p, s->scal.p + slot);
+  return BCS_OK;
+}
+
+bcs_status dot(Solver* s, const double* x, const double* y, size_t N, int slot) {
+  return multidot(s, x, N, 1, y, N, slot);
+}
+
+bcs_status fetch_scalars(Solver* s, int count) {
+  BCS_CU(s, cudaMemcpyAsync(s->hscal, s->scal.p, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  return BCS_OK;
+}
+
+bcs_status gs_update(Solver* s, const double* V, size_t ldv, int k, const double* hdev, double* w, size_t N) {
+  BCS_LAUNCH(s, K_BLAS, 8.0 * N * (k + 2), 2.0 * N * k, k_gs_update, vgrid(N), 256, 0, V, ldv, k, hdev, w, N);
+  return BCS_OK;
+}
+
+bcs_status add_combination(Solver* s, const void* Z, bool z_float, size_t ldz, int k, const double* y, double* x,
+                           size_t N) {
+  if (k > 72) return s->fail(BCS_EINVAL, "too many vectors in one combination");
+  Coefs c{};
+  for (int q = 0; q < k; ++q) c.c[q] = y[q];
+  if (z_float)
+    BCS_LAUNCH(s, K_BLAS, (4.0 * k + 16.0) * N, 2.0 * N * k, k_add_combination<float>, vgrid(N), 256, 0,
+               (const float*)Z, ldz, k, c, x, N);
+  else
+    BCS_LAUNCH(s, K_BLAS, (8.0 * k + 16.0) * N, 2.0 * N * k, k_add_combination<double>, vgrid(N), 256, 0,
+               (const double*)Z, ldz, k, c, x, N);
+  return BCS_OK;
+}
+
+bcs_status axpby(Solver* s, double a, const double* x, double b, double* y, size_t N) {
+  BCS_LAUNCH(s, K_BLAS, 24.0 * N, 3.0 * N, k_axpby, vgrid(N), 256, 0, a, x, b, y, N);
+  return BCS_OK;
+}
+
+bcs_status scale_copy(Solver* s, double a, const double* x, double* y, size_t N) {
+  BCS_LAUNCH(s, K_BLAS, 16.0 * N, 1.0 * N, k_scale, vgrid(N), 256, 0, a, x, y, N);
+  return BCS_OK;
+}
+
+bcs_status bicg_p_update(Solver* s, double beta, double omega, const double* r, const double* v, double* p,
+                         size_t N) {
+  BCS_LAUNCH(s, K_BLAS, 32.0 * N, 4.0 * N, k_bicg_p, vgrid(N), 256, 0, beta, omega, r, v, p, N);
+  return BCS_OK;
+}
+
+
+}  // namespace bcs

@@ -237,8 +237,6 @@ bcs_status add_combination(Solver* s, const void* Z, bool z_float, size_t ldz, i
                            const double* ydev, double* x, size_t N);
 bcs_status bicg_p_update(Solver* s, double beta, double omega, const double* r, const double* v,
                          double* p, size_t N);
-bcs_status bicg_x_update(Solver* s, double alpha, const double* ph, double omega, const double* sh,
-                         double* x, size_t N);
 
 // ------------------------------------------------------------------- cycle.cu
 enum Mode { M_SPMV = 0, M_ADD = 1, M_RESID = 2 };

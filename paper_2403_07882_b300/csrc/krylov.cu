@@ -1,0 +1,326 @@
+// Krylov solvers (Sec. 2.3: GMRES and BiCGStab with an AMG preconditioner).
+//
+// FGMRES(m): right-preconditioned flexible GMRES (GMRES of Saad & Schultz;
+// flexible because the mixed-precision preconditioner is not a fixed linear
+// operator), classical Gram-Schmidt applied twice, Givens rotations on the
+// host, restart after m steps. A cycle ends when the rotated residual
+// |g_{j+1}| <= tol ||b||; convergence is decided on the true residual
+// ||b - A x|| / ||b|| recomputed in FP64 at every cycle end. Happy breakdown
+// when h_{j+1,j} <= 1e-14 ||A z_j||.
+//
+// BiCGStab (van der Vorst), right-preconditioned, r_hat = r_0; a converged
+// recurrence residual is confirmed with the true residual and the iteration
+// restarted from it otherwise; rho = 0, (r_hat, v) = 0 or (t, t) = 0 restart
+// once from the true residual, a second time report breakdown.
+//
+// All vectors are FP64 on the device; the preconditioner output z is stored
+// in the cycle precision (FP32 in mixed mode, exactly representable in FP64).
+#include <chrono>
+#include <cmath>
+
+#include "internal.h"
+
+namespace bcs {
+
+namespace {
+
+constexpr int SLOT_A = 0;     // first Gram-Schmidt pass
+constexpr int SLOT_B = 72;    // second pass
+constexpr int SLOT_N = 144;   // norms
+
+size_t zbytes(const Solver* s) { return cycle_is_float(s) ? sizeof(float) : sizeof(double); }
+
+// z = M^{-1} v (z in the cycle precision)
+bcs_status apply_M(Solver* s, const double* v, void* z, size_t N) {
+  switch (s->setup_cfg.precond) {
+    case BCS_PC_AMG:
+      return precond_apply(s, v, z);
+    case BCS_PC_JACOBI:
+      return jacobi_apply(s, v, (double*)z);
+    default:
+      BCS_CU(s, cudaMemcpyAsync(z, v, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+      return BCS_OK;
+  }
+}
+
+bcs_status norm(Solver* s, const double* x, size_t N, double* out) {
+  BCS_OKR(dot(s, x, x, N, SLOT_N));
+  BCS_OKR(fetch_scalars(s, SLOT_N + 1));
+  *out = std::sqrt(s->hscal[SLOT_N]);
+  return BCS_OK;
+}
+
+// r = b - A x, returns ||r||
+bcs_status true_residual(Solver* s, const double* b, const double* x, double* r, size_t N, double* rn) {
+  BCS_OKR(spmv64(s, s->lv[0].A, x, false, r, b, K_SPMV64));
+  return norm(s, r, N, rn);
+}
+
+bcs_status fgmres(Solver* s, const double* b, double* x, bcs_result* res) {
+  const bcs_config& cfg = s->cfg;
+  const int m = cfg.restart;
+  const size_t N = (size_t)s->C * s->n;
+  const bool zf = cycle_is_float(s);
+  BCS_ALLOC(s, s->kv, (size_t)(m + 1) * N);
+  BCS_ALLOC(s, s->kz, (size_t)m * N * zbytes(s));
+  BCS_ALLOC(s, s->kr, N);
+  double* V = s->kv.p;
+  char* Z = s->kz.p;
+  double* r = s->kr.p;
+  double bnorm = 0.0;
+  BCS_OKR(norm(s, b, N, &bnorm));
+  res->iters = 0;
+  res->restarts = 0;
+  if (bnorm == 0.0) {
+    BCS_CU(s, cudaMemsetAsync(x, 0, N * sizeof(double), s->stream));
+    res->rel_res_initial = res->rel_res_final = 0.0;
+    return BCS_OK;
+  }
+  double beta = 0.0;
+  BCS_OKR(true_residual(s, b, x, r, N, &beta));
+  res->rel_res_initial = res->rel_res_final = beta / bnorm;
+  if (!std::isfinite(beta)) return BCS_BREAKDOWN;
+  if (beta <= cfg.tol * bnorm) return BCS_OK;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), g(m + 1), cs(m), sn(m), y(m);
+  int iters = 0;
+  bcs_status status = BCS_OK;
+  for (;;) {
+    BCS_OKR(scale_copy(s, 1.0 / beta, r, V, N));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jend = 0;
+    bool breakdown = false;
+    for (int j = 0; j < m; ++j) {
+      double* w = V + (size_t)(j + 1) * N;
+      void* zj = Z + (size_t)j * N * zbytes(s);
+      BCS_OKR(apply_M(s, V + (size_t)j * N, zj, N));
+      BCS_OKR(spmv64(s, s->lv[0].A, zj, zf, w, nullptr, K_SPMV64));
+      // pass 1 also yields ||w||^2 (w is vector j+1 of V)
+      BCS_OKR(multidot(s, V, N, j + 2, w, N, SLOT_A));
+      BCS_OKR(gs_update(s, V, N, j + 1, s->scal.p + SLOT_A, w, N));
+      BCS_OKR(multidot(s, V, N, j + 1, w, N, SLOT_B));
+      BCS_OKR(gs_update(s, V, N, j + 1, s->scal.p + SLOT_B, w, N));
+      BCS_OKR(dot(s, w, w, N, SLOT_N));
+      BCS_OKR(fetch_scalars(s, SLOT_N + 1));
+      const double* hs = s->hscal;
+      const double wn0 = std::sqrt(hs[SLOT_A + j + 1]);
+      const double hn = std::sqrt(hs[SLOT_N]);
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hs[SLOT_A + i] + hs[SLOT_B + i];
+      H[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+      if (c == 0.0) {
+        cs[j] = 1.0;
+        sn[j] = 0.0;
+      } else {
+        const double d = std::sqrt(a * a + c * c);
+        cs[j] = a / d;
+        sn[j] = c / d;
+      }
+      H[(size_t)j * m + j] = cs[j] * a + sn[j] * c;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++iters;
+      jend = j + 1;
+      if (!std::isfinite(hn) || !std::isfinite(g[j + 1])) {
+        breakdown = true;
+        break;
+      }
+      if (!(hn > 1e-14 * wn0)) break;  // happy breakdown: no v_{j+1}
+      BCS_OKR(scale_copy(s, 1.0 / hn, w, w, N));
+      if (std::fabs(g[j + 1]) <= cfg.tol * bnorm || iters >= cfg.maxiter) break;
+    }
+    for (int i = jend - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int k = i + 1; k < jend; ++k) t -= H[(size_t)i * m + k] * y[k];
+      y[i] = t / H[(size_t)i * m + i];
+    }
+    if (!breakdown) BCS_OKR(add_combination(s, Z, zf, N, jend, y.data(), x, N));
+    BCS_OKR(true_residual(s, b, x, r, N, &beta));
+    res->rel_res_final = beta / bnorm;
+    if (breakdown || !std::isfinite(beta)) {
+      status = BCS_BREAKDOWN;
+      break;
+    }
+    if (beta <= cfg.tol * bnorm) {
+      status = BCS_OK;
+      break;
+    }
+    if (iters >= cfg.maxiter) {
+      status = BCS_NOT_CONVERGED;
+      break;
+    }
+    res->restarts++;
+  }
+  res->iters = iters;
+  return status;
+}
+
+bcs_status bicgstab(Solver* s, const double* b, double* x, bcs_result* res) {
+  const bcs_config& cfg = s->cfg;
+  const size_t N = (size_t)s->C * s->n;
+  const bool zf = cycle_is_float(s);
+  BCS_ALLOC(s, s->kv, (size_t)6 * N);
+  BCS_ALLOC(s, s->kz, (size_t)2 * N * zbytes(s));
+  double *r = s->kv.p, *rhat = r + N, *p = r + 2 * N, *v = r + 3 * N, *sv = r + 4 * N, *t = r + 5 * N;
+  void* ph = s->kz.p;
+  void* sh = s->kz.p + N * zbytes(s);
+  const double tol = cfg.tol;
+  double bnorm = 0.0;
+  BCS_OKR(norm(s, b, N, &bnorm));
+  res->iters = 0;
+  res->restarts = 0;
+  if (bnorm == 0.0) {
+    BCS_CU(s, cudaMemsetAsync(x, 0, N * sizeof(double), s->stream));
+    res->rel_res_initial = res->rel_res_final = 0.0;
+    return BCS_OK;
+  }
+  double rn = 0.0;
+  BCS_OKR(true_residual(s, b, x, r, N, &rn));
+  res->rel_res_initial = res->rel_res_final = rn / bnorm;
+  if (!std::isfinite(rn)) return BCS_BREAKDOWN;
+  if (rn <= tol * bnorm) return BCS_OK;
+  BCS_CU(s, cudaMemcpyAsync(rhat, r, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+  bool first = true, restarted = false;
+  int it = 0;
+  bcs_status status = BCS_NOT_CONVERGED;
+  // restart from the true residual; false when a breakdown recurs
+  auto restart = [&](bool breakdown, bool* ok) -> bcs_status {
+    *ok = true;
+    if (breakdown) {
+      if (restarted) {
+        *ok = false;
+        return BCS_OK;
+      }
+      restarted = true;
+    }
+    double tr = 0.0;
+    BCS_OKR(true_residual(s, b, x, r, N, &tr));
+    BCS_CU(s, cudaMemcpyAsync(rhat, r, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    first = true;
+    res->restarts++;
+    return BCS_OK;
+  };
+  bool ok = true;
+  while (it < cfg.maxiter) {
+    BCS_OKR(dot(s, rhat, r, N, SLOT_A));
+    BCS_OKR(fetch_scalars(s, 1));
+    const double rho = s->hscal[0];
+    if (rho == 0.0 || !std::isfinite(rho)) {
+      BCS_OKR(restart(true, &ok));
+      if (!ok) {
+        status = BCS_BREAKDOWN;
+        break;
+      }
+      continue;
+    }
+    if (first) {
+      BCS_CU(s, cudaMemcpyAsync(p, r, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    } else {
+      const double beta = (rho / rho_old) * (alpha / omega);
+      BCS_OKR(bicg_p_update(s, beta, omega, r, v, p, N));
+    }
+    first = false;
+    BCS_OKR(apply_M(s, p, ph, N));
+    BCS_OKR(spmv64(s, s->lv[0].A, ph, zf, v, nullptr, K_SPMV64));
+    BCS_OKR(dot(s, rhat, v, N, SLOT_A));
+    BCS_OKR(fetch_scalars(s, 1));
+    const double den = s->hscal[0];
+    if (den == 0.0 || !std::isfinite(den)) {
+      BCS_OKR(restart(true, &ok));
+      if (!ok) {
+        status = BCS_BREAKDOWN;
+        break;
+      }
+      continue;
+    }
+    alpha = rho / den;
+    BCS_CU(s, cudaMemcpyAsync(sv, r, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    BCS_OKR(axpby(s, -alpha, v, 1.0, sv, N));
+    ++it;
+    double snrm = 0.0;
+    BCS_OKR(norm(s, sv, N, &snrm));
+    if (snrm <= tol * bnorm) {
+      BCS_OKR(add_combination(s, ph, zf, N, 1, &alpha, x, N));
+      double tr = 0.0;
+      BCS_OKR(true_residual(s, b, x, r, N, &tr));
+      if (tr <= tol * bnorm) {
+        status = BCS_OK;
+        break;
+      }
+      BCS_OKR(restart(false, &ok));
+      continue;
+    }
+    BCS_OKR(apply_M(s, sv, sh, N));
+    BCS_OKR(spmv64(s, s->lv[0].A, sh, zf, t, nullptr, K_SPMV64));
+    BCS_OKR(multidot(s, sv, N, 2, t, N, SLOT_A));  // (s, t), (t, t)
+    BCS_OKR(fetch_scalars(s, 2));
+    const double ts = s->hscal[0], tt = s->hscal[1];
+    if (tt == 0.0 || !std::isfinite(tt)) {
+      BCS_OKR(restart(true, &ok));
+      if (!ok) {
+        status = BCS_BREAKDOWN;
+        break;
+      }
+      continue;
+    }
+    omega = ts / tt;
+    {
+      const double coef[2] = {alpha, omega};
+      BCS_OKR(add_combination(s, ph, zf, N, 2, coef, x, N));  // ph and sh are consecutive
+    }
+    BCS_CU(s, cudaMemcpyAsync(r, sv, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    BCS_OKR(axpby(s, -omega, t, 1.0, r, N));
+    rho_old = rho;
+    BCS_OKR(norm(s, r, N, &rn));
+    if (rn <= tol * bnorm) {
+      double tr = 0.0;
+      BCS_OKR(true_residual(s, b, x, r, N, &tr));
+      if (tr <= tol * bnorm) {
+        status = BCS_OK;
+        break;
+      }
+      BCS_OKR(restart(false, &ok));
+      continue;
+    }
+    if (omega == 0.0) {
+      BCS_OKR(restart(true, &ok));
+      if (!ok) {
+        status = BCS_BREAKDOWN;
+        break;
+      }
+    }
+  }
+  double tr = 0.0;
+  BCS_OKR(true_residual(s, b, x, s->kv.p, N, &tr));
+  res->rel_res_final = tr / bnorm;
+  if (status == BCS_NOT_CONVERGED && res->rel_res_final <= tol) status = BCS_OK;
+  if (status == BCS_NOT_CONVERGED && !std::isfinite(tr)) status = BCS_BREAKDOWN;
+  res->iters = it;
+  return status;
+}
+
+}  // namespace
+
+bcs_status solve(Solver* s, const double* b, double* x, bcs_result* res) {
+  const auto t0 = std::chrono::steady_clock::now();
+  bcs_status st = s->cfg.solver == BCS_BICGSTAB ? bicgstab(s, b, x, res) : fgmres(s, b, x, res);
+  if (st == BCS_ECUDA || st == BCS_ENOMEM || st == BCS_EINVAL) return st;
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return s->fail(BCS_ECUDA, std::string("solve: ") + cudaGetErrorString(e));
+  res->status = st;
+  res->levels = (int)s->lv.size();
+  res->setup_ms = s->last_setup_ms;
+  res->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (st == BCS_NOT_CONVERGED) s->err = "maximum iterations reached above the tolerance";
+  if (st == BCS_BREAKDOWN) s->err = "Krylov breakdown or non-finite residual";
+  return st;
+}
+
+}  // namespace bcs

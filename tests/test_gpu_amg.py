@@ -1,0 +1,130 @@
+"""GPU parity of the AMG setup (aggregates, Galerkin operators, block and
+coarse inverses, smoothed prolongation: bit-exact with the FP64 CPU
+reference) and of the V-cycle (1e-12 in FP64; FP32/BF16 storage within a
+tolerance derived from the storage precision)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_07882_b300 import bcs, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+CASES = [
+    ("density 16^3", lambda: synth.density(16, seed=0), {}),
+    ("density 10x7x5 smoothed", lambda: synth.density(10, 7, 5, seed=3), dict(pmode=0)),
+    ("pressure 12^3", lambda: synth.pressure(12, seed=1), {}),
+    ("pressure 9^3 smoothed", lambda: synth.pressure(9, seed=2), dict(pmode=0)),
+    ("random n=3 one pass", lambda: synth.random_graph(300, 900, 3, seed=5), dict(agg_passes=1, coarse_size=8)),
+    ("random n=2 three passes", lambda: synth.random_graph(400, 1000, 2, seed=6), dict(agg_passes=3, coarse_size=4)),
+]
+
+
+def oracle_cfg(**kw):
+    return oracle.config(**{k: v for k, v in kw.items() if k != "precision"})
+
+
+def compare_hierarchy(s, amg, n, pmode):
+    assert s.levels == amg.levels
+    for l in range(amg.levels):
+        g = s.level(l)
+        A = amg.A(l)
+        assert np.array_equal(g["row_ptr"], A["row_ptr"]), l
+        assert np.array_equal(g["col"], A["col"]), l
+        assert np.array_equal(g["val"], A["val"]), l
+        assert np.array_equal(g["dinv"], amg.dinv(l)), l
+        info = amg.info(l)
+        assert g["coarse_kind"] == info["coarse_kind"]
+        if info["coarse_kind"] < 0:
+            P = amg.P(l)
+            assert np.array_equal(g["agg"], P["agg"]), l
+            if pmode == 0:
+                gp = s.prolongation(l)
+                assert gp["omega"] == P["omega"]
+                assert np.array_equal(gp["row_ptr"], P["row_ptr"]) and np.array_equal(gp["col"], P["col"])
+                assert np.array_equal(gp["val"], P["val"])
+    if amg.info(amg.levels - 1)["coarse_kind"] == 0:
+        assert np.array_equal(s.coarse_inverse(), amg.coarse_inverse())
+
+
+@pytest.mark.parametrize("name,gen,kw", CASES, ids=[c[0] for c in CASES])
+def test_setup_bit_exact(name, gen, kw):
+    system = gen()
+    ref = oracle.ldu_to_bsr(system)
+    amg = oracle.Amg(ref, oracle_cfg(**kw))
+    assert amg.status == 0
+    with bcs.Solver(system["n"], precision=bcs.BCS_PREC_FP64, **kw) as s:
+        s.load(system, device=DEV)
+        compare_hierarchy(s, amg, system["n"], kw.get("pmode", 1))
+
+
+@pytest.mark.parametrize("name,gen,kw", CASES, ids=[c[0] for c in CASES])
+def test_resetup_bit_exact(name, gen, kw):
+    system = gen()
+    ref = oracle.ldu_to_bsr(system)
+    amg = oracle.Amg(ref, oracle_cfg(**kw))
+    rng = np.random.default_rng(11)
+    with bcs.Solver(system["n"], precision=bcs.BCS_PREC_FP64, **kw) as s:
+        s.load(system, device=DEV)
+        for _ in range(2):
+            system = synth.perturb(system, rng, 0.02)
+            new = oracle.ldu_to_bsr(system)
+            assert amg.resetup(new["val"]) == 0
+            s.set_values(*(torch.from_numpy(system[k]).to(DEV) for k in ("diag", "upper", "lower")))
+            compare_hierarchy(s, amg, system["n"], kw.get("pmode", 1))
+
+
+@pytest.mark.parametrize("name,gen,kw", CASES, ids=[c[0] for c in CASES])
+def test_vcycle_fp64_parity(name, gen, kw):
+    system = gen()
+    ref = oracle.ldu_to_bsr(system)
+    amg = oracle.Amg(ref, oracle_cfg(**kw))
+    v = np.random.default_rng(4).standard_normal(system["b"].shape)
+    z_ref = amg.vcycle(v)
+    with bcs.Solver(system["n"], precision=bcs.BCS_PREC_FP64, **kw) as s:
+        s.load(system, device=DEV)
+        z = s.precond(torch.from_numpy(v).to(DEV)).cpu().numpy()
+    assert np.abs(z - z_ref).max() <= 1e-12 * np.abs(z_ref).max()
+
+
+@pytest.mark.parametrize("precision,tol", [(bcs.BCS_PREC_FP32, 2e-5), (bcs.BCS_PREC_BF16, 5e-2)])
+@pytest.mark.parametrize("name,gen,kw", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_vcycle_low_precision(precision, tol, name, gen, kw):
+    """FP32 storage/arithmetic: unit roundoff 6e-8 amplified by the cycle's
+    few dozen operations and the operator norms gives a 2e-5 bound relative
+    to ||z||; BF16 storage (roundoff 4e-3) perturbs the operator itself, so
+    only a 5e-2 relative agreement is expected."""
+    system = gen()
+    ref = oracle.ldu_to_bsr(system)
+    amg = oracle.Amg(ref, oracle_cfg(**kw))
+    v = np.random.default_rng(5).standard_normal(system["b"].shape)
+    z_ref = amg.vcycle(v)
+    with bcs.Solver(system["n"], precision=precision, **kw) as s:
+        s.load(system, device=DEV)
+        z = s.precond(torch.from_numpy(v).to(DEV)).cpu().numpy()
+    assert np.linalg.norm(z - z_ref) <= tol * np.linalg.norm(z_ref)
+
+
+def test_singular_block_reported():
+    system = synth.density(6, seed=6)
+    system["diag"][4] = 0.0
+    with bcs.Solver(5) as s:
+        with pytest.raises(bcs.BcsError) as e:
+            s.load(system, device=DEV)
+        assert e.value.status == bcs.BCS_SINGULAR_BLOCK
+        with pytest.raises(bcs.BcsError) as e:
+            bcs.bcs_solve(s.h, system["b"], np.zeros_like(system["b"]))
+        assert e.value.status == bcs.BCS_ESTATE
+
+
+def test_determinism_two_setups():
+    system = synth.pressure(16, seed=4)
+    outs = []
+    for _ in range(2):
+        with bcs.Solver(4, precision=bcs.BCS_PREC_FP32) as s:
+            s.load(system, device=DEV)
+            v = torch.from_numpy(system["b"]).to(DEV)
+            outs.append(s.precond(v).cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])

@@ -1,0 +1,142 @@
+"""GPU parity of the Krylov solves (Sec. 2.3: GMRES / BiCGStab with AMG):
+every GPU solution reaches the true relative residual 1e-8, recomputed on
+the CPU with the FP64 reference SpMV; the reference solver reaches the same
+tolerance on the same system; the solution difference is reported per case.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_07882_b300 import bcs, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def true_rel(ref, b, x):
+    r = b - oracle.spmv(ref, x)
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+def gpu_solve(system, x0=None, device=True, **cfg):
+    with bcs.Solver(system["n"], **cfg) as s:
+        s.load(system, device=DEV if device else None)
+        if device:
+            b = torch.from_numpy(system["b"]).to(DEV)
+            x = torch.zeros_like(b) if x0 is None else torch.from_numpy(x0).to(DEV)
+            x, st, res = s.solve(b, x)
+            x = x.cpu().numpy()
+        else:
+            x = np.zeros_like(system["b"]) if x0 is None else x0.copy()
+            x, st, res = s.solve(system["b"], x)
+    return x, st, res
+
+
+SOLVES = [
+    ("c1 density 16^3 fgmres fp32", lambda: synth.density(16, seed=0), dict()),
+    ("c1 density 16^3 fgmres fp64", lambda: synth.density(16, seed=0), dict(precision=bcs.BCS_PREC_FP64)),
+    ("c1 density 16^3 fgmres bf16", lambda: synth.density(16, seed=0), dict(precision=bcs.BCS_PREC_BF16)),
+    ("c1 density 16^3 bicgstab fp32", lambda: synth.density(16, seed=0), dict(solver=bcs.BCS_BICGSTAB)),
+    ("pressure 16^3 bicgstab fp32", lambda: synth.pressure(16, seed=1), dict(solver=bcs.BCS_BICGSTAB)),
+    ("pressure 16^3 fgmres fp32", lambda: synth.pressure(16, seed=1), dict()),
+    ("pressure 16^3 bicgstab fp64", lambda: synth.pressure(16, seed=1),
+     dict(solver=bcs.BCS_BICGSTAB, precision=bcs.BCS_PREC_FP64)),
+    ("density 12^3 smoothed P", lambda: synth.density(12, seed=3), dict(pmode=bcs.BCS_P_SMOOTHED)),
+    ("random n=3", lambda: synth.random_graph(500, 1500, 3, seed=2), dict(coarse_size=16)),
+]
+
+
+@pytest.mark.parametrize("name,gen,cfg", SOLVES, ids=[c[0] for c in SOLVES])
+def test_solve_reaches_tolerance(name, gen, cfg):
+    system = gen()
+    ref = oracle.ldu_to_bsr(system)
+    x, st, res = gpu_solve(system, **cfg)
+    assert st == bcs.BCS_OK, res
+    rel = true_rel(ref, system["b"], x)
+    assert rel <= 1e-8, rel
+    assert rel == pytest.approx(res["rel_res_final"], rel=1e-5, abs=1e-14)
+    ocfg = oracle.config(**{k: v for k, v in cfg.items() if k != "precision"})
+    xo, ores, _ = oracle.solve(ref, system["b"], cfg=ocfg)
+    assert ores["status"] == 0 and true_rel(ref, system["b"], xo) <= 1e-8
+    if cfg.get("precision") == bcs.BCS_PREC_FP64:
+        # FP64 everywhere: the same iteration count as the reference (+-1)
+        assert abs(res["iters"] - ores["iters"]) <= 1, (res["iters"], ores["iters"])
+    dx = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    print(f"{name}: iters gpu={res['iters']} ref={ores['iters']} rel={rel:.2e} |dx|/|x|={dx:.2e}")
+
+
+def test_host_memory_path_matches_device():
+    system = synth.density(12, seed=1)
+    xd, st1, r1 = gpu_solve(system, device=True)
+    xh, st2, r2 = gpu_solve(system, device=False)
+    assert st1 == st2 == bcs.BCS_OK
+    assert np.array_equal(xd, xh) and r1["iters"] == r2["iters"]
+
+
+def test_warm_start_and_zero_rhs():
+    system = synth.density(10, seed=2)
+    ref = oracle.ldu_to_bsr(system)
+    x, st, res = gpu_solve(system)
+    x2, st2, res2 = gpu_solve(system, x0=x)
+    assert st2 == bcs.BCS_OK and res2["iters"] <= 1
+    z = dict(system)
+    z["b"] = np.zeros_like(system["b"])
+    x3, st3, res3 = gpu_solve(z, x0=np.ones_like(system["b"]))
+    assert st3 == bcs.BCS_OK and np.all(x3 == 0)
+
+
+def test_maxiter_and_preconditioner_variants():
+    system = synth.density(8, seed=4)
+    ref = oracle.ldu_to_bsr(system)
+    x, st, res = gpu_solve(system, maxiter=1, precond=bcs.BCS_PC_NONE)
+    assert st == bcs.BCS_NOT_CONVERGED and res["iters"] == 1
+    for pc in (bcs.BCS_PC_NONE, bcs.BCS_PC_JACOBI):
+        for solver in (bcs.BCS_FGMRES, bcs.BCS_BICGSTAB):
+            x, st, res = gpu_solve(system, precond=pc, solver=solver)
+            assert st == bcs.BCS_OK and true_rel(ref, system["b"], x) <= 1e-8
+
+
+def test_exact_preconditioner_one_iteration():
+    system = synth.density(3, seed=4)
+    for solver in (bcs.BCS_FGMRES, bcs.BCS_BICGSTAB):
+        x, st, res = gpu_solve(system, solver=solver, coarse_size=10 ** 6, precision=bcs.BCS_PREC_FP64)
+        assert st == bcs.BCS_OK and res["iters"] == 1
+
+
+def test_state_errors():
+    with bcs.Solver(5) as s:
+        with pytest.raises(bcs.BcsError) as e:
+            s.solve(np.ones((4, 5)))
+        assert e.value.status == bcs.BCS_ESTATE
+        with pytest.raises(bcs.BcsError) as e:
+            s.set_values(np.ones((4, 5, 5)), np.ones((3, 5, 5)), np.ones((3, 5, 5)))
+        assert e.value.status == bcs.BCS_ESTATE
+
+
+def test_values_only_resetup_sequence():
+    """Alg. 1: first iteration full setup, later iterations replace values on
+    the fixed sparsity. Ten 2% perturbations, each solved to 1e-8."""
+    system = synth.density(16, seed=3)
+    rng = np.random.default_rng(31)
+    with bcs.Solver(5) as s:
+        s.load(system, device=DEV)
+        agg0 = s.level(0)["agg"].copy()
+        b = torch.from_numpy(system["b"]).to(DEV)
+        for it in range(10):
+            system = synth.perturb(system, rng, 0.02)
+            s.set_values(*(torch.from_numpy(system[k]).to(DEV) for k in ("diag", "upper", "lower")))
+            assert np.array_equal(s.level(0)["agg"], agg0)
+            x, st, res = s.solve(b)
+            assert st == bcs.BCS_OK
+            assert true_rel(oracle.ldu_to_bsr(system), system["b"], x.cpu().numpy()) <= 1e-8
+
+
+def test_full_size_128cube_mixed_solve():
+    """The benchmark workload: 128^3 density-based 5x5 system, FGMRES(30)
+    with FP32 AMG to 1e-8; true residual recomputed on the CPU."""
+    system = synth.density(128, seed=2)
+    ref = oracle.ldu_to_bsr(system)
+    x, st, res = gpu_solve(system)
+    assert st == bcs.BCS_OK, res
+    assert true_rel(ref, system["b"], x) <= 1e-8
