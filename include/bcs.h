@@ -198,6 +198,27 @@ BCS_API bcs_status bcs_reset_stats(bcs_solver* s);
 /* Name of kernel kind k (0 <= k < BCS_NUM_KERNEL_KINDS), "" if unused. */
 BCS_API const char* bcs_kernel_kind_name(int k);
 
+/* Allocation-free block-CSR structure build (the paper has no counterpart).
+ * For callers that cannot let a library allocate device memory: programs that
+ * reserve the GPU's memory up front under a hard budget, and programs that
+ * forbid cudaMalloc / cudaFree after start-up because those calls synchronise
+ * the device and stall their other streams. Builds exactly what
+ * bcs_set_structure builds (row_ptr[C+1], col[C+2F], pos_diag[C], pos_up[F],
+ * pos_lo[F], all int32 DEVICE arrays owned by the caller) from DEVICE arrays
+ * owner[F], neighbour[F], launching on `stream` (a cudaStream_t, NULL = legacy
+ * default stream) and synchronising it before returning. It allocates
+ * nothing: its scratch lives in a fixed ~4 MB device array inside the library
+ * that every GPU loading the library keeps until the process exits. Limit:
+ * n_cells <= 1048576; larger sizes return BCS_EINVAL with a message. The
+ * first call on each device looks up that array's device address (do it
+ * before any stream capture). All calls share the scratch, so calls that
+ * overlap on the GPU race; serialise them. Errors as bcs_set_structure; when
+ * err is not NULL, a message of at most errlen bytes is written there. */
+BCS_API bcs_status bcs_ldu_structure_noalloc(int32_t n_cells, int32_t n_faces, const int32_t* owner,
+                                             const int32_t* neighbour, int32_t* row_ptr, int32_t* col,
+                                             int32_t* pos_diag, int32_t* pos_up, int32_t* pos_lo,
+                                             void* stream, char* err, size_t errlen);
+
 /* Message for the last failed call on s (never NULL). */
 BCS_API const char* bcs_last_error(const bcs_solver* s);
 

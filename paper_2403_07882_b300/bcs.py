@@ -92,6 +92,7 @@ def lib():
             "bcs_kernel_kind_name": (ct.c_char_p, [ct.c_int]),
             "bcs_last_error": (ct.c_char_p, [_vp]),
             "bcs_device_bytes": (ct.c_size_t, [_vp]),
+            "bcs_ldu_structure_noalloc": (ct.c_int, [ct.c_int32, ct.c_int32] + [_vp] * 8 + [ct.c_char_p, ct.c_size_t]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -106,7 +107,7 @@ def exported_names():
             "bcs_set_values", "bcs_invalidate_hierarchy", "bcs_solve", "bcs_spmv", "bcs_precond_apply",
             "bcs_get_bsr", "bcs_num_levels", "bcs_get_level_info", "bcs_get_level", "bcs_get_prolongation",
             "bcs_get_coarse_inverse", "bcs_get_stats", "bcs_reset_stats", "bcs_kernel_kind_name",
-            "bcs_last_error", "bcs_device_bytes"]
+            "bcs_last_error", "bcs_device_bytes", "bcs_ldu_structure_noalloc"]
 
 
 # ------------------------------------------------------------ marshalling
@@ -287,6 +288,20 @@ def bcs_last_error(h):
 
 def bcs_device_bytes(h):
     return lib().bcs_device_bytes(h)
+
+
+def bcs_ldu_structure_noalloc(n_cells, owner, neighbour, row_ptr, col, pos_diag, pos_up, pos_lo, stream=None):
+    """Allocation-free structure build into caller-provided CUDA tensors.
+
+    Returns (status, message); the library allocates no device memory here.
+    """
+    (po, pn, prp, pc, pd, pu, pl), mem = _ptr_mem(owner, neighbour, row_ptr, col, pos_diag, pos_up, pos_lo)
+    if mem != BCS_MEM_DEVICE:
+        raise ValueError("bcs_ldu_structure_noalloc takes device arrays only")
+    buf = ct.create_string_buffer(256)
+    st = lib().bcs_ldu_structure_noalloc(n_cells, len(owner), po, pn, prp, pc, pd, pu, pl,
+                                         stream if stream is not None else _current_stream(), buf, 256)
+    return st, buf.value.decode()
 
 
 class Solver:
