@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--side", type=int, default=SIDE)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison run")
     return p.parse_args()
 
 
@@ -227,8 +228,10 @@ def run_native(args):
             resetup_ms = e0.elapsed_time(e1)
     clocks = clk.summary()
     # all-FP64 comparison (same step, FP64 AMG)
-    with bcs.Solver(n, precision=bcs.BCS_PREC_FP64) as s64:
-        ms_fp64, res_fp64, _ = timed(s64, d, x, max(1, min(args.steps, 3)), 1)
+    ms_fp64, res_fp64 = None, None
+    if not args.no_fp64:
+        with bcs.Solver(n, precision=bcs.BCS_PREC_FP64) as s64:
+            ms_fp64, res_fp64, _ = timed(s64, d, x, max(1, min(args.steps, 3)), 1)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -274,8 +277,8 @@ def run_native(args):
                    "step": "set_structure + set_values (full AMG setup) + solve, device-resident inputs"},
         "iters": res_mixed[-1]["iters"], "rel_res_final": res_mixed[-1]["rel_res_final"],
         "levels": res_mixed[-1]["levels"],
-        "fp64": {"value": ms_fp64, "unit": "ms", "iters": res_fp64[-1]["iters"],
-                 "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed},
+        "fp64": None if ms_fp64 is None else {"value": ms_fp64, "unit": "ms", "iters": res_fp64[-1]["iters"],
+                                              "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed},
         "resetup_ms": resetup_ms,
         "roofline": roofline,
         "kernel_breakdown": breakdown,

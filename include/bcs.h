@@ -79,7 +79,7 @@ typedef struct bcs_config {
   int agg_passes;          /* matching passes per level (2: aggregates of ~4) */
   double jacobi_omega;     /* damped block-Jacobi weight (0.8) */
   int nu1, nu2;            /* pre / post smoothing sweeps (2, 2) */
-  int coarse_size;         /* stop coarsening at <= this many block rows (128) */
+  int coarse_size;         /* stop coarsening at <= this many block rows (32) */
   int max_levels;          /* hierarchy depth cap (20) */
   double max_coarsen_ratio;/* stop when C_{l+1} > ratio * C_l (0.8) */
   double p_omega;          /* smoothed P: omega_P = p_omega / rho_hat (4/3) */

@@ -59,7 +59,7 @@ void or_config_default(or_config* c) {
   c->jacobi_omega = 0.8;
   c->nu1 = 2;
   c->nu2 = 2;
-  c->coarse_size = 128;
+  c->coarse_size = 32;
   c->max_levels = 20;
   c->max_coarsen_ratio = 0.8;
   c->p_omega = 4.0 / 3.0;
@@ -153,9 +153,10 @@ void or_bsr_spmv(int rows, int n, const int32_t* rp, const int32_t* ci, const do
 
 // Gauss-Jordan on [A | I] with implicit partial pivoting and deferred
 // normalisation. Step k picks, among rows not yet used as pivots, the largest
-// |M[i][k]| (first such row on ties), then for every other row i computes
-// l = M[i][k] / pivot and M[i][j] = fma(-l, M[p][j], M[i][j]) for j >= k.
-// Finally inv[k][:] = M[p_k][N:] / M[p_k][k].
+// |M[i][k]| (first such row on ties), takes its reciprocal r = 1 / pivot, then
+// for every other row i computes l = M[i][k] * r and
+// M[i][j] = fma(-l, M[p][j], M[i][j]) for j >= k. Finally
+// inv[k][:] = M[p_k][N:] * (1 / M[p_k][k]).
 int or_dense_inverse(int N, const double* A, double* inv) {
   const size_t W = 2 * (size_t)N;
   std::vector<double> M((size_t)N * W, 0.0);
@@ -177,16 +178,17 @@ int or_dense_inverse(int N, const double* A, double* inv) {
     if (piv == 0.0) return 1;
     used[p] = 1;
     prow[k] = p;
+    const double rpiv = 1.0 / piv;
     for (int i = 0; i < N; ++i) {
       if (i == p) continue;
-      double l = M[i * W + k] / piv;
+      double l = M[i * W + k] * rpiv;
       for (size_t j = k; j < W; ++j) M[i * W + j] = std::fma(-l, M[p * W + j], M[i * W + j]);
     }
   }
   for (int k = 0; k < N; ++k) {
     int p = prow[k];
-    double d = M[p * W + k];
-    for (int j = 0; j < N; ++j) inv[(size_t)k * N + j] = M[p * W + N + j] / d;
+    const double rd = 1.0 / M[p * W + k];
+    for (int j = 0; j < N; ++j) inv[(size_t)k * N + j] = M[p * W + N + j] * rd;
   }
   return 0;
 }

@@ -142,7 +142,7 @@ bcs_status bcs_config_default(bcs_config* c) {
   c->jacobi_omega = 0.8;
   c->nu1 = 2;
   c->nu2 = 2;
-  c->coarse_size = 128;
+  c->coarse_size = 32;
   c->max_levels = 20;
   c->max_coarsen_ratio = 0.8;
   c->p_omega = 4.0 / 3.0;

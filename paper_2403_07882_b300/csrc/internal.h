@@ -103,6 +103,7 @@ struct Level {
   DBuf<int32_t> mptr, mem;   // aggregate member lists (members ascending)
   Bsr P, R, AP;              // smoothed mode only (FP64)
   DBuf<int32_t> Prow, Rrow, AProw, Crow;  // row of every nonzero of P, R, AP, A_{l+1}
+  DBuf<int32_t> Gptr, Glist;              // tentative Galerkin gather lists (per coarse block)
   DBuf<float> P32, R32;
   DBuf<bf16> P16, R16;
   double omega_p = 0.0;
@@ -136,7 +137,7 @@ struct Solver {
   // Krylov work space
   DBuf<double> kv;               // FGMRES V (m+1 vectors) / BiCGStab vectors
   DBuf<char> kz;                 // FGMRES Z (m vectors, cycle precision)
-  DBuf<double> kw, kr, kx, kb;
+  DBuf<double> kw, kr, kx, kb, kt;  // kt: FP64 copy of an FP32 preconditioned vector
   DBuf<double> red;              // reduction partials
   DBuf<double> scal;             // device scalars
   double* hscal = nullptr;       // pinned host mirror of scal

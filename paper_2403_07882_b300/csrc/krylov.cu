@@ -43,6 +43,19 @@ bcs_status apply_M(Solver* s, const double* v, void* z, size_t N) {
   }
 }
 
+// y = A z for a preconditioned vector z in the cycle precision. An FP32 z is
+// widened once into s->kt first: converting inside the SpMV would cost one
+// F32->F64 conversion per matrix entry on the FP64 pipe, as many as the FMAs.
+bcs_status apply_A(Solver* s, const void* z, double* y, size_t N) {
+  const void* x = z;
+  if (cycle_is_float(s)) {
+    BCS_ALLOC(s, s->kt, N);
+    BCS_OKR(cast_vec<float, double>(s, (const float*)z, s->kt.p, N));
+    x = s->kt.p;
+  }
+  return spmv64(s, s->lv[0].A, x, false, y, nullptr, K_SPMV64);
+}
+
 bcs_status norm(Solver* s, const double* x, size_t N, double* out) {
   BCS_OKR(dot(s, x, x, N, SLOT_N));
   BCS_OKR(fetch_scalars(s, SLOT_N + 1));
@@ -94,7 +107,7 @@ bcs_status fgmres(Solver* s, const double* b, double* x, bcs_result* res) {
       double* w = V + (size_t)(j + 1) * N;
       void* zj = Z + (size_t)j * N * zbytes(s);
       BCS_OKR(apply_M(s, V + (size_t)j * N, zj, N));
-      BCS_OKR(spmv64(s, s->lv[0].A, zj, zf, w, nullptr, K_SPMV64));
+      BCS_OKR(apply_A(s, zj, w, N));
       // pass 1 also yields ||w||^2 (w is vector j+1 of V)
       BCS_OKR(multidot(s, V, N, j + 2, w, N, SLOT_A));
       BCS_OKR(gs_update(s, V, N, j + 1, s->scal.p + SLOT_A, w, N));
@@ -228,7 +241,7 @@ bcs_status bicgstab(Solver* s, const double* b, double* x, bcs_result* res) {
     }
     first = false;
     BCS_OKR(apply_M(s, p, ph, N));
-    BCS_OKR(spmv64(s, s->lv[0].A, ph, zf, v, nullptr, K_SPMV64));
+    BCS_OKR(apply_A(s, ph, v, N));
     BCS_OKR(dot(s, rhat, v, N, SLOT_A));
     BCS_OKR(fetch_scalars(s, 1));
     const double den = s->hscal[0];
@@ -258,7 +271,7 @@ bcs_status bicgstab(Solver* s, const double* b, double* x, bcs_result* res) {
       continue;
     }
     BCS_OKR(apply_M(s, sv, sh, N));
-    BCS_OKR(spmv64(s, s->lv[0].A, sh, zf, t, nullptr, K_SPMV64));
+    BCS_OKR(apply_A(s, sh, t, N));
     BCS_OKR(multidot(s, sv, N, 2, t, N, SLOT_A));  // (s, t), (t, t)
     BCS_OKR(fetch_scalars(s, 2));
     const double ts = s->hscal[0], tt = s->hscal[1];

@@ -22,6 +22,7 @@
 #include <cooperative_groups.h>
 
 #include <climits>
+#include <utility>
 
 #include "internal.h"
 
@@ -52,57 +53,98 @@ __global__ void k_diag_pos(int rows, const int32_t* __restrict__ rp, const int32
 }
 
 // Gauss-Jordan inverse of one N x N block per thread: implicit partial
-// pivoting (largest |M[r][k]| among unused rows, first on ties), deferred
-// normalisation, updates M[r][j] = fma(-l, M[p][j], M[r][j]) for j >= k.
+// pivoting (largest |M[r][k]| among unused rows, first on ties), one
+// reciprocal per pivot, l = M[r][k] * (1 / pivot), updates
+// M[r][j] = fma(-l, M[p][j], M[r][j]) for j >= k, deferred normalisation
+// inv[k][:] = M[p_k][N:] * (1 / M[p_k][k]). Steps are unrolled at compile
+// time and the pivot row is picked with bit masks, so M stays in registers.
+__device__ __forceinline__ double pick(double v, bool on) {
+  return __longlong_as_double(__double_as_longlong(v) & (0ll - (long long)on));
+}
+
 template <int N>
-__global__ void k_block_inverse(int rows, const int32_t* __restrict__ dpos, const double* __restrict__ val,
-                                double* __restrict__ dinv, int32_t* __restrict__ err) {
+struct BlockGJ {
+  double M[N][2 * N];
+  unsigned used = 0;
+  int prow[N];
+  bool bad = false;
+
+  template <int K>
+  __device__ __forceinline__ void step() {
+    int p = 0;
+    double best = -1.0;
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      const double v = fabs(M[r][K]);
+      const bool take = !(used & (1u << r)) && v > best;
+      best = take ? v : best;
+      p = take ? r : p;
+    }
+    double pr[2 * N];
+#pragma unroll
+    for (int j = K; j < 2 * N; ++j) {
+      long long t = 0;
+#pragma unroll
+      for (int r = 0; r < N; ++r) t |= __double_as_longlong(pick(M[r][j], p == r));
+      pr[j] = __longlong_as_double(t);
+    }
+    bad |= pr[K] == 0.0;
+    used |= 1u << p;
+    prow[K] = p;
+    const double rpiv = 1.0 / pr[K];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      const double l = M[r][K] * rpiv;
+#pragma unroll
+      for (int j = K; j < 2 * N; ++j) {
+        const double nv = fma(-l, pr[j], M[r][j]);
+        M[r][j] = __longlong_as_double(__double_as_longlong(pick(M[r][j], r == p)) |
+                                       __double_as_longlong(pick(nv, r != p)));
+      }
+    }
+  }
+  template <int... K>
+  __device__ __forceinline__ void run(std::integer_sequence<int, K...>) {
+    (step<K>(), ...);
+  }
+};
+
+template <int N>
+__global__ void __launch_bounds__(64) k_block_inverse(int rows, const int32_t* __restrict__ dpos,
+                                                      const double* __restrict__ val, double* __restrict__ dinv,
+                                                      int32_t* __restrict__ err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const int dp = dpos[i];
   if (dp < 0) return;
-  double M[N][2 * N];
+  BlockGJ<N> g;
   const double* a = val + (size_t)dp * N * N;
 #pragma unroll
   for (int r = 0; r < N; ++r)
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-      M[r][c] = a[r * N + c];
-      M[r][N + c] = r == c ? 1.0 : 0.0;
+      g.M[r][c] = a[r * N + c];
+      g.M[r][N + c] = r == c ? 1.0 : 0.0;
     }
-  bool used[N];
-  int prow[N];
-#pragma unroll
-  for (int r = 0; r < N; ++r) used[r] = false;
-  for (int k = 0; k < N; ++k) {
-    int p = 0;
-    double best = -1.0;
-    for (int r = 0; r < N; ++r) {
-      if (used[r]) continue;
-      const double v = fabs(M[r][k]);
-      if (v > best) {
-        best = v;
-        p = r;
-      }
-    }
-    const double piv = M[p][k];
-    if (piv == 0.0) {
-      atomicOr(err, 8);
-      return;
-    }
-    used[p] = true;
-    prow[k] = p;
-    for (int r = 0; r < N; ++r) {
-      if (r == p) continue;
-      const double l = M[r][k] / piv;
-      for (int j = k; j < 2 * N; ++j) M[r][j] = fma(-l, M[p][j], M[r][j]);
-    }
+  g.run(std::make_integer_sequence<int, N>{});
+  if (g.bad) {
+    atomicOr(err, 8);
+    return;
   }
   double* o = dinv + (size_t)i * N * N;
+#pragma unroll
   for (int k = 0; k < N; ++k) {
-    const int p = prow[k];
-    const double d = M[p][k];
-    for (int j = 0; j < N; ++j) o[k * N + j] = M[p][N + j] / d;
+    double pr[2 * N];
+#pragma unroll
+    for (int j = 0; j < 2 * N; ++j) {
+      long long t = 0;
+#pragma unroll
+      for (int r = 0; r < N; ++r) t |= __double_as_longlong(pick(g.M[r][j], g.prow[k] == r));
+      pr[j] = __longlong_as_double(t);
+    }
+    const double rd = 1.0 / pr[k];
+#pragma unroll
+    for (int j = 0; j < N; ++j) o[k * N + j] = pr[N + j] * rd;
   }
 }
 
@@ -265,40 +307,86 @@ __global__ void k_cand_fill_tent(int nagg, const int32_t* __restrict__ mptr, con
   }
 }
 
-// R A P with tentative P: block (I, J) = sum over members i of I
+// Tentative Galerkin gather lists. Fine block (i, j) lands in coarse block
+// (agg(i), agg(j)). k_tent_count counts the contributions of each coarse
+// block; k_tent_fill then walks every coarse row's members in ascending order
+// (one thread per coarse row, which alone owns that row's blocks) and appends
+// each fine block position to its coarse block's list, so every list is in
+// ascending fine position without sorting. The first entry a member row
+// contributes to a list is stored as -1 - k to mark the member boundary.
+__global__ void k_tent_count(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const int32_t* __restrict__ agg, const int32_t* __restrict__ crp,
+                             const int32_t* __restrict__ cci, int32_t* __restrict__ gcnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const int I = agg[i], cb = crp[I], ce = crp[I + 1];
+  for (int k = rp[i]; k < rp[i + 1]; ++k) atomicAdd(&gcnt[find_col(cci, cb, ce, agg[ci[k]])], 1);
+}
+
+__global__ void k_tent_fill(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
+                            const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const int32_t* __restrict__ agg, const int32_t* __restrict__ crp,
+                            const int32_t* __restrict__ cci, const int32_t* __restrict__ gptr,
+                            int32_t* __restrict__ cursor, int32_t* __restrict__ lastmem,
+                            int32_t* __restrict__ glist) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nagg) return;
+  const int cb = crp[I], ce = crp[I + 1];
+  for (int q = cb; q < ce; ++q) {
+    cursor[q] = 0;
+    lastmem[q] = -1;
+  }
+  for (int m = mptr[I]; m < mptr[I + 1]; ++m) {
+    const int i = mem[m];
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const int q = find_col(cci, cb, ce, agg[ci[k]]);
+      const bool first = lastmem[q] != i;
+      lastmem[q] = i;
+      glist[gptr[q] + cursor[q]++] = first ? -1 - k : k;
+    }
+  }
+}
+
+// R A P with tentative P: coarse block (I, J) = sum over members i of I
 // (ascending) of [sum over row i's blocks k (ascending) with agg(col k) = J
 // of A_k], each sum a plain left-to-right FP64 add from +0. (This is the
 // general product with identity blocks: fma(a, 1, acc) = acc + a and
-// fma(a, 0, acc) = acc.)
+// fma(a, 0, acc) = acc.) One thread per coarse element: the n*n threads of a
+// block read each contributing fine block as one coalesced span; list
+// entries are prefetched four at a time.
 template <int NN>
-__global__ void k_gal_tent_values(int cnnz, const int32_t* __restrict__ crow, const int32_t* __restrict__ cci,
-                                  const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
-                                  const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                  const double* __restrict__ val, const int32_t* __restrict__ agg,
-                                  double* __restrict__ out) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= cnnz) return;
-  const int I = crow[q], J = cci[q];
-  double acc[NN];
+__global__ void k_gal_gather(int cnnz, const int32_t* __restrict__ gptr, const int32_t* __restrict__ glist,
+                             const double* __restrict__ val, double* __restrict__ out) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)cnnz * NN) return;
+  const size_t q = t / NN;
+  const int e = (int)(t - q * NN);
+  double acc = 0.0, part = 0.0;
+  bool started = false;
+  const int pb = __ldg(gptr + q), pe = __ldg(gptr + q + 1);
+  for (int p = pb; p < pe; p += 4) {
+    int kk[4];
+    double v[4];
 #pragma unroll
-  for (int e = 0; e < NN; ++e) acc[e] = 0.0;
-  for (int m = mptr[I]; m < mptr[I + 1]; ++m) {
-    const int i = mem[m];
-    double t[NN];
+    for (int u = 0; u < 4; ++u) kk[u] = p + u < pe ? __ldg(glist + p + u) : 0;
 #pragma unroll
-    for (int e = 0; e < NN; ++e) t[e] = 0.0;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {
-      if (agg[ci[k]] != J) continue;
-      const double* a = val + (size_t)k * NN;
-#pragma unroll
-      for (int e = 0; e < NN; ++e) t[e] = t[e] + a[e];
+    for (int u = 0; u < 4; ++u) {
+      const int k = kk[u] < 0 ? -1 - kk[u] : kk[u];
+      v[u] = p + u < pe ? __ldg(val + (size_t)k * NN + e) : 0.0;
     }
 #pragma unroll
-    for (int e = 0; e < NN; ++e) acc[e] = acc[e] + t[e];
+    for (int u = 0; u < 4; ++u) {
+      if (p + u >= pe) break;
+      if (kk[u] < 0) {
+        if (started) acc = acc + part;
+        part = 0.0;
+      }
+      part = part + v[u];
+      started = true;
+    }
   }
-  double* o = out + (size_t)q * NN;
-#pragma unroll
-  for (int e = 0; e < NN; ++e) o[e] = acc[e];
+  if (started) acc = acc + part;
+  out[t] = acc;
 }
 
 // ----------------------------------------------------- smoothed prolongation
@@ -524,6 +612,7 @@ __global__ void k_gauss_jordan(int N, double* __restrict__ M, double* __restrict
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 16);
       return;  // every block sees the same pivot and leaves before the next barrier
     }
+    const double rpiv = 1.0 / piv;
     double* nxt = colbuf + (size_t)((k + 1) & 1) * N;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
       if (i == p) {
@@ -531,7 +620,7 @@ __global__ void k_gauss_jordan(int N, double* __restrict__ M, double* __restrict
         continue;
       }
       double* row = M + (size_t)i * W;
-      if (threadIdx.x == 0) s_l = row[k] / piv;
+      if (threadIdx.x == 0) s_l = row[k] * rpiv;
       __syncthreads();
       const double l = s_l;
       for (size_t j = k + threadIdx.x; j < W; j += blockDim.x) row[j] = fma(-l, prow[j], row[j]);
@@ -549,7 +638,7 @@ __global__ void k_gj_finish(int N, const double* __restrict__ M, const int32_t* 
        t += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(t / N), j = (int)(t % N);
     const int p = prow[k];
-    inv[t] = M[(size_t)p * W + N + j] / M[(size_t)p * W + k];
+    inv[t] = M[(size_t)p * W + N + j] * (1.0 / M[(size_t)p * W + k]);
   }
 }
 
@@ -665,8 +754,14 @@ bcs_status members(Solver* s, int rows, int nagg, const int32_t* agg, DBuf<int32
   return segmented_sort_unique(s, mptr.p, mem.p, cnt.p, nagg, mx);
 }
 
+// Gather lists of the tentative Galerkin product: per coarse block, its
+// contributing fine blocks in ascending position.
+struct TentGather {
+  DBuf<int32_t> gptr, glist;
+};
+
 bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, const int32_t* mptr,
-                        const int32_t* mem, Bsr& Ac, DBuf<int32_t>& crow) {
+                        const int32_t* mem, Bsr& Ac, DBuf<int32_t>& crow, TentGather& g) {
   DBuf<int32_t> cnt;
   BCS_ALLOC(s, cnt, nagg);
   BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p,
@@ -678,18 +773,29 @@ bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, c
   };
   BCS_OKR(pattern_from_candidates(s, nagg, cnt, fill, Ac, crow));
   Ac.cols = nagg;
+  DBuf<int32_t> gcnt, cursor, lastmem;
+  BCS_ALLOC(s, gcnt, Ac.nnz);
+  BCS_ALLOC(s, cursor, Ac.nnz);
+  BCS_ALLOC(s, lastmem, Ac.nnz);
+  BCS_ALLOC(s, g.gptr, Ac.nnz + 1);
+  BCS_ALLOC(s, g.glist, A.nnz);
+  BCS_CU(s, cudaMemsetAsync(gcnt.p, 0, Ac.nnz * sizeof(int32_t), s->stream));
+  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_tent_count, grid_for(A.rows, 256), 256, 0, A.rows, A.rp.p, A.ci.p, agg,
+             Ac.rp.p, Ac.ci.p, gcnt.p);
+  BCS_OKR(exclusive_scan(s, gcnt.p, g.gptr.p, Ac.nnz));
+  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_tent_fill, grid_for(nagg, 128), 128, 0, nagg, mptr, mem, A.rp.p, A.ci.p, agg,
+             Ac.rp.p, Ac.ci.p, g.gptr.p, cursor.p, lastmem.p, g.glist.p);
   return BCS_OK;
 }
 
-bcs_status tent_values(Solver* s, const Bsr& A, const int32_t* agg, const int32_t* mptr, const int32_t* mem,
-                       Bsr& Ac, const int32_t* crow) {
+bcs_status tent_values(Solver* s, const Bsr& A, const TentGather& g, Bsr& Ac) {
   const int n = s->n;
   BCS_ALLOC(s, Ac.v, (size_t)Ac.nnz * n * n);
   return with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + Ac.nnz) * N * N, 1.0 * A.nnz * N * N, k_gal_tent_values<N * N>,
-               grid_for(Ac.nnz, 128), 128, 0, Ac.nnz, crow, Ac.ci.p, mptr, mem, A.rp.p, A.ci.p, A.v.p, agg,
-               Ac.v.p);
+    const size_t work = (size_t)Ac.nnz * N * N;
+    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + Ac.nnz) * N * N + 8.0 * A.nnz + 4.0 * Ac.nnz, 1.0 * A.nnz * N * N,
+               k_gal_gather<N * N>, grid_for(work, 256), 256, 0, Ac.nnz, g.gptr.p, g.glist.p, A.v.p, Ac.v.p);
     return BCS_OK;
   });
 }
@@ -708,8 +814,9 @@ bcs_status aggregate_level(Solver* s, Level& L) {
     DBuf<int32_t> mptr, mem, crow;
     BCS_OKR(members(s, cur->rows, nagg, cur_agg.p, mptr, mem));
     Bsr Abar;
-    BCS_OKR(tent_pattern(s, *cur, nagg, cur_agg.p, mptr.p, mem.p, Abar, crow));
-    BCS_OKR(tent_values(s, *cur, cur_agg.p, mptr.p, mem.p, Abar, crow.p));
+    TentGather g;
+    BCS_OKR(tent_pattern(s, *cur, nagg, cur_agg.p, mptr.p, mem.p, Abar, crow, g));
+    BCS_OKR(tent_values(s, *cur, g, Abar));
     DBuf<int32_t> a2;
     int n2 = 0;
     BCS_OKR(match_pass(s, Abar, a2, &n2));
@@ -893,8 +1000,21 @@ bcs_status build_transfer(Solver* s, int l, bool full) {
   Level& Lc = s->lv[l + 1];
   if (full) BCS_OKR(members(s, L.A.rows, L.nagg, L.agg.p, L.mptr, L.mem));
   if (s->setup_cfg.pmode == BCS_P_TENTATIVE) {
-    if (full) BCS_OKR(tent_pattern(s, L.A, L.nagg, L.agg.p, L.mptr.p, L.mem.p, Lc.A, L.Crow));
-    BCS_OKR(tent_values(s, L.A, L.agg.p, L.mptr.p, L.mem.p, Lc.A, L.Crow.p));
+    if (full) {
+      TentGather g;
+      BCS_OKR(tent_pattern(s, L.A, L.nagg, L.agg.p, L.mptr.p, L.mem.p, Lc.A, L.Crow, g));
+      L.Gptr = std::move(g.gptr);
+      L.Glist = std::move(g.glist);
+    }
+    {
+      TentGather g;
+      g.gptr = std::move(L.Gptr);
+      g.glist = std::move(L.Glist);
+      const bcs_status st = tent_values(s, L.A, g, Lc.A);
+      L.Gptr = std::move(g.gptr);
+      L.Glist = std::move(g.glist);
+      BCS_OKR(st);
+    }
   } else {
     BCS_OKR(smoothed_prolongation(s, L, full));
     BCS_OKR(spgemm(s, L.A, L.P, L.AP, L.AProw, full));
