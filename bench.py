@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison run")
+    p.add_argument("--staging", action="store_true", help="bulk-copy staging in the FP32 sweeps")
     return p.parse_args()
 
 
@@ -216,8 +217,9 @@ def run_native(args):
     # mixed precision (the headline) with per-kernel event timing
     x = torch.zeros_like(d["b"])
     with ClockSampler(local) as clk:
-        with bcs.Solver(n, precision=bcs.BCS_PREC_FP32, profile=1) as s:
+        with bcs.Solver(n, precision=bcs.BCS_PREC_FP32, profile=1, staging=int(args.staging)) as s:
             ms_mixed, res_mixed, stats = timed(s, d, x, args.steps, args.warmup)
+            ktimes = s.kernel_times()
             # values-only resetup (Alg. 1: replace coefficients on fixed sparsity)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -282,6 +284,8 @@ def run_native(args):
         "resetup_ms": resetup_ms,
         "roofline": roofline,
         "kernel_breakdown": breakdown,
+        "kernels": {k: {"ms_per_step": round(v["ms"] / args.steps, 4), "launches_per_step": v["launches"] / args.steps}
+                    for k, v in sorted(ktimes.items(), key=lambda kv: -kv[1]["ms"])[:40]},
         "gpu_launches": int(stats["launches"]),
         "gpu_launches_per_step": stats["launches"] / args.steps,
         "clocks": clocks,

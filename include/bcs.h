@@ -87,6 +87,8 @@ typedef struct bcs_config {
   int coarse_sweeps;       /* else this many block-Jacobi sweeps there (8) */
   int precision;           /* AMG storage: BCS_PREC_FP64, BCS_PREC_FP32 (default), BCS_PREC_BF16 */
   int profile;             /* 1: time kernels with CUDA events (bcs_get_stats) */
+  int staging;             /* 1: FP32/BF16 sweeps and residuals stage block rows in shared
+                              memory with bulk copies (default 0: direct loads) */
 } bcs_config;
 
 typedef struct bcs_result {
@@ -195,8 +197,54 @@ BCS_API bcs_status bcs_get_coarse_inverse(bcs_solver* s, double* inv);
 /* Statistics (launch counts always; times only with cfg.profile = 1). */
 BCS_API bcs_status bcs_get_stats(bcs_solver* s, bcs_stats* st);
 BCS_API bcs_status bcs_reset_stats(bcs_solver* s);
+/* Per-kernel timing table (cfg.profile = 1): one line per kernel,
+ * "name<TAB>launches<TAB>ms<TAB>algorithmic bytes", written to buf (NUL
+ * terminated); BCS_EINVAL when it does not fit in len bytes. */
+BCS_API bcs_status bcs_get_kernel_times(bcs_solver* s, char* buf, size_t len);
 /* Name of kernel kind k (0 <= k < BCS_NUM_KERNEL_KINDS), "" if unused. */
 BCS_API const char* bcs_kernel_kind_name(int k);
+
+/* ---- Serving: continuous batching of solves from many cases ----------
+ * A server owns worker threads ("slots") on the current device. A case is a
+ * fixed LDU face addressing (Alg. 1: the structure set up on the first
+ * iteration); each request brings one later iteration's coefficients and
+ * right-hand side for a case. Requests are taken in arrival order, skipping
+ * those whose case is busy or does not fit yet; a case's requests run one at a
+ * time in submission order (values-only resetup of its resident hierarchy,
+ * then a solve), different cases run concurrently on their own streams.
+ * Cases are admitted while their device footprint fits in budget_bytes,
+ * evicting least-recently-used idle cases; a case larger than the budget is
+ * answered with BCS_REJECTED. Results are deterministic per case, the same
+ * alone or in any mix. */
+typedef struct bcs_server bcs_server;
+
+typedef struct bcs_server_stats {
+  long long submitted, completed, rejected, evictions, admissions, queued;
+  size_t resident_bytes, budget_bytes;
+  int resident_cases;
+  double p50_ms, p99_ms, mean_ms;   /* submit -> completion latency */
+} bcs_server_stats;
+
+/* budget_bytes = 0: 80 % of the device's free memory. slots: 1..64. cfg may
+ * be NULL (defaults). */
+BCS_API bcs_status bcs_server_create(bcs_server** out, size_t budget_bytes, int slots, const bcs_config* cfg);
+/* Finishes every queued request, then frees everything. */
+BCS_API bcs_status bcs_server_destroy(bcs_server* srv);
+/* Copies the face addressing (HOST arrays) of a case with n x n blocks. */
+BCS_API bcs_status bcs_server_register_case(bcs_server* srv, int n, int32_t n_cells, int32_t n_faces,
+                                            const int32_t* owner, const int32_t* neighbour, int* case_id);
+/* Queue a solve: HOST arrays diag[C][n][n], upper / lower[F][n][n],
+ * b[C][n]; x[C][n] holds the initial guess and receives the solution. The
+ * arrays must stay valid until the request completes. */
+BCS_API bcs_status bcs_server_submit(bcs_server* srv, int case_id, const double* diag, const double* upper,
+                                    const double* lower, const double* b, double* x, int64_t* ticket);
+/* Wait for a request (timeout_ms < 0: no limit); returns the request's
+ * status (BCS_TIMEOUT when still running after timeout_ms, the ticket then
+ * stays valid). res and latency_ms (submit -> completion) may be NULL. */
+BCS_API bcs_status bcs_server_wait(bcs_server* srv, int64_t ticket, int timeout_ms, bcs_result* res,
+                                  double* latency_ms);
+BCS_API bcs_status bcs_server_get_stats(bcs_server* srv, bcs_server_stats* st);
+BCS_API bcs_status bcs_server_reset_stats(bcs_server* srv);
 
 /* Allocation-free block-CSR structure build (the paper has no counterpart).
  * For callers that cannot let a library allocate device memory: programs that

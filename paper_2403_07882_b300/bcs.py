@@ -33,7 +33,7 @@ class bcs_config(ct.Structure):
         ("agg_passes", ct.c_int), ("jacobi_omega", ct.c_double), ("nu1", ct.c_int), ("nu2", ct.c_int),
         ("coarse_size", ct.c_int), ("max_levels", ct.c_int), ("max_coarsen_ratio", ct.c_double),
         ("p_omega", ct.c_double), ("coarse_dense_max", ct.c_int), ("coarse_sweeps", ct.c_int),
-        ("precision", ct.c_int), ("profile", ct.c_int),
+        ("precision", ct.c_int), ("profile", ct.c_int), ("staging", ct.c_int),
     ]
 
 
@@ -50,6 +50,16 @@ class bcs_stats(ct.Structure):
     _fields_ = [("launches", ct.c_longlong), ("kind_launches", ct.c_longlong * NUM_KERNEL_KINDS),
                 ("kind_ms", ct.c_double * NUM_KERNEL_KINDS), ("kind_bytes", ct.c_double * NUM_KERNEL_KINDS),
                 ("kind_flops", ct.c_double * NUM_KERNEL_KINDS)]
+
+
+class bcs_server_stats(ct.Structure):
+    _fields_ = [("submitted", ct.c_longlong), ("completed", ct.c_longlong), ("rejected", ct.c_longlong),
+                ("evictions", ct.c_longlong), ("admissions", ct.c_longlong), ("queued", ct.c_longlong),
+                ("resident_bytes", ct.c_size_t), ("budget_bytes", ct.c_size_t), ("resident_cases", ct.c_int),
+                ("p50_ms", ct.c_double), ("p99_ms", ct.c_double), ("mean_ms", ct.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class BcsError(RuntimeError):
@@ -89,10 +99,20 @@ def lib():
             "bcs_get_coarse_inverse": (ct.c_int, [_vp, _vp]),
             "bcs_get_stats": (ct.c_int, [_vp, ct.POINTER(bcs_stats)]),
             "bcs_reset_stats": (ct.c_int, [_vp]),
+            "bcs_get_kernel_times": (ct.c_int, [_vp, ct.c_char_p, ct.c_size_t]),
             "bcs_kernel_kind_name": (ct.c_char_p, [ct.c_int]),
             "bcs_last_error": (ct.c_char_p, [_vp]),
             "bcs_device_bytes": (ct.c_size_t, [_vp]),
             "bcs_ldu_structure_noalloc": (ct.c_int, [ct.c_int32, ct.c_int32] + [_vp] * 8 + [ct.c_char_p, ct.c_size_t]),
+            "bcs_server_create": (ct.c_int, [ct.POINTER(_vp), ct.c_size_t, ct.c_int, ct.POINTER(bcs_config)]),
+            "bcs_server_destroy": (ct.c_int, [_vp]),
+            "bcs_server_register_case": (ct.c_int, [_vp, ct.c_int, ct.c_int32, ct.c_int32, _vp, _vp,
+                                                    ct.POINTER(ct.c_int)]),
+            "bcs_server_submit": (ct.c_int, [_vp, ct.c_int, _vp, _vp, _vp, _vp, _vp, ct.POINTER(ct.c_int64)]),
+            "bcs_server_wait": (ct.c_int, [_vp, ct.c_int64, ct.c_int, ct.POINTER(bcs_result),
+                                           ct.POINTER(ct.c_double)]),
+            "bcs_server_get_stats": (ct.c_int, [_vp, ct.POINTER(bcs_server_stats)]),
+            "bcs_server_reset_stats": (ct.c_int, [_vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -106,8 +126,10 @@ def exported_names():
     return ["bcs_config_default", "bcs_create", "bcs_destroy", "bcs_set_config", "bcs_set_structure",
             "bcs_set_values", "bcs_invalidate_hierarchy", "bcs_solve", "bcs_spmv", "bcs_precond_apply",
             "bcs_get_bsr", "bcs_num_levels", "bcs_get_level_info", "bcs_get_level", "bcs_get_prolongation",
-            "bcs_get_coarse_inverse", "bcs_get_stats", "bcs_reset_stats", "bcs_kernel_kind_name",
-            "bcs_last_error", "bcs_device_bytes", "bcs_ldu_structure_noalloc"]
+            "bcs_get_coarse_inverse", "bcs_get_stats", "bcs_reset_stats", "bcs_get_kernel_times", "bcs_kernel_kind_name",
+            "bcs_last_error", "bcs_device_bytes", "bcs_ldu_structure_noalloc", "bcs_server_create",
+            "bcs_server_destroy", "bcs_server_register_case", "bcs_server_submit", "bcs_server_wait",
+            "bcs_server_get_stats", "bcs_server_reset_stats"]
 
 
 # ------------------------------------------------------------ marshalling
@@ -274,6 +296,17 @@ def bcs_get_stats(h):
     return dict(launches=st.launches, kinds=kinds)
 
 
+def bcs_get_kernel_times(h):
+    """{kernel name: dict(launches, ms, bytes)} (profile = 1)."""
+    buf = ct.create_string_buffer(1 << 20)
+    _check(lib().bcs_get_kernel_times(h, buf, len(buf)), h)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, n, ms, b = line.split("\t")
+        out[name] = dict(launches=int(n), ms=float(ms), bytes=float(b))
+    return out
+
+
 def bcs_reset_stats(h):
     return _check(lib().bcs_reset_stats(h), h)
 
@@ -392,3 +425,96 @@ class Solver:
 
     def reset_stats(self):
         bcs_reset_stats(self.h)
+
+    def kernel_times(self):
+        return bcs_get_kernel_times(self.h)
+
+
+# ---------------------------------------------------------------- serving
+def bcs_server_create(budget_bytes=0, slots=4, cfg=None):
+    h = _vp()
+    _check(lib().bcs_server_create(ct.byref(h), budget_bytes, slots, ct.byref(cfg) if cfg is not None else None))
+    return h
+
+
+def bcs_server_destroy(h):
+    return lib().bcs_server_destroy(h)
+
+
+def bcs_server_register_case(h, n, n_cells, owner, neighbour):
+    owner = np.ascontiguousarray(owner, np.int32)
+    neighbour = np.ascontiguousarray(neighbour, np.int32)
+    cid = ct.c_int()
+    _check(lib().bcs_server_register_case(h, n, n_cells, owner.size, owner.ctypes.data, neighbour.ctypes.data,
+                                          ct.byref(cid)))
+    return cid.value
+
+
+def bcs_server_submit(h, case_id, diag, upper, lower, b, x):
+    """Host arrays only; they must stay alive until the request completes."""
+    t = ct.c_int64()
+    _check(lib().bcs_server_submit(h, case_id, diag.ctypes.data, upper.ctypes.data, lower.ctypes.data,
+                                   b.ctypes.data, x.ctypes.data, ct.byref(t)))
+    return t.value
+
+
+def bcs_server_wait(h, ticket, timeout_ms=-1):
+    res = bcs_result()
+    lat = ct.c_double()
+    st = lib().bcs_server_wait(h, ticket, timeout_ms, ct.byref(res), ct.byref(lat))
+    return st, res.as_dict(), lat.value
+
+
+def bcs_server_get_stats(h):
+    st = bcs_server_stats()
+    _check(lib().bcs_server_get_stats(h, ct.byref(st)))
+    return st.as_dict()
+
+
+def bcs_server_reset_stats(h):
+    return _check(lib().bcs_server_reset_stats(h))
+
+
+class Server:
+    """Owning wrapper of a serving instance; keeps submitted arrays alive."""
+
+    def __init__(self, budget_bytes=0, slots=4, **cfg):
+        self.h = bcs_server_create(budget_bytes, slots, bcs_config_default(**cfg))
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            bcs_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def register(self, system):
+        return bcs_server_register_case(self.h, system["n"], system["n_cells"], system["owner"],
+                                        system["neighbour"])
+
+    def submit(self, case_id, system, x=None):
+        arrs = [np.ascontiguousarray(system[k], np.float64) for k in ("diag", "upper", "lower", "b")]
+        if x is None:
+            x = np.zeros_like(arrs[3])
+        t = bcs_server_submit(self.h, case_id, *arrs, x)
+        self._keep[t] = (arrs, x)
+        return t
+
+    def wait(self, ticket, timeout_ms=-1):
+        st, res, lat = bcs_server_wait(self.h, ticket, timeout_ms)
+        if st == BCS_TIMEOUT:
+            return st, res, lat, None
+        arrs, x = self._keep.pop(ticket)
+        return st, res, lat, x
+
+    def stats(self):
+        return bcs_server_get_stats(self.h)

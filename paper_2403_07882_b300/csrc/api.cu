@@ -2,6 +2,7 @@
 // staging, the Alg. 1 call sequence (structure once, values every
 // iteration with full setup or values-only resetup, solve), statistics.
 #include <chrono>
+#include <cstdio>
 #include <cmath>
 #include <new>
 
@@ -16,9 +17,11 @@ const char* kind_name(int k) {
   return (k >= 0 && k < K_NKINDS) ? names[k] : "";
 }
 
+// Every buffer gets 16 bytes of tail padding so that 16-byte-aligned bulk
+// copies of any span of it stay inside the allocation.
 void* Alloc::get(size_t bytes) {
   void* p = nullptr;
-  if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+  if (cudaMallocAsync(&p, bytes + 16, stream) != cudaSuccess) {
     (void)cudaGetLastError();
     return nullptr;
   }
@@ -41,7 +44,7 @@ void Solver::pre(int kind) {
       event_pool.push_back(e);
     }
   }
-  Timer t{kind, event_pool[event_next], event_pool[event_next + 1]};
+  Timer t{kind, event_pool[event_next], event_pool[event_next + 1], nullptr, 0.0};
   event_next += 2;
   cudaEventRecord(t.a, stream);
   timers.push_back(t);
@@ -54,7 +57,11 @@ bcs_status Solver::post(int kind, const char* what, double bytes, double flops) 
   kind_launches[kind]++;
   kind_bytes[kind] += bytes;
   kind_flops[kind] += flops;
-  if (cfg.profile && !timers.empty() && timers.back().kind == kind) cudaEventRecord(timers.back().b, stream);
+  if (cfg.profile && !timers.empty() && timers.back().kind == kind && !timers.back().what) {
+    cudaEventRecord(timers.back().b, stream);
+    timers.back().what = what;
+    timers.back().bytes = bytes;
+  }
   return BCS_OK;
 }
 
@@ -63,7 +70,15 @@ void Solver::flush_timers() {
   cudaStreamSynchronize(stream);
   for (const Timer& t : timers) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) kind_ms[t.kind] += ms;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      kind_ms[t.kind] += ms;
+      if (t.what) {
+        NamedTime& nt = named[t.what];
+        nt.launches++;
+        nt.ms += ms;
+        nt.bytes += t.bytes;
+      }
+    }
   }
   timers.clear();
   event_next = 0;
@@ -86,6 +101,7 @@ bcs_status check_config(const bcs_config* c) {
   if (c->coarse_size < 1 || c->max_levels < 1 || c->coarse_sweeps < 1) return BCS_EINVAL;
   if (c->coarse_dense_max < 1 || c->coarse_dense_max > 8192) return BCS_EINVAL;
   if (c->precision < BCS_PREC_FP64 || c->precision > BCS_PREC_BF16) return BCS_EINVAL;
+  if (c->staging < 0 || c->staging > 1) return BCS_EINVAL;
   if (!(c->max_coarsen_ratio > 0.0) || !(c->p_omega > 0.0) || !(c->jacobi_omega > 0.0)) return BCS_EINVAL;
   return BCS_OK;
 }
@@ -150,6 +166,7 @@ bcs_status bcs_config_default(bcs_config* c) {
   c->coarse_sweeps = 8;
   c->precision = BCS_PREC_FP32;
   c->profile = 0;
+  c->staging = 0;
   return BCS_OK;
 }
 
@@ -434,10 +451,26 @@ bcs_status bcs_get_stats(bcs_solver* h, bcs_stats* st) {
   return BCS_OK;
 }
 
+bcs_status bcs_get_kernel_times(bcs_solver* h, char* buf, size_t len) {
+  if (!h || !buf || !len) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  s->flush_timers();
+  std::string out;
+  char line[512];
+  for (const auto& kv : s->named) {
+    std::snprintf(line, sizeof(line), "%s\t%lld\t%.6f\t%.0f\n", kv.first.c_str(), kv.second.launches, kv.second.ms,
+                  kv.second.bytes);
+    out += line;
+  }
+  std::snprintf(buf, len, "%s", out.c_str());
+  return out.size() < len ? BCS_OK : BCS_EINVAL;
+}
+
 bcs_status bcs_reset_stats(bcs_solver* h) {
   if (!h) return BCS_EINVAL;
   Solver* s = &h->impl;
   s->flush_timers();
+  s->named.clear();
   s->launches = 0;
   for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {
     s->kind_launches[k] = 0;

@@ -7,7 +7,7 @@ namespace bcs {
 
 namespace {
 
-constexpr int RED_BLOCKS = 296;  // 2 x 148 SMs; fixed for reproducibility
+constexpr int RED_BLOCKS = 1184;  // 8 x 148 SMs; fixed, so results do not depend on timing
 constexpr int RED_THREADS = 256;
 constexpr int MD_CHUNK = 8;      // vectors per multidot block row
 

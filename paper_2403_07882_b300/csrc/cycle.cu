@@ -237,6 +237,11 @@ struct Cycle {
   bcs_status sweep(const Level& L, const TC* x, const TC* b, TC* y) {
     const int rows = L.A.rows;
     const AT om = (AT)s->setup_cfg.jacobi_omega;
+    if constexpr (std::is_same<TC, float>::value) {
+      bool used = false;
+      if (s->cfg.staging) BCS_OKR(staged_sweep<N, TV>(s, const_cast<Level&>(L), mat(L), dinv(L), x, b, y, om, &used));
+      if (used) return BCS_OK;
+    }
     const double bytes = (double)L.A.nnz * (N * N * sizeof(TV) + 4) + 4.0 * (rows + 1) +
                          (double)rows * N * (N * sizeof(TD) + 3 * sizeof(TC));
     BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_jacobi<N, AT, TV, TD, TC>),
@@ -246,6 +251,11 @@ struct Cycle {
   template <int N>
   bcs_status resid(const Level& L, const TC* x, const TC* b, TC* r) {
     const int rows = L.A.rows;
+    if constexpr (std::is_same<TC, float>::value) {
+      bool used = false;
+      if (s->cfg.staging) BCS_OKR(staged_resid<N, TV>(s, const_cast<Level&>(L), mat(L), x, b, r, &used));
+      if (used) return BCS_OK;
+    }
     const double bytes = (double)L.A.nnz * (N * N * sizeof(TV) + 4) + 4.0 * (rows + 1) +
                          (double)rows * N * 3 * sizeof(TC);
     BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_rows<N, AT, TV, TC, TC, M_RESID>), rows_grid(rows, N),
@@ -369,6 +379,7 @@ bcs_status cycle_prepare(Solver* s) {
     BCS_ALLOC(s, L.vr, N * vsz);
     BCS_ALLOC(s, L.vt, N * vsz);
     if (prec == BCS_PREC_FP64 || s->setup_cfg.precond != BCS_PC_AMG) continue;
+    if (s->cfg.staging) BCS_OKR(level_tile_stats(s, L));
     BCS_ALLOC(s, L.dinv32, (size_t)L.A.rows * nn);
     BCS_OKR(cast_vec<double, float>(s, L.dinv.p, L.dinv32.p, (size_t)L.A.rows * nn));
     const size_t an = (size_t)L.A.nnz * nn;

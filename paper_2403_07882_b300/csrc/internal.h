@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <string>
 #include <type_traits>
 #include <utility>
@@ -101,19 +102,27 @@ struct Level {
   int nagg = 0;
   DBuf<int32_t> agg;         // aggregate of each row
   DBuf<int32_t> mptr, mem;   // aggregate member lists (members ascending)
-  Bsr P, R, AP;              // smoothed mode only (FP64)
+  Bsr P, R, AP;              // P, R: smoothed mode only; AP pattern kept for resetup (FP64)
   DBuf<int32_t> Prow, Rrow, AProw, Crow;  // row of every nonzero of P, R, AP, A_{l+1}
-  DBuf<int32_t> Gptr, Glist;              // tentative Galerkin gather lists (per coarse block)
+  DBuf<int32_t> apg_ptr, apg_list, cg_ptr, cg_list;  // tentative product gather lists
   DBuf<float> P32, R32;
   DBuf<bf16> P16, R16;
   double omega_p = 0.0;
   int coarse_kind = -1;      // -1 not coarsest, 0 dense inverse, 1 sweeps
+  int max_tile_blocks = -1;  // most blocks in one warp tile (floor(32/n) rows); -1 unknown
   DBuf<char> vx, vb, vr, vt; // V-cycle vectors (cycle precision)
 };
 
 struct Timer {
   int kind;
   cudaEvent_t a, b;
+  const char* what;
+  double bytes;
+};
+
+struct NamedTime {
+  long long launches = 0;
+  double ms = 0.0, bytes = 0.0;
 };
 
 struct Solver {
@@ -149,6 +158,7 @@ struct Solver {
   double kind_flops[BCS_NUM_KERNEL_KINDS] = {};
   double kind_ms[BCS_NUM_KERNEL_KINDS] = {};
   std::vector<Timer> timers;
+  std::map<std::string, NamedTime> named;  // per kernel name (profile = 1)
   std::vector<cudaEvent_t> event_pool;
   size_t event_next = 0;
   double last_setup_ms = 0.0;
@@ -248,6 +258,17 @@ bcs_status cycle_prepare(Solver* s);
 bcs_status precond_apply(Solver* s, const double* v, void* z);  // z in cycle precision
 bcs_status jacobi_apply(Solver* s, const double* v, double* z);
 bool cycle_is_float(const Solver* s);
+
+// ------------------------------------------------------------------ staged.cu
+// Block-Jacobi sweep / residual with per-warp bulk-copy staging of the
+// warp's block rows; *used is false when the level's tiles are too large for
+// the staging buffers (the caller then uses the direct kernels).
+template <int N, class TV>
+bcs_status staged_sweep(Solver* s, Level& L, const TV* val, const float* dinv, const float* x, const float* b,
+                        float* y, float omega, bool* used);
+template <int N, class TV>
+bcs_status staged_resid(Solver* s, Level& L, const TV* val, const float* x, const float* b, float* r, bool* used);
+bcs_status level_tile_stats(Solver* s, Level& L);
 template <class TI, class TO>
 bcs_status cast_vec(Solver* s, const TI* in, TO* out, size_t N);
 

@@ -323,10 +323,17 @@ bcs_status bicgstab(Solver* s, const double* b, double* x, bcs_result* res) {
 
 bcs_status solve(Solver* s, const double* b, double* x, bcs_result* res) {
   const auto t0 = std::chrono::steady_clock::now();
+  BCS_CU(s, cudaMemsetAsync(s->flag.p + 1, 0, sizeof(int32_t), s->stream));
   bcs_status st = s->cfg.solver == BCS_BICGSTAB ? bicgstab(s, b, x, res) : fgmres(s, b, x, res);
   if (st == BCS_ECUDA || st == BCS_ENOMEM || st == BCS_EINVAL) return st;
   cudaError_t e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return s->fail(BCS_ECUDA, std::string("solve: ") + cudaGetErrorString(e));
+  int32_t timeout_flag = 0;
+  BCS_CU(s, cudaMemcpy(&timeout_flag, s->flag.p + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (timeout_flag) {
+    st = BCS_TIMEOUT;
+    s->err = "a bounded device wait gave up (staged row kernel)";
+  }
   res->status = st;
   res->levels = (int)s->lv.size();
   res->setup_ms = s->last_setup_ms;

@@ -179,6 +179,33 @@ __global__ void k_seg_sort_block(const int32_t* __restrict__ seg_ptr, int32_t* _
   if (threadIdx.x == 0) count[r] = base;
 }
 
+// Segments of at most THREAD_SEG_MAX keys: one thread sorts its segment in
+// registers-backed local storage (insertion sort) and compacts duplicates.
+constexpr int THREAD_SEG_MAX = 16;
+
+__global__ void k_seg_sort_thread(const int32_t* __restrict__ seg_ptr, int32_t* __restrict__ keys,
+                                  int32_t* __restrict__ count, int rows) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const int b = seg_ptr[r], len = seg_ptr[r + 1] - b;
+  int32_t a[THREAD_SEG_MAX];
+#pragma unroll
+  for (int i = 0; i < THREAD_SEG_MAX; ++i) a[i] = i < len ? keys[b + i] : INT_MAX;
+#pragma unroll
+  for (int i = 1; i < THREAD_SEG_MAX; ++i)
+#pragma unroll
+    for (int j = i; j > 0; --j) {
+      const int32_t lo = min(a[j - 1], a[j]), hi = max(a[j - 1], a[j]);
+      a[j - 1] = lo;
+      a[j] = hi;
+    }
+  int out = 0;
+#pragma unroll
+  for (int i = 0; i < THREAD_SEG_MAX; ++i)
+    if (i < len && (i == 0 || a[i] != a[i - 1])) keys[b + out++] = a[i];
+  count[r] = out;
+}
+
 }  // namespace
 
 bcs_status segmented_sort_unique(Solver* s, const int32_t* seg_ptr, int32_t* keys, int32_t* count,
@@ -186,6 +213,10 @@ bcs_status segmented_sort_unique(Solver* s, const int32_t* seg_ptr, int32_t* key
   if (rows <= 0) return BCS_OK;
   if (max_len > BLOCK_SEG_MAX)
     return s->fail(BCS_EINVAL, "a sparsity-pattern row has more than 16384 candidate entries");
+  if (max_len <= THREAD_SEG_MAX) {
+    BCS_LAUNCH(s, K_MISC, 0, 0, k_seg_sort_thread, grid_for(rows, 128), 128, 0, seg_ptr, keys, count, rows);
+    return BCS_OK;
+  }
   DBuf<int32_t> long_rows, aux;
   BCS_ALLOC(s, long_rows, rows);
   BCS_ALLOC(s, aux, 1);

@@ -270,9 +270,21 @@ __global__ void k_place_by(int m, const int32_t* __restrict__ key, const int32_t
   if (q < m) out[ptr[key[q]] + atomicAdd(&cursor[key[q]], 1)] = val ? val[q] : q;
 }
 
+// Block-reduced maximum: one atomic per block (an atomic per element on one
+// address serialises millions of updates).
 __global__ void k_max_int(int n, const int32_t* __restrict__ a, int32_t* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) atomicMax(out, a[i]);
+  __shared__ int32_t wm[32];
+  int v = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v = max(v, a[i]);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, d));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, wm[w]);
+    atomicMax(out, m);
+  }
 }
 
 __global__ void k_compact(int rows, const int32_t* __restrict__ cptr, const int32_t* __restrict__ cand,
@@ -307,86 +319,100 @@ __global__ void k_cand_fill_tent(int nagg, const int32_t* __restrict__ mptr, con
   }
 }
 
-// Tentative Galerkin gather lists. Fine block (i, j) lands in coarse block
-// (agg(i), agg(j)). k_tent_count counts the contributions of each coarse
-// block; k_tent_fill then walks every coarse row's members in ascending order
-// (one thread per coarse row, which alone owns that row's blocks) and appends
-// each fine block position to its coarse block's list, so every list is in
-// ascending fine position without sorting. The first entry a member row
-// contributes to a list is stored as -1 - k to mark the member boundary.
-__global__ void k_tent_count(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                             const int32_t* __restrict__ agg, const int32_t* __restrict__ crp,
-                             const int32_t* __restrict__ cci, int32_t* __restrict__ gcnt) {
+// R A P with tentative P (identity blocks), as the two products of its
+// definition, which is also how the general block product orders the sums
+// (fma(a, 1, acc) = acc + a, fma(a, 0, acc) = acc):
+//   AP(i, J)   = sum over row i's blocks k (ascending) with agg(col k) = J of A_k
+//   A_c(I, J)  = sum over members i of I (ascending) with J in AP's row i of AP(i, J)
+// each a plain left-to-right FP64 sum from +0. The contributing positions of
+// every output block are listed once per structure (full setup), in
+// summation order; the value passes then gather a few blocks per output with
+// one thread per (block, element), so the n*n threads of an output read each
+// source block as one coalesced span.
+
+// Per fine row (which owns its AP entries): the AP entry of each block.
+__global__ void k_apg(int rows, int pass, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                      const int32_t* __restrict__ agg, const int32_t* __restrict__ aprp,
+                      const int32_t* __restrict__ apci, int32_t* __restrict__ cnt, const int32_t* __restrict__ gptr,
+                      int32_t* __restrict__ glist) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
-  const int I = agg[i], cb = crp[I], ce = crp[I + 1];
-  for (int k = rp[i]; k < rp[i + 1]; ++k) atomicAdd(&gcnt[find_col(cci, cb, ce, agg[ci[k]])], 1);
+  const int ab = aprp[i], ae = aprp[i + 1];
+  if (pass == 0) {
+    for (int a = ab; a < ae; ++a) cnt[a] = 0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) cnt[find_col(apci, ab, ae, agg[ci[k]])]++;
+  } else {
+    for (int a = ab; a < ae; ++a) cnt[a] = 0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const int a = find_col(apci, ab, ae, agg[ci[k]]);
+      glist[gptr[a] + cnt[a]++] = k;
+    }
+  }
 }
 
-__global__ void k_tent_fill(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
-                            const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                            const int32_t* __restrict__ agg, const int32_t* __restrict__ crp,
-                            const int32_t* __restrict__ cci, const int32_t* __restrict__ gptr,
-                            int32_t* __restrict__ cursor, int32_t* __restrict__ lastmem,
-                            int32_t* __restrict__ glist) {
+// Per coarse row (which owns its entries): the contributing AP entries of
+// each coarse block, members in ascending order.
+__global__ void k_cg(int nagg, int pass, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
+                     const int32_t* __restrict__ aprp, const int32_t* __restrict__ apci,
+                     const int32_t* __restrict__ crp, const int32_t* __restrict__ cci, int32_t* __restrict__ cnt,
+                     const int32_t* __restrict__ gptr, int32_t* __restrict__ glist) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nagg) return;
   const int cb = crp[I], ce = crp[I + 1];
-  for (int q = cb; q < ce; ++q) {
-    cursor[q] = 0;
-    lastmem[q] = -1;
-  }
+  for (int q = cb; q < ce; ++q) cnt[q] = 0;
   for (int m = mptr[I]; m < mptr[I + 1]; ++m) {
     const int i = mem[m];
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {
-      const int q = find_col(cci, cb, ce, agg[ci[k]]);
-      const bool first = lastmem[q] != i;
-      lastmem[q] = i;
-      glist[gptr[q] + cursor[q]++] = first ? -1 - k : k;
+    for (int a = aprp[i]; a < aprp[i + 1]; ++a) {
+      const int q = find_col(cci, cb, ce, apci[a]);
+      if (pass == 0) cnt[q]++;
+      else glist[gptr[q] + cnt[q]++] = a;
     }
   }
 }
 
-// R A P with tentative P: coarse block (I, J) = sum over members i of I
-// (ascending) of [sum over row i's blocks k (ascending) with agg(col k) = J
-// of A_k], each sum a plain left-to-right FP64 add from +0. (This is the
-// general product with identity blocks: fma(a, 1, acc) = acc + a and
-// fma(a, 0, acc) = acc.) One thread per coarse element: the n*n threads of a
-// block read each contributing fine block as one coalesced span; list
-// entries are prefetched four at a time.
+// out[q] = sum over list[gptr[q] .. gptr[q+1]) of src[list[p]] (n*n blocks),
+// plain FP64 adds from +0 in list order. Each thread serves LS_OUT outputs
+// (elements t, t + T, ...) whose dependent load chains it interleaves, so
+// enough loads are in flight to cover HBM latency.
+constexpr int LS_OUT = 4;
+
 template <int NN>
-__global__ void k_gal_gather(int cnnz, const int32_t* __restrict__ gptr, const int32_t* __restrict__ glist,
-                             const double* __restrict__ val, double* __restrict__ out) {
-  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t >= (size_t)cnnz * NN) return;
-  const size_t q = t / NN;
-  const int e = (int)(t - q * NN);
-  double acc = 0.0, part = 0.0;
-  bool started = false;
-  const int pb = __ldg(gptr + q), pe = __ldg(gptr + q + 1);
-  for (int p = pb; p < pe; p += 4) {
-    int kk[4];
-    double v[4];
+__global__ void __launch_bounds__(256) k_list_sum(unsigned nout, const int32_t* __restrict__ gptr,
+                                                  const int32_t* __restrict__ glist,
+                                                  const double* __restrict__ src, double* __restrict__ out) {
+  const unsigned total = nout * NN;
+  const unsigned T = gridDim.x * blockDim.x;
+  for (unsigned base = blockIdx.x * blockDim.x + threadIdx.x; base < total; base += LS_OUT * T) {
+    unsigned q[LS_OUT], e[LS_OUT];
+    int pb[LS_OUT], len[LS_OUT];
+    double acc[LS_OUT];
+    int maxlen = 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) kk[u] = p + u < pe ? __ldg(glist + p + u) : 0;
+    for (int u = 0; u < LS_OUT; ++u) {
+      const unsigned t = base + u * T;
+      const bool ok = t < total;
+      q[u] = ok ? t / NN : 0;
+      e[u] = ok ? t - q[u] * NN : 0;
+      pb[u] = ok ? __ldg(gptr + q[u]) : 0;
+      len[u] = ok ? __ldg(gptr + q[u] + 1) - pb[u] : 0;
+      acc[u] = 0.0;
+      maxlen = max(maxlen, len[u]);
+    }
+    for (int o = 0; o < maxlen; ++o) {
+      int k[LS_OUT];
+      double v[LS_OUT];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int k = kk[u] < 0 ? -1 - kk[u] : kk[u];
-      v[u] = p + u < pe ? __ldg(val + (size_t)k * NN + e) : 0.0;
+      for (int u = 0; u < LS_OUT; ++u) k[u] = o < len[u] ? __ldg(glist + pb[u] + o) : -1;
+#pragma unroll
+      for (int u = 0; u < LS_OUT; ++u) v[u] = k[u] >= 0 ? __ldg(src + (size_t)k[u] * NN + e[u]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < LS_OUT; ++u)
+        if (k[u] >= 0) acc[u] = acc[u] + v[u];
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (p + u >= pe) break;
-      if (kk[u] < 0) {
-        if (started) acc = acc + part;
-        part = 0.0;
-      }
-      part = part + v[u];
-      started = true;
-    }
+    for (int u = 0; u < LS_OUT; ++u)
+      if (base + u * T < total) out[base + u * T] = acc[u];
   }
-  if (started) acc = acc + part;
-  out[t] = acc;
 }
 
 // ----------------------------------------------------- smoothed prolongation
@@ -657,7 +683,7 @@ bcs_status max_of(Solver* s, const int32_t* a, int n, int32_t* out) {
   DBuf<int32_t> m;
   BCS_ALLOC(s, m, 1);
   BCS_CU(s, cudaMemsetAsync(m.p, 0, sizeof(int32_t), s->stream));
-  if (n > 0) BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_max_int, grid_for(n, 256), 256, 0, n, a, m.p);
+  if (n > 0) BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_max_int, grid_for(n, 256) < 1024 ? grid_for(n, 256) : 1024, 256, 0, n, a, m.p);
   return read_int(s, m.p, out);
 }
 
@@ -756,48 +782,79 @@ bcs_status members(Solver* s, int rows, int nagg, const int32_t* agg, DBuf<int32
 
 // Gather lists of the tentative Galerkin product: per coarse block, its
 // contributing fine blocks in ascending position.
-struct TentGather {
-  DBuf<int32_t> gptr, glist;
+// Gather lists of the two tentative products (see k_list_sum).
+struct TentPlan {
+  DBuf<int32_t> apg_ptr, apg_list, cg_ptr, cg_list;
 };
 
+// Patterns of AP = A P_tent (row i: sorted aggregates of its neighbours) and
+// of A_c = P_tent^T AP (row I: sorted aggregates reached from its members),
+// and the gather lists of both products.
 bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, const int32_t* mptr,
-                        const int32_t* mem, Bsr& Ac, DBuf<int32_t>& crow, TentGather& g) {
+                        const int32_t* mem, Bsr& AP, DBuf<int32_t>& aprow, Bsr& Ac, DBuf<int32_t>& crow,
+                        TentPlan& plan) {
+  const int rows = A.rows;
+  {
+    DBuf<int32_t> cnt;
+    BCS_ALLOC(s, cnt, rows);
+    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_p, grid_for(rows, 256), 256, 0, rows, A.rp.p, cnt.p);
+    auto fill = [&](const int32_t*, int32_t* cand) -> bcs_status {
+      BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_fill_p, grid_for(rows, 256), 256, 0, rows, A.rp.p, A.ci.p, agg,
+                 cand);
+      return BCS_OK;
+    };
+    BCS_OKR(pattern_from_candidates(s, rows, cnt, fill, AP, aprow));
+    AP.cols = nagg;
+  }
+  {
+    DBuf<int32_t> cnt;
+    BCS_ALLOC(s, cnt, nagg);
+    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p,
+               cnt.p);
+    auto fill = [&](const int32_t* cptr, int32_t* cand) -> bcs_status {
+      BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_fill_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p,
+                 A.ci.p, agg, cptr, cand);
+      return BCS_OK;
+    };
+    BCS_OKR(pattern_from_candidates(s, nagg, cnt, fill, Ac, crow));
+    Ac.cols = nagg;
+  }
   DBuf<int32_t> cnt;
-  BCS_ALLOC(s, cnt, nagg);
-  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p,
-             cnt.p);
-  auto fill = [&](const int32_t* cptr, int32_t* cand) -> bcs_status {
-    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_fill_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p,
-               A.ci.p, agg, cptr, cand);
-    return BCS_OK;
-  };
-  BCS_OKR(pattern_from_candidates(s, nagg, cnt, fill, Ac, crow));
-  Ac.cols = nagg;
-  DBuf<int32_t> gcnt, cursor, lastmem;
-  BCS_ALLOC(s, gcnt, Ac.nnz);
-  BCS_ALLOC(s, cursor, Ac.nnz);
-  BCS_ALLOC(s, lastmem, Ac.nnz);
-  BCS_ALLOC(s, g.gptr, Ac.nnz + 1);
-  BCS_ALLOC(s, g.glist, A.nnz);
-  BCS_CU(s, cudaMemsetAsync(gcnt.p, 0, Ac.nnz * sizeof(int32_t), s->stream));
-  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_tent_count, grid_for(A.rows, 256), 256, 0, A.rows, A.rp.p, A.ci.p, agg,
-             Ac.rp.p, Ac.ci.p, gcnt.p);
-  BCS_OKR(exclusive_scan(s, gcnt.p, g.gptr.p, Ac.nnz));
-  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_tent_fill, grid_for(nagg, 128), 128, 0, nagg, mptr, mem, A.rp.p, A.ci.p, agg,
-             Ac.rp.p, Ac.ci.p, g.gptr.p, cursor.p, lastmem.p, g.glist.p);
+  BCS_ALLOC(s, cnt, (AP.nnz > Ac.nnz ? AP.nnz : Ac.nnz) + 1);
+  BCS_ALLOC(s, plan.apg_ptr, AP.nnz + 1);
+  BCS_ALLOC(s, plan.apg_list, A.nnz);
+  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_apg, grid_for(rows, 128), 128, 0, rows, 0, A.rp.p, A.ci.p, agg, AP.rp.p,
+             AP.ci.p, cnt.p, (const int32_t*)nullptr, (int32_t*)nullptr);
+  BCS_OKR(exclusive_scan(s, cnt.p, plan.apg_ptr.p, AP.nnz));
+  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_apg, grid_for(rows, 128), 128, 0, rows, 1, A.rp.p, A.ci.p, agg, AP.rp.p,
+             AP.ci.p, cnt.p, plan.apg_ptr.p, plan.apg_list.p);
+  BCS_ALLOC(s, plan.cg_ptr, Ac.nnz + 1);
+  BCS_ALLOC(s, plan.cg_list, AP.nnz);
+  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cg, grid_for(nagg, 128), 128, 0, nagg, 0, mptr, mem, AP.rp.p, AP.ci.p,
+             Ac.rp.p, Ac.ci.p, cnt.p, (const int32_t*)nullptr, (int32_t*)nullptr);
+  BCS_OKR(exclusive_scan(s, cnt.p, plan.cg_ptr.p, Ac.nnz));
+  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cg, grid_for(nagg, 128), 128, 0, nagg, 1, mptr, mem, AP.rp.p, AP.ci.p,
+             Ac.rp.p, Ac.ci.p, cnt.p, plan.cg_ptr.p, plan.cg_list.p);
   return BCS_OK;
 }
 
-bcs_status tent_values(Solver* s, const Bsr& A, const TentGather& g, Bsr& Ac) {
+bcs_status tent_values(Solver* s, const Bsr& A, const TentPlan& plan, Bsr& AP, Bsr& Ac) {
   const int n = s->n;
+  BCS_ALLOC(s, AP.v, (size_t)AP.nnz * n * n);
   BCS_ALLOC(s, Ac.v, (size_t)Ac.nnz * n * n);
-  return with_n(n, [&](auto NC) -> bcs_status {
+  BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    const size_t work = (size_t)Ac.nnz * N * N;
-    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + Ac.nnz) * N * N + 8.0 * A.nnz + 4.0 * Ac.nnz, 1.0 * A.nnz * N * N,
-               k_gal_gather<N * N>, grid_for(work, 256), 256, 0, Ac.nnz, g.gptr.p, g.glist.p, A.v.p, Ac.v.p);
+    if ((size_t)AP.nnz * N * N >= (1ull << 31)) return s->fail(BCS_EINVAL, "Galerkin product too large");
+    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + AP.nnz) * N * N + 4.0 * A.nnz, 1.0 * A.nnz * N * N,
+               k_list_sum<N * N>, grid_for(((size_t)AP.nnz * N * N + LS_OUT - 1) / LS_OUT, 256), 256, 0,
+               (unsigned)AP.nnz, plan.apg_ptr.p, plan.apg_list.p, A.v.p, AP.v.p);
+    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (AP.nnz + Ac.nnz) * N * N + 4.0 * AP.nnz, 1.0 * AP.nnz * N * N,
+               k_list_sum<N * N>, grid_for(((size_t)Ac.nnz * N * N + LS_OUT - 1) / LS_OUT, 256), 256, 0,
+               (unsigned)Ac.nnz, plan.cg_ptr.p, plan.cg_list.p, AP.v.p, Ac.v.p);
     return BCS_OK;
-  });
+  }));
+  AP.v.release();  // AP values are a temporary of the product
+  return BCS_OK;
 }
 
 // Aggregation with agg_passes matching passes; fills L.agg / L.nagg.
@@ -813,10 +870,11 @@ bcs_status aggregate_level(Solver* s, Level& L) {
   for (int pass = 1; pass < s->setup_cfg.agg_passes; ++pass) {
     DBuf<int32_t> mptr, mem, crow;
     BCS_OKR(members(s, cur->rows, nagg, cur_agg.p, mptr, mem));
-    Bsr Abar;
-    TentGather g;
-    BCS_OKR(tent_pattern(s, *cur, nagg, cur_agg.p, mptr.p, mem.p, Abar, crow, g));
-    BCS_OKR(tent_values(s, *cur, g, Abar));
+    Bsr Abar, AP;
+    DBuf<int32_t> aprow;
+    TentPlan plan;
+    BCS_OKR(tent_pattern(s, *cur, nagg, cur_agg.p, mptr.p, mem.p, AP, aprow, Abar, crow, plan));
+    BCS_OKR(tent_values(s, *cur, plan, AP, Abar));
     DBuf<int32_t> a2;
     int n2 = 0;
     BCS_OKR(match_pass(s, Abar, a2, &n2));
@@ -1000,21 +1058,21 @@ bcs_status build_transfer(Solver* s, int l, bool full) {
   Level& Lc = s->lv[l + 1];
   if (full) BCS_OKR(members(s, L.A.rows, L.nagg, L.agg.p, L.mptr, L.mem));
   if (s->setup_cfg.pmode == BCS_P_TENTATIVE) {
+    TentPlan plan;
     if (full) {
-      TentGather g;
-      BCS_OKR(tent_pattern(s, L.A, L.nagg, L.agg.p, L.mptr.p, L.mem.p, Lc.A, L.Crow, g));
-      L.Gptr = std::move(g.gptr);
-      L.Glist = std::move(g.glist);
+      BCS_OKR(tent_pattern(s, L.A, L.nagg, L.agg.p, L.mptr.p, L.mem.p, L.AP, L.AProw, Lc.A, L.Crow, plan));
+    } else {
+      plan.apg_ptr = std::move(L.apg_ptr);
+      plan.apg_list = std::move(L.apg_list);
+      plan.cg_ptr = std::move(L.cg_ptr);
+      plan.cg_list = std::move(L.cg_list);
     }
-    {
-      TentGather g;
-      g.gptr = std::move(L.Gptr);
-      g.glist = std::move(L.Glist);
-      const bcs_status st = tent_values(s, L.A, g, Lc.A);
-      L.Gptr = std::move(g.gptr);
-      L.Glist = std::move(g.glist);
-      BCS_OKR(st);
-    }
+    const bcs_status st = tent_values(s, L.A, plan, L.AP, Lc.A);
+    L.apg_ptr = std::move(plan.apg_ptr);
+    L.apg_list = std::move(plan.apg_list);
+    L.cg_ptr = std::move(plan.cg_ptr);
+    L.cg_list = std::move(plan.cg_list);
+    BCS_OKR(st);
   } else {
     BCS_OKR(smoothed_prolongation(s, L, full));
     BCS_OKR(spgemm(s, L.A, L.P, L.AP, L.AProw, full));

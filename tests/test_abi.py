@@ -64,3 +64,12 @@ def test_struct_layouts_match_header():
     names = [f.strip() for group in re.findall(r"^\s*(?:int|double)\s+([\w, ]+);", body, re.M)
              for f in group.split(",")]
     assert names == [f for f, _ in bcs.bcs_result._fields_]
+
+
+def test_server_argument_checks(lib):
+    h = ct.c_void_p()
+    assert lib.bcs_server_create(ct.byref(h), 0, 0, None) == bcs.BCS_EINVAL    # no slots
+    assert lib.bcs_server_create(None, 0, 2, None) == bcs.BCS_EINVAL
+    assert lib.bcs_server_destroy(None) == bcs.BCS_OK
+    cid = ct.c_int()
+    assert lib.bcs_server_register_case(None, 5, 10, 0, None, None, ct.byref(cid)) == bcs.BCS_EINVAL

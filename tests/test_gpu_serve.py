@@ -1,0 +1,104 @@
+"""Serving (continuous batching across cases): every result is bit-identical
+whether its case runs alone or interleaved with other cases on several
+slots; admission by memory budget evicts idle cases and rejects cases that
+can never fit; every solve reaches the 1e-8 true residual."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_07882_b300 import bcs, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def cases():
+    return [synth.density(10, seed=1), synth.pressure(8, seed=2), synth.density(12, 9, 7, seed=3),
+            synth.random_graph(500, 1500, 3, seed=4)]
+
+
+def sequences(systems, k=3):
+    out = []
+    for c, sys0 in enumerate(systems):
+        rng = np.random.default_rng(100 + c)
+        seq, cur = [], sys0
+        for _ in range(k):
+            cur = synth.perturb(cur, rng, 0.02)
+            seq.append(cur)
+        out.append(seq)
+    return out
+
+
+def true_rel(system, x):
+    ref = oracle.ldu_to_bsr(system)
+    r = system["b"] - oracle.spmv(ref, x)
+    return np.linalg.norm(r) / np.linalg.norm(system["b"])
+
+
+def test_results_identical_alone_and_in_mix():
+    systems = cases()
+    seqs = sequences(systems)
+    alone = []
+    for c, system in enumerate(systems):
+        with bcs.Server(slots=1) as srv:
+            cid = srv.register(system)
+            tickets = [srv.submit(cid, s) for s in seqs[c]]
+            xs = []
+            for t in tickets:
+                st, res, lat, x = srv.wait(t)
+                assert st == bcs.BCS_OK, res
+                xs.append(x)
+            alone.append(xs)
+    with bcs.Server(slots=3) as srv:
+        ids = [srv.register(s) for s in systems]
+        tickets = []
+        for j in range(3):                      # round-robin arrivals
+            for c in range(len(systems)):
+                tickets.append((c, j, srv.submit(ids[c], seqs[c][j])))
+        for c, j, t in tickets:
+            st, res, lat, x = srv.wait(t)
+            assert st == bcs.BCS_OK, res
+            assert np.array_equal(x, alone[c][j]), (c, j)
+            assert true_rel(seqs[c][j], x) <= 1e-8
+            assert lat > 0
+        stats = srv.stats()
+    assert stats["completed"] == 12 and stats["rejected"] == 0
+    assert stats["p99_ms"] >= stats["p50_ms"] > 0
+
+
+def test_tight_budget_evicts_and_oversize_is_rejected():
+    systems = cases()
+    sizes = []
+    for s_ in systems:                           # measured footprint of each case alone
+        with bcs.Server(slots=1) as probe:
+            cid = probe.register(s_)
+            st, *_ = probe.wait(probe.submit(cid, s_))
+            assert st == bcs.BCS_OK
+            sizes.append(probe.stats()["resident_bytes"])
+    budget = int(2.0 * max(sizes))
+    assert sum(sizes) > budget                   # not every case fits at once
+    with bcs.Server(budget_bytes=budget, slots=2) as srv:
+        ids = [srv.register(s_) for s_ in systems]
+        tickets = [(c % 4, srv.submit(ids[c % 4], systems[c % 4])) for c in range(12)]
+        for c, t in tickets:
+            st, res, lat, x = srv.wait(t)
+            assert st == bcs.BCS_OK, res
+            assert true_rel(systems[c], x) <= 1e-8
+        st = srv.stats()
+        assert st["resident_bytes"] <= budget
+    assert st["evictions"] > 0 and st["completed"] == 12
+    with bcs.Server(budget_bytes=1 << 16, slots=1) as srv:   # 64 KiB: nothing fits
+        cid = srv.register(systems[0])
+        st, res, lat, x = srv.wait(srv.submit(cid, systems[0]))
+        assert st == bcs.BCS_REJECTED
+
+
+def test_wait_with_timeout():
+    system = synth.density(24, seed=5)
+    with bcs.Server(slots=1) as srv:
+        cid = srv.register(system)
+        t = srv.submit(cid, system)
+        st, res, lat, x = srv.wait(t, timeout_ms=0)
+        if st == bcs.BCS_TIMEOUT:
+            st, res, lat, x = srv.wait(t)
+        assert st == bcs.BCS_OK and true_rel(system, x) <= 1e-8
