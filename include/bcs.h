@@ -87,8 +87,6 @@ typedef struct bcs_config {
   int coarse_sweeps;       /* else this many block-Jacobi sweeps there (8) */
   int precision;           /* AMG storage: BCS_PREC_FP64, BCS_PREC_FP32 (default), BCS_PREC_BF16 */
   int profile;             /* 1: time kernels with CUDA events (bcs_get_stats) */
-  int staging;             /* 1: FP32/BF16 sweeps and residuals stage block rows in shared
-                              memory with bulk copies (default 0: direct loads) */
 } bcs_config;
 
 typedef struct bcs_result {

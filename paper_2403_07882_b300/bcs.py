@@ -33,7 +33,7 @@ class bcs_config(ct.Structure):
         ("agg_passes", ct.c_int), ("jacobi_omega", ct.c_double), ("nu1", ct.c_int), ("nu2", ct.c_int),
         ("coarse_size", ct.c_int), ("max_levels", ct.c_int), ("max_coarsen_ratio", ct.c_double),
         ("p_omega", ct.c_double), ("coarse_dense_max", ct.c_int), ("coarse_sweeps", ct.c_int),
-        ("precision", ct.c_int), ("profile", ct.c_int), ("staging", ct.c_int),
+        ("precision", ct.c_int), ("profile", ct.c_int),
     ]
 
 

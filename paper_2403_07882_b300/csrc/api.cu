@@ -101,7 +101,6 @@ bcs_status check_config(const bcs_config* c) {
   if (c->coarse_size < 1 || c->max_levels < 1 || c->coarse_sweeps < 1) return BCS_EINVAL;
   if (c->coarse_dense_max < 1 || c->coarse_dense_max > 8192) return BCS_EINVAL;
   if (c->precision < BCS_PREC_FP64 || c->precision > BCS_PREC_BF16) return BCS_EINVAL;
-  if (c->staging < 0 || c->staging > 1) return BCS_EINVAL;
   if (!(c->max_coarsen_ratio > 0.0) || !(c->p_omega > 0.0) || !(c->jacobi_omega > 0.0)) return BCS_EINVAL;
   return BCS_OK;
 }
@@ -166,7 +165,6 @@ bcs_status bcs_config_default(bcs_config* c) {
   c->coarse_sweeps = 8;
   c->precision = BCS_PREC_FP32;
   c->profile = 0;
-  c->staging = 0;
   return BCS_OK;
 }
 

@@ -71,6 +71,118 @@ __global__ void __launch_bounds__(128) k_rows(int rows, const int32_t* __restric
   else y[o] = (TY)((AT)b[o] - acc);
 }
 
+// ---- sliced (SELL) copy for the FP32 / BF16 cycle ---------------------------
+// A slice is floor(32/n) consecutive block rows served by one warp (lane l:
+// scalar row r = l % n of block row rw = l / n). Step t of a slice holds the
+// k-th block of each of its rows, stored column-major so that for a fixed
+// column c the warp reads one contiguous run: value (rw, r, c) of step t sits
+// at t * n*n*RPW + (c * RPW + rw) * n + r. Rows shorter than the slice's
+// longest are padded (the padding is skipped). Each lane loads one component
+// of its row's x block and the row's lanes exchange them by shuffle.
+__global__ void k_slice_len(int rows, int rpw, int nslices, const int32_t* __restrict__ rp,
+                            int32_t* __restrict__ slen) {
+  const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= nslices) return;
+  int m = 0;
+  for (int rw = 0; rw < rpw; ++rw) {
+    const int i = sl * rpw + rw;
+    if (i < rows) m = max(m, rp[i + 1] - rp[i]);
+  }
+  slen[sl] = m;
+}
+
+template <int N, class TV>
+__global__ void k_slice_fill(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const double* __restrict__ val, const int32_t* __restrict__ sptr,
+                             int32_t* __restrict__ sci, TV* __restrict__ sv) {
+  constexpr int NN = N * N, RPW = 32 / N;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)rows * NN) return;
+  const int i = (int)(t / NN), e = (int)(t - (size_t)i * NN);
+  const int r = e / N, c = e - r * N, rw = i % RPW;
+  const int step0 = sptr[i / RPW];
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const size_t step = (size_t)step0 + (p - rp[i]);
+    const double v = val[(size_t)p * NN + e];
+    if constexpr (std::is_same<TV, bf16>::value) sv[step * NN * RPW + (c * RPW + rw) * N + r] = __double2bfloat16(v);
+    else sv[step * NN * RPW + (c * RPW + rw) * N + r] = (TV)v;
+    if (e == 0) sci[step * RPW + rw] = ci[p];
+  }
+}
+
+__device__ __forceinline__ float ldsv(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldsv(const bf16* p) { return __bfloat162float(__ldg(p)); }
+
+// JACOBI: y = x + omega D^-1 (b - A x); otherwise y = b - A x. Same fma order
+// as k_jacobi / k_rows (blocks in row order, columns ascending). Steps are
+// consumed in chunks of SELL_U: the chunk's column indices are loaded
+// together, then the x components they select, then the values, so a warp
+// keeps several HBM round trips in flight instead of one per step; the
+// epilogue's operands are loaded before the row loop.
+constexpr int SELL_U = 4;
+
+template <int N, class TV, bool JACOBI>
+__global__ void __launch_bounds__(128) k_sell(int rows, int nslices, const int32_t* __restrict__ rp,
+                                              const int32_t* __restrict__ sptr, const int32_t* __restrict__ sci,
+                                              const TV* __restrict__ sv, const float* __restrict__ dinv,
+                                              const float* __restrict__ x, const float* __restrict__ b,
+                                              float* __restrict__ y, float omega) {
+  constexpr int RPW = 32 / N, NN = N * N, TILE = NN * RPW;
+  const int lane = threadIdx.x & 31;
+  const int rw = lane / N, r = lane - rw * N;
+  const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (sl >= nslices) return;  // uniform across the warp
+  const int i = sl * RPW + rw;
+  const bool active = rw < RPW && i < rows;
+  const size_t o = (size_t)i * N + r;
+  const float bo = active ? __ldg(b + o) : 0.f;
+  float xo = 0.f, d[N];
+  if (JACOBI) {
+    xo = active ? x[o] : 0.f;
+#pragma unroll
+    for (int c = 0; c < N; ++c) d[c] = active ? __ldg(dinv + o * N + c) : 0.f;
+  }
+  const int len = active ? __ldg(rp + i + 1) - __ldg(rp + i) : 0;
+  const int t0 = __ldg(sptr + sl), nt = __ldg(sptr + sl + 1) - t0;
+  float acc = 0.f;
+  for (int k0 = 0; k0 < nt; k0 += SELL_U) {
+    int j[SELL_U];
+    float xv[SELL_U], a[SELL_U][N];
+#pragma unroll
+    for (int u = 0; u < SELL_U; ++u) {
+      const bool live = active && k0 + u < len;
+      j[u] = live ? __ldg(sci + (size_t)(t0 + k0 + u) * RPW + rw) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < SELL_U; ++u) xv[u] = (active && k0 + u < len) ? __ldg(x + (size_t)j[u] * N + r) : 0.f;
+#pragma unroll
+    for (int u = 0; u < SELL_U; ++u) {
+      const TV* tile = sv + (size_t)(t0 + k0 + u) * TILE;
+#pragma unroll
+      for (int c = 0; c < N; ++c) a[u][c] = (active && k0 + u < len) ? ldsv(tile + c * RPW * N + lane) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < SELL_U; ++u)
+#pragma unroll
+      for (int c = 0; c < N; ++c) {
+        const float xc = __shfl_sync(0xffffffffu, xv[u], (rw * N + c) & 31);
+        if (active && k0 + u < len) acc = fmaf(a[u][c], xc, acc);
+      }
+  }
+  if (!JACOBI) {
+    if (active) y[o] = bo - acc;
+    return;
+  }
+  const float res = active ? bo - acc : 0.f;
+  float tt = 0.f;
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    const float rc = __shfl_sync(0xffffffffu, res, (rw * N + c) & 31);
+    if (active) tt = fmaf(d[c], rc, tt);
+  }
+  if (active) y[o] = xo + omega * tt;
+}
+
 // y = x + omega D^-1 (b - A x)
 template <int N, class AT, class TV, class TD, class TC>
 __global__ void __launch_bounds__(128) k_jacobi(int rows, const int32_t* __restrict__ rp,
@@ -224,6 +336,7 @@ struct Cycle {
   static const TD* dinv(const Level& L);
   static const TV* pmat(const Level& L);
   static const TV* rmat(const Level& L);
+  static const TV* smat(const Level& L);
 
   template <int N>
   bcs_status sweep0(const Level& L, const TC* b, TC* y) {
@@ -237,29 +350,31 @@ struct Cycle {
   bcs_status sweep(const Level& L, const TC* x, const TC* b, TC* y) {
     const int rows = L.A.rows;
     const AT om = (AT)s->setup_cfg.jacobi_omega;
-    if constexpr (std::is_same<TC, float>::value) {
-      bool used = false;
-      if (s->cfg.staging) BCS_OKR(staged_sweep<N, TV>(s, const_cast<Level&>(L), mat(L), dinv(L), x, b, y, om, &used));
-      if (used) return BCS_OK;
-    }
     const double bytes = (double)L.A.nnz * (N * N * sizeof(TV) + 4) + 4.0 * (rows + 1) +
                          (double)rows * N * (N * sizeof(TD) + 3 * sizeof(TC));
-    BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_jacobi<N, AT, TV, TD, TC>),
-               rows_grid(rows, N), 128, 0, rows, L.A.rp.p, L.A.ci.p, mat(L), dinv(L), x, b, y, om);
+    if constexpr (std::is_same<TC, float>::value) {
+      BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_sell<N, TV, true>),
+                 grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.sptr.p, L.sci.p,
+                 smat(L), dinv(L), x, b, y, om);
+    } else {
+      BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_jacobi<N, AT, TV, TD, TC>),
+                 rows_grid(rows, N), 128, 0, rows, L.A.rp.p, L.A.ci.p, mat(L), dinv(L), x, b, y, om);
+    }
     return BCS_OK;
   }
   template <int N>
   bcs_status resid(const Level& L, const TC* x, const TC* b, TC* r) {
     const int rows = L.A.rows;
-    if constexpr (std::is_same<TC, float>::value) {
-      bool used = false;
-      if (s->cfg.staging) BCS_OKR(staged_resid<N, TV>(s, const_cast<Level&>(L), mat(L), x, b, r, &used));
-      if (used) return BCS_OK;
-    }
     const double bytes = (double)L.A.nnz * (N * N * sizeof(TV) + 4) + 4.0 * (rows + 1) +
                          (double)rows * N * 3 * sizeof(TC);
-    BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_rows<N, AT, TV, TC, TC, M_RESID>), rows_grid(rows, N),
-               128, 0, rows, L.A.rp.p, L.A.ci.p, mat(L), x, r, b);
+    if constexpr (std::is_same<TC, float>::value) {
+      BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_sell<N, TV, false>),
+                 grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.sptr.p, L.sci.p,
+                 smat(L), (const float*)nullptr, x, b, r, 0.f);
+    } else {
+      BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_rows<N, AT, TV, TC, TC, M_RESID>),
+                 rows_grid(rows, N), 128, 0, rows, L.A.rp.p, L.A.ci.p, mat(L), x, r, b);
+    }
     return BCS_OK;
   }
   template <int N>
@@ -345,11 +460,14 @@ template <> const double* Cycle<double, double, double, double>::mat(const Level
 template <> const double* Cycle<double, double, double, double>::dinv(const Level& L) { return L.dinv.p; }
 template <> const double* Cycle<double, double, double, double>::pmat(const Level& L) { return L.P.v.p; }
 template <> const double* Cycle<double, double, double, double>::rmat(const Level& L) { return L.R.v.p; }
-template <> const float* Cycle<float, float, float, float>::mat(const Level& L) { return L.v32.p; }
+template <> const double* Cycle<double, double, double, double>::smat(const Level&) { return nullptr; }
+template <> const float* Cycle<float, float, float, float>::smat(const Level& L) { return L.s32.p; }
+template <> const bf16* Cycle<bf16, float, float, float>::smat(const Level& L) { return L.s16.p; }
+template <> const float* Cycle<float, float, float, float>::mat(const Level&) { return nullptr; }
 template <> const float* Cycle<float, float, float, float>::dinv(const Level& L) { return L.dinv32.p; }
 template <> const float* Cycle<float, float, float, float>::pmat(const Level& L) { return L.P32.p; }
 template <> const float* Cycle<float, float, float, float>::rmat(const Level& L) { return L.R32.p; }
-template <> const bf16* Cycle<bf16, float, float, float>::mat(const Level& L) { return L.v16.p; }
+template <> const bf16* Cycle<bf16, float, float, float>::mat(const Level&) { return nullptr; }
 template <> const float* Cycle<bf16, float, float, float>::dinv(const Level& L) { return L.dinv32.p; }
 template <> const bf16* Cycle<bf16, float, float, float>::pmat(const Level& L) { return L.P16.p; }
 template <> const bf16* Cycle<bf16, float, float, float>::rmat(const Level& L) { return L.R16.p; }
@@ -365,6 +483,42 @@ bcs_status run_cycle(Solver* s, const TC* b, TC* x) {
 
 }  // namespace
 
+// Sliced copy of level L's operator in the cycle precision (structure once
+// per hierarchy, values at every setup / resetup).
+bcs_status build_slices(Solver* s, Level& L, int prec) {
+  const int n = s->n, rows = L.A.rows, rpw = 32 / n;
+  if (L.nslices == 0) {
+    const int ns = (rows + rpw - 1) / rpw;
+    DBuf<int32_t> slen;
+    BCS_ALLOC(s, slen, ns);
+    BCS_ALLOC(s, L.sptr, ns + 1);
+    BCS_LAUNCH(s, K_CAST, 0, 0, k_slice_len, grid_for(ns, 256), 256, 0, rows, rpw, ns, L.A.rp.p, slen.p);
+    BCS_OKR(exclusive_scan(s, slen.p, L.sptr.p, ns));
+    int32_t steps = 0;
+    BCS_CU(s, cudaMemcpyAsync(&steps, L.sptr.p + ns, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    BCS_CU(s, cudaStreamSynchronize(s->stream));
+    L.nslices = ns;
+    L.nsteps = steps;
+    BCS_ALLOC(s, L.sci, (size_t)steps * rpw);
+  }
+  const size_t nv = (size_t)L.nsteps * rpw * n * n;
+  return with_n(n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    const unsigned g = grid_for((size_t)rows * N * N, 256);
+    const double bytes = (double)L.A.nnz * N * N * (8 + (prec == BCS_PREC_FP32 ? 4 : 2));
+    if (prec == BCS_PREC_FP32) {
+      BCS_ALLOC(s, L.s32, nv);
+      BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, float>), g, 256, 0, rows, L.A.rp.p, L.A.ci.p, L.A.v.p,
+                 L.sptr.p, L.sci.p, L.s32.p);
+    } else {
+      BCS_ALLOC(s, L.s16, nv);
+      BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, bf16>), g, 256, 0, rows, L.A.rp.p, L.A.ci.p, L.A.v.p,
+                 L.sptr.p, L.sci.p, L.s16.p);
+    }
+    return BCS_OK;
+  });
+}
+
 // Cycle vectors and storage copies of the hierarchy in the configured
 // precision (after every setup / resetup).
 bcs_status cycle_prepare(Solver* s) {
@@ -379,29 +533,22 @@ bcs_status cycle_prepare(Solver* s) {
     BCS_ALLOC(s, L.vr, N * vsz);
     BCS_ALLOC(s, L.vt, N * vsz);
     if (prec == BCS_PREC_FP64 || s->setup_cfg.precond != BCS_PC_AMG) continue;
-    if (s->cfg.staging) BCS_OKR(level_tile_stats(s, L));
     BCS_ALLOC(s, L.dinv32, (size_t)L.A.rows * nn);
     BCS_OKR(cast_vec<double, float>(s, L.dinv.p, L.dinv32.p, (size_t)L.A.rows * nn));
-    const size_t an = (size_t)L.A.nnz * nn;
     const bool smoothed = L.coarse_kind < 0 && s->setup_cfg.pmode == BCS_P_SMOOTHED;
+    BCS_OKR(build_slices(s, L, prec));
     if (prec == BCS_PREC_FP32) {
-      BCS_ALLOC(s, L.v32, an);
-      BCS_OKR(cast_vec<double, float>(s, L.A.v.p, L.v32.p, an));
       if (smoothed) {
         BCS_ALLOC(s, L.P32, (size_t)L.P.nnz * nn);
         BCS_ALLOC(s, L.R32, (size_t)L.R.nnz * nn);
         BCS_OKR(cast_vec<double, float>(s, L.P.v.p, L.P32.p, (size_t)L.P.nnz * nn));
         BCS_OKR(cast_vec<double, float>(s, L.R.v.p, L.R32.p, (size_t)L.R.nnz * nn));
       }
-    } else {
-      BCS_ALLOC(s, L.v16, an);
-      BCS_OKR(cast_vec<double, bf16>(s, L.A.v.p, L.v16.p, an));
-      if (smoothed) {
-        BCS_ALLOC(s, L.P16, (size_t)L.P.nnz * nn);
-        BCS_ALLOC(s, L.R16, (size_t)L.R.nnz * nn);
-        BCS_OKR(cast_vec<double, bf16>(s, L.P.v.p, L.P16.p, (size_t)L.P.nnz * nn));
-        BCS_OKR(cast_vec<double, bf16>(s, L.R.v.p, L.R16.p, (size_t)L.R.nnz * nn));
-      }
+    } else if (smoothed) {
+      BCS_ALLOC(s, L.P16, (size_t)L.P.nnz * nn);
+      BCS_ALLOC(s, L.R16, (size_t)L.R.nnz * nn);
+      BCS_OKR(cast_vec<double, bf16>(s, L.P.v.p, L.P16.p, (size_t)L.P.nnz * nn));
+      BCS_OKR(cast_vec<double, bf16>(s, L.R.v.p, L.R16.p, (size_t)L.R.nnz * nn));
     }
   }
   return BCS_OK;

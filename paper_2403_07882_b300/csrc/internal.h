@@ -96,8 +96,7 @@ struct Level {
   Bsr A;                     // FP64 operator of this level
   DBuf<int32_t> dpos;        // diagonal block position per row
   DBuf<double> dinv;         // FP64 diagonal block inverses
-  DBuf<float> v32, dinv32;   // storage copies for the V-cycle
-  DBuf<bf16> v16;
+  DBuf<float> dinv32;        // FP32 block inverses for the FP32 / BF16 cycle
   // transfer to level l+1 (absent at the coarsest level)
   int nagg = 0;
   DBuf<int32_t> agg;         // aggregate of each row
@@ -109,7 +108,13 @@ struct Level {
   DBuf<bf16> P16, R16;
   double omega_p = 0.0;
   int coarse_kind = -1;      // -1 not coarsest, 0 dense inverse, 1 sweeps
-  int max_tile_blocks = -1;  // most blocks in one warp tile (floor(32/n) rows); -1 unknown
+  // sliced copy of A for the FP32 / BF16 cycle: slices of floor(32/n) block
+  // rows; slice s covers steps sptr[s] .. sptr[s+1]; step t holds one block per
+  // row (padding past a row's end), column-major inside the step
+  int nslices = 0, nsteps = 0;
+  DBuf<int32_t> sptr, sci;
+  DBuf<float> s32;
+  DBuf<bf16> s16;
   DBuf<char> vx, vb, vr, vt; // V-cycle vectors (cycle precision)
 };
 
@@ -259,16 +264,7 @@ bcs_status precond_apply(Solver* s, const double* v, void* z);  // z in cycle pr
 bcs_status jacobi_apply(Solver* s, const double* v, double* z);
 bool cycle_is_float(const Solver* s);
 
-// ------------------------------------------------------------------ staged.cu
-// Block-Jacobi sweep / residual with per-warp bulk-copy staging of the
-// warp's block rows; *used is false when the level's tiles are too large for
-// the staging buffers (the caller then uses the direct kernels).
-template <int N, class TV>
-bcs_status staged_sweep(Solver* s, Level& L, const TV* val, const float* dinv, const float* x, const float* b,
-                        float* y, float omega, bool* used);
-template <int N, class TV>
-bcs_status staged_resid(Solver* s, Level& L, const TV* val, const float* x, const float* b, float* r, bool* used);
-bcs_status level_tile_stats(Solver* s, Level& L);
+
 template <class TI, class TO>
 bcs_status cast_vec(Solver* s, const TI* in, TO* out, size_t N);
 
