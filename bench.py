@@ -46,6 +46,15 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison run")
+    p.add_argument("--workload", default="density128", choices=["density128", "knn", "serve"],
+                   help="density128: the benchmark line; knn: unstructured resetup sequence; serve: serving mix")
+    p.add_argument("--knn-side", type=int, default=160)
+    p.add_argument("--serve-cases", type=int, default=32)
+    p.add_argument("--serve-requests", type=int, default=2000)
+    p.add_argument("--serve-warmup", type=int, default=200)
+    p.add_argument("--serve-rate", type=float, default=200.0)
+    p.add_argument("--serve-max-cells", type=float, default=3e6)
+    p.add_argument("--serve-slots", type=int, default=8)
     return p.parse_args()
 
 
@@ -321,10 +330,138 @@ def run_native(args):
     print(json.dumps(line), flush=True)
 
 
+def run_knn(args):
+    """Config 4: unstructured k-NN mesh, one full setup, then ten values-only
+    resetups (2 % perturbation each, compounding) each followed by a solve."""
+    import torch
+    from paper_2403_07882_b300 import bcs, synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t0 = time.perf_counter()
+    system = synth.knn(args.knn_side, seed=3)
+    gen_s = time.perf_counter() - t0
+    keys = ("owner", "neighbour", "diag", "upper", "lower", "b")
+    d = {k: torch.from_numpy(system[k]).to(dev) for k in keys}
+    rng = np.random.default_rng(30)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"knn {args.knn_side}^3 jittered points, k~U{{4..12}}, 5x5 blocks, seed 3",
+           "cells": system["n_cells"], "faces": system["n_faces"], "generation_s": gen_s}
+    with bcs.Solver(5, precision=bcs.BCS_PREC_FP32) as s:
+        s.set_structure(system["n_cells"], d["owner"], d["neighbour"])
+        a, b_ = ev(), ev()
+        a.record(); s.set_values(d["diag"], d["upper"], d["lower"]); b_.record(); torch.cuda.synchronize()
+        out["full_setup_ms"] = a.elapsed_time(b_)
+        x = torch.zeros_like(d["b"])
+        _, st, res = s.solve(d["b"], x)
+        out["first_solve"] = {"status": st, "iters": res["iters"], "ms": res["solve_ms"], "levels": res["levels"]}
+        rs, ss, its = [], [], []
+        for it in range(10):
+            system = synth.perturb(system, rng, 0.02)
+            vals = [torch.from_numpy(system[k]).to(dev) for k in ("diag", "upper", "lower")]
+            torch.cuda.synchronize()
+            a, b_ = ev(), ev()
+            a.record(); s.set_values(*vals); b_.record(); torch.cuda.synchronize()
+            rs.append(a.elapsed_time(b_))
+            x.zero_()
+            a, b_ = ev(), ev()
+            a.record(); _, st, res = s.solve(d["b"], x); b_.record(); torch.cuda.synchronize()
+            assert st == bcs.BCS_OK, res
+            ss.append(a.elapsed_time(b_))
+            its.append(res["iters"])
+        out.update({"resetup_ms_mean": statistics.mean(rs), "solve_ms_mean": statistics.mean(ss),
+                    "iters": its, "resetup_over_full_setup": statistics.mean(rs) / out["full_setup_ms"]})
+    print(json.dumps({"impl": "native", "mode": "knn", **out}), flush=True)
+
+
+def run_serve(args):
+    """Config 5: many cases of different sizes, Poisson arrivals, values-only
+    resetup + solve per request, admission by HBM budget; p50 / p99 latency."""
+    import psutil
+    import torch
+    from paper_2403_07882_b300 import bcs, synth
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(4)
+    ncases = args.serve_cases
+    max_cells = args.serve_max_cells
+    # keep two value sets per case in host memory; shrink the size range if
+    # the host cannot hold them
+    avail = psutil.virtual_memory().available
+    while True:
+        cells = np.round(np.exp(np.random.default_rng(4).uniform(np.log(5e4), np.log(max_cells), ncases)))
+        host = float(np.sum(cells * 7.0 * 25 * 8 * 2.5))
+        if host < 0.4 * avail or max_cells <= 2e5:
+            break
+        max_cells *= 0.7
+    cases, ids = [], []
+    rng_case = np.random.default_rng(4)
+    _ = rng_case.uniform(np.log(5e4), np.log(max_cells), ncases)
+    with bcs.Server(slots=args.serve_slots) as srv:
+        for c in range(ncases):
+            nx = int(round(cells[c] ** (1.0 / 3.0)))
+            nz = max(1, int(round(cells[c] / (nx * nx))))
+            if rng_case.uniform() < 0.5:
+                sys0 = synth.pressure(nx, nx, nz, seed=1000 + c)
+            else:
+                sys0 = synth.density(nx, nx, nz, seed=1000 + c)
+            sys1 = synth.perturb(sys0, rng_case, 0.02)
+            cases.append((sys0, sys1))
+            ids.append(srv.register(sys0))
+        arr = np.random.default_rng(5)
+        total = args.serve_warmup + args.serve_requests
+        picks = arr.integers(0, ncases, total)
+        gaps = arr.exponential(1.0 / args.serve_rate, total)
+        pending = []
+        t_start = time.perf_counter()
+        t_next = t_start
+        lat = []
+        measure_from = None
+        for r in range(total):
+            t_next += gaps[r]
+            now = time.perf_counter()
+            if t_next > now:
+                time.sleep(t_next - now)
+            if r == args.serve_warmup:
+                measure_from = time.perf_counter()
+            c = int(picks[r])
+            sysv = cases[c][r % 2]
+            pending.append((r, srv.submit(ids[c], sysv)))
+            # collect finished requests without blocking the arrival clock
+            keep = []
+            for rr, t in pending:
+                st, res, l, x = srv.wait(t, timeout_ms=0)
+                if st == bcs.BCS_TIMEOUT:
+                    keep.append((rr, t))
+                else:
+                    assert st == bcs.BCS_OK, res
+                    if rr >= args.serve_warmup:
+                        lat.append(l)
+            pending = keep
+        for rr, t in pending:
+            st, res, l, x = srv.wait(t)
+            assert st == bcs.BCS_OK, res
+            if rr >= args.serve_warmup:
+                lat.append(l)
+        elapsed = time.perf_counter() - measure_from
+        stats = srv.stats()
+    lat = np.array(lat)
+    print(json.dumps({"impl": "native", "mode": "serve", "cases": ncases,
+                      "cells_range": [5e4, max_cells], "cells_mean": float(cells.mean()),
+                      "requests": args.serve_requests, "arrival_rate_per_s": args.serve_rate,
+                      "slots": args.serve_slots, "solves_per_s": args.serve_requests / elapsed,
+                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                      "mean_ms": float(lat.mean()), "evictions": stats["evictions"],
+                      "resident_bytes": stats["resident_bytes"], "budget_bytes": stats["budget_bytes"]}),
+          flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "knn":
+        run_knn(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_native(args)
 
