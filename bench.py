@@ -128,27 +128,30 @@ def peaks():
         return 6400.0, "fallback"
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary
-    (profiles/traffic.json), or None when absent or when the kernel's source
-    file has changed since the counters were taken."""
+def kernel_source_digest(path, func):
+    """SHA-256 of the text of __global__ function `func` in `path` (from its
+    definition line to the first line that closes it at column 0)."""
     import hashlib
+    lines = open(path).read().splitlines()
+    start = next(i for i, l in enumerate(lines) if "__global__" in l and (" " + func + "(") in l)
+    end = next(i for i in range(start, len(lines)) if lines[i] == "}")
+    return hashlib.sha256("\n".join(lines[start:end + 1]).encode()).hexdigest()
+
+
+def measured_traffic(kernel, bytes_per_launch):
+    """DRAM bytes per launch of `kernel`, from the committed ncu summary
+    (profiles/traffic.json: DRAM bytes over algorithmic bytes of a captured
+    launch), scaled to this run's algorithmic bytes per launch; None when
+    absent or when the kernel's source text changed since the capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             entries = json.load(f)
-    except (OSError, ValueError):
+        e = entries[kernel]
+        if kernel_source_digest(os.path.join(ROOT, e["source"]), e["function"]) != e["sha256"]:
+            return None
+    except (OSError, ValueError, KeyError, StopIteration):
         return None
-    e = entries.get(kernel)
-    if not e:
-        return None
-    src = os.path.join(ROOT, e["source"])
-    try:
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
-        return None
-    if digest != e["sha256"]:
-        return None
-    return e["bytes_per_launch_at_workload"]
+    return e["dram_over_algorithmic"] * bytes_per_launch
 
 
 # --------------------------------------------------------------- CPU (oracle)
@@ -292,7 +295,7 @@ def run_native(args):
     per_launch_bytes = top["bytes"] / max(top["launches"], 1)
     per_launch_ms = top["ms"] / max(top["launches"], 1)
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
-    traffic = measured_traffic(top_name)
+    traffic = measured_traffic(top_name, per_launch_bytes)
     roofline = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind + " (copy bandwidth)",
                 "launches_in_timed_region": top["launches"], "bytes_per_launch": per_launch_bytes,

@@ -91,22 +91,33 @@ __global__ void k_slice_len(int rows, int rpw, int nslices, const int32_t* __res
   slen[sl] = m;
 }
 
+// One warp per slice, the same lane mapping as the sweep: lane (w, r) reads
+// row r of each block of row w (the n lanes of a row cover the block's
+// contiguous span) and writes it column-major, so for a fixed column the
+// warp writes one contiguous run.
 template <int N, class TV>
-__global__ void k_slice_fill(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                             const double* __restrict__ val, const int32_t* __restrict__ sptr,
-                             int32_t* __restrict__ sci, TV* __restrict__ sv) {
-  constexpr int NN = N * N, RPW = 32 / N;
-  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t >= (size_t)rows * NN) return;
-  const int i = (int)(t / NN), e = (int)(t - (size_t)i * NN);
-  const int r = e / N, c = e - r * N, rw = i % RPW;
-  const int step0 = sptr[i / RPW];
-  for (int p = rp[i]; p < rp[i + 1]; ++p) {
-    const size_t step = (size_t)step0 + (p - rp[i]);
-    const double v = val[(size_t)p * NN + e];
-    if constexpr (std::is_same<TV, bf16>::value) sv[step * NN * RPW + (c * RPW + rw) * N + r] = __double2bfloat16(v);
-    else sv[step * NN * RPW + (c * RPW + rw) * N + r] = (TV)v;
-    if (e == 0) sci[step * RPW + rw] = ci[p];
+__global__ void k_slice_fill(int rows, int nslices, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const double* __restrict__ val, const int32_t* __restrict__ sptr, int32_t* __restrict__ sci,
+                             TV* __restrict__ sv) {
+  constexpr int NN = N * N, RPW = 32 / N, TILE = NN * RPW;
+  const int lane = threadIdx.x & 31;
+  const int w = lane / N, r = lane - w * N;
+  const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (sl >= nslices) return;
+  const int i = sl * RPW + w;
+  const bool active = w < RPW && i < rows;
+  const int p0 = active ? rp[i] : 0, len = active ? rp[i + 1] - p0 : 0;
+  const int t0 = sptr[sl];
+  for (int k = 0; k < len; ++k) {
+    const int p = p0 + k;
+    const double* a = val + (size_t)p * NN + r * N;
+    TV* tile = sv + (size_t)(t0 + k) * TILE;
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      if constexpr (std::is_same<TV, bf16>::value) tile[c * RPW * N + lane] = __double2bfloat16(a[c]);
+      else tile[c * RPW * N + lane] = (TV)a[c];
+    }
+    if (r == 0) sci[(size_t)(t0 + k) * RPW + w] = ci[p];
   }
 }
 
@@ -504,16 +515,16 @@ bcs_status build_slices(Solver* s, Level& L, int prec) {
   const size_t nv = (size_t)L.nsteps * rpw * n * n;
   return with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    const unsigned g = grid_for((size_t)rows * N * N, 256);
+    const unsigned g = grid_for((size_t)L.nslices * 32, 128);
     const double bytes = (double)L.A.nnz * N * N * (8 + (prec == BCS_PREC_FP32 ? 4 : 2));
     if (prec == BCS_PREC_FP32) {
       BCS_ALLOC(s, L.s32, nv);
-      BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, float>), g, 256, 0, rows, L.A.rp.p, L.A.ci.p, L.A.v.p,
-                 L.sptr.p, L.sci.p, L.s32.p);
+      BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, float>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
+                 L.A.v.p, L.sptr.p, L.sci.p, L.s32.p);
     } else {
       BCS_ALLOC(s, L.s16, nv);
-      BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, bf16>), g, 256, 0, rows, L.A.rp.p, L.A.ci.p, L.A.v.p,
-                 L.sptr.p, L.sci.p, L.s16.p);
+      BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, bf16>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
+                 L.A.v.p, L.sptr.p, L.sci.p, L.s16.p);
     }
     return BCS_OK;
   });

@@ -371,10 +371,17 @@ __global__ void k_cg(int nagg, int pass, const int32_t* __restrict__ mptr, const
 }
 
 // out[q] = sum over list[gptr[q] .. gptr[q+1]) of src[list[p]] (n*n blocks),
-// plain FP64 adds from +0 in list order. Each thread serves LS_OUT outputs
-// (elements t, t + T, ...) whose dependent load chains it interleaves, so
-// enough loads are in flight to cover HBM latency.
+// plain FP64 adds from +0 in list order. The first add 0 + v equals v except
+// that -0 becomes +0, so the sum starts from its first term with that sign
+// fix (integer operations) and only the remaining terms use the FP64 pipe.
+// Each thread serves LS_OUT outputs (elements t, t + T, ...) whose dependent
+// load chains it interleaves, so enough loads are in flight.
 constexpr int LS_OUT = 4;
+
+__device__ __forceinline__ double plus_zero(double v) {
+  const long long b = __double_as_longlong(v);
+  return b == (long long)0x8000000000000000ll ? 0.0 : v;  // 0 + v, without the add
+}
 
 template <int NN>
 __global__ void __launch_bounds__(256) k_list_sum(unsigned nout, const int32_t* __restrict__ gptr,
@@ -383,7 +390,7 @@ __global__ void __launch_bounds__(256) k_list_sum(unsigned nout, const int32_t* 
   const unsigned total = nout * NN;
   const unsigned T = gridDim.x * blockDim.x;
   for (unsigned base = blockIdx.x * blockDim.x + threadIdx.x; base < total; base += LS_OUT * T) {
-    unsigned q[LS_OUT], e[LS_OUT];
+    unsigned e[LS_OUT];
     int pb[LS_OUT], len[LS_OUT];
     double acc[LS_OUT];
     int maxlen = 0;
@@ -391,14 +398,20 @@ __global__ void __launch_bounds__(256) k_list_sum(unsigned nout, const int32_t* 
     for (int u = 0; u < LS_OUT; ++u) {
       const unsigned t = base + u * T;
       const bool ok = t < total;
-      q[u] = ok ? t / NN : 0;
-      e[u] = ok ? t - q[u] * NN : 0;
-      pb[u] = ok ? __ldg(gptr + q[u]) : 0;
-      len[u] = ok ? __ldg(gptr + q[u] + 1) - pb[u] : 0;
-      acc[u] = 0.0;
+      const unsigned q = ok ? t / NN : 0;
+      e[u] = ok ? t - q * NN : 0;
+      pb[u] = ok ? __ldg(gptr + q) : 0;
+      len[u] = ok ? __ldg(gptr + q + 1) - pb[u] : 0;
       maxlen = max(maxlen, len[u]);
     }
-    for (int o = 0; o < maxlen; ++o) {
+    {
+      int k[LS_OUT];
+#pragma unroll
+      for (int u = 0; u < LS_OUT; ++u) k[u] = len[u] > 0 ? __ldg(glist + pb[u]) : -1;
+#pragma unroll
+      for (int u = 0; u < LS_OUT; ++u) acc[u] = k[u] >= 0 ? plus_zero(__ldg(src + (size_t)k[u] * NN + e[u])) : 0.0;
+    }
+    for (int o = 1; o < maxlen; ++o) {
       int k[LS_OUT];
       double v[LS_OUT];
 #pragma unroll
