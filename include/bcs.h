@@ -55,7 +55,7 @@ typedef enum bcs_status {
   BCS_NOT_CONVERGED = 4,   /* maxiter reached above the tolerance */
   BCS_BREAKDOWN = 5,       /* NaN/Inf or a Krylov breakdown */
   BCS_SINGULAR_BLOCK = 6,  /* a diagonal block (or the coarse matrix) is singular */
-  BCS_TIMEOUT = 7,         /* a bounded device wait gave up */
+  BCS_TIMEOUT = 7,         /* bcs_server_wait: the request is still running after timeout_ms */
   BCS_REJECTED = 8,        /* serving: request does not fit the memory budget */
   BCS_ESTATE = 9           /* call out of order (e.g. solve before set_values) */
 } bcs_status;
@@ -87,6 +87,14 @@ typedef struct bcs_config {
   int coarse_sweeps;       /* else this many block-Jacobi sweeps there (8) */
   int precision;           /* AMG storage: BCS_PREC_FP64, BCS_PREC_FP32 (default), BCS_PREC_BF16 */
   int profile;             /* 1: time kernels with CUDA events (bcs_get_stats) */
+  int profile_kinds;       /* with profile = 1: bitmask of the kernel kinds to time (bit k:
+                              kind k of bcs_kernel_kind_name); 0 = every kind */
+  int slice_layout;        /* FP32 / BF16 level storage: 0 one lane per scalar row, 1 one thread
+                              per block row, -1 (default) timed per level at full setup and the
+                              faster kept; both give identical results */
+  int cycle_graph;         /* FP32 / BF16 V-cycle replayed as one CUDA graph: 1 on, 0 off,
+                              -1 (default) on up to 4,194,304 unknowns, where launch latency
+                              matters; never while profile = 1 (per-kernel events) */
 } bcs_config;
 
 typedef struct bcs_result {
@@ -231,11 +239,14 @@ BCS_API bcs_status bcs_server_destroy(bcs_server* srv);
 /* Copies the face addressing (HOST arrays) of a case with n x n blocks. */
 BCS_API bcs_status bcs_server_register_case(bcs_server* srv, int n, int32_t n_cells, int32_t n_faces,
                                             const int32_t* owner, const int32_t* neighbour, int* case_id);
-/* Queue a solve: HOST arrays diag[C][n][n], upper / lower[F][n][n],
- * b[C][n]; x[C][n] holds the initial guess and receives the solution. The
- * arrays must stay valid until the request completes. */
+/* Queue a solve: arrays diag[C][n][n], upper / lower[F][n][n], b[C][n];
+ * x[C][n] holds the initial guess and receives the solution. mem says where
+ * all five live: BCS_MEM_HOST, or BCS_MEM_DEVICE (memory of the device the
+ * server was created on, complete before this call: the request runs on the
+ * case's own stream). The arrays must stay valid until the request
+ * completes. */
 BCS_API bcs_status bcs_server_submit(bcs_server* srv, int case_id, const double* diag, const double* upper,
-                                    const double* lower, const double* b, double* x, int64_t* ticket);
+                                    const double* lower, const double* b, double* x, int mem, int64_t* ticket);
 /* Wait for a request (timeout_ms < 0: no limit); returns the request's
  * status (BCS_TIMEOUT when still running after timeout_ms, the ticket then
  * stays valid). res and latency_ms (submit -> completion) may be NULL. */

@@ -33,7 +33,8 @@ class bcs_config(ct.Structure):
         ("agg_passes", ct.c_int), ("jacobi_omega", ct.c_double), ("nu1", ct.c_int), ("nu2", ct.c_int),
         ("coarse_size", ct.c_int), ("max_levels", ct.c_int), ("max_coarsen_ratio", ct.c_double),
         ("p_omega", ct.c_double), ("coarse_dense_max", ct.c_int), ("coarse_sweeps", ct.c_int),
-        ("precision", ct.c_int), ("profile", ct.c_int),
+        ("precision", ct.c_int), ("profile", ct.c_int), ("profile_kinds", ct.c_int),
+        ("slice_layout", ct.c_int), ("cycle_graph", ct.c_int),
     ]
 
 
@@ -108,7 +109,8 @@ def lib():
             "bcs_server_destroy": (ct.c_int, [_vp]),
             "bcs_server_register_case": (ct.c_int, [_vp, ct.c_int, ct.c_int32, ct.c_int32, _vp, _vp,
                                                     ct.POINTER(ct.c_int)]),
-            "bcs_server_submit": (ct.c_int, [_vp, ct.c_int, _vp, _vp, _vp, _vp, _vp, ct.POINTER(ct.c_int64)]),
+            "bcs_server_submit": (ct.c_int, [_vp, ct.c_int, _vp, _vp, _vp, _vp, _vp, ct.c_int,
+                                             ct.POINTER(ct.c_int64)]),
             "bcs_server_wait": (ct.c_int, [_vp, ct.c_int64, ct.c_int, ct.POINTER(bcs_result),
                                            ct.POINTER(ct.c_double)]),
             "bcs_server_get_stats": (ct.c_int, [_vp, ct.POINTER(bcs_server_stats)]),
@@ -315,6 +317,12 @@ def bcs_kernel_kind_name(k):
     return lib().bcs_kernel_kind_name(k).decode()
 
 
+def kind_mask(*names):
+    """profile_kinds bitmask for the kernel kinds with these names."""
+    table = {bcs_kernel_kind_name(k): k for k in range(NUM_KERNEL_KINDS)}
+    return sum(1 << table[nm] for nm in names)
+
+
 def bcs_last_error(h):
     return lib().bcs_last_error(h).decode()
 
@@ -451,10 +459,11 @@ def bcs_server_register_case(h, n, n_cells, owner, neighbour):
 
 
 def bcs_server_submit(h, case_id, diag, upper, lower, b, x):
-    """Host arrays only; they must stay alive until the request completes."""
+    """numpy arrays (host) or CUDA tensors (device), all five alike; they must
+    stay alive until the request completes."""
     t = ct.c_int64()
-    _check(lib().bcs_server_submit(h, case_id, diag.ctypes.data, upper.ctypes.data, lower.ctypes.data,
-                                   b.ctypes.data, x.ctypes.data, ct.byref(t)))
+    ptrs, mem = _ptr_mem(diag, upper, lower, b, x)
+    _check(lib().bcs_server_submit(h, case_id, *ptrs, mem, ct.byref(t)))
     return t.value
 
 
@@ -502,9 +511,15 @@ class Server:
                                         system["neighbour"])
 
     def submit(self, case_id, system, x=None):
-        arrs = [np.ascontiguousarray(system[k], np.float64) for k in ("diag", "upper", "lower", "b")]
-        if x is None:
-            x = np.zeros_like(arrs[3])
+        """system: dict of numpy arrays or of CUDA tensors (diag, upper,
+        lower, b); x: initial guess of the same kind (zeros when None)."""
+        arrs = [system[k] for k in ("diag", "upper", "lower", "b")]
+        if isinstance(arrs[0], np.ndarray):
+            arrs = [np.ascontiguousarray(a, np.float64) for a in arrs]
+            if x is None:
+                x = np.zeros_like(arrs[3])
+        elif x is None:
+            x = arrs[3].new_zeros(arrs[3].shape)
         t = bcs_server_submit(self.h, case_id, *arrs, x)
         self._keep[t] = (arrs, x)
         return t
@@ -515,6 +530,9 @@ class Server:
             return st, res, lat, None
         arrs, x = self._keep.pop(ticket)
         return st, res, lat, x
+
+    def reset_stats(self):
+        _check(lib().bcs_server_reset_stats(self.h))
 
     def stats(self):
         return bcs_server_get_stats(self.h)

@@ -13,7 +13,8 @@ namespace bcs {
 const char* kind_name(int k) {
   static const char* names[K_NKINDS] = {"ldu_to_bsr", "spmv_fp64",   "jacobi_sweep", "residual",
                                         "transfer",   "coarse_solve", "blas1",       "setup_aggregation",
-                                        "setup_galerkin", "setup_inverse", "cast",   "scan_sort"};
+                                        "setup_galerkin", "setup_inverse", "cast",   "scan_sort",
+                                        "autotune"};
   return (k >= 0 && k < K_NKINDS) ? names[k] : "";
 }
 
@@ -36,7 +37,7 @@ void Alloc::put(void* p, size_t bytes) {
 }
 
 void Solver::pre(int kind) {
-  if (!cfg.profile) return;
+  if (!cfg.profile || (cfg.profile_kinds && !(cfg.profile_kinds & (1 << kind)))) return;
   if (event_next + 2 > event_pool.size()) {
     for (int q = 0; q < 64; ++q) {
       cudaEvent_t e;
@@ -101,6 +102,8 @@ bcs_status check_config(const bcs_config* c) {
   if (c->coarse_size < 1 || c->max_levels < 1 || c->coarse_sweeps < 1) return BCS_EINVAL;
   if (c->coarse_dense_max < 1 || c->coarse_dense_max > 8192) return BCS_EINVAL;
   if (c->precision < BCS_PREC_FP64 || c->precision > BCS_PREC_BF16) return BCS_EINVAL;
+  if (c->cycle_graph < -1 || c->cycle_graph > 1) return BCS_EINVAL;
+  if (c->slice_layout < -1 || c->slice_layout > 1) return BCS_EINVAL;
   if (!(c->max_coarsen_ratio > 0.0) || !(c->p_omega > 0.0) || !(c->jacobi_omega > 0.0)) return BCS_EINVAL;
   return BCS_OK;
 }
@@ -111,7 +114,7 @@ bool same_hierarchy_options(const bcs_config& a, const bcs_config& b) {
          a.coarse_size == b.coarse_size && a.max_levels == b.max_levels &&
          a.max_coarsen_ratio == b.max_coarsen_ratio && a.p_omega == b.p_omega &&
          a.coarse_dense_max == b.coarse_dense_max && a.coarse_sweeps == b.coarse_sweeps &&
-         a.precision == b.precision;
+         a.precision == b.precision && a.slice_layout == b.slice_layout;
 }
 
 // Copy a host array into a device staging buffer (or pass a device pointer).
@@ -165,6 +168,9 @@ bcs_status bcs_config_default(bcs_config* c) {
   c->coarse_sweeps = 8;
   c->precision = BCS_PREC_FP32;
   c->profile = 0;
+  c->profile_kinds = 0;
+  c->slice_layout = -1;
+  c->cycle_graph = -1;
   return BCS_OK;
 }
 
@@ -214,6 +220,8 @@ bcs_status bcs_destroy(bcs_solver* h) {
   if (!h) return BCS_OK;
   Solver* s = &h->impl;
   cudaStreamSynchronize(s->stream);
+  s->drop_graph();
+  if (s->gstream) cudaStreamDestroy(s->gstream);
   for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
   if (s->hscal) cudaFreeHost(s->hscal);
   cudaStream_t st = s->stream;

@@ -12,33 +12,35 @@ constexpr int RED_THREADS = 256;
 constexpr int MD_CHUNK = 8;      // vectors per multidot block row
 
 // partial[q * RED_BLOCKS + block] = sum over this block's share of i of
-// V[q][i] * w[i], for q in this chunk.
-__global__ void __launch_bounds__(RED_THREADS) k_multidot(const double* __restrict__ V, size_t ldv, int k,
+// V[q][i] * w[i], for q = q_base + blockIdx.y * K + (0 .. K-1). K is a
+// compile-time count: FP64 FMAs are scarce on this part, a predicated-off FMA
+// still takes its issue slot on the FP64 pipe, and small K keeps registers
+// (and so occupancy) low.
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS) k_multidot(const double* __restrict__ V, size_t ldv, int q_base,
                                                           const double* __restrict__ w, size_t N,
                                                           double* __restrict__ partial) {
-  __shared__ double sm[MD_CHUNK][RED_THREADS / 32];
-  const int q0 = blockIdx.y * MD_CHUNK;
-  const int nq = min(MD_CHUNK, k - q0);
-  double acc[MD_CHUNK];
+  __shared__ double sm[K][RED_THREADS / 32];
+  const int q0 = q_base + blockIdx.y * K;
+  double acc[K];
 #pragma unroll
-  for (int q = 0; q < MD_CHUNK; ++q) acc[q] = 0.0;
+  for (int q = 0; q < K; ++q) acc[q] = 0.0;
   const size_t stride = (size_t)RED_BLOCKS * RED_THREADS;
   for (size_t i = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; i < N; i += stride) {
     const double wi = __ldg(w + i);
 #pragma unroll
-    for (int q = 0; q < MD_CHUNK; ++q)
-      if (q < nq) acc[q] = fma(__ldg(V + (size_t)(q0 + q) * ldv + i), wi, acc[q]);
+    for (int q = 0; q < K; ++q) acc[q] = fma(__ldg(V + (size_t)(q0 + q) * ldv + i), wi, acc[q]);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < MD_CHUNK; ++q) {
+  for (int q = 0; q < K; ++q) {
     double v = acc[q];
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
     if (lane == 0) sm[q][warp] = v;
   }
   __syncthreads();
-  if (threadIdx.x < nq) {
+  if (threadIdx.x < K) {
     double v = 0.0;
     for (int wv = 0; wv < RED_THREADS / 32; ++wv) v += sm[threadIdx.x][wv];
     partial[(size_t)(q0 + threadIdx.x) * RED_BLOCKS + blockIdx.x] = v;
@@ -62,6 +64,14 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_partials(const double* _
     for (int wv = 0; wv < RED_THREADS / 32; ++wv) t += sm[wv];
     out[q] = t;
   }
+}
+
+// *flag = 1.0 if some x[i] != 0 (flag cleared to 0.0 beforehand).
+__global__ void k_any_nonzero(const double* __restrict__ x, size_t N, double* __restrict__ flag) {
+  bool nz = false;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    nz |= x[i] != 0.0;
+  if (__syncthreads_or(nz) && threadIdx.x == 0) *flag = 1.0;
 }
 
 // w[i] -= sum_q h[q] V[q][i]
@@ -117,18 +127,35 @@ unsigned vgrid(size_t N) {
 
 bcs_status multidot(Solver* s, const double* V, size_t ldv, int k, const double* w, size_t N, int slot) {
   if (k <= 0) return BCS_OK;
-  const int chunks = (k + MD_CHUNK - 1) / MD_CHUNK;
   BCS_ALLOC(s, s->red, (size_t)72 * RED_BLOCKS);
   if (k > 72) return s->fail(BCS_EINVAL, "too many vectors in one multidot");
-  const dim3 grid(RED_BLOCKS, chunks);
-  BCS_LAUNCH(s, K_BLAS, 8.0 * N * (k + chunks), 2.0 * N * k, k_multidot, grid, RED_THREADS, 0, V, ldv, k, w, N,
-             s->red.p);
+  const int full = k / MD_CHUNK, rem = k % MD_CHUNK;
+  if (full > 0)
+    BCS_LAUNCH(s, K_BLAS, 8.0 * N * (full * MD_CHUNK + full), 2.0 * N * full * MD_CHUNK, k_multidot<MD_CHUNK>,
+               dim3(RED_BLOCKS, full), RED_THREADS, 0, V, ldv, 0, w, N, s->red.p);
+  const int qb = full * MD_CHUNK;
+  switch (rem) {
+#define BCS_MD_TAIL(R)                                                                                   \
+  case R:                                                                                                \
+    BCS_LAUNCH(s, K_BLAS, 8.0 * N * (R + 1), 2.0 * N * R, k_multidot<R>, dim3(RED_BLOCKS, 1), RED_THREADS, 0, \
+               V, ldv, qb, w, N, s->red.p);                                                              \
+    break;
+    BCS_MD_TAIL(1) BCS_MD_TAIL(2) BCS_MD_TAIL(3) BCS_MD_TAIL(4) BCS_MD_TAIL(5) BCS_MD_TAIL(6) BCS_MD_TAIL(7)
+#undef BCS_MD_TAIL
+    default: break;
+  }
   BCS_LAUNCH(s, K_BLAS, 8.0 * k * RED_BLOCKS, 0, k_reduce_partials, k, RED_THREADS, 0, s->red.p, s->scal.p + slot);
   return BCS_OK;
 }
 
 bcs_status dot(Solver* s, const double* x, const double* y, size_t N, int slot) {
   return multidot(s, x, N, 1, y, N, slot);
+}
+
+bcs_status any_nonzero(Solver* s, const double* x, size_t N, int slot) {
+  BCS_CU(s, cudaMemsetAsync(s->scal.p + slot, 0, sizeof(double), s->stream));
+  BCS_LAUNCH(s, K_BLAS, 8.0 * N, 0, k_any_nonzero, RED_BLOCKS, RED_THREADS, 0, x, N, s->scal.p + slot);
+  return BCS_OK;
 }
 
 bcs_status fetch_scalars(Solver* s, int count) {

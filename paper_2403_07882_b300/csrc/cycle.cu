@@ -13,6 +13,10 @@
 // first from x = 0 is x = w D^-1 b), residual, restriction R = P^T,
 // recursion, prolongation-correction, nu2 sweeps; the coarsest level applies
 // its dense FP64 inverse (or smoother sweeps when too large for one).
+#include <array>
+#include <map>
+#include <mutex>
+
 #include "internal.h"
 
 namespace bcs {
@@ -194,6 +198,104 @@ __global__ void __launch_bounds__(128) k_sell(int rows, int nslices, const int32
   if (active) y[o] = xo + omega * tt;
 }
 
+// ---- thread-per-block-row layout (smap = 1) ---------------------------------
+// Slices of 32 block rows, one warp each, one thread per block row. Step t of
+// a slice holds the t-th block of each of its rows, element-major: value
+// (row w, r, c) at t * n*n*32 + (r * n + c) * 32 + w, so for a fixed element
+// the warp reads 128 (FP32) or 64 (BF16) contiguous bytes; sci[t * 32 + w].
+// A thread keeps n*n value loads of one step in flight (one lane-per-row warp
+// of the other layout moves n*n*floor(32/n) values per step).
+template <int N, class TV>
+__global__ void k_tpr_fill(int rows, int nslices, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ val, const int32_t* __restrict__ sptr,
+                           int32_t* __restrict__ sci, TV* __restrict__ sv) {
+  constexpr int NN = N * N, TILE = NN * 32;
+  const int lane = threadIdx.x & 31;
+  const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (sl >= nslices) return;
+  const int i = sl * 32 + lane;
+  const int p0 = i < rows ? rp[i] : 0, len = i < rows ? rp[i + 1] - p0 : 0;
+  const int t0 = sptr[sl];
+  for (int k = 0; k < len; ++k) {
+    const double* a = val + (size_t)(p0 + k) * NN;
+    TV* tile = sv + (size_t)(t0 + k) * TILE + lane;
+#pragma unroll
+    for (int e = 0; e < NN; ++e) {
+      if constexpr (std::is_same<TV, bf16>::value) tile[e * 32] = __double2bfloat16(a[e]);
+      else tile[e * 32] = (TV)a[e];
+    }
+    sci[(size_t)(t0 + k) * 32 + lane] = ci[p0 + k];
+  }
+}
+
+// JACOBI: y = x + omega D^-1 (b - A x); otherwise y = b - A x. Per scalar row
+// the fma sequence is the one of k_sell (blocks in row order, columns
+// ascending; the epilogue in column order), so both layouts give identical
+// results.
+template <int N, class TV, bool JACOBI>
+__global__ void __launch_bounds__(128) k_tpr(int rows, int nslices, const int32_t* __restrict__ rp,
+                                             const int32_t* __restrict__ sptr, const int32_t* __restrict__ sci,
+                                             const TV* __restrict__ sv, const float* __restrict__ dinv,
+                                             const float* __restrict__ x, const float* __restrict__ b,
+                                             float* __restrict__ y, float omega) {
+  constexpr int NN = N * N, TILE = NN * 32;
+  const int lane = threadIdx.x & 31;
+  const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (sl >= nslices) return;
+  const int i = sl * 32 + lane;
+  if (i >= rows) return;
+  const int len = __ldg(rp + i + 1) - __ldg(rp + i);
+  const int t0 = __ldg(sptr + sl);
+  const size_t o = (size_t)i * N;
+  float acc[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) acc[r] = 0.f;
+  // software pipeline: the next step's column index and values are loaded
+  // while the current step's x block arrives and is used
+  float a[NN];
+  int j = 0;
+  if (len > 0) {
+    j = __ldg(sci + (size_t)t0 * 32 + lane);
+#pragma unroll
+    for (int e = 0; e < NN; ++e) a[e] = ldsv(sv + (size_t)t0 * TILE + lane + e * 32);
+  }
+  for (int k = 0; k < len; ++k) {
+    float xv[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) xv[c] = __ldg(x + (size_t)j * N + c);
+    float an[NN];
+    int jn = 0;
+    if (k + 1 < len) {
+      jn = __ldg(sci + (size_t)(t0 + k + 1) * 32 + lane);
+#pragma unroll
+      for (int e = 0; e < NN; ++e) an[e] = ldsv(sv + (size_t)(t0 + k + 1) * TILE + lane + e * 32);
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+      for (int c = 0; c < N; ++c) acc[r] = fmaf(a[r * N + c], xv[c], acc[r]);
+#pragma unroll
+    for (int e = 0; e < NN; ++e) a[e] = an[e];
+    j = jn;
+  }
+  if (!JACOBI) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) y[o + r] = __ldg(b + o + r) - acc[r];
+    return;
+  }
+  float res[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) res[r] = __ldg(b + o + r) - acc[r];
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const float xo = x[o + r];
+    float tt = 0.f;
+#pragma unroll
+    for (int c = 0; c < N; ++c) tt = fmaf(__ldg(dinv + (o + r) * N + c), res[c], tt);
+    y[o + r] = xo + omega * tt;
+  }
+}
+
 // y = x + omega D^-1 (b - A x)
 template <int N, class AT, class TV, class TD, class TC>
 __global__ void __launch_bounds__(128) k_jacobi(int rows, const int32_t* __restrict__ rp,
@@ -364,9 +466,14 @@ struct Cycle {
     const double bytes = (double)L.A.nnz * (N * N * sizeof(TV) + 4) + 4.0 * (rows + 1) +
                          (double)rows * N * (N * sizeof(TD) + 3 * sizeof(TC));
     if constexpr (std::is_same<TC, float>::value) {
-      BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_sell<N, TV, true>),
-                 grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.sptr.p, L.sci.p,
-                 smat(L), dinv(L), x, b, y, om);
+      if (L.smap == 1)
+        BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_tpr<N, TV, true>),
+                   grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.sptr.p, L.sci.p,
+                   smat(L), dinv(L), x, b, y, om);
+      else
+        BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_sell<N, TV, true>),
+                   grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.sptr.p, L.sci.p,
+                   smat(L), dinv(L), x, b, y, om);
     } else {
       BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_jacobi<N, AT, TV, TD, TC>),
                  rows_grid(rows, N), 128, 0, rows, L.A.rp.p, L.A.ci.p, mat(L), dinv(L), x, b, y, om);
@@ -379,9 +486,14 @@ struct Cycle {
     const double bytes = (double)L.A.nnz * (N * N * sizeof(TV) + 4) + 4.0 * (rows + 1) +
                          (double)rows * N * 3 * sizeof(TC);
     if constexpr (std::is_same<TC, float>::value) {
-      BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_sell<N, TV, false>),
-                 grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.sptr.p, L.sci.p,
-                 smat(L), (const float*)nullptr, x, b, r, 0.f);
+      if (L.smap == 1)
+        BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_tpr<N, TV, false>),
+                   grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.sptr.p, L.sci.p,
+                   smat(L), (const float*)nullptr, x, b, r, 0.f);
+      else
+        BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_sell<N, TV, false>),
+                   grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.sptr.p, L.sci.p,
+                   smat(L), (const float*)nullptr, x, b, r, 0.f);
     } else {
       BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_rows<N, AT, TV, TC, TC, M_RESID>),
                  rows_grid(rows, N), 128, 0, rows, L.A.rp.p, L.A.ci.p, mat(L), x, r, b);
@@ -494,11 +606,14 @@ bcs_status run_cycle(Solver* s, const TC* b, TC* x) {
 
 }  // namespace
 
-// Sliced copy of level L's operator in the cycle precision (structure once
-// per hierarchy, values at every setup / resetup).
-bcs_status build_slices(Solver* s, Level& L, int prec) {
-  const int n = s->n, rows = L.A.rows, rpw = 32 / n;
-  if (L.nslices == 0) {
+// Sliced copy of level L's operator in layout `map` and the cycle precision
+// (structure once per hierarchy and layout, values at every setup / resetup).
+bcs_status fill_layout(Solver* s, Level& L, int prec, int map) {
+  const int n = s->n, rows = L.A.rows, rpw = map == 1 ? 32 : 32 / n;
+  if (L.nslices == 0 || L.smap != map) {
+    L.sci.release();
+    L.s32.release();
+    L.s16.release();
     const int ns = (rows + rpw - 1) / rpw;
     DBuf<int32_t> slen;
     BCS_ALLOC(s, slen, ns);
@@ -510,6 +625,7 @@ bcs_status build_slices(Solver* s, Level& L, int prec) {
     BCS_CU(s, cudaStreamSynchronize(s->stream));
     L.nslices = ns;
     L.nsteps = steps;
+    L.smap = map;
     BCS_ALLOC(s, L.sci, (size_t)steps * rpw);
   }
   const size_t nv = (size_t)L.nsteps * rpw * n * n;
@@ -519,20 +635,121 @@ bcs_status build_slices(Solver* s, Level& L, int prec) {
     const double bytes = (double)L.A.nnz * N * N * (8 + (prec == BCS_PREC_FP32 ? 4 : 2));
     if (prec == BCS_PREC_FP32) {
       BCS_ALLOC(s, L.s32, nv);
-      BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, float>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
-                 L.A.v.p, L.sptr.p, L.sci.p, L.s32.p);
+      if (map == 1)
+        BCS_LAUNCH(s, K_CAST, bytes, 0, (k_tpr_fill<N, float>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
+                   L.A.v.p, L.sptr.p, L.sci.p, L.s32.p);
+      else
+        BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, float>), g, 128, 0, rows, L.nslices, L.A.rp.p,
+                   L.A.ci.p, L.A.v.p, L.sptr.p, L.sci.p, L.s32.p);
     } else {
       BCS_ALLOC(s, L.s16, nv);
-      BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, bf16>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
-                 L.A.v.p, L.sptr.p, L.sci.p, L.s16.p);
+      if (map == 1)
+        BCS_LAUNCH(s, K_CAST, bytes, 0, (k_tpr_fill<N, bf16>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
+                   L.A.v.p, L.sptr.p, L.sci.p, L.s16.p);
+      else
+        BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, bf16>), g, 128, 0, rows, L.nslices, L.A.rp.p,
+                   L.A.ci.p, L.A.v.p, L.sptr.p, L.sci.p, L.s16.p);
     }
     return BCS_OK;
   });
 }
 
+// ---- layout autotuner --------------------------------------------------------
+// For a level of at least TUNE_MIN_ROWS block rows, both layouts are built and
+// one smoother sweep of each is timed (CUDA events, best of TUNE_REPS after a
+// warm-up launch); the faster layout is kept. Decisions are cached per
+// process by (n, precision, log2 rows, blocks per row x 4), so later setups of
+// similar levels skip the timing. Both layouts give identical results.
+constexpr int TUNE_MIN_ROWS = 4096;
+constexpr int TUNE_REPS = 3;
+
+std::mutex g_tune_mu;
+std::map<std::array<int, 4>, int> g_tune_cache;
+
+template <int N, class TV>
+bcs_status time_sweep(Solver* s, const Level& L, cudaEvent_t e0, cudaEvent_t e1, float* best) {
+  const TV* sv;
+  if constexpr (std::is_same<TV, bf16>::value) sv = L.s16.p;
+  else sv = L.s32.p;
+  const float* x = (const float*)L.vx.p;
+  const float* b = (const float*)L.vb.p;
+  float* y = (float*)L.vt.p;
+  const unsigned g = grid_for((size_t)L.nslices * 32, 128);
+  *best = 1e30f;
+  for (int rep = 0; rep <= TUNE_REPS; ++rep) {
+    BCS_CU(s, cudaEventRecord(e0, s->stream));
+    if (L.smap == 1)
+      BCS_LAUNCH(s, K_TUNE, 0, 0, (k_tpr<N, TV, true>), g, 128, 0, L.A.rows, L.nslices, L.A.rp.p, L.sptr.p,
+                 L.sci.p, sv, L.dinv32.p, x, b, y, 0.8f);
+    else
+      BCS_LAUNCH(s, K_TUNE, 0, 0, (k_sell<N, TV, true>), g, 128, 0, L.A.rows, L.nslices, L.A.rp.p, L.sptr.p,
+                 L.sci.p, sv, L.dinv32.p, x, b, y, 0.8f);
+    BCS_CU(s, cudaEventRecord(e1, s->stream));
+    BCS_CU(s, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    BCS_CU(s, cudaEventElapsedTime(&ms, e0, e1));
+    if (rep > 0 && ms < *best) *best = ms;
+  }
+  return BCS_OK;
+}
+
+bcs_status choose_layout(Solver* s, Level& L, int prec, int* map) {
+  *map = 0;
+  const int rows = L.A.rows;
+  if (rows < TUNE_MIN_ROWS) return BCS_OK;
+  int lg = 0;
+  while ((1 << (lg + 1)) <= rows) ++lg;
+  const std::array<int, 4> key{s->n, prec, lg, (int)(4.0 * L.A.nnz / rows + 0.5)};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      *map = it->second;
+      return BCS_OK;
+    }
+  }
+  const size_t N = (size_t)rows * s->n;
+  BCS_CU(s, cudaMemsetAsync(L.vx.p, 0, N * sizeof(float), s->stream));
+  BCS_CU(s, cudaMemsetAsync(L.vb.p, 0, N * sizeof(float), s->stream));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BCS_CU(s, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return s->fail(BCS_ECUDA, "cudaEventCreate failed");
+  }
+  float t[2] = {0.f, 0.f};
+  bcs_status st = BCS_OK;
+  for (int m = 0; m < 2 && st == BCS_OK; ++m) {
+    st = fill_layout(s, L, prec, m);
+    if (st == BCS_OK)
+      st = with_n(s->n, [&](auto NC) -> bcs_status {
+        constexpr int NN = decltype(NC)::value;
+        return prec == BCS_PREC_FP32 ? time_sweep<NN, float>(s, L, e0, e1, &t[m])
+                                     : time_sweep<NN, bf16>(s, L, e0, e1, &t[m]);
+      });
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  BCS_OKR(st);
+  *map = t[1] < t[0] ? 1 : 0;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = *map;
+  return BCS_OK;
+}
+
+bcs_status build_slices(Solver* s, Level& L, int prec) {
+  int map = L.smap;
+  if (map < 0) {
+    if (s->setup_cfg.slice_layout >= 0) map = s->setup_cfg.slice_layout;
+    else BCS_OKR(choose_layout(s, L, prec, &map));
+  }
+  return fill_layout(s, L, prec, map);
+}
+
 // Cycle vectors and storage copies of the hierarchy in the configured
 // precision (after every setup / resetup).
 bcs_status cycle_prepare(Solver* s) {
+  s->drop_graph();
   const int prec = s->setup_cfg.precision;
   const size_t vsz = prec == BCS_PREC_FP64 ? sizeof(double) : sizeof(float);
   const int n = s->n, nn = n * n;
@@ -565,20 +782,93 @@ bcs_status cycle_prepare(Solver* s) {
   return BCS_OK;
 }
 
+namespace {
+
+constexpr size_t GRAPH_AUTO_MAX_UNKNOWNS = size_t(1) << 22;
+
+bool use_graph(const Solver* s) {
+  if (s->cfg.profile || s->setup_cfg.precision == BCS_PREC_FP64) return false;
+  if (s->cfg.cycle_graph >= 0) return s->cfg.cycle_graph == 1;
+  return (size_t)s->lv[0].A.rows * s->n <= GRAPH_AUTO_MAX_UNKNOWNS;
+}
+
+template <class TV>
+bcs_status run_cycle_f(Solver* s, const float* b, float* x) {
+  return run_cycle<TV, float, float, float>(s, b, x);
+}
+
+// Replays the cycle lv[0].vb -> lv[0].vx as one CUDA graph, capturing it on
+// first use after a setup. The captured launches are counted in the solver's
+// statistics at every replay, as if launched one by one.
+template <class TV>
+bcs_status graph_cycle(Solver* s) {
+  Level& L0 = s->lv[0];
+  if (!s->cyc_exec) {
+    long long kl[BCS_NUM_KERNEL_KINDS];
+    double kb[BCS_NUM_KERNEL_KINDS], kf[BCS_NUM_KERNEL_KINDS];
+    const long long l0 = s->launches;
+    for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {
+      kl[k] = s->kind_launches[k];
+      kb[k] = s->kind_bytes[k];
+      kf[k] = s->kind_flops[k];
+    }
+    // capture on a private stream (the solver's may be the legacy default
+    // stream, which cannot be captured); the graph is then launched on the
+    // solver's stream
+    if (!s->gstream) BCS_CU(s, cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
+    const cudaStream_t own = s->stream;
+    BCS_CU(s, cudaStreamBeginCapture(s->gstream, cudaStreamCaptureModeThreadLocal));
+    s->stream = s->gstream;
+    const bcs_status st = run_cycle_f<TV>(s, (const float*)L0.vb.p, (float*)L0.vx.p);
+    s->stream = own;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s->gstream, &g);
+    // the capture ran nothing: take its launches back out of the statistics
+    s->launches = l0;
+    for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {
+      s->cyc_kind_launches[k] = s->kind_launches[k] - kl[k];
+      s->cyc_kind_bytes[k] = s->kind_bytes[k] - kb[k];
+      s->cyc_kind_flops[k] = s->kind_flops[k] - kf[k];
+      s->kind_launches[k] = kl[k];
+      s->kind_bytes[k] = kb[k];
+      s->kind_flops[k] = kf[k];
+    }
+    if (st != BCS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (ce != cudaSuccess) return s->fail(BCS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&s->cyc_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      s->cyc_exec = nullptr;
+      return s->fail(BCS_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    }
+  }
+  BCS_CU(s, cudaGraphLaunch(s->cyc_exec, s->stream));
+  for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {
+    s->launches += s->cyc_kind_launches[k];
+    s->kind_launches[k] += s->cyc_kind_launches[k];
+    s->kind_bytes[k] += s->cyc_kind_bytes[k];
+    s->kind_flops[k] += s->cyc_kind_flops[k];
+  }
+  return BCS_OK;
+}
+
+}  // namespace
+
 // z = M^{-1} v in the cycle precision; v is FP64 (a Krylov vector).
 bcs_status precond_apply(Solver* s, const double* v, void* z) {
   Level& L0 = s->lv[0];
   const size_t N = (size_t)L0.A.rows * s->n;
-  switch (s->setup_cfg.precision) {
-    case BCS_PREC_FP64:
-      return run_cycle<double, double, double, double>(s, v, (double*)z);
-    case BCS_PREC_FP32:
-      BCS_OKR(cast_vec<double, float>(s, v, (float*)L0.vb.p, N));
-      return run_cycle<float, float, float, float>(s, (const float*)L0.vb.p, (float*)z);
-    default:
-      BCS_OKR(cast_vec<double, float>(s, v, (float*)L0.vb.p, N));
-      return run_cycle<bf16, float, float, float>(s, (const float*)L0.vb.p, (float*)z);
-  }
+  if (s->setup_cfg.precision == BCS_PREC_FP64) return run_cycle<double, double, double, double>(s, v, (double*)z);
+  BCS_OKR(cast_vec<double, float>(s, v, (float*)L0.vb.p, N));
+  if (!use_graph(s))
+    return s->setup_cfg.precision == BCS_PREC_FP32 ? run_cycle_f<float>(s, (const float*)L0.vb.p, (float*)z)
+                                                   : run_cycle_f<bf16>(s, (const float*)L0.vb.p, (float*)z);
+  BCS_OKR(s->setup_cfg.precision == BCS_PREC_FP32 ? graph_cycle<float>(s) : graph_cycle<bf16>(s));
+  BCS_CU(s, cudaMemcpyAsync(z, L0.vx.p, N * sizeof(float), cudaMemcpyDeviceToDevice, s->stream));
+  return BCS_OK;
 }
 
 // Block-Jacobi preconditioner (one undamped block solve): z = D^-1 v.

@@ -65,6 +65,9 @@ __global__ void k_sort_rows(int C, const int32_t* __restrict__ rp, int32_t* __re
                             int32_t* __restrict__ pos_up, int32_t* __restrict__ pos_lo,
                             int32_t* __restrict__ err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // longest row -> err[2] (one atomic per warp)
+  const int m = __reduce_max_sync(0xffffffffu, i < C ? rp[i + 1] - rp[i] : 0);
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(err + 2, m);
   if (i >= C) return;
   const int b = rp[i], e = rp[i + 1];
   for (int p = b + 1; p < e; ++p) {
@@ -107,7 +110,10 @@ __global__ void k_gather_values(size_t total, const int32_t* __restrict__ src,
 bcs_status build_structure(Solver* s, const int32_t* owner, const int32_t* nb) {
   const int C = s->C, F = s->F;
   const size_t nnz = (size_t)C + 2 * (size_t)F;
-  if (nnz > (size_t)INT32_MAX / 64) return s->fail(BCS_EINVAL, "too many blocks for int32 indexing");
+  // block counts are int32 throughout; element offsets are computed in 64
+  // bits, but keep every value array's element count in int32 range too
+  if (nnz * (size_t)s->n * s->n > (size_t)INT32_MAX)
+    return s->fail(BCS_EINVAL, "too many blocks for int32 indexing");
   s->nnz = (int)nnz;
   s->lv.clear();
   s->lv.emplace_back();
@@ -141,9 +147,11 @@ bcs_status build_structure(Solver* s, const int32_t* owner, const int32_t* nb) {
                A.ci.p, s->src.p, cursor.p);
   BCS_LAUNCH(s, K_CONVERT, 16.0 * nnz, 0, k_sort_rows, grid_for(C, 128), 128, 0, C, A.rp.p, A.ci.p,
              s->src.p, s->pos_diag.p, s->pos_up.p, s->pos_lo.p, s->flag.p);
-  BCS_CU(s, cudaMemcpyAsync(&h, s->flag.p, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+  int32_t hf[3] = {0, 0, 0};
+  BCS_CU(s, cudaMemcpyAsync(hf, s->flag.p, sizeof(hf), cudaMemcpyDeviceToHost, s->stream));
   BCS_CU(s, cudaStreamSynchronize(s->stream));
-  if (h & 2) return s->fail(BCS_EINVAL, "face addressing: a face (cell pair) is repeated");
+  if (hf[0] & 2) return s->fail(BCS_EINVAL, "face addressing: a face (cell pair) is repeated");
+  A.maxrow = hf[2];
   return BCS_OK;
 }
 

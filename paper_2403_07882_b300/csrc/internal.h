@@ -32,7 +32,8 @@ enum Kind {
   K_SETUP_INV = 9,  // block inverses, coarse inverse
   K_CAST = 10,      // precision casts
   K_MISC = 11,      // scans, sorts
-  K_NKINDS = 12
+  K_TUNE = 12,      // layout autotuning launches
+  K_NKINDS = 13
 };
 const char* kind_name(int k);
 
@@ -88,6 +89,7 @@ struct DBuf {
 // Block-CSR matrix on the device; values FP64 (setup precision).
 struct Bsr {
   int rows = 0, cols = 0, nnz = 0;
+  int maxrow = -1;  // longest row (blocks), -1 when not known
   DBuf<int32_t> rp, ci;
   DBuf<double> v;
 };
@@ -108,9 +110,13 @@ struct Level {
   DBuf<bf16> P16, R16;
   double omega_p = 0.0;
   int coarse_kind = -1;      // -1 not coarsest, 0 dense inverse, 1 sweeps
-  // sliced copy of A for the FP32 / BF16 cycle: slices of floor(32/n) block
+  // sliced copy of A for the FP32 / BF16 cycle: slices of consecutive block
   // rows; slice s covers steps sptr[s] .. sptr[s+1]; step t holds one block per
-  // row (padding past a row's end), column-major inside the step
+  // row (padding past a row's end)
+  // layout (smap): 0 = one lane per scalar row, floor(32/n) block rows per
+  // warp; 1 = one thread per block row, 32 block rows per warp; -1 = not
+  // chosen yet (picked by the layout autotuner at full setup)
+  int smap = -1;
   int nslices = 0, nsteps = 0;
   DBuf<int32_t> sptr, sci;
   DBuf<float> s32;
@@ -167,6 +173,16 @@ struct Solver {
   std::vector<cudaEvent_t> event_pool;
   size_t event_next = 0;
   double last_setup_ms = 0.0;
+  // V-cycle captured as a CUDA graph (FP32 / BF16 cycle): input lv[0].vb,
+  // output lv[0].vx; dropped at every setup / resetup and on destroy
+  cudaGraphExec_t cyc_exec = nullptr;
+  cudaStream_t gstream = nullptr;  // private stream the graph is captured on
+  long long cyc_kind_launches[BCS_NUM_KERNEL_KINDS] = {};
+  double cyc_kind_bytes[BCS_NUM_KERNEL_KINDS] = {}, cyc_kind_flops[BCS_NUM_KERNEL_KINDS] = {};
+  void drop_graph() {
+    if (cyc_exec) cudaGraphExecDestroy(cyc_exec);
+    cyc_exec = nullptr;
+  }
 
   bcs_status fail(bcs_status st, const std::string& m) {
     err = m;
@@ -238,6 +254,8 @@ bcs_status exclusive_scan(Solver* s, const int32_t* in, int32_t* out, int n);
 // segment starts with its sorted unique keys. max_len bounds the segments.
 bcs_status segmented_sort_unique(Solver* s, const int32_t* seg_ptr, int32_t* keys,
                                  int32_t* count, int rows, int max_len);
+// Ascending sort of every segment of 64-bit keys (duplicates kept).
+bcs_status segmented_sort64(Solver* s, const int32_t* seg_ptr, uint64_t* keys, int rows, int max_len);
 
 // -------------------------------------------------------------------- blas.cu
 // Deterministic FP64 reductions into s->scal[slot...].
@@ -245,6 +263,8 @@ bcs_status dot(Solver* s, const double* x, const double* y, size_t N, int slot);
 bcs_status multidot(Solver* s, const double* V, size_t ldv, int k, const double* w, size_t N,
                     int slot);
 bcs_status fetch_scalars(Solver* s, int count);  // scal[0..count) -> hscal, synchronises
+// scal[slot] = 1.0 if any x[i] != 0, else 0.0 (no sync)
+bcs_status any_nonzero(Solver* s, const double* x, size_t N, int slot);
 bcs_status axpby(Solver* s, double a, const double* x, double b, double* y, size_t N);
 bcs_status scale_copy(Solver* s, double a, const double* x, double* y, size_t N);
 bcs_status gs_update(Solver* s, const double* V, size_t ldv, int k, const double* hdev, double* w,

@@ -27,6 +27,7 @@ namespace {
 constexpr int SLOT_A = 0;     // first Gram-Schmidt pass
 constexpr int SLOT_B = 72;    // second pass
 constexpr int SLOT_N = 144;   // norms
+constexpr int SLOT_X = 145;   // nonzero flag of the initial guess
 
 size_t zbytes(const Solver* s) { return cycle_is_float(s) ? sizeof(float) : sizeof(double); }
 
@@ -69,6 +70,21 @@ bcs_status true_residual(Solver* s, const double* b, const double* x, double* r,
   return norm(s, r, N, rn);
 }
 
+// ||b|| and the initial residual r = b - A x, ||r||. When x is exactly zero
+// the product is skipped: b - A 0 = b element by element, so r is a copy of b
+// and ||r|| = ||b|| (the same reduction over the same values).
+bcs_status initial_residual(Solver* s, const double* b, const double* x, double* r, size_t N, double* bnorm,
+                            double* rnorm) {
+  BCS_OKR(dot(s, b, b, N, SLOT_N));
+  BCS_OKR(any_nonzero(s, x, N, SLOT_X));
+  BCS_OKR(fetch_scalars(s, SLOT_X + 1));
+  *bnorm = std::sqrt(s->hscal[SLOT_N]);
+  if (s->hscal[SLOT_X] != 0.0) return true_residual(s, b, x, r, N, rnorm);
+  BCS_CU(s, cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  *rnorm = *bnorm;
+  return BCS_OK;
+}
+
 bcs_status fgmres(Solver* s, const double* b, double* x, bcs_result* res) {
   const bcs_config& cfg = s->cfg;
   const int m = cfg.restart;
@@ -80,8 +96,8 @@ bcs_status fgmres(Solver* s, const double* b, double* x, bcs_result* res) {
   double* V = s->kv.p;
   char* Z = s->kz.p;
   double* r = s->kr.p;
-  double bnorm = 0.0;
-  BCS_OKR(norm(s, b, N, &bnorm));
+  double bnorm = 0.0, beta = 0.0;
+  BCS_OKR(initial_residual(s, b, x, r, N, &bnorm, &beta));
   res->iters = 0;
   res->restarts = 0;
   if (bnorm == 0.0) {
@@ -89,8 +105,6 @@ bcs_status fgmres(Solver* s, const double* b, double* x, bcs_result* res) {
     res->rel_res_initial = res->rel_res_final = 0.0;
     return BCS_OK;
   }
-  double beta = 0.0;
-  BCS_OKR(true_residual(s, b, x, r, N, &beta));
   res->rel_res_initial = res->rel_res_final = beta / bnorm;
   if (!std::isfinite(beta)) return BCS_BREAKDOWN;
   if (beta <= cfg.tol * bnorm) return BCS_OK;
@@ -184,8 +198,8 @@ bcs_status bicgstab(Solver* s, const double* b, double* x, bcs_result* res) {
   void* ph = s->kz.p;
   void* sh = s->kz.p + N * zbytes(s);
   const double tol = cfg.tol;
-  double bnorm = 0.0;
-  BCS_OKR(norm(s, b, N, &bnorm));
+  double bnorm = 0.0, rn = 0.0;
+  BCS_OKR(initial_residual(s, b, x, r, N, &bnorm, &rn));
   res->iters = 0;
   res->restarts = 0;
   if (bnorm == 0.0) {
@@ -193,8 +207,6 @@ bcs_status bicgstab(Solver* s, const double* b, double* x, bcs_result* res) {
     res->rel_res_initial = res->rel_res_final = 0.0;
     return BCS_OK;
   }
-  double rn = 0.0;
-  BCS_OKR(true_residual(s, b, x, r, N, &rn));
   res->rel_res_initial = res->rel_res_final = rn / bnorm;
   if (!std::isfinite(rn)) return BCS_BREAKDOWN;
   if (rn <= tol * bnorm) return BCS_OK;
@@ -323,17 +335,10 @@ bcs_status bicgstab(Solver* s, const double* b, double* x, bcs_result* res) {
 
 bcs_status solve(Solver* s, const double* b, double* x, bcs_result* res) {
   const auto t0 = std::chrono::steady_clock::now();
-  BCS_CU(s, cudaMemsetAsync(s->flag.p + 1, 0, sizeof(int32_t), s->stream));
   bcs_status st = s->cfg.solver == BCS_BICGSTAB ? bicgstab(s, b, x, res) : fgmres(s, b, x, res);
   if (st == BCS_ECUDA || st == BCS_ENOMEM || st == BCS_EINVAL) return st;
   cudaError_t e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return s->fail(BCS_ECUDA, std::string("solve: ") + cudaGetErrorString(e));
-  int32_t timeout_flag = 0;
-  BCS_CU(s, cudaMemcpy(&timeout_flag, s->flag.p + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
-  if (timeout_flag) {
-    st = BCS_TIMEOUT;
-    s->err = "a bounded device wait gave up (staged row kernel)";
-  }
   res->status = st;
   res->levels = (int)s->lv.size();
   res->setup_ms = s->last_setup_ms;

@@ -55,20 +55,88 @@ __global__ void k_scan_tile(const int32_t* __restrict__ in, int32_t* __restrict_
   }
 }
 
-__global__ void k_scan_add(int32_t* __restrict__ out, const int32_t* __restrict__ tile_off, int n) {
+// out[i] += tile_off[i / SCAN_TILE]; thread n writes the grand total.
+__global__ void k_scan_add(int32_t* __restrict__ out, const int32_t* __restrict__ tile_off, int n, int tiles) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] += tile_off[i / SCAN_TILE];
+  else if (i == n) out[n] = tile_off[tiles];
 }
 
-__global__ void k_scan_total(const int32_t* __restrict__ in, int32_t* __restrict__ out, int n) {
-  out[n] = out[n - 1] + in[n - 1];
+// Whole exclusive scan of n <= SMALL_SCAN_MAX values in one block, total to
+// out[n]. Values move through shared memory with coalesced global loads and
+// stores; each thread scans SMALL_ITEMS consecutive values (row index padded
+// by one word per 32 so those reads are free of bank conflicts).
+constexpr int SMALL_THREADS = 1024;
+constexpr int SMALL_ITEMS = 8;
+constexpr int SMALL_SCAN_MAX = SMALL_THREADS * SMALL_ITEMS;
+
+__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+
+__global__ void __launch_bounds__(SMALL_THREADS) k_scan_small(const int32_t* __restrict__ in,
+                                                             int32_t* __restrict__ out, int n) {
+  __shared__ int32_t buf[SMALL_SCAN_MAX + SMALL_SCAN_MAX / 32];
+  __shared__ int32_t warp_tot[SMALL_THREADS / 32];
+#pragma unroll
+  for (int k = 0; k < SMALL_ITEMS; ++k) {
+    const int i = k * SMALL_THREADS + threadIdx.x;
+    buf[pad32(i)] = i < n ? in[i] : 0;
+  }
+  __syncthreads();
+  const int base = threadIdx.x * SMALL_ITEMS;
+  int32_t v[SMALL_ITEMS];
+  int32_t local = 0;
+#pragma unroll
+  for (int k = 0; k < SMALL_ITEMS; ++k) {
+    v[k] = buf[pad32(base + k)];
+    local += v[k];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t incl = local;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int32_t w = warp_tot[lane];
+    int32_t wi = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t t = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) wi += t;
+    }
+    warp_tot[lane] = wi - w;
+    if (lane == 31) out[n] = wi;
+  }
+  __syncthreads();
+  int32_t run = warp_tot[warp] + incl - local;
+#pragma unroll
+  for (int k = 0; k < SMALL_ITEMS; ++k) {
+    buf[pad32(base + k)] = run;
+    run += v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < SMALL_ITEMS; ++k) {
+    const int i = k * SMALL_THREADS + threadIdx.x;
+    if (i < n) out[i] = buf[pad32(i)];
+  }
 }
 
 }  // namespace
 
+// out[0..n) = exclusive prefix sums of in[0..n), out[n] = the total; in and
+// out must not overlap. One launch up to SMALL_SCAN_MAX values, else tiles of
+// SCAN_TILE, a scan of the tile sums and an add pass.
 bcs_status exclusive_scan(Solver* s, const int32_t* in, int32_t* out, int n) {
   if (n <= 0) {
     BCS_CU(s, cudaMemsetAsync(out, 0, sizeof(int32_t), s->stream));
+    return BCS_OK;
+  }
+  if (n <= SMALL_SCAN_MAX) {
+    BCS_LAUNCH(s, K_MISC, 8.0 * n, 0, k_scan_small, 1, SMALL_THREADS, 0, in, out, n);
     return BCS_OK;
   }
   const int tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
@@ -76,25 +144,32 @@ bcs_status exclusive_scan(Solver* s, const int32_t* in, int32_t* out, int n) {
   BCS_ALLOC(s, sums, tiles);
   BCS_ALLOC(s, offs, tiles + 1);
   BCS_LAUNCH(s, K_MISC, 8.0 * n, 0, k_scan_tile, tiles, SCAN_THREADS, 0, in, out, sums.p, n);
-  if (tiles > 1) {
-    BCS_OKR(exclusive_scan(s, sums.p, offs.p, tiles));
-    BCS_LAUNCH(s, K_MISC, 8.0 * n, 0, k_scan_add, grid_for(n, 256), 256, 0, out, offs.p, n);
-  }
-  BCS_LAUNCH(s, K_MISC, 0, 0, k_scan_total, 1, 1, 0, in, out, n);
+  BCS_OKR(exclusive_scan(s, sums.p, offs.p, tiles));
+  BCS_LAUNCH(s, K_MISC, 8.0 * n, 0, k_scan_add, grid_for((size_t)n + 1, 256), 256, 0, out, offs.p, n, tiles);
   return BCS_OK;
 }
 
 // ------------------------------------------------------------------ sort/unique
+// Per-segment ascending sort of int32 keys with duplicates removed (counts
+// written), or of uint64 keys kept whole (sort only). Segments up to 32 keys:
+// one thread (register insertion network); up to 256: one warp (bitonic in
+// shared memory); longer: one block per segment (bitonic in dynamic shared
+// memory).
 namespace {
 
 constexpr int WARP_SEG_MAX = 256;  // segments up to this length: one warp
 constexpr int WARPS_PER_BLOCK = 4;
 constexpr int BLOCK_SEG_MAX = 16384;
 
-__global__ void k_seg_sort_warp(const int32_t* __restrict__ seg_ptr, int32_t* __restrict__ keys,
+template <class T> __device__ __forceinline__ T key_max();
+template <> __device__ __forceinline__ int32_t key_max<int32_t>() { return INT_MAX; }
+template <> __device__ __forceinline__ uint64_t key_max<uint64_t>() { return ~0ull; }
+
+template <class T, bool UNIQUE>
+__global__ void k_seg_sort_warp(const int32_t* __restrict__ seg_ptr, T* __restrict__ keys,
                                 int32_t* __restrict__ count, int32_t* __restrict__ long_rows,
                                 int32_t* __restrict__ n_long, int rows) {
-  __shared__ int32_t sm[WARPS_PER_BLOCK][WARP_SEG_MAX];
+  __shared__ T sm[WARPS_PER_BLOCK][WARP_SEG_MAX];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * WARPS_PER_BLOCK + warp;
   if (r >= rows) return;
@@ -103,17 +178,17 @@ __global__ void k_seg_sort_warp(const int32_t* __restrict__ seg_ptr, int32_t* __
     if (lane == 0) long_rows[atomicAdd(n_long, 1)] = r;
     return;
   }
-  int32_t* a = sm[warp];
+  T* a = sm[warp];
   int S = 32;
   while (S < len) S <<= 1;
-  for (int i = lane; i < S; i += 32) a[i] = i < len ? keys[b + i] : INT_MAX;
+  for (int i = lane; i < S; i += 32) a[i] = i < len ? keys[b + i] : key_max<T>();
   __syncwarp();
   for (int k = 2; k <= S; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = lane; i < S; i += 32) {
         const int l = i ^ j;
         if (l > i) {
-          const int32_t x = a[i], y = a[l];
+          const T x = a[i], y = a[l];
           const bool up = (i & k) == 0;
           if ((x > y) == up) {
             a[i] = y;
@@ -123,6 +198,10 @@ __global__ void k_seg_sort_warp(const int32_t* __restrict__ seg_ptr, int32_t* __
       }
       __syncwarp();
     }
+  if (!UNIQUE) {
+    for (int i = lane; i < len; i += 32) keys[b + i] = a[i];
+    return;
+  }
   int outpos = 0;
   for (int i0 = 0; i0 < len; i0 += 32) {
     const int i = i0 + lane;
@@ -134,22 +213,24 @@ __global__ void k_seg_sort_warp(const int32_t* __restrict__ seg_ptr, int32_t* __
   if (lane == 0) count[r] = outpos;
 }
 
-__global__ void k_seg_sort_block(const int32_t* __restrict__ seg_ptr, int32_t* __restrict__ keys,
+template <class T, bool UNIQUE>
+__global__ void k_seg_sort_block(const int32_t* __restrict__ seg_ptr, T* __restrict__ keys,
                                  int32_t* __restrict__ count, const int32_t* __restrict__ long_rows) {
-  extern __shared__ int32_t a[];
+  extern __shared__ __align__(16) unsigned char dyn[];
+  T* a = reinterpret_cast<T*>(dyn);
   __shared__ int32_t wsum[32];
   const int r = long_rows[blockIdx.x];
   const int b = seg_ptr[r], len = seg_ptr[r + 1] - b;
   int S = 32;
   while (S < len) S <<= 1;
-  for (int i = threadIdx.x; i < S; i += blockDim.x) a[i] = i < len ? keys[b + i] : INT_MAX;
+  for (int i = threadIdx.x; i < S; i += blockDim.x) a[i] = i < len ? keys[b + i] : key_max<T>();
   __syncthreads();
   for (int k = 2; k <= S; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = threadIdx.x; i < S; i += blockDim.x) {
         const int l = i ^ j;
         if (l > i) {
-          const int32_t x = a[i], y = a[l];
+          const T x = a[i], y = a[l];
           const bool up = (i & k) == 0;
           if ((x > y) == up) {
             a[i] = y;
@@ -159,6 +240,10 @@ __global__ void k_seg_sort_block(const int32_t* __restrict__ seg_ptr, int32_t* _
       }
       __syncthreads();
     }
+  if (!UNIQUE) {
+    for (int i = threadIdx.x; i < len; i += blockDim.x) keys[b + i] = a[i];
+    return;
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int base = 0;
   for (int i0 = 0; i0 < len; i0 += blockDim.x) {
@@ -179,49 +264,58 @@ __global__ void k_seg_sort_block(const int32_t* __restrict__ seg_ptr, int32_t* _
   if (threadIdx.x == 0) count[r] = base;
 }
 
-// Segments of at most THREAD_SEG_MAX keys: one thread sorts its segment in
-// registers-backed local storage (insertion sort) and compacts duplicates.
-constexpr int THREAD_SEG_MAX = 16;
-
-__global__ void k_seg_sort_thread(const int32_t* __restrict__ seg_ptr, int32_t* __restrict__ keys,
+// Segments of at most M keys: one thread sorts its segment in registers
+// (an unrolled insertion network of min/max pairs).
+template <int M, class T, bool UNIQUE>
+__global__ void k_seg_sort_thread(const int32_t* __restrict__ seg_ptr, T* __restrict__ keys,
                                   int32_t* __restrict__ count, int rows) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   const int b = seg_ptr[r], len = seg_ptr[r + 1] - b;
-  int32_t a[THREAD_SEG_MAX];
+  T a[M];
 #pragma unroll
-  for (int i = 0; i < THREAD_SEG_MAX; ++i) a[i] = i < len ? keys[b + i] : INT_MAX;
+  for (int i = 0; i < M; ++i) a[i] = i < len ? keys[b + i] : key_max<T>();
 #pragma unroll
-  for (int i = 1; i < THREAD_SEG_MAX; ++i)
+  for (int i = 1; i < M; ++i)
 #pragma unroll
     for (int j = i; j > 0; --j) {
-      const int32_t lo = min(a[j - 1], a[j]), hi = max(a[j - 1], a[j]);
+      const T lo = min(a[j - 1], a[j]), hi = max(a[j - 1], a[j]);
       a[j - 1] = lo;
       a[j] = hi;
     }
+  if (!UNIQUE) {
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+      if (i < len) keys[b + i] = a[i];
+    return;
+  }
   int out = 0;
 #pragma unroll
-  for (int i = 0; i < THREAD_SEG_MAX; ++i)
+  for (int i = 0; i < M; ++i)
     if (i < len && (i == 0 || a[i] != a[i - 1])) keys[b + out++] = a[i];
   count[r] = out;
 }
 
-}  // namespace
-
-bcs_status segmented_sort_unique(Solver* s, const int32_t* seg_ptr, int32_t* keys, int32_t* count,
-                                 int rows, int max_len) {
+template <class T, bool UNIQUE>
+bcs_status seg_sort(Solver* s, const int32_t* seg_ptr, T* keys, int32_t* count, int rows, int max_len) {
   if (rows <= 0) return BCS_OK;
   if (max_len > BLOCK_SEG_MAX)
     return s->fail(BCS_EINVAL, "a sparsity-pattern row has more than 16384 candidate entries");
-  if (max_len <= THREAD_SEG_MAX) {
-    BCS_LAUNCH(s, K_MISC, 0, 0, k_seg_sort_thread, grid_for(rows, 128), 128, 0, seg_ptr, keys, count, rows);
+  if (max_len <= 16) {
+    BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_thread<16, T, UNIQUE>), grid_for(rows, 128), 128, 0, seg_ptr, keys,
+               count, rows);
+    return BCS_OK;
+  }
+  if (max_len <= 32) {
+    BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_thread<32, T, UNIQUE>), grid_for(rows, 128), 128, 0, seg_ptr, keys,
+               count, rows);
     return BCS_OK;
   }
   DBuf<int32_t> long_rows, aux;
   BCS_ALLOC(s, long_rows, rows);
   BCS_ALLOC(s, aux, 1);
   BCS_CU(s, cudaMemsetAsync(aux.p, 0, sizeof(int32_t), s->stream));
-  BCS_LAUNCH(s, K_MISC, 0, 0, k_seg_sort_warp, grid_for(rows, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, 0,
+  BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_warp<T, UNIQUE>), grid_for(rows, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, 0,
              seg_ptr, keys, count, long_rows.p, aux.p, rows);
   if (max_len > WARP_SEG_MAX) {
     int32_t h = 0;
@@ -230,12 +324,24 @@ bcs_status segmented_sort_unique(Solver* s, const int32_t* seg_ptr, int32_t* key
     if (h > 0) {
       int S = 32;
       while (S < max_len) S <<= 1;
-      const size_t smem = (size_t)S * sizeof(int32_t);
-      BCS_CU(s, cudaFuncSetAttribute(k_seg_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      BCS_LAUNCH(s, K_MISC, 0, 0, k_seg_sort_block, h, 512, smem, seg_ptr, keys, count, long_rows.p);
+      const size_t smem = (size_t)S * sizeof(T);
+      BCS_CU(s, cudaFuncSetAttribute(k_seg_sort_block<T, UNIQUE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+      BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_block<T, UNIQUE>), h, 512, smem, seg_ptr, keys, count, long_rows.p);
     }
   }
   return BCS_OK;
+}
+
+}  // namespace
+
+bcs_status segmented_sort_unique(Solver* s, const int32_t* seg_ptr, int32_t* keys, int32_t* count,
+                                 int rows, int max_len) {
+  return seg_sort<int32_t, true>(s, seg_ptr, keys, count, rows, max_len);
+}
+
+bcs_status segmented_sort64(Solver* s, const int32_t* seg_ptr, uint64_t* keys, int rows, int max_len) {
+  return seg_sort<uint64_t, false>(s, seg_ptr, keys, nullptr, rows, max_len);
 }
 
 }  // namespace bcs

@@ -34,6 +34,7 @@ struct Request {
   int case_id;
   const double *diag, *upper, *lower, *b;
   double* x;
+  int mem;  // BCS_MEM_HOST or BCS_MEM_DEVICE for all five arrays
   Clock::time_point submitted;
 };
 
@@ -180,8 +181,8 @@ void worker(bcs_server* srv) {
       if (st == BCS_OK)
         st = bcs_set_structure(c.solver, c.C, c.F, c.owner.data(), c.neighbour.data(), BCS_MEM_HOST);
     }
-    if (st == BCS_OK) st = bcs_set_values(c.solver, r.diag, r.upper, r.lower, BCS_MEM_HOST);
-    if (st == BCS_OK) st = bcs_solve(c.solver, r.b, r.x, BCS_MEM_HOST, &res);
+    if (st == BCS_OK) st = bcs_set_values(c.solver, r.diag, r.upper, r.lower, r.mem);
+    if (st == BCS_OK) st = bcs_solve(c.solver, r.b, r.x, r.mem, &res);
     res.status = st;
     const size_t actual = c.solver ? bcs_device_bytes(c.solver) : 0;
 
@@ -280,12 +281,13 @@ BCS_API bcs_status bcs_server_register_case(bcs_server* srv, int n, int32_t n_ce
 }
 
 BCS_API bcs_status bcs_server_submit(bcs_server* srv, int case_id, const double* diag, const double* upper,
-                                    const double* lower, const double* b, double* x, int64_t* ticket) {
+                                    const double* lower, const double* b, double* x, int mem, int64_t* ticket) {
   if (!srv || !ticket || !diag || !b || !x) return BCS_EINVAL;
+  if (mem != BCS_MEM_HOST && mem != BCS_MEM_DEVICE) return BCS_EINVAL;
   std::lock_guard<std::mutex> lk(srv->mu);
   if (case_id < 0 || case_id >= (int)srv->cases.size()) return BCS_EINVAL;
   if (srv->cases[case_id]->F > 0 && (!upper || !lower)) return BCS_EINVAL;
-  Request r{srv->next_ticket++, case_id, diag, upper, lower, b, x, Clock::now()};
+  Request r{srv->next_ticket++, case_id, diag, upper, lower, b, x, mem, Clock::now()};
   srv->done[r.ticket] = Done{};
   srv->queue.push_back(r);
   srv->submitted++;

@@ -295,28 +295,83 @@ __global__ void k_compact(int rows, const int32_t* __restrict__ cptr, const int3
   for (int q = 0; q < len; ++q) ci[o + q] = cand[b + q];
 }
 
-// Candidates of the tentative Galerkin pattern: row I gathers agg(col) over
-// the rows of its members.
-__global__ void k_cand_count_tent(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
-                                  const int32_t* __restrict__ rp, int32_t* __restrict__ cnt) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= nagg) return;
-  int c = 0;
-  for (int q = mptr[I]; q < mptr[I + 1]; ++q) c += rp[mem[q] + 1] - rp[mem[q]];
-  cnt[I] = c;
+// Tentative Galerkin pattern and gather lists from one sort per product.
+// A candidate packs (output column J) << 32 | (source block position); the
+// candidates of an output row are sorted ascending, so each run of equal J is
+// one output block and lists its sources in ascending position, which is the
+// summation order of the product.
+__global__ void k_pack_ap(int nnz, const int32_t* __restrict__ ci, const int32_t* __restrict__ agg,
+                          uint64_t* __restrict__ cand) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nnz) cand[p] = ((uint64_t)(uint32_t)agg[ci[p]] << 32) | (uint32_t)p;
 }
 
-__global__ void k_cand_fill_tent(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
-                                 const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                 const int32_t* __restrict__ agg, const int32_t* __restrict__ cptr,
-                                 int32_t* __restrict__ cand) {
+// Candidate count of A_c's row I (the AP rows of its members); longest -> *mx.
+__global__ void k_count_ac(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
+                           const int32_t* __restrict__ aprp, int32_t* __restrict__ cnt, int32_t* __restrict__ mx) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = 0;
+  if (I < nagg)
+    for (int q = mptr[I]; q < mptr[I + 1]; ++q) c += aprp[mem[q] + 1] - aprp[mem[q]];
+  const int m = __reduce_max_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(mx, m);
+  if (I < nagg) cnt[I] = c;
+}
+
+__global__ void k_pack_ac(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
+                          const int32_t* __restrict__ aprp, const int32_t* __restrict__ apci,
+                          const int32_t* __restrict__ cptr, uint64_t* __restrict__ cand) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nagg) return;
   int o = cptr[I];
   for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
     const int i = mem[q];
-    for (int k = rp[i]; k < rp[i + 1]; ++k) cand[o++] = agg[ci[k]];
+    for (int a = aprp[i]; a < aprp[i + 1]; ++a) cand[o++] = ((uint64_t)(uint32_t)apci[a] << 32) | (uint32_t)a;
   }
+}
+
+// Number of runs (distinct columns) in each sorted segment; longest -> *mx
+// when mx is given.
+__global__ void k_runs_count(int rows, const int32_t* __restrict__ seg, const uint64_t* __restrict__ cand,
+                             int32_t* __restrict__ cnt, int32_t* __restrict__ mx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = 0;
+  if (i < rows) {
+    uint32_t prev = 0;
+    for (int t = seg[i]; t < seg[i + 1]; ++t) {
+      const uint32_t J = (uint32_t)(cand[t] >> 32);
+      if (t == seg[i] || J != prev) ++c;
+      prev = J;
+    }
+  }
+  if (mx) {
+    const int m = __reduce_max_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(mx, m);
+  }
+  if (i < rows) cnt[i] = c;
+}
+
+// One output block per run: column col[o], first list entry gptr[o]; the
+// list holds the source positions (gptr[nnz] = total).
+__global__ void k_runs_emit(int rows, const int32_t* __restrict__ seg, const uint64_t* __restrict__ cand,
+                            const int32_t* __restrict__ rp, int32_t* __restrict__ col, int32_t* __restrict__ gptr,
+                            int32_t* __restrict__ glist) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  int o = rp[i];
+  uint32_t prev = 0;
+  for (int t = seg[i]; t < seg[i + 1]; ++t) {
+    const uint64_t v = cand[t];
+    const uint32_t J = (uint32_t)(v >> 32);
+    glist[t] = (int32_t)(uint32_t)v;
+    if (t == seg[i] || J != prev) {
+      col[o] = (int32_t)J;
+      gptr[o] = t;
+      ++o;
+    }
+    prev = J;
+  }
+  if (i == rows - 1) gptr[rp[rows]] = seg[rows];
 }
 
 // R A P with tentative P (identity blocks), as the two products of its
@@ -329,46 +384,6 @@ __global__ void k_cand_fill_tent(int nagg, const int32_t* __restrict__ mptr, con
 // summation order; the value passes then gather a few blocks per output with
 // one thread per (block, element), so the n*n threads of an output read each
 // source block as one coalesced span.
-
-// Per fine row (which owns its AP entries): the AP entry of each block.
-__global__ void k_apg(int rows, int pass, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                      const int32_t* __restrict__ agg, const int32_t* __restrict__ aprp,
-                      const int32_t* __restrict__ apci, int32_t* __restrict__ cnt, const int32_t* __restrict__ gptr,
-                      int32_t* __restrict__ glist) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= rows) return;
-  const int ab = aprp[i], ae = aprp[i + 1];
-  if (pass == 0) {
-    for (int a = ab; a < ae; ++a) cnt[a] = 0;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) cnt[find_col(apci, ab, ae, agg[ci[k]])]++;
-  } else {
-    for (int a = ab; a < ae; ++a) cnt[a] = 0;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {
-      const int a = find_col(apci, ab, ae, agg[ci[k]]);
-      glist[gptr[a] + cnt[a]++] = k;
-    }
-  }
-}
-
-// Per coarse row (which owns its entries): the contributing AP entries of
-// each coarse block, members in ascending order.
-__global__ void k_cg(int nagg, int pass, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
-                     const int32_t* __restrict__ aprp, const int32_t* __restrict__ apci,
-                     const int32_t* __restrict__ crp, const int32_t* __restrict__ cci, int32_t* __restrict__ cnt,
-                     const int32_t* __restrict__ gptr, int32_t* __restrict__ glist) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= nagg) return;
-  const int cb = crp[I], ce = crp[I + 1];
-  for (int q = cb; q < ce; ++q) cnt[q] = 0;
-  for (int m = mptr[I]; m < mptr[I + 1]; ++m) {
-    const int i = mem[m];
-    for (int a = aprp[i]; a < aprp[i + 1]; ++a) {
-      const int q = find_col(cci, cb, ce, apci[a]);
-      if (pass == 0) cnt[q]++;
-      else glist[gptr[q] + cnt[q]++] = a;
-    }
-  }
-}
 
 // out[q] = sum over list[gptr[q] .. gptr[q+1]) of src[list[p]] (n*n blocks),
 // plain FP64 adds from +0 in list order. The first add 0 + v equals v except
@@ -700,6 +715,20 @@ bcs_status max_of(Solver* s, const int32_t* a, int n, int32_t* out) {
   return read_int(s, m.p, out);
 }
 
+// h[0] = *d_total, h[1] = max of a[0..n) (n >= 0, values >= 0), one sync.
+bcs_status total_and_max(Solver* s, const int32_t* d_total, const int32_t* a, int n, int32_t* h) {
+  DBuf<int32_t> m;
+  BCS_ALLOC(s, m, 2);
+  BCS_CU(s, cudaMemsetAsync(m.p, 0, 2 * sizeof(int32_t), s->stream));
+  if (n > 0)
+    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_max_int, grid_for(n, 256) < 1024 ? grid_for(n, 256) : 1024, 256, 0, n, a,
+               m.p + 1);
+  BCS_CU(s, cudaMemcpyAsync(m.p, d_total, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->stream));
+  BCS_CU(s, cudaMemcpyAsync(h, m.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  return BCS_OK;
+}
+
 // Sorted unique pattern from per-row candidate segments. cnt[rows] holds the
 // candidate counts on entry; fills out.rp / ci / nnz and crow (row of each
 // nonzero).
@@ -709,18 +738,19 @@ bcs_status pattern_from_candidates(Solver* s, int rows, DBuf<int32_t>& cnt, Fill
   DBuf<int32_t> cptr, cand;
   BCS_ALLOC(s, cptr, rows + 1);
   BCS_OKR(exclusive_scan(s, cnt.p, cptr.p, rows));
-  int32_t total = 0, mx = 0;
-  BCS_OKR(read_int(s, cptr.p + rows, &total));
+  int32_t tm[2] = {0, 0};
+  BCS_OKR(total_and_max(s, cptr.p + rows, cnt.p, rows, tm));
+  const int32_t total = tm[0], mx = tm[1];
   BCS_ALLOC(s, cand, total > 0 ? total : 1);
   BCS_OKR(fill(cptr.p, cand.p));
-  BCS_OKR(max_of(s, cnt.p, rows, &mx));
   BCS_OKR(segmented_sort_unique(s, cptr.p, cand.p, cnt.p, rows, mx));
   BCS_ALLOC(s, out.rp, rows + 1);
   BCS_OKR(exclusive_scan(s, cnt.p, out.rp.p, rows));
-  int32_t nnz = 0;
-  BCS_OKR(read_int(s, out.rp.p + rows, &nnz));
+  BCS_OKR(total_and_max(s, out.rp.p + rows, cnt.p, rows, tm));
+  const int32_t nnz = tm[0];
   out.rows = rows;
   out.nnz = nnz;
+  out.maxrow = tm[1];
   BCS_ALLOC(s, out.ci, nnz > 0 ? nnz : 1);
   BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_compact, grid_for(rows, 256), 256, 0, rows, cptr.p, cand.p, out.rp.p,
              out.ci.p);
@@ -793,61 +823,76 @@ bcs_status members(Solver* s, int rows, int nagg, const int32_t* agg, DBuf<int32
   return segmented_sort_unique(s, mptr.p, mem.p, cnt.p, nagg, mx);
 }
 
-// Gather lists of the tentative Galerkin product: per coarse block, its
-// contributing fine blocks in ascending position.
 // Gather lists of the two tentative products (see k_list_sum).
 struct TentPlan {
   DBuf<int32_t> apg_ptr, apg_list, cg_ptr, cg_list;
 };
 
 // Patterns of AP = A P_tent (row i: sorted aggregates of its neighbours) and
-// of A_c = P_tent^T AP (row I: sorted aggregates reached from its members),
-// and the gather lists of both products.
+// of A_c = P_tent^T AP (row I: sorted columns of its members' AP rows), and
+// the gather lists of both products, each from one segmented sort of packed
+// (column, source position) candidates. Sets A_c.maxrow. Two host reads.
 bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, const int32_t* mptr,
-                        const int32_t* mem, Bsr& AP, DBuf<int32_t>& aprow, Bsr& Ac, DBuf<int32_t>& crow,
-                        TentPlan& plan) {
+                        const int32_t* mem, Bsr& AP, Bsr& Ac, TentPlan& plan) {
   const int rows = A.rows;
+  if (A.maxrow < 0) return s->fail(BCS_EINVAL, "internal: longest row of the operator unknown");
+  DBuf<int32_t> cnt, cptr, hv;
+  BCS_ALLOC(s, cnt, rows > nagg ? rows : nagg);
+  BCS_ALLOC(s, cptr, nagg + 1);
+  BCS_ALLOC(s, hv, 4);
+  BCS_CU(s, cudaMemsetAsync(hv.p, 0, 4 * sizeof(int32_t), s->stream));
+  int32_t h[2] = {0, 0};
+  // AP: candidates are A's blocks, segments are A's rows
   {
-    DBuf<int32_t> cnt;
-    BCS_ALLOC(s, cnt, rows);
-    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_p, grid_for(rows, 256), 256, 0, rows, A.rp.p, cnt.p);
-    auto fill = [&](const int32_t*, int32_t* cand) -> bcs_status {
-      BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_fill_p, grid_for(rows, 256), 256, 0, rows, A.rp.p, A.ci.p, agg,
-                 cand);
-      return BCS_OK;
-    };
-    BCS_OKR(pattern_from_candidates(s, rows, cnt, fill, AP, aprow));
+    DBuf<uint64_t> cand;
+    BCS_ALLOC(s, cand, A.nnz);
+    BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_pack_ap, grid_for(A.nnz, 256), 256, 0, A.nnz, A.ci.p, agg,
+               cand.p);
+    BCS_OKR(segmented_sort64(s, A.rp.p, cand.p, rows, A.maxrow));
+    BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_runs_count, grid_for(rows, 256), 256, 0, rows, A.rp.p, cand.p,
+               cnt.p, (int32_t*)nullptr);
+    BCS_ALLOC(s, AP.rp, rows + 1);
+    BCS_OKR(exclusive_scan(s, cnt.p, AP.rp.p, rows));
+    // A_c candidate counts (the members' AP rows) before the one host read
+    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_count_ac, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, AP.rp.p, cnt.p,
+               hv.p + 1);
+    BCS_OKR(exclusive_scan(s, cnt.p, cptr.p, nagg));
+    BCS_CU(s, cudaMemcpyAsync(hv.p, AP.rp.p + rows, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->stream));
+    BCS_CU(s, cudaMemcpyAsync(h, hv.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    BCS_CU(s, cudaStreamSynchronize(s->stream));
+    AP.rows = rows;
     AP.cols = nagg;
+    AP.nnz = h[0];
+    BCS_ALLOC(s, AP.ci, AP.nnz);
+    BCS_ALLOC(s, plan.apg_ptr, AP.nnz + 1);
+    BCS_ALLOC(s, plan.apg_list, A.nnz);
+    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * A.nnz + 8.0 * AP.nnz, 0, k_runs_emit, grid_for(rows, 256), 256, 0, rows,
+               A.rp.p, cand.p, AP.rp.p, AP.ci.p, plan.apg_ptr.p, plan.apg_list.p);
   }
+  // A_c: candidates are the AP blocks of each aggregate's members
+  const int max_ac = h[1];
   {
-    DBuf<int32_t> cnt;
-    BCS_ALLOC(s, cnt, nagg);
-    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p,
-               cnt.p);
-    auto fill = [&](const int32_t* cptr, int32_t* cand) -> bcs_status {
-      BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_fill_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p,
-                 A.ci.p, agg, cptr, cand);
-      return BCS_OK;
-    };
-    BCS_OKR(pattern_from_candidates(s, nagg, cnt, fill, Ac, crow));
-    Ac.cols = nagg;
+    DBuf<uint64_t> cand;
+    BCS_ALLOC(s, cand, AP.nnz);
+    BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * AP.nnz, 0, k_pack_ac, grid_for(nagg, 256), 256, 0, nagg, mptr, mem,
+               AP.rp.p, AP.ci.p, cptr.p, cand.p);
+    BCS_OKR(segmented_sort64(s, cptr.p, cand.p, nagg, max_ac));
+    BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * AP.nnz, 0, k_runs_count, grid_for(nagg, 256), 256, 0, nagg, cptr.p, cand.p,
+               cnt.p, hv.p + 3);
+    BCS_ALLOC(s, Ac.rp, nagg + 1);
+    BCS_OKR(exclusive_scan(s, cnt.p, Ac.rp.p, nagg));
+    BCS_CU(s, cudaMemcpyAsync(hv.p + 2, Ac.rp.p + nagg, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->stream));
+    BCS_CU(s, cudaMemcpyAsync(h, hv.p + 2, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    BCS_CU(s, cudaStreamSynchronize(s->stream));
+    Ac.rows = Ac.cols = nagg;
+    Ac.nnz = h[0];
+    Ac.maxrow = h[1];
+    BCS_ALLOC(s, Ac.ci, Ac.nnz);
+    BCS_ALLOC(s, plan.cg_ptr, Ac.nnz + 1);
+    BCS_ALLOC(s, plan.cg_list, AP.nnz);
+    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * AP.nnz + 8.0 * Ac.nnz, 0, k_runs_emit, grid_for(nagg, 256), 256, 0, nagg,
+               cptr.p, cand.p, Ac.rp.p, Ac.ci.p, plan.cg_ptr.p, plan.cg_list.p);
   }
-  DBuf<int32_t> cnt;
-  BCS_ALLOC(s, cnt, (AP.nnz > Ac.nnz ? AP.nnz : Ac.nnz) + 1);
-  BCS_ALLOC(s, plan.apg_ptr, AP.nnz + 1);
-  BCS_ALLOC(s, plan.apg_list, A.nnz);
-  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_apg, grid_for(rows, 128), 128, 0, rows, 0, A.rp.p, A.ci.p, agg, AP.rp.p,
-             AP.ci.p, cnt.p, (const int32_t*)nullptr, (int32_t*)nullptr);
-  BCS_OKR(exclusive_scan(s, cnt.p, plan.apg_ptr.p, AP.nnz));
-  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_apg, grid_for(rows, 128), 128, 0, rows, 1, A.rp.p, A.ci.p, agg, AP.rp.p,
-             AP.ci.p, cnt.p, plan.apg_ptr.p, plan.apg_list.p);
-  BCS_ALLOC(s, plan.cg_ptr, Ac.nnz + 1);
-  BCS_ALLOC(s, plan.cg_list, AP.nnz);
-  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cg, grid_for(nagg, 128), 128, 0, nagg, 0, mptr, mem, AP.rp.p, AP.ci.p,
-             Ac.rp.p, Ac.ci.p, cnt.p, (const int32_t*)nullptr, (int32_t*)nullptr);
-  BCS_OKR(exclusive_scan(s, cnt.p, plan.cg_ptr.p, Ac.nnz));
-  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cg, grid_for(nagg, 128), 128, 0, nagg, 1, mptr, mem, AP.rp.p, AP.ci.p,
-             Ac.rp.p, Ac.ci.p, cnt.p, plan.cg_ptr.p, plan.cg_list.p);
   return BCS_OK;
 }
 
@@ -881,12 +926,11 @@ bcs_status aggregate_level(Solver* s, Level& L) {
   Bsr G;  // current aggregate graph (passes >= 2)
   const Bsr* cur = &L.A;
   for (int pass = 1; pass < s->setup_cfg.agg_passes; ++pass) {
-    DBuf<int32_t> mptr, mem, crow;
+    DBuf<int32_t> mptr, mem;
     BCS_OKR(members(s, cur->rows, nagg, cur_agg.p, mptr, mem));
     Bsr Abar, AP;
-    DBuf<int32_t> aprow;
     TentPlan plan;
-    BCS_OKR(tent_pattern(s, *cur, nagg, cur_agg.p, mptr.p, mem.p, AP, aprow, Abar, crow, plan));
+    BCS_OKR(tent_pattern(s, *cur, nagg, cur_agg.p, mptr.p, mem.p, AP, Abar, plan));
     BCS_OKR(tent_values(s, *cur, plan, AP, Abar));
     DBuf<int32_t> a2;
     int n2 = 0;
@@ -1073,7 +1117,7 @@ bcs_status build_transfer(Solver* s, int l, bool full) {
   if (s->setup_cfg.pmode == BCS_P_TENTATIVE) {
     TentPlan plan;
     if (full) {
-      BCS_OKR(tent_pattern(s, L.A, L.nagg, L.agg.p, L.mptr.p, L.mem.p, L.AP, L.AProw, Lc.A, L.Crow, plan));
+      BCS_OKR(tent_pattern(s, L.A, L.nagg, L.agg.p, L.mptr.p, L.mem.p, L.AP, Lc.A, plan));
     } else {
       plan.apg_ptr = std::move(L.apg_ptr);
       plan.apg_list = std::move(L.apg_list);

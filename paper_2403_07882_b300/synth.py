@@ -53,10 +53,10 @@ def _one_norm(blocks):
 
 
 def _row_offdiag_sum(C, owner, neighbour, up_val, lo_val):
-    s = np.zeros(C)
-    np.add.at(s, owner, up_val)
-    np.add.at(s, neighbour, lo_val)
-    return s
+    # one pass over owner contributions then neighbour contributions, each
+    # cell's sum accumulated in that order from 0.0
+    idx = np.concatenate([owner, neighbour])
+    return np.bincount(idx, weights=np.concatenate([up_val, lo_val]), minlength=C).astype(np.float64)
 
 
 def _density_values(C, owner, neighbour, rng, n=5):
@@ -203,7 +203,8 @@ def knn(side=160, seed=3, kmin=4, kmax=12):
     dst = nbrs[keep]
     o = np.minimum(src, dst).astype(np.int64)
     nb = np.maximum(src, dst).astype(np.int64)
-    key = np.unique(o * C + nb)
+    key = np.sort(o * C + nb)
+    key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     owner = (key // C).astype(np.int64)
     neighbour = (key % C).astype(np.int64)
     diag, upper, lower, b = _density_values(C, owner, neighbour, rng)

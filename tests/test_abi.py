@@ -73,3 +73,6 @@ def test_server_argument_checks(lib):
     assert lib.bcs_server_destroy(None) == bcs.BCS_OK
     cid = ct.c_int()
     assert lib.bcs_server_register_case(None, 5, 10, 0, None, None, ct.byref(cid)) == bcs.BCS_EINVAL
+    t = ct.c_int64()
+    assert lib.bcs_server_submit(None, 0, None, None, None, None, None, bcs.BCS_MEM_HOST,
+                                 ct.byref(t)) == bcs.BCS_EINVAL

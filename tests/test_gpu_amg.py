@@ -144,3 +144,59 @@ def test_fp32_sliced_cycle_on_uneven_rows(gen):
         s.load(system, device=DEV)
         z = s.precond(torch.from_numpy(v).to(DEV)).cpu().numpy()
     assert np.linalg.norm(z - z_ref) <= 2e-5 * np.linalg.norm(z_ref)
+
+
+@pytest.mark.parametrize("precision", [bcs.BCS_PREC_FP32, bcs.BCS_PREC_BF16])
+@pytest.mark.parametrize("gen", [lambda: synth.density(20, seed=1), lambda: synth.pressure(18, seed=2),
+                                 lambda: synth.knn(16, seed=5), lambda: synth.random_graph(5000, 20000, 3, seed=3)])
+def test_slice_layouts_identical(gen, precision):
+    """Both storage layouts of the low-precision cycle (one lane per scalar
+    row; one thread per block row) run the same fma sequence per scalar row,
+    so the preconditioner outputs are bit-identical; the tuned default equals
+    both, and all agree with the FP64 reference cycle to storage precision."""
+    system = gen()
+    v = np.random.default_rng(12).standard_normal(system["b"].shape)
+    outs = {}
+    for layout in (0, 1, -1):
+        with bcs.Solver(system["n"], precision=precision, slice_layout=layout) as s:
+            s.load(system, device=DEV)
+            outs[layout] = s.precond(torch.from_numpy(v).to(DEV)).cpu().numpy()
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[-1])
+    amg = oracle.Amg(oracle.ldu_to_bsr(system), oracle.config())
+    z_ref = amg.vcycle(v)
+    tol = 2e-5 if precision == bcs.BCS_PREC_FP32 else 5e-2
+    assert np.linalg.norm(outs[0] - z_ref) <= tol * np.linalg.norm(z_ref)
+
+
+@pytest.mark.parametrize("precision", [bcs.BCS_PREC_FP32, bcs.BCS_PREC_BF16])
+def test_graph_cycle_identical(precision):
+    """The V-cycle replayed as a CUDA graph gives the same bits as the same
+    cycle launched kernel by kernel, counts the same launches, and solves
+    (FGMRES and BiCGStab) give identical iterates; a resetup drops and
+    recaptures the graph."""
+    system = synth.density(12, 10, 9, seed=7)
+    v = np.random.default_rng(3).standard_normal(system["b"].shape)
+    res = {}
+    for graph in (0, 1):
+        with bcs.Solver(5, precision=precision, cycle_graph=graph) as s:
+            s.load(system, device=DEV)
+            vt = torch.from_numpy(v).to(DEV)
+            s.reset_stats()
+            z1 = s.precond(vt).cpu().numpy()
+            z2 = s.precond(vt).cpu().numpy()
+            launches = s.stats()["launches"]
+            b = torch.from_numpy(system["b"]).to(DEV)
+            x, st, r = s.solve(b)
+            assert st == bcs.BCS_OK
+            rng = np.random.default_rng(5)
+            sys2 = synth.perturb(system, rng, 0.02)
+            s.set_values(*(torch.from_numpy(sys2[k]).to(DEV) for k in ("diag", "upper", "lower")))
+            z3 = s.precond(vt).cpu().numpy()
+            res[graph] = (z1, z2, launches, x.cpu().numpy(), z3)
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert np.array_equal(res[1][0], res[1][1])
+    assert res[0][2] == res[1][2]
+    assert np.array_equal(res[0][3], res[1][3])
+    assert np.array_equal(res[0][4], res[1][4])
+    assert not np.array_equal(res[1][0], res[1][4])

@@ -1,0 +1,143 @@
+"""Full-size parity in the benchmark's launch configuration (default solver
+settings, FP32-stored AMG inside FP64 FGMRES unless stated):
+
+* density-based 128^3 5x5 (2.1 M cells): the whole AMG hierarchy bit-exact
+  with the CPU reference (aggregates, Galerkin operators, block inverses,
+  coarse inverse) and the FP32 V-cycle within FP32 rounding of the FP64
+  reference cycle;
+* pressure-based 64^3 4x4 with permuted numbering (262,144 cells): hierarchy
+  bit-exact, FP64 V-cycle at 1e-12, BiCGStab and FGMRES(30) to a true
+  relative residual of 1e-8;
+* unstructured k-NN 160^3 (4.1 M cells, k ~ U{4..12}): structure maps exact,
+  FP64 SpMV at 1e-12, sampled Galerkin rows of every level (Sec. 2.3: with
+  the piecewise-constant prolongation a coarse block is the sum of the fine
+  blocks between the two aggregates), and a values-only resetup sequence
+  solved to 1e-8 at every step.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_07882_b300 import bcs, synth
+from test_gpu_amg import compare_hierarchy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def true_rel(ref, b, x):
+    return np.linalg.norm(b - oracle.spmv(ref, x)) / np.linalg.norm(b)
+
+
+def dev(a):
+    return torch.from_numpy(a).to(DEV)
+
+
+def test_density_128_hierarchy_and_cycle():
+    system = synth.density(128, seed=2)
+    ref = oracle.ldu_to_bsr(system)
+    amg = oracle.Amg(ref, oracle.config())
+    assert amg.status == 0
+    v = np.random.default_rng(4).standard_normal(system["b"].shape)
+    z_ref = amg.vcycle(v)
+    with bcs.Solver(5) as s:
+        s.load(system, device=DEV)
+        compare_hierarchy(s, amg, 5, 1)
+        z = s.precond(dev(v)).cpu().numpy()
+    # FP32 storage and arithmetic: the 2e-5 bound of the small-case tests
+    assert np.linalg.norm(z - z_ref) <= 2e-5 * np.linalg.norm(z_ref)
+
+
+@pytest.fixture(scope="module")
+def pressure64():
+    system = synth.pressure(64, seed=1)
+    ref = oracle.ldu_to_bsr(system)
+    return system, ref
+
+
+def test_pressure_64_hierarchy_and_fp64_cycle(pressure64):
+    system, ref = pressure64
+    amg = oracle.Amg(ref, oracle.config())
+    assert amg.status == 0
+    v = np.random.default_rng(8).standard_normal(system["b"].shape)
+    z_ref = amg.vcycle(v)
+    with bcs.Solver(4, precision=bcs.BCS_PREC_FP64) as s:
+        s.load(system, device=DEV)
+        compare_hierarchy(s, amg, 4, 1)
+        z = s.precond(dev(v)).cpu().numpy()
+    assert np.abs(z - z_ref).max() <= 1e-12 * np.abs(z_ref).max()
+
+
+@pytest.mark.parametrize("solver", [bcs.BCS_BICGSTAB, bcs.BCS_FGMRES], ids=["bicgstab", "fgmres"])
+def test_pressure_64_solve(pressure64, solver):
+    system, ref = pressure64
+    with bcs.Solver(4, solver=solver) as s:
+        s.load(system, device=DEV)
+        x, st, res = s.solve(dev(system["b"]))
+    assert st == bcs.BCS_OK, res
+    assert true_rel(ref, system["b"], x.cpu().numpy()) <= 1e-8
+
+
+def galerkin_rows_ok(fine, agg, coarse, rows):
+    """Coarse rows `rows` of R A P with the piecewise-constant P, summed here
+    block by block from the fine operator, against the GPU's coarse rows."""
+    n = fine["val"].shape[-1]
+    order = np.argsort(agg, kind="stable")
+    start = np.concatenate(([0], np.cumsum(np.bincount(agg, minlength=coarse["row_ptr"].size - 1))))
+    for I in rows:
+        acc, mag = {}, {}
+        for i in order[start[I]:start[I + 1]]:
+            for p in range(fine["row_ptr"][i], fine["row_ptr"][i + 1]):
+                J = int(agg[fine["col"][p]])
+                acc[J] = acc.get(J, 0.0) + fine["val"][p]
+                mag[J] = mag.get(J, 0.0) + np.abs(fine["val"][p])
+        b, e = coarse["row_ptr"][I], coarse["row_ptr"][I + 1]
+        cols = coarse["col"][b:e]
+        if sorted(acc) != list(cols):
+            return False
+        for q, J in enumerate(cols):
+            if np.any(np.abs(coarse["val"][b + q].reshape(n, n) - acc[J]) > 1e-12 * mag[J]):
+                return False
+    return True
+
+
+def test_knn_160_structure_spmv_galerkin_and_resetups():
+    system = synth.knn(160, seed=4)
+    ref = oracle.ldu_to_bsr(system)
+    rng = np.random.default_rng(17)
+    with bcs.Solver(5) as s:
+        s.load(system, device=DEV)
+        got = s.bsr(values=False)
+        for key in ("row_ptr", "col", "pos_diag", "pos_up", "pos_lo"):
+            assert np.array_equal(got[key], ref[key]), key
+        x = np.random.default_rng(3).standard_normal(system["b"].shape)
+        y = s.spmv(dev(x)).cpu().numpy()
+        absref = dict(ref)
+        absref["val"] = np.abs(ref["val"])
+        assert np.all(np.abs(y - oracle.spmv(ref, x)) <= 1e-12 * oracle.spmv(absref, np.abs(x)))
+        del absref, y
+
+        fine = s.level(0)
+        for l in range(s.levels - 1):
+            if fine["coarse_kind"] >= 0:
+                break
+            coarse = s.level(l + 1)
+            agg = fine["agg"]
+            nagg = coarse["row_ptr"].size - 1
+            assert agg.min() >= 0 and agg.max() == nagg - 1
+            assert np.all(np.bincount(agg, minlength=nagg) >= 1)
+            sample = np.random.default_rng(l).choice(nagg, size=min(nagg, 64), replace=False)
+            assert galerkin_rows_ok(fine, agg, coarse, sample), l
+            fine = coarse
+        del fine, coarse
+
+        b = dev(system["b"])
+        for it in range(3):
+            if it:
+                system = synth.perturb(system, rng, 0.02)
+                s.set_values(*(dev(system[k]) for k in ("diag", "upper", "lower")))
+                ref = oracle.ldu_to_bsr(system)
+            xs, st, res = s.solve(b)
+            assert st == bcs.BCS_OK, res
+            assert true_rel(ref, system["b"], xs.cpu().numpy()) <= 1e-8

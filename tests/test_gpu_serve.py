@@ -102,3 +102,29 @@ def test_wait_with_timeout():
         if st == bcs.BCS_TIMEOUT:
             st, res, lat, x = srv.wait(t)
         assert st == bcs.BCS_OK and true_rel(system, x) <= 1e-8
+
+
+def test_device_inputs_match_host_inputs():
+    """Requests whose arrays live in device memory give the same solutions,
+    bit for bit, as requests with host arrays."""
+    systems = cases()[:2]
+    seqs = sequences(systems, k=2)
+    out = {}
+    for where in ("host", "device"):
+        with bcs.Server(slots=2) as srv:
+            ids = [srv.register(s) for s in systems]
+            tickets = []
+            for c in range(len(systems)):
+                for j, s_ in enumerate(seqs[c]):
+                    if where == "device":
+                        s_ = {k: torch.from_numpy(s_[k]).cuda() for k in ("diag", "upper", "lower", "b")}
+                        torch.cuda.synchronize()
+                    tickets.append((c, j, srv.submit(ids[c], s_)))
+            for c, j, t in tickets:
+                st, res, lat, x = srv.wait(t)
+                assert st == bcs.BCS_OK, res
+                out[(where, c, j)] = x if where == "host" else x.cpu().numpy()
+    for c in range(len(systems)):
+        for j in range(2):
+            assert np.array_equal(out[("host", c, j)], out[("device", c, j)])
+            assert true_rel(seqs[c][j], out[("host", c, j)]) <= 1e-8
