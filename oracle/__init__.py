@@ -25,7 +25,7 @@ class Config(ct.Structure):
         ("jacobi_omega", ct.c_double), ("nu1", ct.c_int), ("nu2", ct.c_int),
         ("coarse_size", ct.c_int), ("max_levels", ct.c_int),
         ("max_coarsen_ratio", ct.c_double), ("p_omega", ct.c_double),
-        ("coarse_dense_max", ct.c_int), ("coarse_sweeps", ct.c_int),
+        ("coarse_dense_max", ct.c_int), ("coarse_sweeps", ct.c_int), ("smoother", ct.c_int),
     ]
 
 
@@ -74,6 +74,10 @@ def lib():
         L.or_amg_get_dinv.argtypes = [ct.c_void_p, ct.c_int, _f64p]
         L.or_amg_get_coarse_inverse.argtypes = [ct.c_void_p, _f64p]
         L.or_amg_vcycle.argtypes = [ct.c_void_p, _f64p, _f64p]
+        L.or_amg_get_dilu.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p]
+        L.or_colour.argtypes = [ct.c_int, _i32p, _i32p, _i32p]
+        L.or_dilu_factor.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, _i32p, _f64p]
+        L.or_dilu_apply.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, _i32p, ct.c_int, _f64p, _f64p, _f64p]
         L.or_solve.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, ct.c_void_p, ct.POINTER(Config),
                                _f64p, _f64p, ct.POINTER(Result), ct.c_void_p, ct.c_int]
         L.or_fgmres_arnoldi.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, ct.c_void_p,
@@ -230,6 +234,16 @@ class Amg:
         lib().or_amg_get_coarse_inverse(self.h, out)
         return out.reshape(N, N)
 
+    def dilu(self, l):
+        """(number of colours, colour[rows], einv[rows][n][n]) of level l, or
+        (-1, None, None) when the level keeps block Jacobi."""
+        rows = self.info(l)["rows"]
+        n = self.n
+        col = np.zeros(rows, np.int32)
+        einv = np.zeros((rows, n, n))
+        nc = lib().or_amg_get_dilu(self.h, l, _p(col), _p(einv))
+        return (nc, col, einv) if nc > 0 else (-1, None, None)
+
     def vcycle(self, v):
         v = np.ascontiguousarray(v, np.float64).ravel()
         z = np.zeros_like(v)
@@ -267,3 +281,32 @@ def arnoldi(bsr, b, j_steps, cfg=None, amg=None):
                                    amg.h if amg is not None else None, ct.byref(cfg),
                                    np.ascontiguousarray(b, np.float64).ravel(), j_steps, V, Z, H)
     return done, V.reshape(j_steps + 1, N), Z.reshape(j_steps, N), H.reshape(j_steps + 1, j_steps)
+
+
+def colour(bsr):
+    """Multicolouring of a BSR pattern: (number of colours or -1, colour[rows])."""
+    col = np.zeros(bsr["rows"], np.int32)
+    nc = lib().or_colour(bsr["rows"], bsr["row_ptr"], bsr["col"], col)
+    return nc, col
+
+
+def dilu_factor(bsr, colour_):
+    """DILU block inverses E_i^{-1} for a colouring: (status, einv)."""
+    n = bsr["n"]
+    einv = np.zeros((bsr["rows"], n, n))
+    st = lib().or_dilu_factor(bsr["rows"], n, bsr["row_ptr"], bsr["col"],
+                              np.ascontiguousarray(bsr["val"], np.float64).ravel(),
+                              np.ascontiguousarray(colour_, np.int32), einv.reshape(-1))
+    return st, einv
+
+
+def dilu_apply(bsr, colour_, einv, r):
+    """z = M^{-1} r for the DILU factorisation (einv) of bsr."""
+    n = bsr["n"]
+    z = np.zeros((bsr["rows"], n))
+    lib().or_dilu_apply(bsr["rows"], n, bsr["row_ptr"], bsr["col"],
+                        np.ascontiguousarray(bsr["val"], np.float64).ravel(),
+                        np.ascontiguousarray(colour_, np.int32), int(np.max(colour_)) + 1,
+                        np.ascontiguousarray(einv, np.float64).ravel(),
+                        np.ascontiguousarray(r, np.float64).ravel(), z.reshape(-1))
+    return z

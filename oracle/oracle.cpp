@@ -65,6 +65,7 @@ void or_config_default(or_config* c) {
   c->p_omega = 4.0 / 3.0;
   c->coarse_dense_max = 1024;
   c->coarse_sweeps = 8;
+  c->smoother = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -396,6 +397,142 @@ int diag_inverses(const Bsr& A, std::vector<double>& dinv) {
   return 0;
 }
 
+// ---- multicolour block DILU (see oracle.h) ----
+uint32_t lowbias32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+constexpr int MAX_COLOURS = 128;
+
+// (h(i), i) > (h(j), j)
+bool beats(int i, int j) {
+  const uint32_t hi = lowbias32((uint32_t)i), hj = lowbias32((uint32_t)j);
+  return hi != hj ? hi > hj : i > j;
+}
+
+int colour_rows(const Bsr& A, std::vector<int32_t>& colour) {
+  const int rows = A.rows;
+  colour.assign(rows, -1);
+  int left = rows, ncol = 0;
+  while (left > 0) {
+    // the round's independent set, judged on the state at the round's start
+    std::vector<int> pick;
+    for (int i = 0; i < rows; ++i) {
+      if (colour[i] >= 0) continue;
+      bool top = true;
+      for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+        const int j = A.ci[k];
+        if (j != i && colour[j] < 0 && beats(j, i)) top = false;
+      }
+      if (top) pick.push_back(i);
+    }
+    std::vector<int32_t> chosen(pick.size());
+    for (size_t q = 0; q < pick.size(); ++q) {
+      const int i = pick[q];
+      std::vector<bool> used(MAX_COLOURS, false);
+      for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+        const int j = A.ci[k];
+        if (j != i && colour[j] >= 0) used[colour[j]] = true;
+      }
+      int c = 0;
+      while (c < MAX_COLOURS && used[c]) ++c;
+      if (c == MAX_COLOURS) return -1;
+      chosen[q] = c;
+    }
+    for (size_t q = 0; q < pick.size(); ++q) {
+      colour[pick[q]] = chosen[q];
+      if (chosen[q] + 1 > ncol) ncol = chosen[q] + 1;
+    }
+    left -= (int)pick.size();
+  }
+  return ncol;
+}
+
+int dilu_factor(const Bsr& A, const std::vector<int32_t>& colour, std::vector<double>& einv) {
+  const int n = A.n, nn = n * n, rows = A.rows;
+  einv.assign((size_t)rows * nn, 0.0);
+  int ncol = 0;
+  for (int i = 0; i < rows; ++i) ncol = std::max(ncol, colour[i] + 1);
+  std::vector<double> E(nn), W(nn), Z(nn);
+  for (int c = 0; c < ncol; ++c)
+    for (int i = 0; i < rows; ++i) {
+      if (colour[i] != c) continue;
+      const int kd = find_in_row(A, i, i);
+      if (kd < 0) return 1;
+      std::copy(A.blk(kd), A.blk(kd) + nn, E.begin());
+      for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+        const int j = A.ci[k];
+        if (colour[j] >= c) continue;
+        const int kt = find_in_row(A, j, i);
+        block_mul(n, A.blk(k), einv.data() + (size_t)j * nn, W.data());
+        block_mul(n, W.data(), A.blk(kt), Z.data());
+        for (int e = 0; e < nn; ++e) E[e] = E[e] - Z[e];
+      }
+      if (or_dense_inverse(n, E.data(), einv.data() + (size_t)i * nn)) return 1;
+    }
+  return 0;
+}
+
+// z = M^{-1} r (plain sums, row-major block order)
+void dilu_apply(const Bsr& A, const std::vector<int32_t>& colour, int ncol, const std::vector<double>& einv,
+                const double* r, double* z) {
+  const int n = A.n, nn = n * n, rows = A.rows;
+  std::vector<double> y((size_t)rows * n, 0.0), t(n);
+  for (int c = 0; c < ncol; ++c)
+    for (int i = 0; i < rows; ++i) {
+      if (colour[i] != c) continue;
+      for (int a = 0; a < n; ++a) t[a] = r[(size_t)i * n + a];
+      for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+        const int j = A.ci[k];
+        if (colour[j] >= c) continue;
+        for (int a = 0; a < n; ++a) {
+          double s = 0.0;
+          for (int b = 0; b < n; ++b) s += A.blk(k)[a * n + b] * y[(size_t)j * n + b];
+          t[a] = t[a] - s;
+        }
+      }
+      for (int a = 0; a < n; ++a) {
+        double s = 0.0;
+        for (int b = 0; b < n; ++b) s += einv[(size_t)i * nn + a * n + b] * t[b];
+        y[(size_t)i * n + a] = s;
+      }
+    }
+  for (int c = ncol - 1; c >= 0; --c)
+    for (int i = 0; i < rows; ++i) {
+      if (colour[i] != c) continue;
+      for (int a = 0; a < n; ++a) t[a] = 0.0;
+      for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+        const int j = A.ci[k];
+        if (colour[j] <= c) continue;
+        for (int a = 0; a < n; ++a) {
+          double s = 0.0;
+          for (int b = 0; b < n; ++b) s += A.blk(k)[a * n + b] * z[(size_t)j * n + b];
+          t[a] = t[a] + s;
+        }
+      }
+      for (int a = 0; a < n; ++a) {
+        double s = 0.0;
+        for (int b = 0; b < n; ++b) s += einv[(size_t)i * nn + a * n + b] * t[b];
+        z[(size_t)i * n + a] = y[(size_t)i * n + a] - s;
+      }
+    }
+}
+
+Bsr bsr_view(int rows, int n, const int32_t* rp, const int32_t* ci, const double* val) {
+  Bsr A;
+  A.rows = A.cols = rows;
+  A.n = n;
+  A.rp.assign(rp, rp + rows + 1);
+  A.ci.assign(ci, ci + rp[rows]);
+  if (val) A.v.assign(val, val + (size_t)rp[rows] * n * n);
+  return A;
+}
+
 // Smoothed prolongation P = (I - omega_P D^{-1} A) P_tent with
 // omega_P = p_omega / rho, rho = max_i sum_j ||D_i^{-1} A_ij||_inf.
 // Row i's columns are the sorted aggregates of its neighbours; block
@@ -460,6 +597,10 @@ struct or_amg {
     double omega_p = 0.0;
     Bsr P, R, AP;
     int coarse_kind = -1;  // -1 not coarsest, 0 dense inverse, 1 sweeps
+    // multicolour DILU (smoother = 1); ncol = -1: this level keeps block Jacobi
+    std::vector<int32_t> colour;
+    int ncol = -1;
+    std::vector<double> einv;
   };
   int n = 0;
   or_config cfg{};
@@ -525,6 +666,10 @@ or_amg* or_amg_setup(int rows, int n, const int32_t* rp, const int32_t* ci, cons
   for (int l = 0;; ++l) {
     auto& L = h->lv[l];
     if (diag_inverses(L.A, L.dinv)) { *status = 6; return h; }
+    if (cfg->smoother == 1) {
+      L.ncol = colour_rows(L.A, L.colour);
+      if (L.ncol > 0 && dilu_factor(L.A, L.colour, L.einv)) { *status = 6; return h; }
+    }
     const int C = L.A.rows;
     bool last = C <= cfg->coarse_size || l == cfg->max_levels - 1;
     if (!last) {
@@ -550,6 +695,7 @@ int or_amg_resetup(or_amg* h, const double* val) {
   for (int l = 0; l < L; ++l) {
     auto& lev = h->lv[l];
     if (diag_inverses(lev.A, lev.dinv)) return 6;
+    if (lev.ncol > 0 && dilu_factor(lev.A, lev.colour, lev.einv)) return 6;
     if (lev.coarse_kind >= 0) return finish_coarsest(h, l);
     build_transfer(h, l);
   }
@@ -588,6 +734,40 @@ void or_amg_get_dinv(const or_amg* h, int l, double* dinv) {
   std::copy(h->lv[l].dinv.begin(), h->lv[l].dinv.end(), dinv);
 }
 
+int or_amg_get_dilu(const or_amg* h, int l, int32_t* colour, double* einv) {
+  const auto& L = h->lv[l];
+  if (L.ncol <= 0) return -1;
+  if (colour) std::copy(L.colour.begin(), L.colour.end(), colour);
+  if (einv) std::copy(L.einv.begin(), L.einv.end(), einv);
+  return L.ncol;
+}
+
+int or_colour(int rows, const int32_t* rp, const int32_t* ci, int32_t* colour) {
+  Bsr A = bsr_view(rows, 1, rp, ci, nullptr);
+  std::vector<int32_t> c;
+  const int nc = colour_rows(A, c);
+  std::copy(c.begin(), c.end(), colour);
+  return nc;
+}
+
+int or_dilu_factor(int rows, int n, const int32_t* rp, const int32_t* ci, const double* val,
+                   const int32_t* colour, double* einv) {
+  Bsr A = bsr_view(rows, n, rp, ci, val);
+  std::vector<int32_t> c(colour, colour + rows);
+  std::vector<double> e;
+  const int st = dilu_factor(A, c, e);
+  std::copy(e.begin(), e.end(), einv);
+  return st;
+}
+
+void or_dilu_apply(int rows, int n, const int32_t* rp, const int32_t* ci, const double* val,
+                   const int32_t* colour, int ncolours, const double* einv, const double* r, double* z) {
+  Bsr A = bsr_view(rows, n, rp, ci, val);
+  std::vector<int32_t> c(colour, colour + rows);
+  std::vector<double> e(einv, einv + (size_t)rows * n * n);
+  dilu_apply(A, c, ncolours, e, r, z);
+}
+
 void or_amg_get_coarse_inverse(const or_amg* h, double* inv) {
   std::copy(h->cinv.begin(), h->cinv.end(), inv);
 }
@@ -616,11 +796,49 @@ void jacobi_sweep(const Bsr& A, const std::vector<double>& dinv, double omega, c
     }
 }
 
+// DILU step x <- x + M^{-1} (b - A x)
+void dilu_sweep(const Bsr& A, const std::vector<int32_t>& colour, int ncol, const std::vector<double>& einv,
+                const double* b, std::vector<double>& x) {
+  const size_t N = (size_t)A.rows * A.n;
+  std::vector<double> r(N), d(N);
+  or_bsr_spmv(A.rows, A.n, A.rp.data(), A.ci.data(), A.v.data(), x.data(), r.data());
+  for (size_t e = 0; e < N; ++e) r[e] = b[e] - r[e];
+  dilu_apply(A, colour, ncol, einv, r.data(), d.data());
+  for (size_t e = 0; e < N; ++e) x[e] = x[e] + d[e];
+}
+
+void vcycle(const or_amg* h, int l, const double* b, std::vector<double>& x);
+
+// One smoothing step on level l with the configured smoother.
+void smooth(const or_amg* h, int l, const double* b, std::vector<double>& x) {
+  const auto& L = h->lv[l];
+  if (L.ncol > 0) dilu_sweep(L.A, L.colour, L.ncol, L.einv, b, x);
+  else jacobi_sweep(L.A, L.dinv, h->cfg.jacobi_omega, b, x);
+}
+
 void vcycle(const or_amg* h, int l, const double* b, std::vector<double>& x) {
   const auto& L = h->lv[l];
   const int n = h->n, nn = n * n, N = L.A.rows * n;
   const double om = h->cfg.jacobi_omega;
   x.assign(N, 0.0);
+  if (L.ncol > 0 && L.coarse_kind != 0) {
+    // DILU: every sweep, the first one included, is the general step from x
+    if (L.coarse_kind == 1) {
+      for (int s = 0; s < h->cfg.coarse_sweeps; ++s) smooth(h, l, b, x);
+      return;
+    }
+    for (int s = 0; s < h->cfg.nu1; ++s) smooth(h, l, b, x);
+    std::vector<double> r(N), bc((size_t)L.P.cols * n), xc;
+    or_bsr_spmv(L.A.rows, n, L.A.rp.data(), L.A.ci.data(), L.A.v.data(), x.data(), r.data());
+    for (int e = 0; e < N; ++e) r[e] = b[e] - r[e];
+    or_bsr_spmv(L.R.rows, n, L.R.rp.data(), L.R.ci.data(), L.R.v.data(), r.data(), bc.data());
+    vcycle(h, l + 1, bc.data(), xc);
+    std::vector<double> px(N);
+    or_bsr_spmv(L.P.rows, n, L.P.rp.data(), L.P.ci.data(), L.P.v.data(), xc.data(), px.data());
+    for (int e = 0; e < N; ++e) x[e] = x[e] + px[e];
+    for (int s = 0; s < h->cfg.nu2; ++s) smooth(h, l, b, x);
+    return;
+  }
   if (L.coarse_kind == 0) {
     for (int r = 0; r < N; ++r) {
       double t = 0.0;

@@ -51,7 +51,8 @@ typedef struct {
   double max_coarsen_ratio; /* stop if C_{l+1} > ratio * C_l */
   double p_omega;        /* prolongation smoothing numerator: omega_P = p_omega / rho */
   int coarse_dense_max;  /* dense inverse at the coarsest level if rows*n <= this */
-  int coarse_sweeps;     /* otherwise this many block-Jacobi sweeps */
+  int coarse_sweeps;     /* otherwise this many smoother sweeps */
+  int smoother;          /* 0 = damped block Jacobi, 1 = multicolour block DILU */
 } or_config;
 
 typedef struct {
@@ -103,6 +104,29 @@ void or_block_norms(int nblocks, int n, const double* val, double* nrm);
 int or_aggregate(int rows, int n, const int32_t* row_ptr, const int32_t* col,
                  const double* val, const or_config* cfg, int32_t* agg);
 
+/* ---- multicolour block DILU (Sec. 4: the GPU runs' smoother) ---------- *
+ * Colouring: synchronous Jones-Plassmann rounds. Row priority = (h(i), i)
+ * with h the 32-bit "lowbias32" integer hash (xorshift-multiply, constants
+ * 0x7feb352d and 0x846ca68b). In a round every uncoloured row whose priority
+ * exceeds that of all its uncoloured neighbours takes the smallest colour
+ * not held by a neighbour coloured in an earlier round. Returns the number
+ * of colours, or -1 if some row would need colour >= 128 (the level then
+ * keeps block Jacobi). colour[rows].
+ * Factor (j before i iff colour(j) < colour(i)):
+ *   E_i = A_ii - sum over j before i, A_ij != 0, columns ascending, of
+ *         (A_ij E_j^{-1}) A_ji, each block product an fma chain from +0;
+ *   einv_i = E_i^{-1} (Gauss-Jordan as or_dense_inverse). Returns 0 or 1
+ *   (singular E_i).
+ * Apply z = M^{-1} r, M = (E + L) E^{-1} (E + U), L / U the blocks A_ij with
+ * j before / after i: forward y_i = E_i^{-1} (r_i - sum_{j before i} A_ij y_j)
+ * by colours ascending, backward z_i = y_i - E_i^{-1} sum_{j after i} A_ij z_j
+ * by colours descending. The smoother step is x <- x + M^{-1} (b - A x). */
+int or_colour(int rows, const int32_t* row_ptr, const int32_t* col, int32_t* colour);
+int or_dilu_factor(int rows, int n, const int32_t* row_ptr, const int32_t* col, const double* val,
+                   const int32_t* colour, double* einv);
+void or_dilu_apply(int rows, int n, const int32_t* row_ptr, const int32_t* col, const double* val,
+                   const int32_t* colour, int ncolours, const double* einv, const double* r, double* z);
+
 /* ---- AMG hierarchy ---------------------------------------------------- */
 typedef struct or_amg or_amg;
 
@@ -124,6 +148,9 @@ void or_amg_get_A(const or_amg* h, int l, int32_t* row_ptr, int32_t* col, double
 void or_amg_get_P(const or_amg* h, int l, int32_t* row_ptr, int32_t* col, double* val,
                   int32_t* agg, double* omega_p);
 void or_amg_get_dinv(const or_amg* h, int l, double* dinv);
+/* DILU data of level l (smoother = 1): returns the number of colours (-1 when
+ * the level keeps block Jacobi); colour[rows] and einv[rows][n][n] may be NULL. */
+int or_amg_get_dilu(const or_amg* h, int l, int32_t* colour, double* einv);
 void or_amg_get_coarse_inverse(const or_amg* h, double* inv);
 /* z = M^{-1} v: one V-cycle from a zero initial guess. */
 void or_amg_vcycle(const or_amg* h, const double* v, double* z);
