@@ -277,12 +277,14 @@ def run_native(args):
         ktimes = sp.kernel_times()
         kinds = sp.stats()["kinds"]
     # all-FP64 comparison (same step, FP64 AMG) and BF16-stored AMG
-    ms_fp64, res_fp64, ms_bf16, res_bf16 = None, None, None, None
+    ms_fp64, res_fp64, ms_bf16, res_bf16, ms_dilu, res_dilu = None, None, None, None, None, None
     if not args.no_fp64:
         with bcs.Solver(n, precision=bcs.BCS_PREC_FP64) as s64:
             ms_fp64, res_fp64, _ = timed(s64, d, x, max(1, min(args.steps, 3)), 1)
         with bcs.Solver(n, precision=bcs.BCS_PREC_BF16) as s16:
             ms_bf16, res_bf16, _ = timed(s16, d, x, max(1, min(args.steps, 3)), 1)
+        with bcs.Solver(n, precision=bcs.BCS_PREC_FP32, smoother=bcs.BCS_SMOOTH_DILU) as sd:
+            ms_dilu, res_dilu, _ = timed(sd, d, x, max(1, min(args.steps, 3)), 1)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -334,6 +336,9 @@ def run_native(args):
                                               "speedup_mixed_vs_fp64": ms_fp64 / ms_mixed},
         "bf16": None if ms_bf16 is None else {"value": ms_bf16, "unit": "ms", "iters": res_bf16[-1]["iters"],
                                               "rel_res_final": res_bf16[-1]["rel_res_final"]},
+        "dilu": None if ms_dilu is None else {"value": ms_dilu, "unit": "ms", "iters": res_dilu[-1]["iters"],
+                                              "rel_res_final": res_dilu[-1]["rel_res_final"],
+                                              "smoother": "multicolour block DILU, FP32 storage"},
         "resetup_ms": resetup_ms,
         "roofline": roofline,
         "kernel_breakdown": breakdown,

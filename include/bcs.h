@@ -68,6 +68,13 @@ enum { BCS_PREC_FP64 = 0, BCS_PREC_FP32 = 1, BCS_PREC_BF16 = 2 };
 
 /* Solver options (Alg. 1: "initialize with linear solver options"). Fill with
  * bcs_config_default(), then override fields. */
+/* Smoothers of the V-cycle (Sec. 4 names DILU for the GPU runs). DILU:
+ * rows are coloured (Jones-Plassmann, first-fit, lowbias32 priorities, at
+ * most 128 colours; a level needing more keeps block Jacobi); j precedes i
+ * when colour(j) < colour(i); E_i = A_ii - sum_{j before i} A_ij E_j^-1 A_ji;
+ * M = (E + L) E^-1 (E + U); one step x <- x + M^-1 (b - A x). */
+enum { BCS_SMOOTH_JACOBI = 0, BCS_SMOOTH_DILU = 1 };
+
 typedef struct bcs_config {
   int solver;              /* BCS_FGMRES (default) or BCS_BICGSTAB */
   int restart;             /* FGMRES restart length m (default 30, 1..64) */
@@ -86,6 +93,8 @@ typedef struct bcs_config {
   int coarse_dense_max;    /* dense inverse at the coarsest level when rows*n <= this (1024) */
   int coarse_sweeps;       /* else this many block-Jacobi sweeps there (8) */
   int precision;           /* AMG storage: BCS_PREC_FP64, BCS_PREC_FP32 (default), BCS_PREC_BF16 */
+  int smoother;            /* BCS_SMOOTH_JACOBI (default, damped by jacobi_omega) or
+                              BCS_SMOOTH_DILU (multicolour block DILU, undamped) */
   int profile;             /* 1: time kernels with CUDA events (bcs_get_stats) */
   int profile_kinds;       /* with profile = 1: bitmask of the kernel kinds to time (bit k:
                               kind k of bcs_kernel_kind_name); 0 = every kind */
@@ -199,6 +208,10 @@ BCS_API bcs_status bcs_get_prolongation(bcs_solver* s, int l, int32_t* row_ptr, 
                                 double* val, double* omega_p);
 /* Dense inverse of the coarsest matrix, [N][N] with N = rows * n. */
 BCS_API bcs_status bcs_get_coarse_inverse(bcs_solver* s, double* inv);
+/* DILU data of level l (smoother = BCS_SMOOTH_DILU): *ncolours = number of
+ * colours, or -1 when the level keeps block Jacobi (then nothing is copied);
+ * colour[rows] and einv[rows][n][n] (FP64 E_i^{-1}) may be NULL. */
+BCS_API bcs_status bcs_get_dilu(bcs_solver* s, int level, int* ncolours, int32_t* colour, double* einv);
 
 /* Statistics (launch counts always; times only with cfg.profile = 1). */
 BCS_API bcs_status bcs_get_stats(bcs_solver* s, bcs_stats* st);

@@ -23,6 +23,7 @@ BCS_FGMRES, BCS_BICGSTAB = 0, 1
 BCS_PC_AMG, BCS_PC_NONE, BCS_PC_JACOBI = 0, 1, 2
 BCS_P_SMOOTHED, BCS_P_TENTATIVE = 0, 1
 BCS_PREC_FP64, BCS_PREC_FP32, BCS_PREC_BF16 = 0, 1, 2
+BCS_SMOOTH_JACOBI, BCS_SMOOTH_DILU = 0, 1
 NUM_KERNEL_KINDS = 16
 
 
@@ -33,7 +34,7 @@ class bcs_config(ct.Structure):
         ("agg_passes", ct.c_int), ("jacobi_omega", ct.c_double), ("nu1", ct.c_int), ("nu2", ct.c_int),
         ("coarse_size", ct.c_int), ("max_levels", ct.c_int), ("max_coarsen_ratio", ct.c_double),
         ("p_omega", ct.c_double), ("coarse_dense_max", ct.c_int), ("coarse_sweeps", ct.c_int),
-        ("precision", ct.c_int), ("profile", ct.c_int), ("profile_kinds", ct.c_int),
+        ("precision", ct.c_int), ("smoother", ct.c_int), ("profile", ct.c_int), ("profile_kinds", ct.c_int),
         ("slice_layout", ct.c_int), ("cycle_graph", ct.c_int),
     ]
 
@@ -98,6 +99,7 @@ def lib():
             "bcs_get_level": (ct.c_int, [_vp, ct.c_int] + [_vp] * 5),
             "bcs_get_prolongation": (ct.c_int, [_vp, ct.c_int] + [_vp] * 3 + [ct.POINTER(ct.c_double)]),
             "bcs_get_coarse_inverse": (ct.c_int, [_vp, _vp]),
+            "bcs_get_dilu": (ct.c_int, [_vp, ct.c_int, ct.POINTER(ct.c_int), _vp, _vp]),
             "bcs_get_stats": (ct.c_int, [_vp, ct.POINTER(bcs_stats)]),
             "bcs_reset_stats": (ct.c_int, [_vp]),
             "bcs_get_kernel_times": (ct.c_int, [_vp, ct.c_char_p, ct.c_size_t]),
@@ -128,7 +130,7 @@ def exported_names():
     return ["bcs_config_default", "bcs_create", "bcs_destroy", "bcs_set_config", "bcs_set_structure",
             "bcs_set_values", "bcs_invalidate_hierarchy", "bcs_solve", "bcs_spmv", "bcs_precond_apply",
             "bcs_get_bsr", "bcs_num_levels", "bcs_get_level_info", "bcs_get_level", "bcs_get_prolongation",
-            "bcs_get_coarse_inverse", "bcs_get_stats", "bcs_reset_stats", "bcs_get_kernel_times", "bcs_kernel_kind_name",
+            "bcs_get_coarse_inverse", "bcs_get_dilu", "bcs_get_stats", "bcs_reset_stats", "bcs_get_kernel_times", "bcs_kernel_kind_name",
             "bcs_last_error", "bcs_device_bytes", "bcs_ldu_structure_noalloc", "bcs_server_create",
             "bcs_server_destroy", "bcs_server_register_case", "bcs_server_submit", "bcs_server_wait",
             "bcs_server_get_stats", "bcs_server_reset_stats"]
@@ -280,6 +282,15 @@ def bcs_get_prolongation(h, l, n):
     return dict(rows=i["rows"], n=n, row_ptr=rp, col=col, val=val, omega=om.value)
 
 
+def bcs_get_dilu(h, l, rows, n):
+    """(ncolours, colour[rows], einv[rows][n][n]) of level l, or (-1, None, None)."""
+    nc = ct.c_int()
+    col = np.zeros(rows, np.int32)
+    einv = np.zeros((rows, n, n))
+    _check(lib().bcs_get_dilu(h, l, ct.byref(nc), col.ctypes.data, einv.ctypes.data), h)
+    return (nc.value, col, einv) if nc.value > 0 else (-1, None, None)
+
+
 def bcs_get_coarse_inverse(h, N):
     out = np.zeros((N, N))
     _check(lib().bcs_get_coarse_inverse(h, out.ctypes.data), h)
@@ -423,6 +434,9 @@ class Solver:
 
     def prolongation(self, l):
         return bcs_get_prolongation(self.h, l, self.n)
+
+    def dilu(self, l):
+        return bcs_get_dilu(self.h, l, self.level_info(l)["rows"], self.n)
 
     def coarse_inverse(self):
         info = self.level_info(self.levels - 1)

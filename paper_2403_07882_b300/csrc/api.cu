@@ -104,6 +104,7 @@ bcs_status check_config(const bcs_config* c) {
   if (c->precision < BCS_PREC_FP64 || c->precision > BCS_PREC_BF16) return BCS_EINVAL;
   if (c->cycle_graph < -1 || c->cycle_graph > 1) return BCS_EINVAL;
   if (c->slice_layout < -1 || c->slice_layout > 1) return BCS_EINVAL;
+  if (c->smoother != BCS_SMOOTH_JACOBI && c->smoother != BCS_SMOOTH_DILU) return BCS_EINVAL;
   if (!(c->max_coarsen_ratio > 0.0) || !(c->p_omega > 0.0) || !(c->jacobi_omega > 0.0)) return BCS_EINVAL;
   return BCS_OK;
 }
@@ -114,7 +115,8 @@ bool same_hierarchy_options(const bcs_config& a, const bcs_config& b) {
          a.coarse_size == b.coarse_size && a.max_levels == b.max_levels &&
          a.max_coarsen_ratio == b.max_coarsen_ratio && a.p_omega == b.p_omega &&
          a.coarse_dense_max == b.coarse_dense_max && a.coarse_sweeps == b.coarse_sweeps &&
-         a.precision == b.precision && a.slice_layout == b.slice_layout;
+         a.precision == b.precision && a.slice_layout == b.slice_layout &&
+         a.smoother == b.smoother;
 }
 
 // Copy a host array into a device staging buffer (or pass a device pointer).
@@ -169,6 +171,7 @@ bcs_status bcs_config_default(bcs_config* c) {
   c->precision = BCS_PREC_FP32;
   c->profile = 0;
   c->profile_kinds = 0;
+  c->smoother = BCS_SMOOTH_JACOBI;
   c->slice_layout = -1;
   c->cycle_graph = -1;
   return BCS_OK;
@@ -440,6 +443,18 @@ bcs_status bcs_get_coarse_inverse(bcs_solver* h, double* inv) {
   Solver* s = &h->impl;
   if (!s->have_hierarchy || s->lv.back().coarse_kind != 0) return s->fail(BCS_EINVAL, "no dense coarse inverse");
   return to_host(s, inv, s->cinv.p, (size_t)s->cN * s->cN * sizeof(double));
+}
+
+bcs_status bcs_get_dilu(bcs_solver* h, int level, int* ncolours, int32_t* colour, double* einv) {
+  if (!h || !ncolours) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  if (!s->have_hierarchy || level < 0 || level >= (int)s->lv.size()) return s->fail(BCS_EINVAL, "no such level");
+  const Level& L = s->lv[level];
+  *ncolours = L.ncol > 0 ? L.ncol : -1;
+  if (L.ncol <= 0) return BCS_OK;
+  if (colour) BCS_OKR(to_host(s, colour, L.colour.p, (size_t)L.A.rows * sizeof(int32_t)));
+  if (einv) BCS_OKR(to_host(s, einv, L.einv.p, (size_t)L.A.rows * s->n * s->n * sizeof(double)));
+  return BCS_OK;
 }
 
 bcs_status bcs_get_stats(bcs_solver* h, bcs_stats* st) {

@@ -75,6 +75,50 @@ __global__ void __launch_bounds__(128) k_rows(int rows, const int32_t* __restric
   else y[o] = (TY)((AT)b[o] - acc);
 }
 
+// ---- multicolour DILU sweeps (one launch per colour) -------------------------
+// Rows of colour c (list rows_c), lane (w, r) = scalar row r of the w-th row.
+// Forward:  y_i = E_i^{-1} (r_i - sum_{colour(j) < c} A_ij y_j).
+// Backward: d_i = y_i - E_i^{-1} sum_{colour(j) > c} A_ij d_j;  x_i += d_i.
+template <int N, class AT, class TV, class TD, class TC, bool FWD>
+__global__ void __launch_bounds__(128) k_dilu_sweep(int cnt, const int32_t* __restrict__ rows_c, int c,
+                                                    const int32_t* __restrict__ colour,
+                                                    const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                    const TV* __restrict__ val, const TD* __restrict__ einv,
+                                                    const TC* __restrict__ r, TC* __restrict__ y,
+                                                    TC* __restrict__ d, TC* __restrict__ x) {
+  RowMap<N> m(cnt);
+  const int i = m.active ? __ldg(rows_c + m.i) : 0;
+  AT acc = 0;
+  if (m.active) {
+    const int kb = __ldg(rp + i), ke = __ldg(rp + i + 1);
+    for (int k = kb; k < ke; ++k) {
+      const int j = __ldg(ci + k);
+      const int cj = __ldg(colour + j);
+      if (FWD ? cj >= c : cj <= c) continue;
+      const TV* a = val + (size_t)k * (N * N) + m.r * N;
+      const TC* v = (FWD ? y : d) + (size_t)j * N;
+#pragma unroll
+      for (int cc = 0; cc < N; ++cc) acc = fma(lda<AT>(a + cc), (AT)v[cc], acc);
+    }
+  }
+  const size_t o = (size_t)i * N + m.r;
+  const AT t = m.active ? (FWD ? (AT)r[o] - acc : acc) : (AT)0;
+  AT s = 0;
+#pragma unroll
+  for (int cc = 0; cc < N; ++cc) {
+    const AT tc = __shfl_sync(0xffffffffu, t, (m.rw * N + cc) & 31);
+    if (m.active) s = fma(lda<AT>(einv + o * N + cc), tc, s);
+  }
+  if (!m.active) return;
+  if (FWD) {
+    y[o] = (TC)s;
+  } else {
+    const AT dv = (AT)y[o] - s;
+    d[o] = (TC)dv;
+    x[o] = (TC)((AT)x[o] + dv);
+  }
+}
+
 // ---- sliced (SELL) copy for the FP32 / BF16 cycle ---------------------------
 // A slice is floor(32/n) consecutive block rows served by one warp (lane l:
 // scalar row r = l % n of block row rw = l / n). Step t of a slice holds the
@@ -500,6 +544,34 @@ struct Cycle {
     }
     return BCS_OK;
   }
+  static const TV* dmat(const Level& L);
+  static const TD* deinv(const Level& L);
+
+  // One DILU step x <- x + M^{-1} (b - A x).
+  template <int N>
+  bcs_status dilu_step(const Level& L, TC* x, const TC* b) {
+    TC* r = (TC*)L.vr.p;
+    TC* y = (TC*)L.vt.p;
+    TC* d = (TC*)L.vd.p;
+    BCS_OKR(resid<N>(L, x, b, r));
+    const double per_row = (double)N * N * sizeof(TV) + N * N * sizeof(TD) + 3.0 * N * sizeof(TC);
+    for (int c = 0; c < L.ncol; ++c) {
+      const int b0 = L.cstart[c], m = L.cstart[c + 1] - b0;
+      if (m > 0)
+        BCS_LAUNCH(s, K_SWEEP, per_row * m, 2.0 * m * N * N, (k_dilu_sweep<N, AT, TV, TD, TC, true>),
+                   rows_grid(m, N), 128, 0, m, L.crow.p + b0, c, L.colour.p, L.A.rp.p, L.A.ci.p, dmat(L),
+                   deinv(L), r, y, d, x);
+    }
+    for (int c = L.ncol - 1; c >= 0; --c) {
+      const int b0 = L.cstart[c], m = L.cstart[c + 1] - b0;
+      if (m > 0)
+        BCS_LAUNCH(s, K_SWEEP, per_row * m, 2.0 * m * N * N, (k_dilu_sweep<N, AT, TV, TD, TC, false>),
+                   rows_grid(m, N), 128, 0, m, L.crow.p + b0, c, L.colour.p, L.A.rp.p, L.A.ci.p, dmat(L),
+                   deinv(L), r, y, d, x);
+    }
+    return BCS_OK;
+  }
+
   template <int N>
   bcs_status restrict_(const Level& L, const TC* r, TC* bc) {
     if (s->setup_cfg.pmode == BCS_P_TENTATIVE) {
@@ -552,6 +624,23 @@ struct Cycle {
                  grid_for((size_t)s->cN * 32, 256), 256, 0, s->cN, s->cinv.p, b, x);
       return BCS_OK;
     }
+    if (L.ncol > 0) {
+      // DILU: every step, the first included, is the general step from x = 0
+      BCS_CU(s, cudaMemsetAsync(x, 0, (size_t)L.A.rows * N * sizeof(TC), s->stream));
+      if (L.coarse_kind == 1) {
+        for (int k = 0; k < s->setup_cfg.coarse_sweeps; ++k) BCS_OKR(dilu_step<N>(L, x, b));
+        return BCS_OK;
+      }
+      for (int k = 0; k < nu1; ++k) BCS_OKR(dilu_step<N>(L, x, b));
+      Level& Lc = s->lv[l + 1];
+      TC* r = (TC*)L.vr.p;
+      BCS_OKR(resid<N>(L, x, b, r));
+      BCS_OKR(restrict_<N>(L, r, (TC*)Lc.vb.p));
+      BCS_OKR(run<N>(l + 1, (const TC*)Lc.vb.p, (TC*)Lc.vx.p));
+      BCS_OKR(prolong<N>(L, (const TC*)Lc.vx.p, x));
+      for (int k = 0; k < nu2; ++k) BCS_OKR(dilu_step<N>(L, x, b));
+      return BCS_OK;
+    }
     if (L.coarse_kind == 1) return sweeps_from_zero<N>(L, s->setup_cfg.coarse_sweeps, b, x, tmp);
     const int swaps = (nu1 > 1 ? nu1 - 1 : 0) + nu2;
     TC* cur = swaps % 2 == 0 ? x : tmp;
@@ -579,6 +668,12 @@ struct Cycle {
   }
 };
 
+template <> const double* Cycle<double, double, double, double>::dmat(const Level& L) { return L.A.v.p; }
+template <> const double* Cycle<double, double, double, double>::deinv(const Level& L) { return L.einv.p; }
+template <> const float* Cycle<float, float, float, float>::dmat(const Level& L) { return L.a32.p; }
+template <> const float* Cycle<float, float, float, float>::deinv(const Level& L) { return L.einv32.p; }
+template <> const bf16* Cycle<bf16, float, float, float>::dmat(const Level& L) { return L.a16.p; }
+template <> const float* Cycle<bf16, float, float, float>::deinv(const Level& L) { return L.einv32.p; }
 template <> const double* Cycle<double, double, double, double>::mat(const Level& L) { return L.A.v.p; }
 template <> const double* Cycle<double, double, double, double>::dinv(const Level& L) { return L.dinv.p; }
 template <> const double* Cycle<double, double, double, double>::pmat(const Level& L) { return L.P.v.p; }
@@ -760,7 +855,9 @@ bcs_status cycle_prepare(Solver* s) {
     BCS_ALLOC(s, L.vb, N * vsz);
     BCS_ALLOC(s, L.vr, N * vsz);
     BCS_ALLOC(s, L.vt, N * vsz);
+    if (L.ncol > 0) BCS_ALLOC(s, L.vd, N * vsz);
     if (prec == BCS_PREC_FP64 || s->setup_cfg.precond != BCS_PC_AMG) continue;
+    BCS_OKR(dilu_prepare(s, L));
     BCS_ALLOC(s, L.dinv32, (size_t)L.A.rows * nn);
     BCS_OKR(cast_vec<double, float>(s, L.dinv.p, L.dinv32.p, (size_t)L.A.rows * nn));
     const bool smoothed = L.coarse_kind < 0 && s->setup_cfg.pmode == BCS_P_SMOOTHED;

@@ -1,0 +1,261 @@
+// Multicolour block DILU smoother (Sec. 4: the smoother of the paper's GPU
+// runs): colouring, colour-ordered FP64 factorisation, and the forward /
+// backward sweeps of one smoothing step x <- x + M^{-1} (b - A x) with
+// M = (E + L) E^{-1} (E + U), L / U the blocks A_ij whose column's colour is
+// lower / higher than the row's.
+//
+// Colouring: synchronous Jones-Plassmann rounds. A row's priority is
+// (h(i), i), h the 32-bit lowbias32 integer hash (xorshift-multiply rounds
+// with the constants 0x7feb352d and 0x846ca68b). In a round every uncoloured
+// row whose priority exceeds that of all its uncoloured neighbours takes the
+// smallest colour not held by a neighbour coloured in an earlier round.
+// Rounds read the previous round's colours only, so the result does not
+// depend on scheduling. At most 128 colours; a level that would need more
+// keeps block Jacobi.
+//
+// Factor: E_i = A_ii - sum over j with colour(j) < colour(i) and A_ij != 0,
+// columns ascending, of (A_ij E_j^{-1}) A_ji, each block product an fma chain
+// from +0 (m ascending); E_i^{-1} by the register Gauss-Jordan of the block
+// inverses. Rows of one colour are independent: one launch per colour.
+#include "gj.cuh"
+#include "internal.h"
+
+namespace bcs {
+
+namespace {
+
+constexpr int DILU_MAX_COLOURS = 128;
+
+__device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// One Jones-Plassmann round: cin -> cout; uncoloured rows after the round are
+// counted into *left (one atomic per warp); err |= 32 when a row would need a
+// colour >= 128.
+__global__ void k_jp_round(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const int32_t* __restrict__ cin, int32_t* __restrict__ cout, int32_t* __restrict__ left,
+                           int32_t* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int uncoloured = 0;
+  if (i < rows) {
+    int c = cin[i];
+    if (c < 0) {
+      const uint32_t hi = lowbias32((uint32_t)i);
+      bool top = true;
+      unsigned long long m0 = 0, m1 = 0;
+      for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        const int j = ci[k];
+        if (j == i) continue;
+        const int cj = cin[j];
+        if (cj < 0) {
+          const uint32_t hj = lowbias32((uint32_t)j);
+          if (hj > hi || (hj == hi && j > i)) top = false;
+        } else if (cj < 64) {
+          m0 |= 1ull << cj;
+        } else {
+          m1 |= 1ull << (cj - 64);
+        }
+      }
+      if (top) {
+        if (~m0) c = __ffsll((long long)~m0) - 1;
+        else if (~m1) c = 64 + __ffsll((long long)~m1) - 1;
+        else atomicOr(err, 32);
+      }
+      uncoloured = c < 0;
+    }
+    cout[i] = c;
+  }
+  const int u = __reduce_add_sync(0xffffffffu, uncoloured);
+  if ((threadIdx.x & 31) == 0 && u) atomicAdd(left, u);
+}
+
+// Per-colour row counts (block-local histogram, one atomic per colour and
+// block). blockDim >= DILU_MAX_COLOURS.
+__global__ void k_colour_count(int rows, const int32_t* __restrict__ colour, int32_t* __restrict__ cnt) {
+  __shared__ int32_t hist[DILU_MAX_COLOURS];
+  const int t = threadIdx.x, i = blockIdx.x * blockDim.x + t;
+  if (t < DILU_MAX_COLOURS) hist[t] = 0;
+  __syncthreads();
+  if (i < rows) atomicAdd(&hist[colour[i]], 1);
+  __syncthreads();
+  if (t < DILU_MAX_COLOURS && hist[t]) atomicAdd(&cnt[t], hist[t]);
+}
+
+// Rows grouped by colour: each block reserves one range per colour; the
+// order inside a colour does not matter (its rows are independent).
+__global__ void k_colour_place(int rows, const int32_t* __restrict__ colour, const int32_t* __restrict__ start,
+                               int32_t* __restrict__ cursor, int32_t* __restrict__ crow) {
+  __shared__ int32_t hist[DILU_MAX_COLOURS], base[DILU_MAX_COLOURS];
+  const int t = threadIdx.x, i = blockIdx.x * blockDim.x + t;
+  if (t < DILU_MAX_COLOURS) hist[t] = 0;
+  __syncthreads();
+  const int c = i < rows ? colour[i] : 0;
+  const int rank = i < rows ? atomicAdd(&hist[c], 1) : 0;
+  __syncthreads();
+  if (t < DILU_MAX_COLOURS && hist[t]) base[t] = atomicAdd(&cursor[t], hist[t]);
+  __syncthreads();
+  if (i < rows) crow[start[c] + base[c] + rank] = i;
+}
+
+// E_i^{-1} for the rows of colour c (one thread per row).
+template <int N>
+__global__ void __launch_bounds__(64) k_dilu_factor(int cnt, const int32_t* __restrict__ rows_c, int c,
+                                                    const int32_t* __restrict__ colour, const int32_t* __restrict__ rp,
+                                                    const int32_t* __restrict__ ci, const double* __restrict__ val,
+                                                    const int32_t* __restrict__ dpos, double* __restrict__ einv,
+                                                    int32_t* __restrict__ err) {
+  constexpr int NN = N * N;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= cnt) return;
+  const int i = rows_c[q];
+  BlockGJ<N> g;
+  const double* d = val + (size_t)dpos[i] * NN;
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+#pragma unroll
+    for (int cc = 0; cc < N; ++cc) g.M[r][cc] = d[r * N + cc];
+  for (int k = rp[i]; k < rp[i + 1]; ++k) {
+    const int j = ci[k];
+    if (colour[j] >= c) continue;
+    // position of A_ji in row j (columns ascending)
+    int b = rp[j], e = rp[j + 1], kt = -1;
+    while (b < e) {
+      const int m = (b + e) >> 1;
+      const int cm = ci[m];
+      if (cm == i) {
+        kt = m;
+        break;
+      }
+      if (cm < i) b = m + 1;
+      else e = m;
+    }
+    if (kt < 0) {
+      atomicOr(err, 128);  // structurally unsymmetric pattern
+      return;
+    }
+    const double* aij = val + (size_t)k * NN;
+    const double* ej = einv + (size_t)j * NN;
+    const double* aji = val + (size_t)kt * NN;
+    double W[NN];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+      for (int cc = 0; cc < N; ++cc) {
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < N; ++m) acc = fma(aij[r * N + m], ej[m * N + cc], acc);
+        W[r * N + cc] = acc;
+      }
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+      for (int cc = 0; cc < N; ++cc) {
+        double z = 0.0;
+#pragma unroll
+        for (int m = 0; m < N; ++m) z = fma(W[r * N + m], aji[m * N + cc], z);
+        g.M[r][cc] = g.M[r][cc] - z;
+      }
+  }
+  if (!gj_finish<N>(g, einv + (size_t)i * NN)) atomicOr(err, 64);
+}
+
+}  // namespace
+
+bcs_status dilu_setup(Solver* s, Level& L, bool full) {
+  const int rows = L.A.rows, n = s->n;
+  if (full) {
+    L.ncol = -1;
+    L.cstart.clear();
+    L.colour.release();
+    L.crow.release();
+    DBuf<int32_t> other, aux;
+    BCS_ALLOC(s, L.colour, rows);
+    BCS_ALLOC(s, other, rows);
+    BCS_ALLOC(s, aux, 2);
+    BCS_CU(s, cudaMemsetAsync(L.colour.p, 0xff, rows * sizeof(int32_t), s->stream));
+    BCS_CU(s, cudaMemsetAsync(aux.p + 1, 0, sizeof(int32_t), s->stream));
+    int32_t* cin = L.colour.p;
+    int32_t* cout = other.p;
+    int32_t h[2] = {1, 0};
+    // Rounds in batches of four between host checks; a round with nothing
+    // left to colour copies the colours unchanged.
+    for (int round = 0; h[0] > 0 && !(h[1] & 32); ++round) {
+      if (round > rows + 4) return s->fail(BCS_EINVAL, "colouring did not finish");
+      BCS_CU(s, cudaMemsetAsync(aux.p, 0, sizeof(int32_t), s->stream));
+      BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_jp_round, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, L.A.ci.p, cin,
+                 cout, aux.p, aux.p + 1);
+      std::swap(cin, cout);
+      if (round % 4 == 3) {
+        BCS_CU(s, cudaMemcpyAsync(h, aux.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+        BCS_CU(s, cudaStreamSynchronize(s->stream));
+      }
+    }
+    if (h[1] & 32) return BCS_OK;  // more than 128 colours: this level keeps block Jacobi
+    if (cin != L.colour.p) L.colour = std::move(other);
+    // colour lists
+    DBuf<int32_t> cnt, start, cursor;
+    BCS_ALLOC(s, cnt, DILU_MAX_COLOURS);
+    BCS_ALLOC(s, start, DILU_MAX_COLOURS + 1);
+    BCS_ALLOC(s, cursor, DILU_MAX_COLOURS);
+    BCS_CU(s, cudaMemsetAsync(cnt.p, 0, DILU_MAX_COLOURS * sizeof(int32_t), s->stream));
+    BCS_CU(s, cudaMemsetAsync(cursor.p, 0, DILU_MAX_COLOURS * sizeof(int32_t), s->stream));
+    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_colour_count, grid_for(rows, 256), 256, 0, rows, L.colour.p, cnt.p);
+    std::vector<int32_t> hc(DILU_MAX_COLOURS);
+    BCS_CU(s, cudaMemcpyAsync(hc.data(), cnt.p, DILU_MAX_COLOURS * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                              s->stream));
+    BCS_CU(s, cudaStreamSynchronize(s->stream));
+    int ncol = 0;
+    for (int c = 0; c < DILU_MAX_COLOURS; ++c)
+      if (hc[c] > 0) ncol = c + 1;
+    L.cstart.assign(ncol + 1, 0);
+    for (int c = 0; c < ncol; ++c) L.cstart[c + 1] = L.cstart[c] + hc[c];
+    BCS_CU(s, cudaMemcpyAsync(start.p, L.cstart.data(), (ncol + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                              s->stream));
+    BCS_ALLOC(s, L.crow, rows);
+    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_colour_place, grid_for(rows, 256), 256, 0, rows, L.colour.p, start.p,
+               cursor.p, L.crow.p);
+    // the host vector L.cstart is read by this copy: finish it before return
+    BCS_CU(s, cudaStreamSynchronize(s->stream));
+    L.ncol = ncol;
+  }
+  if (L.ncol <= 0) return BCS_OK;
+  BCS_ALLOC(s, L.einv, (size_t)rows * n * n);
+  BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    for (int c = 0; c < L.ncol; ++c) {
+      const int b = L.cstart[c], m = L.cstart[c + 1] - b;
+      if (m <= 0) continue;
+      BCS_LAUNCH(s, K_SETUP_INV, 8.0 * m * N * N * 8, 4.0 * m * N * N * N * 4, k_dilu_factor<N>, grid_for(m, 64),
+                 64, 0, m, L.crow.p + b, c, L.colour.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.dpos.p, L.einv.p,
+                 s->flag.p);
+    }
+    return BCS_OK;
+  }));
+  int32_t h = 0;
+  BCS_CU(s, cudaMemcpyAsync(&h, s->flag.p, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  if (h & 128) return s->fail(BCS_EINVAL, "DILU needs a structurally symmetric pattern");
+  if (h & 64) return s->fail(BCS_SINGULAR_BLOCK, "singular DILU diagonal block");
+  return BCS_OK;
+}
+
+bcs_status dilu_prepare(Solver* s, Level& L) {
+  if (L.ncol <= 0) return BCS_OK;
+  const size_t nn = (size_t)s->n * s->n;
+  BCS_ALLOC(s, L.einv32, (size_t)L.A.rows * nn);
+  BCS_OKR(cast_vec<double, float>(s, L.einv.p, L.einv32.p, (size_t)L.A.rows * nn));
+  if (s->setup_cfg.precision == BCS_PREC_BF16) {
+    BCS_ALLOC(s, L.a16, (size_t)L.A.nnz * nn);
+    return cast_vec<double, bf16>(s, L.A.v.p, L.a16.p, (size_t)L.A.nnz * nn);
+  }
+  BCS_ALLOC(s, L.a32, (size_t)L.A.nnz * nn);
+  return cast_vec<double, float>(s, L.A.v.p, L.a32.p, (size_t)L.A.nnz * nn);
+}
+
+}  // namespace bcs

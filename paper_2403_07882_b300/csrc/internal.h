@@ -122,6 +122,15 @@ struct Level {
   DBuf<float> s32;
   DBuf<bf16> s16;
   DBuf<char> vx, vb, vr, vt; // V-cycle vectors (cycle precision)
+  // multicolour block DILU smoother (smoother = 1); ncol = -1: block Jacobi
+  int ncol = -1;
+  DBuf<int32_t> colour;      // colour of each row
+  DBuf<int32_t> crow;        // rows grouped by colour: cstart[c] .. cstart[c+1]
+  std::vector<int> cstart;
+  DBuf<double> einv;         // E_i^{-1}, FP64
+  DBuf<float> einv32, a32;   // FP32 copies for the FP32 / BF16 cycle (a32: BSR values)
+  DBuf<bf16> a16;            // BF16 BSR values for the BF16 cycle
+  DBuf<char> vd;             // DILU correction vector (cycle precision)
 };
 
 struct Timer {
@@ -290,6 +299,12 @@ bcs_status cast_vec(Solver* s, const TI* in, TO* out, size_t N);
 
 // ------------------------------------------------------------------- setup.cu
 bcs_status amg_setup(Solver* s, bool full);
+// Multicolour DILU of level L: colouring and colour lists when full, then
+// the FP64 factor (E_i^{-1}); marks the level block-Jacobi (ncol = -1) when
+// it would need more than 128 colours.
+bcs_status dilu_setup(Solver* s, Level& L, bool full);
+// FP32 copies of a DILU level for the FP32 / BF16 cycle.
+bcs_status dilu_prepare(Solver* s, Level& L);
 
 // ------------------------------------------------------------------ krylov.cu
 bcs_status solve(Solver* s, const double* b_d, double* x_d, bcs_result* res);
