@@ -16,7 +16,11 @@
 // Factor: E_i = A_ii - sum over j with colour(j) < colour(i) and A_ij != 0,
 // columns ascending, of (A_ij E_j^{-1}) A_ji, each block product an fma chain
 // from +0 (m ascending); E_i^{-1} by the register Gauss-Jordan of the block
-// inverses. Rows of one colour are independent: one launch per colour.
+// inverses. Rows of one colour are independent: per colour one launch forms
+// E_i, a second inverts it (the Gauss-Jordan's registers kept out of the
+// accumulation pass).
+#include <algorithm>
+
 #include "gj.cuh"
 #include "internal.h"
 
@@ -103,66 +107,119 @@ __global__ void k_colour_place(int rows, const int32_t* __restrict__ colour, con
   if (i < rows) crow[start[c] + base[c] + rank] = i;
 }
 
-// E_i^{-1} for the rows of colour c (one thread per row).
+__device__ __forceinline__ int find_pos(const int32_t* __restrict__ ci, int b, int e, int col) {
+  while (b < e) {
+    const int m = (b + e) >> 1;
+    const int cm = ci[m];
+    if (cm == col) return m;
+    if (cm < col) b = m + 1;
+    else e = m;
+  }
+  return -1;
+}
+
+// E_i for the rows of colour c, written to E[q] (q = index in the colour's
+// list). n*n <= 32: one warp per row, lane (r, cc) holds E_i[r][cc]; per
+// earlier neighbour j it forms W[r][cc] = (A_ij E_j^{-1})[r][cc] and, from
+// its row's W by shuffles, Z[r][cc] = (W A_ji)[r][cc], each the fma chain of
+// the definition. Larger blocks: one thread per row, W one row at a time.
 template <int N>
-__global__ void __launch_bounds__(64) k_dilu_factor(int cnt, const int32_t* __restrict__ rows_c, int c,
+__global__ void __launch_bounds__(128) k_dilu_schur(int cnt, const int32_t* __restrict__ rows_c, int c,
                                                     const int32_t* __restrict__ colour, const int32_t* __restrict__ rp,
                                                     const int32_t* __restrict__ ci, const double* __restrict__ val,
-                                                    const int32_t* __restrict__ dpos, double* __restrict__ einv,
+                                                    const int32_t* __restrict__ dpos, const double* __restrict__ einv,
+                                                    double* __restrict__ E, int32_t* __restrict__ err) {
+  constexpr int NN = N * N;
+  if constexpr (NN <= 32) {
+    const int lane = threadIdx.x & 31;
+    const int q = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (q >= cnt) return;  // uniform across the warp
+    const int i = rows_c[q];
+    const bool act = lane < NN;
+    const int r = act ? lane / N : 0, cc = act ? lane - (lane / N) * N : 0;
+    double m = act ? val[(size_t)dpos[i] * NN + lane] : 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const int j = ci[k];
+      if (colour[j] >= c) continue;
+      const int kt = find_pos(ci, rp[j], rp[j + 1], i);
+      if (kt < 0) {
+        if (lane == 0) atomicOr(err, 128);  // structurally unsymmetric pattern
+        return;
+      }
+      const double* aij = val + (size_t)k * NN;
+      const double* ej = einv + (size_t)j * NN;
+      const double* aji = val + (size_t)kt * NN;
+      double w = 0.0;
+#pragma unroll
+      for (int mm = 0; mm < N; ++mm) w = fma(aij[r * N + mm], ej[mm * N + cc], w);
+      double z = 0.0;
+#pragma unroll
+      for (int mm = 0; mm < N; ++mm) {
+        const double wm = __shfl_sync(0xffffffffu, w, (r * N + mm) & 31);
+        z = fma(wm, aji[mm * N + cc], z);
+      }
+      m = m - z;
+    }
+    if (act) E[(size_t)q * NN + lane] = m;
+  } else {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cnt) return;
+    const int i = rows_c[q];
+    double M[NN];
+    const double* d = val + (size_t)dpos[i] * NN;
+#pragma unroll
+    for (int e = 0; e < NN; ++e) M[e] = d[e];
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const int j = ci[k];
+      if (colour[j] >= c) continue;
+      const int kt = find_pos(ci, rp[j], rp[j + 1], i);
+      if (kt < 0) {
+        atomicOr(err, 128);
+        return;
+      }
+      const double* aij = val + (size_t)k * NN;
+      const double* ej = einv + (size_t)j * NN;
+      const double* aji = val + (size_t)kt * NN;
+#pragma unroll
+      for (int r = 0; r < N; ++r) {
+        double w[N];
+#pragma unroll
+        for (int cc = 0; cc < N; ++cc) {
+          double acc = 0.0;
+#pragma unroll
+          for (int mm = 0; mm < N; ++mm) acc = fma(aij[r * N + mm], ej[mm * N + cc], acc);
+          w[cc] = acc;
+        }
+#pragma unroll
+        for (int cc = 0; cc < N; ++cc) {
+          double z = 0.0;
+#pragma unroll
+          for (int mm = 0; mm < N; ++mm) z = fma(w[mm], aji[mm * N + cc], z);
+          M[r * N + cc] = M[r * N + cc] - z;
+        }
+      }
+    }
+    double* o = E + (size_t)q * NN;
+#pragma unroll
+    for (int e = 0; e < NN; ++e) o[e] = M[e];
+  }
+}
+
+// E_i^{-1} for the rows of colour c from E (one thread per row).
+template <int N>
+__global__ void __launch_bounds__(64) k_dilu_invert(int cnt, const int32_t* __restrict__ rows_c,
+                                                    const double* __restrict__ E, double* __restrict__ einv,
                                                     int32_t* __restrict__ err) {
   constexpr int NN = N * N;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= cnt) return;
-  const int i = rows_c[q];
   BlockGJ<N> g;
-  const double* d = val + (size_t)dpos[i] * NN;
+  const double* a = E + (size_t)q * NN;
 #pragma unroll
   for (int r = 0; r < N; ++r)
 #pragma unroll
-    for (int cc = 0; cc < N; ++cc) g.M[r][cc] = d[r * N + cc];
-  for (int k = rp[i]; k < rp[i + 1]; ++k) {
-    const int j = ci[k];
-    if (colour[j] >= c) continue;
-    // position of A_ji in row j (columns ascending)
-    int b = rp[j], e = rp[j + 1], kt = -1;
-    while (b < e) {
-      const int m = (b + e) >> 1;
-      const int cm = ci[m];
-      if (cm == i) {
-        kt = m;
-        break;
-      }
-      if (cm < i) b = m + 1;
-      else e = m;
-    }
-    if (kt < 0) {
-      atomicOr(err, 128);  // structurally unsymmetric pattern
-      return;
-    }
-    const double* aij = val + (size_t)k * NN;
-    const double* ej = einv + (size_t)j * NN;
-    const double* aji = val + (size_t)kt * NN;
-    double W[NN];
-#pragma unroll
-    for (int r = 0; r < N; ++r)
-#pragma unroll
-      for (int cc = 0; cc < N; ++cc) {
-        double acc = 0.0;
-#pragma unroll
-        for (int m = 0; m < N; ++m) acc = fma(aij[r * N + m], ej[m * N + cc], acc);
-        W[r * N + cc] = acc;
-      }
-#pragma unroll
-    for (int r = 0; r < N; ++r)
-#pragma unroll
-      for (int cc = 0; cc < N; ++cc) {
-        double z = 0.0;
-#pragma unroll
-        for (int m = 0; m < N; ++m) z = fma(W[r * N + m], aji[m * N + cc], z);
-        g.M[r][cc] = g.M[r][cc] - z;
-      }
-  }
-  if (!gj_finish<N>(g, einv + (size_t)i * NN)) atomicOr(err, 64);
+    for (int cc = 0; cc < N; ++cc) g.M[r][cc] = a[r * N + cc];
+  if (!gj_finish<N>(g, einv + (size_t)rows_c[q] * NN)) atomicOr(err, 64);
 }
 
 }  // namespace
@@ -226,14 +283,20 @@ bcs_status dilu_setup(Solver* s, Level& L, bool full) {
   }
   if (L.ncol <= 0) return BCS_OK;
   BCS_ALLOC(s, L.einv, (size_t)rows * n * n);
+  int maxc = 0;
+  for (int c = 0; c < L.ncol; ++c) maxc = std::max(maxc, L.cstart[c + 1] - L.cstart[c]);
+  DBuf<double> E;
+  BCS_ALLOC(s, E, (size_t)maxc * n * n);
   BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
     for (int c = 0; c < L.ncol; ++c) {
       const int b = L.cstart[c], m = L.cstart[c + 1] - b;
       if (m <= 0) continue;
-      BCS_LAUNCH(s, K_SETUP_INV, 8.0 * m * N * N * 8, 4.0 * m * N * N * N * 4, k_dilu_factor<N>, grid_for(m, 64),
-                 64, 0, m, L.crow.p + b, c, L.colour.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.dpos.p, L.einv.p,
-                 s->flag.p);
+      const unsigned gs = N * N <= 32 ? grid_for((size_t)m * 32, 128) : grid_for(m, 128);
+      BCS_LAUNCH(s, K_SETUP_INV, 8.0 * m * N * N * 4, 4.0 * m * N * N * N * 3, k_dilu_schur<N>, gs, 128, 0, m,
+                 L.crow.p + b, c, L.colour.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.dpos.p, L.einv.p, E.p, s->flag.p);
+      BCS_LAUNCH(s, K_SETUP_INV, 16.0 * m * N * N, 4.0 * m * N * N * N, k_dilu_invert<N>, grid_for(m, 64), 64, 0,
+                 m, L.crow.p + b, E.p, L.einv.p, s->flag.p);
     }
     return BCS_OK;
   }));

@@ -321,7 +321,7 @@ __device__ __forceinline__ double plus_zero(double v) {
 }
 
 template <int NN>
-__global__ void __launch_bounds__(256) k_list_sum(unsigned nout, const int32_t* __restrict__ gptr,
+__global__ void __launch_bounds__(256, 6) k_list_sum(unsigned nout, const int32_t* __restrict__ gptr,
                                                   const int32_t* __restrict__ glist,
                                                   const double* __restrict__ src, double* __restrict__ out) {
   const unsigned total = nout * NN;
