@@ -305,6 +305,42 @@ void galerkin(const Bsr& A, const Bsr& P, Bsr& R, Bsr& AP, Bsr& Ac) {
   spgemm(R, AP, Ac);
 }
 
+// Galerkin product with the piecewise-constant (tentative) P: block (I, J)
+// of P^T A P is the sum of the fine blocks A_ij with agg(i) = I and
+// agg(j) = J, taken directly from its definition: rows i of aggregate I in
+// ascending order, each row's blocks in ascending column order, a plain
+// left-to-right FP64 sum from +0. Columns of row I: the sorted aggregates
+// of its rows' columns.
+void galerkin_tentative(const Bsr& A, const std::vector<int32_t>& agg, int nagg, Bsr& Ac) {
+  const int n = A.n, nn = n * n;
+  std::vector<std::vector<int>> members(nagg);
+  for (int i = 0; i < A.rows; ++i) members[agg[i]].push_back(i);
+  Ac.rows = Ac.cols = nagg;
+  Ac.n = n;
+  Ac.rp.assign(nagg + 1, 0);
+  Ac.ci.clear();
+  for (int I = 0; I < nagg; ++I) {
+    std::vector<int> cols;
+    for (int i : members[I])
+      for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) cols.push_back(agg[A.ci[k]]);
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+    Ac.ci.insert(Ac.ci.end(), cols.begin(), cols.end());
+    Ac.rp[I + 1] = (int32_t)Ac.ci.size();
+  }
+  Ac.v.assign((size_t)Ac.nnz() * nn, 0.0);
+  for (int I = 0; I < nagg; ++I)
+    for (int q = Ac.rp[I]; q < Ac.rp[I + 1]; ++q) {
+      const int J = Ac.ci[q];
+      double* acc = Ac.blk(q);
+      for (int i : members[I])
+        for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+          if (agg[A.ci[k]] != J) continue;
+          for (int e = 0; e < nn; ++e) acc[e] = acc[e] + A.blk(k)[e];
+        }
+    }
+}
+
 // One matching pass on the graph of A, weights from block norms.
 int match_pass(const Bsr& A, const or_config& cfg, std::vector<int32_t>& agg) {
   const int C = A.rows, nnz = A.nnz();
@@ -370,8 +406,8 @@ int aggregate(const Bsr& A, const or_config& cfg, std::vector<int32_t>& agg) {
   const Bsr* cur = &A;
   std::vector<int32_t> cur_agg = agg;
   for (int pass = 1; pass < cfg.agg_passes; ++pass) {
-    Bsr P = tentative_P(cur->rows, A.n, cur_agg, nagg), R, AP, Abar;
-    galerkin(*cur, P, R, AP, Abar);
+    Bsr Abar;
+    galerkin_tentative(*cur, cur_agg, nagg, Abar);
     std::vector<int32_t> a2;
     int n2 = match_pass(Abar, cfg, a2);
     for (int i = 0; i < A.rows; ++i) agg[i] = a2[agg[i]];
@@ -640,7 +676,12 @@ void build_transfer(or_amg* h, int l) {
     smoothed_P(L.A, L.dinv, L.agg, L.nagg, h->cfg.p_omega, L.P, L.omega_p);
   }
   Bsr Ac;
-  galerkin(L.A, L.P, L.R, L.AP, Ac);
+  if (h->cfg.pmode == 1) {
+    transpose(L.P, L.R);
+    galerkin_tentative(L.A, L.agg, L.nagg, Ac);
+  } else {
+    galerkin(L.A, L.P, L.R, L.AP, Ac);
+  }
   if ((int)h->lv.size() <= l + 1) h->lv.emplace_back();
   h->lv[l + 1].A = std::move(Ac);
 }

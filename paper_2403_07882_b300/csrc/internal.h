@@ -103,9 +103,9 @@ struct Level {
   int nagg = 0;
   DBuf<int32_t> agg;         // aggregate of each row
   DBuf<int32_t> mptr, mem;   // aggregate member lists (members ascending)
-  Bsr P, R, AP;              // P, R: smoothed mode only; AP pattern kept for resetup (FP64)
+  Bsr P, R, AP;              // smoothed mode only: P, R and the product A P (FP64)
   DBuf<int32_t> Prow, Rrow, AProw, Crow;  // row of every nonzero of P, R, AP, A_{l+1}
-  DBuf<int32_t> apg_ptr, apg_list, cg_ptr, cg_list;  // tentative product gather lists
+  DBuf<int32_t> cg_ptr, cg_list;  // tentative Galerkin product gather lists
   DBuf<float> P32, R32;
   DBuf<bf16> P16, R16;
   double omega_p = 0.0;

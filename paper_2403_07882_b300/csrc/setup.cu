@@ -217,38 +217,35 @@ __global__ void k_compact(int rows, const int32_t* __restrict__ cptr, const int3
   for (int q = 0; q < len; ++q) ci[o + q] = cand[b + q];
 }
 
-// Tentative Galerkin pattern and gather lists from one sort per product.
-// A candidate packs (output column J) << 32 | (source block position); the
-// candidates of an output row are sorted ascending, so each run of equal J is
-// one output block and lists its sources in ascending position, which is the
-// summation order of the product.
-__global__ void k_pack_ap(int nnz, const int32_t* __restrict__ ci, const int32_t* __restrict__ agg,
-                          uint64_t* __restrict__ cand) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < nnz) cand[p] = ((uint64_t)(uint32_t)agg[ci[p]] << 32) | (uint32_t)p;
-}
+// Tentative Galerkin pattern and gather lists from one segmented sort. A
+// candidate packs (coarse column agg(j)) << 32 | (fine block position); the
+// candidates of coarse row I are the blocks of its member rows, sorted
+// ascending, so each run of equal column is one coarse block and lists its
+// fine blocks in ascending position (members ascending, columns ascending
+// within a row), the summation order of the definition.
 
-// Candidate count of A_c's row I (the AP rows of its members); longest -> *mx.
-__global__ void k_count_ac(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
-                           const int32_t* __restrict__ aprp, int32_t* __restrict__ cnt, int32_t* __restrict__ mx) {
+// Candidate count of coarse row I (its members' row lengths); longest -> *mx.
+__global__ void k_cand_count_tent(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
+                                  const int32_t* __restrict__ rp, int32_t* __restrict__ cnt, int32_t* __restrict__ mx) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   int c = 0;
   if (I < nagg)
-    for (int q = mptr[I]; q < mptr[I + 1]; ++q) c += aprp[mem[q] + 1] - aprp[mem[q]];
+    for (int q = mptr[I]; q < mptr[I + 1]; ++q) c += rp[mem[q] + 1] - rp[mem[q]];
   const int m = __reduce_max_sync(0xffffffffu, c);
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(mx, m);
   if (I < nagg) cnt[I] = c;
 }
 
-__global__ void k_pack_ac(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
-                          const int32_t* __restrict__ aprp, const int32_t* __restrict__ apci,
-                          const int32_t* __restrict__ cptr, uint64_t* __restrict__ cand) {
+__global__ void k_cand_pack_tent(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
+                                 const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                 const int32_t* __restrict__ agg, const int32_t* __restrict__ cptr,
+                                 uint64_t* __restrict__ cand) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nagg) return;
   int o = cptr[I];
   for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
     const int i = mem[q];
-    for (int a = aprp[i]; a < aprp[i + 1]; ++a) cand[o++] = ((uint64_t)(uint32_t)apci[a] << 32) | (uint32_t)a;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) cand[o++] = ((uint64_t)(uint32_t)agg[ci[p]] << 32) | (uint32_t)p;
   }
 }
 
@@ -296,24 +293,17 @@ __global__ void k_runs_emit(int rows, const int32_t* __restrict__ seg, const uin
   if (i == rows - 1) gptr[rp[rows]] = seg[rows];
 }
 
-// R A P with tentative P (identity blocks), as the two products of its
-// definition, which is also how the general block product orders the sums
-// (fma(a, 1, acc) = acc + a, fma(a, 0, acc) = acc):
-//   AP(i, J)   = sum over row i's blocks k (ascending) with agg(col k) = J of A_k
-//   A_c(I, J)  = sum over members i of I (ascending) with J in AP's row i of AP(i, J)
-// each a plain left-to-right FP64 sum from +0. The contributing positions of
-// every output block are listed once per structure (full setup), in
-// summation order; the value passes then gather a few blocks per output with
-// one thread per (block, element), so the n*n threads of an output read each
-// source block as one coalesced span.
-
-// out[q] = sum over list[gptr[q] .. gptr[q+1]) of src[list[p]] (n*n blocks),
-// plain FP64 adds from +0 in list order. The first add 0 + v equals v except
-// that -0 becomes +0, so the sum starts from its first term with that sign
-// fix (integer operations) and only the remaining terms use the FP64 pipe.
-// Each thread serves LS_OUT outputs (elements t, t + T, ...) whose dependent
-// load chains it interleaves, so enough loads are in flight.
-constexpr int LS_OUT = 4;
+// Coarse block values: out[q] = left-to-right FP64 sum from +0 of the fine
+// blocks src[list[ptr[q]] ..]. The first add 0 + v equals v except that -0
+// becomes +0, so a sum starts from its first term with that sign fix
+// (integer operations). One thread per output element, LS_OUT outputs per
+// thread; list entries and their values are fetched LS_CH at a time (two
+// memory round trips per chunk), and each add runs only where some lane of
+// the warp needs it (a predicated-off FP64 add would still take an FP64
+// issue slot). One pass: the grid covers every element (the launch
+// guarantees it) and every lane reaches the votes.
+constexpr int LS_OUT = 2;
+constexpr int LS_CH = 4;
 
 __device__ __forceinline__ double plus_zero(double v) {
   const long long b = __double_as_longlong(v);
@@ -321,47 +311,55 @@ __device__ __forceinline__ double plus_zero(double v) {
 }
 
 template <int NN>
-__global__ void __launch_bounds__(256, 6) k_list_sum(unsigned nout, const int32_t* __restrict__ gptr,
+__global__ void __launch_bounds__(256) k_list_sum(unsigned nout, const int32_t* __restrict__ gptr,
                                                   const int32_t* __restrict__ glist,
                                                   const double* __restrict__ src, double* __restrict__ out) {
   const unsigned total = nout * NN;
   const unsigned T = gridDim.x * blockDim.x;
-  for (unsigned base = blockIdx.x * blockDim.x + threadIdx.x; base < total; base += LS_OUT * T) {
-    unsigned e[LS_OUT];
-    int pb[LS_OUT], len[LS_OUT];
-    double acc[LS_OUT];
-    int maxlen = 0;
+  const unsigned base = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned e[LS_OUT];
+  int pb[LS_OUT], len[LS_OUT];
+  double acc[LS_OUT];
+  int mylen = 0;
 #pragma unroll
-    for (int u = 0; u < LS_OUT; ++u) {
-      const unsigned t = base + u * T;
-      const bool ok = t < total;
-      const unsigned q = ok ? t / NN : 0;
-      e[u] = ok ? t - q * NN : 0;
-      pb[u] = ok ? __ldg(gptr + q) : 0;
-      len[u] = ok ? __ldg(gptr + q + 1) - pb[u] : 0;
-      maxlen = max(maxlen, len[u]);
-    }
-    {
-      int k[LS_OUT];
-#pragma unroll
-      for (int u = 0; u < LS_OUT; ++u) k[u] = len[u] > 0 ? __ldg(glist + pb[u]) : -1;
-#pragma unroll
-      for (int u = 0; u < LS_OUT; ++u) acc[u] = k[u] >= 0 ? plus_zero(__ldg(src + (size_t)k[u] * NN + e[u])) : 0.0;
-    }
-    for (int o = 1; o < maxlen; ++o) {
-      int k[LS_OUT];
-      double v[LS_OUT];
-#pragma unroll
-      for (int u = 0; u < LS_OUT; ++u) k[u] = o < len[u] ? __ldg(glist + pb[u] + o) : -1;
-#pragma unroll
-      for (int u = 0; u < LS_OUT; ++u) v[u] = k[u] >= 0 ? __ldg(src + (size_t)k[u] * NN + e[u]) : 0.0;
-#pragma unroll
-      for (int u = 0; u < LS_OUT; ++u)
-        if (k[u] >= 0) acc[u] = acc[u] + v[u];
-    }
+  for (int u = 0; u < LS_OUT; ++u) {
+    const unsigned t = base + u * T;
+    const bool ok = t < total;
+    const unsigned q = ok ? t / NN : 0;
+    e[u] = ok ? t - q * NN : 0;
+    pb[u] = ok ? __ldg(gptr + q) : 0;
+    len[u] = ok ? __ldg(gptr + q + 1) - pb[u] : 0;
+    mylen = max(mylen, len[u]);
+    acc[u] = 0.0;
+  }
+  const int wmax = __reduce_max_sync(0xffffffffu, mylen);
+  for (int o = 0; o < wmax; o += LS_CH) {
+    int k[LS_OUT][LS_CH];
+    double v[LS_OUT][LS_CH];
 #pragma unroll
     for (int u = 0; u < LS_OUT; ++u)
-      if (base + u * T < total) out[base + u * T] = acc[u];
+#pragma unroll
+      for (int c = 0; c < LS_CH; ++c) k[u][c] = o + c < len[u] ? __ldg(glist + pb[u] + o + c) : -1;
+#pragma unroll
+    for (int u = 0; u < LS_OUT; ++u)
+#pragma unroll
+      for (int c = 0; c < LS_CH; ++c) v[u][c] = k[u][c] >= 0 ? __ldg(src + (size_t)k[u][c] * NN + e[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < LS_OUT; ++u)
+#pragma unroll
+      for (int c = 0; c < LS_CH; ++c) {
+        const bool need = k[u][c] >= 0;
+        if (o + c == 0) {
+          acc[u] = plus_zero(v[u][0]);
+        } else if (__any_sync(0xffffffffu, need)) {
+          if (need) acc[u] = acc[u] + v[u][c];
+        }
+      }
+  }
+#pragma unroll
+  for (int u = 0; u < LS_OUT; ++u) {
+    const unsigned t = base + u * T;
+    if (t < total) out[t] = acc[u];
   }
 }
 
@@ -745,96 +743,63 @@ bcs_status members(Solver* s, int rows, int nagg, const int32_t* agg, DBuf<int32
   return segmented_sort_unique(s, mptr.p, mem.p, cnt.p, nagg, mx);
 }
 
-// Gather lists of the two tentative products (see k_list_sum).
+// Gather lists of the tentative Galerkin product (see k_list_sum).
 struct TentPlan {
-  DBuf<int32_t> apg_ptr, apg_list, cg_ptr, cg_list;
+  DBuf<int32_t> ptr, list;
 };
 
-// Patterns of AP = A P_tent (row i: sorted aggregates of its neighbours) and
-// of A_c = P_tent^T AP (row I: sorted columns of its members' AP rows), and
-// the gather lists of both products, each from one segmented sort of packed
-// (column, source position) candidates. Sets A_c.maxrow. Two host reads.
+// Pattern of A_c = P_tent^T A P_tent (row I: sorted aggregates of its
+// members' columns) and its gather lists, from one segmented sort of packed
+// (coarse column, fine position) candidates. Sets A_c.maxrow. Two host reads.
 bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, const int32_t* mptr,
-                        const int32_t* mem, Bsr& AP, Bsr& Ac, TentPlan& plan) {
-  const int rows = A.rows;
-  if (A.maxrow < 0) return s->fail(BCS_EINVAL, "internal: longest row of the operator unknown");
+                        const int32_t* mem, Bsr& Ac, TentPlan& plan) {
   DBuf<int32_t> cnt, cptr, hv;
-  BCS_ALLOC(s, cnt, rows > nagg ? rows : nagg);
+  BCS_ALLOC(s, cnt, nagg);
   BCS_ALLOC(s, cptr, nagg + 1);
   BCS_ALLOC(s, hv, 4);
   BCS_CU(s, cudaMemsetAsync(hv.p, 0, 4 * sizeof(int32_t), s->stream));
+  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p, cnt.p,
+             hv.p + 1);
+  BCS_OKR(exclusive_scan(s, cnt.p, cptr.p, nagg));
   int32_t h[2] = {0, 0};
-  // AP: candidates are A's blocks, segments are A's rows
-  {
-    DBuf<uint64_t> cand;
-    BCS_ALLOC(s, cand, A.nnz);
-    BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_pack_ap, grid_for(A.nnz, 256), 256, 0, A.nnz, A.ci.p, agg,
-               cand.p);
-    BCS_OKR(segmented_sort64(s, A.rp.p, cand.p, rows, A.maxrow));
-    BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_runs_count, grid_for(rows, 256), 256, 0, rows, A.rp.p, cand.p,
-               cnt.p, (int32_t*)nullptr);
-    BCS_ALLOC(s, AP.rp, rows + 1);
-    BCS_OKR(exclusive_scan(s, cnt.p, AP.rp.p, rows));
-    // A_c candidate counts (the members' AP rows) before the one host read
-    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_count_ac, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, AP.rp.p, cnt.p,
-               hv.p + 1);
-    BCS_OKR(exclusive_scan(s, cnt.p, cptr.p, nagg));
-    BCS_CU(s, cudaMemcpyAsync(hv.p, AP.rp.p + rows, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->stream));
-    BCS_CU(s, cudaMemcpyAsync(h, hv.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
-    BCS_CU(s, cudaStreamSynchronize(s->stream));
-    AP.rows = rows;
-    AP.cols = nagg;
-    AP.nnz = h[0];
-    BCS_ALLOC(s, AP.ci, AP.nnz);
-    BCS_ALLOC(s, plan.apg_ptr, AP.nnz + 1);
-    BCS_ALLOC(s, plan.apg_list, A.nnz);
-    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * A.nnz + 8.0 * AP.nnz, 0, k_runs_emit, grid_for(rows, 256), 256, 0, rows,
-               A.rp.p, cand.p, AP.rp.p, AP.ci.p, plan.apg_ptr.p, plan.apg_list.p);
-  }
-  // A_c: candidates are the AP blocks of each aggregate's members
-  const int max_ac = h[1];
-  {
-    DBuf<uint64_t> cand;
-    BCS_ALLOC(s, cand, AP.nnz);
-    BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * AP.nnz, 0, k_pack_ac, grid_for(nagg, 256), 256, 0, nagg, mptr, mem,
-               AP.rp.p, AP.ci.p, cptr.p, cand.p);
-    BCS_OKR(segmented_sort64(s, cptr.p, cand.p, nagg, max_ac));
-    BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * AP.nnz, 0, k_runs_count, grid_for(nagg, 256), 256, 0, nagg, cptr.p, cand.p,
-               cnt.p, hv.p + 3);
-    BCS_ALLOC(s, Ac.rp, nagg + 1);
-    BCS_OKR(exclusive_scan(s, cnt.p, Ac.rp.p, nagg));
-    BCS_CU(s, cudaMemcpyAsync(hv.p + 2, Ac.rp.p + nagg, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->stream));
-    BCS_CU(s, cudaMemcpyAsync(h, hv.p + 2, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
-    BCS_CU(s, cudaStreamSynchronize(s->stream));
-    Ac.rows = Ac.cols = nagg;
-    Ac.nnz = h[0];
-    Ac.maxrow = h[1];
-    BCS_ALLOC(s, Ac.ci, Ac.nnz);
-    BCS_ALLOC(s, plan.cg_ptr, Ac.nnz + 1);
-    BCS_ALLOC(s, plan.cg_list, AP.nnz);
-    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * AP.nnz + 8.0 * Ac.nnz, 0, k_runs_emit, grid_for(nagg, 256), 256, 0, nagg,
-               cptr.p, cand.p, Ac.rp.p, Ac.ci.p, plan.cg_ptr.p, plan.cg_list.p);
-  }
+  BCS_CU(s, cudaMemcpyAsync(h, hv.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  const int max_c = h[1];
+  DBuf<uint64_t> cand;
+  BCS_ALLOC(s, cand, A.nnz);
+  BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_cand_pack_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem,
+             A.rp.p, A.ci.p, agg, cptr.p, cand.p);
+  BCS_OKR(segmented_sort64(s, cptr.p, cand.p, nagg, max_c));
+  BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_runs_count, grid_for(nagg, 256), 256, 0, nagg, cptr.p, cand.p, cnt.p,
+             hv.p + 3);
+  BCS_ALLOC(s, Ac.rp, nagg + 1);
+  BCS_OKR(exclusive_scan(s, cnt.p, Ac.rp.p, nagg));
+  BCS_CU(s, cudaMemcpyAsync(hv.p + 2, Ac.rp.p + nagg, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->stream));
+  BCS_CU(s, cudaMemcpyAsync(h, hv.p + 2, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  Ac.rows = Ac.cols = nagg;
+  Ac.nnz = h[0];
+  Ac.maxrow = h[1];
+  BCS_ALLOC(s, Ac.ci, Ac.nnz);
+  BCS_ALLOC(s, plan.ptr, Ac.nnz + 1);
+  BCS_ALLOC(s, plan.list, A.nnz);
+  BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * A.nnz + 8.0 * Ac.nnz, 0, k_runs_emit, grid_for(nagg, 256), 256, 0, nagg, cptr.p,
+             cand.p, Ac.rp.p, Ac.ci.p, plan.ptr.p, plan.list.p);
   return BCS_OK;
 }
 
-bcs_status tent_values(Solver* s, const Bsr& A, const TentPlan& plan, Bsr& AP, Bsr& Ac) {
+bcs_status tent_values(Solver* s, const Bsr& A, const TentPlan& plan, Bsr& Ac) {
   const int n = s->n;
-  BCS_ALLOC(s, AP.v, (size_t)AP.nnz * n * n);
   BCS_ALLOC(s, Ac.v, (size_t)Ac.nnz * n * n);
-  BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
+  return with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    if ((size_t)AP.nnz * N * N >= (1ull << 31)) return s->fail(BCS_EINVAL, "Galerkin product too large");
-    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + AP.nnz) * N * N + 4.0 * A.nnz, 1.0 * A.nnz * N * N,
-               k_list_sum<N * N>, grid_for(((size_t)AP.nnz * N * N + LS_OUT - 1) / LS_OUT, 256), 256, 0,
-               (unsigned)AP.nnz, plan.apg_ptr.p, plan.apg_list.p, A.v.p, AP.v.p);
-    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (AP.nnz + Ac.nnz) * N * N + 4.0 * AP.nnz, 1.0 * AP.nnz * N * N,
-               k_list_sum<N * N>, grid_for(((size_t)Ac.nnz * N * N + LS_OUT - 1) / LS_OUT, 256), 256, 0,
-               (unsigned)Ac.nnz, plan.cg_ptr.p, plan.cg_list.p, AP.v.p, Ac.v.p);
+    if ((size_t)Ac.nnz * N * N >= (1ull << 31)) return s->fail(BCS_EINVAL, "Galerkin product too large");
+    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + Ac.nnz) * N * N + 4.0 * A.nnz + 4.0 * Ac.nnz,
+               1.0 * (A.nnz - Ac.nnz) * N * N, k_list_sum<N * N>,
+               grid_for(((size_t)Ac.nnz * N * N + LS_OUT - 1) / LS_OUT, 256), 256, 0, (unsigned)Ac.nnz, plan.ptr.p,
+               plan.list.p, A.v.p, Ac.v.p);
     return BCS_OK;
-  }));
-  AP.v.release();  // AP values are a temporary of the product
-  return BCS_OK;
+  });
 }
 
 // Aggregation with agg_passes matching passes; fills L.agg / L.nagg.
@@ -850,10 +815,10 @@ bcs_status aggregate_level(Solver* s, Level& L) {
   for (int pass = 1; pass < s->setup_cfg.agg_passes; ++pass) {
     DBuf<int32_t> mptr, mem;
     BCS_OKR(members(s, cur->rows, nagg, cur_agg.p, mptr, mem));
-    Bsr Abar, AP;
+    Bsr Abar;
     TentPlan plan;
-    BCS_OKR(tent_pattern(s, *cur, nagg, cur_agg.p, mptr.p, mem.p, AP, Abar, plan));
-    BCS_OKR(tent_values(s, *cur, plan, AP, Abar));
+    BCS_OKR(tent_pattern(s, *cur, nagg, cur_agg.p, mptr.p, mem.p, Abar, plan));
+    BCS_OKR(tent_values(s, *cur, plan, Abar));
     DBuf<int32_t> a2;
     int n2 = 0;
     BCS_OKR(match_pass(s, Abar, a2, &n2));
@@ -1039,18 +1004,14 @@ bcs_status build_transfer(Solver* s, int l, bool full) {
   if (s->setup_cfg.pmode == BCS_P_TENTATIVE) {
     TentPlan plan;
     if (full) {
-      BCS_OKR(tent_pattern(s, L.A, L.nagg, L.agg.p, L.mptr.p, L.mem.p, L.AP, Lc.A, plan));
+      BCS_OKR(tent_pattern(s, L.A, L.nagg, L.agg.p, L.mptr.p, L.mem.p, Lc.A, plan));
     } else {
-      plan.apg_ptr = std::move(L.apg_ptr);
-      plan.apg_list = std::move(L.apg_list);
-      plan.cg_ptr = std::move(L.cg_ptr);
-      plan.cg_list = std::move(L.cg_list);
+      plan.ptr = std::move(L.cg_ptr);
+      plan.list = std::move(L.cg_list);
     }
-    const bcs_status st = tent_values(s, L.A, plan, L.AP, Lc.A);
-    L.apg_ptr = std::move(plan.apg_ptr);
-    L.apg_list = std::move(plan.apg_list);
-    L.cg_ptr = std::move(plan.cg_ptr);
-    L.cg_list = std::move(plan.cg_list);
+    const bcs_status st = tent_values(s, L.A, plan, Lc.A);
+    L.cg_ptr = std::move(plan.ptr);
+    L.cg_list = std::move(plan.list);
     BCS_OKR(st);
   } else {
     BCS_OKR(smoothed_prolongation(s, L, full));
