@@ -90,18 +90,32 @@ __global__ void k_sort_rows(int C, const int32_t* __restrict__ rp, int32_t* __re
   }
 }
 
+// Grid-stride over elements, GV_U independent elements per iteration (codes
+// first, then values) so each thread keeps several loads in flight.
+constexpr int GV_U = 4;
+
 template <int NN>
 __global__ void k_gather_values(size_t total, const int32_t* __restrict__ src,
                                 const double* __restrict__ diag, const double* __restrict__ upper,
                                 const double* __restrict__ lower, double* __restrict__ val) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = t / NN;
-    const int e = (int)(t - p * NN);
-    const int code = __ldg(src + p);
-    const double* base = code < 0 ? diag + (size_t)(-1 - code) * NN
-                                  : ((code & 1) ? lower : upper) + (size_t)(code >> 1) * NN;
-    val[t] = __ldg(base + e);
+  const size_t S = (size_t)gridDim.x * blockDim.x;
+  for (size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t0 < total; t0 += GV_U * S) {
+    const double* a[GV_U];
+#pragma unroll
+    for (int u = 0; u < GV_U; ++u) {
+      const size_t t = t0 + u * S;
+      const size_t p = t < total ? t / NN : 0;
+      const int e = (int)(t - p * NN);
+      const int code = t < total ? __ldg(src + p) : -1;
+      a[u] = (code < 0 ? diag + (size_t)(-1 - code) * NN : ((code & 1) ? lower : upper) + (size_t)(code >> 1) * NN) +
+             (t < total ? e : 0);
+    }
+    double v[GV_U];
+#pragma unroll
+    for (int u = 0; u < GV_U; ++u) v[u] = t0 + u * S < total ? __ldg(a[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < GV_U; ++u)
+      if (t0 + u * S < total) val[t0 + u * S] = v[u];
   }
 }
 

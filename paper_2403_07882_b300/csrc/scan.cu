@@ -1,5 +1,6 @@
 // Device prefix sums and per-segment sort/unique used by the structure and
 // setup phases (row pointers, sparsity patterns of Galerkin products).
+#include <algorithm>
 #include <climits>
 
 #include "internal.h"
@@ -165,52 +166,95 @@ template <class T> __device__ __forceinline__ T key_max();
 template <> __device__ __forceinline__ int32_t key_max<int32_t>() { return INT_MAX; }
 template <> __device__ __forceinline__ uint64_t key_max<uint64_t>() { return ~0ull; }
 
+// One warp per row of list[0 .. *n_list) (rows longer than 32 keys), grid-
+// stride over the list; rows longer than WARP_SEG_MAX go to long_rows.
 template <class T, bool UNIQUE>
 __global__ void k_seg_sort_warp(const int32_t* __restrict__ seg_ptr, T* __restrict__ keys,
-                                int32_t* __restrict__ count, int32_t* __restrict__ long_rows,
-                                int32_t* __restrict__ n_long, int rows) {
+                                int32_t* __restrict__ count, const int32_t* __restrict__ list,
+                                const int32_t* __restrict__ n_list, int32_t* __restrict__ long_rows,
+                                int32_t* __restrict__ n_long) {
   __shared__ T sm[WARPS_PER_BLOCK][WARP_SEG_MAX];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = blockIdx.x * WARPS_PER_BLOCK + warp;
-  if (r >= rows) return;
-  const int b = seg_ptr[r], len = seg_ptr[r + 1] - b;
-  if (len > WARP_SEG_MAX) {
-    if (lane == 0) long_rows[atomicAdd(n_long, 1)] = r;
-    return;
-  }
-  T* a = sm[warp];
-  int S = 32;
-  while (S < len) S <<= 1;
-  for (int i = lane; i < S; i += 32) a[i] = i < len ? keys[b + i] : key_max<T>();
-  __syncwarp();
-  for (int k = 2; k <= S; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = lane; i < S; i += 32) {
-        const int l = i ^ j;
-        if (l > i) {
-          const T x = a[i], y = a[l];
-          const bool up = (i & k) == 0;
-          if ((x > y) == up) {
-            a[i] = y;
-            a[l] = x;
+  const int nl = *n_list;
+  for (int idx = blockIdx.x * WARPS_PER_BLOCK + warp; idx < nl; idx += gridDim.x * WARPS_PER_BLOCK) {
+    const int r = list[idx];
+    const int b = seg_ptr[r], len = seg_ptr[r + 1] - b;
+    if (len > WARP_SEG_MAX) {
+      if (lane == 0) long_rows[atomicAdd(n_long, 1)] = r;
+      continue;
+    }
+    if (len <= 64) {
+      // register bitonic sort of 64 slots: lane l holds elements l and l + 32
+      T a0 = lane < len ? keys[b + lane] : key_max<T>();
+      T a1 = lane + 32 < len ? keys[b + 32 + lane] : key_max<T>();
+      for (int k = 2; k <= 64; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          if (j == 32) {  // k == 64: elements l and l + 32, ascending
+            const T lo = a0 < a1 ? a0 : a1, hi = a0 < a1 ? a1 : a0;
+            a0 = lo;
+            a1 = hi;
+          } else {
+            const T p0 = __shfl_xor_sync(0xffffffffu, a0, j), p1 = __shfl_xor_sync(0xffffffffu, a1, j);
+            const bool lower = (lane & j) == 0;
+            const bool up0 = (lane & k) == 0, up1 = ((lane + 32) & k) == 0;
+            a0 = (lower == up0) ? (p0 < a0 ? p0 : a0) : (p0 < a0 ? a0 : p0);
+            a1 = (lower == up1) ? (p1 < a1 ? p1 : a1) : (p1 < a1 ? a1 : p1);
           }
         }
+      if (!UNIQUE) {
+        if (lane < len) keys[b + lane] = a0;
+        if (lane + 32 < len) keys[b + 32 + lane] = a1;
+        continue;
       }
-      __syncwarp();
+      const T prev0 = __shfl_up_sync(0xffffffffu, a0, 1);
+      const T last0 = __shfl_sync(0xffffffffu, a0, 31);
+      const T up1v = __shfl_up_sync(0xffffffffu, a1, 1);
+      const T prev1 = lane == 0 ? last0 : up1v;
+      const bool keep0 = lane < len && (lane == 0 || a0 != prev0);
+      const bool keep1 = lane + 32 < len && a1 != prev1;
+      const unsigned m0 = __ballot_sync(0xffffffffu, keep0), m1 = __ballot_sync(0xffffffffu, keep1);
+      const unsigned below = (1u << lane) - 1u;
+      if (keep0) keys[b + __popc(m0 & below)] = a0;
+      if (keep1) keys[b + __popc(m0) + __popc(m1 & below)] = a1;
+      if (lane == 0) count[r] = __popc(m0) + __popc(m1);
+      continue;
     }
-  if (!UNIQUE) {
-    for (int i = lane; i < len; i += 32) keys[b + i] = a[i];
-    return;
+    T* a = sm[warp];
+    int S = 32;
+    while (S < len) S <<= 1;
+    for (int i = lane; i < S; i += 32) a[i] = i < len ? keys[b + i] : key_max<T>();
+    __syncwarp();
+    for (int k = 2; k <= S; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = lane; i < S; i += 32) {
+          const int l = i ^ j;
+          if (l > i) {
+            const T x = a[i], y = a[l];
+            const bool up = (i & k) == 0;
+            if ((x > y) == up) {
+              a[i] = y;
+              a[l] = x;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    if (!UNIQUE) {
+      for (int i = lane; i < len; i += 32) keys[b + i] = a[i];
+      __syncwarp();
+      continue;
+    }
+    int outpos = 0;
+    for (int i0 = 0; i0 < len; i0 += 32) {
+      const int i = i0 + lane;
+      const bool keep = i < len && (i == 0 || a[i] != a[i - 1]);
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) keys[b + outpos + __popc(m & ((1u << lane) - 1u))] = a[i];
+      outpos += __popc(m);
+    }
+    if (lane == 0) count[r] = outpos;
+    __syncwarp();
   }
-  int outpos = 0;
-  for (int i0 = 0; i0 < len; i0 += 32) {
-    const int i = i0 + lane;
-    const bool keep = i < len && (i == 0 || a[i] != a[i - 1]);
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
-    if (keep) keys[b + outpos + __popc(m & ((1u << lane) - 1u))] = a[i];
-    outpos += __popc(m);
-  }
-  if (lane == 0) count[r] = outpos;
 }
 
 template <class T, bool UNIQUE>
@@ -268,10 +312,15 @@ __global__ void k_seg_sort_block(const int32_t* __restrict__ seg_ptr, T* __restr
 // (an unrolled insertion network of min/max pairs).
 template <int M, class T, bool UNIQUE>
 __global__ void k_seg_sort_thread(const int32_t* __restrict__ seg_ptr, T* __restrict__ keys,
-                                  int32_t* __restrict__ count, int rows) {
+                                  int32_t* __restrict__ count, int rows, int32_t* __restrict__ defer,
+                                  int32_t* __restrict__ n_defer) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   const int b = seg_ptr[r], len = seg_ptr[r + 1] - b;
+  if (len > M) {  // longer rows (only present when defer is given) go to the warp kernel
+    defer[atomicAdd(n_defer, 1)] = r;
+    return;
+  }
   T a[M];
 #pragma unroll
   for (int i = 0; i < M; ++i) a[i] = i < len ? keys[b + i] : key_max<T>();
@@ -303,23 +352,29 @@ bcs_status seg_sort(Solver* s, const int32_t* seg_ptr, T* keys, int32_t* count, 
     return s->fail(BCS_EINVAL, "a sparsity-pattern row has more than 16384 candidate entries");
   if (max_len <= 16) {
     BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_thread<16, T, UNIQUE>), grid_for(rows, 128), 128, 0, seg_ptr, keys,
-               count, rows);
+               count, rows, (int32_t*)nullptr, (int32_t*)nullptr);
     return BCS_OK;
   }
   if (max_len <= 32) {
     BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_thread<32, T, UNIQUE>), grid_for(rows, 128), 128, 0, seg_ptr, keys,
-               count, rows);
+               count, rows, (int32_t*)nullptr, (int32_t*)nullptr);
     return BCS_OK;
   }
-  DBuf<int32_t> long_rows, aux;
+  // rows of up to 32 keys by one thread each; longer rows listed for one
+  // warp each; rows beyond WARP_SEG_MAX listed again for one block each
+  DBuf<int32_t> mid_rows, long_rows, aux;
+  BCS_ALLOC(s, mid_rows, rows);
   BCS_ALLOC(s, long_rows, rows);
-  BCS_ALLOC(s, aux, 1);
-  BCS_CU(s, cudaMemsetAsync(aux.p, 0, sizeof(int32_t), s->stream));
-  BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_warp<T, UNIQUE>), grid_for(rows, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, 0,
-             seg_ptr, keys, count, long_rows.p, aux.p, rows);
+  BCS_ALLOC(s, aux, 2);
+  BCS_CU(s, cudaMemsetAsync(aux.p, 0, 2 * sizeof(int32_t), s->stream));
+  BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_thread<32, T, UNIQUE>), grid_for(rows, 128), 128, 0, seg_ptr, keys, count,
+             rows, mid_rows.p, aux.p);
+  const unsigned gw = std::min<unsigned>(grid_for(rows, WARPS_PER_BLOCK), 2048u);
+  BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_warp<T, UNIQUE>), gw, 32 * WARPS_PER_BLOCK, 0, seg_ptr, keys, count,
+             mid_rows.p, aux.p, long_rows.p, aux.p + 1);
   if (max_len > WARP_SEG_MAX) {
     int32_t h = 0;
-    BCS_CU(s, cudaMemcpyAsync(&h, aux.p, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    BCS_CU(s, cudaMemcpyAsync(&h, aux.p + 1, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
     BCS_CU(s, cudaStreamSynchronize(s->stream));
     if (h > 0) {
       int S = 32;

@@ -224,29 +224,33 @@ __global__ void k_compact(int rows, const int32_t* __restrict__ cptr, const int3
 // fine blocks in ascending position (members ascending, columns ascending
 // within a row), the summation order of the definition.
 
-// Candidate count of coarse row I (its members' row lengths); longest -> *mx.
+// Candidate count of coarse row I (its members' row lengths); longest -> *mx;
+// moff[i] = where member row i's candidates start inside its coarse row.
 __global__ void k_cand_count_tent(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
-                                  const int32_t* __restrict__ rp, int32_t* __restrict__ cnt, int32_t* __restrict__ mx) {
+                                  const int32_t* __restrict__ rp, int32_t* __restrict__ cnt, int32_t* __restrict__ moff,
+                                  int32_t* __restrict__ mx) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   int c = 0;
   if (I < nagg)
-    for (int q = mptr[I]; q < mptr[I + 1]; ++q) c += rp[mem[q] + 1] - rp[mem[q]];
+    for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
+      const int i = mem[q];
+      moff[i] = c;
+      c += rp[i + 1] - rp[i];
+    }
   const int m = __reduce_max_sync(0xffffffffu, c);
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(mx, m);
   if (I < nagg) cnt[I] = c;
 }
 
-__global__ void k_cand_pack_tent(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
-                                 const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+// One thread per fine row: its blocks' candidates, contiguous in its coarse
+// row's segment.
+__global__ void k_cand_pack_tent(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                  const int32_t* __restrict__ agg, const int32_t* __restrict__ cptr,
-                                 uint64_t* __restrict__ cand) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= nagg) return;
-  int o = cptr[I];
-  for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
-    const int i = mem[q];
-    for (int p = rp[i]; p < rp[i + 1]; ++p) cand[o++] = ((uint64_t)(uint32_t)agg[ci[p]] << 32) | (uint32_t)p;
-  }
+                                 const int32_t* __restrict__ moff, uint64_t* __restrict__ cand) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const long long o = (long long)cptr[agg[i]] + moff[i] - rp[i];
+  for (int p = rp[i]; p < rp[i + 1]; ++p) cand[o + p] = ((uint64_t)(uint32_t)agg[ci[p]] << 32) | (uint32_t)p;
 }
 
 // Number of runs (distinct columns) in each sorted segment; longest -> *mx
@@ -302,8 +306,8 @@ __global__ void k_runs_emit(int rows, const int32_t* __restrict__ seg, const uin
 // the warp needs it (a predicated-off FP64 add would still take an FP64
 // issue slot). One pass: the grid covers every element (the launch
 // guarantees it) and every lane reaches the votes.
-constexpr int LS_OUT = 2;
-constexpr int LS_CH = 4;
+constexpr int LS_OUT = 1;
+constexpr int LS_CH = 2;
 
 __device__ __forceinline__ double plus_zero(double v) {
   const long long b = __double_as_longlong(v);
@@ -753,13 +757,14 @@ struct TentPlan {
 // (coarse column, fine position) candidates. Sets A_c.maxrow. Two host reads.
 bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, const int32_t* mptr,
                         const int32_t* mem, Bsr& Ac, TentPlan& plan) {
-  DBuf<int32_t> cnt, cptr, hv;
+  DBuf<int32_t> cnt, cptr, hv, moff;
   BCS_ALLOC(s, cnt, nagg);
   BCS_ALLOC(s, cptr, nagg + 1);
   BCS_ALLOC(s, hv, 4);
+  BCS_ALLOC(s, moff, A.rows);
   BCS_CU(s, cudaMemsetAsync(hv.p, 0, 4 * sizeof(int32_t), s->stream));
   BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p, cnt.p,
-             hv.p + 1);
+             moff.p, hv.p + 1);
   BCS_OKR(exclusive_scan(s, cnt.p, cptr.p, nagg));
   int32_t h[2] = {0, 0};
   BCS_CU(s, cudaMemcpyAsync(h, hv.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
@@ -767,8 +772,8 @@ bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, c
   const int max_c = h[1];
   DBuf<uint64_t> cand;
   BCS_ALLOC(s, cand, A.nnz);
-  BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_cand_pack_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem,
-             A.rp.p, A.ci.p, agg, cptr.p, cand.p);
+  BCS_LAUNCH(s, K_SETUP_GAL, 16.0 * A.nnz, 0, k_cand_pack_tent, grid_for(A.rows, 256), 256, 0, A.rows, A.rp.p,
+             A.ci.p, agg, cptr.p, moff.p, cand.p);
   BCS_OKR(segmented_sort64(s, cptr.p, cand.p, nagg, max_c));
   BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_runs_count, grid_for(nagg, 256), 256, 0, nagg, cptr.p, cand.p, cnt.p,
              hv.p + 3);
