@@ -121,6 +121,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value, device):
+    """Largest per-rank value (the step time of the slowest replica); every
+    rank gets it. Needs an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -250,12 +260,21 @@ def run_native(args):
         barrier()
         return e0.elapsed_time(e1) / steps, results, s.stats()
 
-    # mixed precision (the headline). Inside the timed region only the
-    # candidates for the dominant kernel carry CUDA events (smoother sweeps and
-    # Galerkin products), so that per-launch event records do not slow the
-    # step; the full per-kernel table comes from one more, untimed, step.
+    # mixed precision (the headline). One untimed step with CUDA events on
+    # every launch gives the per-kernel table and the dominant kernel; inside
+    # the timed region only that kernel's kind carries events (so event
+    # records do not slow the step, and the cycle can still run as a CUDA
+    # graph when the dominant kernel is outside it).
     x = torch.zeros_like(d["b"])
-    live_kinds = bcs.kind_mask("jacobi_sweep", "setup_galerkin")
+    with bcs.Solver(n, precision=bcs.BCS_PREC_FP32, profile=1) as sp:
+        step(sp, d, x)
+        torch.cuda.synchronize()
+        sp.reset_stats()
+        step(sp, d, x)
+        ktimes = sp.kernel_times()
+        kinds = sp.stats()["kinds"]
+    top_name = max(ktimes.items(), key=lambda kv: kv[1]["ms"])[0]
+    live_kinds = 1 << ktimes[top_name]["kind"]
     with ClockSampler(local) as clk:
         with bcs.Solver(n, precision=bcs.BCS_PREC_FP32, profile=1, profile_kinds=live_kinds) as s:
             ms_mixed, res_mixed, stats = timed(s, d, x, args.steps, args.warmup)
@@ -269,13 +288,6 @@ def run_native(args):
             torch.cuda.synchronize()
             resetup_ms = e0.elapsed_time(e1)
     clocks = clk.summary()
-    with bcs.Solver(n, precision=bcs.BCS_PREC_FP32, profile=1) as sp:
-        step(sp, d, x)
-        torch.cuda.synchronize()
-        sp.reset_stats()
-        step(sp, d, x)
-        ktimes = sp.kernel_times()
-        kinds = sp.stats()["kinds"]
     # all-FP64 comparison (same step, FP64 AMG) and BF16-stored AMG
     ms_fp64, res_fp64, ms_bf16, res_bf16, ms_dilu, res_dilu = None, None, None, None, None, None
     if not args.no_fp64:
@@ -297,17 +309,13 @@ def run_native(args):
         e2e = {"value": ms_e2e, "unit": "ms", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(xh.numel() * 8)}
 
-    ms_max = ms_mixed
-    if world > 1:
-        t = torch.tensor([ms_mixed], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms_mixed, dev) if world > 1 else ms_mixed
     if rank != 0:
         return
 
     peak, peak_kind = peaks()
-    # dominant kernel by event time inside the timed region
-    top_name, top = max(live.items(), key=lambda kv: kv[1]["ms"])
+    # the dominant kernel's events inside the timed region
+    top = live[top_name]
     per_launch_bytes = top["bytes"] / max(top["launches"], 1)
     per_launch_ms = top["ms"] / max(top["launches"], 1)
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9

@@ -101,9 +101,9 @@ typedef struct bcs_config {
   int slice_layout;        /* FP32 / BF16 level storage: 0 one lane per scalar row, 1 one thread
                               per block row, -1 (default) timed per level at full setup and the
                               faster kept; both give identical results */
-  int cycle_graph;         /* FP32 / BF16 V-cycle replayed as one CUDA graph: 1 on, 0 off,
-                              -1 (default) on up to 4,194,304 unknowns, where launch latency
-                              matters; never while profile = 1 (per-kernel events) */
+  int cycle_graph;         /* FP32 / BF16 V-cycle replayed as one CUDA graph: 0 off, 1 or -1
+                              (default) on, except while profile = 1 times kernels inside
+                              the cycle (per-kernel events) */
 } bcs_config;
 
 typedef struct bcs_result {
@@ -217,8 +217,8 @@ BCS_API bcs_status bcs_get_dilu(bcs_solver* s, int level, int* ncolours, int32_t
 BCS_API bcs_status bcs_get_stats(bcs_solver* s, bcs_stats* st);
 BCS_API bcs_status bcs_reset_stats(bcs_solver* s);
 /* Per-kernel timing table (cfg.profile = 1): one line per kernel,
- * "name<TAB>launches<TAB>ms<TAB>algorithmic bytes", written to buf (NUL
- * terminated); BCS_EINVAL when it does not fit in len bytes. */
+ * "name<TAB>launches<TAB>ms<TAB>algorithmic bytes<TAB>kind", written to buf
+ * (NUL terminated); BCS_EINVAL when it does not fit in len bytes. */
 BCS_API bcs_status bcs_get_kernel_times(bcs_solver* s, char* buf, size_t len);
 /* Name of kernel kind k (0 <= k < BCS_NUM_KERNEL_KINDS), "" if unused. */
 BCS_API const char* bcs_kernel_kind_name(int k);

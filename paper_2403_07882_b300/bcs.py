@@ -310,13 +310,13 @@ def bcs_get_stats(h):
 
 
 def bcs_get_kernel_times(h):
-    """{kernel name: dict(launches, ms, bytes)} (profile = 1)."""
+    """{kernel name: dict(launches, ms, bytes, kind)} (profile = 1)."""
     buf = ct.create_string_buffer(1 << 20)
     _check(lib().bcs_get_kernel_times(h, buf, len(buf)), h)
     out = {}
     for line in buf.value.decode().splitlines():
-        name, n, ms, b = line.split("\t")
-        out[name] = dict(launches=int(n), ms=float(ms), bytes=float(b))
+        name, n, ms, b, kind = line.split("\t")
+        out[name] = dict(launches=int(n), ms=float(ms), bytes=float(b), kind=int(kind))
     return out
 
 

@@ -78,6 +78,7 @@ void Solver::flush_timers() {
         nt.launches++;
         nt.ms += ms;
         nt.bytes += t.bytes;
+        nt.kind = t.kind;
       }
     }
   }
@@ -479,8 +480,8 @@ bcs_status bcs_get_kernel_times(bcs_solver* h, char* buf, size_t len) {
   std::string out;
   char line[512];
   for (const auto& kv : s->named) {
-    std::snprintf(line, sizeof(line), "%s\t%lld\t%.6f\t%.0f\n", kv.first.c_str(), kv.second.launches, kv.second.ms,
-                  kv.second.bytes);
+    std::snprintf(line, sizeof(line), "%s\t%lld\t%.6f\t%.0f\t%d\n", kv.first.c_str(), kv.second.launches,
+                  kv.second.ms, kv.second.bytes, kv.second.kind);
     out += line;
   }
   std::snprintf(buf, len, "%s", out.c_str());

@@ -79,6 +79,45 @@ __global__ void __launch_bounds__(128) k_rows(int rows, const int32_t* __restric
 // Rows of colour c (list rows_c), lane (w, r) = scalar row r of the w-th row.
 // Forward:  y_i = E_i^{-1} (r_i - sum_{colour(j) < c} A_ij y_j).
 // Backward: d_i = y_i - E_i^{-1} sum_{colour(j) > c} A_ij d_j;  x_i += d_i.
+// One row of a colour's sweep: lane (rw, r) of a row group; every lane of the
+// warp calls it (shuffles), active says whether the lane has a row. Vectors
+// the sweeps write (r, y, d, x) are read with ordinary loads.
+template <int N, class AT, class TV, class TD, class TC, bool FWD>
+__device__ __forceinline__ void dilu_row(bool active, int i, int rw, int r, int c, const int32_t* __restrict__ colour,
+                                         const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                         const TV* __restrict__ val, const TD* __restrict__ einv, const TC* rv, TC* y,
+                                         TC* d, TC* x) {
+  AT acc = 0;
+  if (active) {
+    const int kb = __ldg(rp + i), ke = __ldg(rp + i + 1);
+    for (int k = kb; k < ke; ++k) {
+      const int j = __ldg(ci + k);
+      const int cj = __ldg(colour + j);
+      if (FWD ? cj >= c : cj <= c) continue;
+      const TV* a = val + (size_t)k * (N * N) + r * N;
+      const TC* v = (FWD ? y : d) + (size_t)j * N;
+#pragma unroll
+      for (int cc = 0; cc < N; ++cc) acc = fma(lda<AT>(a + cc), (AT)v[cc], acc);
+    }
+  }
+  const size_t o = (size_t)i * N + r;
+  const AT t = active ? (FWD ? (AT)rv[o] - acc : acc) : (AT)0;
+  AT s = 0;
+#pragma unroll
+  for (int cc = 0; cc < N; ++cc) {
+    const AT tc = __shfl_sync(0xffffffffu, t, (rw * N + cc) & 31);
+    if (active) s = fma(lda<AT>(einv + o * N + cc), tc, s);
+  }
+  if (!active) return;
+  if (FWD) {
+    y[o] = (TC)s;
+  } else {
+    const AT dv = (AT)y[o] - s;
+    d[o] = (TC)dv;
+    x[o] = (TC)((AT)x[o] + dv);
+  }
+}
+
 template <int N, class AT, class TV, class TD, class TC, bool FWD>
 __global__ void __launch_bounds__(128) k_dilu_sweep(int cnt, const int32_t* __restrict__ rows_c, int c,
                                                     const int32_t* __restrict__ colour,
@@ -88,35 +127,7 @@ __global__ void __launch_bounds__(128) k_dilu_sweep(int cnt, const int32_t* __re
                                                     TC* __restrict__ d, TC* __restrict__ x) {
   RowMap<N> m(cnt);
   const int i = m.active ? __ldg(rows_c + m.i) : 0;
-  AT acc = 0;
-  if (m.active) {
-    const int kb = __ldg(rp + i), ke = __ldg(rp + i + 1);
-    for (int k = kb; k < ke; ++k) {
-      const int j = __ldg(ci + k);
-      const int cj = __ldg(colour + j);
-      if (FWD ? cj >= c : cj <= c) continue;
-      const TV* a = val + (size_t)k * (N * N) + m.r * N;
-      const TC* v = (FWD ? y : d) + (size_t)j * N;
-#pragma unroll
-      for (int cc = 0; cc < N; ++cc) acc = fma(lda<AT>(a + cc), (AT)v[cc], acc);
-    }
-  }
-  const size_t o = (size_t)i * N + m.r;
-  const AT t = m.active ? (FWD ? (AT)r[o] - acc : acc) : (AT)0;
-  AT s = 0;
-#pragma unroll
-  for (int cc = 0; cc < N; ++cc) {
-    const AT tc = __shfl_sync(0xffffffffu, t, (m.rw * N + cc) & 31);
-    if (m.active) s = fma(lda<AT>(einv + o * N + cc), tc, s);
-  }
-  if (!m.active) return;
-  if (FWD) {
-    y[o] = (TC)s;
-  } else {
-    const AT dv = (AT)y[o] - s;
-    d[o] = (TC)dv;
-    x[o] = (TC)((AT)x[o] + dv);
-  }
+  dilu_row<N, AT, TV, TD, TC, FWD>(m.active, i, m.rw, m.r, c, colour, rp, ci, val, einv, r, y, d, x);
 }
 
 // ---- sliced (SELL) copy for the FP32 / BF16 cycle ---------------------------
@@ -881,12 +892,14 @@ bcs_status cycle_prepare(Solver* s) {
 
 namespace {
 
-constexpr size_t GRAPH_AUTO_MAX_UNKNOWNS = size_t(1) << 22;
+// Kinds of the kernels inside the cycle: with per-launch events on any of
+// them the cycle runs kernel by kernel.
+constexpr int CYCLE_KINDS = (1 << K_SWEEP) | (1 << K_RESID) | (1 << K_TRANSFER) | (1 << K_COARSE);
 
 bool use_graph(const Solver* s) {
-  if (s->cfg.profile || s->setup_cfg.precision == BCS_PREC_FP64) return false;
-  if (s->cfg.cycle_graph >= 0) return s->cfg.cycle_graph == 1;
-  return (size_t)s->lv[0].A.rows * s->n <= GRAPH_AUTO_MAX_UNKNOWNS;
+  if (s->setup_cfg.precision == BCS_PREC_FP64 || s->cfg.cycle_graph == 0) return false;
+  if (s->cfg.profile && (s->cfg.profile_kinds == 0 || (s->cfg.profile_kinds & CYCLE_KINDS))) return false;
+  return true;
 }
 
 template <class TV>

@@ -143,6 +143,7 @@ struct Timer {
 struct NamedTime {
   long long launches = 0;
   double ms = 0.0, bytes = 0.0;
+  int kind = -1;
 };
 
 struct Solver {

@@ -20,6 +20,7 @@ CASES = [
     ("pressure 10^3", lambda: synth.pressure(10, seed=1), {}),
     ("knn 10^3", lambda: synth.knn(10, seed=2), {}),
     ("random n=3", lambda: synth.random_graph(400, 1500, 3, seed=5), dict(coarse_size=8)),
+    ("density 24^3", lambda: synth.density(24, seed=4), {}),
 ]
 
 
