@@ -139,13 +139,15 @@ __global__ void __launch_bounds__(128) k_dilu_sweep(int cnt, const int32_t* __re
 // longest are padded (the padding is skipped). Each lane loads one component
 // of its row's x block and the row's lanes exchange them by shuffle.
 __global__ void k_slice_len(int rows, int rpw, int nslices, const int32_t* __restrict__ rp,
-                            int32_t* __restrict__ slen) {
+                            const int32_t* __restrict__ order, int32_t* __restrict__ slen) {
   const int sl = blockIdx.x * blockDim.x + threadIdx.x;
   if (sl >= nslices) return;
   int m = 0;
   for (int rw = 0; rw < rpw; ++rw) {
-    const int i = sl * rpw + rw;
-    if (i < rows) m = max(m, rp[i + 1] - rp[i]);
+    const int pos = sl * rpw + rw;
+    if (pos >= rows) break;
+    const int i = order ? order[pos] : pos;
+    m = max(m, rp[i + 1] - rp[i]);
   }
   slen[sl] = m;
 }
@@ -259,17 +261,41 @@ __global__ void __launch_bounds__(128) k_sell(int rows, int nslices, const int32
 // (row w, r, c) at t * n*n*32 + (r * n + c) * 32 + w, so for a fixed element
 // the warp reads 128 (FP32) or 64 (BF16) contiguous bytes; sci[t * 32 + w].
 // A thread keeps n*n value loads of one step in flight (one lane-per-row warp
-// of the other layout moves n*n*floor(32/n) values per step).
+// of the other layout moves n*n*floor(32/n) values per step). Slice position
+// p holds block row srow[p]: rows are taken in windows of SORT_WIN
+// consecutive rows, longest first (ties by row index), so the rows of a slice
+// have similar lengths and little padding (coarse levels mix rows of 7 to 30
+// blocks).
+constexpr int SORT_WIN = 256;
+
+__global__ void __launch_bounds__(SORT_WIN) k_window_order(int rows, const int32_t* __restrict__ rp,
+                                                          int32_t* __restrict__ srow) {
+  __shared__ int len[SORT_WIN];
+  const int w0 = blockIdx.x * SORT_WIN, i = w0 + threadIdx.x;
+  const int cnt = min(SORT_WIN, rows - w0);
+  const int li = i < rows ? rp[i + 1] - rp[i] : -1;
+  len[threadIdx.x] = li;
+  __syncthreads();
+  if ((int)threadIdx.x >= cnt) return;
+  int rank = 0;
+  for (int j = 0; j < cnt; ++j) {
+    const int lj = len[j];
+    rank += (lj > li) || (lj == li && j < (int)threadIdx.x);
+  }
+  srow[w0 + rank] = i;
+}
+
 template <int N, class TV>
 __global__ void k_tpr_fill(int rows, int nslices, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                           const double* __restrict__ val, const int32_t* __restrict__ sptr,
-                           int32_t* __restrict__ sci, TV* __restrict__ sv) {
+                           const double* __restrict__ val, const int32_t* __restrict__ srow,
+                           const int32_t* __restrict__ sptr, int32_t* __restrict__ sci, TV* __restrict__ sv) {
   constexpr int NN = N * N, TILE = NN * 32;
   const int lane = threadIdx.x & 31;
   const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (sl >= nslices) return;
-  const int i = sl * 32 + lane;
-  const int p0 = i < rows ? rp[i] : 0, len = i < rows ? rp[i + 1] - p0 : 0;
+  const int pos = sl * 32 + lane;
+  const int i = pos < rows ? srow[pos] : 0;
+  const int p0 = pos < rows ? rp[i] : 0, len = pos < rows ? rp[i + 1] - p0 : 0;
   const int t0 = sptr[sl];
   for (int k = 0; k < len; ++k) {
     const double* a = val + (size_t)(p0 + k) * NN;
@@ -289,16 +315,17 @@ __global__ void k_tpr_fill(int rows, int nslices, const int32_t* __restrict__ rp
 // results.
 template <int N, class TV, bool JACOBI>
 __global__ void __launch_bounds__(128) k_tpr(int rows, int nslices, const int32_t* __restrict__ rp,
-                                             const int32_t* __restrict__ sptr, const int32_t* __restrict__ sci,
-                                             const TV* __restrict__ sv, const float* __restrict__ dinv,
-                                             const float* __restrict__ x, const float* __restrict__ b,
-                                             float* __restrict__ y, float omega) {
+                                             const int32_t* __restrict__ srow, const int32_t* __restrict__ sptr,
+                                             const int32_t* __restrict__ sci, const TV* __restrict__ sv,
+                                             const float* __restrict__ dinv, const float* __restrict__ x,
+                                             const float* __restrict__ b, float* __restrict__ y, float omega) {
   constexpr int NN = N * N, TILE = NN * 32;
   const int lane = threadIdx.x & 31;
   const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (sl >= nslices) return;
-  const int i = sl * 32 + lane;
-  if (i >= rows) return;
+  const int pos = sl * 32 + lane;
+  if (pos >= rows) return;
+  const int i = __ldg(srow + pos);
   const int len = __ldg(rp + i + 1) - __ldg(rp + i);
   const int t0 = __ldg(sptr + sl);
   const size_t o = (size_t)i * N;
@@ -523,7 +550,8 @@ struct Cycle {
     if constexpr (std::is_same<TC, float>::value) {
       if (L.smap == 1)
         BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_tpr<N, TV, true>),
-                   grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.sptr.p, L.sci.p,
+                   grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.srow.p, L.sptr.p,
+                   L.sci.p,
                    smat(L), dinv(L), x, b, y, om);
       else
         BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_sell<N, TV, true>),
@@ -543,7 +571,8 @@ struct Cycle {
     if constexpr (std::is_same<TC, float>::value) {
       if (L.smap == 1)
         BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_tpr<N, TV, false>),
-                   grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.sptr.p, L.sci.p,
+                   grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.srow.p, L.sptr.p,
+                   L.sci.p,
                    smat(L), (const float*)nullptr, x, b, r, 0.f);
       else
         BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_sell<N, TV, false>),
@@ -720,11 +749,18 @@ bcs_status fill_layout(Solver* s, Level& L, int prec, int map) {
     L.sci.release();
     L.s32.release();
     L.s16.release();
+    L.srow.release();
     const int ns = (rows + rpw - 1) / rpw;
     DBuf<int32_t> slen;
     BCS_ALLOC(s, slen, ns);
     BCS_ALLOC(s, L.sptr, ns + 1);
-    BCS_LAUNCH(s, K_CAST, 0, 0, k_slice_len, grid_for(ns, 256), 256, 0, rows, rpw, ns, L.A.rp.p, slen.p);
+    if (map == 1) {
+      BCS_ALLOC(s, L.srow, rows);
+      BCS_LAUNCH(s, K_CAST, 0, 0, k_window_order, grid_for(rows, SORT_WIN), SORT_WIN, 0, rows, L.A.rp.p,
+                 L.srow.p);
+    }
+    BCS_LAUNCH(s, K_CAST, 0, 0, k_slice_len, grid_for(ns, 256), 256, 0, rows, rpw, ns, L.A.rp.p, L.srow.p,
+               slen.p);
     BCS_OKR(exclusive_scan(s, slen.p, L.sptr.p, ns));
     int32_t steps = 0;
     BCS_CU(s, cudaMemcpyAsync(&steps, L.sptr.p + ns, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
@@ -743,7 +779,7 @@ bcs_status fill_layout(Solver* s, Level& L, int prec, int map) {
       BCS_ALLOC(s, L.s32, nv);
       if (map == 1)
         BCS_LAUNCH(s, K_CAST, bytes, 0, (k_tpr_fill<N, float>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
-                   L.A.v.p, L.sptr.p, L.sci.p, L.s32.p);
+                   L.A.v.p, L.srow.p, L.sptr.p, L.sci.p, L.s32.p);
       else
         BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, float>), g, 128, 0, rows, L.nslices, L.A.rp.p,
                    L.A.ci.p, L.A.v.p, L.sptr.p, L.sci.p, L.s32.p);
@@ -751,7 +787,7 @@ bcs_status fill_layout(Solver* s, Level& L, int prec, int map) {
       BCS_ALLOC(s, L.s16, nv);
       if (map == 1)
         BCS_LAUNCH(s, K_CAST, bytes, 0, (k_tpr_fill<N, bf16>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
-                   L.A.v.p, L.sptr.p, L.sci.p, L.s16.p);
+                   L.A.v.p, L.srow.p, L.sptr.p, L.sci.p, L.s16.p);
       else
         BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, bf16>), g, 128, 0, rows, L.nslices, L.A.rp.p,
                    L.A.ci.p, L.A.v.p, L.sptr.p, L.sci.p, L.s16.p);
@@ -785,8 +821,8 @@ bcs_status time_sweep(Solver* s, const Level& L, cudaEvent_t e0, cudaEvent_t e1,
   for (int rep = 0; rep <= TUNE_REPS; ++rep) {
     BCS_CU(s, cudaEventRecord(e0, s->stream));
     if (L.smap == 1)
-      BCS_LAUNCH(s, K_TUNE, 0, 0, (k_tpr<N, TV, true>), g, 128, 0, L.A.rows, L.nslices, L.A.rp.p, L.sptr.p,
-                 L.sci.p, sv, L.dinv32.p, x, b, y, 0.8f);
+      BCS_LAUNCH(s, K_TUNE, 0, 0, (k_tpr<N, TV, true>), g, 128, 0, L.A.rows, L.nslices, L.A.rp.p, L.srow.p,
+                 L.sptr.p, L.sci.p, sv, L.dinv32.p, x, b, y, 0.8f);
     else
       BCS_LAUNCH(s, K_TUNE, 0, 0, (k_sell<N, TV, true>), g, 128, 0, L.A.rows, L.nslices, L.A.rp.p, L.sptr.p,
                  L.sci.p, sv, L.dinv32.p, x, b, y, 0.8f);

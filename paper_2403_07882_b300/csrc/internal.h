@@ -94,6 +94,13 @@ struct Bsr {
   DBuf<double> v;
 };
 
+// Plan of the tentative Galerkin product: per coarse row I its fine blocks
+// in ascending position, seqk[seg[I] .. seg[I+1]), and each one's output
+// block seqd (the first term of an output flagged by the sign bit).
+struct TentPlan {
+  DBuf<int32_t> seg, seqk, seqd;
+};
+
 struct Level {
   Bsr A;                     // FP64 operator of this level
   DBuf<int32_t> dpos;        // diagonal block position per row
@@ -105,7 +112,7 @@ struct Level {
   DBuf<int32_t> mptr, mem;   // aggregate member lists (members ascending)
   Bsr P, R, AP;              // smoothed mode only: P, R and the product A P (FP64)
   DBuf<int32_t> Prow, Rrow, AProw, Crow;  // row of every nonzero of P, R, AP, A_{l+1}
-  DBuf<int32_t> cg_ptr, cg_list;  // tentative Galerkin product gather lists
+  TentPlan tent;              // plan of the tentative Galerkin product
   DBuf<float> P32, R32;
   DBuf<bf16> P16, R16;
   double omega_p = 0.0;
@@ -119,6 +126,7 @@ struct Level {
   int smap = -1;
   int nslices = 0, nsteps = 0;
   DBuf<int32_t> sptr, sci;
+  DBuf<int32_t> srow;        // layout 1: block row at each slice position
   DBuf<float> s32;
   DBuf<bf16> s16;
   DBuf<char> vx, vb, vr, vt; // V-cycle vectors (cycle precision)

@@ -242,15 +242,23 @@ __global__ void k_cand_count_tent(int nagg, const int32_t* __restrict__ mptr, co
   if (I < nagg) cnt[I] = c;
 }
 
-// One thread per fine row: its blocks' candidates, contiguous in its coarse
-// row's segment.
+// One thread per fine row: its blocks' candidates (coarse column, index in
+// the coarse row's sequence of fine positions), contiguous in its coarse
+// row's segment, and that sequence itself (seqk). Members ascending and each
+// row's blocks ascending make the sequence ascending in position, so sorting
+// by (column, index) orders every run as the fine positions do.
 __global__ void k_cand_pack_tent(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                  const int32_t* __restrict__ agg, const int32_t* __restrict__ cptr,
-                                 const int32_t* __restrict__ moff, uint64_t* __restrict__ cand) {
+                                 const int32_t* __restrict__ moff, uint64_t* __restrict__ cand,
+                                 int32_t* __restrict__ seqk) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const long long o = (long long)cptr[agg[i]] + moff[i] - rp[i];
-  for (int p = rp[i]; p < rp[i + 1]; ++p) cand[o + p] = ((uint64_t)(uint32_t)agg[ci[p]] << 32) | (uint32_t)p;
+  const uint32_t l0 = (uint32_t)(moff[i] - rp[i]);
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    cand[o + p] = ((uint64_t)(uint32_t)agg[ci[p]] << 32) | (l0 + (uint32_t)p);
+    seqk[o + p] = p;
+  }
 }
 
 // Number of runs (distinct columns) in each sorted segment; longest -> *mx
@@ -274,97 +282,107 @@ __global__ void k_runs_count(int rows, const int32_t* __restrict__ seg, const ui
   if (i < rows) cnt[i] = c;
 }
 
-// One output block per run: column col[o], first list entry gptr[o]; the
-// list holds the source positions (gptr[nnz] = total).
+// One output block per run: column col[o]; every fine block of the run gets
+// seqd = o at its place in the coarse row's sequence, the run's first (in
+// position order) flagged by the sign bit.
+constexpr int32_t TS_FIRST = INT32_MIN;
+
 __global__ void k_runs_emit(int rows, const int32_t* __restrict__ seg, const uint64_t* __restrict__ cand,
-                            const int32_t* __restrict__ rp, int32_t* __restrict__ col, int32_t* __restrict__ gptr,
-                            int32_t* __restrict__ glist) {
+                            const int32_t* __restrict__ rp, int32_t* __restrict__ col, int32_t* __restrict__ seqd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
-  int o = rp[i];
+  int o = rp[i] - 1;
   uint32_t prev = 0;
   for (int t = seg[i]; t < seg[i + 1]; ++t) {
     const uint64_t v = cand[t];
     const uint32_t J = (uint32_t)(v >> 32);
-    glist[t] = (int32_t)(uint32_t)v;
-    if (t == seg[i] || J != prev) {
-      col[o] = (int32_t)J;
-      gptr[o] = t;
-      ++o;
-    }
+    const bool first = t == seg[i] || J != prev;
+    if (first) col[++o] = (int32_t)J;
+    seqd[seg[i] + (int32_t)(uint32_t)v] = first ? (o | TS_FIRST) : o;
     prev = J;
   }
-  if (i == rows - 1) gptr[rp[rows]] = seg[rows];
 }
-
-// Coarse block values: out[q] = left-to-right FP64 sum from +0 of the fine
-// blocks src[list[ptr[q]] ..]. The first add 0 + v equals v except that -0
-// becomes +0, so a sum starts from its first term with that sign fix
-// (integer operations). One thread per output element, LS_OUT outputs per
-// thread; list entries and their values are fetched LS_CH at a time (two
-// memory round trips per chunk), and each add runs only where some lane of
-// the warp needs it (a predicated-off FP64 add would still take an FP64
-// issue slot). One pass: the grid covers every element (the launch
-// guarantees it) and every lane reaches the votes.
-constexpr int LS_OUT = 1;
-constexpr int LS_CH = 2;
 
 __device__ __forceinline__ double plus_zero(double v) {
   const long long b = __double_as_longlong(v);
   return b == (long long)0x8000000000000000ll ? 0.0 : v;  // 0 + v, without the add
 }
 
+// Coarse block values of P_tent^T A P_tent: out[q] = left-to-right FP64 sum
+// from +0 of the fine blocks of q in position order. One group of lanes per
+// coarse row walks the row's fine blocks in ascending position (seqk),
+// adding each into the accumulator of its output block (seqd), so every
+// output sees its terms in position order. Lane e of a group owns entry e
+// (and e + 32, ... when n^2 > 32) of every output block of the row; its
+// accumulators sit in its own column of shared memory (rows with more than
+// cap output blocks accumulate in place in global memory). The first term of
+// an output is stored, not added: 0 + v equals v except that -0 becomes +0
+// (integer operations), so no FP64 add is spent on it. TS_U fine blocks are
+// fetched per round trip.
+constexpr int TS_U = 8;
+constexpr int TS_WARPS = 4;
+constexpr int TS_SMEM_DOUBLES = 32;  // per lane: cap * ceil(n^2 / 32) <= this
+
 template <int NN>
-__global__ void __launch_bounds__(256) k_list_sum(unsigned nout, const int32_t* __restrict__ gptr,
-                                                  const int32_t* __restrict__ glist,
-                                                  const double* __restrict__ src, double* __restrict__ out) {
-  const unsigned total = nout * NN;
-  const unsigned T = gridDim.x * blockDim.x;
-  const unsigned base = blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned e[LS_OUT];
-  int pb[LS_OUT], len[LS_OUT];
-  double acc[LS_OUT];
-  int mylen = 0;
+struct TentShape {
+  static constexpr int W = NN >= 32 ? 32 : NN;  // lanes per coarse row
+  static constexpr int G = 32 / W;              // coarse rows per warp
+  static constexpr int E = (NN + 31) / 32;      // entries per lane
+};
+
+template <int NN>
+__global__ void __launch_bounds__(TS_WARPS * 32) k_tent_sum(int nagg, int cap, const int32_t* __restrict__ seg,
+                                                           const int32_t* __restrict__ seqk,
+                                                           const int32_t* __restrict__ seqd,
+                                                           const int32_t* __restrict__ crp,
+                                                           const double* __restrict__ src, double* out) {
+  using S = TentShape<NN>;
+  extern __shared__ double ts_acc[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / S::W, e0 = lane - g * S::W;
+  const int I = (blockIdx.x * TS_WARPS + warp) * S::G + g;
+  if (g >= S::G || I >= nagg) return;
+  const int base = crp[I], slots = crp[I + 1] - base;
+  const bool in_smem = slots <= cap;
+  // accumulator of (slot, j): acc + slot * ss + j * sj
+  double* acc = in_smem ? ts_acc + (size_t)warp * 32 * cap * S::E + lane : out + (size_t)base * NN + e0;
+  const int ss = in_smem ? 32 * S::E : NN, sj = in_smem ? 32 : S::W;
+  const int t1 = seg[I + 1];
+  for (int t = seg[I]; t < t1; t += TS_U) {
+    int k[TS_U], d[TS_U];
 #pragma unroll
-  for (int u = 0; u < LS_OUT; ++u) {
-    const unsigned t = base + u * T;
-    const bool ok = t < total;
-    const unsigned q = ok ? t / NN : 0;
-    e[u] = ok ? t - q * NN : 0;
-    pb[u] = ok ? __ldg(gptr + q) : 0;
-    len[u] = ok ? __ldg(gptr + q + 1) - pb[u] : 0;
-    mylen = max(mylen, len[u]);
-    acc[u] = 0.0;
-  }
-  const int wmax = __reduce_max_sync(0xffffffffu, mylen);
-  for (int o = 0; o < wmax; o += LS_CH) {
-    int k[LS_OUT][LS_CH];
-    double v[LS_OUT][LS_CH];
+    for (int u = 0; u < TS_U; ++u) {
+      const bool ok = t + u < t1;
+      k[u] = ok ? __ldg(seqk + t + u) : -1;
+      d[u] = ok ? __ldg(seqd + t + u) : 0;
+    }
+    double v[TS_U][S::E];
 #pragma unroll
-    for (int u = 0; u < LS_OUT; ++u)
+    for (int u = 0; u < TS_U; ++u)
 #pragma unroll
-      for (int c = 0; c < LS_CH; ++c) k[u][c] = o + c < len[u] ? __ldg(glist + pb[u] + o + c) : -1;
-#pragma unroll
-    for (int u = 0; u < LS_OUT; ++u)
-#pragma unroll
-      for (int c = 0; c < LS_CH; ++c) v[u][c] = k[u][c] >= 0 ? __ldg(src + (size_t)k[u][c] * NN + e[u]) : 0.0;
-#pragma unroll
-    for (int u = 0; u < LS_OUT; ++u)
-#pragma unroll
-      for (int c = 0; c < LS_CH; ++c) {
-        const bool need = k[u][c] >= 0;
-        if (o + c == 0) {
-          acc[u] = plus_zero(v[u][0]);
-        } else if (__any_sync(0xffffffffu, need)) {
-          if (need) acc[u] = acc[u] + v[u][c];
-        }
+      for (int j = 0; j < S::E; ++j) {
+        const int e = e0 + j * S::W;
+        v[u][j] = (k[u] >= 0 && e < NN) ? __ldg(src + (size_t)k[u] * NN + e) : 0.0;
       }
-  }
 #pragma unroll
-  for (int u = 0; u < LS_OUT; ++u) {
-    const unsigned t = base + u * T;
-    if (t < total) out[t] = acc[u];
+    for (int u = 0; u < TS_U; ++u) {
+      if (k[u] < 0) continue;
+      double* a = acc + (size_t)((d[u] & ~TS_FIRST) - base) * ss;
+#pragma unroll
+      for (int j = 0; j < S::E; ++j) {
+        if (e0 + j * S::W >= NN) continue;
+        if (d[u] < 0)
+          a[j * sj] = plus_zero(v[u][j]);
+        else
+          a[j * sj] = a[j * sj] + v[u][j];
+      }
+    }
   }
+  if (in_smem)
+    for (int q = 0; q < slots; ++q)
+#pragma unroll
+      for (int j = 0; j < S::E; ++j)
+        if (e0 + j * S::W < NN) out[(size_t)(base + q) * NN + e0 + j * S::W] = acc[q * ss + j * sj];
 }
 
 // ----------------------------------------------------- smoothed prolongation
@@ -747,36 +765,35 @@ bcs_status members(Solver* s, int rows, int nagg, const int32_t* agg, DBuf<int32
   return segmented_sort_unique(s, mptr.p, mem.p, cnt.p, nagg, mx);
 }
 
-// Gather lists of the tentative Galerkin product (see k_list_sum).
-struct TentPlan {
-  DBuf<int32_t> ptr, list;
-};
-
 // Pattern of A_c = P_tent^T A P_tent (row I: sorted aggregates of its
-// members' columns) and its gather lists, from one segmented sort of packed
-// (coarse column, fine position) candidates. Sets A_c.maxrow. Two host reads.
+// members' columns) and the plan of k_tent_sum (per coarse row its fine
+// blocks in position order and each one's output block), from one segmented
+// sort of packed (coarse column, sequence index) candidates. Sets A_c.maxrow.
+// Two host reads.
 bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, const int32_t* mptr,
                         const int32_t* mem, Bsr& Ac, TentPlan& plan) {
-  DBuf<int32_t> cnt, cptr, hv, moff;
+  DBuf<int32_t> cnt, hv, moff;
   BCS_ALLOC(s, cnt, nagg);
-  BCS_ALLOC(s, cptr, nagg + 1);
+  BCS_ALLOC(s, plan.seg, nagg + 1);
   BCS_ALLOC(s, hv, 4);
   BCS_ALLOC(s, moff, A.rows);
   BCS_CU(s, cudaMemsetAsync(hv.p, 0, 4 * sizeof(int32_t), s->stream));
   BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p, cnt.p,
              moff.p, hv.p + 1);
-  BCS_OKR(exclusive_scan(s, cnt.p, cptr.p, nagg));
+  BCS_OKR(exclusive_scan(s, cnt.p, plan.seg.p, nagg));
   int32_t h[2] = {0, 0};
   BCS_CU(s, cudaMemcpyAsync(h, hv.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
   BCS_CU(s, cudaStreamSynchronize(s->stream));
   const int max_c = h[1];
   DBuf<uint64_t> cand;
   BCS_ALLOC(s, cand, A.nnz);
-  BCS_LAUNCH(s, K_SETUP_GAL, 16.0 * A.nnz, 0, k_cand_pack_tent, grid_for(A.rows, 256), 256, 0, A.rows, A.rp.p,
-             A.ci.p, agg, cptr.p, moff.p, cand.p);
-  BCS_OKR(segmented_sort64(s, cptr.p, cand.p, nagg, max_c));
-  BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_runs_count, grid_for(nagg, 256), 256, 0, nagg, cptr.p, cand.p, cnt.p,
-             hv.p + 3);
+  BCS_ALLOC(s, plan.seqk, A.nnz);
+  BCS_ALLOC(s, plan.seqd, A.nnz);
+  BCS_LAUNCH(s, K_SETUP_GAL, 20.0 * A.nnz, 0, k_cand_pack_tent, grid_for(A.rows, 256), 256, 0, A.rows, A.rp.p,
+             A.ci.p, agg, plan.seg.p, moff.p, cand.p, plan.seqk.p);
+  BCS_OKR(segmented_sort64(s, plan.seg.p, cand.p, nagg, max_c));
+  BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_runs_count, grid_for(nagg, 256), 256, 0, nagg, plan.seg.p, cand.p,
+             cnt.p, hv.p + 3);
   BCS_ALLOC(s, Ac.rp, nagg + 1);
   BCS_OKR(exclusive_scan(s, cnt.p, Ac.rp.p, nagg));
   BCS_CU(s, cudaMemcpyAsync(hv.p + 2, Ac.rp.p + nagg, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->stream));
@@ -786,10 +803,8 @@ bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, c
   Ac.nnz = h[0];
   Ac.maxrow = h[1];
   BCS_ALLOC(s, Ac.ci, Ac.nnz);
-  BCS_ALLOC(s, plan.ptr, Ac.nnz + 1);
-  BCS_ALLOC(s, plan.list, A.nnz);
-  BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * A.nnz + 8.0 * Ac.nnz, 0, k_runs_emit, grid_for(nagg, 256), 256, 0, nagg, cptr.p,
-             cand.p, Ac.rp.p, Ac.ci.p, plan.ptr.p, plan.list.p);
+  BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz + 4.0 * Ac.nnz, 0, k_runs_emit, grid_for(nagg, 256), 256, 0, nagg,
+             plan.seg.p, cand.p, Ac.rp.p, Ac.ci.p, plan.seqd.p);
   return BCS_OK;
 }
 
@@ -798,11 +813,15 @@ bcs_status tent_values(Solver* s, const Bsr& A, const TentPlan& plan, Bsr& Ac) {
   BCS_ALLOC(s, Ac.v, (size_t)Ac.nnz * n * n);
   return with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
+    using S = TentShape<N * N>;
     if ((size_t)Ac.nnz * N * N >= (1ull << 31)) return s->fail(BCS_EINVAL, "Galerkin product too large");
-    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + Ac.nnz) * N * N + 4.0 * A.nnz + 4.0 * Ac.nnz,
-               1.0 * (A.nnz - Ac.nnz) * N * N, k_list_sum<N * N>,
-               grid_for(((size_t)Ac.nnz * N * N + LS_OUT - 1) / LS_OUT, 256), 256, 0, (unsigned)Ac.nnz, plan.ptr.p,
-               plan.list.p, A.v.p, Ac.v.p);
+    const int nagg = Ac.rows;
+    const int cap = std::min(Ac.maxrow, TS_SMEM_DOUBLES / S::E);
+    const size_t smem = (size_t)TS_WARPS * 32 * cap * S::E * sizeof(double);
+    const unsigned grid = grid_for(nagg, TS_WARPS * S::G);
+    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + Ac.nnz) * N * N + 8.0 * A.nnz + 8.0 * (nagg + 1),
+               1.0 * (A.nnz - Ac.nnz) * N * N, k_tent_sum<N * N>, grid, TS_WARPS * 32, smem, nagg, cap, plan.seg.p,
+               plan.seqk.p, plan.seqd.p, Ac.rp.p, A.v.p, Ac.v.p);
     return BCS_OK;
   });
 }
@@ -1007,17 +1026,8 @@ bcs_status build_transfer(Solver* s, int l, bool full) {
   Level& Lc = s->lv[l + 1];
   if (full) BCS_OKR(members(s, L.A.rows, L.nagg, L.agg.p, L.mptr, L.mem));
   if (s->setup_cfg.pmode == BCS_P_TENTATIVE) {
-    TentPlan plan;
-    if (full) {
-      BCS_OKR(tent_pattern(s, L.A, L.nagg, L.agg.p, L.mptr.p, L.mem.p, Lc.A, plan));
-    } else {
-      plan.ptr = std::move(L.cg_ptr);
-      plan.list = std::move(L.cg_list);
-    }
-    const bcs_status st = tent_values(s, L.A, plan, Lc.A);
-    L.cg_ptr = std::move(plan.ptr);
-    L.cg_list = std::move(plan.list);
-    BCS_OKR(st);
+    if (full) BCS_OKR(tent_pattern(s, L.A, L.nagg, L.agg.p, L.mptr.p, L.mem.p, Lc.A, L.tent));
+    BCS_OKR(tent_values(s, L.A, L.tent, Lc.A));
   } else {
     BCS_OKR(smoothed_prolongation(s, L, full));
     BCS_OKR(spgemm(s, L.A, L.P, L.AP, L.AProw, full));
