@@ -12,6 +12,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.cpp")
+_SRCS = [_SRC, os.path.join(_HERE, "assembly.cpp")]
 
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -38,10 +39,10 @@ class Result(ct.Structure):
 def build(force=False):
     """Compile liboracle.so (plain C++17, no implicit FMA contraction)."""
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+            [os.path.getmtime(p) for p in _SRCS] + [os.path.getmtime(os.path.join(_HERE, "oracle.h"))]):
         return _SO
     cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", _SO, _SRC]
+           "-shared", "-o", _SO] + _SRCS
     subprocess.check_call(cmd)
     return _SO
 
@@ -82,6 +83,13 @@ def lib():
                                _f64p, _f64p, ct.POINTER(Result), ct.c_void_p, ct.c_int]
         L.or_fgmres_arnoldi.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, ct.c_void_p,
                                         ct.POINTER(Config), _f64p, ct.c_int, _f64p, _f64p, _f64p]
+        d3 = [_f64p, _f64p, ct.c_double, _f64p]
+        L.or_euler_flux.argtypes = d3
+        L.or_flux_jacobian.argtypes = d3
+        L.or_face_lambda.argtypes = [_f64p, _f64p, _f64p, ct.c_double, ct.c_double, ct.c_double, ct.c_double,
+                                     ct.POINTER(ct.c_double)]
+        L.or_assemble_density.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p,
+                                          ct.c_double, ct.c_double, ct.c_double, ct.c_double, _f64p, _f64p, _f64p]
         _lib = L
     return _lib
 
@@ -310,3 +318,44 @@ def dilu_apply(bsr, colour_, einv, r):
                         np.ascontiguousarray(einv, np.float64).ravel(),
                         np.ascontiguousarray(r, np.float64).ravel(), z.reshape(-1))
     return z
+
+
+# ---- assembly of the density-based system (assembly.cpp) -------------------
+FLOW_DEFAULTS = dict(gamma=1.4, mu=1e-3, prandtl=0.72, cfl=10.0)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, np.float64)
+
+
+def euler_flux(Q, n, gamma=1.4):
+    """Inviscid normal flux F(Q, n) of one state; None for an invalid state."""
+    F = np.zeros(5)
+    return None if lib().or_euler_flux(_f64(Q), _f64(n), gamma, F) else F
+
+
+def flux_jacobian(Q, n, gamma=1.4):
+    """J(Q, n) = dF/dQ (5 x 5); None for an invalid state."""
+    J = np.zeros(25)
+    return None if lib().or_flux_jacobian(_f64(Q), _f64(n), gamma, J) else J.reshape(5, 5)
+
+
+def face_lambda(Qo, Qn, n, d, gamma=1.4, mu=1e-3, prandtl=0.72):
+    lam = ct.c_double()
+    st = lib().or_face_lambda(_f64(Qo), _f64(Qn), _f64(n), d, gamma, mu, prandtl, ct.byref(lam))
+    return None if st else lam.value
+
+
+def assemble_density(flow, **prm):
+    """LDU blocks (diag, upper, lower) of the density-based system from a
+    flow dict (synth.flow); (status, diag, upper, lower)."""
+    p = dict(FLOW_DEFAULTS, **prm)
+    C, F = flow["n_cells"], flow["n_faces"]
+    diag = np.zeros((C, 5, 5))
+    upper = np.zeros((F, 5, 5))
+    lower = np.zeros((F, 5, 5))
+    st = lib().or_assemble_density(C, F, flow["owner"], flow["neighbour"], _f64(flow["Q"]).ravel(),
+                                   _f64(flow["area"]), _f64(flow["normal"]).ravel(), _f64(flow["dist"]),
+                                   p["gamma"], p["mu"], p["prandtl"], p["cfl"], diag.reshape(-1),
+                                   upper.reshape(-1), lower.reshape(-1))
+    return st, diag, upper, lower

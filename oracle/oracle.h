@@ -166,6 +166,20 @@ int or_fgmres_arnoldi(int rows, int n, const int32_t* row_ptr, const int32_t* co
                       const double* val, const or_amg* h, const or_config* cfg,
                       const double* b, int j_steps, double* V, double* Z, double* H);
 
+/* ---- Assembly of the density-based system (assembly.cpp) -------------- */
+/* Sec. 2.1, Eqs. approxJac1 / approxJac2 and Eq. discretBackward. Q per cell
+ * = (rho, rho u, rho v, rho w, rho E), ideal gas with ratio gamma. Returns 0,
+ * or 1 for an invalid state (rho <= 0 or p <= 0) or parameter. */
+int or_euler_flux(const double* Q, const double* n, double gamma, double* F);
+int or_flux_jacobian(const double* Q, const double* n, double gamma, double* J);
+int or_face_lambda(const double* Qo, const double* Qn, const double* n, double d, double gamma, double mu,
+                   double prandtl, double* lam);
+/* diag[C][5][5], upper / lower[F][5][5] of the LDU input (upper = block
+ * (owner, neighbour)); normal[F][3] unit, from owner to neighbour. */
+int or_assemble_density(int C, int F, const int32_t* owner, const int32_t* nb, const double* Q,
+                        const double* area, const double* normal, const double* dist, double gamma, double mu,
+                        double prandtl, double cfl, double* diag, double* upper, double* lower);
+
 #ifdef __cplusplus
 }
 #endif

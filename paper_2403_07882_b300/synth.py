@@ -21,6 +21,8 @@ in for them with the block structure of Sec. 2.1 and Sec. 2.2):
     knn(npts, seed)             unstructured: jittered lattice, k-nearest
                                 neighbour faces, 5x5 blocks as density()
     perturb(sys, rng, eps)      values-only change on a fixed sparsity
+    flow(nx, ny, nz, seed)      cell flow state Q and face geometry of a hex
+                                grid, the input of the density-based assembly
 """
 import numpy as np
 
@@ -248,3 +250,56 @@ CONFIGS = {
     "c3": lambda: density(128, seed=2),
     "c4": lambda: knn(160, seed=3),
 }
+
+
+def flow(nx=16, ny=None, nz=None, seed=5, gamma=1.4, mach=0.5, skew=False):
+    """Flow state and face geometry for assembling the density-based system
+    (Sec. 2.1) on an nx*ny*nz hex grid of cubic cells, spacing h = 1/nx.
+
+    Per cell (x, y, z the cell centre), with N ~ N(0, 1) drawn in this order:
+        rho = 1 + 0.1 sin(2 pi x) cos(2 pi y) + 0.02 N
+        p   = (1 + 0.1 cos(2 pi z) + 0.02 N) / gamma        (sound speed ~ 1)
+        u   = mach * (1 + 0.1 N, 0.2 sin(2 pi x) + 0.1 N, 0.1 N)
+        Q   = (rho, rho u, rho v, rho w, p / (gamma - 1) + rho |u|^2 / 2)
+    then b ~ U(-1, 1) per unknown. Faces as density() (owner < neighbour,
+    upper-triangular order) with area h^2, unit normal along +axis (owner to
+    neighbour) and centre distance h. skew=True then perturbs the geometry:
+    normal = unit(axis + 0.3 N^3), area and distance x (1 + 0.2 U(-1, 1)).
+    """
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    C = nx * ny * nz
+    h = 1.0 / nx
+    lo, hi, axis = _hex_faces(nx, ny, nz)
+    owner, neighbour, axis = _sort_faces(lo, hi, axis)
+    F = owner.size
+    idx = np.arange(C)
+    x = (idx % nx + 0.5) * h
+    y = ((idx // nx) % ny + 0.5) * h
+    z = (idx // (nx * ny) + 0.5) * h
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + 0.1 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) + 0.02 * rng.standard_normal(C)
+    p = (1.0 + 0.1 * np.cos(2 * np.pi * z) + 0.02 * rng.standard_normal(C)) / gamma
+    N = rng.standard_normal((C, 3))
+    u = mach * np.stack([1.0 + 0.1 * N[:, 0], 0.2 * np.sin(2 * np.pi * x) + 0.1 * N[:, 1], 0.1 * N[:, 2]], -1)
+    Q = np.empty((C, 5))
+    Q[:, 0] = rho
+    Q[:, 1:4] = rho[:, None] * u
+    Q[:, 4] = p / (gamma - 1.0) + 0.5 * rho * (u * u).sum(-1)
+    b = rng.uniform(-1.0, 1.0, (C, 5))
+    normal = np.zeros((F, 3))
+    normal[np.arange(F), axis] = 1.0
+    area = np.full(F, h * h)
+    dist = np.full(F, h)
+    if skew:
+        normal += 0.3 * rng.standard_normal((F, 3))
+        normal /= np.linalg.norm(normal, axis=1, keepdims=True)
+        area *= 1.0 + 0.2 * rng.uniform(-1.0, 1.0, F)
+        dist *= 1.0 + 0.2 * rng.uniform(-1.0, 1.0, F)
+    return dict(n_cells=int(C), n_faces=int(F), n=5,
+                owner=np.ascontiguousarray(owner, dtype=np.int32),
+                neighbour=np.ascontiguousarray(neighbour, dtype=np.int32),
+                Q=np.ascontiguousarray(Q), area=np.ascontiguousarray(area),
+                normal=np.ascontiguousarray(normal), dist=np.ascontiguousarray(dist),
+                b=np.ascontiguousarray(b), gamma=gamma,
+                name=f"flow {nx}x{ny}x{nz} mach={mach} seed={seed}{' skewed' if skew else ''}")
