@@ -710,6 +710,10 @@ or_amg* or_amg_setup(int rows, int n, const int32_t* rp, const int32_t* ci, cons
     if (cfg->smoother == 1) {
       L.ncol = colour_rows(L.A, L.colour);
       if (L.ncol > 0 && dilu_factor(L.A, L.colour, L.einv)) { *status = 6; return h; }
+    } else if (cfg->smoother == 2) {
+      // SGS: the DILU form with E = D (no modification of the diagonal)
+      L.ncol = colour_rows(L.A, L.colour);
+      if (L.ncol > 0) L.einv = L.dinv;
     }
     const int C = L.A.rows;
     bool last = C <= cfg->coarse_size || l == cfg->max_levels - 1;
@@ -942,6 +946,12 @@ struct Sys {
   const or_amg* h;
   const or_config* cfg;
   std::vector<double> dinv;
+  // precond = 3: multicolour block SGS, M = (D + L) D^-1 (D + U) with the
+  // colour order of the DILU smoother (ncol <= 0: more colours than allowed,
+  // block Jacobi instead)
+  Bsr A;
+  std::vector<int32_t> colour;
+  int ncol = 0;
 };
 
 double dot(const std::vector<double>& a, const std::vector<double>& b) {
@@ -960,7 +970,9 @@ void precond(const Sys& S, const std::vector<double>& v, std::vector<double>& z)
   z.resize(S.N);
   if (S.cfg->precond == 0) {
     or_amg_vcycle(S.h, v.data(), z.data());
-  } else if (S.cfg->precond == 2) {
+  } else if (S.cfg->precond == 3 && S.ncol > 0) {
+    dilu_apply(S.A, S.colour, S.ncol, S.dinv, v.data(), z.data());
+  } else if (S.cfg->precond == 2 || S.cfg->precond == 3) {
     const int n = S.n, nn = n * n;
     for (int i = 0; i < S.rows; ++i)
       for (int a = 0; a < n; ++a) {
@@ -1176,10 +1188,10 @@ int bicgstab(const Sys& S, const double* b, double* x0, or_result* res, double* 
 
 Sys make_sys(int rows, int n, const int32_t* rp, const int32_t* ci, const double* val,
              const or_amg* h, const or_config* cfg, int* bad) {
-  Sys S{rows, n, rows * n, rp, ci, val, h, cfg, {}};
+  Sys S{rows, n, rows * n, rp, ci, val, h, cfg, {}, {}, {}, 0};
   *bad = 0;
-  if (cfg->precond == 2) {
-    Bsr A;
+  if (cfg->precond == 2 || cfg->precond == 3) {
+    Bsr& A = S.A;
     A.rows = rows;
     A.cols = rows;
     A.n = n;
@@ -1187,6 +1199,7 @@ Sys make_sys(int rows, int n, const int32_t* rp, const int32_t* ci, const double
     A.ci.assign(ci, ci + rp[rows]);
     A.v.assign(val, val + (size_t)rp[rows] * n * n);
     *bad = diag_inverses(A, S.dinv);
+    if (cfg->precond == 3) S.ncol = colour_rows(A, S.colour);
   }
   return S;
 }

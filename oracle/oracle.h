@@ -40,7 +40,8 @@ typedef struct {
   int restart;           /* FGMRES restart length m */
   double tol;            /* relative residual target ||b - A x|| / ||b|| */
   int maxiter;           /* total Krylov iterations allowed */
-  int precond;           /* 0 = AMG V-cycle, 1 = none, 2 = block Jacobi (one sweep) */
+  int precond;           /* 0 = AMG V-cycle, 1 = none, 2 = block Jacobi (one sweep),
+                            3 = multicolour block SGS (one application of M^-1) */
   int pmode;             /* 0 = smoothed prolongation, 1 = tentative (default) */
   int matching_rounds;   /* synchronous handshake rounds per matching pass */
   int agg_passes;        /* matching passes per level (2 gives aggregates of ~4) */
@@ -52,7 +53,8 @@ typedef struct {
   double p_omega;        /* prolongation smoothing numerator: omega_P = p_omega / rho */
   int coarse_dense_max;  /* dense inverse at the coarsest level if rows*n <= this */
   int coarse_sweeps;     /* otherwise this many smoother sweeps */
-  int smoother;          /* 0 = damped block Jacobi, 1 = multicolour block DILU */
+  int smoother;          /* 0 = damped block Jacobi, 1 = multicolour block DILU,
+                            2 = multicolour block SGS */
 } or_config;
 
 typedef struct {
