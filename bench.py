@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison run")
+    p.add_argument("--no-assembly", action="store_true", help="skip the density-based assembly measurement")
     p.add_argument("--workload", default="density128",
                    choices=["density128", "density16", "pressure64", "knn", "serve"],
                    help="density128: the benchmark line; density16 / pressure64: the small density-based and "
@@ -309,6 +310,8 @@ def run_native(args):
         e2e = {"value": ms_e2e, "unit": "ms", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(xh.numel() * 8)}
 
+    assembly = None if args.no_assembly else assembly_entry(args.side, dev, args.steps)
+
     ms_max = max_over_ranks(ms_mixed, dev) if world > 1 else ms_mixed
     if rank != 0:
         return
@@ -357,10 +360,85 @@ def run_native(args):
         "gpu_launches_per_step": stats["launches"] / args.steps,
         "clocks": clocks,
         "e2e": e2e,
+        "assembly": assembly,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_entry(args.side)
     print(json.dumps(line), flush=True)
+
+
+# FP64 operations per launch unit of the assembly kernels, counted from the
+# source (an FMA counts as one operation): k_face_lambda per face,
+# k_assemble_cells per face side plus per cell.
+ASSEMBLY_FP64_OPS = {"k_face_lambda": 150.0, "k_assemble_cells_face_side": 55.0, "k_assemble_cells_cell": 80.0}
+FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 vector peak (an FMA counted as two flops)
+
+
+def assembly_entry(side, dev, reps):
+    """Density-based assembly (Sec. 2.1) on the side^3 mesh: the assembly
+    kernels alone (LDU blocks on the device) and one nonlinear iteration
+    (assembly straight into the solver's values, values-only resetup, solve)."""
+    import torch
+    from paper_2403_07882_b300 import bcs, synth
+    fl = synth.flow(side, seed=5)
+    C, F = fl["n_cells"], fl["n_faces"]
+    g = {k: torch.from_numpy(np.ascontiguousarray(fl[k])).to(dev)
+         for k in ("owner", "neighbour", "Q", "area", "normal", "dist", "b")}
+    stream = torch.cuda.current_stream()
+    reps = max(3, reps)
+    with bcs.Solver(5, profile=1, profile_kinds=bcs.kind_mask("assembly")) as s:
+        s.set_structure(C, g["owner"], g["neighbour"])
+        out = (torch.empty((C, 5, 5), dtype=torch.float64, device=dev),
+               torch.empty((F, 5, 5), dtype=torch.float64, device=dev),
+               torch.empty((F, 5, 5), dtype=torch.float64, device=dev))
+        prm = bcs.bcs_flow_params_default()
+        for _ in range(2):
+            bcs.bcs_assemble_density(s.h, g["Q"], g["area"], g["normal"], g["dist"], prm, *out)
+        torch.cuda.synchronize()
+        s.reset_stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            bcs.bcs_assemble_density(s.h, g["Q"], g["area"], g["normal"], g["dist"], prm, *out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        kt = s.kernel_times()
+        # one nonlinear iteration: assemble into the solver's values (the first
+        # call runs the full setup), then values-only resetup + solve
+        s.assemble_density(g["Q"], g["area"], g["normal"], g["dist"], to_values=True)
+        x = torch.zeros_like(g["b"])
+        torch.cuda.synchronize()
+        e0.record(stream)
+        iters = []
+        for _ in range(reps):
+            s.assemble_density(g["Q"], g["area"], g["normal"], g["dist"], to_values=True)
+            x.zero_()
+            _, st, res = s.solve(g["b"], x)
+            assert st == bcs.BCS_OK, res
+            iters.append(res["iters"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_nl = e0.elapsed_time(e1) / reps
+    kernels = {}
+    for name, v in kt.items():
+        if not v["launches"]:
+            continue
+        per = v["ms"] / v["launches"]
+        kernels[name] = {"ms_per_launch": per, "GBps": v["bytes"] / v["launches"] / (per * 1e-3) / 1e9}
+    fp64_ops = (ASSEMBLY_FP64_OPS["k_face_lambda"] * F + ASSEMBLY_FP64_OPS["k_assemble_cells_face_side"] * 2 * F
+                + ASSEMBLY_FP64_OPS["k_assemble_cells_cell"] * C)
+    peak_ops = FP64_NOMINAL_TFLOPS * 1e12 / 2  # FP64 instructions per second (FMA = one)
+    return {"workload": f"density-based assembly (Sec. 2.1, Eqs. approxJac1/2), {side}^3 hex mesh, "
+                        f"{C} cells, {F} faces, LDU blocks on the device",
+            "ms": ms, "kernels": kernels,
+            "roofline": {"bound": "alu", "unit": "FP64 op/s", "achieved": fp64_ops / (ms * 1e-3),
+                         "peak": peak_ops, "frac": fp64_ops / (ms * 1e-3) / peak_ops,
+                         "peak_source": "nominal 1.25 TFLOP/s FP64 (FMA = 2 flops) = 0.625 T FP64 instructions/s",
+                         "ops_per_assembly": fp64_ops},
+            "nonlinear_iteration_ms": ms_nl, "nonlinear_iteration":
+                "assembly into the solver's values + values-only resetup + FGMRES solve to 1e-8",
+            "iters": iters[-1]}
 
 
 def run_system(args):

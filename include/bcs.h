@@ -62,7 +62,11 @@ typedef enum bcs_status {
 
 enum { BCS_MEM_HOST = 0, BCS_MEM_DEVICE = 1 };
 enum { BCS_FGMRES = 0, BCS_BICGSTAB = 1 };
-enum { BCS_PC_AMG = 0, BCS_PC_NONE = 1, BCS_PC_JACOBI = 2 };
+/* BCS_PC_SGS: one application of the multicolour block symmetric
+ * Gauss-Seidel (LU-SGS) preconditioner M = (D + L) D^-1 (D + U), colour
+ * order as the DILU smoother (Sec. 2.1's CPU preconditioner; Sec. 5's GPU
+ * GMRES + SGS runs). */
+enum { BCS_PC_AMG = 0, BCS_PC_NONE = 1, BCS_PC_JACOBI = 2, BCS_PC_SGS = 3 };
 enum { BCS_P_SMOOTHED = 0, BCS_P_TENTATIVE = 1 };
 enum { BCS_PREC_FP64 = 0, BCS_PREC_FP32 = 1, BCS_PREC_BF16 = 2 };
 
@@ -73,14 +77,14 @@ enum { BCS_PREC_FP64 = 0, BCS_PREC_FP32 = 1, BCS_PREC_BF16 = 2 };
  * most 128 colours; a level needing more keeps block Jacobi); j precedes i
  * when colour(j) < colour(i); E_i = A_ii - sum_{j before i} A_ij E_j^-1 A_ji;
  * M = (E + L) E^-1 (E + U); one step x <- x + M^-1 (b - A x). */
-enum { BCS_SMOOTH_JACOBI = 0, BCS_SMOOTH_DILU = 1 };
+enum { BCS_SMOOTH_JACOBI = 0, BCS_SMOOTH_DILU = 1, BCS_SMOOTH_SGS = 2 };
 
 typedef struct bcs_config {
   int solver;              /* BCS_FGMRES (default) or BCS_BICGSTAB */
   int restart;             /* FGMRES restart length m (default 30, 1..64) */
   double tol;              /* stop when ||b - A x||_2 / ||b||_2 <= tol (1e-8) */
   int maxiter;             /* Krylov iteration cap (1000) */
-  int precond;             /* BCS_PC_AMG (default), BCS_PC_NONE, BCS_PC_JACOBI */
+  int precond;             /* BCS_PC_AMG (default), BCS_PC_NONE, BCS_PC_JACOBI, BCS_PC_SGS */
   int pmode;               /* BCS_P_TENTATIVE (default) or BCS_P_SMOOTHED */
   int matching_rounds;     /* handshake rounds per matching pass (4) */
   int agg_passes;          /* matching passes per level (2: aggregates of ~4) */
@@ -93,8 +97,9 @@ typedef struct bcs_config {
   int coarse_dense_max;    /* dense inverse at the coarsest level when rows*n <= this (1024) */
   int coarse_sweeps;       /* else this many block-Jacobi sweeps there (8) */
   int precision;           /* AMG storage: BCS_PREC_FP64, BCS_PREC_FP32 (default), BCS_PREC_BF16 */
-  int smoother;            /* BCS_SMOOTH_JACOBI (default, damped by jacobi_omega) or
-                              BCS_SMOOTH_DILU (multicolour block DILU, undamped) */
+  int smoother;            /* BCS_SMOOTH_JACOBI (default, damped by jacobi_omega),
+                              BCS_SMOOTH_DILU (multicolour block DILU, undamped) or
+                              BCS_SMOOTH_SGS (multicolour block SGS, undamped) */
   int profile;             /* 1: time kernels with CUDA events (bcs_get_stats) */
   int profile_kinds;       /* with profile = 1: bitmask of the kernel kinds to time (bit k:
                               kind k of bcs_kernel_kind_name); 0 = every kind */
@@ -166,6 +171,40 @@ BCS_API bcs_status bcs_set_structure(bcs_solver* s, int32_t n_cells, int32_t n_f
  * singular (the hierarchy is then dropped). */
 BCS_API bcs_status bcs_set_values(bcs_solver* s, const double* diag, const double* upper,
                           const double* lower, int mem);
+
+/* Flow parameters of the density-based assembly (bcs_assemble_density). */
+typedef struct bcs_flow_params {
+  double gamma;    /* ratio of specific heats, > 1 (default 1.4) */
+  double mu;       /* dynamic viscosity, >= 0 (default 1e-3) */
+  double prandtl;  /* Prandtl number, > 0 (default 0.72) */
+  double cfl;      /* pseudo-time CFL number, > 0 (default 10) */
+} bcs_flow_params;
+
+BCS_API bcs_status bcs_flow_params_default(bcs_flow_params* p);
+
+/* Assemble the density-based coupled system on the device (Sec. 2.1,
+ * Eqs. approxJac1 / approxJac2 with the pseudo-time term of
+ * Eq. discretBackward) on the structure of bcs_set_structure; n must be 5.
+ * Inputs (host or device per mem): Q[C][5] = (rho, rho u, rho v, rho w,
+ * rho E) per cell (ideal gas), area[F] face areas, normal[F][3] unit face
+ * normals pointing from owner to neighbour, dist[F] owner-neighbour centre
+ * distances. For face f with spectral radius lambda_f (Roe average of the two
+ * states plus max(4/3, gamma) mu / (Pr rho~ dist)):
+ *   A_oo += S/2 (J(Q_o, n) + lambda I),  upper[f] = S/2 (J(Q_nb, n) - lambda I),
+ *   A_nn += S/2 (-J(Q_nb, n) + lambda I), lower[f] = S/2 (-J(Q_o, n) - lambda I),
+ * J the inviscid normal-flux Jacobian, plus (sum_f lambda_f S_f / CFL) I on
+ * every diagonal block (local pseudo-time step). With diag, upper and lower
+ * all NULL the blocks are written straight into the solver's block-CSR values
+ * and the call continues as bcs_set_values (full setup or values-only
+ * resetup); otherwise diag[C][5][5], upper[F][5][5], lower[F][5][5] (in the
+ * inputs' memory space) receive the LDU blocks and the solver is unchanged.
+ * BCS_ESTATE before set_structure; BCS_EINVAL for n != 5, NULL inputs, bad
+ * parameters, a state with rho <= 0 or p <= 0 (or NaN), area < 0 or
+ * dist <= 0 (when writing the solver's values the solver is then left
+ * without values until the next successful upload). */
+BCS_API bcs_status bcs_assemble_density(bcs_solver* s, const double* Q, const double* area, const double* normal,
+                                        const double* dist, const bcs_flow_params* prm, double* diag,
+                                        double* upper, double* lower, int mem);
 
 /* Forget the hierarchy: the next set_values runs a full setup (new
  * aggregates). */

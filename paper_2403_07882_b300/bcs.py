@@ -20,10 +20,10 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "NOT_CONVERGED", "BREAKDOWN",
                 "SINGULAR_BLOCK", "TIMEOUT", "REJECTED", "ESTATE"]
 BCS_MEM_HOST, BCS_MEM_DEVICE = 0, 1
 BCS_FGMRES, BCS_BICGSTAB = 0, 1
-BCS_PC_AMG, BCS_PC_NONE, BCS_PC_JACOBI = 0, 1, 2
+BCS_PC_AMG, BCS_PC_NONE, BCS_PC_JACOBI, BCS_PC_SGS = 0, 1, 2, 3
 BCS_P_SMOOTHED, BCS_P_TENTATIVE = 0, 1
 BCS_PREC_FP64, BCS_PREC_FP32, BCS_PREC_BF16 = 0, 1, 2
-BCS_SMOOTH_JACOBI, BCS_SMOOTH_DILU = 0, 1
+BCS_SMOOTH_JACOBI, BCS_SMOOTH_DILU, BCS_SMOOTH_SGS = 0, 1, 2
 NUM_KERNEL_KINDS = 16
 
 
@@ -64,6 +64,10 @@ class bcs_server_stats(ct.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class bcs_flow_params(ct.Structure):
+    _fields_ = [("gamma", ct.c_double), ("mu", ct.c_double), ("prandtl", ct.c_double), ("cfl", ct.c_double)]
+
+
 class BcsError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 10 else status}: {msg}")
@@ -90,6 +94,9 @@ def lib():
             "bcs_set_structure": (ct.c_int, [_vp, ct.c_int32, ct.c_int32, _vp, _vp, ct.c_int]),
             "bcs_set_values": (ct.c_int, [_vp, _vp, _vp, _vp, ct.c_int]),
             "bcs_invalidate_hierarchy": (ct.c_int, [_vp]),
+            "bcs_flow_params_default": (ct.c_int, [ct.POINTER(bcs_flow_params)]),
+            "bcs_assemble_density": (ct.c_int, [_vp] + [_vp] * 4 + [ct.POINTER(bcs_flow_params)] + [_vp] * 3
+                                     + [ct.c_int]),
             "bcs_solve": (ct.c_int, [_vp, _vp, _vp, ct.c_int, ct.POINTER(bcs_result)]),
             "bcs_spmv": (ct.c_int, [_vp, _vp, _vp, ct.c_int]),
             "bcs_precond_apply": (ct.c_int, [_vp, _vp, _vp, ct.c_int]),
@@ -128,7 +135,8 @@ def lib():
 
 def exported_names():
     return ["bcs_config_default", "bcs_create", "bcs_destroy", "bcs_set_config", "bcs_set_structure",
-            "bcs_set_values", "bcs_invalidate_hierarchy", "bcs_solve", "bcs_spmv", "bcs_precond_apply",
+            "bcs_set_values", "bcs_invalidate_hierarchy", "bcs_flow_params_default", "bcs_assemble_density",
+            "bcs_solve", "bcs_spmv", "bcs_precond_apply",
             "bcs_get_bsr", "bcs_num_levels", "bcs_get_level_info", "bcs_get_level", "bcs_get_prolongation",
             "bcs_get_coarse_inverse", "bcs_get_dilu", "bcs_get_stats", "bcs_reset_stats", "bcs_get_kernel_times", "bcs_kernel_kind_name",
             "bcs_last_error", "bcs_device_bytes", "bcs_ldu_structure_noalloc", "bcs_server_create",
@@ -211,6 +219,21 @@ def bcs_set_structure(h, n_cells, owner, neighbour):
 def bcs_set_values(h, diag, upper, lower):
     (pd, pu, pl), mem = _ptr_mem(diag, upper, lower)
     return _check(lib().bcs_set_values(h, pd, pu, pl, mem), h)
+
+
+def bcs_flow_params_default(**overrides):
+    p = bcs_flow_params()
+    _check(lib().bcs_flow_params_default(ct.byref(p)))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def bcs_assemble_density(h, Q, area, normal, dist, prm, diag=None, upper=None, lower=None):
+    (pq, pa, pn, pd, pdg, pu, pl), mem = _ptr_mem(Q, area, normal, dist, diag, upper, lower)
+    return _check(lib().bcs_assemble_density(h, pq, pa, pn, pd, ct.byref(prm), pdg, pu, pl, mem), h)
 
 
 def bcs_invalidate_hierarchy(h):
@@ -400,6 +423,22 @@ class Solver:
             arr = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in arr.items()}
         self.set_structure(system["n_cells"], arr["owner"], arr["neighbour"])
         self.set_values(arr["diag"], arr["upper"], arr["lower"])
+
+    def assemble_density(self, Q, area, normal, dist, to_values=False, **prm):
+        """Density-based system from cell states and face geometry (Sec. 2.1).
+        to_values: write the solver's own values and set up (as set_values);
+        otherwise return (diag, upper, lower) in the inputs' memory space."""
+        p = bcs_flow_params_default(**prm)
+        if to_values:
+            bcs_assemble_density(self.h, Q, area, normal, dist, p)
+            return None
+        C, F = self.C, self.F
+        if isinstance(Q, np.ndarray):
+            out = [np.zeros((C, 5, 5)), np.zeros((F, 5, 5)), np.zeros((F, 5, 5))]
+        else:
+            out = [Q.new_zeros((C, 5, 5)), Q.new_zeros((F, 5, 5)), Q.new_zeros((F, 5, 5))]
+        bcs_assemble_density(self.h, Q, area, normal, dist, p, *out)
+        return tuple(out)
 
     def solve(self, b, x=None):
         if x is None:

@@ -14,7 +14,7 @@ const char* kind_name(int k) {
   static const char* names[K_NKINDS] = {"ldu_to_bsr", "spmv_fp64",   "jacobi_sweep", "residual",
                                         "transfer",   "coarse_solve", "blas1",       "setup_aggregation",
                                         "setup_galerkin", "setup_inverse", "cast",   "scan_sort",
-                                        "autotune"};
+                                        "autotune",   "assembly"};
   return (k >= 0 && k < K_NKINDS) ? names[k] : "";
 }
 
@@ -96,7 +96,7 @@ bcs_status check_config(const bcs_config* c) {
   if (c->solver != BCS_FGMRES && c->solver != BCS_BICGSTAB) return BCS_EINVAL;
   if (c->restart < 1 || c->restart > 64) return BCS_EINVAL;
   if (!(c->tol > 0.0) || c->maxiter < 1) return BCS_EINVAL;
-  if (c->precond < BCS_PC_AMG || c->precond > BCS_PC_JACOBI) return BCS_EINVAL;
+  if (c->precond < BCS_PC_AMG || c->precond > BCS_PC_SGS) return BCS_EINVAL;
   if (c->pmode != BCS_P_SMOOTHED && c->pmode != BCS_P_TENTATIVE) return BCS_EINVAL;
   if (c->matching_rounds < 1 || c->agg_passes < 1 || c->agg_passes > 4) return BCS_EINVAL;
   if (c->nu1 < 0 || c->nu2 < 0 || c->nu1 + c->nu2 < 1) return BCS_EINVAL;
@@ -105,7 +105,7 @@ bcs_status check_config(const bcs_config* c) {
   if (c->precision < BCS_PREC_FP64 || c->precision > BCS_PREC_BF16) return BCS_EINVAL;
   if (c->cycle_graph < -1 || c->cycle_graph > 1) return BCS_EINVAL;
   if (c->slice_layout < -1 || c->slice_layout > 1) return BCS_EINVAL;
-  if (c->smoother != BCS_SMOOTH_JACOBI && c->smoother != BCS_SMOOTH_DILU) return BCS_EINVAL;
+  if (c->smoother < BCS_SMOOTH_JACOBI || c->smoother > BCS_SMOOTH_SGS) return BCS_EINVAL;
   if (!(c->max_coarsen_ratio > 0.0) || !(c->p_omega > 0.0) || !(c->jacobi_omega > 0.0)) return BCS_EINVAL;
   return BCS_OK;
 }
@@ -142,6 +142,20 @@ bcs_status to_host(Solver* s, void* dst, const void* src, size_t bytes) {
   if (!dst || bytes == 0) return BCS_OK;
   BCS_CU(s, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->stream));
   BCS_CU(s, cudaStreamSynchronize(s->stream));
+  return BCS_OK;
+}
+
+// After new fine values: full AMG setup, or values-only resetup.
+bcs_status values_changed(Solver* s, std::chrono::steady_clock::time_point t0) {
+  s->have_values = true;
+  const bool full = !s->have_hierarchy;
+  if (full) s->setup_cfg = s->cfg;
+  s->have_hierarchy = false;
+  BCS_OKR(amg_setup(s, full));
+  BCS_OKR(cycle_prepare(s));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  s->have_hierarchy = true;
+  s->last_setup_ms = ms_since(t0);
   return BCS_OK;
 }
 
@@ -277,15 +291,66 @@ bcs_status bcs_set_values(bcs_solver* h, const double* diag, const double* upper
   BCS_OKR(stage(s, upper, s->F * nn, mem, s->stage_u, &u));
   BCS_OKR(stage(s, lower, s->F * nn, mem, s->stage_l, &l));
   BCS_OKR(permute_values(s, d, u, l));
-  s->have_values = true;
-  const bool full = !s->have_hierarchy;
-  if (full) s->setup_cfg = s->cfg;
-  s->have_hierarchy = false;
-  BCS_OKR(amg_setup(s, full));
-  BCS_OKR(cycle_prepare(s));
-  BCS_CU(s, cudaStreamSynchronize(s->stream));
-  s->have_hierarchy = true;
-  s->last_setup_ms = ms_since(t0);
+  return values_changed(s, t0);
+}
+
+bcs_status bcs_flow_params_default(bcs_flow_params* p) {
+  if (!p) return BCS_EINVAL;
+  p->gamma = 1.4;
+  p->mu = 1e-3;
+  p->prandtl = 0.72;
+  p->cfl = 10.0;
+  return BCS_OK;
+}
+
+bcs_status bcs_assemble_density(bcs_solver* h, const double* Q, const double* area, const double* normal,
+                                const double* dist, const bcs_flow_params* prm, double* diag, double* upper,
+                                double* lower, int mem) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  if (!s->have_structure) return s->fail(BCS_ESTATE, "assemble before set_structure");
+  if (s->n != 5) return s->fail(BCS_EINVAL, "the density-based assembly needs 5x5 blocks");
+  const bool to_values = !diag && !upper && !lower;
+  if (!prm || !Q || (s->F > 0 && (!area || !normal || !dist)) || (mem != BCS_MEM_HOST && mem != BCS_MEM_DEVICE) ||
+      (!to_values && (!diag || (s->F > 0 && (!upper || !lower)))))
+    return s->fail(BCS_EINVAL, "invalid assembly arguments");
+  if (!(prm->gamma > 1.0) || !(prm->mu >= 0.0) || !(prm->prandtl > 0.0) || !(prm->cfl > 0.0) ||
+      !std::isfinite(prm->gamma) || !std::isfinite(prm->mu) || !std::isfinite(prm->prandtl) ||
+      !std::isfinite(prm->cfl))
+    return s->fail(BCS_EINVAL, "invalid flow parameters");
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t C = s->C, F = s->F;
+  const double *q = nullptr, *a = nullptr, *nv = nullptr, *d = nullptr;
+  DBuf<double> sq, sa, sn, sd, od, ou, ol;
+  BCS_OKR(stage(s, Q, C * 5, mem, sq, &q));
+  BCS_OKR(stage(s, area, F, mem, sa, &a));
+  BCS_OKR(stage(s, normal, F * 3, mem, sn, &nv));
+  BCS_OKR(stage(s, dist, F, mem, sd, &d));
+  if (to_values) {
+    // the fine values are replaced: on failure the solver has no values and
+    // no hierarchy until the next successful upload
+    s->have_values = false;
+    const bool had = s->have_hierarchy;
+    s->have_hierarchy = false;
+    BCS_OKR(assemble_density(s, q, a, nv, d, *prm, nullptr, nullptr, nullptr));
+    s->have_hierarchy = had;
+    return values_changed(s, t0);
+  }
+  double *dd = diag, *du = upper, *dl = lower;
+  if (mem == BCS_MEM_HOST) {
+    BCS_ALLOC(s, od, C * 25);
+    BCS_ALLOC(s, ou, F > 0 ? F * 25 : 1);
+    BCS_ALLOC(s, ol, F > 0 ? F * 25 : 1);
+    dd = od.p;
+    du = ou.p;
+    dl = ol.p;
+  }
+  BCS_OKR(assemble_density(s, q, a, nv, d, *prm, dd, du, dl));
+  if (mem == BCS_MEM_HOST) {
+    BCS_OKR(to_host(s, diag, dd, C * 25 * sizeof(double)));
+    BCS_OKR(to_host(s, upper, du, F * 25 * sizeof(double)));
+    BCS_OKR(to_host(s, lower, dl, F * 25 * sizeof(double)));
+  }
   return BCS_OK;
 }
 

@@ -487,7 +487,8 @@ template bcs_status cast_vec<double, double>(Solver*, const double*, double*, si
 template bcs_status cast_vec<double, bf16>(Solver*, const double*, bf16*, size_t);
 
 bool cycle_is_float(const Solver* s) {
-  return s->setup_cfg.precond == BCS_PC_AMG && s->setup_cfg.precision != BCS_PREC_FP64;
+  return (s->setup_cfg.precond == BCS_PC_AMG || s->setup_cfg.precond == BCS_PC_SGS) &&
+         s->setup_cfg.precision != BCS_PREC_FP64;
 }
 
 // ------------------------------------------------------------ outer FP64 SpMV
@@ -654,6 +655,20 @@ struct Cycle {
     return BCS_OK;
   }
 
+  // Stand-alone SGS preconditioner on level 0: x = M^-1 b, the smoother step
+  // from x = 0 (block Jacobi when the level has more than 128 colours).
+  template <int N>
+  bcs_status sgs(const TC* b, TC* x) {
+    Level& L = s->lv[0];
+    const int rows = L.A.rows;
+    if (L.ncol > 0) {
+      BCS_CU(s, cudaMemsetAsync(x, 0, (size_t)rows * N * sizeof(TC), s->stream));
+      return dilu_step<N>(L, x, b);
+    }
+    BCS_LAUNCH(s, K_SWEEP, (double)rows * N * (N * sizeof(TD) + 2 * sizeof(TC)), 2.0 * rows * N * N,
+               (k_jacobi0<N, AT, TD, TC>), grid_for((size_t)rows * N, 256), 256, 0, rows, dinv(L), b, x, (AT)1);
+    return BCS_OK;
+  }
   template <int N>
   bcs_status run(int l, const TC* b, TC* x) {
     Level& L = s->lv[l];
@@ -903,7 +918,7 @@ bcs_status cycle_prepare(Solver* s) {
     BCS_ALLOC(s, L.vr, N * vsz);
     BCS_ALLOC(s, L.vt, N * vsz);
     if (L.ncol > 0) BCS_ALLOC(s, L.vd, N * vsz);
-    if (prec == BCS_PREC_FP64 || s->setup_cfg.precond != BCS_PC_AMG) continue;
+    if (prec == BCS_PREC_FP64 || (s->setup_cfg.precond != BCS_PC_AMG && s->setup_cfg.precond != BCS_PC_SGS)) continue;
     BCS_OKR(dilu_prepare(s, L));
     BCS_ALLOC(s, L.dinv32, (size_t)L.A.rows * nn);
     BCS_OKR(cast_vec<double, float>(s, L.dinv.p, L.dinv32.p, (size_t)L.A.rows * nn));
@@ -1015,6 +1030,26 @@ bcs_status precond_apply(Solver* s, const double* v, void* z) {
   BCS_OKR(s->setup_cfg.precision == BCS_PREC_FP32 ? graph_cycle<float>(s) : graph_cycle<bf16>(s));
   BCS_CU(s, cudaMemcpyAsync(z, L0.vx.p, N * sizeof(float), cudaMemcpyDeviceToDevice, s->stream));
   return BCS_OK;
+}
+
+template <class TV, class TD, class TC, class AT>
+bcs_status run_sgs(Solver* s, const TC* b, TC* x) {
+  Cycle<TV, TD, TC, AT> c{s};
+  return with_n(s->n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    return c.template sgs<N>(b, x);
+  });
+}
+
+// z = M^-1 v for the stand-alone SGS preconditioner, in the cycle precision.
+bcs_status sgs_apply(Solver* s, const double* v, void* z) {
+  Level& L0 = s->lv[0];
+  const size_t N = (size_t)L0.A.rows * s->n;
+  const int prec = s->setup_cfg.precision;
+  if (prec == BCS_PREC_FP64) return run_sgs<double, double, double, double>(s, v, (double*)z);
+  BCS_OKR(cast_vec<double, float>(s, v, (float*)L0.vb.p, N));
+  return prec == BCS_PREC_FP32 ? run_sgs<float, float, float, float>(s, (const float*)L0.vb.p, (float*)z)
+                               : run_sgs<bf16, float, float, float>(s, (const float*)L0.vb.p, (float*)z);
 }
 
 // Block-Jacobi preconditioner (one undamped block solve): z = D^-1 v.

@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(64) k_dilu_invert(int cnt, const int32_t* __re
 
 }  // namespace
 
-bcs_status dilu_setup(Solver* s, Level& L, bool full) {
+bcs_status dilu_setup(Solver* s, Level& L, bool full, bool sgs) {
   const int rows = L.A.rows, n = s->n;
   if (full) {
     L.ncol = -1;
@@ -283,6 +283,12 @@ bcs_status dilu_setup(Solver* s, Level& L, bool full) {
   }
   if (L.ncol <= 0) return BCS_OK;
   BCS_ALLOC(s, L.einv, (size_t)rows * n * n);
+  if (sgs) {
+    // symmetric Gauss-Seidel: E = D, so E^-1 is the block-Jacobi inverse
+    BCS_CU(s, cudaMemcpyAsync(L.einv.p, L.dinv.p, (size_t)rows * n * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                              s->stream));
+    return BCS_OK;
+  }
   int maxc = 0;
   for (int c = 0; c < L.ncol; ++c) maxc = std::max(maxc, L.cstart[c + 1] - L.cstart[c]);
   DBuf<double> E;

@@ -33,7 +33,8 @@ enum Kind {
   K_CAST = 10,      // precision casts
   K_MISC = 11,      // scans, sorts
   K_TUNE = 12,      // layout autotuning launches
-  K_NKINDS = 13
+  K_ASSEMBLE = 13,  // assembly of the density-based system
+  K_NKINDS = 14
 };
 const char* kind_name(int k);
 
@@ -261,6 +262,10 @@ bcs_status with_n(int n, F&& f) {
 
 // ------------------------------------------------------------------ format.cu
 bcs_status build_structure(Solver* s, const int32_t* owner_d, const int32_t* nb_d);
+// assemble.cu: density-based system from cell states and face geometry;
+// diag == nullptr writes the fine block-CSR values, else the LDU arrays
+bcs_status assemble_density(Solver* s, const double* Q, const double* area, const double* normal, const double* dist,
+                            const bcs_flow_params& prm, double* diag, double* upper, double* lower);
 bcs_status permute_values(Solver* s, const double* diag_d, const double* upper_d,
                           const double* lower_d);
 
@@ -300,6 +305,7 @@ bcs_status spmv64(Solver* s, const Bsr& A, const void* x, bool x_is_float, doubl
 bcs_status cycle_prepare(Solver* s);
 bcs_status precond_apply(Solver* s, const double* v, void* z);  // z in cycle precision
 bcs_status jacobi_apply(Solver* s, const double* v, double* z);
+bcs_status sgs_apply(Solver* s, const double* v, void* z);  // z in cycle precision
 bool cycle_is_float(const Solver* s);
 
 
@@ -311,7 +317,8 @@ bcs_status amg_setup(Solver* s, bool full);
 // Multicolour DILU of level L: colouring and colour lists when full, then
 // the FP64 factor (E_i^{-1}); marks the level block-Jacobi (ncol = -1) when
 // it would need more than 128 colours.
-bcs_status dilu_setup(Solver* s, Level& L, bool full);
+// sgs: E = D (multicolour block SGS) instead of the DILU factor
+bcs_status dilu_setup(Solver* s, Level& L, bool full, bool sgs);
 // FP32 copies of a DILU level for the FP32 / BF16 cycle.
 bcs_status dilu_prepare(Solver* s, Level& L);
 

@@ -38,6 +38,8 @@ bcs_status apply_M(Solver* s, const double* v, void* z, size_t N) {
       return precond_apply(s, v, z);
     case BCS_PC_JACOBI:
       return jacobi_apply(s, v, (double*)z);
+    case BCS_PC_SGS:
+      return sgs_apply(s, v, z);
     default:
       BCS_CU(s, cudaMemcpyAsync(z, v, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
       return BCS_OK;

@@ -1055,7 +1055,8 @@ bcs_status amg_setup(Solver* s, bool full) {
     bool singular = false;
     BCS_OKR(check_flags(s, &singular));
     if (singular) return s->fail(BCS_SINGULAR_BLOCK, "singular diagonal block at level " + std::to_string(l));
-    if (cfg.smoother == BCS_SMOOTH_DILU && cfg.precond == BCS_PC_AMG) BCS_OKR(dilu_setup(s, L, full));
+    if (cfg.precond == BCS_PC_SGS || (cfg.precond == BCS_PC_AMG && cfg.smoother != BCS_SMOOTH_JACOBI))
+      BCS_OKR(dilu_setup(s, L, full, cfg.precond == BCS_PC_SGS || cfg.smoother == BCS_SMOOTH_SGS));
     bool last;
     if (full) {
       const int C = L.A.rows;
