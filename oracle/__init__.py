@@ -359,3 +359,47 @@ def assemble_density(flow, **prm):
                                    p["gamma"], p["mu"], p["prandtl"], p["cfl"], diag.reshape(-1),
                                    upper.reshape(-1), lower.reshape(-1))
     return st, diag, upper, lower
+
+
+# ---- segregated fields <-> block AoS (Alg. 1 steps 1, 5 and 15) -------------
+# A coupled system's unknowns come as a list of fields, field k with ncomp[k]
+# components per cell (1: scalar field, 3: vector field stored [cell][3]); the
+# block unknown order is the fields' order with each field's components in
+# turn. Plain definitions with numpy.
+
+def field_offsets(ncomp):
+    return np.concatenate(([0], np.cumsum(ncomp))).astype(int)
+
+
+def pack_vector(fields, ncomp):
+    """Block AoS vector [C][n] from the list of fields (Alg. 1 step 1)."""
+    C = fields[0].size // ncomp[0]
+    off = field_offsets(ncomp)
+    out = np.zeros((C, off[-1]))
+    for k, f in enumerate(fields):
+        out[:, off[k]:off[k + 1]] = np.asarray(f, np.float64).reshape(C, ncomp[k])
+    return out
+
+
+def unpack_vector(vec, ncomp):
+    """The list of fields from a block AoS vector (Alg. 1 step 15)."""
+    off = field_offsets(ncomp)
+    vec = np.asarray(vec).reshape(vec.shape[0], off[-1])
+    return [np.ascontiguousarray(vec[:, off[k]:off[k + 1]]).reshape(-1) for k in range(len(ncomp))]
+
+
+def pack_coefficients(coupling, ncomp, C, F):
+    """LDU blocks diag[C][n][n], upper / lower[F][n][n] (Alg. 1 step 5) from
+    the couplings: coupling[a][b] = (diag, upper, lower) with ncomp[a] x
+    ncomp[b] row-major sub-blocks, or None for a zero coupling."""
+    off = field_offsets(ncomp)
+    n = off[-1]
+    out = [np.zeros((C, n, n)), np.zeros((F, n, n)), np.zeros((F, n, n))]
+    for a in range(len(ncomp)):
+        for b in range(len(ncomp)):
+            cp = coupling[a][b]
+            if cp is None:
+                continue
+            for o, src, m in zip(out, cp, (C, F, F)):
+                o[:, off[a]:off[a + 1], off[b]:off[b + 1]] = np.asarray(src, np.float64).reshape(m, ncomp[a], ncomp[b])
+    return out
