@@ -291,6 +291,7 @@ def run_native(args):
     clocks = clk.summary()
     # all-FP64 comparison (same step, FP64 AMG) and BF16-stored AMG
     ms_fp64, res_fp64, ms_bf16, res_bf16, ms_dilu, res_dilu = None, None, None, None, None, None
+    ms_sgs, res_sgs = None, None
     if not args.no_fp64:
         with bcs.Solver(n, precision=bcs.BCS_PREC_FP64) as s64:
             ms_fp64, res_fp64, _ = timed(s64, d, x, max(1, min(args.steps, 3)), 1)
@@ -298,6 +299,8 @@ def run_native(args):
             ms_bf16, res_bf16, _ = timed(s16, d, x, max(1, min(args.steps, 3)), 1)
         with bcs.Solver(n, precision=bcs.BCS_PREC_FP32, smoother=bcs.BCS_SMOOTH_DILU) as sd:
             ms_dilu, res_dilu, _ = timed(sd, d, x, max(1, min(args.steps, 3)), 1)
+        with bcs.Solver(n, precision=bcs.BCS_PREC_FP32, precond=bcs.BCS_PC_SGS, maxiter=5000) as ss:
+            ms_sgs, res_sgs, _ = timed(ss, d, x, max(1, min(args.steps, 3)), 1)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -311,6 +314,7 @@ def run_native(args):
                "d2h_bytes_per_step": int(xh.numel() * 8)}
 
     assembly = None if args.no_assembly else assembly_entry(args.side, dev, args.steps)
+    packing = None if args.no_assembly else packing_entry(system, dev, args.steps)
 
     ms_max = max_over_ranks(ms_mixed, dev) if world > 1 else ms_mixed
     if rank != 0:
@@ -350,6 +354,10 @@ def run_native(args):
         "dilu": None if ms_dilu is None else {"value": ms_dilu, "unit": "ms", "iters": res_dilu[-1]["iters"],
                                               "rel_res_final": res_dilu[-1]["rel_res_final"],
                                               "smoother": "multicolour block DILU, FP32 storage"},
+        "sgs": None if ms_sgs is None else {"value": ms_sgs, "unit": "ms", "iters": res_sgs[-1]["iters"],
+                                            "rel_res_final": res_sgs[-1]["rel_res_final"],
+                                            "preconditioner": "GMRES + multicolour block SGS (LU-SGS form), "
+                                                              "FP32 storage, no AMG"},
         "resetup_ms": resetup_ms,
         "roofline": roofline,
         "kernel_breakdown": breakdown,
@@ -361,17 +369,21 @@ def run_native(args):
         "clocks": clocks,
         "e2e": e2e,
         "assembly": assembly,
+        "packing": packing,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_entry(args.side)
     print(json.dumps(line), flush=True)
 
 
-# FP64 operations per launch unit of the assembly kernels, counted from the
-# source (an FMA counts as one operation): k_face_lambda per face,
-# k_assemble_cells per face side plus per cell.
-ASSEMBLY_FP64_OPS = {"k_face_lambda": 150.0, "k_assemble_cells_face_side": 55.0, "k_assemble_cells_cell": 80.0}
-FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 vector peak (an FMA counted as two flops)
+# FP64 thread instructions (DADD + DMUL + DFMA) of the assembly, measured by
+# ncu on the 64^3 mesh (profiles/assembly_density64.md): k_cell_prims and
+# k_assemble_cells 481 per cell (a cell with its face sides), k_face_lambda
+# 42 per face. Peak: 296 DFMA thread instructions per cycle on the GPU (ncu's
+# sustained peak of sm__sass_thread_inst_executed_op_dfma_pred_on) at the
+# 2032 MHz maximum SM clock.
+ASSEMBLY_FP64_OPS = {"per_cell": 481.0, "per_face": 42.0}
+FP64_PEAK_OPS = 296 * 2032e6
 
 
 def assembly_entry(side, dev, reps):
@@ -426,19 +438,69 @@ def assembly_entry(side, dev, reps):
             continue
         per = v["ms"] / v["launches"]
         kernels[name] = {"ms_per_launch": per, "GBps": v["bytes"] / v["launches"] / (per * 1e-3) / 1e9}
-    fp64_ops = (ASSEMBLY_FP64_OPS["k_face_lambda"] * F + ASSEMBLY_FP64_OPS["k_assemble_cells_face_side"] * 2 * F
-                + ASSEMBLY_FP64_OPS["k_assemble_cells_cell"] * C)
-    peak_ops = FP64_NOMINAL_TFLOPS * 1e12 / 2  # FP64 instructions per second (FMA = one)
+    fp64_ops = ASSEMBLY_FP64_OPS["per_cell"] * C + ASSEMBLY_FP64_OPS["per_face"] * F
+    peak_ops = FP64_PEAK_OPS
     return {"workload": f"density-based assembly (Sec. 2.1, Eqs. approxJac1/2), {side}^3 hex mesh, "
                         f"{C} cells, {F} faces, LDU blocks on the device",
             "ms": ms, "kernels": kernels,
-            "roofline": {"bound": "alu", "unit": "FP64 op/s", "achieved": fp64_ops / (ms * 1e-3),
+            "roofline": {"bound": "alu", "unit": "FP64 thread instructions/s", "achieved": fp64_ops / (ms * 1e-3),
                          "peak": peak_ops, "frac": fp64_ops / (ms * 1e-3) / peak_ops,
-                         "peak_source": "nominal 1.25 TFLOP/s FP64 (FMA = 2 flops) = 0.625 T FP64 instructions/s",
-                         "ops_per_assembly": fp64_ops},
+                         "peak_source": "296 DFMA thread instructions per cycle (ncu sustained peak) x 2032 MHz",
+                         "ops_per_assembly": fp64_ops,
+                         "ops_source": "DADD + DMUL + DFMA thread instructions counted by ncu on 64^3, "
+                                       "481 per cell + 42 per face"},
             "nonlinear_iteration_ms": ms_nl, "nonlinear_iteration":
                 "assembly into the solver's values + values-only resetup + FGMRES solve to 1e-8",
             "iters": iters[-1]}
+
+
+def packing_entry(system, dev, reps):
+    """Coefficients from segregated field couplings to block AoS (Alg. 1 step
+    5) on the benchmark system: density-based, fields (rho, rhoU, rhoE), nine
+    couplings, all on the device. LDU blocks out (HBM-bound copy: every value
+    read once and written once), and straight into the solver's block-CSR
+    values (step 5 fused with the LDU -> block-CSR permutation)."""
+    import torch
+    from paper_2403_07882_b300 import bcs
+    C, F = system["n_cells"], system["n_faces"]
+    ncomp = [1, 3, 1]
+    off = [0, 1, 4, 5]
+    cp = [[tuple(torch.from_numpy(np.ascontiguousarray(system[k][:, off[a]:off[a + 1], off[b]:off[b + 1]])).to(dev)
+                 for k in ("diag", "upper", "lower")) for b in range(3)] for a in range(3)]
+    stream = torch.cuda.current_stream()
+    reps = max(3, reps)
+    out = {}
+    with bcs.Solver(5, profile=1, profile_kinds=bcs.kind_mask("ldu_to_bsr")) as s:
+        s.set_structure(C, torch.from_numpy(system["owner"]).to(dev), torch.from_numpy(system["neighbour"]).to(dev))
+        ldu = (torch.empty((C, 5, 5), dtype=torch.float64, device=dev),
+               torch.empty((F, 5, 5), dtype=torch.float64, device=dev),
+               torch.empty((F, 5, 5), dtype=torch.float64, device=dev))
+        for mode in ("ldu", "values"):
+            for _ in range(2):
+                if mode == "ldu":
+                    bcs.bcs_pack_coefficients(s.h, ncomp, cp, *ldu)
+            torch.cuda.synchronize()
+            s.reset_stats()
+            for _ in range(reps):
+                if mode == "ldu":
+                    bcs.bcs_pack_coefficients(s.h, ncomp, cp, *ldu)
+                else:
+                    # the first call runs the full setup; the kernel is timed by its events
+                    s.pack_coefficients(cp, ncomp, to_values=True)
+            torch.cuda.synchronize()
+            kt = {k: v for k, v in s.kernel_times().items() if "pack_coefficients" in k}
+            (name, v), = kt.items()
+            per = v["ms"] / v["launches"]
+            bpl = v["bytes"] / v["launches"]
+            out[mode] = {"kernel": name, "ms_per_launch": per, "GBps": bpl / (per * 1e-3) / 1e9,
+                         "bytes_per_launch": bpl}
+    peak, peak_kind = peaks()
+    best = out["ldu"]
+    return {"workload": f"segregated fields (rho, rhoU, rhoE) -> block AoS coefficients, {C} cells, {F} faces, "
+                        f"9 couplings, device-resident",
+            "ldu": out["ldu"], "into_values": out["values"],
+            "roofline": {"bound": "hbm", "kernel": best["kernel"], "achieved": best["GBps"], "peak": peak,
+                         "unit": "GB/s", "frac": best["GBps"] / peak, "peak_source": peak_kind + " (copy bandwidth)"}}
 
 
 def run_system(args):

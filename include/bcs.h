@@ -206,6 +206,40 @@ BCS_API bcs_status bcs_assemble_density(bcs_solver* s, const double* Q, const do
                                         const double* dist, const bcs_flow_params* prm, double* diag,
                                         double* upper, double* lower, int mem);
 
+/* Segregated fields <-> block AoS (Alg. 1 steps 1, 5 and 15). The unknowns
+ * come as nfields fields (1 <= nfields <= 8), field k with ncomp[k] >= 1
+ * components per cell (1: scalar field, 3: vector field stored [cell][3]),
+ * sum ncomp = n; the block unknown order is the fields' order with each
+ * field's components in turn. Need bcs_set_structure (for C and F); every
+ * array host or device per mem; BCS_EINVAL on a bad field split or NULL. */
+/* out[C][n] from fields[k][C][ncomp[k]] (source term and solution, step 1). */
+BCS_API bcs_status bcs_pack_vector(bcs_solver* s, int nfields, const int* ncomp, const double* const* fields,
+                                   double* out, int mem);
+/* fields[k][C][ncomp[k]] from in[C][n] (solution back to fields, step 15). */
+BCS_API bcs_status bcs_unpack_vector(bcs_solver* s, int nfields, const int* ncomp, const double* in,
+                                     double* const* fields, int mem);
+
+/* One coupling of the coefficient matrix: LDU arrays of the sub-blocks of
+ * row field a and column field b, diag[C][na][nb], upper[F][na][nb] (row
+ * owner), lower[F][na][nb] (row neighbour), row-major; all three NULL for a
+ * zero coupling. */
+typedef struct bcs_coupling {
+  const double* diag;
+  const double* upper;
+  const double* lower;
+} bcs_coupling;
+
+/* Coefficients in block AoS (step 5) from coupling[a * nfields + b]. With
+ * diag, upper and lower all NULL the blocks go straight into the solver's
+ * block-CSR values (step 5 and the LDU -> block-CSR permutation in one pass)
+ * and the call continues as bcs_set_values (full setup or values-only
+ * resetup); otherwise diag[C][n][n], upper[F][n][n], lower[F][n][n] (in the
+ * inputs' memory space) receive the LDU blocks. A coupling with only some of
+ * its three arrays given is BCS_EINVAL. */
+BCS_API bcs_status bcs_pack_coefficients(bcs_solver* s, int nfields, const int* ncomp,
+                                         const bcs_coupling* coupling, double* diag, double* upper,
+                                         double* lower, int mem);
+
 /* Forget the hierarchy: the next set_values runs a full setup (new
  * aggregates). */
 BCS_API bcs_status bcs_invalidate_hierarchy(bcs_solver* s);

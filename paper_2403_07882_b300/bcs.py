@@ -68,6 +68,10 @@ class bcs_flow_params(ct.Structure):
     _fields_ = [("gamma", ct.c_double), ("mu", ct.c_double), ("prandtl", ct.c_double), ("cfl", ct.c_double)]
 
 
+class bcs_coupling(ct.Structure):
+    _fields_ = [("diag", ct.c_void_p), ("upper", ct.c_void_p), ("lower", ct.c_void_p)]
+
+
 class BcsError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 10 else status}: {msg}")
@@ -95,6 +99,9 @@ def lib():
             "bcs_set_values": (ct.c_int, [_vp, _vp, _vp, _vp, ct.c_int]),
             "bcs_invalidate_hierarchy": (ct.c_int, [_vp]),
             "bcs_flow_params_default": (ct.c_int, [ct.POINTER(bcs_flow_params)]),
+            "bcs_pack_vector": (ct.c_int, [_vp, ct.c_int, _vp, _vp, _vp, ct.c_int]),
+            "bcs_unpack_vector": (ct.c_int, [_vp, ct.c_int, _vp, _vp, _vp, ct.c_int]),
+            "bcs_pack_coefficients": (ct.c_int, [_vp, ct.c_int, _vp, _vp, _vp, _vp, _vp, ct.c_int]),
             "bcs_assemble_density": (ct.c_int, [_vp] + [_vp] * 4 + [ct.POINTER(bcs_flow_params)] + [_vp] * 3
                                      + [ct.c_int]),
             "bcs_solve": (ct.c_int, [_vp, _vp, _vp, ct.c_int, ct.POINTER(bcs_result)]),
@@ -136,6 +143,7 @@ def lib():
 def exported_names():
     return ["bcs_config_default", "bcs_create", "bcs_destroy", "bcs_set_config", "bcs_set_structure",
             "bcs_set_values", "bcs_invalidate_hierarchy", "bcs_flow_params_default", "bcs_assemble_density",
+            "bcs_pack_vector", "bcs_unpack_vector", "bcs_pack_coefficients",
             "bcs_solve", "bcs_spmv", "bcs_precond_apply",
             "bcs_get_bsr", "bcs_num_levels", "bcs_get_level_info", "bcs_get_level", "bcs_get_prolongation",
             "bcs_get_coarse_inverse", "bcs_get_dilu", "bcs_get_stats", "bcs_reset_stats", "bcs_get_kernel_times", "bcs_kernel_kind_name",
@@ -234,6 +242,37 @@ def bcs_flow_params_default(**overrides):
 def bcs_assemble_density(h, Q, area, normal, dist, prm, diag=None, upper=None, lower=None):
     (pq, pa, pn, pd, pdg, pu, pl), mem = _ptr_mem(Q, area, normal, dist, diag, upper, lower)
     return _check(lib().bcs_assemble_density(h, pq, pa, pn, pd, ct.byref(prm), pdg, pu, pl, mem), h)
+
+
+def _ints(vals):
+    return (ct.c_int * len(vals))(*vals)
+
+
+def bcs_pack_vector(h, ncomp, fields, out):
+    ptrs, mem = _ptr_mem(*fields, out)
+    arr = (ct.c_void_p * len(fields))(*ptrs[:-1])
+    return _check(lib().bcs_pack_vector(h, len(ncomp), _ints(ncomp), arr, ptrs[-1], mem), h)
+
+
+def bcs_unpack_vector(h, ncomp, vec, fields):
+    ptrs, mem = _ptr_mem(vec, *fields)
+    arr = (ct.c_void_p * len(fields))(*ptrs[1:])
+    return _check(lib().bcs_unpack_vector(h, len(ncomp), _ints(ncomp), ptrs[0], arr, mem), h)
+
+
+def bcs_pack_coefficients(h, ncomp, coupling, diag=None, upper=None, lower=None):
+    """coupling[a][b] = (diag, upper, lower) arrays or None (zero coupling)."""
+    nf = len(ncomp)
+    flat = [a for row in coupling for cp in row if cp is not None for a in cp]
+    ptrs, mem = _ptr_mem(*flat, diag, upper, lower)
+    tab = (bcs_coupling * (nf * nf))()
+    it = iter(ptrs[:len(flat)])
+    for a in range(nf):
+        for b in range(nf):
+            if coupling[a][b] is not None:
+                tab[a * nf + b] = bcs_coupling(next(it), next(it), next(it))
+    pd, pu, pl = ptrs[len(flat):]
+    return _check(lib().bcs_pack_coefficients(h, nf, _ints(ncomp), tab, pd, pu, pl, mem), h)
 
 
 def bcs_invalidate_hierarchy(h):
@@ -423,6 +462,33 @@ class Solver:
             arr = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in arr.items()}
         self.set_structure(system["n_cells"], arr["owner"], arr["neighbour"])
         self.set_values(arr["diag"], arr["upper"], arr["lower"])
+
+    def _like(self, ref, shape):
+        return np.zeros(shape) if isinstance(ref, np.ndarray) else ref.new_zeros(shape)
+
+    def pack_vector(self, fields, ncomp):
+        """Block AoS vector [C][n] from segregated fields (Alg. 1 step 1)."""
+        out = self._like(fields[0], (self.C, self.n))
+        bcs_pack_vector(self.h, ncomp, fields, out)
+        return out
+
+    def unpack_vector(self, vec, ncomp):
+        """Segregated fields from a block AoS vector (Alg. 1 step 15)."""
+        fields = [self._like(vec, (self.C * m,)) for m in ncomp]
+        bcs_unpack_vector(self.h, ncomp, vec, fields)
+        return fields
+
+    def pack_coefficients(self, coupling, ncomp, to_values=False):
+        """LDU blocks (diag, upper, lower) from field couplings (Alg. 1 step
+        5), or straight into the solver's values followed by setup."""
+        if to_values:
+            bcs_pack_coefficients(self.h, ncomp, coupling)
+            return None
+        ref = next(a for row in coupling for cp in row if cp is not None for a in cp)
+        n = self.n
+        out = (self._like(ref, (self.C, n, n)), self._like(ref, (self.F, n, n)), self._like(ref, (self.F, n, n)))
+        bcs_pack_coefficients(self.h, ncomp, coupling, *out)
+        return out
 
     def assemble_density(self, Q, area, normal, dist, to_values=False, **prm):
         """Density-based system from cell states and face geometry (Sec. 2.1).

@@ -354,6 +354,123 @@ bcs_status bcs_assemble_density(bcs_solver* h, const double* Q, const double* ar
   return BCS_OK;
 }
 
+static bcs_status check_fields(Solver* s, int nfields, const int* ncomp, int mem) {
+  if (!s->have_structure) return s->fail(BCS_ESTATE, "field conversion before set_structure");
+  if (nfields < 1 || nfields > PK_MAX_FIELDS || !ncomp || (mem != BCS_MEM_HOST && mem != BCS_MEM_DEVICE))
+    return s->fail(BCS_EINVAL, "invalid field arguments");
+  int n = 0;
+  for (int k = 0; k < nfields; ++k) {
+    if (ncomp[k] < 1) return s->fail(BCS_EINVAL, "a field with no components");
+    n += ncomp[k];
+  }
+  if (n != s->n) return s->fail(BCS_EINVAL, "field components do not add up to the block size");
+  return BCS_OK;
+}
+
+bcs_status bcs_pack_vector(bcs_solver* h, int nfields, const int* ncomp, const double* const* fields, double* out,
+                           int mem) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  BCS_OKR(check_fields(s, nfields, ncomp, mem));
+  if (!fields || !out) return s->fail(BCS_EINVAL, "null field array");
+  for (int k = 0; k < nfields; ++k)
+    if (!fields[k]) return s->fail(BCS_EINVAL, "null field array");
+  const size_t C = s->C;
+  DBuf<double> st[PK_MAX_FIELDS], o;
+  const double* in[PK_MAX_FIELDS] = {};
+  for (int k = 0; k < nfields; ++k) BCS_OKR(stage(s, fields[k], C * ncomp[k], mem, st[k], &in[k]));
+  double* od = out;
+  if (mem == BCS_MEM_HOST) {
+    BCS_ALLOC(s, o, C * s->n);
+    od = o.p;
+  }
+  BCS_OKR(pack_vector(s, nfields, ncomp, in, od));
+  if (mem == BCS_MEM_HOST) return to_host(s, out, od, C * s->n * sizeof(double));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  return BCS_OK;
+}
+
+bcs_status bcs_unpack_vector(bcs_solver* h, int nfields, const int* ncomp, const double* in, double* const* fields,
+                             int mem) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  BCS_OKR(check_fields(s, nfields, ncomp, mem));
+  if (!fields || !in) return s->fail(BCS_EINVAL, "null field array");
+  for (int k = 0; k < nfields; ++k)
+    if (!fields[k]) return s->fail(BCS_EINVAL, "null field array");
+  const size_t C = s->C;
+  DBuf<double> si, so[PK_MAX_FIELDS];
+  const double* ind = nullptr;
+  BCS_OKR(stage(s, in, C * s->n, mem, si, &ind));
+  double* outs[PK_MAX_FIELDS] = {};
+  for (int k = 0; k < nfields; ++k) {
+    outs[k] = fields[k];
+    if (mem == BCS_MEM_HOST) {
+      BCS_ALLOC(s, so[k], C * ncomp[k]);
+      outs[k] = so[k].p;
+    }
+  }
+  BCS_OKR(unpack_vector(s, nfields, ncomp, ind, outs));
+  if (mem == BCS_MEM_HOST)
+    for (int k = 0; k < nfields; ++k) BCS_OKR(to_host(s, fields[k], outs[k], C * ncomp[k] * sizeof(double)));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  return BCS_OK;
+}
+
+bcs_status bcs_pack_coefficients(bcs_solver* h, int nfields, const int* ncomp, const bcs_coupling* coupling,
+                                 double* diag, double* upper, double* lower, int mem) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  BCS_OKR(check_fields(s, nfields, ncomp, mem));
+  const bool to_values = !diag && !upper && !lower;
+  if (!coupling || (!to_values && (!diag || (s->F > 0 && (!upper || !lower)))))
+    return s->fail(BCS_EINVAL, "invalid coefficient arguments");
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t C = s->C, F = s->F;
+  std::vector<DBuf<double>> st(3 * nfields * nfields);
+  std::vector<const double*> src(3 * nfields * nfields, nullptr);
+  for (int a = 0; a < nfields; ++a)
+    for (int b = 0; b < nfields; ++b) {
+      const int p = a * nfields + b;
+      const bcs_coupling& cp = coupling[p];
+      const bool none = !cp.diag && !cp.upper && !cp.lower;
+      if (none) continue;
+      if (!cp.diag || (F > 0 && (!cp.upper || !cp.lower)))
+        return s->fail(BCS_EINVAL, "a coupling with only some of its arrays");
+      const size_t m = (size_t)ncomp[a] * ncomp[b];
+      BCS_OKR(stage(s, cp.diag, C * m, mem, st[3 * p], &src[3 * p]));
+      BCS_OKR(stage(s, cp.upper, F * m, mem, st[3 * p + 1], &src[3 * p + 1]));
+      BCS_OKR(stage(s, cp.lower, F * m, mem, st[3 * p + 2], &src[3 * p + 2]));
+    }
+  if (to_values) {
+    s->have_values = false;
+    const bool had = s->have_hierarchy;
+    s->have_hierarchy = false;
+    BCS_OKR(pack_coefficients(s, nfields, ncomp, src.data(), nullptr, nullptr, nullptr));
+    s->have_hierarchy = had;
+    return values_changed(s, t0);
+  }
+  const size_t nn = (size_t)s->n * s->n;
+  DBuf<double> od, ou, ol;
+  double *dd = diag, *du = upper, *dl = lower;
+  if (mem == BCS_MEM_HOST) {
+    BCS_ALLOC(s, od, C * nn);
+    BCS_ALLOC(s, ou, F > 0 ? F * nn : 1);
+    BCS_ALLOC(s, ol, F > 0 ? F * nn : 1);
+    dd = od.p;
+    du = ou.p;
+    dl = ol.p;
+  }
+  BCS_OKR(pack_coefficients(s, nfields, ncomp, src.data(), dd, du, dl));
+  if (mem == BCS_MEM_HOST) {
+    BCS_OKR(to_host(s, diag, dd, C * nn * sizeof(double)));
+    BCS_OKR(to_host(s, upper, du, F * nn * sizeof(double)));
+    BCS_OKR(to_host(s, lower, dl, F * nn * sizeof(double)));
+  }
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  return BCS_OK;
+}
+
 bcs_status bcs_invalidate_hierarchy(bcs_solver* h) {
   if (!h) return BCS_EINVAL;
   h->impl.have_hierarchy = false;
@@ -426,7 +543,8 @@ bcs_status bcs_precond_apply(bcs_solver* h, const double* v, double* z, int mem)
   double* zd = mem == BCS_MEM_HOST ? s->kx.p : z;
   switch (s->setup_cfg.precond) {
     case BCS_PC_AMG:
-      BCS_OKR(precond_apply(s, vd, zt.p));
+    case BCS_PC_SGS:
+      BCS_OKR(s->setup_cfg.precond == BCS_PC_AMG ? precond_apply(s, vd, zt.p) : sgs_apply(s, vd, zt.p));
       if (cycle_is_float(s)) BCS_OKR(cast_vec<float, double>(s, (const float*)zt.p, zd, N));
       else BCS_CU(s, cudaMemcpyAsync(zd, zt.p, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
       break;

@@ -262,6 +262,15 @@ bcs_status with_n(int n, F&& f) {
 
 // ------------------------------------------------------------------ format.cu
 bcs_status build_structure(Solver* s, const int32_t* owner_d, const int32_t* nb_d);
+// pack.cu: segregated fields <-> block AoS (at most PK_MAX_FIELDS fields);
+// src of pack_coefficients: 3 pointers (diag, upper, lower) per (row field,
+// column field) pair, nullptr = zero coupling; diag == nullptr writes the fine
+// block-CSR values
+constexpr int PK_MAX_FIELDS = 8;
+bcs_status pack_vector(Solver* s, int nfields, const int* ncomp, const double* const* fields, double* out);
+bcs_status unpack_vector(Solver* s, int nfields, const int* ncomp, const double* in, double* const* fields);
+bcs_status pack_coefficients(Solver* s, int nfields, const int* ncomp, const double* const* src, double* diag,
+                             double* upper, double* lower);
 // assemble.cu: density-based system from cell states and face geometry;
 // diag == nullptr writes the fine block-CSR values, else the LDU arrays
 bcs_status assemble_density(Solver* s, const double* Q, const double* area, const double* normal, const double* dist,
