@@ -12,7 +12,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.cpp")
-_SRCS = [_SRC, os.path.join(_HERE, "assembly.cpp")]
+_SRCS = [_SRC, os.path.join(_HERE, "assembly.cpp"), os.path.join(_HERE, "reorder.cpp")]
 
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -83,6 +83,7 @@ def lib():
                                _f64p, _f64p, ct.POINTER(Result), ct.c_void_p, ct.c_int]
         L.or_fgmres_arnoldi.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, ct.c_void_p,
                                         ct.POINTER(Config), _f64p, ct.c_int, _f64p, _f64p, _f64p]
+        L.or_rcm.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _i32p]
         d3 = [_f64p, _f64p, ct.c_double, _f64p]
         L.or_euler_flux.argtypes = d3
         L.or_flux_jacobian.argtypes = d3
@@ -403,3 +404,12 @@ def pack_coefficients(coupling, ncomp, C, F):
             for o, src, m in zip(out, cp, (C, F, F)):
                 o[:, off[a]:off[a + 1], off[b]:off[b + 1]] = np.asarray(src, np.float64).reshape(m, ncomp[a], ncomp[b])
     return out
+
+
+# ---- locality ordering (reorder.cpp) ----------------------------------------
+def rcm(C, owner, neighbour):
+    """Reverse Cuthill-McKee permutation perm[new] = old; None for bad faces."""
+    perm = np.zeros(C, np.int32)
+    st = lib().or_rcm(C, len(owner), np.ascontiguousarray(owner, np.int32),
+                      np.ascontiguousarray(neighbour, np.int32), perm)
+    return None if st else perm

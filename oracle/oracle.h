@@ -182,6 +182,11 @@ int or_assemble_density(int C, int F, const int32_t* owner, const int32_t* nb, c
                         const double* area, const double* normal, const double* dist, double gamma, double mu,
                         double prandtl, double cfl, double* diag, double* upper, double* lower);
 
+/* ---- Locality ordering (reorder.cpp) ---------------------------------- */
+/* Reverse Cuthill-McKee order of the cell graph (one edge per face):
+ * perm[new] = old. Returns 0, or 1 for a bad face. */
+int or_rcm(int C, int F, const int32_t* owner, const int32_t* nb, int32_t* perm);
+
 #ifdef __cplusplus
 }
 #endif
