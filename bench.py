@@ -515,21 +515,25 @@ def run_system(args):
     if args.workload == "density16":
         system, n = synth.density(16, seed=0), 5
         name = "density-based 16^3 5x5 (4,096 cells), seed 0"
-        runs = [("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32), ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP64)]
+        runs = [("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32, 0), ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP64, 0)]
     else:
         system, n = synth.pressure(64, seed=1), 4
         name = "pressure-based 64^3 4x4 (262,144 cells), permuted numbering, seed 1"
-        runs = [("bicgstab", bcs.BCS_BICGSTAB, bcs.BCS_PREC_FP32), ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32),
-                ("bicgstab", bcs.BCS_BICGSTAB, bcs.BCS_PREC_FP64)]
+        # with and without the internal reverse Cuthill-McKee renumbering
+        runs = [("bicgstab", bcs.BCS_BICGSTAB, bcs.BCS_PREC_FP32, 0), ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32, 0),
+                ("bicgstab", bcs.BCS_BICGSTAB, bcs.BCS_PREC_FP64, 0),
+                ("bicgstab", bcs.BCS_BICGSTAB, bcs.BCS_PREC_FP32, 1), ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32, 1)]
     keys = ("owner", "neighbour", "diag", "upper", "lower", "b")
     d = {k: torch.from_numpy(system[k]).to(dev) for k in keys}
     ev = lambda: torch.cuda.Event(enable_timing=True)
     pnames = {bcs.BCS_PREC_FP32: "fp32", bcs.BCS_PREC_FP64: "fp64", bcs.BCS_PREC_BF16: "bf16"}
     out = []
-    for label, solver, prec in runs:
-        setup, resetup, solve, total, iters, launches = [], [], [], [], [], []
+    C, F = system["n_cells"], system["n_faces"]
+    spmv_bytes = 8.0 * n * n * (C + 2 * F) + 4.0 * (C + 2 * F) + 4.0 * (C + 1) + 16.0 * n * C
+    for label, solver, prec, reorder in runs:
+        setup, resetup, solve, total, iters, launches, spmv_ms = [], [], [], [], [], [], []
         for rep in range(args.warmup + args.steps):
-            with bcs.Solver(n, solver=solver, precision=prec) as s:
+            with bcs.Solver(n, solver=solver, precision=prec, reorder=reorder) as s:
                 x = torch.zeros_like(d["b"])
                 torch.cuda.synchronize()
                 e = [ev() for _ in range(5)]
@@ -543,6 +547,10 @@ def run_system(args):
                 nl = s.stats()["launches"]
                 s.set_values(d["diag"], d["upper"], d["lower"])
                 e[3].record()
+                y = torch.empty_like(x)
+                for _ in range(10):
+                    s.spmv(x, y)
+                e[4].record()
                 torch.cuda.synchronize()
                 assert st == bcs.BCS_OK, res
                 if rep >= args.warmup:
@@ -552,7 +560,10 @@ def run_system(args):
                     resetup.append(e[2].elapsed_time(e[3]))
                     iters.append(res["iters"])
                     launches.append(nl)
-        out.append({"solver": label, "amg_precision": pnames[prec],
+                    spmv_ms.append(e[3].elapsed_time(e[4]) / 10)
+        out.append({"solver": label, "amg_precision": pnames[prec], "rcm_reorder": bool(reorder),
+                    "spmv_fp64_ms": statistics.median(spmv_ms),
+                    "spmv_fp64_GBps": spmv_bytes / (statistics.median(spmv_ms) * 1e-3) / 1e9,
                     "time_to_1e-8_ms": statistics.median(total), "setup_ms": statistics.median(setup),
                     "solve_ms": statistics.median(solve), "resetup_ms": statistics.median(resetup),
                     "iters": iters[-1], "launches_per_solve": launches[-1]})

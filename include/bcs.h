@@ -109,6 +109,10 @@ typedef struct bcs_config {
   int cycle_graph;         /* FP32 / BF16 V-cycle replayed as one CUDA graph: 0 off, 1 or -1
                               (default) on, except while profile = 1 times kernels inside
                               the cycle (per-kernel events) */
+  int reorder;             /* read by bcs_set_structure: 1 = renumber the cells internally in
+                              reverse Cuthill-McKee order for locality (vectors, LDU arrays and
+                              results stay in the caller's numbering; bcs_get_permutation);
+                              0 (default) = keep the caller's numbering */
 } bcs_config;
 
 typedef struct bcs_result {
@@ -259,6 +263,10 @@ BCS_API bcs_status bcs_spmv(bcs_solver* s, const double* x, double* y, int mem);
 /* z = M^{-1} v: one application of the configured preconditioner (one AMG
  * V-cycle from zero) in the configured precision, returned in FP64. */
 BCS_API bcs_status bcs_precond_apply(bcs_solver* s, const double* v, double* z, int mem);
+
+/* perm[C] (HOST): the caller's cell of every internal row (the identity
+ * unless the structure was built with cfg.reorder = 1). */
+BCS_API bcs_status bcs_get_permutation(bcs_solver* s, int32_t* perm);
 
 /* Test hooks: copies of internal state to HOST arrays (any may be NULL).
  * bcs_get_bsr: row_ptr[C+1], col[nnz], val[nnz][n][n] of the fine matrix and

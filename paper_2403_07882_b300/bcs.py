@@ -35,7 +35,7 @@ class bcs_config(ct.Structure):
         ("coarse_size", ct.c_int), ("max_levels", ct.c_int), ("max_coarsen_ratio", ct.c_double),
         ("p_omega", ct.c_double), ("coarse_dense_max", ct.c_int), ("coarse_sweeps", ct.c_int),
         ("precision", ct.c_int), ("smoother", ct.c_int), ("profile", ct.c_int), ("profile_kinds", ct.c_int),
-        ("slice_layout", ct.c_int), ("cycle_graph", ct.c_int),
+        ("slice_layout", ct.c_int), ("cycle_graph", ct.c_int), ("reorder", ct.c_int),
     ]
 
 
@@ -100,6 +100,7 @@ def lib():
             "bcs_invalidate_hierarchy": (ct.c_int, [_vp]),
             "bcs_flow_params_default": (ct.c_int, [ct.POINTER(bcs_flow_params)]),
             "bcs_pack_vector": (ct.c_int, [_vp, ct.c_int, _vp, _vp, _vp, ct.c_int]),
+            "bcs_get_permutation": (ct.c_int, [_vp, _vp]),
             "bcs_unpack_vector": (ct.c_int, [_vp, ct.c_int, _vp, _vp, _vp, ct.c_int]),
             "bcs_pack_coefficients": (ct.c_int, [_vp, ct.c_int, _vp, _vp, _vp, _vp, _vp, ct.c_int]),
             "bcs_assemble_density": (ct.c_int, [_vp] + [_vp] * 4 + [ct.POINTER(bcs_flow_params)] + [_vp] * 3
@@ -143,7 +144,7 @@ def lib():
 def exported_names():
     return ["bcs_config_default", "bcs_create", "bcs_destroy", "bcs_set_config", "bcs_set_structure",
             "bcs_set_values", "bcs_invalidate_hierarchy", "bcs_flow_params_default", "bcs_assemble_density",
-            "bcs_pack_vector", "bcs_unpack_vector", "bcs_pack_coefficients",
+            "bcs_pack_vector", "bcs_unpack_vector", "bcs_pack_coefficients", "bcs_get_permutation",
             "bcs_solve", "bcs_spmv", "bcs_precond_apply",
             "bcs_get_bsr", "bcs_num_levels", "bcs_get_level_info", "bcs_get_level", "bcs_get_prolongation",
             "bcs_get_coarse_inverse", "bcs_get_dilu", "bcs_get_stats", "bcs_reset_stats", "bcs_get_kernel_times", "bcs_kernel_kind_name",
@@ -489,6 +490,12 @@ class Solver:
         out = (self._like(ref, (self.C, n, n)), self._like(ref, (self.F, n, n)), self._like(ref, (self.F, n, n)))
         bcs_pack_coefficients(self.h, ncomp, coupling, *out)
         return out
+
+    def permutation(self):
+        """The caller's cell of every internal row (identity without reorder)."""
+        perm = np.zeros(self.C, np.int32)
+        _check(lib().bcs_get_permutation(self.h, perm.ctypes.data), self.h)
+        return perm
 
     def assemble_density(self, Q, area, normal, dist, to_values=False, **prm):
         """Density-based system from cell states and face geometry (Sec. 2.1).

@@ -104,6 +104,7 @@ bcs_status check_config(const bcs_config* c) {
   if (c->coarse_dense_max < 1 || c->coarse_dense_max > 8192) return BCS_EINVAL;
   if (c->precision < BCS_PREC_FP64 || c->precision > BCS_PREC_BF16) return BCS_EINVAL;
   if (c->cycle_graph < -1 || c->cycle_graph > 1) return BCS_EINVAL;
+  if (c->reorder < 0 || c->reorder > 1) return BCS_EINVAL;
   if (c->slice_layout < -1 || c->slice_layout > 1) return BCS_EINVAL;
   if (c->smoother < BCS_SMOOTH_JACOBI || c->smoother > BCS_SMOOTH_SGS) return BCS_EINVAL;
   if (!(c->max_coarsen_ratio > 0.0) || !(c->p_omega > 0.0) || !(c->jacobi_omega > 0.0)) return BCS_EINVAL;
@@ -189,6 +190,7 @@ bcs_status bcs_config_default(bcs_config* c) {
   c->smoother = BCS_SMOOTH_JACOBI;
   c->slice_layout = -1;
   c->cycle_graph = -1;
+  c->reorder = 0;
   return BCS_OK;
 }
 
@@ -269,7 +271,26 @@ bcs_status bcs_set_structure(bcs_solver* h, int32_t C, int32_t F, const int32_t*
   const int32_t *o = nullptr, *m = nullptr;
   BCS_OKR(stage(s, owner, (size_t)F, mem, s->stage_o, &o));
   BCS_OKR(stage(s, nb, (size_t)F, mem, s->stage_n, &m));
+  s->reordered = false;
+  s->perm.release();
+  s->inv.release();
   bcs_status st = build_structure(s, o, m);
+  if (st == BCS_OK && s->cfg.reorder == 1) {
+    // reverse Cuthill-McKee on the caller's numbering, then the structure
+    // again with relabelled faces; face blocks keep their LDU slots
+    BCS_ALLOC(s, s->perm, C);
+    BCS_ALLOC(s, s->inv, C);
+    st = rcm_order(s, s->lv[0].A, s->perm.p, s->inv.p);
+    DBuf<int32_t> o2, m2;
+    if (st == BCS_OK && F > 0) {
+      BCS_ALLOC(s, o2, F);
+      BCS_ALLOC(s, m2, F);
+      st = relabel_faces(s, o, m, o2.p, m2.p);
+    }
+    if (st == BCS_OK) st = build_structure(s, o2.p, m2.p);
+    if (st == BCS_OK) st = user_diag_maps(s);
+    if (st == BCS_OK) s->reordered = true;
+  }
   s->stage_o.release();
   s->stage_n.release();
   if (st != BCS_OK) return st;
@@ -471,6 +492,18 @@ bcs_status bcs_pack_coefficients(bcs_solver* h, int nfields, const int* ncomp, c
   return BCS_OK;
 }
 
+bcs_status bcs_get_permutation(bcs_solver* h, int32_t* perm) {
+  if (!h) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  if (!s->have_structure) return s->fail(BCS_ESTATE, "no structure");
+  if (!perm) return s->fail(BCS_EINVAL, "null permutation");
+  if (!s->reordered) {
+    for (int i = 0; i < s->C; ++i) perm[i] = i;
+    return BCS_OK;
+  }
+  return to_host(s, perm, s->perm.p, (size_t)s->C * sizeof(int32_t));
+}
+
 bcs_status bcs_invalidate_hierarchy(bcs_solver* h) {
   if (!h) return BCS_EINVAL;
   h->impl.have_hierarchy = false;
@@ -498,9 +531,19 @@ bcs_status bcs_solve(bcs_solver* h, const double* b, double* x, int mem, bcs_res
     bd = s->kb.p;
     xd = s->kx.p;
   }
+  double* xu = xd;  // x in the caller's numbering on the device
+  if (s->reordered) {
+    BCS_ALLOC(s, s->rb, N);
+    BCS_ALLOC(s, s->rx, N);
+    BCS_OKR(to_internal(s, bd, s->rb.p));
+    BCS_OKR(to_internal(s, xd, s->rx.p));
+    bd = s->rb.p;
+    xd = s->rx.p;
+  }
   bcs_status st = solve(s, bd, xd, res);
   if (st == BCS_ECUDA || st == BCS_ENOMEM || st == BCS_EINVAL) return st;
-  if (mem == BCS_MEM_HOST) BCS_OKR(to_host(s, x, xd, N * sizeof(double)));
+  if (s->reordered) BCS_OKR(to_user(s, xd, xu));
+  if (mem == BCS_MEM_HOST) BCS_OKR(to_host(s, x, xu, N * sizeof(double)));
   return st;
 }
 
@@ -519,7 +562,15 @@ bcs_status bcs_spmv(bcs_solver* h, const double* x, double* y, int mem) {
     xd = s->kb.p;
     yd = s->kx.p;
   }
-  BCS_OKR(spmv64(s, s->lv[0].A, xd, false, yd, nullptr, K_SPMV64));
+  if (s->reordered) {
+    BCS_ALLOC(s, s->rb, N);
+    BCS_ALLOC(s, s->rx, N);
+    BCS_OKR(to_internal(s, xd, s->rb.p));
+    BCS_OKR(spmv64(s, s->lv[0].A, s->rb.p, false, s->rx.p, nullptr, K_SPMV64));
+    BCS_OKR(to_user(s, s->rx.p, yd));
+  } else {
+    BCS_OKR(spmv64(s, s->lv[0].A, xd, false, yd, nullptr, K_SPMV64));
+  }
   if (mem == BCS_MEM_HOST) BCS_OKR(to_host(s, y, yd, N * sizeof(double)));
   BCS_CU(s, cudaStreamSynchronize(s->stream));
   return BCS_OK;
@@ -541,6 +592,14 @@ bcs_status bcs_precond_apply(bcs_solver* h, const double* v, double* z, int mem)
     vd = s->kb.p;
   }
   double* zd = mem == BCS_MEM_HOST ? s->kx.p : z;
+  double* zu = zd;  // z in the caller's numbering on the device
+  if (s->reordered) {
+    BCS_ALLOC(s, s->rb, N);
+    BCS_ALLOC(s, s->rx, N);
+    BCS_OKR(to_internal(s, vd, s->rb.p));
+    vd = s->rb.p;
+    zd = s->rx.p;
+  }
   switch (s->setup_cfg.precond) {
     case BCS_PC_AMG:
     case BCS_PC_SGS:
@@ -554,7 +613,8 @@ bcs_status bcs_precond_apply(bcs_solver* h, const double* v, double* z, int mem)
     default:
       BCS_CU(s, cudaMemcpyAsync(zd, vd, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
   }
-  if (mem == BCS_MEM_HOST) BCS_OKR(to_host(s, z, zd, N * sizeof(double)));
+  if (s->reordered) BCS_OKR(to_user(s, zd, zu));
+  if (mem == BCS_MEM_HOST) BCS_OKR(to_host(s, z, zu, N * sizeof(double)));
   BCS_CU(s, cudaStreamSynchronize(s->stream));
   return BCS_OK;
 }

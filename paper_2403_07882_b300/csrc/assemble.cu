@@ -34,12 +34,13 @@ struct Gas {
 constexpr int AS_WARPS = 4;
 constexpr int AS_NN = 25;
 
-// prim[c] = (sqrt(rho), u, v, w, H); flag bit 1 for rho <= 0 or p <= 0 (or NaN)
-__global__ void k_cell_prims(int C, const double* __restrict__ Q, double gamma, double* __restrict__ prim,
-                             int32_t* __restrict__ flag) {
+// prim[c] = (sqrt(rho), u, v, w, H) of row c (the caller's cell perm[c] when
+// the cells are renumbered); flag bit 1 for rho <= 0 or p <= 0 (or NaN)
+__global__ void k_cell_prims(int C, const double* __restrict__ Q, const int32_t* __restrict__ perm, double gamma,
+                             double* __restrict__ prim, int32_t* __restrict__ flag) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
-  const double* q = Q + (size_t)c * 5;
+  const double* q = Q + (size_t)(perm ? perm[c] : c) * 5;
   const double rho = __ldg(q), rE = __ldg(q + 4);
   const double ir = 1.0 / rho;
   const double u = __ldg(q + 1) * ir, v = __ldg(q + 2) * ir, w = __ldg(q + 3) * ir;
@@ -128,8 +129,7 @@ __global__ void k_face_lambda(int F, const int32_t* __restrict__ pos_up, const i
 // the stores are whole blocks.
 template <bool BSR>
 __global__ void __launch_bounds__(AS_WARPS * 32) k_assemble_cells(
-    int C, const int32_t* __restrict__ rp, const int32_t* __restrict__ src, const int32_t* __restrict__ pos_diag,
-    const int32_t* __restrict__ pos_up, const int32_t* __restrict__ pos_lo, const double* __restrict__ prim,
+    int C, const int32_t* __restrict__ rp, const int32_t* __restrict__ src, const int32_t* __restrict__ pos_up, const int32_t* __restrict__ pos_lo, const double* __restrict__ prim,
     const double* __restrict__ area, const double* __restrict__ normal, const double* __restrict__ lam, double gamma,
     double inv_cfl, double* __restrict__ diag, double* __restrict__ upper, double* __restrict__ lower,
     double* __restrict__ val) {
@@ -152,13 +152,17 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assemble_cells(
   const int slots = __reduce_max_sync(0xffffffffu, live ? p1 - p0 - 1 : 0);
   double N[3] = {0.0, 0.0, 0.0};
   double hl = 0.0;
-  int p = p0;
+  int p = p0, pd = -1, cd = -1;  // diagonal block: position, caller's cell
   for (int k = 0; k <= slots; ++k) {
     double* dest = nullptr;
     if (k < slots) {
       // next off-diagonal block of this row, if any
       int code = -1;
-      while (p < p1 && (code = __ldg(src + p)) < 0) ++p;
+      while (p < p1 && (code = __ldg(src + p)) < 0) {
+        pd = p;
+        cd = -1 - code;
+        ++p;
+      }
       if (p < p1) {
         ++p;
         const int f = code >> 1;
@@ -177,8 +181,16 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assemble_cells(
                    : (own ? lower : upper) + (size_t)f * AS_NN;
       }
     } else if (live) {
+      // a row whose diagonal comes after all its faces: find it now
+      for (; pd < 0 && p < p1; ++p) {
+        const int code = __ldg(src + p);
+        if (code < 0) {
+          pd = p;
+          cd = -1 - code;
+        }
+      }
       put_jacobian(mine, g, N, gamma, 1.0, hl + 2.0 * hl * inv_cfl);
-      dest = BSR ? val + (size_t)__ldg(pos_diag + c) * AS_NN : diag + (size_t)c * AS_NN;
+      dest = BSR ? val + (size_t)pd * AS_NN : diag + (size_t)cd * AS_NN;
     }
     __syncwarp();
     // write the staged blocks: element i of the warp's 32 x 25 stage
@@ -204,8 +216,8 @@ bcs_status assemble_density(Solver* s, const double* Q, const double* area, cons
   BCS_ALLOC(s, prim, (size_t)C * 5);
   BCS_CU(s, cudaMemsetAsync(s->flag.p, 0, sizeof(int32_t), s->stream));
   const double visc = (prm.gamma > 4.0 / 3.0 ? prm.gamma : 4.0 / 3.0) * prm.mu / prm.prandtl;
-  BCS_LAUNCH(s, K_ASSEMBLE, 80.0 * C, 0, k_cell_prims, grid_for(C, 256), 256, 0, C, Q, prm.gamma, prim.p,
-             s->flag.p);
+  BCS_LAUNCH(s, K_ASSEMBLE, 80.0 * C, 0, k_cell_prims, grid_for(C, 256), 256, 0, C, Q,
+             s->reordered ? (const int32_t*)s->perm.p : nullptr, prm.gamma, prim.p, s->flag.p);
   if (F > 0)
     BCS_LAUNCH(s, K_ASSEMBLE, 104.0 * F, 0, k_face_lambda, grid_for(F, 256), 256, 0, F, s->pos_up.p, s->pos_lo.p,
                A.ci.p, prim.p, normal, area, dist, prm.gamma, visc, lam.p, s->flag.p);
@@ -215,11 +227,11 @@ bcs_status assemble_density(Solver* s, const double* Q, const double* area, cons
   const unsigned grid = grid_for(C, AS_WARPS * 32);
   if (bsr)
     BCS_LAUNCH(s, K_ASSEMBLE, bytes, flops, k_assemble_cells<true>, grid, AS_WARPS * 32, 0, C, A.rp.p, s->src.p,
-               s->pos_diag.p, s->pos_up.p, s->pos_lo.p, prim.p, area, normal, lam.p, prm.gamma, 1.0 / prm.cfl,
+               s->pos_up.p, s->pos_lo.p, prim.p, area, normal, lam.p, prm.gamma, 1.0 / prm.cfl,
                nullptr, nullptr, nullptr, s->lv[0].A.v.p);
   else
     BCS_LAUNCH(s, K_ASSEMBLE, bytes, flops, k_assemble_cells<false>, grid, AS_WARPS * 32, 0, C, A.rp.p, s->src.p,
-               s->pos_diag.p, s->pos_up.p, s->pos_lo.p, prim.p, area, normal, lam.p, prm.gamma, 1.0 / prm.cfl, diag,
+               s->pos_up.p, s->pos_lo.p, prim.p, area, normal, lam.p, prm.gamma, 1.0 / prm.cfl, diag,
                upper, lower, nullptr);
   int32_t h = 0;
   BCS_CU(s, cudaMemcpyAsync(&h, s->flag.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));

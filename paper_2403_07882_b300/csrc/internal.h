@@ -167,6 +167,12 @@ struct Solver {
   bool have_structure = false, have_values = false, have_hierarchy = false;
   DBuf<int32_t> src;             // BSR position -> LDU source code
   DBuf<int32_t> pos_diag, pos_up, pos_lo;
+  // locality reorder (cfg.reorder): internal row i is the caller's cell
+  // perm[i], inv[cell] = i; pos_diag and the diagonal source codes stay in
+  // the caller's numbering
+  bool reordered = false;
+  DBuf<int32_t> perm, inv;
+  DBuf<double> rb, rx;           // vectors in the internal numbering
   DBuf<double> stage_d, stage_u, stage_l;  // host-input staging
   DBuf<int32_t> stage_o, stage_n;
   // hierarchy
@@ -262,6 +268,13 @@ bcs_status with_n(int n, F&& f) {
 
 // ------------------------------------------------------------------ format.cu
 bcs_status build_structure(Solver* s, const int32_t* owner_d, const int32_t* nb_d);
+// reorder.cu: reverse Cuthill-McKee order of A's rows (perm[new] = old,
+// inv[old] = new) and its application
+bcs_status rcm_order(Solver* s, const Bsr& A, int32_t* perm, int32_t* inv);
+bcs_status relabel_faces(Solver* s, const int32_t* o, const int32_t* nb, int32_t* o2, int32_t* nb2);
+bcs_status user_diag_maps(Solver* s);
+bcs_status to_internal(Solver* s, const double* user, double* internal);  // [C][n] vectors
+bcs_status to_user(Solver* s, const double* internal, double* user);
 // pack.cu: segregated fields <-> block AoS (at most PK_MAX_FIELDS fields);
 // src of pack_coefficients: 3 pointers (diag, upper, lower) per (row field,
 // column field) pair, nullptr = zero coupling; diag == nullptr writes the fine
