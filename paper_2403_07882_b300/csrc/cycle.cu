@@ -257,15 +257,65 @@ __global__ void __launch_bounds__(128) k_sell(int rows, int nslices, const int32
 
 // ---- thread-per-block-row layout (smap = 1) ---------------------------------
 // Slices of 32 block rows, one warp each, one thread per block row. Step t of
-// a slice holds the t-th block of each of its rows, element-major: value
-// (row w, r, c) at t * n*n*32 + (r * n + c) * 32 + w, so for a fixed element
-// the warp reads 128 (FP32) or 64 (BF16) contiguous bytes; sci[t * 32 + w].
-// A thread keeps n*n value loads of one step in flight (one lane-per-row warp
-// of the other layout moves n*n*floor(32/n) values per step). Slice position
-// p holds block row srow[p]: rows are taken in windows of SORT_WIN
-// consecutive rows, longest first (ties by row index), so the rows of a slice
-// have similar lengths and little padding (coarse levels mix rows of 7 to 30
-// blocks).
+// a slice holds the t-th block of each of its rows in a tile of n*n*32
+// values, in groups of G = 16 bytes / value size consecutive block entries:
+// group g of row w at t * n*n*32 + g * G * 32 + w * G, so a thread loads G
+// entries with one 16-byte load and the warp's load is 512 contiguous bytes;
+// the n*n mod G remaining entries are element-major after the groups. Rows
+// shorter than their slice's longest are padded (the padding is skipped).
+// Slice position p holds block row srow[p]: rows are taken in windows of
+// SORT_WIN consecutive rows, longest first (ties by row index), so the rows
+// of a slice have similar lengths and little padding (coarse levels mix rows
+// of 7 to 30 blocks).
+template <int NN, class TV>
+struct TprTile {
+  static constexpr int G = 16 / (int)sizeof(TV);  // entries per 16-byte group
+  static constexpr int NG = NN / G;               // full groups
+  static constexpr int R = NN - NG * G;           // remaining entries
+  static constexpr int TILE = NN * 32;
+  __host__ __device__ static constexpr int off(int e, int w) {
+    return e < NG * G ? (e / G) * G * 32 + w * G + e % G : NG * G * 32 + (e - NG * G) * 32 + w;
+  }
+};
+
+// resident blocks of 128 threads per SM the sweep is compiled for (caps its
+// registers at 64)
+#define TPR_MINB 7
+
+// the NN entries of row w in one step tile, widened to FP32
+template <int NN>
+__device__ __forceinline__ void load_tile_row(const float* __restrict__ tile, int w, float* a) {
+  using T = TprTile<NN, float>;
+#pragma unroll
+  for (int g = 0; g < T::NG; ++g) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(tile + g * 4 * 32 + w * 4));
+    a[4 * g] = v.x;
+    a[4 * g + 1] = v.y;
+    a[4 * g + 2] = v.z;
+    a[4 * g + 3] = v.w;
+  }
+#pragma unroll
+  for (int r = 0; r < T::R; ++r) a[T::NG * 4 + r] = __ldg(tile + T::NG * 4 * 32 + r * 32 + w);
+}
+
+template <int NN>
+__device__ __forceinline__ void load_tile_row(const bf16* __restrict__ tile, int w, float* a) {
+  using T = TprTile<NN, bf16>;
+#pragma unroll
+  for (int g = 0; g < T::NG; ++g) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(tile + g * 8 * 32 + w * 8));
+    const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[k]));
+      a[8 * g + 2 * k] = f.x;
+      a[8 * g + 2 * k + 1] = f.y;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < T::R; ++r) a[T::NG * 8 + r] = __bfloat162float(__ldg(tile + T::NG * 8 * 32 + r * 32 + w));
+}
+
 constexpr int SORT_WIN = 256;
 
 __global__ void __launch_bounds__(SORT_WIN) k_window_order(int rows, const int32_t* __restrict__ rp,
@@ -289,7 +339,8 @@ template <int N, class TV>
 __global__ void k_tpr_fill(int rows, int nslices, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const double* __restrict__ val, const int32_t* __restrict__ srow,
                            const int32_t* __restrict__ sptr, int32_t* __restrict__ sci, TV* __restrict__ sv) {
-  constexpr int NN = N * N, TILE = NN * 32;
+  constexpr int NN = N * N;
+  using T = TprTile<NN, TV>;
   const int lane = threadIdx.x & 31;
   const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (sl >= nslices) return;
@@ -299,11 +350,22 @@ __global__ void k_tpr_fill(int rows, int nslices, const int32_t* __restrict__ rp
   const int t0 = sptr[sl];
   for (int k = 0; k < len; ++k) {
     const double* a = val + (size_t)(p0 + k) * NN;
-    TV* tile = sv + (size_t)(t0 + k) * TILE + lane;
+    TV* tile = sv + (size_t)(t0 + k) * T::TILE;
+    // one 16-byte store per group: the warp writes 512 contiguous bytes
 #pragma unroll
-    for (int e = 0; e < NN; ++e) {
-      if constexpr (std::is_same<TV, bf16>::value) tile[e * 32] = __double2bfloat16(a[e]);
-      else tile[e * 32] = (TV)a[e];
+    for (int g = 0; g < T::NG; ++g) {
+      alignas(16) TV v[T::G];
+#pragma unroll
+      for (int q = 0; q < T::G; ++q) {
+        if constexpr (std::is_same<TV, bf16>::value) v[q] = __double2bfloat16(a[g * T::G + q]);
+        else v[q] = (TV)a[g * T::G + q];
+      }
+      *reinterpret_cast<uint4*>(tile + g * T::G * 32 + lane * T::G) = *reinterpret_cast<const uint4*>(v);
+    }
+#pragma unroll
+    for (int r = 0; r < T::R; ++r) {
+      if constexpr (std::is_same<TV, bf16>::value) tile[T::NG * T::G * 32 + r * 32 + lane] = __double2bfloat16(a[T::NG * T::G + r]);
+      else tile[T::NG * T::G * 32 + r * 32 + lane] = (TV)a[T::NG * T::G + r];
     }
     sci[(size_t)(t0 + k) * 32 + lane] = ci[p0 + k];
   }
@@ -314,7 +376,7 @@ __global__ void k_tpr_fill(int rows, int nslices, const int32_t* __restrict__ rp
 // ascending; the epilogue in column order), so both layouts give identical
 // results.
 template <int N, class TV, bool JACOBI>
-__global__ void __launch_bounds__(128) k_tpr(int rows, int nslices, const int32_t* __restrict__ rp,
+__global__ void __launch_bounds__(128, TPR_MINB) k_tpr(int rows, int nslices, const int32_t* __restrict__ rp,
                                              const int32_t* __restrict__ srow, const int32_t* __restrict__ sptr,
                                              const int32_t* __restrict__ sci, const TV* __restrict__ sv,
                                              const float* __restrict__ dinv, const float* __restrict__ x,
@@ -326,6 +388,7 @@ __global__ void __launch_bounds__(128) k_tpr(int rows, int nslices, const int32_
   const int pos = sl * 32 + lane;
   if (pos >= rows) return;
   const int i = __ldg(srow + pos);
+  static_assert(TprTile<NN, TV>::TILE == TILE, "tile size");
   const int len = __ldg(rp + i + 1) - __ldg(rp + i);
   const int t0 = __ldg(sptr + sl);
   const size_t o = (size_t)i * N;
@@ -338,8 +401,7 @@ __global__ void __launch_bounds__(128) k_tpr(int rows, int nslices, const int32_
   int j = 0;
   if (len > 0) {
     j = __ldg(sci + (size_t)t0 * 32 + lane);
-#pragma unroll
-    for (int e = 0; e < NN; ++e) a[e] = ldsv(sv + (size_t)t0 * TILE + lane + e * 32);
+    load_tile_row<NN>(sv + (size_t)t0 * TILE, lane, a);
   }
   for (int k = 0; k < len; ++k) {
     float xv[N];
@@ -349,8 +411,7 @@ __global__ void __launch_bounds__(128) k_tpr(int rows, int nslices, const int32_
     int jn = 0;
     if (k + 1 < len) {
       jn = __ldg(sci + (size_t)(t0 + k + 1) * 32 + lane);
-#pragma unroll
-      for (int e = 0; e < NN; ++e) an[e] = ldsv(sv + (size_t)(t0 + k + 1) * TILE + lane + e * 32);
+      load_tile_row<NN>(sv + (size_t)(t0 + k + 1) * TILE, lane, an);
     }
 #pragma unroll
     for (int r = 0; r < N; ++r)

@@ -318,7 +318,7 @@ __device__ __forceinline__ double plus_zero(double v) {
 // cap output blocks accumulate in place in global memory). The first term of
 // an output is stored, not added: 0 + v equals v except that -0 becomes +0
 // (integer operations), so no FP64 add is spent on it. TS_U fine blocks are
-// fetched per round trip.
+// fetched per round trip, their positions one round ahead.
 constexpr int TS_U = 8;
 constexpr int TS_WARPS = 4;
 constexpr int TS_SMEM_DOUBLES = 32;  // per lane: cap * ceil(n^2 / 32) <= this
@@ -348,13 +348,22 @@ __global__ void __launch_bounds__(TS_WARPS * 32) k_tent_sum(int nagg, int cap, c
   double* acc = in_smem ? ts_acc + (size_t)warp * 32 * cap * S::E + lane : out + (size_t)base * NN + e0;
   const int ss = in_smem ? 32 * S::E : NN, sj = in_smem ? 32 : S::W;
   const int t1 = seg[I + 1];
-  for (int t = seg[I]; t < t1; t += TS_U) {
+  // software pipeline: the next round's positions are fetched while this
+  // round's values are in flight
+  int kn[TS_U], dn[TS_U];
+  const int tb = seg[I];
+#pragma unroll
+  for (int u = 0; u < TS_U; ++u) {
+    const bool ok = tb + u < t1;
+    kn[u] = ok ? __ldg(seqk + tb + u) : -1;
+    dn[u] = ok ? __ldg(seqd + tb + u) : 0;
+  }
+  for (int t = tb; t < t1; t += TS_U) {
     int k[TS_U], d[TS_U];
 #pragma unroll
     for (int u = 0; u < TS_U; ++u) {
-      const bool ok = t + u < t1;
-      k[u] = ok ? __ldg(seqk + t + u) : -1;
-      d[u] = ok ? __ldg(seqd + t + u) : 0;
+      k[u] = kn[u];
+      d[u] = dn[u];
     }
     double v[TS_U][S::E];
 #pragma unroll
@@ -364,6 +373,13 @@ __global__ void __launch_bounds__(TS_WARPS * 32) k_tent_sum(int nagg, int cap, c
         const int e = e0 + j * S::W;
         v[u][j] = (k[u] >= 0 && e < NN) ? __ldg(src + (size_t)k[u] * NN + e) : 0.0;
       }
+#pragma unroll
+    for (int u = 0; u < TS_U; ++u) {
+      const int tn = t + TS_U + u;
+      const bool ok = tn < t1;
+      kn[u] = ok ? __ldg(seqk + tn) : -1;
+      dn[u] = ok ? __ldg(seqd + tn) : 0;
+    }
 #pragma unroll
     for (int u = 0; u < TS_U; ++u) {
       if (k[u] < 0) continue;
