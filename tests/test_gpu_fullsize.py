@@ -8,6 +8,11 @@ settings, FP32-stored AMG inside FP64 FGMRES unless stated):
 * pressure-based 64^3 4x4 with permuted numbering (262,144 cells): hierarchy
   bit-exact, FP64 V-cycle at 1e-12, BiCGStab and FGMRES(30) to a true
   relative residual of 1e-8;
+* the benchmark's other arms on density 128^3: GMRES + multicolour SGS and
+  FGMRES + AMG with the DILU smoother to a true relative residual of 1e-8,
+  the SGS colouring valid (no coupled pair shares a colour);
+* pressure-based 64^3 with the reverse Cuthill-McKee renumbering: the
+  permutation equal to the CPU reference's, solve to 1e-8;
 * unstructured k-NN 160^3 (4.1 M cells, k ~ U{4..12}): structure maps exact,
   FP64 SpMV at 1e-12, sampled Galerkin rows of every level (Sec. 2.3: with
   the piecewise-constant prolongation a coarse block is the sum of the fine
@@ -141,3 +146,35 @@ def test_knn_160_structure_spmv_galerkin_and_resetups():
             xs, st, res = s.solve(b)
             assert st == bcs.BCS_OK, res
             assert true_rel(ref, system["b"], xs.cpu().numpy()) <= 1e-8
+
+
+def test_density_128_sgs_and_dilu_arms():
+    system = synth.density(128, seed=2)
+    ref = oracle.ldu_to_bsr(system)
+    d = {k: dev(system[k]) for k in ("owner", "neighbour", "diag", "upper", "lower", "b")}
+    for kw in (dict(precond=bcs.BCS_PC_SGS, maxiter=5000), dict(smoother=bcs.BCS_SMOOTH_DILU)):
+        with bcs.Solver(5, **kw) as s:
+            s.set_structure(system["n_cells"], d["owner"], d["neighbour"])
+            s.set_values(d["diag"], d["upper"], d["lower"])
+            x, st, res = s.solve(d["b"])
+            assert st == bcs.BCS_OK, (kw, res)
+            assert true_rel(ref, system["b"], x.cpu().numpy()) <= 1e-8 * (1 + 1e-3), kw
+            if "precond" in kw:
+                nc, col, einv = s.dilu(0)
+                assert nc > 0
+                rp, ci = ref["row_ptr"], ref["col"]
+                rows = np.repeat(np.arange(system["n_cells"]), np.diff(rp))
+                off = rows != ci
+                assert not np.any(col[rows[off]] == col[ci[off]])
+
+
+def test_pressure_64_renumbered(pressure64):
+    system, ref = pressure64
+    perm_ref = oracle.rcm(system["n_cells"], system["owner"], system["neighbour"])
+    with bcs.Solver(4, solver=bcs.BCS_BICGSTAB, reorder=1) as s:
+        s.set_structure(system["n_cells"], dev(system["owner"]), dev(system["neighbour"]))
+        assert np.array_equal(s.permutation(), perm_ref)
+        s.set_values(dev(system["diag"]), dev(system["upper"]), dev(system["lower"]))
+        x, st, res = s.solve(dev(system["b"]))
+        assert st == bcs.BCS_OK, res
+    assert true_rel(ref, system["b"], x.cpu().numpy()) <= 1e-8 * (1 + 1e-3)
