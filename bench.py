@@ -329,6 +329,7 @@ def run_native(args):
     traffic = measured_traffic(top_name, per_launch_bytes)
     roofline = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind + " (copy bandwidth)",
+                "frac_of_nominal_7700": achieved / 7700.0,
                 "launches_in_timed_region": top["launches"], "bytes_per_launch": per_launch_bytes,
                 "ms_per_launch": per_launch_ms}
     # per-kind and per-kernel tables: one profiled step outside the timed region
