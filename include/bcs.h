@@ -113,6 +113,17 @@ typedef struct bcs_config {
                               reverse Cuthill-McKee order for locality (vectors, LDU arrays and
                               results stay in the caller's numbering; bcs_get_permutation);
                               0 (default) = keep the caller's numbering */
+  /* Device memory, read by bcs_create (later changes are ignored): with alloc
+     and release both set, every device buffer of the solver comes from
+     alloc(bytes, stream, alloc_user) and goes back through release(ptr,
+     bytes, stream, alloc_user), stream being the solver's stream, on the
+     thread that calls into the library; memory is used stream-ordered on that
+     stream; alloc returns NULL when it cannot allocate (the call then fails
+     with BCS_ENOMEM). Both NULL (default): cudaMallocAsync / cudaFreeAsync on
+     the solver's stream. Exactly one of them set is BCS_EINVAL. */
+  void* (*alloc)(size_t bytes, void* stream, void* alloc_user);
+  void (*release)(void* ptr, size_t bytes, void* stream, void* alloc_user);
+  void* alloc_user;
 } bcs_config;
 
 typedef struct bcs_result {

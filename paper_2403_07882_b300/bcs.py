@@ -27,6 +27,11 @@ BCS_SMOOTH_JACOBI, BCS_SMOOTH_DILU, BCS_SMOOTH_SGS = 0, 1, 2
 NUM_KERNEL_KINDS = 16
 
 
+# device allocator callbacks of bcs_config
+ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
+RELEASE_FN = ct.CFUNCTYPE(None, ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
+
+
 class bcs_config(ct.Structure):
     _fields_ = [
         ("solver", ct.c_int), ("restart", ct.c_int), ("tol", ct.c_double), ("maxiter", ct.c_int),
@@ -36,6 +41,7 @@ class bcs_config(ct.Structure):
         ("p_omega", ct.c_double), ("coarse_dense_max", ct.c_int), ("coarse_sweeps", ct.c_int),
         ("precision", ct.c_int), ("smoother", ct.c_int), ("profile", ct.c_int), ("profile_kinds", ct.c_int),
         ("slice_layout", ct.c_int), ("cycle_graph", ct.c_int), ("reorder", ct.c_int),
+        ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_user", ct.c_void_p),
     ]
 
 
@@ -419,12 +425,36 @@ def bcs_ldu_structure_noalloc(n_cells, owner, neighbour, row_ptr, col, pos_diag,
     return st, buf.value.decode()
 
 
-class Solver:
-    """Owning wrapper: a solver handle for n x n blocks."""
+def torch_allocator():
+    """(alloc, release) callbacks drawing the solver's device memory from
+    PyTorch's caching allocator on the solver's stream."""
+    import torch
 
-    def __init__(self, n, **cfg):
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(nbytes, stream=stream or 0)
+        except RuntimeError:
+            return None
+
+    def _release(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return ALLOC_FN(_alloc), RELEASE_FN(_release)
+
+
+class Solver:
+    """Owning wrapper: a solver handle for n x n blocks. allocator="torch"
+    takes the device memory from PyTorch's caching allocator."""
+
+    def __init__(self, n, allocator=None, **cfg):
         self.n = n
         self.cfg = bcs_config_default(**cfg)
+        self._alloc_cbs = None
+        if allocator == "torch":
+            self._alloc_cbs = torch_allocator()
+            self.cfg.alloc, self.cfg.release = self._alloc_cbs
+        elif allocator is not None:
+            raise ValueError("allocator: None or 'torch'")
         self.h = bcs_create(n, self.cfg)
         self.C = self.F = 0
 

@@ -22,6 +22,11 @@ const char* kind_name(int k) {
 // copies of any span of it stay inside the allocation.
 void* Alloc::get(size_t bytes) {
   void* p = nullptr;
+  if (fa) {
+    p = fa(bytes + 16, (void*)stream, user);
+    if (p) live += bytes;
+    return p;
+  }
   if (cudaMallocAsync(&p, bytes + 16, stream) != cudaSuccess) {
     (void)cudaGetLastError();
     return nullptr;
@@ -32,7 +37,8 @@ void* Alloc::get(size_t bytes) {
 
 void Alloc::put(void* p, size_t bytes) {
   if (!p) return;
-  (void)cudaFreeAsync(p, stream);
+  if (fr) fr(p, bytes + 16, (void*)stream, user);
+  else (void)cudaFreeAsync(p, stream);
   live -= bytes;
 }
 
@@ -105,6 +111,7 @@ bcs_status check_config(const bcs_config* c) {
   if (c->precision < BCS_PREC_FP64 || c->precision > BCS_PREC_BF16) return BCS_EINVAL;
   if (c->cycle_graph < -1 || c->cycle_graph > 1) return BCS_EINVAL;
   if (c->reorder < 0 || c->reorder > 1) return BCS_EINVAL;
+  if ((c->alloc == nullptr) != (c->release == nullptr)) return BCS_EINVAL;
   if (c->slice_layout < -1 || c->slice_layout > 1) return BCS_EINVAL;
   if (c->smoother < BCS_SMOOTH_JACOBI || c->smoother > BCS_SMOOTH_SGS) return BCS_EINVAL;
   if (!(c->max_coarsen_ratio > 0.0) || !(c->p_omega > 0.0) || !(c->jacobi_omega > 0.0)) return BCS_EINVAL;
@@ -222,6 +229,9 @@ bcs_status bcs_create(bcs_solver** out, int n, const bcs_config* cfg, void* stre
   s->setup_cfg = c;
   s->stream = (cudaStream_t)stream;
   s->alloc.stream = s->stream;
+  s->alloc.fa = c.alloc;
+  s->alloc.fr = c.release;
+  s->alloc.user = c.alloc_user;
   if (!s->flag.resize(&s->alloc, 4) || !s->scal.resize(&s->alloc, 160) ||
       cudaMallocHost(&s->hscal, 160 * sizeof(double)) != cudaSuccess) {
     (void)cudaGetLastError();

@@ -43,6 +43,10 @@ const char* kind_name(int k);
 struct Alloc {
   cudaStream_t stream = nullptr;
   size_t live = 0;
+  // caller's allocator (bcs_config.alloc / release), else cudaMallocAsync
+  void* (*fa)(size_t, void*, void*) = nullptr;
+  void (*fr)(void*, size_t, void*, void*) = nullptr;
+  void* user = nullptr;
   void* get(size_t bytes);
   void put(void* p, size_t bytes);
 };

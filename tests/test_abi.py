@@ -43,6 +43,9 @@ def test_config_default_and_null_checks(lib):
     assert lib.bcs_create(ct.byref(h), 9, None, None) == bcs.BCS_EINVAL   # block size out of range
     bad = bcs.bcs_config_default(restart=0)
     assert lib.bcs_create(ct.byref(h), 5, ct.byref(bad), None) == bcs.BCS_EINVAL
+    half = bcs.bcs_config_default()
+    half.alloc = bcs.ALLOC_FN(lambda nbytes, stream, user: None)   # alloc without release
+    assert lib.bcs_create(ct.byref(h), 5, ct.byref(half), None) == bcs.BCS_EINVAL
     assert lib.bcs_solve(None, None, None, 0, None) == bcs.BCS_EINVAL
     assert lib.bcs_num_levels(None) == 0
     assert lib.bcs_last_error(None) == b"null solver"
@@ -57,9 +60,10 @@ def test_kernel_kind_names(lib):
 def test_struct_layouts_match_header():
     text = open(os.path.join(ROOT, "include", "bcs.h")).read()
     body = re.search(r"typedef struct bcs_config \{(.*?)\} bcs_config;", text, re.S).group(1)
-    fields = re.findall(r"^\s*(?:int|double)\s+([\w, ]+);", body, re.M)
-    names = [f.strip() for group in fields for f in group.split(",")]
+    fields = re.findall(r"^\s*(?:int|double|void\s*\*)\s+([\w, ]+);|^\s*void\s*\*?\s*\(\*(\w+)\)", body, re.M)
+    names = [f.strip() for a, b in fields for f in (a.split(",") if a else [b])]
     assert names == [f for f, _ in bcs.bcs_config._fields_]
+    assert names[-3:] == ["alloc", "release", "alloc_user"]
     body = re.search(r"typedef struct bcs_result \{(.*?)\} bcs_result;", text, re.S).group(1)
     names = [f.strip() for group in re.findall(r"^\s*(?:int|double)\s+([\w, ]+);", body, re.M)
              for f in group.split(",")]
