@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=200.0)
     p.add_argument("--serve-max-cells", type=float, default=3e6)
     p.add_argument("--serve-slots", type=int, default=8)
+    p.add_argument("--serve-budget-gb", type=float, default=0.0,
+                   help="HBM budget of the server in GB (0: the default, 80 %% of free memory)")
     return p.parse_args()
 
 
@@ -650,7 +652,8 @@ def run_serve(args):
     _ = rng_case.uniform(np.log(5e4), np.log(max_cells), ncases)
     keys = ("diag", "upper", "lower", "b")
     t0 = time.perf_counter()
-    with bcs.Server(slots=args.serve_slots) as srv:
+    budget = int(args.serve_budget_gb * 1e9)
+    with bcs.Server(budget_bytes=budget, slots=args.serve_slots) as srv:
         cases, ids, kinds = [], [], []
         for c in range(ncases):
             nx = int(round(cells[c] ** (1.0 / 3.0)))
@@ -682,8 +685,8 @@ def run_serve(args):
                     while len(pending) >= 2 * args.serve_slots:
                         rr, t = pending.pop(0)
                         st, res, l, _ = srv.wait(t)
-                        assert st == bcs.BCS_OK, res
-                        if rr >= warmup:
+                        assert st in (bcs.BCS_OK, bcs.BCS_REJECTED), res
+                        if rr >= warmup and st == bcs.BCS_OK:
                             lat.append(l)
                             iters.append(res["iters"])
                 else:
@@ -702,22 +705,22 @@ def run_serve(args):
                         if st == bcs.BCS_TIMEOUT:
                             keep.append((rr, t))
                         else:
-                            assert st == bcs.BCS_OK, res
-                            if rr >= warmup:
+                            assert st in (bcs.BCS_OK, bcs.BCS_REJECTED), res
+                            if rr >= warmup and st == bcs.BCS_OK:
                                 lat.append(l)
                                 iters.append(res["iters"])
                     pending = keep
             for rr, t in pending:
                 st, res, l, _ = srv.wait(t)
-                assert st == bcs.BCS_OK, res
-                if rr >= warmup:
+                assert st in (bcs.BCS_OK, bcs.BCS_REJECTED), res
+                if rr >= warmup and st == bcs.BCS_OK:
                     lat.append(l)
                     iters.append(res["iters"])
             elapsed = time.perf_counter() - measure_from
             stats = srv.stats()
             lat = np.array(lat)
             return {"offered_per_s": rate if not closed else None, "requests": total - warmup,
-                    "solves_per_s": (total - warmup) / elapsed,
+                    "solves_per_s": len(lat) / elapsed,
                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                     "mean_ms": float(lat.mean()), "iters_max": int(max(iters)),
                     "evictions": stats["evictions"], "rejected": stats["rejected"],
@@ -732,6 +735,7 @@ def run_serve(args):
     print(json.dumps({"impl": "native", "mode": "serve", "cases": ncases,
                       "cells_range": [5e4, max_cells], "cells_mean": float(cells.mean()),
                       "block_sizes": {"5": kinds.count(5), "4": kinds.count(4)}, "slots": args.serve_slots,
+                      "budget": "default (80 % of free memory)" if budget == 0 else f"{args.serve_budget_gb:g} GB",
                       "inputs": "two value sets per case resident in device memory, alternated per request",
                       "setup_s": gen_s, "configured_rate": configured, "closed_loop_capacity": capacity,
                       "at_80pct_capacity": below}), flush=True)
