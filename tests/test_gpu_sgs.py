@@ -94,3 +94,25 @@ def test_sgs_solves(gen, solver):
         assert st == bcs.BCS_OK, res
     r = system["b"] - oracle.spmv(ref, x.cpu().numpy())
     assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(system["b"])
+
+
+def test_sgs_beyond_128_colours_is_block_jacobi():
+    """130 mutually coupled cells need more than the 128 colours allowed: the
+    SGS preconditioner is then one block-Jacobi solve, as in the reference."""
+    m, n = 130, 2
+    rng = np.random.default_rng(9)
+    pairs = [(i, j) for i in range(m) for j in range(i + 1, m)]
+    owner = np.array([i for i, _ in pairs], np.int32)
+    nb = np.array([j for _, j in pairs], np.int32)
+    F = owner.size
+    diag = np.repeat((4.0 * m * np.eye(n))[None], m, 0) + rng.standard_normal((m, n, n))
+    system = dict(n_cells=m, n_faces=F, n=n, owner=owner, neighbour=nb, diag=diag,
+                  upper=0.1 * rng.standard_normal((F, n, n)), lower=0.1 * rng.standard_normal((F, n, n)),
+                  b=rng.standard_normal((m, n)))
+    v = rng.standard_normal((m, n))
+    z_ref = np.einsum("iab,ib->ia", np.linalg.inv(diag), v)
+    with bcs.Solver(n, precond=bcs.BCS_PC_SGS, precision=bcs.BCS_PREC_FP64) as s:
+        s.load(system, device=DEV)
+        assert s.dilu(0)[0] <= 0
+        z = s.precond(torch.from_numpy(v).to(DEV)).cpu().numpy()
+    assert np.allclose(z, z_ref, rtol=1e-12, atol=1e-14)

@@ -128,3 +128,26 @@ def test_gmres_sgs_and_amg_sgs_solve(gen):
         its[name] = res["iters"]
     assert its["gmres+sgs"] < its["gmres+jacobi"]
     assert its["gmres+amg(sgs)"] < its["gmres+sgs"]
+
+
+def test_sgs_beyond_128_colours_is_block_jacobi():
+    """A complete graph of 130 cells needs 130 colours, more than the 128
+    allowed: the SGS preconditioner falls back to one block-Jacobi solve."""
+    m, n = 130, 2
+    rng = np.random.default_rng(9)
+    rows = [(i, j) for i in range(m) for j in range(i + 1, m)]
+    owner = np.array([i for i, _ in rows], np.int32)
+    nb = np.array([j for _, j in rows], np.int32)
+    F = owner.size
+    diag = np.repeat((4.0 * m * np.eye(n))[None], m, 0) + rng.standard_normal((m, n, n))
+    sys_ = dict(n_cells=m, n_faces=F, n=n, owner=owner, neighbour=nb, diag=diag,
+                upper=0.1 * rng.standard_normal((F, n, n)), lower=0.1 * rng.standard_normal((F, n, n)),
+                b=rng.standard_normal((m, n)))
+    bsr = oracle.ldu_to_bsr(sys_)
+    nc, _ = oracle.colour(bsr)
+    assert nc == -1
+    done, V, Z, H = oracle.arnoldi(bsr, sys_["b"], 3, cfg=oracle.config(precond=3))
+    Dinv = np.linalg.inv(diag)
+    for j in range(done):
+        assert np.allclose(Z[j].reshape(m, n), np.einsum("iab,ib->ia", Dinv, V[j].reshape(m, n)), rtol=1e-12,
+                           atol=1e-14)
