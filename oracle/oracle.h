@@ -17,6 +17,14 @@
  *   Sec. 2.3              aggregation AMG for block systems built by graph
  *                         matching, smoothers, Krylov solvers (GMRES, BiCGStab).
  *   Sec. 2 (ref. Saad & Schultz)  GMRES.
+ *   Sec. 2.1, Eqs. approxJac1/2   assembly of the density-based blocks from
+ *                         cell states and face geometry (assembly.cpp).
+ *   Sec. 2.1 / Sec. 5     LU-SGS / SGS preconditioning (multicolour block SGS,
+ *                         precond = 3, smoother = 2).
+ *   Sec. 2.3              cell renumbering: reverse Cuthill-McKee
+ *                         (reorder.cpp). The segregated-field <-> block AoS
+ *                         conversions of Alg. 1 steps 1, 5, 15 are plain numpy
+ *                         definitions in __init__.py.
  * The paper leaves the AMG and Krylov details unspecified; the readings used
  * here (matching rule, smoothed prolongation, block-Jacobi smoother, CGS2,
  * stopping rule, coarse solve) are written out beside each function.
