@@ -119,8 +119,10 @@ typedef struct bcs_config {
      bytes, stream, alloc_user), stream being the solver's stream, on the
      thread that calls into the library; memory is used stream-ordered on that
      stream; alloc returns NULL when it cannot allocate (the call then fails
-     with BCS_ENOMEM). Both NULL (default): cudaMallocAsync / cudaFreeAsync on
-     the solver's stream. Exactly one of them set is BCS_EINVAL. */
+     with BCS_ENOMEM); memory must be 256-byte aligned (anything else is
+     handed back and treated as a failed allocation). Both NULL (default):
+     cudaMallocAsync / cudaFreeAsync on the solver's stream. Exactly one of
+     them set is BCS_EINVAL. */
   void* (*alloc)(size_t bytes, void* stream, void* alloc_user);
   void (*release)(void* ptr, size_t bytes, void* stream, void* alloc_user);
   void* alloc_user;

@@ -24,6 +24,11 @@ void* Alloc::get(size_t bytes) {
   void* p = nullptr;
   if (fa) {
     p = fa(bytes + 16, (void*)stream, user);
+    if (p && reinterpret_cast<uintptr_t>(p) % 256 != 0) {
+      // the kernels use 16-byte vector accesses and rely on 256-byte bases
+      fr(p, bytes + 16, (void*)stream, user);
+      return nullptr;
+    }
     if (p) live += bytes;
     return p;
   }

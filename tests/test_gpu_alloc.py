@@ -66,3 +66,30 @@ def test_allocator_running_dry_gives_enomem():
         bcs.bcs_destroy(h)
     torch.cuda.synchronize()
     assert torch.cuda.memory_allocated() == base
+
+
+def test_misaligned_allocator_memory_is_refused():
+    """Memory that is not 256-byte aligned is handed back unused and the
+    upload fails with BCS_ENOMEM (the kernels' vector accesses rely on it)."""
+    system = synth.density(4, seed=2)
+
+    def _alloc(nbytes, stream, user):
+        return torch.cuda.caching_allocator_alloc(nbytes + 64, stream=stream or 0) + 16
+
+    def _release(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr - 16)
+
+    cbs = (bcs.ALLOC_FN(_alloc), bcs.RELEASE_FN(_release))
+    cfg = bcs.bcs_config_default()
+    cfg.alloc, cfg.release = cbs
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    with pytest.raises(bcs.BcsError) as e:
+        h = bcs.bcs_create(5, cfg)
+        try:
+            bcs.bcs_set_structure(h, system["n_cells"], system["owner"], system["neighbour"])
+        finally:
+            bcs.bcs_destroy(h)
+    assert e.value.status == bcs.BCS_ENOMEM
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == base
