@@ -283,7 +283,10 @@ BCS_API bcs_status bcs_get_permutation(bcs_solver* s, int32_t* perm);
 
 /* Test hooks: copies of internal state to HOST arrays (any may be NULL).
  * bcs_get_bsr: row_ptr[C+1], col[nnz], val[nnz][n][n] of the fine matrix and
- * the LDU -> BSR maps pos_diag[C], pos_up[F], pos_lo[F]. */
+ * the LDU -> BSR maps pos_diag[C], pos_up[F], pos_lo[F]. Matrices and level
+ * data are in the internal row numbering (bcs_get_permutation maps it to the
+ * caller's cells when cfg.reorder = 1); pos_diag is indexed by the caller's
+ * cell, pos_up / pos_lo by face. */
 BCS_API bcs_status bcs_get_bsr(bcs_solver* s, int32_t* row_ptr, int32_t* col, double* val,
                        int32_t* pos_diag, int32_t* pos_up, int32_t* pos_lo);
 /* Number of AMG levels (0 without a hierarchy). */
