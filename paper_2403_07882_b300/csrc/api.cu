@@ -276,6 +276,7 @@ bcs_status bcs_set_config(bcs_solver* h, const bcs_config* cfg) {
 
 bcs_status bcs_set_structure(bcs_solver* h, int32_t C, int32_t F, const int32_t* owner, const int32_t* nb,
                              int mem) {
+  NvtxRange nvtx_("bcs_set_structure");
   if (!h) return BCS_EINVAL;
   Solver* s = &h->impl;
   s->have_structure = s->have_values = s->have_hierarchy = false;
@@ -315,6 +316,7 @@ bcs_status bcs_set_structure(bcs_solver* h, int32_t C, int32_t F, const int32_t*
 }
 
 bcs_status bcs_set_values(bcs_solver* h, const double* diag, const double* upper, const double* lower, int mem) {
+  NvtxRange nvtx_("bcs_set_values");
   if (!h) return BCS_EINVAL;
   Solver* s = &h->impl;
   if (!s->have_structure) return s->fail(BCS_ESTATE, "set_values before set_structure");
@@ -342,6 +344,7 @@ bcs_status bcs_flow_params_default(bcs_flow_params* p) {
 bcs_status bcs_assemble_density(bcs_solver* h, const double* Q, const double* area, const double* normal,
                                 const double* dist, const bcs_flow_params* prm, double* diag, double* upper,
                                 double* lower, int mem) {
+  NvtxRange nvtx_("bcs_assemble_density");
   if (!h) return BCS_EINVAL;
   Solver* s = &h->impl;
   if (!s->have_structure) return s->fail(BCS_ESTATE, "assemble before set_structure");
@@ -405,6 +408,7 @@ static bcs_status check_fields(Solver* s, int nfields, const int* ncomp, int mem
 
 bcs_status bcs_pack_vector(bcs_solver* h, int nfields, const int* ncomp, const double* const* fields, double* out,
                            int mem) {
+  NvtxRange nvtx_("bcs_pack_vector");
   if (!h) return BCS_EINVAL;
   Solver* s = &h->impl;
   BCS_OKR(check_fields(s, nfields, ncomp, mem));
@@ -428,6 +432,7 @@ bcs_status bcs_pack_vector(bcs_solver* h, int nfields, const int* ncomp, const d
 
 bcs_status bcs_unpack_vector(bcs_solver* h, int nfields, const int* ncomp, const double* in, double* const* fields,
                              int mem) {
+  NvtxRange nvtx_("bcs_unpack_vector");
   if (!h) return BCS_EINVAL;
   Solver* s = &h->impl;
   BCS_OKR(check_fields(s, nfields, ncomp, mem));
@@ -455,6 +460,7 @@ bcs_status bcs_unpack_vector(bcs_solver* h, int nfields, const int* ncomp, const
 
 bcs_status bcs_pack_coefficients(bcs_solver* h, int nfields, const int* ncomp, const bcs_coupling* coupling,
                                  double* diag, double* upper, double* lower, int mem) {
+  NvtxRange nvtx_("bcs_pack_coefficients");
   if (!h) return BCS_EINVAL;
   Solver* s = &h->impl;
   BCS_OKR(check_fields(s, nfields, ncomp, mem));
@@ -526,6 +532,7 @@ bcs_status bcs_invalidate_hierarchy(bcs_solver* h) {
 }
 
 bcs_status bcs_solve(bcs_solver* h, const double* b, double* x, int mem, bcs_result* res) {
+  NvtxRange nvtx_("bcs_solve");
   if (!h) return BCS_EINVAL;
   Solver* s = &h->impl;
   bcs_result local{};
@@ -563,6 +570,7 @@ bcs_status bcs_solve(bcs_solver* h, const double* b, double* x, int mem, bcs_res
 }
 
 bcs_status bcs_spmv(bcs_solver* h, const double* x, double* y, int mem) {
+  NvtxRange nvtx_("bcs_spmv");
   if (!h) return BCS_EINVAL;
   Solver* s = &h->impl;
   if (!s->have_values) return s->fail(BCS_ESTATE, "spmv before set_values");
@@ -592,6 +600,7 @@ bcs_status bcs_spmv(bcs_solver* h, const double* x, double* y, int mem) {
 }
 
 bcs_status bcs_precond_apply(bcs_solver* h, const double* v, double* z, int mem) {
+  NvtxRange nvtx_("bcs_precond_apply");
   if (!h) return BCS_EINVAL;
   Solver* s = &h->impl;
   if (!s->have_hierarchy) return s->fail(BCS_ESTATE, "precond_apply before set_values");

@@ -3,6 +3,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <cstring>
@@ -17,6 +18,15 @@
 namespace bcs {
 
 using bf16 = __nv_bfloat16;
+
+// NVTX range over a library call (header-only NVTX 3: a no-op unless a
+// profiler such as Nsight attaches its tool).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Kernel kinds for launch counting and event timing.
 enum Kind {
