@@ -185,3 +185,25 @@ def test_assembled_system_solves():
         assert res["status"] == 0
         r = fl["b"] - oracle.spmv(bsr, x)
         assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(fl["b"])
+
+
+def test_single_cell_and_single_face():
+    """No faces: the diagonal block is zero (no face terms, no time term). One
+    face: the two diagonal blocks and the two off-diagonal blocks are the
+    four terms of Eqs. approxJac1/2 written out."""
+    fl = synth.flow(1, 1, 1, seed=2)
+    st, d, u, l = oracle.assemble_density(fl)
+    assert st == 0 and u.shape == (0, 5, 5) and np.array_equal(d, np.zeros((1, 5, 5)))
+    fl = synth.flow(2, 1, 1, seed=3)
+    p = oracle.FLOW_DEFAULTS
+    st, d, u, l = oracle.assemble_density(fl)
+    assert st == 0
+    n, S = fl["normal"][0], fl["area"][0]
+    Qi, Qj = fl["Q"][0], fl["Q"][1]
+    lam = oracle.face_lambda(Qi, Qj, n, fl["dist"][0], p["gamma"], p["mu"], p["prandtl"])
+    Ji, Jj, I = oracle.flux_jacobian(Qi, n), oracle.flux_jacobian(Qj, n), np.eye(5)
+    t = lam * S / p["cfl"]
+    assert np.allclose(d[0], 0.5 * S * (Ji + lam * I) + t * I, rtol=1e-14, atol=1e-15)
+    assert np.allclose(d[1], 0.5 * S * (-Jj + lam * I) + t * I, rtol=1e-14, atol=1e-15)
+    assert np.allclose(u[0], 0.5 * S * (Jj - lam * I), rtol=1e-14, atol=1e-15)
+    assert np.allclose(l[0], 0.5 * S * (-Ji - lam * I), rtol=1e-14, atol=1e-15)

@@ -50,3 +50,12 @@ def test_round_trips():
                                        system["n_cells"], system["n_faces"])
     assert np.array_equal(d, system["diag"]) and np.array_equal(u, system["upper"])
     assert np.array_equal(l, system["lower"])
+
+
+def test_single_field_is_identity_and_all_zero_couplings():
+    rng = np.random.default_rng(4)
+    C, F = 5, 4
+    v = rng.standard_normal(C * 4)
+    assert np.array_equal(oracle.pack_vector([v], [4]), v.reshape(C, 4))
+    d, u, l = oracle.pack_coefficients([[None, None], [None, None]], [2, 2], C, F)
+    assert not d.any() and not u.any() and not l.any() and d.shape == (C, 4, 4)

@@ -53,3 +53,13 @@ def test_face_order_does_not_matter_and_random_grid_recovers_lattice_bandwidth()
     assert bandwidth(np.arange(C, dtype=np.int32), o, nb) > 5 * 81    # random numbering
     assert bandwidth(perm, o, nb) <= 1.5 * 81                          # lattice numbering: 9^2
     assert oracle.rcm(3, np.array([0], np.int32), np.array([0], np.int32)) is None
+
+
+def test_degenerate_graphs():
+    assert list(oracle.rcm(1, np.zeros(0, np.int32), np.zeros(0, np.int32))) == [0]
+    # no faces: every cell its own component, taken by index and reversed
+    assert list(oracle.rcm(4, np.zeros(0, np.int32), np.zeros(0, np.int32))) == [3, 2, 1, 0]
+    # owner > neighbour is the same edge
+    a = oracle.rcm(3, np.array([0, 1], np.int32), np.array([1, 2], np.int32))
+    b = oracle.rcm(3, np.array([1, 2], np.int32), np.array([0, 1], np.int32))
+    assert np.array_equal(a, b)
