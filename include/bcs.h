@@ -197,6 +197,7 @@ typedef struct bcs_flow_params {
   double cfl;      /* pseudo-time CFL number, > 0 (default 10) */
 } bcs_flow_params;
 
+/* Fill p with the defaults above; BCS_EINVAL for NULL. */
 BCS_API bcs_status bcs_flow_params_default(bcs_flow_params* p);
 
 /* Assemble the density-based coupled system on the device (Sec. 2.1,
@@ -277,8 +278,10 @@ BCS_API bcs_status bcs_spmv(bcs_solver* s, const double* x, double* y, int mem);
  * V-cycle from zero) in the configured precision, returned in FP64. */
 BCS_API bcs_status bcs_precond_apply(bcs_solver* s, const double* v, double* z, int mem);
 
-/* perm[C] (HOST): the caller's cell of every internal row (the identity
- * unless the structure was built with cfg.reorder = 1). */
+/* perm[C] (HOST, caller-owned): the caller's cell of every internal row
+ * (the identity unless the structure was built with cfg.reorder = 1, the
+ * reverse Cuthill-McKee order standing in for Sec. 2.3's renumbering).
+ * BCS_ESTATE before bcs_set_structure, BCS_EINVAL for NULL. */
 BCS_API bcs_status bcs_get_permutation(bcs_solver* s, int32_t* perm);
 
 /* Test hooks: copies of internal state to HOST arrays (any may be NULL).
