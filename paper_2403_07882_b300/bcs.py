@@ -478,10 +478,14 @@ class Solver:
         bcs_set_config(self.h, self.cfg)
 
     def set_structure(self, n_cells, owner, neighbour):
+        """LDU face addressing (int32 owner / neighbour per face, Sec. 2.3):
+        builds the block-CSR structure; drops any values and hierarchy."""
         self.C, self.F = int(n_cells), len(owner)
         bcs_set_structure(self.h, n_cells, owner, neighbour)
 
     def set_values(self, diag, upper, lower):
+        """Coefficients diag[C][n][n], upper / lower[F][n][n] (FP64): full AMG
+        setup the first time, values-only resetup afterwards (Alg. 1)."""
         bcs_set_values(self.h, diag, upper, lower)
 
     def load(self, system, device=None):
@@ -544,18 +548,22 @@ class Solver:
         return tuple(out)
 
     def solve(self, b, x=None):
+        """Solve A x = b to cfg.tol (x holds x0 on entry, zeros when None);
+        returns (x, status, result dict)."""
         if x is None:
             x = np.zeros_like(b) if isinstance(b, np.ndarray) else b.new_zeros(b.shape)
         st, res = bcs_solve(self.h, b, x)
         return x, st, res
 
     def spmv(self, x, y=None):
+        """y = A x with the fine FP64 matrix."""
         if y is None:
             y = np.zeros_like(x) if isinstance(x, np.ndarray) else x.new_zeros(x.shape)
         bcs_spmv(self.h, x, y)
         return y
 
     def precond(self, v, z=None):
+        """z = M^-1 v: one application of the configured preconditioner."""
         if z is None:
             z = np.zeros_like(v) if isinstance(v, np.ndarray) else v.new_zeros(v.shape)
         bcs_precond_apply(self.h, v, z)
