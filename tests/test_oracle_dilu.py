@@ -163,3 +163,27 @@ def test_dilu_resetup_and_solve():
         assert nc1 == nc0 and np.array_equal(col0, col1)
         st, e_ref = oracle.dilu_factor(bsr2, col0)
         assert np.array_equal(e1, e_ref)
+
+
+def test_level_beyond_128_colours_keeps_block_jacobi():
+    """A level whose graph needs more than 128 colours keeps the damped block
+    Jacobi smoother: with the DILU option the one-level cycle equals the
+    Jacobi one exactly."""
+    m, n = 130, 2
+    rng = np.random.default_rng(11)
+    pairs = [(i, j) for i in range(m) for j in range(i + 1, m)]
+    owner = np.array([i for i, _ in pairs], np.int32)
+    nb = np.array([j for _, j in pairs], np.int32)
+    F = owner.size
+    sys_ = dict(n_cells=m, n_faces=F, n=n, owner=owner, neighbour=nb,
+                diag=np.repeat((4.0 * m * np.eye(n))[None], m, 0) + rng.standard_normal((m, n, n)),
+                upper=0.1 * rng.standard_normal((F, n, n)), lower=0.1 * rng.standard_normal((F, n, n)),
+                b=rng.standard_normal((m, n)))
+    bsr = oracle.ldu_to_bsr(sys_)
+    kw = dict(coarse_size=10 ** 6, coarse_dense_max=0, coarse_sweeps=3)   # one level, smoother sweeps
+    a_dilu = oracle.Amg(bsr, oracle.config(smoother=1, **kw))
+    a_jac = oracle.Amg(bsr, oracle.config(smoother=0, **kw))
+    assert a_dilu.status == 0 and a_dilu.levels == 1
+    assert a_dilu.dilu(0)[0] == -1
+    v = rng.standard_normal((m, n))
+    assert np.array_equal(a_dilu.vcycle(v), a_jac.vcycle(v))
