@@ -81,6 +81,9 @@ def lib():
         L.or_dilu_apply.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, _i32p, ct.c_int, _f64p, _f64p, _f64p]
         L.or_solve.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, ct.c_void_p, ct.POINTER(Config),
                                _f64p, _f64p, ct.POINTER(Result), ct.c_void_p, ct.c_int]
+        L.or_solve_trace.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, ct.c_void_p, ct.POINTER(Config),
+                                     _f64p, _f64p, ct.POINTER(Result), ct.c_void_p, ct.c_int,
+                                     ct.c_void_p, ct.c_void_p, ct.c_int]
         L.or_fgmres_arnoldi.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _f64p, ct.c_void_p,
                                         ct.POINTER(Config), _f64p, ct.c_int, _f64p, _f64p, _f64p]
         L.or_rcm.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _i32p]
@@ -277,6 +280,24 @@ def solve(bsr, b, x0=None, cfg=None, amg=None, hist_len=0):
                    _p(hist) if hist_len else None, hist_len)
     out = {k: getattr(res, k) for k, _ in Result._fields_}
     return x.reshape(rows, n), out, hist[:min(hist_len, res.iters)] if hist_len else None
+
+
+def bicgstab_trace(bsr, b, cfg, amg=None, max_iters=200):
+    """BiCGStab (cfg.solver must be 1) with its per-iteration iterates x_k
+    and recurrence residuals: (x, result dict, xs[k], rs[k])."""
+    assert cfg.solver == 1
+    n, rows = bsr["n"], bsr["rows"]
+    N = rows * n
+    x = np.zeros(N)
+    res = Result()
+    xs = np.zeros((max_iters, N))
+    rs = np.zeros((max_iters, N))
+    cnt = lib().or_solve_trace(rows, n, bsr["row_ptr"], bsr["col"], np.ascontiguousarray(bsr["val"]).ravel(),
+                               amg.h if amg is not None else None, ct.byref(cfg),
+                               np.ascontiguousarray(b, np.float64).ravel(), x, ct.byref(res), None, 0,
+                               _p(xs), _p(rs), max_iters)
+    out = {k: getattr(res, k) for k, _ in Result._fields_}
+    return x.reshape(rows, n), out, xs[:cnt], rs[:cnt]
 
 
 def arnoldi(bsr, b, j_steps, cfg=None, amg=None):

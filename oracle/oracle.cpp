@@ -1092,7 +1092,25 @@ int fgmres(const Sys& S, const double* b, double* x0, or_result* res, double* hi
   return status;
 }
 
-int bicgstab(const Sys& S, const double* b, double* x0, or_result* res, double* hist, int hist_len) {
+// Per-iteration record of BiCGStab's iterate x_k and its recurrence residual
+// (the vector the recurrence carries as b - A x_k: r_k after a full step, s
+// after a half step that ends the solve). Test hook.
+struct Trace {
+  double* x = nullptr;
+  double* r = nullptr;
+  int cap = 0;
+  int count = 0;
+  void record(const std::vector<double>& xv, const std::vector<double>& rv) {
+    if (count >= cap) return;
+    const size_t N = xv.size();
+    std::copy(xv.begin(), xv.end(), x + (size_t)count * N);
+    std::copy(rv.begin(), rv.end(), r + (size_t)count * N);
+    ++count;
+  }
+};
+
+int bicgstab(const Sys& S, const double* b, double* x0, or_result* res, double* hist, int hist_len,
+             Trace* tr) {
   const int N = S.N;
   const double tol = S.cfg->tol;
   std::vector<double> bb(b, b + N), x(x0, x0 + N), r, rhat, p(N, 0.0), v(N, 0.0), s(N), t, ph, sh;
@@ -1148,6 +1166,7 @@ int bicgstab(const Sys& S, const double* b, double* x0, or_result* res, double* 
     if (sn <= tol * bnorm) {
       for (int e = 0; e < N; ++e) x[e] = x[e] + alpha * ph[e];
       if (hist && it <= hist_len) hist[it - 1] = sn / bnorm;
+      if (tr) tr->record(x, s);
       true_residual(S, b, x, r);
       if (nrm2(r) <= tol * bnorm) { status = 0; break; }
       restart(false);
@@ -1168,6 +1187,7 @@ int bicgstab(const Sys& S, const double* b, double* x0, or_result* res, double* 
     rho_old = rho;
     double rn = nrm2(r);
     if (hist && it <= hist_len) hist[it - 1] = rn / bnorm;
+    if (tr) tr->record(x, r);
     if (rn <= tol * bnorm) {
       true_residual(S, b, x, r);
       if (nrm2(r) <= tol * bnorm) { status = 0; break; }
@@ -1206,17 +1226,28 @@ Sys make_sys(int rows, int n, const int32_t* rp, const int32_t* ci, const double
 
 }  // namespace
 
-extern "C" int or_solve(int rows, int n, const int32_t* rp, const int32_t* ci, const double* val,
-                        const or_amg* h, const or_config* cfg, const double* b, double* x,
-                        or_result* res, double* hist, int hist_len) {
+extern "C" int or_solve_trace(int rows, int n, const int32_t* rp, const int32_t* ci, const double* val,
+                              const or_amg* h, const or_config* cfg, const double* b, double* x,
+                              or_result* res, double* hist, int hist_len, double* xtrace, double* rtrace,
+                              int trace_len) {
   int bad = 0;
   Sys S = make_sys(rows, n, rp, ci, val, h, cfg, &bad);
   res->levels = h ? or_amg_levels(h) : 0;
   if (bad) { res->status = 6; return 6; }
-  int st = cfg->solver == 1 ? bicgstab(S, b, x, res, hist, hist_len)
+  Trace tr;
+  tr.x = xtrace;
+  tr.r = rtrace;
+  tr.cap = (xtrace && rtrace) ? trace_len : 0;
+  int st = cfg->solver == 1 ? bicgstab(S, b, x, res, hist, hist_len, tr.cap > 0 ? &tr : nullptr)
                             : fgmres(S, b, x, res, hist, hist_len);
   res->status = st;
-  return st;
+  return tr.cap > 0 ? tr.count : st;
+}
+
+extern "C" int or_solve(int rows, int n, const int32_t* rp, const int32_t* ci, const double* val,
+                        const or_amg* h, const or_config* cfg, const double* b, double* x,
+                        or_result* res, double* hist, int hist_len) {
+  return or_solve_trace(rows, n, rp, ci, val, h, cfg, b, x, res, hist, hist_len, nullptr, nullptr, 0);
 }
 
 extern "C" int or_fgmres_arnoldi(int rows, int n, const int32_t* rp, const int32_t* ci,

@@ -170,6 +170,16 @@ int or_solve(int rows, int n, const int32_t* row_ptr, const int32_t* col,
              const double* val, const or_amg* h, const or_config* cfg,
              const double* b, double* x, or_result* res, double* hist, int hist_len);
 
+/* As or_solve; BiCGStab (solver = 1) also records, for each of the first
+ * trace_len iterations, its iterate x_k in xtrace[k][rows*n] and the
+ * residual its recurrence carries for x_k in rtrace[k][rows*n] (r_k after a
+ * full step, s after a half step that ends the solve). Returns the number of
+ * iterations recorded (the status when nothing is traced). Test hook. */
+int or_solve_trace(int rows, int n, const int32_t* row_ptr, const int32_t* col,
+                   const double* val, const or_amg* h, const or_config* cfg,
+                   const double* b, double* x, or_result* res, double* hist, int hist_len,
+                   double* xtrace, double* rtrace, int trace_len);
+
 /* Arnoldi check hook: runs j_steps of FGMRES's Arnoldi process from x0 = 0 and
  * returns V (j+1 vectors) and Z (j vectors), H ((j+1) x j, row-major). */
 int or_fgmres_arnoldi(int rows, int n, const int32_t* row_ptr, const int32_t* col,

@@ -2,12 +2,17 @@
 GPU solvers of Sec. 2.3: GMRES and BiCGStab with AMG).
 
 Pinned against: the Arnoldi relation and orthonormality, brute-force
-least-squares minimality over the Krylov space (numpy lstsq), termination in
-N steps, one-iteration convergence with an exact preconditioner, and the true
-residual recomputed with numpy.
+least-squares minimality over the Krylov space (numpy lstsq) for one cycle
+and for a chain of restarted cycles, termination in N steps, one-iteration
+convergence with an exact preconditioner, the true residual recomputed with
+numpy, BiCGStab's recurrence residual against the true residual of every
+iterate, and BiCGStab's iterates against SciPy's independent implementation
+of the same method (van der Vorst's BiCGStab, right preconditioned, shadow
+residual r_0).
 """
 import numpy as np
 import pytest
+import scipy.sparse.linalg as sla
 
 import oracle
 from paper_2403_07882_b300 import synth
@@ -115,3 +120,100 @@ def test_block_jacobi_and_none_preconditioners_converge():
     for pc in (1, 2):
         x, res, _ = oracle.solve(bsr, sys["b"], cfg=oracle.config(precond=pc))
         assert res["status"] == 0 and true_rel_residual(bsr, sys["b"], x) <= 1e-8
+
+
+def test_restarted_gmres_cycles_are_krylov_minima():
+    """FGMRES(3), M = I, x0 = 0: within each restart cycle c the residual
+    after j steps is min ||r_c - A y|| over y in K_j(A, r_c), r_c the true
+    residual the cycle starts from. Brute force: numpy builds each cycle's
+    Krylov basis by QR, solves the least-squares problem and carries its own
+    iterate to the next cycle."""
+    for sys in (synth.random_graph(8, 12, 2, seed=3), synth.random_graph(12, 20, 3, seed=5)):
+        bsr = oracle.ldu_to_bsr(sys)
+        A = dense_from_bsr(bsr)
+        b = sys["b"].ravel()
+        N, m, cycles = A.shape[0], 3, 5
+        assert N >= 12
+        cfg = oracle.config(precond=1, restart=m, maxiter=m * cycles, tol=1e-300)
+        x, res, hist = oracle.solve(bsr, b, cfg=cfg, hist_len=m * cycles)
+        assert res["iters"] == m * cycles and res["restarts"] == cycles - 1
+        xc = np.zeros(N)
+        bn = np.linalg.norm(b)
+        ref = []
+        for _ in range(cycles):
+            r = b - A @ xc
+            Q = (r / np.linalg.norm(r))[:, None]
+            for j in range(1, m + 1):
+                y, *_ = np.linalg.lstsq(A @ Q, r, rcond=None)
+                ref.append(np.linalg.norm(r - A @ Q @ y) / bn)
+                if j < m:
+                    Q, _ = np.linalg.qr(np.column_stack([Q, A @ Q[:, -1]]))
+            xc = xc + Q @ y
+        np.testing.assert_allclose(hist, ref, rtol=1e-9, atol=0)
+        # a restarted method loses the minimality over the whole space: the
+        # chain ends above the unrestarted minimum of the same step count
+        assert np.linalg.norm(x.ravel() - xc) <= 1e-12 * np.linalg.norm(xc)
+
+
+def _bicgstab_cases():
+    return [synth.density(3, seed=4), synth.random_graph(30, 60, 4, seed=3), synth.random_graph(36, 80, 5, seed=7)]
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_bicgstab_recurrence_equals_true_residual(case):
+    """The residual BiCGStab carries by recurrence (r_k = s - omega t) is the
+    true residual b - A x_k of its iterate, at every iteration, up to
+    rounding (Sec. 2.3's PBiCGStab; van der Vorst's update of x and r)."""
+    sys = _bicgstab_cases()[case]
+    bsr = oracle.ldu_to_bsr(sys)
+    A = dense_from_bsr(bsr)
+    b = sys["b"].ravel()
+    for precond in (1, 2, 0):
+        cfg = oracle.config(solver=1, precond=precond, tol=1e-12, maxiter=80, coarse_size=8)
+        amg = oracle.Amg(bsr, cfg) if precond == 0 else None
+        x, res, xs, rs = oracle.bicgstab_trace(bsr, b, cfg, amg=amg)
+        assert res["status"] == 0 and res["restarts"] == 0 and len(xs) == res["iters"] >= 2
+        for k in range(len(xs)):
+            drift = np.linalg.norm(rs[k] - (b - A @ xs[k]))
+            assert drift <= 1e-10 * np.linalg.norm(b), (precond, k, drift)
+        assert np.array_equal(xs[-1], x.ravel())
+
+
+def _block_jacobi_operator(bsr):
+    n, rows = bsr["n"], bsr["rows"]
+    D = np.zeros((rows, n, n))
+    for i in range(rows):
+        k = bsr["row_ptr"][i] + int(np.nonzero(bsr["col"][bsr["row_ptr"][i]:bsr["row_ptr"][i + 1]] == i)[0][0])
+        D[i] = np.linalg.inv(bsr["val"][k])
+    return sla.LinearOperator((rows * n, rows * n), matvec=lambda v: np.einsum("irc,ic->ir", D, v.reshape(rows, n)).ravel())
+
+
+@pytest.mark.parametrize("case", range(3))
+@pytest.mark.parametrize("precond", [1, 2])
+def test_bicgstab_iterates_match_scipy(case, precond):
+    """Same method, independent code: SciPy's bicgstab (shadow residual r_0,
+    beta = (rho / rho_old)(alpha / omega), omega = (t, s) / (t, t), right
+    preconditioned: x += alpha M p + omega M s). Without a preconditioner and
+    with one block-Jacobi solve z = D^-1 v as M, every iterate x_k agrees to
+    rounding, and so do the residual norms while they are above the rounding
+    floor."""
+    sys = _bicgstab_cases()[case]
+    bsr = oracle.ldu_to_bsr(sys)
+    A = dense_from_bsr(bsr)
+    b = sys["b"].ravel()
+    assert A.shape[0] <= 200
+    cfg = oracle.config(solver=1, precond=precond, tol=1e-13, maxiter=60)
+    x, res, xs, rs = oracle.bicgstab_trace(bsr, b, cfg)
+    sx = []
+    M = _block_jacobi_operator(bsr) if precond == 2 else None
+    sla.bicgstab(A, b, x0=np.zeros_like(b), rtol=1e-13, atol=0.0, maxiter=60, M=M,
+                 callback=lambda xk: sx.append(xk.copy()))
+    # SciPy calls back after full steps only; the oracle also records the
+    # half step that ends the solve
+    assert len(sx) >= 5 and len(xs) - 1 <= len(sx) <= len(xs)
+    bn = np.linalg.norm(b)
+    for k in range(len(sx)):
+        assert np.linalg.norm(xs[k] - sx[k]) <= 1e-10 * np.linalg.norm(sx[k]), k
+        ro, rsc = np.linalg.norm(b - A @ xs[k]) / bn, np.linalg.norm(b - A @ sx[k]) / bn
+        if rsc > 1e-7:
+            assert ro == pytest.approx(rsc, rel=1e-8), k
