@@ -140,3 +140,51 @@ def test_full_size_128cube_mixed_solve():
     x, st, res = gpu_solve(system)
     assert st == bcs.BCS_OK, res
     assert true_rel(ref, system["b"], x) <= 1e-8
+
+
+RESTARTS = [
+    ("density 16^3 m=5", lambda: synth.density(16, seed=0), dict(restart=5)),
+    ("pressure 12^3 m=5", lambda: synth.pressure(12, seed=1), dict(restart=5)),
+    ("pressure 12^3 m=3", lambda: synth.pressure(12, seed=1), dict(restart=3)),
+    ("density 12^3 m=2 no AMG", lambda: synth.density(12, seed=4), dict(restart=2, precond=bcs.BCS_PC_JACOBI)),
+]
+
+
+@pytest.mark.parametrize("name,gen,cfg", RESTARTS, ids=[c[0] for c in RESTARTS])
+def test_restarted_fgmres_fp64_matches_oracle(name, gen, cfg):
+    """FGMRES(m) with m below the iteration count (GMRES restarted after m
+    steps from the true residual, Sec. 2), all in FP64: the GPU restarts as
+    often as the oracle, takes the same number of iterations (+-1) and
+    reaches the true relative residual 1e-8 recomputed on the CPU."""
+    system = gen()
+    ref = oracle.ldu_to_bsr(system)
+    xo, ores, _ = oracle.solve(ref, system["b"], cfg=oracle.config(**cfg))
+    assert ores["status"] == 0 and ores["restarts"] >= 1
+    x, st, res = gpu_solve(system, precision=bcs.BCS_PREC_FP64, **cfg)
+    assert st == bcs.BCS_OK, res
+    assert abs(res["iters"] - ores["iters"]) <= 1, (res["iters"], ores["iters"])
+    assert abs(res["restarts"] - ores["restarts"]) <= 1, (res["restarts"], ores["restarts"])
+    assert res["restarts"] >= 1
+    rel = true_rel(ref, system["b"], x)
+    assert rel <= 1e-8
+    dx = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    print(f"{name}: iters gpu={res['iters']} ref={ores['iters']} restarts gpu={res['restarts']} "
+          f"ref={ores['restarts']} |dx|/|x|={dx:.2e}")
+
+
+@pytest.mark.parametrize("solver", [bcs.BCS_FGMRES, bcs.BCS_BICGSTAB])
+@pytest.mark.parametrize("precision", [bcs.BCS_PREC_FP64, bcs.BCS_PREC_FP32])
+def test_coarse_smoother_sweeps_solve(solver, precision):
+    """Coarsest level without the dense inverse (coarse_dense_max = 1: eight
+    block-Jacobi sweeps there instead): solves still reach 1e-8, FP64 in the
+    oracle's iteration count (+-1)."""
+    system = synth.pressure(12, seed=1)
+    cfg = dict(coarse_dense_max=1, solver=solver)
+    ref = oracle.ldu_to_bsr(system)
+    xo, ores, _ = oracle.solve(ref, system["b"], cfg=oracle.config(**cfg))
+    assert ores["status"] == 0
+    x, st, res = gpu_solve(system, precision=precision, **cfg)
+    assert st == bcs.BCS_OK, res
+    assert true_rel(ref, system["b"], x) <= 1e-8
+    if precision == bcs.BCS_PREC_FP64:
+        assert abs(res["iters"] - ores["iters"]) <= 1, (res["iters"], ores["iters"])
