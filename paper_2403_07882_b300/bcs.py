@@ -160,27 +160,82 @@ def exported_names():
 
 
 # ------------------------------------------------------------ marshalling
-def _ptr_mem(*arrays):
-    """Pointers and the memory kind of a group of arrays (all host or all device)."""
+# Sizes the library cannot check (it receives bare pointers): per solver
+# handle [n, C, F], per (server, case id) the case's [n, C, F].
+_dims = {}
+
+
+def _key(h):
+    return h.value if isinstance(h, ct.c_void_p) else h
+
+
+def _current_device():
+    import torch
+    return torch.cuda.current_device()
+
+
+def _marshal(*specs):
+    """Pointers and the memory kind of one call's arrays, validated first.
+
+    specs: (array or None, dtype name, element count or None). Arrays are
+    numpy arrays (host) or torch tensors (CUDA: device memory; CPU: host).
+    Raises ValueError, before anything reaches the library, for a wrong
+    dtype or element count, a non-contiguous array, a mix of host and
+    device arrays, or a CUDA tensor on another device than the current one
+    (the library launches on the current device)."""
     mems = set()
     ptrs = []
-    for a in arrays:
+    for a, dt, count in specs:
         if a is None:
             ptrs.append(None)
             continue
         if isinstance(a, np.ndarray):
+            if a.dtype != np.dtype(dt):
+                raise ValueError(f"expected a {dt} array, got {a.dtype}")
             if not a.flags["C_CONTIGUOUS"]:
                 raise ValueError("arrays must be C-contiguous")
+            numel = a.size
             ptrs.append(a.ctypes.data)
             mems.add(BCS_MEM_HOST)
         else:  # torch tensor
+            if str(a.dtype) != "torch." + dt:
+                raise ValueError(f"expected a {dt} tensor, got {a.dtype}")
             if not a.is_contiguous():
                 raise ValueError("tensors must be contiguous")
+            numel = a.numel()
+            if a.is_cuda:
+                if a.device.index != _current_device():
+                    raise ValueError(f"tensor on {a.device}, but the current CUDA device is "
+                                     f"cuda:{_current_device()}")
+                mems.add(BCS_MEM_DEVICE)
+            else:
+                mems.add(BCS_MEM_HOST)
             ptrs.append(a.data_ptr())
-            mems.add(BCS_MEM_DEVICE if a.is_cuda else BCS_MEM_HOST)
+        if count is not None and numel != count:
+            raise ValueError(f"expected {count} elements, got {numel}")
     if len(mems) > 1:
         raise ValueError("mix of host and device arrays in one call")
     return ptrs, (mems.pop() if mems else BCS_MEM_HOST)
+
+
+def _solver_dims(h):
+    """(n, C, F) of a solver handle; C and F are None before set_structure
+    (the library then refuses the call with BCS_ESTATE, touching no array)."""
+    d = _dims.get(_key(h))
+    if d is None:
+        raise ValueError("unknown or destroyed solver handle")
+    return d[0], (d[1] if d[1] > 0 else None), (d[2] if d[1] > 0 else None)
+
+
+def _cnt(*factors):
+    """Product of the factors; None (no size check: the library judges the
+    call) when one is unknown or not positive."""
+    out = 1
+    for f in factors:
+        if f is None or f <= 0:
+            return None
+        out *= f
+    return out
 
 
 def _check(status, handle=None):
@@ -215,10 +270,12 @@ def bcs_create(n, cfg=None, stream=None):
     st = lib().bcs_create(ct.byref(h), n, ct.byref(cfg) if cfg is not None else None,
                           stream if stream is not None else _current_stream())
     _check(st)
+    _dims[_key(h)] = [int(n), 0, 0]
     return h
 
 
 def bcs_destroy(h):
+    _dims.pop(_key(h), None)
     return lib().bcs_destroy(h)
 
 
@@ -227,12 +284,18 @@ def bcs_set_config(h, cfg):
 
 
 def bcs_set_structure(h, n_cells, owner, neighbour):
-    (po, pn), mem = _ptr_mem(owner, neighbour)
-    return _check(lib().bcs_set_structure(h, n_cells, len(owner), po, pn, mem), h)
+    _solver_dims(h)
+    F = len(owner)
+    (po, pn), mem = _marshal((owner, "int32", F), (neighbour, "int32", F))
+    _check(lib().bcs_set_structure(h, n_cells, F, po, pn, mem), h)
+    _dims[_key(h)][1:] = [int(n_cells), F]
+    return BCS_OK
 
 
 def bcs_set_values(h, diag, upper, lower):
-    (pd, pu, pl), mem = _ptr_mem(diag, upper, lower)
+    n, C, F = _solver_dims(h)
+    (pd, pu, pl), mem = _marshal((diag, "float64", _cnt(C, n, n)), (upper, "float64", _cnt(F, n, n)),
+                                 (lower, "float64", _cnt(F, n, n)))
     return _check(lib().bcs_set_values(h, pd, pu, pl, mem), h)
 
 
@@ -247,7 +310,11 @@ def bcs_flow_params_default(**overrides):
 
 
 def bcs_assemble_density(h, Q, area, normal, dist, prm, diag=None, upper=None, lower=None):
-    (pq, pa, pn, pd, pdg, pu, pl), mem = _ptr_mem(Q, area, normal, dist, diag, upper, lower)
+    n, C, F = _solver_dims(h)
+    f = "float64"
+    (pq, pa, pn, pd, pdg, pu, pl), mem = _marshal((Q, f, _cnt(C, 5)), (area, f, F), (normal, f, _cnt(F, 3)),
+                                                  (dist, f, F), (diag, f, _cnt(C, 25)), (upper, f, _cnt(F, 25)),
+                                                  (lower, f, _cnt(F, 25)))
     return _check(lib().bcs_assemble_density(h, pq, pa, pn, pd, ct.byref(prm), pdg, pu, pl, mem), h)
 
 
@@ -256,22 +323,41 @@ def _ints(vals):
 
 
 def bcs_pack_vector(h, ncomp, fields, out):
-    ptrs, mem = _ptr_mem(*fields, out)
+    n, C, F = _solver_dims(h)
+    if len(fields) != len(ncomp):
+        raise ValueError("one field per entry of ncomp")
+    ptrs, mem = _marshal(*((a, "float64", _cnt(C, m)) for a, m in zip(fields, ncomp)), (out, "float64", _cnt(C, n)))
     arr = (ct.c_void_p * len(fields))(*ptrs[:-1])
     return _check(lib().bcs_pack_vector(h, len(ncomp), _ints(ncomp), arr, ptrs[-1], mem), h)
 
 
 def bcs_unpack_vector(h, ncomp, vec, fields):
-    ptrs, mem = _ptr_mem(vec, *fields)
+    n, C, F = _solver_dims(h)
+    if len(fields) != len(ncomp):
+        raise ValueError("one field per entry of ncomp")
+    ptrs, mem = _marshal((vec, "float64", _cnt(C, n)), *((a, "float64", _cnt(C, m)) for a, m in zip(fields, ncomp)))
     arr = (ct.c_void_p * len(fields))(*ptrs[1:])
     return _check(lib().bcs_unpack_vector(h, len(ncomp), _ints(ncomp), ptrs[0], arr, mem), h)
 
 
 def bcs_pack_coefficients(h, ncomp, coupling, diag=None, upper=None, lower=None):
     """coupling[a][b] = (diag, upper, lower) arrays or None (zero coupling)."""
+    n, C, F = _solver_dims(h)
     nf = len(ncomp)
-    flat = [a for row in coupling for cp in row if cp is not None for a in cp]
-    ptrs, mem = _ptr_mem(*flat, diag, upper, lower)
+    if len(coupling) != nf or any(len(row) != nf for row in coupling):
+        raise ValueError("coupling must be an nfields x nfields table")
+    specs = []
+    for a in range(nf):
+        for b in range(nf):
+            cp = coupling[a][b]
+            if cp is not None:
+                if len(cp) != 3:
+                    raise ValueError("a coupling is (diag, upper, lower)")
+                m = ncomp[a] * ncomp[b]
+                specs += [(cp[0], "float64", _cnt(C, m)), (cp[1], "float64", _cnt(F, m)), (cp[2], "float64", _cnt(F, m))]
+    flat = [sp[0] for sp in specs]
+    ptrs, mem = _marshal(*specs, (diag, "float64", _cnt(C, n, n)), (upper, "float64", _cnt(F, n, n)),
+                         (lower, "float64", _cnt(F, n, n)))
     tab = (bcs_coupling * (nf * nf))()
     it = iter(ptrs[:len(flat)])
     for a in range(nf):
@@ -288,7 +374,8 @@ def bcs_invalidate_hierarchy(h):
 
 def bcs_solve(h, b, x, check=False):
     """Solve in place into x; returns (status, result dict)."""
-    (pb, px), mem = _ptr_mem(b, x)
+    n, C, F = _solver_dims(h)
+    (pb, px), mem = _marshal((b, "float64", _cnt(C, n)), (x, "float64", _cnt(C, n)))
     res = bcs_result()
     st = lib().bcs_solve(h, pb, px, mem, ct.byref(res))
     if st in (BCS_EINVAL, BCS_ENOMEM, BCS_ECUDA, BCS_ESTATE) or (check and st != BCS_OK):
@@ -297,12 +384,14 @@ def bcs_solve(h, b, x, check=False):
 
 
 def bcs_spmv(h, x, y):
-    (px, py), mem = _ptr_mem(x, y)
+    n, C, F = _solver_dims(h)
+    (px, py), mem = _marshal((x, "float64", _cnt(C, n)), (y, "float64", _cnt(C, n)))
     return _check(lib().bcs_spmv(h, px, py, mem), h)
 
 
 def bcs_precond_apply(h, v, z):
-    (pv, pz), mem = _ptr_mem(v, z)
+    n, C, F = _solver_dims(h)
+    (pv, pz), mem = _marshal((v, "float64", _cnt(C, n)), (z, "float64", _cnt(C, n)))
     return _check(lib().bcs_precond_apply(h, pv, pz, mem), h)
 
 
@@ -416,11 +505,16 @@ def bcs_ldu_structure_noalloc(n_cells, owner, neighbour, row_ptr, col, pos_diag,
 
     Returns (status, message); the library allocates no device memory here.
     """
-    (po, pn, prp, pc, pd, pu, pl), mem = _ptr_mem(owner, neighbour, row_ptr, col, pos_diag, pos_up, pos_lo)
+    C, F, i = int(n_cells), len(owner), "int32"
+    sized = 1 <= C <= (1 << 20)   # beyond the limit the library answers BCS_EINVAL by itself
+    (po, pn, prp, pc, pd, pu, pl), mem = _marshal(
+        (owner, i, F), (neighbour, i, F), (row_ptr, i, C + 1 if sized else None),
+        (col, i, C + 2 * F if sized else None), (pos_diag, i, C if sized else None), (pos_up, i, F),
+        (pos_lo, i, F))
     if mem != BCS_MEM_DEVICE:
         raise ValueError("bcs_ldu_structure_noalloc takes device arrays only")
     buf = ct.create_string_buffer(256)
-    st = lib().bcs_ldu_structure_noalloc(n_cells, len(owner), po, pn, prp, pc, pd, pu, pl,
+    st = lib().bcs_ldu_structure_noalloc(n_cells, F, po, pn, prp, pc, pd, pu, pl,
                                          stream if stream is not None else _current_stream(), buf, 256)
     return st, buf.value.decode()
 
@@ -610,15 +704,21 @@ def bcs_server_create(budget_bytes=0, slots=4, cfg=None):
 
 
 def bcs_server_destroy(h):
+    k = _key(h)
+    for key in [key for key in _dims if isinstance(key, tuple) and key[0] == k]:
+        del _dims[key]
     return lib().bcs_server_destroy(h)
 
 
 def bcs_server_register_case(h, n, n_cells, owner, neighbour):
     owner = np.ascontiguousarray(owner, np.int32)
     neighbour = np.ascontiguousarray(neighbour, np.int32)
+    if owner.size != neighbour.size:
+        raise ValueError("owner and neighbour must have one entry per face")
     cid = ct.c_int()
     _check(lib().bcs_server_register_case(h, n, n_cells, owner.size, owner.ctypes.data, neighbour.ctypes.data,
                                           ct.byref(cid)))
+    _dims[(_key(h), cid.value)] = [int(n), int(n_cells), int(owner.size)]
     return cid.value
 
 
@@ -626,7 +726,13 @@ def bcs_server_submit(h, case_id, diag, upper, lower, b, x):
     """numpy arrays (host) or CUDA tensors (device), all five alike; they must
     stay alive until the request completes."""
     t = ct.c_int64()
-    ptrs, mem = _ptr_mem(diag, upper, lower, b, x)
+    d = _dims.get((_key(h), case_id))
+    if d is None:
+        raise ValueError(f"case {case_id} is not registered with this server")
+    n, C, F = d
+    f = "float64"
+    ptrs, mem = _marshal((diag, f, C * n * n), (upper, f, F * n * n), (lower, f, F * n * n), (b, f, C * n),
+                         (x, f, C * n))
     _check(lib().bcs_server_submit(h, case_id, *ptrs, mem, ct.byref(t)))
     return t.value
 
