@@ -379,11 +379,20 @@ BCS_API bcs_status bcs_server_reset_stats(bcs_server* srv);
  * default stream) and synchronising it before returning. It allocates
  * nothing: its scratch lives in a fixed ~4 MB device array inside the library
  * that every GPU loading the library keeps until the process exits. Limit:
- * n_cells <= 1048576; larger sizes return BCS_EINVAL with a message. The
- * first call on each device looks up that array's device address (do it
- * before any stream capture). All calls share the scratch, so calls that
- * overlap on the GPU race; serialise them. Errors as bcs_set_structure; when
- * err is not NULL, a message of at most errlen bytes is written there. */
+ * n_cells <= 1048576; larger sizes return BCS_EINVAL with a message. Before
+ * any launch every array is checked to be device memory of the current
+ * device (cudaPointerGetAttributes); a host pointer returns BCS_EINVAL with
+ * nothing launched. The call reads one status word back from the device
+ * once, at the end, and waits for the stream there. The first call on each
+ * device, with that device current, looks up the fixed array's device
+ * address and keeps it for the process (make that first call before any
+ * stream capture); the kept address does not survive a reset of the
+ * device's primary context (cudaDeviceReset), so do not call this entry
+ * point after one. All calls share the scratch and it keeps the last call's
+ * contents (the kernels clear what must start at zero), so calls that
+ * overlap on the GPU race; serialise them. Errors as bcs_set_structure
+ * (bad cell ids, owner == neighbour, a repeated face); when err is not NULL,
+ * a message of at most errlen bytes is written there. */
 BCS_API bcs_status bcs_ldu_structure_noalloc(int32_t n_cells, int32_t n_faces, const int32_t* owner,
                                              const int32_t* neighbour, int32_t* row_ptr, int32_t* col,
                                              int32_t* pos_diag, int32_t* pos_up, int32_t* pos_lo,

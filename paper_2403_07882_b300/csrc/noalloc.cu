@@ -31,7 +31,10 @@ static __device__ __align__(256) int32_t g_na_scratch[NA_SCRATCH_INTS];
 
 // Device addresses of g_na_scratch, one per device, filled on the first call
 // made with that device current. In host code the symbol itself is only a
-// host-side stand-in, never a device address.
+// host-side stand-in, never a device address. The cached address belongs to
+// the device's primary context as it stood at that first call: it does not
+// survive a reset of that context (cudaDeviceReset), after which this entry
+// point must not be called again in the same process.
 std::mutex g_na_mutex;
 int32_t* g_na_ptr[256] = {};
 
@@ -123,8 +126,13 @@ __global__ void k_na_scan_add(int C, int32_t* __restrict__ a, const int32_t* __r
   if (i < C) a[i] += tiles[i / NA_TILE];
 }
 
+// The kernels after the face check skip their work when it failed (flag bit
+// 1), so a bad face never indexes the output arrays and the host reads the
+// flag once, at the end.
 __global__ void k_na_place(int C, int F, const int32_t* __restrict__ owner, const int32_t* __restrict__ nb,
-                           const int32_t* __restrict__ rp, int32_t* __restrict__ cursor, int32_t* __restrict__ col) {
+                           const int32_t* __restrict__ rp, int32_t* __restrict__ cursor, int32_t* __restrict__ col,
+                           const int32_t* __restrict__ flag) {
+  if (*flag & 1) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < C) col[rp[t]] = t;
   if (t < F) {
@@ -134,7 +142,8 @@ __global__ void k_na_place(int C, int F, const int32_t* __restrict__ owner, cons
   }
 }
 
-__global__ void k_na_sort(int C, const int32_t* __restrict__ rp, int32_t* __restrict__ col, int32_t* __restrict__ flag) {
+__global__ void k_na_sort(int C, const int32_t* __restrict__ rp, int32_t* __restrict__ col, int32_t* flag) {
+  if (*flag & 1) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= C) return;
   const int b = rp[i], e = rp[i + 1];
@@ -164,7 +173,8 @@ __device__ __forceinline__ int na_find(const int32_t* __restrict__ col, int b, i
 __global__ void k_na_positions(int C, int F, const int32_t* __restrict__ owner, const int32_t* __restrict__ nb,
                                const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                int32_t* __restrict__ pos_diag, int32_t* __restrict__ pos_up,
-                               int32_t* __restrict__ pos_lo) {
+                               int32_t* __restrict__ pos_lo, const int32_t* __restrict__ flag) {
+  if (*flag & 1) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < C) pos_diag[t] = na_find(col, rp[t], rp[t + 1], t);
   if (t < F) {
@@ -206,6 +216,22 @@ extern "C" BCS_API bcs_status bcs_ldu_structure_noalloc(int32_t C, int32_t F, co
   int dev = 0;
   NA_CU(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 256) return na_fail(err, errlen, BCS_EINVAL, "device ordinal out of range");
+  // every array must be device memory of the current device: a host pointer
+  // handed to the kernels would be dereferenced on the GPU
+  {
+    const void* arrays[7] = {owner, neighbour, row_ptr, col, pos_diag, pos_up, pos_lo};
+    for (const void* a : arrays) {
+      if (!a) continue;
+      cudaPointerAttributes at{};
+      const cudaError_t e = cudaPointerGetAttributes(&at, a);
+      if (e != cudaSuccess) {
+        (void)cudaGetLastError();  // clear the error this query leaves behind
+        return na_fail(err, errlen, BCS_EINVAL, "an array is not device memory");
+      }
+      if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+        return na_fail(err, errlen, BCS_EINVAL, "an array is not device memory of the current device");
+    }
+  }
   int32_t* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_na_mutex);
@@ -224,21 +250,20 @@ extern "C" BCS_API bcs_status bcs_ldu_structure_noalloc(int32_t C, int32_t F, co
   const int ntiles = (C + NA_TILE - 1) / NA_TILE;
   k_na_init<<<bcs::grid_for(C, 256), 256, 0, st>>>(C, row_ptr, cursor, flag);
   if (F > 0) k_na_count<<<bcs::grid_for(F, 256), 256, 0, st>>>(C, F, owner, neighbour, row_ptr, flag);
+  k_na_scan_tile<<<ntiles, NA_TILE, 0, st>>>(C, row_ptr, tiles);
+  k_na_scan_tiles<<<1, NA_TILE, 0, st>>>(ntiles, tiles, row_ptr, C);
+  k_na_scan_add<<<bcs::grid_for(C, 256), 256, 0, st>>>(C, row_ptr, tiles);
+  k_na_place<<<bcs::grid_for(CF, 256), 256, 0, st>>>(C, F, owner, neighbour, row_ptr, cursor, col, flag);
+  k_na_sort<<<bcs::grid_for(C, 128), 128, 0, st>>>(C, row_ptr, col, flag);
+  k_na_positions<<<bcs::grid_for(CF, 256), 256, 0, st>>>(C, F, owner, neighbour, row_ptr, col, pos_diag, pos_up,
+                                                          pos_lo, flag);
   NA_CU(cudaGetLastError());
+  // pinned staging of the flag is not available without allocating, so the
+  // read goes to pageable host memory and completes before the sync returns
   int32_t h = 0;
   NA_CU(cudaMemcpyAsync(&h, flag, sizeof(h), cudaMemcpyDeviceToHost, st));
   NA_CU(cudaStreamSynchronize(st));
   if (h & 1) return na_fail(err, errlen, BCS_EINVAL, "face addressing: cell id out of range or owner == neighbour");
-  k_na_scan_tile<<<ntiles, NA_TILE, 0, st>>>(C, row_ptr, tiles);
-  k_na_scan_tiles<<<1, NA_TILE, 0, st>>>(ntiles, tiles, row_ptr, C);
-  k_na_scan_add<<<bcs::grid_for(C, 256), 256, 0, st>>>(C, row_ptr, tiles);
-  k_na_place<<<bcs::grid_for(CF, 256), 256, 0, st>>>(C, F, owner, neighbour, row_ptr, cursor, col);
-  k_na_sort<<<bcs::grid_for(C, 128), 128, 0, st>>>(C, row_ptr, col, flag);
-  k_na_positions<<<bcs::grid_for(CF, 256), 256, 0, st>>>(C, F, owner, neighbour, row_ptr, col, pos_diag, pos_up,
-                                                          pos_lo);
-  NA_CU(cudaGetLastError());
-  NA_CU(cudaMemcpyAsync(&h, flag, sizeof(h), cudaMemcpyDeviceToHost, st));
-  NA_CU(cudaStreamSynchronize(st));
   if (h & 2) return na_fail(err, errlen, BCS_EINVAL, "face addressing: a face (cell pair) is repeated");
   return BCS_OK;
 }

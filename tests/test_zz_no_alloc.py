@@ -8,6 +8,8 @@ test runs two builds in a row (different meshes, the second smaller than the
 first) to show that the leftovers of one call do not leak into the next.
 This file is collected last on purpose.
 """
+import ctypes as ct
+
 import numpy as np
 import pytest
 
@@ -44,6 +46,66 @@ def test_two_calls_in_a_row_match_set_structure():
         got = noalloc_structure(system)
         for key in ("row_ptr", "col", "pos_diag", "pos_up", "pos_lo"):
             assert np.array_equal(got[key], ref[key]), key
+
+
+def random_structure(C, F, seed):
+    """Random simple graph with C cells and about F faces (vectorised draw,
+    repeated pairs dropped), owner < neighbour, faces in random order."""
+    rng = np.random.default_rng(seed)
+    a, b = rng.integers(0, C, F), rng.integers(0, C, F)
+    keep = a != b
+    lo, hi = np.minimum(a[keep], b[keep]), np.maximum(a[keep], b[keep])
+    key = np.unique(lo.astype(np.int64) * C + hi)
+    rng.shuffle(key)
+    return dict(n=1, n_cells=C, n_faces=key.size, owner=(key // C).astype(np.int32),
+                neighbour=(key % C).astype(np.int32))
+
+
+def test_full_limit_matches_set_structure():
+    """Exactly 1048576 cells: 1024 scan tiles, every thread of the tile-sum
+    scan in use and the tile-sum area of the fixed array full."""
+    system = random_structure(1 << 20, 3 << 20, seed=21)
+    ref = reference_structure(system)
+    got = noalloc_structure(system)
+    for key in ("row_ptr", "col", "pos_diag", "pos_up", "pos_lo"):
+        assert np.array_equal(got[key], ref[key]), key
+
+
+def test_repeated_face_rejected():
+    """A face given twice, also with owner and neighbour swapped, is a
+    repeated cell pair: BCS_EINVAL, and the next valid call is unaffected."""
+    i32 = dict(dtype=torch.int32, device=DEV)
+    for owner, nb in (([0, 1, 0], [1, 2, 1]), ([0, 1, 2], [1, 2, 1])):
+        C, F = 3, len(owner)
+        out = [torch.zeros(k, **i32) for k in (C + 1, C + 2 * F, C, F, F)]
+        st, msg = bcs.bcs_ldu_structure_noalloc(C, torch.tensor(owner, **i32), torch.tensor(nb, **i32), *out)
+        assert st == bcs.BCS_EINVAL and "repeated" in msg, msg
+    system = synth.random_graph(150, 400, 2, seed=9)
+    ref = reference_structure(system)
+    got = noalloc_structure(system)
+    assert all(np.array_equal(got[k], ref[k]) for k in ("row_ptr", "col", "pos_diag", "pos_up", "pos_lo"))
+
+
+def test_host_arrays_rejected_through_the_c_abi():
+    """Host (numpy) arrays handed straight to the C entry point are refused
+    with BCS_EINVAL before anything is launched; the outputs stay as they
+    were."""
+    C, F = 4, 3
+    owner = np.array([0, 1, 2], np.int32)
+    nb = np.array([1, 2, 3], np.int32)
+    outs = [np.full(k, -7, np.int32) for k in (C + 1, C + 2 * F, C, F, F)]
+    buf = ct.create_string_buffer(256)
+    st = bcs.lib().bcs_ldu_structure_noalloc(C, F, owner.ctypes.data, nb.ctypes.data,
+                                             *(o.ctypes.data for o in outs), None, buf, 256)
+    assert st == bcs.BCS_EINVAL and "device memory" in buf.value.decode()
+    assert all(np.all(o == -7) for o in outs)
+    # one host array among device arrays is refused too
+    i32 = dict(dtype=torch.int32, device=DEV)
+    dev_outs = [torch.zeros(k, **i32) for k in (C + 1, C + 2 * F, C, F, F)]
+    dev_owner = torch.tensor(owner, **i32)
+    st = bcs.lib().bcs_ldu_structure_noalloc(C, F, dev_owner.data_ptr(), nb.ctypes.data,
+                                             *(o.data_ptr() for o in dev_outs), None, buf, 256)
+    assert st == bcs.BCS_EINVAL
 
 
 def test_rejects_oversize_and_bad_faces():
