@@ -12,16 +12,21 @@ constexpr int RED_THREADS = 256;
 constexpr int MD_CHUNK = 8;      // vectors per multidot block row
 
 // partial[q * RED_BLOCKS + block] = sum over this block's share of i of
-// V[q][i] * w[i], for q = q_base + blockIdx.y * K + (0 .. K-1). K is a
-// compile-time count: FP64 FMAs are scarce on this part, a predicated-off FMA
-// still takes its issue slot on the FP64 pipe, and small K keeps registers
-// (and so occupancy) low.
+// vec(q)[i] * w[i] for q = q0 .. q0 + K - 1, vec(q) = V + q * ldv for
+// q < nv and w itself for q == nv (so ||w||^2 comes out of the same pass).
+// K is a compile-time count: FP64 FMAs are scarce on this part, a
+// predicated-off FMA still takes its issue slot on the FP64 pipe, and small K
+// keeps registers (and so occupancy) low. Every q's sum runs in the same
+// order whatever K is, so results do not depend on how the vectors are
+// grouped into launches.
 template <int K>
-__global__ void __launch_bounds__(RED_THREADS) k_multidot(const double* __restrict__ V, size_t ldv, int q_base,
-                                                          const double* __restrict__ w, size_t N,
-                                                          double* __restrict__ partial) {
+__device__ __forceinline__ void multidot_body(const double* __restrict__ V, size_t ldv, int nv, int q0,
+                                              const double* __restrict__ w, size_t N,
+                                              double* __restrict__ partial) {
   __shared__ double sm[K][RED_THREADS / 32];
-  const int q0 = q_base + blockIdx.y * K;
+  const double* vp[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) vp[q] = q0 + q < nv ? V + (size_t)(q0 + q) * ldv : w;
   double acc[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) acc[q] = 0.0;
@@ -29,7 +34,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_multidot(const double* __restri
   for (size_t i = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; i < N; i += stride) {
     const double wi = __ldg(w + i);
 #pragma unroll
-    for (int q = 0; q < K; ++q) acc[q] = fma(__ldg(V + (size_t)(q0 + q) * ldv + i), wi, acc[q]);
+    for (int q = 0; q < K; ++q) acc[q] = fma(__ldg(vp[q] + i), wi, acc[q]);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -47,11 +52,44 @@ __global__ void __launch_bounds__(RED_THREADS) k_multidot(const double* __restri
   }
 }
 
-// out[q] = sum of the RED_BLOCKS partials of vector q (fixed tree).
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS) k_multidot(const double* __restrict__ V, size_t ldv, int q_base,
+                                                          const double* __restrict__ w, size_t N,
+                                                          double* __restrict__ partial) {
+  multidot_body<K>(V, ldv, 1 << 30, q_base + blockIdx.y * K, w, N, partial);
+}
+
+// The same products for the device-resident FGMRES step: the vectors are
+// V_0 .. V_j (j read from the step state) and, with with_w, w itself; block
+// row y takes vectors 8y .. 8y + 7 of them (fewer in the last row, none past
+// the end), dispatched to the compile-time count.
+__global__ void __launch_bounds__(RED_THREADS) k_multidot_ks(const double* __restrict__ V, size_t ldv,
+                                                             const KrylovState* __restrict__ ks, int with_w,
+                                                             const double* __restrict__ w, size_t N,
+                                                             double* __restrict__ partial) {
+  const int nv = ks->j + 1, k = nv + with_w;
+  const int q0 = blockIdx.y * MD_CHUNK, cnt = min(MD_CHUNK, k - q0);
+  switch (cnt) {
+    case 8: multidot_body<8>(V, ldv, nv, q0, w, N, partial); break;
+    case 7: multidot_body<7>(V, ldv, nv, q0, w, N, partial); break;
+    case 6: multidot_body<6>(V, ldv, nv, q0, w, N, partial); break;
+    case 5: multidot_body<5>(V, ldv, nv, q0, w, N, partial); break;
+    case 4: multidot_body<4>(V, ldv, nv, q0, w, N, partial); break;
+    case 3: multidot_body<3>(V, ldv, nv, q0, w, N, partial); break;
+    case 2: multidot_body<2>(V, ldv, nv, q0, w, N, partial); break;
+    case 1: multidot_body<1>(V, ldv, nv, q0, w, N, partial); break;
+    default: break;
+  }
+}
+
+// out[q] = sum of the RED_BLOCKS partials of vector q (fixed tree); with ks,
+// vectors q >= j + 1 + extra are absent (their blocks return).
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_partials(const double* __restrict__ partial,
-                                                                 double* __restrict__ out) {
+                                                                 double* __restrict__ out,
+                                                                 const KrylovState* __restrict__ ks, int extra) {
   __shared__ double sm[RED_THREADS / 32];
   const int q = blockIdx.x;
+  if (ks && q >= ks->j + 1 + extra) return;
   double v = 0.0;
   for (int b = threadIdx.x; b < RED_BLOCKS; b += RED_THREADS) v += partial[(size_t)q * RED_BLOCKS + b];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -81,6 +119,37 @@ __global__ void k_gs_update(const double* __restrict__ V, size_t ldv, int k, con
     double t = w[i];
     for (int q = 0; q < k; ++q) t = fma(-__ldg(h + q), __ldg(V + (size_t)q * ldv + i), t);
     w[i] = t;
+  }
+}
+
+// The same update (k = j + 1 from the step state when ks is given) on the
+// reduction grid of k_multidot, and, when partial is given, the partial sums
+// of the updated w's squares with k_multidot<1>'s order and tree: the norm of
+// CGS2's second pass without another read of w.
+__global__ void __launch_bounds__(RED_THREADS) k_gs_update_norm(const double* __restrict__ V, size_t ldv, int k_host,
+                                                                const KrylovState* __restrict__ ks,
+                                                                const double* __restrict__ h, double* __restrict__ w,
+                                                                size_t N, double* __restrict__ partial) {
+  const int k = ks ? ks->j + 1 : k_host;
+  double acc = 0.0;
+  const size_t stride = (size_t)RED_BLOCKS * RED_THREADS;
+  for (size_t i = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; i < N; i += stride) {
+    double t = w[i];
+    for (int q = 0; q < k; ++q) t = fma(-__ldg(h + q), __ldg(V + (size_t)q * ldv + i), t);
+    w[i] = t;
+    acc = fma(t, t, acc);
+  }
+  if (!partial) return;
+  __shared__ double sm[RED_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+  if (lane == 0) sm[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int wv = 0; wv < RED_THREADS / 32; ++wv) v += sm[wv];
+    partial[blockIdx.x] = v;
   }
 }
 
@@ -118,6 +187,148 @@ __global__ void k_bicg_p(double beta, double omega, const double* __restrict__ r
     p[i] = r[i] + beta * (p[i] - omega * v[i]);
 }
 
+// ---- device-resident FGMRES cycle (state in KrylovState) -------------------
+// The scalar recurrences below repeat the host loop's operations one by one
+// with explicitly rounded FP64 operations (no fused multiply-add), as the
+// host compiler evaluates them, so both paths give the same bits.
+__global__ void k_ks_init(KrylovState* ks, double beta, double bnorm, int iters, int m, int maxiter, double tol) {
+  const int t = threadIdx.x;
+  for (int i = t; i <= m; i += blockDim.x) ks->g[i] = i == 0 ? beta : 0.0;
+  if (t == 0) {
+    ks->j = 0;
+    ks->iters = iters;
+    ks->stop = KS_RUN;
+    ks->jend = 0;
+    ks->m = m;
+    ks->maxiter = maxiter;
+    ks->tol = tol;
+    ks->bnorm = bnorm;
+    ks->rhn = 0.0;
+  }
+}
+
+// out = V_j (FP32 rounded to nearest, or FP64 copy)
+template <class TO>
+__global__ void k_ks_take_vj(const double* __restrict__ V, size_t ldv, const KrylovState* __restrict__ ks,
+                             TO* __restrict__ out, size_t N) {
+  const double* v = V + (size_t)ks->j * ldv;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (TO)v[i];
+}
+
+// Z_j = z; widen = z in FP64 when given (the outer SpMV's input)
+template <class TZ>
+__global__ void k_ks_store_z(const TZ* __restrict__ z, TZ* __restrict__ Z, const KrylovState* __restrict__ ks,
+                             double* __restrict__ widen, size_t N) {
+  TZ* zj = Z + (size_t)ks->j * N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    const TZ v = z[i];
+    zj[i] = v;
+    if (widen) widen[i] = (double)v;
+  }
+}
+
+// Step j's column of the Hessenberg matrix from the two Gram-Schmidt passes,
+// the previous rotations applied to it, a new rotation that zeroes its
+// subdiagonal entry, and the stop decision: non-finite values (breakdown),
+// h_{j+1,j} <= 1e-14 ||A z_j|| (happy breakdown: no v_{j+1}), the rotated
+// residual |g_{j+1}| <= tol ||b|| or the iteration limit, the end of the
+// cycle. Sets the loop condition of the graph's WHILE node.
+__global__ void k_ks_givens(KrylovState* __restrict__ ks, const double* __restrict__ scal, int slot_a, int slot_b,
+                            int slot_n, cudaGraphConditionalHandle cond, int use_cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int j = ks->j, m = ks->m;
+  double* H = ks->H;
+  const double wn0 = __dsqrt_rn(scal[slot_a + j + 1]);
+  const double hn = __dsqrt_rn(scal[slot_n]);
+  for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = __dadd_rn(scal[slot_a + i], scal[slot_b + i]);
+  H[(size_t)(j + 1) * m + j] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+    H[(size_t)i * m + j] = __dadd_rn(__dmul_rn(ks->cs[i], a), __dmul_rn(ks->sn[i], c));
+    H[(size_t)(i + 1) * m + j] = __dadd_rn(__dmul_rn(-ks->sn[i], a), __dmul_rn(ks->cs[i], c));
+  }
+  const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+  double cj, sj;
+  if (c == 0.0) {
+    cj = 1.0;
+    sj = 0.0;
+  } else {
+    const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(c, c)));
+    cj = __ddiv_rn(a, d);
+    sj = __ddiv_rn(c, d);
+  }
+  ks->cs[j] = cj;
+  ks->sn[j] = sj;
+  H[(size_t)j * m + j] = __dadd_rn(__dmul_rn(cj, a), __dmul_rn(sj, c));
+  H[(size_t)(j + 1) * m + j] = 0.0;
+  const double gj = ks->g[j];
+  const double g1 = __dmul_rn(-sj, gj);
+  ks->g[j + 1] = g1;
+  ks->g[j] = __dmul_rn(cj, gj);
+  const int iters = ks->iters + 1;
+  ks->iters = iters;
+  ks->jend = j + 1;
+  int stop = KS_RUN;
+  if (!isfinite(hn) || !isfinite(g1)) {
+    stop = KS_BREAKDOWN;
+  } else if (!(hn > __dmul_rn(1e-14, wn0))) {
+    stop = KS_HAPPY;
+  } else {
+    ks->rhn = __ddiv_rn(1.0, hn);
+    if (fabs(g1) <= __dmul_rn(ks->tol, ks->bnorm)) stop = KS_CONVERGED;
+    else if (iters >= ks->maxiter) stop = KS_MAXITER;
+    else if (j + 1 >= m) stop = KS_CYCLE_END;
+  }
+  ks->stop = stop;
+  ks->j = j + 1;
+  if (use_cond) cudaGraphSetConditional(cond, stop == KS_RUN ? 1u : 0u);
+}
+
+// V_{j+1} = w / h_{j+1,j} unless the step broke down (j already advanced)
+__global__ void k_ks_scale_next(const KrylovState* __restrict__ ks, const double* __restrict__ w,
+                                double* __restrict__ V, size_t ldv, size_t N) {
+  const int stop = ks->stop;
+  if (stop == KS_HAPPY || stop == KS_BREAKDOWN) return;
+  const double a = ks->rhn;
+  double* v = V + (size_t)ks->j * ldv;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    v[i] = a * w[i];
+}
+
+// y = R^{-1} g over the cycle's jend steps (back substitution)
+__global__ void k_ks_backsolve(KrylovState* __restrict__ ks) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (ks->stop == KS_BREAKDOWN) return;
+  const int jend = ks->jend, m = ks->m;
+  const double* H = ks->H;
+  for (int i = jend - 1; i >= 0; --i) {
+    double t = ks->g[i];
+    for (int k = i + 1; k < jend; ++k) t = __dsub_rn(t, __dmul_rn(H[(size_t)i * m + k], ks->y[k]));
+    ks->y[i] = __ddiv_rn(t, H[(size_t)i * m + i]);
+  }
+}
+
+// x += sum_{q < jend} y_q Z_q (nothing after a breakdown)
+template <class TZ>
+__global__ void k_ks_combine(const TZ* __restrict__ Z, size_t ldz, const KrylovState* __restrict__ ks,
+                             double* __restrict__ x, size_t N) {
+  const int k = ks->stop == KS_BREAKDOWN ? 0 : ks->jend;
+  const double* y = ks->y;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    double t = x[i];
+    for (int q = 0; q < k; ++q) t = fma(y[q], (double)Z[(size_t)q * ldz + i], t);
+    x[i] = t;
+  }
+}
+
+__global__ void k_ks_export(const KrylovState* __restrict__ ks, double* __restrict__ scal) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  scal[0] = (double)ks->iters;
+  scal[1] = (double)ks->jend;
+  scal[2] = (double)ks->stop;
+}
+
 unsigned vgrid(size_t N) {
   unsigned g = grid_for(N, 256);
   return g > 148u * 16u ? 148u * 16u : g;
@@ -144,7 +355,8 @@ bcs_status multidot(Solver* s, const double* V, size_t ldv, int k, const double*
 #undef BCS_MD_TAIL
     default: break;
   }
-  BCS_LAUNCH(s, K_BLAS, 8.0 * k * RED_BLOCKS, 0, k_reduce_partials, k, RED_THREADS, 0, s->red.p, s->scal.p + slot);
+  BCS_LAUNCH(s, K_BLAS, 8.0 * k * RED_BLOCKS, 0, k_reduce_partials, k, RED_THREADS, 0, s->red.p, s->scal.p + slot,
+             (const KrylovState*)nullptr, 0);
   return BCS_OK;
 }
 
@@ -166,6 +378,95 @@ bcs_status fetch_scalars(Solver* s, int count) {
 
 bcs_status gs_update(Solver* s, const double* V, size_t ldv, int k, const double* hdev, double* w, size_t N) {
   BCS_LAUNCH(s, K_BLAS, 8.0 * N * (k + 2), 2.0 * N * k, k_gs_update, vgrid(N), 256, 0, V, ldv, k, hdev, w, N);
+  return BCS_OK;
+}
+
+bcs_status gs_update_norm(Solver* s, const double* V, size_t ldv, int k, const double* hdev, double* w, size_t N,
+                          int slot) {
+  BCS_ALLOC(s, s->red, (size_t)72 * RED_BLOCKS);
+  BCS_LAUNCH(s, K_BLAS, 8.0 * N * (k + 2), 2.0 * N * (k + 1), k_gs_update_norm, RED_BLOCKS, RED_THREADS, 0, V, ldv, k,
+             (const KrylovState*)nullptr, hdev, w, N, s->red.p);
+  BCS_LAUNCH(s, K_BLAS, 8.0 * RED_BLOCKS, 0, k_reduce_partials, 1, RED_THREADS, 0, s->red.p, s->scal.p + slot,
+             (const KrylovState*)nullptr, 0);
+  return BCS_OK;
+}
+
+bcs_status ks_init(Solver* s, KrylovState* ks, double beta, double bnorm, int iters, int m, int maxiter, double tol) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, k_ks_init, 1, 128, 0, ks, beta, bnorm, iters, m, maxiter, tol);
+  return BCS_OK;
+}
+
+bcs_status ks_take_vj(Solver* s, const double* V, size_t ldv, const KrylovState* ks, void* out, bool to_float,
+                      size_t N) {
+  if (to_float)
+    BCS_LAUNCH(s, K_CAST, 12.0 * N, 0, k_ks_take_vj<float>, vgrid(N), 256, 0, V, ldv, ks, (float*)out, N);
+  else
+    BCS_LAUNCH(s, K_BLAS, 16.0 * N, 0, k_ks_take_vj<double>, vgrid(N), 256, 0, V, ldv, ks, (double*)out, N);
+  return BCS_OK;
+}
+
+bcs_status ks_store_z(Solver* s, const void* zsrc, bool z_float, void* Z, const KrylovState* ks, double* widen,
+                      size_t N) {
+  if (z_float)
+    BCS_LAUNCH(s, K_CAST, (12.0 + (widen ? 8.0 : 0.0)) * N, 0, k_ks_store_z<float>, vgrid(N), 256, 0,
+               (const float*)zsrc, (float*)Z, ks, widen, N);
+  else
+    BCS_LAUNCH(s, K_BLAS, (16.0 + (widen ? 8.0 : 0.0)) * N, 0, k_ks_store_z<double>, vgrid(N), 256, 0,
+               (const double*)zsrc, (double*)Z, ks, widen, N);
+  return BCS_OK;
+}
+
+// bytes and flops are counted for the largest step (j = m - 1); the graph's
+// launch statistics use these per step
+bcs_status ks_multidot(Solver* s, const double* V, size_t ldv, const KrylovState* ks, const double* w, bool with_w,
+                       size_t N, int slot) {
+  const int kmax = s->cfg.restart + (with_w ? 1 : 0);
+  if (kmax > 72) return s->fail(BCS_EINVAL, "too many vectors in one multidot");
+  BCS_ALLOC(s, s->red, (size_t)72 * RED_BLOCKS);
+  const unsigned chunks = (unsigned)((kmax + MD_CHUNK - 1) / MD_CHUNK);
+  BCS_LAUNCH(s, K_BLAS, 8.0 * N * (kmax + 1), 2.0 * N * kmax, k_multidot_ks, dim3(RED_BLOCKS, chunks), RED_THREADS, 0,
+             V, ldv, ks, with_w ? 1 : 0, w, N, s->red.p);
+  BCS_LAUNCH(s, K_BLAS, 8.0 * kmax * RED_BLOCKS, 0, k_reduce_partials, kmax, RED_THREADS, 0, s->red.p,
+             s->scal.p + slot, ks, with_w ? 1 : 0);
+  return BCS_OK;
+}
+
+bcs_status ks_gs_update(Solver* s, const double* V, size_t ldv, const KrylovState* ks, const double* hdev, double* w,
+                        size_t N, int norm_slot) {
+  const int kmax = s->cfg.restart;
+  BCS_ALLOC(s, s->red, (size_t)72 * RED_BLOCKS);
+  BCS_LAUNCH(s, K_BLAS, 8.0 * N * (kmax + 2), 2.0 * N * kmax, k_gs_update_norm, RED_BLOCKS, RED_THREADS, 0, V, ldv, 0,
+             ks, hdev, w, N, norm_slot >= 0 ? s->red.p : nullptr);
+  if (norm_slot >= 0)
+    BCS_LAUNCH(s, K_BLAS, 8.0 * RED_BLOCKS, 0, k_reduce_partials, 1, RED_THREADS, 0, s->red.p,
+               s->scal.p + norm_slot, (const KrylovState*)nullptr, 0);
+  return BCS_OK;
+}
+
+bcs_status ks_givens(Solver* s, KrylovState* ks, int slot_a, int slot_b, int slot_n, cudaGraphConditionalHandle cond) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, k_ks_givens, 1, 32, 0, ks, (const double*)s->scal.p, slot_a, slot_b, slot_n, cond, 1);
+  return BCS_OK;
+}
+
+bcs_status ks_scale_next(Solver* s, const KrylovState* ks, const double* w, double* V, size_t ldv, size_t N) {
+  BCS_LAUNCH(s, K_BLAS, 16.0 * N, 1.0 * N, k_ks_scale_next, vgrid(N), 256, 0, ks, w, V, ldv, N);
+  return BCS_OK;
+}
+
+bcs_status ks_finish_cycle(Solver* s, KrylovState* ks, const void* Z, bool z_float, double* x, size_t N) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, k_ks_backsolve, 1, 32, 0, ks);
+  const double k = s->cfg.restart;
+  if (z_float)
+    BCS_LAUNCH(s, K_BLAS, (4.0 * k + 16.0) * N, 2.0 * N * k, k_ks_combine<float>, vgrid(N), 256, 0, (const float*)Z,
+               N, (const KrylovState*)ks, x, N);
+  else
+    BCS_LAUNCH(s, K_BLAS, (8.0 * k + 16.0) * N, 2.0 * N * k, k_ks_combine<double>, vgrid(N), 256, 0,
+               (const double*)Z, N, (const KrylovState*)ks, x, N);
+  return BCS_OK;
+}
+
+bcs_status ks_export(Solver* s, const KrylovState* ks, int slot) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, k_ks_export, 1, 32, 0, ks, s->scal.p + slot);
   return BCS_OK;
 }
 

@@ -1113,6 +1113,21 @@ bcs_status sgs_apply(Solver* s, const double* v, void* z) {
                                : run_sgs<bf16, float, float, float>(s, (const float*)L0.vb.p, (float*)z);
 }
 
+bcs_status precond_cycle64(Solver* s, const double* v, double* z) {
+  return run_cycle<double, double, double, double>(s, v, z);
+}
+
+bcs_status precond_cycle32(Solver* s, const float* v, float* z) {
+  return s->setup_cfg.precision == BCS_PREC_FP32 ? run_cycle_f<float>(s, v, z) : run_cycle_f<bf16>(s, v, z);
+}
+
+bcs_status sgs_fixed(Solver* s, const void* v, void* z) {
+  const int prec = s->setup_cfg.precision;
+  if (prec == BCS_PREC_FP64) return run_sgs<double, double, double, double>(s, (const double*)v, (double*)z);
+  return prec == BCS_PREC_FP32 ? run_sgs<float, float, float, float>(s, (const float*)v, (float*)z)
+                               : run_sgs<bf16, float, float, float>(s, (const float*)v, (float*)z);
+}
+
 // Block-Jacobi preconditioner (one undamped block solve): z = D^-1 v.
 bcs_status jacobi_apply(Solver* s, const double* v, double* z) {
   Level& L0 = s->lv[0];

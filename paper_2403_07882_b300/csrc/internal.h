@@ -156,6 +156,23 @@ struct Level {
   DBuf<char> vd;             // DILU correction vector (cycle precision)
 };
 
+// FGMRES restart cycle kept on the device (restart length m <= KS_MAXM): the
+// Arnoldi step index, the rotated Hessenberg matrix, the Givens rotations,
+// the rotated right-hand side g and the stop decision, so that a cycle runs
+// without reading anything back to the host.
+constexpr int KS_MAXM = 64;
+struct KrylovState {
+  int j;        // Arnoldi step of the cycle being computed
+  int iters;    // iterations of the whole solve so far
+  int stop;     // KS_RUN or why the cycle ended
+  int jend;     // steps completed in this cycle
+  int m, maxiter;
+  double tol, bnorm, rhn;  // rhn = 1 / h_{j+1,j} of the last step
+  double g[KS_MAXM + 1], cs[KS_MAXM], sn[KS_MAXM], y[KS_MAXM];
+  double H[(KS_MAXM + 1) * KS_MAXM];  // row-major, leading dimension m
+};
+enum { KS_RUN = 0, KS_CONVERGED = 1, KS_HAPPY = 2, KS_BREAKDOWN = 3, KS_MAXITER = 4, KS_CYCLE_END = 5 };
+
 struct Timer {
   int kind;
   cudaEvent_t a, b;
@@ -218,9 +235,20 @@ struct Solver {
   cudaStream_t gstream = nullptr;  // private stream the graph is captured on
   long long cyc_kind_launches[BCS_NUM_KERNEL_KINDS] = {};
   double cyc_kind_bytes[BCS_NUM_KERNEL_KINDS] = {}, cyc_kind_flops[BCS_NUM_KERNEL_KINDS] = {};
+  // FGMRES Arnoldi steps replayed as one graph with a device-side loop exit
+  // (a conditional WHILE node); body launches counted per executed step
+  cudaGraphExec_t kry_exec = nullptr;
+  long long kry_kind_launches[BCS_NUM_KERNEL_KINDS] = {};
+  double kry_kind_bytes[BCS_NUM_KERNEL_KINDS] = {}, kry_kind_flops[BCS_NUM_KERNEL_KINDS] = {};
+  DBuf<char> kst;                // KrylovState
+  const void* kry_key[5] = {};    // buffers the captured step uses (recapture when one moves)
+  int kry_m = 0;
+  DBuf<double> kvj, kzj;         // FP64 cycle: fixed input / output of the preconditioner
   void drop_graph() {
     if (cyc_exec) cudaGraphExecDestroy(cyc_exec);
     cyc_exec = nullptr;
+    if (kry_exec) cudaGraphExecDestroy(kry_exec);
+    kry_exec = nullptr;
   }
 
   bcs_status fail(bcs_status st, const std::string& m) {
@@ -332,6 +360,27 @@ bcs_status add_combination(Solver* s, const void* Z, bool z_float, size_t ldz, i
                            const double* ydev, double* x, size_t N);
 bcs_status bicg_p_update(Solver* s, double beta, double omega, const double* r, const double* v,
                          double* p, size_t N);
+// Gram-Schmidt pass 2 fused with the norm: w -= sum_{q<k} h[q] V_q, then
+// scal[slot] = ||w||^2 with the reduction tree of dot() (same bits).
+bcs_status gs_update_norm(Solver* s, const double* V, size_t ldv, int k, const double* hdev, double* w, size_t N,
+                          int slot);
+// Steps of the device-resident FGMRES cycle; ks is the KrylovState in device
+// memory, the step index j is read from it.
+bcs_status ks_init(Solver* s, KrylovState* ks, double beta, double bnorm, int iters, int m, int maxiter,
+                   double tol);
+bcs_status ks_take_vj(Solver* s, const double* V, size_t ldv, const KrylovState* ks, void* out, bool to_float,
+                      size_t N);
+bcs_status ks_store_z(Solver* s, const void* zsrc, bool z_float, void* Z, const KrylovState* ks, double* widen,
+                      size_t N);
+bcs_status ks_multidot(Solver* s, const double* V, size_t ldv, const KrylovState* ks, const double* w, bool with_w,
+                       size_t N, int slot);
+bcs_status ks_gs_update(Solver* s, const double* V, size_t ldv, const KrylovState* ks, const double* hdev, double* w,
+                        size_t N, int norm_slot);
+bcs_status ks_givens(Solver* s, KrylovState* ks, int slot_a, int slot_b, int slot_n,
+                     cudaGraphConditionalHandle cond);
+bcs_status ks_scale_next(Solver* s, const KrylovState* ks, const double* w, double* V, size_t ldv, size_t N);
+bcs_status ks_finish_cycle(Solver* s, KrylovState* ks, const void* Z, bool z_float, double* x, size_t N);
+bcs_status ks_export(Solver* s, const KrylovState* ks, int slot);
 
 // ------------------------------------------------------------------- cycle.cu
 enum Mode { M_SPMV = 0, M_ADD = 1, M_RESID = 2 };
@@ -342,6 +391,12 @@ bcs_status cycle_prepare(Solver* s);
 bcs_status precond_apply(Solver* s, const double* v, void* z);  // z in cycle precision
 bcs_status jacobi_apply(Solver* s, const double* v, double* z);
 bcs_status sgs_apply(Solver* s, const double* v, void* z);  // z in cycle precision
+// The preconditioners between fixed buffers, launched kernel by kernel (for
+// capture into a larger graph): the FP64 V-cycle, the FP32 / BF16 V-cycle on
+// cycle-precision vectors, and the SGS preconditioner (FP64, or FP32 vectors).
+bcs_status precond_cycle64(Solver* s, const double* v, double* z);
+bcs_status precond_cycle32(Solver* s, const float* v, float* z);
+bcs_status sgs_fixed(Solver* s, const void* v, void* z);
 bool cycle_is_float(const Solver* s);
 
 

@@ -2,9 +2,11 @@
 //
 // FGMRES(m): right-preconditioned flexible GMRES (GMRES of Saad & Schultz;
 // flexible because the mixed-precision preconditioner is not a fixed linear
-// operator), classical Gram-Schmidt applied twice, Givens rotations on the
-// host, restart after m steps. A cycle ends when the rotated residual
-// |g_{j+1}| <= tol ||b||; convergence is decided on the true residual
+// operator), classical Gram-Schmidt applied twice, Givens rotations, restart
+// after m steps. With the AMG or SGS preconditioner and graphs enabled, each
+// restart cycle runs on the device (see fgmres below); otherwise the Givens
+// rotations run on the host after one scalar read per step. A cycle ends
+// when the rotated residual |g_{j+1}| <= tol ||b||; convergence is decided on the true residual
 // ||b - A x|| / ||b|| recomputed in FP64 at every cycle end. Happy breakdown
 // when h_{j+1,j} <= 1e-14 ||A z_j||.
 //
@@ -28,6 +30,7 @@ constexpr int SLOT_A = 0;     // first Gram-Schmidt pass
 constexpr int SLOT_B = 72;    // second pass
 constexpr int SLOT_N = 144;   // norms
 constexpr int SLOT_X = 145;   // nonzero flag of the initial guess
+constexpr int SLOT_S = 146;   // device cycle: iterations, steps, stop reason
 
 size_t zbytes(const Solver* s) { return cycle_is_float(s) ? sizeof(float) : sizeof(double); }
 
@@ -87,14 +90,164 @@ bcs_status initial_residual(Solver* s, const double* b, const double* x, double*
   return BCS_OK;
 }
 
+// ---- device-resident restart cycle ------------------------------------------
+// One FGMRES restart cycle without host round trips: the Arnoldi step (the
+// preconditioner on fixed buffers, the outer SpMV into s->kw, both CGS2
+// passes, the Givens update and stop test of k_ks_givens, v_{j+1}) is
+// captured once into the body of a CUDA graph WHILE node, whose condition the
+// Givens kernel clears when the cycle ends (convergence estimate, happy
+// breakdown, breakdown, iteration limit, or m steps). The host then sees one
+// status read per restart cycle (with the true residual) instead of one per
+// iteration. The step index lives in KrylovState, so every replay of the body
+// is the same graph.
+
+// Kinds launched inside the captured step: per-kernel events there would need
+// event nodes, which a conditional body cannot hold.
+constexpr int LOOP_KINDS = (1 << K_SPMV64) | (1 << K_SWEEP) | (1 << K_RESID) | (1 << K_TRANSFER) | (1 << K_COARSE) |
+                           (1 << K_BLAS) | (1 << K_CAST);
+
+bool device_cycle_ok(const Solver* s) {
+  if (s->cfg.cycle_graph == 0) return false;
+  const int pc = s->setup_cfg.precond;
+  if (pc != BCS_PC_AMG && pc != BCS_PC_SGS) return false;
+  if (pc == BCS_PC_AMG && s->lv.empty()) return false;
+  if (s->cfg.profile && (s->cfg.profile_kinds == 0 || (s->cfg.profile_kinds & LOOP_KINDS))) return false;
+  return s->cfg.restart <= KS_MAXM;
+}
+
+// The preconditioner from its fixed input (lv[0].vb in the cycle precision,
+// or s->kvj in FP64) to its fixed output (lv[0].vx, or s->kzj).
+bcs_status apply_M_fixed(Solver* s) {
+  Level& L0 = s->lv[0];
+  const int pc = s->setup_cfg.precond, prec = s->setup_cfg.precision;
+  if (prec == BCS_PREC_FP64) {
+    if (pc == BCS_PC_AMG) return precond_cycle64(s, s->kvj.p, s->kzj.p);
+    return sgs_fixed(s, s->kvj.p, s->kzj.p);
+  }
+  if (pc == BCS_PC_AMG) return precond_cycle32(s, (const float*)L0.vb.p, (float*)L0.vx.p);
+  return sgs_fixed(s, L0.vb.p, L0.vx.p);
+}
+
+// One Arnoldi step of the device-resident cycle (the body of the WHILE node).
+bcs_status arnoldi_step_dev(Solver* s, KrylovState* ks, cudaGraphConditionalHandle cond) {
+  const size_t N = (size_t)s->C * s->n;
+  const bool zf = cycle_is_float(s);
+  double* V = s->kv.p;
+  double* w = s->kw.p;
+  BCS_OKR(ks_take_vj(s, V, N, ks, zf ? (void*)s->lv[0].vb.p : (void*)s->kvj.p, zf, N));
+  BCS_OKR(apply_M_fixed(s));
+  BCS_OKR(ks_store_z(s, zf ? (const void*)s->lv[0].vx.p : (const void*)s->kzj.p, zf, s->kz.p, ks,
+                     zf ? s->kt.p : nullptr, N));
+  BCS_OKR(spmv64(s, s->lv[0].A, zf ? (const void*)s->kt.p : (const void*)s->kzj.p, false, w, nullptr, K_SPMV64));
+  BCS_OKR(ks_multidot(s, V, N, ks, w, true, N, SLOT_A));
+  BCS_OKR(ks_gs_update(s, V, N, ks, s->scal.p + SLOT_A, w, N, -1));
+  BCS_OKR(ks_multidot(s, V, N, ks, w, false, N, SLOT_B));
+  BCS_OKR(ks_gs_update(s, V, N, ks, s->scal.p + SLOT_B, w, N, SLOT_N));
+  BCS_OKR(ks_givens(s, ks, SLOT_A, SLOT_B, SLOT_N, cond));
+  return ks_scale_next(s, ks, w, V, N, N);
+}
+
+// Builds (once per set of buffers) the executable graph: a WHILE node whose
+// body is one captured Arnoldi step. Its launches are counted per executed
+// step (kry_kind_*).
+bcs_status capture_cycle(Solver* s, KrylovState* ks) {
+  long long kl[BCS_NUM_KERNEL_KINDS];
+  double kb[BCS_NUM_KERNEL_KINDS], kf[BCS_NUM_KERNEL_KINDS];
+  const long long l0 = s->launches;
+  for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {
+    kl[k] = s->kind_launches[k];
+    kb[k] = s->kind_bytes[k];
+    kf[k] = s->kind_flops[k];
+  }
+  if (!s->gstream) BCS_CU(s, cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  BCS_CU(s, cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle cond = 0;
+  cudaGraphNode_t node = nullptr;
+  cudaGraphNodeParams prm{};
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = cond;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &prm);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return s->fail(BCS_ECUDA, std::string("conditional graph node: ") + cudaGetErrorString(e));
+  }
+  cudaGraph_t body = prm.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(s->gstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return s->fail(BCS_ECUDA, std::string("capture into the loop body: ") + cudaGetErrorString(e));
+  }
+  const cudaStream_t own = s->stream;
+  s->stream = s->gstream;
+  const bcs_status st = arnoldi_step_dev(s, ks, cond);
+  s->stream = own;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(s->gstream, &captured);
+  s->launches = l0;
+  for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {
+    s->kry_kind_launches[k] = s->kind_launches[k] - kl[k];
+    s->kry_kind_bytes[k] = s->kind_bytes[k] - kb[k];
+    s->kry_kind_flops[k] = s->kind_flops[k] - kf[k];
+    s->kind_launches[k] = kl[k];
+    s->kind_bytes[k] = kb[k];
+    s->kind_flops[k] = kf[k];
+  }
+  if (st != BCS_OK || ce != cudaSuccess) {
+    cudaGraphDestroy(g);
+    if (st != BCS_OK) return st;
+    return s->fail(BCS_ECUDA, std::string("loop body capture: ") + cudaGetErrorString(ce));
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&s->kry_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    s->kry_exec = nullptr;
+    return s->fail(BCS_ECUDA, std::string("loop graph instantiate: ") + cudaGetErrorString(ie));
+  }
+  return BCS_OK;
+}
+
+// The launches of `steps` executed loop bodies, added to the statistics.
+void count_steps(Solver* s, int steps) {
+  for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {
+    s->launches += s->kry_kind_launches[k] * steps;
+    s->kind_launches[k] += s->kry_kind_launches[k] * steps;
+    s->kind_bytes[k] += s->kry_kind_bytes[k] * steps;
+    s->kind_flops[k] += s->kry_kind_flops[k] * steps;
+  }
+}
+
 bcs_status fgmres(Solver* s, const double* b, double* x, bcs_result* res) {
   const bcs_config& cfg = s->cfg;
   const int m = cfg.restart;
   const size_t N = (size_t)s->C * s->n;
   const bool zf = cycle_is_float(s);
+  const bool dev = device_cycle_ok(s);
   BCS_ALLOC(s, s->kv, (size_t)(m + 1) * N);
   BCS_ALLOC(s, s->kz, (size_t)m * N * zbytes(s));
   BCS_ALLOC(s, s->kr, N);
+  if (dev) {
+    // everything the captured step touches exists before the capture
+    BCS_ALLOC(s, s->kw, N);
+    BCS_ALLOC(s, s->kst, sizeof(KrylovState));
+    BCS_ALLOC(s, s->red, (size_t)72 * 1184);
+    if (zf) BCS_ALLOC(s, s->kt, N);
+    else {
+      BCS_ALLOC(s, s->kvj, N);
+      BCS_ALLOC(s, s->kzj, N);
+    }
+    if (s->kry_exec && (s->kry_key[0] != (const void*)s->kv.p || s->kry_key[1] != (const void*)s->kz.p ||
+                        s->kry_key[2] != (const void*)s->kw.p || s->kry_key[3] != (const void*)s->kt.p ||
+                        s->kry_key[4] != (const void*)s->kvj.p || s->kry_m != m)) {
+      cudaGraphExecDestroy(s->kry_exec);
+      s->kry_exec = nullptr;
+    }
+  }
   double* V = s->kv.p;
   char* Z = s->kz.p;
   double* r = s->kr.p;
@@ -113,64 +266,90 @@ bcs_status fgmres(Solver* s, const double* b, double* x, bcs_result* res) {
   std::vector<double> H((size_t)(m + 1) * m, 0.0), g(m + 1), cs(m), sn(m), y(m);
   int iters = 0;
   bcs_status status = BCS_OK;
+  KrylovState* ks = reinterpret_cast<KrylovState*>(s->kst.p);
   for (;;) {
     BCS_OKR(scale_copy(s, 1.0 / beta, r, V, N));
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    int jend = 0;
     bool breakdown = false;
-    for (int j = 0; j < m; ++j) {
-      double* w = V + (size_t)(j + 1) * N;
-      void* zj = Z + (size_t)j * N * zbytes(s);
-      BCS_OKR(apply_M(s, V + (size_t)j * N, zj, N));
-      BCS_OKR(apply_A(s, zj, w, N));
-      // pass 1 also yields ||w||^2 (w is vector j+1 of V)
-      BCS_OKR(multidot(s, V, N, j + 2, w, N, SLOT_A));
-      BCS_OKR(gs_update(s, V, N, j + 1, s->scal.p + SLOT_A, w, N));
-      BCS_OKR(multidot(s, V, N, j + 1, w, N, SLOT_B));
-      BCS_OKR(gs_update(s, V, N, j + 1, s->scal.p + SLOT_B, w, N));
-      BCS_OKR(dot(s, w, w, N, SLOT_N));
-      BCS_OKR(fetch_scalars(s, SLOT_N + 1));
-      const double* hs = s->hscal;
-      const double wn0 = std::sqrt(hs[SLOT_A + j + 1]);
-      const double hn = std::sqrt(hs[SLOT_N]);
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hs[SLOT_A + i] + hs[SLOT_B + i];
-      H[(size_t)(j + 1) * m + j] = hn;
-      for (int i = 0; i < j; ++i) {
-        const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
-        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+    if (dev) {
+      BCS_OKR(ks_init(s, ks, beta, bnorm, iters, m, cfg.maxiter, cfg.tol));
+      if (!s->kry_exec) {
+        BCS_OKR(capture_cycle(s, ks));
+        s->kry_key[0] = s->kv.p;
+        s->kry_key[1] = s->kz.p;
+        s->kry_key[2] = s->kw.p;
+        s->kry_key[3] = s->kt.p;
+        s->kry_key[4] = s->kvj.p;
+        s->kry_m = m;
       }
-      const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
-      if (c == 0.0) {
-        cs[j] = 1.0;
-        sn[j] = 0.0;
-      } else {
-        const double d = std::sqrt(a * a + c * c);
-        cs[j] = a / d;
-        sn[j] = c / d;
+      BCS_CU(s, cudaGraphLaunch(s->kry_exec, s->stream));
+      BCS_OKR(ks_finish_cycle(s, ks, Z, zf, x, N));
+      // true residual, its norm and the cycle's outcome in one read
+      BCS_OKR(spmv64(s, s->lv[0].A, x, false, r, b, K_SPMV64));
+      BCS_OKR(dot(s, r, r, N, SLOT_N));
+      BCS_OKR(ks_export(s, ks, SLOT_S));
+      BCS_OKR(fetch_scalars(s, SLOT_S + 3));
+      const int it_now = (int)s->hscal[SLOT_S];
+      count_steps(s, it_now - iters);
+      iters = it_now;
+      breakdown = (int)s->hscal[SLOT_S + 2] == KS_BREAKDOWN;
+      beta = std::sqrt(s->hscal[SLOT_N]);
+    } else {
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int jend = 0;
+      for (int j = 0; j < m; ++j) {
+        double* w = V + (size_t)(j + 1) * N;
+        void* zj = Z + (size_t)j * N * zbytes(s);
+        BCS_OKR(apply_M(s, V + (size_t)j * N, zj, N));
+        BCS_OKR(apply_A(s, zj, w, N));
+        // pass 1 also yields ||w||^2 (w is vector j+1 of V); pass 2's
+        // update also yields the new ||w||^2
+        BCS_OKR(multidot(s, V, N, j + 2, w, N, SLOT_A));
+        BCS_OKR(gs_update(s, V, N, j + 1, s->scal.p + SLOT_A, w, N));
+        BCS_OKR(multidot(s, V, N, j + 1, w, N, SLOT_B));
+        BCS_OKR(gs_update_norm(s, V, N, j + 1, s->scal.p + SLOT_B, w, N, SLOT_N));
+        BCS_OKR(fetch_scalars(s, SLOT_N + 1));
+        const double* hs = s->hscal;
+        const double wn0 = std::sqrt(hs[SLOT_A + j + 1]);
+        const double hn = std::sqrt(hs[SLOT_N]);
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hs[SLOT_A + i] + hs[SLOT_B + i];
+        H[(size_t)(j + 1) * m + j] = hn;
+        for (int i = 0; i < j; ++i) {
+          const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+          H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+          H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+        }
+        const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+        if (c == 0.0) {
+          cs[j] = 1.0;
+          sn[j] = 0.0;
+        } else {
+          const double d = std::sqrt(a * a + c * c);
+          cs[j] = a / d;
+          sn[j] = c / d;
+        }
+        H[(size_t)j * m + j] = cs[j] * a + sn[j] * c;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        ++iters;
+        jend = j + 1;
+        if (!std::isfinite(hn) || !std::isfinite(g[j + 1])) {
+          breakdown = true;
+          break;
+        }
+        if (!(hn > 1e-14 * wn0)) break;  // happy breakdown: no v_{j+1}
+        BCS_OKR(scale_copy(s, 1.0 / hn, w, w, N));
+        if (std::fabs(g[j + 1]) <= cfg.tol * bnorm || iters >= cfg.maxiter) break;
       }
-      H[(size_t)j * m + j] = cs[j] * a + sn[j] * c;
-      H[(size_t)(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      ++iters;
-      jend = j + 1;
-      if (!std::isfinite(hn) || !std::isfinite(g[j + 1])) {
-        breakdown = true;
-        break;
+      for (int i = jend - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int k = i + 1; k < jend; ++k) t -= H[(size_t)i * m + k] * y[k];
+        y[i] = t / H[(size_t)i * m + i];
       }
-      if (!(hn > 1e-14 * wn0)) break;  // happy breakdown: no v_{j+1}
-      BCS_OKR(scale_copy(s, 1.0 / hn, w, w, N));
-      if (std::fabs(g[j + 1]) <= cfg.tol * bnorm || iters >= cfg.maxiter) break;
+      if (!breakdown) BCS_OKR(add_combination(s, Z, zf, N, jend, y.data(), x, N));
+      BCS_OKR(true_residual(s, b, x, r, N, &beta));
     }
-    for (int i = jend - 1; i >= 0; --i) {
-      double t = g[i];
-      for (int k = i + 1; k < jend; ++k) t -= H[(size_t)i * m + k] * y[k];
-      y[i] = t / H[(size_t)i * m + i];
-    }
-    if (!breakdown) BCS_OKR(add_combination(s, Z, zf, N, jend, y.data(), x, N));
-    BCS_OKR(true_residual(s, b, x, r, N, &beta));
     res->rel_res_final = beta / bnorm;
     if (breakdown || !std::isfinite(beta)) {
       status = BCS_BREAKDOWN;
