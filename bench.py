@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--side", type=int, default=SIDE)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-full", action="store_true",
+                   help="also run the oracle (OpenMP build) on the full-size system once (minutes, ~20 GB host memory)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison run")
     p.add_argument("--no-assembly", action="store_true", help="skip the density-based assembly measurement")
@@ -170,26 +172,105 @@ def measured_traffic(kernel, bytes_per_launch):
 
 
 # --------------------------------------------------------------- CPU (oracle)
+def host_info():
+    """Host CPU model name and the number of usable cores."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "nproc": len(os.sched_getaffinity(0))}
+
+
+def oracle_run(system, omp=False):
+    """One oracle time-to-solution (LDU -> BSR, AMG setup, FGMRES(30) + AMG
+    to 1e-8 from x0 = 0): (times in ms, x, result dict). omp selects the
+    OpenMP build of the same source (identical results)."""
+    import oracle
+    oracle.use_openmp(omp)
+    try:
+        t0 = time.perf_counter()
+        ref = oracle.ldu_to_bsr(system)
+        amg = oracle.Amg(ref, oracle.config())
+        t1 = time.perf_counter()
+        x, res, _ = oracle.solve(ref, system["b"], cfg=oracle.config(), amg=amg)
+        t2 = time.perf_counter()
+    finally:
+        oracle.use_openmp(False)
+    return {"setup_ms": (t1 - t0) * 1e3, "solve_ms": (t2 - t1) * 1e3, "total_ms": (t2 - t0) * 1e3}, x, res
+
+
 def oracle_sample(side=SAMPLE_SIDE):
     """Oracle time-to-solution on the same generator at side^3, in ms."""
-    import oracle
     from paper_2403_07882_b300 import synth
-    system = synth.density(side, seed=2)
-    t0 = time.perf_counter()
+    t, _, res = oracle_run(synth.density(side, seed=2))
+    return t["total_ms"], res
+
+
+def gpu_error_arms(system, x_ref, dev):
+    """Each GPU arm of the benchmark on `system`, solved to 1e-8 from x0 = 0:
+    ||x - x_oracle|| / ||x_oracle|| and the true relative residual recomputed
+    with the oracle's FP64 SpMV."""
+    import torch
+    import oracle
+    from paper_2403_07882_b300 import bcs
     ref = oracle.ldu_to_bsr(system)
-    amg = oracle.Amg(ref, oracle.config())
-    x, res, _ = oracle.solve(ref, system["b"], cfg=oracle.config(), amg=amg)
-    ms = (time.perf_counter() - t0) * 1e3
-    return ms, res
+    arms = {"mixed_fp32_amg": dict(precision=bcs.BCS_PREC_FP32),
+            "fp64_amg": dict(precision=bcs.BCS_PREC_FP64),
+            "bf16_amg": dict(precision=bcs.BCS_PREC_BF16),
+            "dilu_fp32": dict(precision=bcs.BCS_PREC_FP32, smoother=bcs.BCS_SMOOTH_DILU),
+            "sgs_fp32_no_amg": dict(precision=bcs.BCS_PREC_FP32, precond=bcs.BCS_PC_SGS, maxiter=5000)}
+    bn = np.linalg.norm(system["b"])
+    out = {}
+    for name, cfg in arms.items():
+        with bcs.Solver(system["n"], **cfg) as s:
+            s.load(system, device=dev)
+            x, st, res = s.solve(torch.from_numpy(system["b"]).to(dev))
+            x = x.cpu().numpy()
+        out[name] = {"status": st, "iters": res["iters"],
+                     "rel_err_x_vs_oracle": float(np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref)),
+                     "rel_res_true": float(np.linalg.norm(system["b"] - oracle.spmv(ref, x)) / bn)}
+    return out
 
 
-def cpu_baseline_entry(side):
-    ms, res = oracle_sample()
+def cpu_baseline_entry(side, dev=None, full=False):
+    """The oracle on the host cores: single-threaded (the baseline value) and
+    its OpenMP build on every core, both on the same generator at 64^3,
+    their time scaled to side^3 by cell count (a model: the same iteration
+    count and a setup linear in the cells); with full=True also measured at
+    side^3 itself (minutes). With dev, every GPU arm is solved on the 64^3
+    system and compared with the oracle's solution."""
+    from paper_2403_07882_b300 import synth
+    system = synth.density(SAMPLE_SIDE, seed=2)
     scale = (side / SAMPLE_SIDE) ** 3
-    return {"value": ms * scale, "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"full oracle solve (LDU->BSR, AMG setup, FGMRES(30)+AMG to 1e-8, {res['iters']} iterations) "
-                      f"of the same generator at {SAMPLE_SIDE}^3 = 1/{scale:.0f} of the cells, "
-                      f"{ms / 1e3:.1f} s single-threaded, scaled x{scale:.0f} by cell count"}
+    t1, x_ref, res = oracle_run(system)
+    tn, x_omp, res_omp = oracle_run(system, omp=True)
+    host = host_info()
+    entry = {"value": t1["total_ms"] * scale, "unit": "ms", "cores": 1, "kind": "oracle", "modelled": True,
+             "sample": f"full oracle solve (LDU->BSR, AMG setup, FGMRES(30)+AMG to 1e-8, {res['iters']} iterations) "
+                       f"of the same generator at {SAMPLE_SIDE}^3 = 1/{scale:.0f} of the cells, "
+                       f"{t1['total_ms'] / 1e3:.1f} s single-threaded; value = that time x{scale:.0f} by cell count "
+                       f"(modelled, not measured at {side}^3)",
+             "host": host,
+             "measured_sample": dict(side=SAMPLE_SIDE, iters=res["iters"], **t1),
+             "oracle_omp": dict(cores=host["nproc"], value=tn["total_ms"] * scale, modelled=True,
+                                identical_to_single_thread=bool(np.array_equal(x_ref, x_omp)),
+                                parallel_part="row loops of the SpMV and the smoother sweeps, element-wise vector "
+                                              "updates; the AMG setup and the dot products stay serial",
+                                measured_sample=dict(side=SAMPLE_SIDE, iters=res_omp["iters"], **tn))}
+    if full:
+        big = synth.density(side, seed=2)
+        tf, _, rf = oracle_run(big, omp=True)
+        entry["full_size_omp"] = dict(side=side, cores=host["nproc"], iters=rf["iters"],
+                                      rel_res_final=rf["rel_res_final"], **tf)
+    if dev is not None:
+        entry["gpu_error_vs_oracle"] = {"system": f"density-based {SAMPLE_SIDE}^3, seed 2 (the sample above)",
+                                        "arms": gpu_error_arms(system, x_ref, dev)}
+    return entry
 
 
 def run_reference(args):
@@ -209,10 +290,11 @@ def run_reference(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "solver": "FGMRES(30) + aggregation AMG, FP64 oracle"},
-            "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle", "modelled": True,
+                             "host": host_info(),
                              "sample": f"each step: full oracle solve of the same generator at {SAMPLE_SIDE}^3 "
                                        f"(1/{scale:.0f} of the cells, {res['iters']} iterations), "
-                                       f"scaled x{scale:.0f} by cell count"},
+                                       f"scaled x{scale:.0f} by cell count (modelled, not measured at full size)"},
             "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -375,7 +457,7 @@ def run_native(args):
         "packing": packing,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_entry(args.side)
+        line["cpu_baseline"] = cpu_baseline_entry(args.side, dev=dev, full=args.cpu_full)
     print(json.dumps(line), flush=True)
 
 

@@ -36,25 +36,44 @@ class Result(ct.Structure):
                 ("levels", ct.c_int)]
 
 
-def build(force=False):
-    """Compile liboracle.so (plain C++17, no implicit FMA contraction)."""
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
+_SO_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def build(force=False, omp=False):
+    """Compile liboracle.so (plain C++17, no implicit FMA contraction,
+    single-threaded), or with omp=True liboracle_omp.so: the same source
+    with its OpenMP pragmas enabled. Those sit only on loops whose
+    iterations write disjoint outputs (the row loops of the SpMV and the
+    sweeps, element-wise vector updates); no reduction is split, so both
+    builds give identical results."""
+    so = _SO_OMP if omp else _SO
+    if not force and os.path.exists(so) and os.path.getmtime(so) >= max(
             [os.path.getmtime(p) for p in _SRCS] + [os.path.getmtime(os.path.join(_HERE, "oracle.h"))]):
-        return _SO
+        return so
     cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", _SO] + _SRCS
+           "-shared"] + (["-fopenmp"] if omp else []) + ["-o", so] + _SRCS
     subprocess.check_call(cmd)
-    return _SO
+    return so
 
 
 _lib = None
+_omp = False
+
+
+def use_openmp(flag=True):
+    """Switch this process to the OpenMP build (all host cores) or back to
+    the single-threaded one; takes effect at the next call."""
+    global _lib, _omp
+    if bool(flag) != _omp:
+        _omp = bool(flag)
+        _lib = None
 
 
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = ct.CDLL(_SO)
+        so = build(omp=_omp)
+        L = ct.CDLL(so)
         L.or_config_default.argtypes = [ct.POINTER(Config)]
         L.or_ldu_check.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p]
         L.or_ldu_structure.argtypes = [ct.c_int, ct.c_int, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p]

@@ -140,6 +140,7 @@ void or_bsr_to_ldu(int C, int F, int n, const int32_t* pos_diag, const int32_t* 
 void or_bsr_spmv(int rows, int n, const int32_t* rp, const int32_t* ci, const double* val,
                  const double* x, double* y) {
   size_t nn = (size_t)n * n;
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < rows; ++i)
     for (int r = 0; r < n; ++r) {
       double acc = 0.0;
@@ -832,7 +833,9 @@ void jacobi_sweep(const Bsr& A, const std::vector<double>& dinv, double omega, c
   const int n = A.n, nn = n * n;
   std::vector<double> r((size_t)A.rows * n);
   or_bsr_spmv(A.rows, n, A.rp.data(), A.ci.data(), A.v.data(), x.data(), r.data());
+#pragma omp parallel for schedule(static)
   for (size_t e = 0; e < r.size(); ++e) r[e] = b[e] - r[e];
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < A.rows; ++i)
     for (int a = 0; a < n; ++a) {
       double t = 0.0;
@@ -885,6 +888,7 @@ void vcycle(const or_amg* h, int l, const double* b, std::vector<double>& x) {
     return;
   }
   if (L.coarse_kind == 0) {
+#pragma omp parallel for schedule(static)
     for (int r = 0; r < N; ++r) {
       double t = 0.0;
       for (int c = 0; c < N; ++c) t += h->cinv[(size_t)r * N + c] * b[c];
@@ -897,6 +901,7 @@ void vcycle(const or_amg* h, int l, const double* b, std::vector<double>& x) {
     return;
   }
   if (h->cfg.nu1 >= 1) {
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < L.A.rows; ++i)
       for (int a = 0; a < n; ++a) {
         double t = 0.0;
@@ -907,11 +912,13 @@ void vcycle(const or_amg* h, int l, const double* b, std::vector<double>& x) {
   }
   std::vector<double> r(N), bc((size_t)L.P.cols * n), xc;
   or_bsr_spmv(L.A.rows, n, L.A.rp.data(), L.A.ci.data(), L.A.v.data(), x.data(), r.data());
+#pragma omp parallel for schedule(static)
   for (int e = 0; e < N; ++e) r[e] = b[e] - r[e];
   or_bsr_spmv(L.R.rows, n, L.R.rp.data(), L.R.ci.data(), L.R.v.data(), r.data(), bc.data());
   vcycle(h, l + 1, bc.data(), xc);
   std::vector<double> px(N);
   or_bsr_spmv(L.P.rows, n, L.P.rp.data(), L.P.ci.data(), L.P.v.data(), xc.data(), px.data());
+#pragma omp parallel for schedule(static)
   for (int e = 0; e < N; ++e) x[e] = x[e] + px[e];
   for (int s = 0; s < h->cfg.nu2; ++s) jacobi_sweep(L.A, L.dinv, om, b, x);
 }
@@ -974,6 +981,7 @@ void precond(const Sys& S, const std::vector<double>& v, std::vector<double>& z)
     dilu_apply(S.A, S.colour, S.ncol, S.dinv, v.data(), z.data());
   } else if (S.cfg->precond == 2 || S.cfg->precond == 3) {
     const int n = S.n, nn = n * n;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < S.rows; ++i)
       for (int a = 0; a < n; ++a) {
         double t = 0.0;
@@ -988,6 +996,7 @@ void precond(const Sys& S, const std::vector<double>& v, std::vector<double>& z)
 void true_residual(const Sys& S, const double* b, const std::vector<double>& x,
                    std::vector<double>& r) {
   matvec(S, x, r);
+#pragma omp parallel for schedule(static)
   for (int e = 0; e < S.N; ++e) r[e] = b[e] - r[e];
 }
 
@@ -1003,6 +1012,7 @@ int arnoldi_step(const Sys& S, std::vector<std::vector<double>>& V,
   for (int pass = 0; pass < 2; ++pass) {
     std::vector<double> c(j + 1);
     for (int i = 0; i <= j; ++i) c[i] = dot(V[i], w);
+#pragma omp parallel for schedule(static)
     for (int e = 0; e < S.N; ++e) {
       double t = w[e];
       for (int i = 0; i <= j; ++i) t -= c[i] * V[i][e];
@@ -1014,6 +1024,7 @@ int arnoldi_step(const Sys& S, std::vector<std::vector<double>>& V,
   h[j + 1] = hn;
   if (!(hn > 1e-14 * wn0)) return 1;
   V[j + 1].resize(S.N);
+#pragma omp parallel for schedule(static)
   for (int e = 0; e < S.N; ++e) V[j + 1][e] = w[e] / hn;
   return 0;
 }
@@ -1039,6 +1050,7 @@ int fgmres(const Sys& S, const double* b, double* x0, or_result* res, double* hi
   std::vector<double> H((size_t)(m + 1) * m, 0.0), g(m + 1), cs(m), sn(m), h;
   for (;;) {
     V[0].resize(N);
+#pragma omp parallel for schedule(static)
     for (int e = 0; e < N; ++e) V[0][e] = r[e] / beta;
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
@@ -1074,6 +1086,7 @@ int fgmres(const Sys& S, const double* b, double* x0, or_result* res, double* hi
       for (int k = i + 1; k < jend; ++k) t -= H[(size_t)i * m + k] * y[k];
       y[i] = t / H[(size_t)i * m + i];
     }
+#pragma omp parallel for schedule(static)
     for (int e = 0; e < N; ++e) {
       double t = x[e];
       for (int j = 0; j < jend; ++j) t += y[j] * Z[j][e];
@@ -1149,6 +1162,7 @@ int bicgstab(const Sys& S, const double* b, double* x0, or_result* res, double* 
     if (first) p = r;
     else {
       double beta = (rho / rho_old) * (alpha / omega);
+#pragma omp parallel for schedule(static)
       for (int e = 0; e < N; ++e) p[e] = r[e] + beta * (p[e] - omega * v[e]);
     }
     first = false;
@@ -1160,6 +1174,7 @@ int bicgstab(const Sys& S, const double* b, double* x0, or_result* res, double* 
       continue;
     }
     alpha = rho / den;
+#pragma omp parallel for schedule(static)
     for (int e = 0; e < N; ++e) s[e] = r[e] - alpha * v[e];
     ++it;
     double sn = nrm2(s);
@@ -1180,6 +1195,7 @@ int bicgstab(const Sys& S, const double* b, double* x0, or_result* res, double* 
       continue;
     }
     omega = dot(t, s) / tt;
+#pragma omp parallel for schedule(static)
     for (int e = 0; e < N; ++e) {
       x[e] = x[e] + alpha * ph[e] + omega * sh[e];
       r[e] = s[e] - omega * t[e];

@@ -257,6 +257,11 @@ bcs_status bcs_destroy(bcs_solver* h) {
   cudaStreamSynchronize(s->stream);
   s->drop_graph();
   if (s->gstream) cudaStreamDestroy(s->gstream);
+  if (s->cstream) {
+    cudaStreamSynchronize(s->cstream);
+    cudaStreamDestroy(s->cstream);
+  }
+  for (cudaEvent_t e : s->copy_events) cudaEventDestroy(e);
   for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
   if (s->hscal) cudaFreeHost(s->hscal);
   cudaStream_t st = s->stream;
@@ -323,12 +328,11 @@ bcs_status bcs_set_values(bcs_solver* h, const double* diag, const double* upper
   if (!diag || (s->F > 0 && (!upper || !lower)) || (mem != BCS_MEM_HOST && mem != BCS_MEM_DEVICE))
     return s->fail(BCS_EINVAL, "invalid value arguments");
   const auto t0 = std::chrono::steady_clock::now();
-  const size_t nn = (size_t)s->n * s->n;
-  const double *d = nullptr, *u = nullptr, *l = nullptr;
-  BCS_OKR(stage(s, diag, s->C * nn, mem, s->stage_d, &d));
-  BCS_OKR(stage(s, upper, s->F * nn, mem, s->stage_u, &u));
-  BCS_OKR(stage(s, lower, s->F * nn, mem, s->stage_l, &l));
-  BCS_OKR(permute_values(s, d, u, l));
+  if (mem == BCS_MEM_HOST) {
+    BCS_OKR(upload_values(s, diag, upper, lower));
+    return values_changed(s, t0);
+  }
+  BCS_OKR(permute_values(s, diag, upper, lower));
   return values_changed(s, t0);
 }
 

@@ -13,6 +13,7 @@
 // first from x = 0 is x = w D^-1 b), residual, restriction R = P^T,
 // recursion, prolongation-correction, nu2 sweeps; the coarsest level applies
 // its dense FP64 inverse (or smoother sweeps when too large for one).
+#include <algorithm>
 #include <array>
 #include <map>
 #include <mutex>
@@ -819,33 +820,37 @@ bcs_status run_cycle(Solver* s, const TC* b, TC* x) {
 
 // Sliced copy of level L's operator in layout `map` and the cycle precision
 // (structure once per hierarchy and layout, values at every setup / resetup).
-bcs_status fill_layout(Solver* s, Level& L, int prec, int map) {
+// Structure of layout `map` for level L (slice order and lengths, their
+// scan): launched only; the step count is copied to *steps_dev for the
+// caller to read. False in *needed when L already has that structure.
+bcs_status layout_structure(Solver* s, Level& L, int map, int32_t* steps_dev, bool* needed) {
   const int n = s->n, rows = L.A.rows, rpw = map == 1 ? 32 : 32 / n;
-  if (L.nslices == 0 || L.smap != map) {
-    L.sci.release();
-    L.s32.release();
-    L.s16.release();
-    L.srow.release();
-    const int ns = (rows + rpw - 1) / rpw;
-    DBuf<int32_t> slen;
-    BCS_ALLOC(s, slen, ns);
-    BCS_ALLOC(s, L.sptr, ns + 1);
-    if (map == 1) {
-      BCS_ALLOC(s, L.srow, rows);
-      BCS_LAUNCH(s, K_CAST, 0, 0, k_window_order, grid_for(rows, SORT_WIN), SORT_WIN, 0, rows, L.A.rp.p,
-                 L.srow.p);
-    }
-    BCS_LAUNCH(s, K_CAST, 0, 0, k_slice_len, grid_for(ns, 256), 256, 0, rows, rpw, ns, L.A.rp.p, L.srow.p,
-               slen.p);
-    BCS_OKR(exclusive_scan(s, slen.p, L.sptr.p, ns));
-    int32_t steps = 0;
-    BCS_CU(s, cudaMemcpyAsync(&steps, L.sptr.p + ns, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
-    BCS_CU(s, cudaStreamSynchronize(s->stream));
-    L.nslices = ns;
-    L.nsteps = steps;
-    L.smap = map;
-    BCS_ALLOC(s, L.sci, (size_t)steps * rpw);
+  *needed = L.nslices == 0 || L.smap != map;
+  if (!*needed) return BCS_OK;
+  L.sci.release();
+  L.s32.release();
+  L.s16.release();
+  L.srow.release();
+  const int ns = (rows + rpw - 1) / rpw;
+  DBuf<int32_t> slen;
+  BCS_ALLOC(s, slen, ns);
+  BCS_ALLOC(s, L.sptr, ns + 1);
+  if (map == 1) {
+    BCS_ALLOC(s, L.srow, rows);
+    BCS_LAUNCH(s, K_CAST, 0, 0, k_window_order, grid_for(rows, SORT_WIN), SORT_WIN, 0, rows, L.A.rp.p, L.srow.p);
   }
+  BCS_LAUNCH(s, K_CAST, 0, 0, k_slice_len, grid_for(ns, 256), 256, 0, rows, rpw, ns, L.A.rp.p, L.srow.p, slen.p);
+  BCS_OKR(exclusive_scan(s, slen.p, L.sptr.p, ns));
+  BCS_CU(s, cudaMemcpyAsync(steps_dev, L.sptr.p + ns, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->stream));
+  L.nslices = ns;
+  L.smap = map;
+  return BCS_OK;
+}
+
+// Values of level L's sliced copy (its structure in place, nsteps known).
+bcs_status layout_values(Solver* s, Level& L, int prec) {
+  const int n = s->n, rows = L.A.rows, map = L.smap, rpw = map == 1 ? 32 : 32 / n;
+  if (!L.sci.p) BCS_ALLOC(s, L.sci, (size_t)L.nsteps * rpw);
   const size_t nv = (size_t)L.nsteps * rpw * n * n;
   return with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
@@ -870,6 +875,21 @@ bcs_status fill_layout(Solver* s, Level& L, int prec, int map) {
     }
     return BCS_OK;
   });
+}
+
+// Sliced copy of level L in layout `map` (structure when new, values).
+bcs_status fill_layout(Solver* s, Level& L, int prec, int map) {
+  DBuf<int32_t> steps;
+  BCS_ALLOC(s, steps, 1);
+  bool needed = false;
+  BCS_OKR(layout_structure(s, L, map, steps.p, &needed));
+  if (needed) {
+    int32_t h = 0;
+    BCS_CU(s, cudaMemcpyAsync(&h, steps.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    BCS_CU(s, cudaStreamSynchronize(s->stream));
+    L.nsteps = h;
+  }
+  return layout_values(s, L, prec);
 }
 
 // ---- layout autotuner --------------------------------------------------------
@@ -955,13 +975,15 @@ bcs_status choose_layout(Solver* s, Level& L, int prec, int* map) {
   return BCS_OK;
 }
 
-bcs_status build_slices(Solver* s, Level& L, int prec) {
-  int map = L.smap;
-  if (map < 0) {
-    if (s->setup_cfg.slice_layout >= 0) map = s->setup_cfg.slice_layout;
-    else BCS_OKR(choose_layout(s, L, prec, &map));
+// Layout of level L's sliced copy: kept, forced by the configuration, or
+// picked by the autotuner (which builds and times both).
+bcs_status slice_map(Solver* s, Level& L, int prec, int* map) {
+  *map = L.smap;
+  if (*map < 0) {
+    if (s->setup_cfg.slice_layout >= 0) *map = s->setup_cfg.slice_layout;
+    else BCS_OKR(choose_layout(s, L, prec, map));
   }
-  return fill_layout(s, L, prec, map);
+  return BCS_OK;
 }
 
 // Cycle vectors and storage copies of the hierarchy in the configured
@@ -971,7 +993,14 @@ bcs_status cycle_prepare(Solver* s) {
   const int prec = s->setup_cfg.precision;
   const size_t vsz = prec == BCS_PREC_FP64 ? sizeof(double) : sizeof(float);
   const int n = s->n, nn = n * n;
-  for (size_t l = 0; l < s->lv.size(); ++l) {
+  const bool sliced = prec != BCS_PREC_FP64 && (s->setup_cfg.precond == BCS_PC_AMG || s->setup_cfg.precond == BCS_PC_SGS);
+  const size_t nl = s->lv.size();
+  // slice structures of every level first; their step counts are read back
+  // together in one round trip
+  DBuf<int32_t> steps;
+  BCS_ALLOC(s, steps, nl);
+  std::vector<char> needed(nl, 0);
+  for (size_t l = 0; l < nl; ++l) {
     Level& L = s->lv[l];
     const size_t N = (size_t)L.A.rows * n;
     BCS_ALLOC(s, L.vx, N * vsz);
@@ -979,12 +1008,27 @@ bcs_status cycle_prepare(Solver* s) {
     BCS_ALLOC(s, L.vr, N * vsz);
     BCS_ALLOC(s, L.vt, N * vsz);
     if (L.ncol > 0) BCS_ALLOC(s, L.vd, N * vsz);
-    if (prec == BCS_PREC_FP64 || (s->setup_cfg.precond != BCS_PC_AMG && s->setup_cfg.precond != BCS_PC_SGS)) continue;
+    if (!sliced) continue;
     BCS_OKR(dilu_prepare(s, L));
     BCS_ALLOC(s, L.dinv32, (size_t)L.A.rows * nn);
     BCS_OKR(cast_vec<double, float>(s, L.dinv.p, L.dinv32.p, (size_t)L.A.rows * nn));
+    int map = 0;
+    BCS_OKR(slice_map(s, L, prec, &map));
+    bool need = false;
+    BCS_OKR(layout_structure(s, L, map, steps.p + l, &need));
+    needed[l] = need;
+  }
+  if (sliced && std::find(needed.begin(), needed.end(), 1) != needed.end()) {
+    std::vector<int32_t> h(nl, 0);
+    BCS_CU(s, cudaMemcpyAsync(h.data(), steps.p, nl * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    BCS_CU(s, cudaStreamSynchronize(s->stream));
+    for (size_t l = 0; l < nl; ++l)
+      if (needed[l]) s->lv[l].nsteps = h[l];
+  }
+  for (size_t l = 0; l < nl && sliced; ++l) {
+    Level& L = s->lv[l];
+    BCS_OKR(layout_values(s, L, prec));
     const bool smoothed = L.coarse_kind < 0 && s->setup_cfg.pmode == BCS_P_SMOOTHED;
-    BCS_OKR(build_slices(s, L, prec));
     if (prec == BCS_PREC_FP32) {
       if (smoothed) {
         BCS_ALLOC(s, L.P32, (size_t)L.P.nnz * nn);

@@ -9,6 +9,8 @@
 //   2 f + 1 lower[f]  (row neighbour[f], column owner[f])
 // Values (every nonlinear iteration): val[p] = source block, a pure gather
 // with coalesced n*n-double writes.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace bcs {
@@ -119,6 +121,113 @@ __global__ void k_gather_values(size_t total, const int32_t* __restrict__ src,
   }
 }
 
+// The gather for a full setup, fused with the block Frobenius norms the
+// first matching pass needs (N(M): fma sum of squares in row-major order
+// from +0, then sqrt, as k_block_norms computes them), so the fine matrix is
+// not read again for them. A warp takes 32 consecutive block-CSR positions:
+// each source block (n*n contiguous doubles) is loaded by n*n lanes into a
+// tile in shared memory (rows padded to an odd length: conflict-free), lane
+// b then sums the squares of block b, and the tile is stored to the
+// positions as one contiguous run.
+constexpr int GN_U = 8;
+
+template <int NN>
+struct GnShape {
+  static constexpr int NNP = NN | 1;          // padded tile row
+  static constexpr int WARPS = NN <= 25 ? 4 : 2;
+  static constexpr int LPB = NN < 32 ? NN : 32;  // lanes loading one block
+};
+
+template <int NN>
+__global__ void __launch_bounds__(GnShape<NN>::WARPS * 32) k_gather_norms(int nnz, const int32_t* __restrict__ src,
+                                                                         const double* __restrict__ diag,
+                                                                         const double* __restrict__ upper,
+                                                                         const double* __restrict__ lower,
+                                                                         double* __restrict__ val,
+                                                                         double* __restrict__ nrm) {
+  using G = GnShape<NN>;
+  __shared__ double tile[G::WARPS][32 * G::NNP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* tl = tile[warp];
+  const int p0 = (blockIdx.x * G::WARPS + warp) * 32;
+  if (p0 >= nnz) return;
+  const int cnt = min(32, nnz - p0);
+  const int code = lane < cnt ? __ldg(src + p0 + lane) : -1;
+  const double* mine = code < 0 ? diag + (size_t)(-1 - code) * NN
+                                : ((code & 1) ? lower : upper) + (size_t)(code >> 1) * NN;
+  // GN_U source blocks in flight per lane (E entries of each)
+  constexpr int E = (NN + 31) / 32;
+  constexpr int U = GN_U / E > 0 ? GN_U / E : 1;
+  for (int b0 = 0; b0 < cnt; b0 += U) {
+    double v[U][E];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const double* a =
+          reinterpret_cast<const double*>(__shfl_sync(0xffffffffu, (unsigned long long)mine, (b0 + u) & 31));
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int e = lane + 32 * j;
+        v[u][j] = (b0 + u < cnt && e < NN) ? __ldg(a + e) : 0.0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int e = lane + 32 * j;
+        if (b0 + u < cnt && e < NN) tl[(b0 + u) * G::NNP + e] = v[u][j];
+      }
+  }
+  __syncwarp();
+  if (lane < cnt) {
+    double acc = 0.0;
+#pragma unroll
+    for (int e = 0; e < NN; ++e) {
+      const double v = tl[lane * G::NNP + e];
+      acc = fma(v, v, acc);
+    }
+    nrm[p0 + lane] = sqrt(acc);
+  }
+  double* out = val + (size_t)p0 * NN;
+  for (int q = lane; q < cnt * NN; q += 32) out[q] = tl[(q / NN) * G::NNP + q % NN];
+}
+
+// Scatter of consecutive LDU blocks (one array: diag, upper or lower) to
+// their block-CSR positions, with their Frobenius norms when nrm is given:
+// a warp loads 32 contiguous source blocks into a tile (coalesced), lane b
+// sums the squares of block b as k_block_norms does, and each block is
+// stored whole at its position.
+template <int NN>
+__global__ void __launch_bounds__(GnShape<NN>::WARPS * 32) k_scatter_blocks(int count, const double* __restrict__ src,
+                                                                           const int32_t* __restrict__ pos,
+                                                                           double* __restrict__ val,
+                                                                           double* __restrict__ nrm) {
+  using G = GnShape<NN>;
+  __shared__ double tile[G::WARPS][32 * G::NNP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* tl = tile[warp];
+  const int b0 = (blockIdx.x * G::WARPS + warp) * 32;
+  if (b0 >= count) return;
+  const int cnt = min(32, count - b0);
+  const double* in = src + (size_t)b0 * NN;
+  for (int q = lane; q < cnt * NN; q += 32) tl[(q / NN) * G::NNP + q % NN] = __ldg(in + q);
+  const int my = lane < cnt ? __ldg(pos + b0 + lane) : 0;
+  __syncwarp();
+  if (nrm && lane < cnt) {
+    double acc = 0.0;
+#pragma unroll
+    for (int e = 0; e < NN; ++e) {
+      const double v = tl[lane * G::NNP + e];
+      acc = fma(v, v, acc);
+    }
+    nrm[my] = sqrt(acc);
+  }
+  for (int b = 0; b < cnt; ++b) {
+    const int p = __shfl_sync(0xffffffffu, my, b);
+    for (int e = lane; e < NN; e += 32) val[(size_t)p * NN + e] = tl[b * G::NNP + e];
+  }
+}
+
 }  // namespace
 
 bcs_status build_structure(Solver* s, const int32_t* owner, const int32_t* nb) {
@@ -175,6 +284,21 @@ bcs_status permute_values(Solver* s, const double* diag, const double* upper, co
   BCS_ALLOC(s, A.v, (size_t)A.nnz * nn);
   const size_t total = (size_t)A.nnz * nn;
   const double bytes = 16.0 * total + 4.0 * A.nnz;
+  s->nrm0_fresh = false;
+  if (!s->have_hierarchy) {
+    // a full setup follows: its first matching pass takes these norms
+    BCS_ALLOC(s, s->nrm0, A.nnz);
+    BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
+      constexpr int N = decltype(NC)::value;
+      using G = GnShape<N * N>;
+      BCS_LAUNCH(s, K_CONVERT, bytes + 8.0 * A.nnz, 2.0 * total, k_gather_norms<N * N>,
+                 grid_for((size_t)A.nnz, G::WARPS * 32), G::WARPS * 32, 0, A.nnz, s->src.p, diag, upper, lower,
+                 A.v.p, s->nrm0.p);
+      return BCS_OK;
+    }));
+    s->nrm0_fresh = true;
+    return BCS_OK;
+  }
   return with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
     unsigned grid = grid_for(total, 256);
@@ -183,6 +307,77 @@ bcs_status permute_values(Solver* s, const double* diag, const double* upper, co
                lower, A.v.p);
     return BCS_OK;
   });
+}
+
+}  // namespace bcs
+
+namespace bcs {
+
+// Host values to the block-CSR values with the copy hidden behind the
+// device work: the three LDU arrays go to the device in pieces on a second
+// stream, and each piece is scattered (with its block norms when a full
+// setup follows) as soon as it has landed.
+bcs_status upload_values(Solver* s, const double* diag, const double* upper, const double* lower) {
+  Bsr& A = s->lv[0].A;
+  const int n = s->n, nn = n * n, C = s->C, F = s->F;
+  BCS_ALLOC(s, A.v, (size_t)A.nnz * nn);
+  BCS_ALLOC(s, s->stage_d, (size_t)C * nn);
+  if (F > 0) {
+    BCS_ALLOC(s, s->stage_u, (size_t)F * nn);
+    BCS_ALLOC(s, s->stage_l, (size_t)F * nn);
+  }
+  const bool norms = !s->have_hierarchy;
+  s->nrm0_fresh = false;
+  if (norms) BCS_ALLOC(s, s->nrm0, A.nnz);
+  if (!s->cstream) BCS_CU(s, cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking));
+  struct Part {
+    const double* host;
+    double* dev;
+    const int32_t* pos;
+    int count;
+  };
+  const Part parts[3] = {{diag, s->stage_d.p, s->pos_diag.p, C},
+                         {upper, s->stage_u.p, s->pos_up.p, F},
+                         {lower, s->stage_l.p, s->pos_lo.p, F}};
+  // pieces of about 64 MB
+  const int piece = std::max(1, (int)((64u << 20) / ((size_t)nn * sizeof(double))));
+  size_t ev = 0;
+  auto next_event = [&](cudaEvent_t* e) -> bcs_status {
+    if (ev == s->copy_events.size()) {
+      cudaEvent_t x;
+      BCS_CU(s, cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+      s->copy_events.push_back(x);
+    }
+    *e = s->copy_events[ev++];
+    return BCS_OK;
+  };
+  // the copy stream starts after the allocations on the solver's stream
+  cudaEvent_t e0;
+  BCS_OKR(next_event(&e0));
+  BCS_CU(s, cudaEventRecord(e0, s->stream));
+  BCS_CU(s, cudaStreamWaitEvent(s->cstream, e0, 0));
+  for (const Part& pt : parts) {
+    for (int b = 0; b < pt.count; b += piece) {
+      const int cnt = std::min(piece, pt.count - b);
+      const size_t off = (size_t)b * nn;
+      BCS_CU(s, cudaMemcpyAsync(pt.dev + off, pt.host + off, (size_t)cnt * nn * sizeof(double),
+                                cudaMemcpyHostToDevice, s->cstream));
+      cudaEvent_t e;
+      BCS_OKR(next_event(&e));
+      BCS_CU(s, cudaEventRecord(e, s->cstream));
+      BCS_CU(s, cudaStreamWaitEvent(s->stream, e, 0));
+      BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
+        constexpr int N = decltype(NC)::value;
+        using G = GnShape<N * N>;
+        BCS_LAUNCH(s, K_CONVERT, 16.0 * cnt * N * N + 4.0 * cnt + (norms ? 8.0 * cnt : 0.0),
+                   norms ? 2.0 * cnt * N * N : 0.0, k_scatter_blocks<N * N>, grid_for(cnt, G::WARPS * 32),
+                   G::WARPS * 32, 0, cnt, pt.dev + off, pt.pos + b, A.v.p, norms ? s->nrm0.p : nullptr);
+        return BCS_OK;
+      }));
+    }
+  }
+  s->nrm0_fresh = norms;
+  return BCS_OK;
 }
 
 }  // namespace bcs

@@ -109,11 +109,12 @@ struct Bsr {
   DBuf<double> v;
 };
 
-// Plan of the tentative Galerkin product: per coarse row I its fine blocks
-// in ascending position, seqk[seg[I] .. seg[I+1]), and each one's output
-// block seqd (the first term of an output flagged by the sign bit).
+// Plan of the tentative Galerkin product: per coarse row I its terms
+// sk[seg[I] .. seg[I+1]) sorted by (output block, fine position): the fine
+// block position of each, the first term of every output block flagged by
+// the sign bit (outputs follow in the row's column order).
 struct TentPlan {
-  DBuf<int32_t> seg, seqk, seqd;
+  DBuf<int32_t> seg, sk;
 };
 
 struct Level {
@@ -125,6 +126,8 @@ struct Level {
   int nagg = 0;
   DBuf<int32_t> agg;         // aggregate of each row
   DBuf<int32_t> mptr, mem;   // aggregate member lists (members ascending)
+  DBuf<int32_t> cnt;         // member counts (between aggregation and the member lists)
+  int maxmem = 0;            // largest aggregate (an upper bound)
   Bsr P, R, AP;              // smoothed mode only: P, R and the product A P (FP64)
   DBuf<int32_t> Prow, Rrow, AProw, Crow;  // row of every nonzero of P, R, AP, A_{l+1}
   TentPlan tent;              // plan of the tentative Galerkin product
@@ -205,6 +208,12 @@ struct Solver {
   DBuf<int32_t> perm, inv;
   DBuf<double> rb, rx;           // vectors in the internal numbering
   DBuf<double> stage_d, stage_u, stage_l;  // host-input staging
+  // block Frobenius norms of the fine matrix, computed by the value gather
+  // when a full setup follows (fresh: they belong to the current values)
+  DBuf<double> nrm0;
+  bool nrm0_fresh = false;
+  cudaStream_t cstream = nullptr;          // host -> device copies of the values in pieces
+  std::vector<cudaEvent_t> copy_events;     // one per piece
   DBuf<int32_t> stage_o, stage_n;
   // hierarchy
   std::vector<Level> lv;
@@ -332,6 +341,8 @@ bcs_status assemble_density(Solver* s, const double* Q, const double* area, cons
                             const bcs_flow_params& prm, double* diag, double* upper, double* lower);
 bcs_status permute_values(Solver* s, const double* diag_d, const double* upper_d,
                           const double* lower_d);
+// The same from HOST arrays, the copy overlapped with the scatter.
+bcs_status upload_values(Solver* s, const double* diag_h, const double* upper_h, const double* lower_h);
 
 // -------------------------------------------------------------------- scan.cu
 // out[0..n] = exclusive prefix sums of in[0..n-1]; out[n] = total. Device.

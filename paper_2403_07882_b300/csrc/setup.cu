@@ -242,64 +242,96 @@ __global__ void k_cand_count_tent(int nagg, const int32_t* __restrict__ mptr, co
   if (I < nagg) cnt[I] = c;
 }
 
-// One thread per fine row: its blocks' candidates (coarse column, index in
-// the coarse row's sequence of fine positions), contiguous in its coarse
-// row's segment, and that sequence itself (seqk). Members ascending and each
-// row's blocks ascending make the sequence ascending in position, so sorting
-// by (column, index) orders every run as the fine positions do.
+// One thread per fine row: its blocks' candidates (coarse column agg(j),
+// fine block position p), contiguous in its coarse row's segment. Sorting a
+// segment by (column, position) groups each coarse block's fine blocks in
+// ascending position, the summation order of the definition.
 __global__ void k_cand_pack_tent(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                  const int32_t* __restrict__ agg, const int32_t* __restrict__ cptr,
-                                 const int32_t* __restrict__ moff, uint64_t* __restrict__ cand,
-                                 int32_t* __restrict__ seqk) {
+                                 const int32_t* __restrict__ moff, uint64_t* __restrict__ cand) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const long long o = (long long)cptr[agg[i]] + moff[i] - rp[i];
-  const uint32_t l0 = (uint32_t)(moff[i] - rp[i]);
-  for (int p = rp[i]; p < rp[i + 1]; ++p) {
-    cand[o + p] = ((uint64_t)(uint32_t)agg[ci[p]] << 32) | (l0 + (uint32_t)p);
-    seqk[o + p] = p;
-  }
+  for (int p = rp[i]; p < rp[i + 1]; ++p) cand[o + p] = ((uint64_t)(uint32_t)agg[ci[p]] << 32) | (uint32_t)p;
 }
 
-// Number of runs (distinct columns) in each sorted segment; longest -> *mx
-// when mx is given.
-__global__ void k_runs_count(int rows, const int32_t* __restrict__ seg, const uint64_t* __restrict__ cand,
-                             int32_t* __restrict__ cnt, int32_t* __restrict__ mx) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int c = 0;
-  if (i < rows) {
-    uint32_t prev = 0;
-    for (int t = seg[i]; t < seg[i + 1]; ++t) {
-      const uint32_t J = (uint32_t)(cand[t] >> 32);
-      if (t == seg[i] || J != prev) ++c;
-      prev = J;
+// Runs (distinct columns) of the sorted segments, one warp per segment: lane
+// l looks at candidate t0 + l of each 32-candidate chunk; a candidate starts
+// a run when it is the segment's first or its column differs from the one
+// before it.
+struct RunScan {
+  unsigned first_mask;
+  uint32_t J;
+  bool live, first;
+};
+
+__device__ __forceinline__ RunScan run_chunk(const uint64_t* __restrict__ cand, int t, int t0, int t1,
+                                             uint32_t* carry) {
+  const int lane = threadIdx.x & 31;
+  RunScan r;
+  r.live = t < t1;
+  r.J = r.live ? (uint32_t)(__ldg(cand + t) >> 32) : 0u;
+  uint32_t prev = __shfl_up_sync(0xffffffffu, r.J, 1);
+  if (lane == 0) prev = *carry;
+  r.first = r.live && (t == t0 || r.J != prev);
+  r.first_mask = __ballot_sync(0xffffffffu, r.first);
+  *carry = __shfl_sync(0xffffffffu, r.J, 31);
+  return r;
+}
+
+// Number of runs of each segment; the longest -> *mx when mx is given (one
+// atomic per block: warps loop over the segments, the block reduces).
+constexpr int RC_BLOCKS = 148 * 8;
+
+__global__ void __launch_bounds__(256) k_runs_count(int rows, const int32_t* __restrict__ seg,
+                                                    const uint64_t* __restrict__ cand, int32_t* __restrict__ cnt,
+                                                    int32_t* __restrict__ mx) {
+  __shared__ int wm[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int best = 0;
+  for (int I = blockIdx.x * 8 + warp; I < rows; I += gridDim.x * 8) {
+    const int t0 = seg[I], t1 = seg[I + 1];
+    uint32_t carry = 0;
+    int c = 0;
+    for (int b = t0; b < t1; b += 32) {
+      const RunScan r = run_chunk(cand, b + lane, t0, t1, &carry);
+      c += __popc(r.first_mask);
     }
+    if (lane == 0) cnt[I] = c;
+    best = max(best, c);
   }
-  if (mx) {
-    const int m = __reduce_max_sync(0xffffffffu, c);
-    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(mx, m);
+  if (lane == 0) wm[warp] = best;
+  __syncthreads();
+  if (threadIdx.x == 0 && mx) {
+    int m = 0;
+    for (int w = 0; w < 8; ++w) m = max(m, wm[w]);
+    if (m > 0) atomicMax(mx, m);
   }
-  if (i < rows) cnt[i] = c;
 }
 
-// One output block per run: column col[o]; every fine block of the run gets
-// seqd = o at its place in the coarse row's sequence, the run's first (in
-// position order) flagged by the sign bit.
+// One output block per run: column col[o]. The sorted candidates are also
+// the plan of the value sum: sk[t] = fine block position, with the sign bit
+// set on the first candidate of each run.
 constexpr int32_t TS_FIRST = INT32_MIN;
 
 __global__ void k_runs_emit(int rows, const int32_t* __restrict__ seg, const uint64_t* __restrict__ cand,
-                            const int32_t* __restrict__ rp, int32_t* __restrict__ col, int32_t* __restrict__ seqd) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= rows) return;
-  int o = rp[i] - 1;
-  uint32_t prev = 0;
-  for (int t = seg[i]; t < seg[i + 1]; ++t) {
-    const uint64_t v = cand[t];
-    const uint32_t J = (uint32_t)(v >> 32);
-    const bool first = t == seg[i] || J != prev;
-    if (first) col[++o] = (int32_t)J;
-    seqd[seg[i] + (int32_t)(uint32_t)v] = first ? (o | TS_FIRST) : o;
-    prev = J;
+                            const int32_t* __restrict__ rp, int32_t* __restrict__ col, int32_t* __restrict__ sk) {
+  const int I = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (I >= rows) return;
+  const int lane = threadIdx.x & 31;
+  const int t0 = seg[I], t1 = seg[I + 1];
+  uint32_t carry = 0;
+  int o = rp[I] - 1;
+  for (int b = t0; b < t1; b += 32) {
+    const int t = b + lane;
+    const RunScan r = run_chunk(cand, t, t0, t1, &carry);
+    const int mine = o + __popc(r.first_mask & (0xffffffffu >> (31 - lane)));
+    if (r.first) col[mine] = (int32_t)r.J;
+    if (r.live) {
+      const int32_t p = (int32_t)(uint32_t)__ldg(cand + t);
+      sk[t] = r.first ? (p | TS_FIRST) : p;
+    }
+    o += __popc(r.first_mask);
   }
 }
 
@@ -309,19 +341,17 @@ __device__ __forceinline__ double plus_zero(double v) {
 }
 
 // Coarse block values of P_tent^T A P_tent: out[q] = left-to-right FP64 sum
-// from +0 of the fine blocks of q in position order. One group of lanes per
-// coarse row walks the row's fine blocks in ascending position (seqk),
-// adding each into the accumulator of its output block (seqd), so every
-// output sees its terms in position order. Lane e of a group owns entry e
-// (and e + 32, ... when n^2 > 32) of every output block of the row; its
-// accumulators sit in its own column of shared memory (rows with more than
-// cap output blocks accumulate in place in global memory). The first term of
-// an output is stored, not added: 0 + v equals v except that -0 becomes +0
-// (integer operations), so no FP64 add is spent on it. TS_U fine blocks are
-// fetched per round trip, their positions one round ahead.
+// from +0 of the fine blocks of q in position order. The plan lists each
+// coarse row's terms sorted by (output block, fine position), so the terms
+// of every output are consecutive and in position order: one group of lanes
+// per coarse row walks them with its running sums in registers and stores a
+// sum when the next output starts. Lane e of a group owns entry e (and
+// e + 32, ... when n^2 > 32) of every block. The first term of an output is
+// stored, not added: 0 + v equals v except that -0 becomes +0 (integer
+// operations), so no FP64 add is spent on it. TS_U fine blocks are fetched
+// per round trip, their positions one round ahead.
 constexpr int TS_U = 8;
 constexpr int TS_WARPS = 4;
-constexpr int TS_SMEM_DOUBLES = 32;  // per lane: cap * ceil(n^2 / 32) <= this
 
 template <int NN>
 struct TentShape {
@@ -331,74 +361,59 @@ struct TentShape {
 };
 
 template <int NN>
-__global__ void __launch_bounds__(TS_WARPS * 32) k_tent_sum(int nagg, int cap, const int32_t* __restrict__ seg,
-                                                           const int32_t* __restrict__ seqk,
-                                                           const int32_t* __restrict__ seqd,
+__global__ void __launch_bounds__(TS_WARPS * 32) k_tent_sum(int nagg, const int32_t* __restrict__ seg,
+                                                           const int32_t* __restrict__ sk,
                                                            const int32_t* __restrict__ crp,
-                                                           const double* __restrict__ src, double* out) {
+                                                           const double* __restrict__ src, double* __restrict__ out) {
   using S = TentShape<NN>;
-  extern __shared__ double ts_acc[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / S::W, e0 = lane - g * S::W;
   const int I = (blockIdx.x * TS_WARPS + warp) * S::G + g;
   if (g >= S::G || I >= nagg) return;
-  const int base = crp[I], slots = crp[I + 1] - base;
-  const bool in_smem = slots <= cap;
-  // accumulator of (slot, j): acc + slot * ss + j * sj
-  double* acc = in_smem ? ts_acc + (size_t)warp * 32 * cap * S::E + lane : out + (size_t)base * NN + e0;
-  const int ss = in_smem ? 32 * S::E : NN, sj = in_smem ? 32 : S::W;
-  const int t1 = seg[I + 1];
-  // software pipeline: the next round's positions are fetched while this
-  // round's values are in flight
-  int kn[TS_U], dn[TS_U];
-  const int tb = seg[I];
+  const int t0 = seg[I], t1 = seg[I + 1];
+  const int obase = crp[I];
+  int o = obase - 1;
+  double acc[S::E];
 #pragma unroll
-  for (int u = 0; u < TS_U; ++u) {
-    const bool ok = tb + u < t1;
-    kn[u] = ok ? __ldg(seqk + tb + u) : -1;
-    dn[u] = ok ? __ldg(seqd + tb + u) : 0;
-  }
-  for (int t = tb; t < t1; t += TS_U) {
-    int k[TS_U], d[TS_U];
+  for (int j = 0; j < S::E; ++j) acc[j] = 0.0;
+  int kn[TS_U];
 #pragma unroll
-    for (int u = 0; u < TS_U; ++u) {
-      k[u] = kn[u];
-      d[u] = dn[u];
-    }
+  for (int u = 0; u < TS_U; ++u) kn[u] = t0 + u < t1 ? __ldg(sk + t0 + u) : 0;
+  for (int t = t0; t < t1; t += TS_U) {
+    int k[TS_U];
+#pragma unroll
+    for (int u = 0; u < TS_U; ++u) k[u] = kn[u];
     double v[TS_U][S::E];
 #pragma unroll
     for (int u = 0; u < TS_U; ++u)
 #pragma unroll
       for (int j = 0; j < S::E; ++j) {
         const int e = e0 + j * S::W;
-        v[u][j] = (k[u] >= 0 && e < NN) ? __ldg(src + (size_t)k[u] * NN + e) : 0.0;
+        v[u][j] = (t + u < t1 && e < NN) ? __ldg(src + (size_t)(k[u] & INT32_MAX) * NN + e) : 0.0;
       }
 #pragma unroll
-    for (int u = 0; u < TS_U; ++u) {
-      const int tn = t + TS_U + u;
-      const bool ok = tn < t1;
-      kn[u] = ok ? __ldg(seqk + tn) : -1;
-      dn[u] = ok ? __ldg(seqd + tn) : 0;
-    }
+    for (int u = 0; u < TS_U; ++u) kn[u] = t + TS_U + u < t1 ? __ldg(sk + t + TS_U + u) : 0;
 #pragma unroll
     for (int u = 0; u < TS_U; ++u) {
-      if (k[u] < 0) continue;
-      double* a = acc + (size_t)((d[u] & ~TS_FIRST) - base) * ss;
+      if (t + u >= t1) break;
+      if (k[u] < 0) {
+        if (o >= obase)
 #pragma unroll
-      for (int j = 0; j < S::E; ++j) {
-        if (e0 + j * S::W >= NN) continue;
-        if (d[u] < 0)
-          a[j * sj] = plus_zero(v[u][j]);
-        else
-          a[j * sj] = a[j * sj] + v[u][j];
+          for (int j = 0; j < S::E; ++j)
+            if (e0 + j * S::W < NN) out[(size_t)o * NN + e0 + j * S::W] = acc[j];
+        ++o;
+#pragma unroll
+        for (int j = 0; j < S::E; ++j) acc[j] = plus_zero(v[u][j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < S::E; ++j) acc[j] = acc[j] + v[u][j];
       }
     }
   }
-  if (in_smem)
-    for (int q = 0; q < slots; ++q)
+  if (o >= obase)
 #pragma unroll
-      for (int j = 0; j < S::E; ++j)
-        if (e0 + j * S::W < NN) out[(size_t)(base + q) * NN + e0 + j * S::W] = acc[q * ss + j * sj];
+    for (int j = 0; j < S::E; ++j)
+      if (e0 + j * S::W < NN) out[(size_t)o * NN + e0 + j * S::W] = acc[j];
 }
 
 // ----------------------------------------------------- smoothed prolongation
@@ -718,11 +733,15 @@ bcs_status pattern_from_candidates(Solver* s, int rows, DBuf<int32_t>& cnt, Fill
 }
 
 // One matching pass on A (rows x rows): agg[rows]; returns the count.
-bcs_status match_pass(Solver* s, const Bsr& A, DBuf<int32_t>& agg, int* nagg) {
+// norms: A's block Frobenius norms when already known, else computed here.
+// Also returns the aggregates' member counts (cnt[0..nagg), an array of
+// rows entries) and their maximum, read back together with the count.
+bcs_status match_pass(Solver* s, const Bsr& A, DBuf<int32_t>& agg, int* nagg, DBuf<int32_t>& cnt, int* maxmem,
+                      const double* norms = nullptr) {
   const int rows = A.rows, nnz = A.nnz;
   DBuf<double> nrm, w;
   DBuf<int32_t> ridx, dpos, mate, choice, root, amin, flag, id;
-  BCS_ALLOC(s, nrm, nnz);
+  if (!norms) BCS_ALLOC(s, nrm, nnz);
   BCS_ALLOC(s, w, nnz);
   BCS_ALLOC(s, ridx, nnz);
   BCS_ALLOC(s, dpos, rows);
@@ -734,15 +753,18 @@ bcs_status match_pass(Solver* s, const Bsr& A, DBuf<int32_t>& agg, int* nagg) {
   BCS_ALLOC(s, id, rows + 1);
   BCS_ALLOC(s, agg, rows);
   const unsigned gr = grid_for(rows, 256), gn = grid_for(nnz, 256);
-  BCS_OKR(with_n(s->n, [&](auto NC) -> bcs_status {
-    constexpr int N = decltype(NC)::value;
-    BCS_LAUNCH(s, K_SETUP_AGG, 8.0 * nnz * (N * N + 1), 2.0 * nnz * N * N, k_block_norms<N * N>, gn, 256, 0, nnz,
-               A.v.p, nrm.p);
-    return BCS_OK;
-  }));
+  if (!norms) {
+    BCS_OKR(with_n(s->n, [&](auto NC) -> bcs_status {
+      constexpr int N = decltype(NC)::value;
+      BCS_LAUNCH(s, K_SETUP_AGG, 8.0 * nnz * (N * N + 1), 2.0 * nnz * N * N, k_block_norms<N * N>, gn, 256, 0, nnz,
+                 A.v.p, nrm.p);
+      return BCS_OK;
+    }));
+  }
   BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_row_index, gr, 256, 0, rows, A.rp.p, ridx.p);
   BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_diag_pos, gr, 256, 0, rows, A.rp.p, A.ci.p, dpos.p, s->flag.p);
-  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_weights, gn, 256, 0, nnz, A.rp.p, A.ci.p, ridx.p, dpos.p, nrm.p, w.p);
+  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_weights, gn, 256, 0, nnz, A.rp.p, A.ci.p, ridx.p, dpos.p,
+             norms ? norms : nrm.p, w.p);
   BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_fill_int, gr, 256, 0, mate.p, rows, -1);
   // A round that pairs nobody leaves the state unchanged, so running every
   // round equals stopping at the first idle one.
@@ -755,30 +777,39 @@ bcs_status match_pass(Solver* s, const Bsr& A, DBuf<int32_t>& agg, int* nagg) {
   BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_is_min, gr, 256, 0, rows, root.p, amin.p, flag.p);
   BCS_OKR(exclusive_scan(s, flag.p, id.p, rows));
   BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_assign, gr, 256, 0, rows, root.p, amin.p, id.p, agg.p);
-  int32_t na = 0;
-  BCS_OKR(read_int(s, id.p + rows, &na));
-  *nagg = na;
+  // member counts (aggregate ids are < rows) and their maximum, read with
+  // the aggregate count in one round trip
+  BCS_ALLOC(s, cnt, rows);
+  DBuf<int32_t> hv;
+  BCS_ALLOC(s, hv, 2);
+  BCS_CU(s, cudaMemsetAsync(cnt.p, 0, (size_t)rows * sizeof(int32_t), s->stream));
+  BCS_CU(s, cudaMemsetAsync(hv.p, 0, 2 * sizeof(int32_t), s->stream));
+  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_count_by, gr, 256, 0, rows, agg.p, cnt.p);
+  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_max_int, gr < 1024 ? gr : 1024, 256, 0, rows, cnt.p, hv.p + 1);
+  BCS_CU(s, cudaMemcpyAsync(hv.p, id.p + rows, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->stream));
+  int32_t h[2] = {0, 0};
+  BCS_CU(s, cudaMemcpyAsync(h, hv.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  *nagg = h[0];
+  *maxmem = h[1];
   return BCS_OK;
 }
 
 // Member lists of an aggregation: mptr[nagg+1], mem (members ascending).
-bcs_status members(Solver* s, int rows, int nagg, const int32_t* agg, DBuf<int32_t>& mptr,
+// cnt[0..nagg): member counts from match_pass (overwritten), mx their maximum.
+bcs_status members(Solver* s, int rows, int nagg, const int32_t* agg, int32_t* cnt, int mx, DBuf<int32_t>& mptr,
                    DBuf<int32_t>& mem) {
-  DBuf<int32_t> cnt, cursor;
-  BCS_ALLOC(s, cnt, nagg);
+  DBuf<int32_t> cursor;
   BCS_ALLOC(s, cursor, nagg);
   BCS_ALLOC(s, mptr, nagg + 1);
   BCS_ALLOC(s, mem, rows);
-  BCS_CU(s, cudaMemsetAsync(cnt.p, 0, nagg * sizeof(int32_t), s->stream));
   BCS_CU(s, cudaMemsetAsync(cursor.p, 0, nagg * sizeof(int32_t), s->stream));
-  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_count_by, grid_for(rows, 256), 256, 0, rows, agg, cnt.p);
-  BCS_OKR(exclusive_scan(s, cnt.p, mptr.p, nagg));
+  if (mx > 4096) BCS_OKR(max_of(s, cnt, nagg, &mx));  // a loose bound: the sort wants the real length
+  BCS_OKR(exclusive_scan(s, cnt, mptr.p, nagg));
   BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_place_by, grid_for(rows, 256), 256, 0, rows, agg, (const int32_t*)nullptr,
              mptr.p, cursor.p, mem.p);
-  int32_t mx = 0;
-  BCS_OKR(max_of(s, cnt.p, nagg, &mx));
   // members are distinct: sort/unique keeps the counts and sorts each list
-  return segmented_sort_unique(s, mptr.p, mem.p, cnt.p, nagg, mx);
+  return segmented_sort_unique(s, mptr.p, mem.p, cnt, nagg, mx);
 }
 
 // Pattern of A_c = P_tent^T A P_tent (row I: sorted aggregates of its
@@ -786,8 +817,10 @@ bcs_status members(Solver* s, int rows, int nagg, const int32_t* agg, DBuf<int32
 // blocks in position order and each one's output block), from one segmented
 // sort of packed (coarse column, sequence index) candidates. Sets A_c.maxrow.
 // Two host reads.
+// maxmem: the largest aggregate; with A.maxrow known, maxmem * A.maxrow
+// bounds the longest candidate segment and its read is skipped.
 bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, const int32_t* mptr,
-                        const int32_t* mem, Bsr& Ac, TentPlan& plan) {
+                        const int32_t* mem, int maxmem, Bsr& Ac, TentPlan& plan) {
   DBuf<int32_t> cnt, hv, moff;
   BCS_ALLOC(s, cnt, nagg);
   BCS_ALLOC(s, plan.seg, nagg + 1);
@@ -798,17 +831,22 @@ bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, c
              moff.p, hv.p + 1);
   BCS_OKR(exclusive_scan(s, cnt.p, plan.seg.p, nagg));
   int32_t h[2] = {0, 0};
-  BCS_CU(s, cudaMemcpyAsync(h, hv.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
-  BCS_CU(s, cudaStreamSynchronize(s->stream));
-  const int max_c = h[1];
+  int max_c;
+  if (A.maxrow >= 0 && maxmem > 0 && (long long)maxmem * A.maxrow <= 4096) {
+    max_c = maxmem * A.maxrow;
+  } else {
+    BCS_CU(s, cudaMemcpyAsync(h, hv.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    BCS_CU(s, cudaStreamSynchronize(s->stream));
+    max_c = h[1];
+  }
   DBuf<uint64_t> cand;
   BCS_ALLOC(s, cand, A.nnz);
-  BCS_ALLOC(s, plan.seqk, A.nnz);
-  BCS_ALLOC(s, plan.seqd, A.nnz);
-  BCS_LAUNCH(s, K_SETUP_GAL, 20.0 * A.nnz, 0, k_cand_pack_tent, grid_for(A.rows, 256), 256, 0, A.rows, A.rp.p,
-             A.ci.p, agg, plan.seg.p, moff.p, cand.p, plan.seqk.p);
+  BCS_ALLOC(s, plan.sk, A.nnz);
+  BCS_LAUNCH(s, K_SETUP_GAL, 16.0 * A.nnz, 0, k_cand_pack_tent, grid_for(A.rows, 256), 256, 0, A.rows, A.rp.p,
+             A.ci.p, agg, plan.seg.p, moff.p, cand.p);
   BCS_OKR(segmented_sort64(s, plan.seg.p, cand.p, nagg, max_c));
-  BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_runs_count, grid_for(nagg, 256), 256, 0, nagg, plan.seg.p, cand.p,
+  BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_runs_count, std::min<unsigned>(grid_for(nagg, 8), RC_BLOCKS), 256,
+             0, nagg, plan.seg.p, cand.p,
              cnt.p, hv.p + 3);
   BCS_ALLOC(s, Ac.rp, nagg + 1);
   BCS_OKR(exclusive_scan(s, cnt.p, Ac.rp.p, nagg));
@@ -819,8 +857,8 @@ bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, c
   Ac.nnz = h[0];
   Ac.maxrow = h[1];
   BCS_ALLOC(s, Ac.ci, Ac.nnz);
-  BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz + 4.0 * Ac.nnz, 0, k_runs_emit, grid_for(nagg, 256), 256, 0, nagg,
-             plan.seg.p, cand.p, Ac.rp.p, Ac.ci.p, plan.seqd.p);
+  BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz + 4.0 * Ac.nnz, 0, k_runs_emit, grid_for((size_t)nagg * 32, 256), 256, 0,
+             nagg, plan.seg.p, cand.p, Ac.rp.p, Ac.ci.p, plan.sk.p);
   return BCS_OK;
 }
 
@@ -832,20 +870,19 @@ bcs_status tent_values(Solver* s, const Bsr& A, const TentPlan& plan, Bsr& Ac) {
     using S = TentShape<N * N>;
     if ((size_t)Ac.nnz * N * N >= (1ull << 31)) return s->fail(BCS_EINVAL, "Galerkin product too large");
     const int nagg = Ac.rows;
-    const int cap = std::min(Ac.maxrow, TS_SMEM_DOUBLES / S::E);
-    const size_t smem = (size_t)TS_WARPS * 32 * cap * S::E * sizeof(double);
     const unsigned grid = grid_for(nagg, TS_WARPS * S::G);
-    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + Ac.nnz) * N * N + 8.0 * A.nnz + 8.0 * (nagg + 1),
-               1.0 * (A.nnz - Ac.nnz) * N * N, k_tent_sum<N * N>, grid, TS_WARPS * 32, smem, nagg, cap, plan.seg.p,
-               plan.seqk.p, plan.seqd.p, Ac.rp.p, A.v.p, Ac.v.p);
+    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + Ac.nnz) * N * N + 4.0 * A.nnz + 4.0 * (nagg + 1) * 2,
+               1.0 * (A.nnz - Ac.nnz) * N * N, k_tent_sum<N * N>, grid, TS_WARPS * 32, 0, nagg, plan.seg.p,
+               plan.sk.p, Ac.rp.p, A.v.p, Ac.v.p);
     return BCS_OK;
   });
 }
 
 // Aggregation with agg_passes matching passes; fills L.agg / L.nagg.
-bcs_status aggregate_level(Solver* s, Level& L) {
-  int nagg = 0;
-  BCS_OKR(match_pass(s, L.A, L.agg, &nagg));
+bcs_status aggregate_level(Solver* s, Level& L, const double* norms) {
+  int nagg = 0, maxmem = 0;
+  DBuf<int32_t> cnt;
+  BCS_OKR(match_pass(s, L.A, L.agg, &nagg, cnt, &maxmem, norms));
   DBuf<int32_t> cur_agg;
   BCS_ALLOC(s, cur_agg, L.A.rows);
   BCS_CU(s, cudaMemcpyAsync(cur_agg.p, L.agg.p, L.A.rows * sizeof(int32_t), cudaMemcpyDeviceToDevice,
@@ -854,14 +891,17 @@ bcs_status aggregate_level(Solver* s, Level& L) {
   const Bsr* cur = &L.A;
   for (int pass = 1; pass < s->setup_cfg.agg_passes; ++pass) {
     DBuf<int32_t> mptr, mem;
-    BCS_OKR(members(s, cur->rows, nagg, cur_agg.p, mptr, mem));
+    BCS_OKR(members(s, cur->rows, nagg, cur_agg.p, cnt.p, maxmem, mptr, mem));
     Bsr Abar;
     TentPlan plan;
-    BCS_OKR(tent_pattern(s, *cur, nagg, cur_agg.p, mptr.p, mem.p, Abar, plan));
+    BCS_OKR(tent_pattern(s, *cur, nagg, cur_agg.p, mptr.p, mem.p, maxmem, Abar, plan));
     BCS_OKR(tent_values(s, *cur, plan, Abar));
     DBuf<int32_t> a2;
-    int n2 = 0;
-    BCS_OKR(match_pass(s, Abar, a2, &n2));
+    int n2 = 0, mm2 = 0;
+    BCS_OKR(match_pass(s, Abar, a2, &n2, cnt, &mm2));
+    // an aggregate of aggregates has at most the product of the largest
+    // sizes (an upper bound is all the sorts need)
+    maxmem = (int)std::min<long long>((long long)maxmem * mm2, L.A.rows);
     BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_compose, grid_for(L.A.rows, 256), 256, 0, L.A.rows, a2.p, L.agg.p);
     cur_agg = std::move(a2);
     const bool stalled = n2 == nagg;
@@ -871,6 +911,14 @@ bcs_status aggregate_level(Solver* s, Level& L) {
     if (stalled) break;
   }
   L.nagg = nagg;
+  // member counts of the final aggregates over the fine rows (recounted when
+  // the graph was coarsened in between; maxmem is then an upper bound)
+  if (cur != &L.A) {
+    BCS_CU(s, cudaMemsetAsync(cnt.p, 0, (size_t)nagg * sizeof(int32_t), s->stream));
+    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_count_by, grid_for(L.A.rows, 256), 256, 0, L.A.rows, L.agg.p, cnt.p);
+  }
+  L.cnt = std::move(cnt);
+  L.maxmem = maxmem;
   return BCS_OK;
 }
 
@@ -1040,9 +1088,12 @@ bcs_status build_transfer(Solver* s, int l, bool full) {
   if ((int)s->lv.size() <= l + 1) s->lv.emplace_back();
   Level& L = s->lv[l];
   Level& Lc = s->lv[l + 1];
-  if (full) BCS_OKR(members(s, L.A.rows, L.nagg, L.agg.p, L.mptr, L.mem));
+  if (full) {
+    BCS_OKR(members(s, L.A.rows, L.nagg, L.agg.p, L.cnt.p, L.maxmem, L.mptr, L.mem));
+    L.cnt.release();
+  }
   if (s->setup_cfg.pmode == BCS_P_TENTATIVE) {
-    if (full) BCS_OKR(tent_pattern(s, L.A, L.nagg, L.agg.p, L.mptr.p, L.mem.p, Lc.A, L.tent));
+    if (full) BCS_OKR(tent_pattern(s, L.A, L.nagg, L.agg.p, L.mptr.p, L.mem.p, L.maxmem, Lc.A, L.tent));
     BCS_OKR(tent_values(s, L.A, L.tent, Lc.A));
   } else {
     BCS_OKR(smoothed_prolongation(s, L, full));
@@ -1055,7 +1106,15 @@ bcs_status build_transfer(Solver* s, int l, bool full) {
 
 }  // namespace
 
+bcs_status amg_setup_levels(Solver* s, bool full);
+
 bcs_status amg_setup(Solver* s, bool full) {
+  const bcs_status st = amg_setup_levels(s, full);
+  s->nrm0_fresh = false;  // the norms belong to these values only
+  return st;
+}
+
+bcs_status amg_setup_levels(Solver* s, bool full) {
   const bcs_config& cfg = s->setup_cfg;
   if (full) {
     s->lv.resize(1);
@@ -1065,20 +1124,25 @@ bcs_status amg_setup(Solver* s, bool full) {
     L0.coarse_kind = -1;
   }
   BCS_CU(s, cudaMemsetAsync(s->flag.p, 0, 4 * sizeof(int32_t), s->stream));
+  // With block Jacobi, a singular diagonal block leaves only garbage values
+  // behind (no index depends on them), so the flags are read once, at the
+  // end; the multicolour factorisations read them per level.
+  const bool dilu = cfg.precond == BCS_PC_SGS || (cfg.precond == BCS_PC_AMG && cfg.smoother != BCS_SMOOTH_JACOBI);
   for (int l = 0;; ++l) {
     Level& L = s->lv[l];
     BCS_OKR(block_inverses(s, L, full));
-    bool singular = false;
-    BCS_OKR(check_flags(s, &singular));
-    if (singular) return s->fail(BCS_SINGULAR_BLOCK, "singular diagonal block at level " + std::to_string(l));
-    if (cfg.precond == BCS_PC_SGS || (cfg.precond == BCS_PC_AMG && cfg.smoother != BCS_SMOOTH_JACOBI))
+    if (dilu) {
+      bool singular = false;
+      BCS_OKR(check_flags(s, &singular));
+      if (singular) return s->fail(BCS_SINGULAR_BLOCK, "singular diagonal block at level " + std::to_string(l));
       BCS_OKR(dilu_setup(s, L, full, cfg.precond == BCS_PC_SGS || cfg.smoother == BCS_SMOOTH_SGS));
+    }
     bool last;
     if (full) {
       const int C = L.A.rows;
       last = C <= cfg.coarse_size || l == cfg.max_levels - 1 || cfg.precond != BCS_PC_AMG;
       if (!last) {
-        BCS_OKR(aggregate_level(s, L));
+        BCS_OKR(aggregate_level(s, L, l == 0 && s->nrm0_fresh ? s->nrm0.p : nullptr));
         if (L.nagg >= C || (double)L.nagg > cfg.max_coarsen_ratio * C) {
           last = true;
           L.agg.release();
@@ -1096,9 +1160,6 @@ bcs_status amg_setup(Solver* s, bool full) {
       } else if ((long long)Lf.A.rows * s->n <= cfg.coarse_dense_max) {
         Lf.coarse_kind = 0;
         BCS_OKR(coarse_inverse(s, Lf));
-        bool sing = false;
-        BCS_OKR(check_flags(s, &sing));
-        if (sing) return s->fail(BCS_SINGULAR_BLOCK, "singular coarsest-level matrix");
       } else {
         Lf.coarse_kind = 1;
         s->cinv.release();
@@ -1109,6 +1170,11 @@ bcs_status amg_setup(Solver* s, bool full) {
     L.coarse_kind = -1;
     BCS_OKR(build_transfer(s, l, full));
   }
+  int32_t h = 0;
+  BCS_OKR(read_int(s, s->flag.p, &h));
+  if (h & 4) return s->fail(BCS_EINVAL, "a block row has no diagonal block");
+  if (h & 8) return s->fail(BCS_SINGULAR_BLOCK, "singular diagonal block");
+  if (h & 16) return s->fail(BCS_SINGULAR_BLOCK, "singular coarsest-level matrix");
   return BCS_OK;
 }
 

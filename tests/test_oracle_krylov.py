@@ -217,3 +217,26 @@ def test_bicgstab_iterates_match_scipy(case, precond):
         ro, rsc = np.linalg.norm(b - A @ xs[k]) / bn, np.linalg.norm(b - A @ sx[k]) / bn
         if rsc > 1e-7:
             assert ro == pytest.approx(rsc, rel=1e-8), k
+
+
+def test_openmp_build_gives_identical_results():
+    """The OpenMP build of the oracle (used as the all-cores CPU baseline)
+    splits only loops with disjoint outputs, so its solves equal the
+    single-threaded build's bit for bit."""
+    sys = synth.density(10, seed=3)
+    bsr = oracle.ldu_to_bsr(sys)
+    outs = []
+    try:
+        for omp in (False, True):
+            oracle.use_openmp(omp)
+            row = []
+            for solver in (0, 1):
+                cfg = oracle.config(solver=solver)
+                x, res, _ = oracle.solve(bsr, sys["b"], cfg=cfg)
+                assert res["status"] == 0
+                row.append((x, res["iters"]))
+            outs.append(row)
+    finally:
+        oracle.use_openmp(False)
+    for (xa, ia), (xb, ib) in zip(*outs):
+        assert ia == ib and np.array_equal(xa, xb)
