@@ -597,17 +597,26 @@ def run_system(args):
     from paper_2403_07882_b300 import bcs, synth
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    # (label, solver, AMG precision, reorder, extra options, preconditioner label)
+    jac, dilu, sgs = dict(), dict(smoother=bcs.BCS_SMOOTH_DILU), dict(precond=bcs.BCS_PC_SGS, maxiter=5000)
     if args.workload == "density16":
         system, n = synth.density(16, seed=0), 5
         name = "density-based 16^3 5x5 (4,096 cells), seed 0"
-        runs = [("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32, 0), ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP64, 0)]
+        runs = [("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32, 0, jac), ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP64, 0, jac),
+                ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32, 0, dilu),
+                ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32, 0, sgs)]
     else:
         system, n = synth.pressure(64, seed=1), 4
         name = "pressure-based 64^3 4x4 (262,144 cells), permuted numbering, seed 1"
         # with and without the internal reverse Cuthill-McKee renumbering
-        runs = [("bicgstab", bcs.BCS_BICGSTAB, bcs.BCS_PREC_FP32, 0), ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32, 0),
-                ("bicgstab", bcs.BCS_BICGSTAB, bcs.BCS_PREC_FP64, 0),
-                ("bicgstab", bcs.BCS_BICGSTAB, bcs.BCS_PREC_FP32, 1), ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32, 1)]
+        runs = [("bicgstab", bcs.BCS_BICGSTAB, bcs.BCS_PREC_FP32, 0, jac),
+                ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32, 0, jac),
+                ("bicgstab", bcs.BCS_BICGSTAB, bcs.BCS_PREC_FP64, 0, jac),
+                ("bicgstab", bcs.BCS_BICGSTAB, bcs.BCS_PREC_FP32, 1, jac),
+                ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32, 1, jac),
+                ("bicgstab", bcs.BCS_BICGSTAB, bcs.BCS_PREC_FP32, 0, dilu),
+                ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32, 0, dilu),
+                ("fgmres", bcs.BCS_FGMRES, bcs.BCS_PREC_FP32, 0, sgs)]
     keys = ("owner", "neighbour", "diag", "upper", "lower", "b")
     d = {k: torch.from_numpy(system[k]).to(dev) for k in keys}
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -615,10 +624,10 @@ def run_system(args):
     out = []
     C, F = system["n_cells"], system["n_faces"]
     spmv_bytes = 8.0 * n * n * (C + 2 * F) + 4.0 * (C + 2 * F) + 4.0 * (C + 1) + 16.0 * n * C
-    for label, solver, prec, reorder in runs:
+    for label, solver, prec, reorder, extra in runs:
         setup, resetup, solve, total, iters, launches, spmv_ms = [], [], [], [], [], [], []
         for rep in range(args.warmup + args.steps):
-            with bcs.Solver(n, solver=solver, precision=prec, reorder=reorder) as s:
+            with bcs.Solver(n, solver=solver, precision=prec, reorder=reorder, **extra) as s:
                 x = torch.zeros_like(d["b"])
                 torch.cuda.synchronize()
                 e = [ev() for _ in range(5)]
@@ -646,7 +655,10 @@ def run_system(args):
                     iters.append(res["iters"])
                     launches.append(nl)
                     spmv_ms.append(e[3].elapsed_time(e[4]) / 10)
-        out.append({"solver": label, "amg_precision": pnames[prec], "rcm_reorder": bool(reorder),
+        pc = ("multicolour block SGS (no AMG)" if extra.get("precond") == bcs.BCS_PC_SGS else
+              "AMG, multicolour block DILU smoother" if extra.get("smoother") == bcs.BCS_SMOOTH_DILU else
+              "AMG, block-Jacobi smoother")
+        out.append({"solver": label, "preconditioner": pc, "amg_precision": pnames[prec], "rcm_reorder": bool(reorder),
                     "spmv_fp64_ms": statistics.median(spmv_ms),
                     "spmv_fp64_GBps": spmv_bytes / (statistics.median(spmv_ms) * 1e-3) / 1e9,
                     "time_to_1e-8_ms": statistics.median(total), "setup_ms": statistics.median(setup),
@@ -697,6 +709,27 @@ def run_knn(args):
             its.append(res["iters"])
         out.update({"resetup_ms_mean": statistics.mean(rs), "solve_ms_mean": statistics.mean(ss),
                     "iters": its, "resetup_over_full_setup": statistics.mean(rs) / out["full_setup_ms"]})
+    # the smoother / preconditioner comparison on the last system: full setup
+    # and solve to 1e-8 with block Jacobi, DILU and the SGS preconditioner
+    vals = [torch.from_numpy(system[k]).to(dev) for k in ("diag", "upper", "lower")]
+    cmp_ = {}
+    for label, extra in (("block_jacobi_amg", {}), ("dilu_amg", dict(smoother=bcs.BCS_SMOOTH_DILU)),
+                         ("sgs_no_amg", dict(precond=bcs.BCS_PC_SGS, maxiter=5000))):
+        times = []
+        for rep in range(2):
+            with bcs.Solver(5, precision=bcs.BCS_PREC_FP32, **extra) as s2:
+                s2.set_structure(system["n_cells"], d["owner"], d["neighbour"])
+                x2 = torch.zeros_like(d["b"])
+                torch.cuda.synchronize()
+                a, b_, c_ = ev(), ev(), ev()
+                a.record(); s2.set_values(*vals); b_.record(); _, st, res = s2.solve(d["b"], x2); c_.record()
+                torch.cuda.synchronize()
+                assert st == bcs.BCS_OK, res
+                times.append((a.elapsed_time(b_), b_.elapsed_time(c_), res["iters"]))
+        setup_ms, solve_ms, it = times[-1]
+        cmp_[label] = {"setup_ms": setup_ms, "solve_ms": solve_ms, "time_to_1e-8_ms": setup_ms + solve_ms,
+                       "iters": it}
+    out["smoother_comparison"] = cmp_
     print(json.dumps({"impl": "native", "mode": "knn", **out}), flush=True)
 
 
@@ -806,7 +839,12 @@ def run_serve(args):
                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                     "mean_ms": float(lat.mean()), "iters_max": int(max(iters)),
                     "evictions": stats["evictions"], "rejected": stats["rejected"],
-                    "resident_bytes": stats["resident_bytes"], "budget_bytes": stats["budget_bytes"]}
+                    "resident_bytes": stats["resident_bytes"], "budget_bytes": stats["budget_bytes"],
+                    "gpu_timeline": {"window_ms": stats["window_ms"], "busy_frac": stats["busy_frac"],
+                                     "overlap2_frac": stats["overlap_frac"],
+                                     "mean_requests_in_flight": stats["mean_in_flight"],
+                                     "how": "per request: CUDA events on its case's stream before the "
+                                            "resetup and after the solve"}}
 
         n_req, n_warm = args.serve_requests, args.serve_warmup
         configured = run(args.serve_rate, n_warm + n_req, n_warm, 5)

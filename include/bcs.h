@@ -342,6 +342,13 @@ typedef struct bcs_server_stats {
   size_t resident_bytes, budget_bytes;
   int resident_cases;
   double p50_ms, p99_ms, mean_ms;   /* submit -> completion latency */
+  /* GPU timeline since the last reset: each request's interval runs from an
+   * event recorded on its case's stream before the resetup to one recorded
+   * after the solve. window_ms: first start to last end; busy_frac: share
+   * of the window covered by at least one request; overlap_frac: share
+   * covered by two or more (their kernels in flight together);
+   * mean_in_flight: summed interval lengths over the window. */
+  double window_ms, busy_frac, overlap_frac, mean_in_flight;
 } bcs_server_stats;
 
 /* budget_bytes = 0: 80 % of the device's free memory. slots: 1..64. cfg may

@@ -64,7 +64,9 @@ class bcs_server_stats(ct.Structure):
     _fields_ = [("submitted", ct.c_longlong), ("completed", ct.c_longlong), ("rejected", ct.c_longlong),
                 ("evictions", ct.c_longlong), ("admissions", ct.c_longlong), ("queued", ct.c_longlong),
                 ("resident_bytes", ct.c_size_t), ("budget_bytes", ct.c_size_t), ("resident_cases", ct.c_int),
-                ("p50_ms", ct.c_double), ("p99_ms", ct.c_double), ("mean_ms", ct.c_double)]
+                ("p50_ms", ct.c_double), ("p99_ms", ct.c_double), ("mean_ms", ct.c_double),
+                ("window_ms", ct.c_double), ("busy_frac", ct.c_double), ("overlap_frac", ct.c_double),
+                ("mean_in_flight", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

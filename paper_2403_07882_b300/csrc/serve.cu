@@ -49,6 +49,7 @@ struct Case {
   std::vector<int32_t> owner, neighbour;
   bcs_solver* solver = nullptr;
   cudaStream_t stream = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;  // a request's start / end on the stream
   bool busy = false;
   size_t bytes = 0;        // measured device footprint (0 until first admission)
   size_t estimate = 0;     // footprint estimate before the first admission
@@ -70,6 +71,9 @@ struct bcs_server {
   uint64_t clock = 0;
   long long submitted = 0, completed = 0, rejected = 0, evictions = 0, admissions = 0;
   std::vector<double> latencies;
+  std::vector<std::pair<double, double>> spans;  // request intervals on the GPU timeline (ms from t0)
+  cudaEvent_t t0 = nullptr;                       // reference of the timeline, recorded at create / reset
+  cudaStream_t tstream = nullptr;
   std::vector<std::thread> workers;
   int device = 0;
 };
@@ -92,12 +96,48 @@ size_t estimate_bytes(const Case& c, const bcs_config& cfg) {
   return (size_t)(levels + index + krylov + 1.5 * N * 16.0);
 }
 
-void release_case(bcs_server* srv, Case& c) {
+void drop_device_state(Case& c) {
   if (c.solver) bcs_destroy(c.solver);
+  if (c.ev_a) cudaEventDestroy(c.ev_a);
+  if (c.ev_b) cudaEventDestroy(c.ev_b);
   if (c.stream) cudaStreamDestroy(c.stream);
   c.solver = nullptr;
   c.stream = nullptr;
+  c.ev_a = c.ev_b = nullptr;
+}
+
+void release_case(bcs_server* srv, Case& c) {
+  drop_device_state(c);
   srv->resident -= c.bytes;
+}
+
+// Time covered by at least one / at least two of the intervals, and their
+// summed length.
+void coverage(std::vector<std::pair<double, double>> sp, double* lo, double* hi, double* one, double* two,
+              double* sum) {
+  *lo = *hi = *one = *two = *sum = 0.0;
+  if (sp.empty()) return;
+  std::vector<std::pair<double, int>> ev;
+  ev.reserve(2 * sp.size());
+  *lo = sp[0].first;
+  *hi = sp[0].second;
+  for (const auto& s : sp) {
+    ev.push_back({s.first, +1});
+    ev.push_back({s.second, -1});
+    *lo = std::min(*lo, s.first);
+    *hi = std::max(*hi, s.second);
+    *sum += s.second - s.first;
+  }
+  std::sort(ev.begin(), ev.end());
+  int depth = 0;
+  double prev = ev[0].first;
+  for (const auto& e : ev) {
+    const double dt = e.first - prev;
+    if (depth >= 1) *one += dt;
+    if (depth >= 2) *two += dt;
+    depth += e.second;
+    prev = e.first;
+  }
 }
 
 // Called with the lock held. Returns true when the case is (or can be made)
@@ -177,24 +217,34 @@ void worker(bcs_server* srv) {
     bcs_status st = BCS_OK;
     if (fresh) {
       st = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) == cudaSuccess ? BCS_OK : BCS_ECUDA;
+      if (st == BCS_OK && (cudaEventCreate(&c.ev_a) != cudaSuccess || cudaEventCreate(&c.ev_b) != cudaSuccess))
+        st = BCS_ECUDA;
       if (st == BCS_OK) st = bcs_create(&c.solver, c.n, &srv->cfg, c.stream);
       if (st == BCS_OK)
         st = bcs_set_structure(c.solver, c.C, c.F, c.owner.data(), c.neighbour.data(), BCS_MEM_HOST);
     }
+    const bool timed = st == BCS_OK && cudaEventRecord(c.ev_a, c.stream) == cudaSuccess;
     if (st == BCS_OK) st = bcs_set_values(c.solver, r.diag, r.upper, r.lower, r.mem);
     if (st == BCS_OK) st = bcs_solve(c.solver, r.b, r.x, r.mem, &res);
     res.status = st;
+    const bool span_ok = timed && st != BCS_ECUDA && cudaEventRecord(c.ev_b, c.stream) == cudaSuccess &&
+                         cudaEventSynchronize(c.ev_b) == cudaSuccess;
     const size_t actual = c.solver ? bcs_device_bytes(c.solver) : 0;
 
     lk.lock();
+    if (span_ok) {
+      float a = 0.f, b = 0.f;
+      if (cudaEventElapsedTime(&a, srv->t0, c.ev_a) == cudaSuccess &&
+          cudaEventElapsedTime(&b, srv->t0, c.ev_b) == cudaSuccess && b > 0.f)
+        srv->spans.push_back({std::max(0.f, a), b});
+      else
+        (void)cudaGetLastError();
+    }
     if (st == BCS_ECUDA || st == BCS_ENOMEM || st == BCS_SINGULAR_BLOCK || st == BCS_EINVAL) {
       // drop the case's device state; a later request rebuilds it
       srv->resident -= c.bytes;
       c.bytes = 0;
-      if (c.solver) bcs_destroy(c.solver);
-      if (c.stream) cudaStreamDestroy(c.stream);
-      c.solver = nullptr;
-      c.stream = nullptr;
+      drop_device_state(c);
     } else if (actual) {
       srv->resident = srv->resident - c.bytes + actual;
       c.bytes = actual;
@@ -245,6 +295,15 @@ BCS_API bcs_status bcs_server_create(bcs_server** out, size_t budget_bytes, int 
     budget_bytes = (size_t)(0.8 * (double)freeb);
   }
   srv->budget = budget_bytes;
+  if (cudaStreamCreateWithFlags(&srv->tstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&srv->t0) != cudaSuccess || cudaEventRecord(srv->t0, srv->tstream) != cudaSuccess ||
+      cudaEventSynchronize(srv->t0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (srv->t0) cudaEventDestroy(srv->t0);
+    if (srv->tstream) cudaStreamDestroy(srv->tstream);
+    delete srv;
+    return BCS_ECUDA;
+  }
   for (int i = 0; i < slots; ++i) srv->workers.emplace_back(worker, srv);
   *out = srv;
   return BCS_OK;
@@ -259,6 +318,8 @@ BCS_API bcs_status bcs_server_destroy(bcs_server* srv) {
   srv->work_cv.notify_all();
   for (auto& t : srv->workers) t.join();
   for (auto& c : srv->cases) release_case(srv, *c);
+  cudaEventDestroy(srv->t0);
+  cudaStreamDestroy(srv->tstream);
   delete srv;
   return BCS_OK;
 }
@@ -340,6 +401,14 @@ BCS_API bcs_status bcs_server_get_stats(bcs_server* srv, bcs_server_stats* st) {
     for (double v : l) s += v;
     st->mean_ms = s / l.size();
   }
+  double lo, hi, one, two, sum;
+  coverage(srv->spans, &lo, &hi, &one, &two, &sum);
+  st->window_ms = hi - lo;
+  if (hi > lo) {
+    st->busy_frac = one / (hi - lo);
+    st->overlap_frac = two / (hi - lo);
+    st->mean_in_flight = sum / (hi - lo);
+  }
   return BCS_OK;
 }
 
@@ -347,7 +416,10 @@ BCS_API bcs_status bcs_server_reset_stats(bcs_server* srv) {
   if (!srv) return BCS_EINVAL;
   std::lock_guard<std::mutex> lk(srv->mu);
   srv->latencies.clear();
+  srv->spans.clear();
   srv->submitted = srv->completed = srv->rejected = srv->evictions = srv->admissions = 0;
+  if (cudaEventRecord(srv->t0, srv->tstream) != cudaSuccess || cudaEventSynchronize(srv->t0) != cudaSuccess)
+    return BCS_ECUDA;
   return BCS_OK;
 }
 

@@ -128,3 +128,34 @@ def test_device_inputs_match_host_inputs():
         for j in range(2):
             assert np.array_equal(out[("host", c, j)], out[("device", c, j)])
             assert true_rel(seqs[c][j], out[("host", c, j)]) <= 1e-8
+
+
+def test_gpu_timeline_statistics():
+    """The server's GPU-timeline statistics: one slot gives requests that
+    never overlap (overlap share 0, at most one in flight on average);
+    several slots over several cases put two or more requests' kernels in
+    flight together for part of the window."""
+    systems = [synth.density(14, seed=1), synth.pressure(12, seed=2), synth.density(13, 11, 9, seed=3),
+               synth.pressure(11, 10, 9, seed=5)]
+    dev = "cuda:0"
+    data = [{k: torch.from_numpy(s[k]).to(dev) for k in ("diag", "upper", "lower", "b")} for s in systems]
+    for slots in (1, 4):
+        with bcs.Server(slots=slots) as srv:
+            ids = [srv.register(s) for s in systems]
+            # warm-up: first admission (full setup) of every case
+            for t in [srv.submit(i, d) for i, d in zip(ids, data)]:
+                assert srv.wait(t)[0] == bcs.BCS_OK
+            srv.reset_stats()
+            tickets = [srv.submit(ids[k % 4], data[k % 4]) for k in range(16)]
+            for t in tickets:
+                assert srv.wait(t)[0] == bcs.BCS_OK
+            st = srv.stats()
+        assert st["completed"] == 16 and st["window_ms"] > 0
+        assert 0.0 < st["busy_frac"] <= 1.0 + 1e-9
+        assert st["overlap_frac"] <= st["busy_frac"] + 1e-9
+        if slots == 1:
+            assert st["overlap_frac"] == 0.0 and st["mean_in_flight"] <= 1.0 + 1e-9
+        else:
+            assert st["overlap_frac"] > 0.0 and st["mean_in_flight"] > 1.0
+        print(f"slots={slots}: window {st['window_ms']:.1f} ms busy {st['busy_frac']:.3f} "
+              f"overlap {st['overlap_frac']:.3f} in flight {st['mean_in_flight']:.2f}")
