@@ -113,6 +113,12 @@ typedef struct bcs_config {
                               reverse Cuthill-McKee order for locality (vectors, LDU arrays and
                               results stay in the caller's numbering; bcs_get_permutation);
                               0 (default) = keep the caller's numbering */
+  int tail_rows;           /* FP32 / BF16 V-cycle with block Jacobi and tentative P: the levels
+                              of at most tail_rows block rows (and all coarser ones) run as one
+                              thread-block-cluster launch per cycle instead of a launch per
+                              sweep, residual and transfer (identical results); read at each
+                              set_values; 0 (default) = off: measured on B300, the graph-replayed
+                              separate launches are faster */
   /* Device memory, read by bcs_create (later changes are ignored): with alloc
      and release both set, every device buffer of the solver comes from
      alloc(bytes, stream, alloc_user) and goes back through release(ptr,

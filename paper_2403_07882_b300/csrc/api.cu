@@ -116,6 +116,7 @@ bcs_status check_config(const bcs_config* c) {
   if (c->precision < BCS_PREC_FP64 || c->precision > BCS_PREC_BF16) return BCS_EINVAL;
   if (c->cycle_graph < -1 || c->cycle_graph > 1) return BCS_EINVAL;
   if (c->reorder < 0 || c->reorder > 1) return BCS_EINVAL;
+  if (c->tail_rows < 0) return BCS_EINVAL;
   if ((c->alloc == nullptr) != (c->release == nullptr)) return BCS_EINVAL;
   if (c->slice_layout < -1 || c->slice_layout > 1) return BCS_EINVAL;
   if (c->smoother < BCS_SMOOTH_JACOBI || c->smoother > BCS_SMOOTH_SGS) return BCS_EINVAL;
@@ -203,6 +204,7 @@ bcs_status bcs_config_default(bcs_config* c) {
   c->slice_layout = -1;
   c->cycle_graph = -1;
   c->reorder = 0;
+  c->tail_rows = 0;
   return BCS_OK;
 }
 

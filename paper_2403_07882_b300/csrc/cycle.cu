@@ -13,6 +13,8 @@
 // first from x = 0 is x = w D^-1 b), residual, restriction R = P^T,
 // recursion, prolongation-correction, nu2 sweeps; the coarsest level applies
 // its dense FP64 inverse (or smoother sweeps when too large for one).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <array>
 #include <map>
@@ -186,32 +188,32 @@ __global__ void k_slice_fill(int rows, int nslices, const int32_t* __restrict__ 
 __device__ __forceinline__ float ldsv(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldsv(const bf16* p) { return __bfloat162float(__ldg(p)); }
 
-// JACOBI: y = x + omega D^-1 (b - A x); otherwise y = b - A x. Same fma order
-// as k_jacobi / k_rows (blocks in row order, columns ascending). Steps are
-// consumed in chunks of SELL_U: the chunk's column indices are loaded
-// together, then the x components they select, then the values, so a warp
-// keeps several HBM round trips in flight instead of one per step; the
-// epilogue's operands are loaded before the row loop.
-constexpr int SELL_U = 4;
+constexpr int SELL_U = 4;  // steps per chunk of the lane-per-row kernels
 
-template <int N, class TV, bool JACOBI>
-__global__ void __launch_bounds__(128) k_sell(int rows, int nslices, const int32_t* __restrict__ rp,
-                                              const int32_t* __restrict__ sptr, const int32_t* __restrict__ sci,
-                                              const TV* __restrict__ sv, const float* __restrict__ dinv,
-                                              const float* __restrict__ x, const float* __restrict__ b,
-                                              float* __restrict__ y, float omega) {
+// Vector loads: the read-only path for vectors that no other block of the
+// same launch writes; the L2 path (coherent across the SMs of a cluster) in
+// the coarse-tail kernel, where earlier phases of the same launch wrote them.
+template <bool COH>
+__device__ __forceinline__ float ldvec(const float* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+
+template <int N, class TV, bool JACOBI, bool COH>
+__device__ __forceinline__ void sell_slice(int sl, int rows, const int32_t* __restrict__ rp,
+                                           const int32_t* __restrict__ sptr, const int32_t* __restrict__ sci,
+                                           const TV* __restrict__ sv, const float* __restrict__ dinv,
+                                           const float* x, const float* b, float* y, float omega) {
   constexpr int RPW = 32 / N, NN = N * N, TILE = NN * RPW;
   const int lane = threadIdx.x & 31;
   const int rw = lane / N, r = lane - rw * N;
-  const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  if (sl >= nslices) return;  // uniform across the warp
   const int i = sl * RPW + rw;
   const bool active = rw < RPW && i < rows;
   const size_t o = (size_t)i * N + r;
-  const float bo = active ? __ldg(b + o) : 0.f;
+  const float bo = active ? ldvec<COH>(b + o) : 0.f;
   float xo = 0.f, d[N];
   if (JACOBI) {
-    xo = active ? x[o] : 0.f;
+    xo = active ? (COH ? __ldcg(x + o) : x[o]) : 0.f;
 #pragma unroll
     for (int c = 0; c < N; ++c) d[c] = active ? __ldg(dinv + o * N + c) : 0.f;
   }
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(128) k_sell(int rows, int nslices, const int32
       j[u] = live ? __ldg(sci + (size_t)(t0 + k0 + u) * RPW + rw) : 0;
     }
 #pragma unroll
-    for (int u = 0; u < SELL_U; ++u) xv[u] = (active && k0 + u < len) ? __ldg(x + (size_t)j[u] * N + r) : 0.f;
+    for (int u = 0; u < SELL_U; ++u) xv[u] = (active && k0 + u < len) ? ldvec<COH>(x + (size_t)j[u] * N + r) : 0.f;
 #pragma unroll
     for (int u = 0; u < SELL_U; ++u) {
       const TV* tile = sv + (size_t)(t0 + k0 + u) * TILE;
@@ -253,7 +255,24 @@ __global__ void __launch_bounds__(128) k_sell(int rows, int nslices, const int32
     const float rc = __shfl_sync(0xffffffffu, res, (rw * N + c) & 31);
     if (active) tt = fmaf(d[c], rc, tt);
   }
-  if (active) y[o] = xo + omega * tt;
+  if (active) y[o] = fmaf(omega, tt, xo);
+}
+
+// JACOBI: y = x + omega D^-1 (b - A x); otherwise y = b - A x. Same fma order
+// as k_jacobi / k_rows (blocks in row order, columns ascending). Steps are
+// consumed in chunks of SELL_U: the chunk's column indices are loaded
+// together, then the x components they select, then the values, so a warp
+// keeps several HBM round trips in flight instead of one per step; the
+// epilogue's operands are loaded before the row loop.
+template <int N, class TV, bool JACOBI>
+__global__ void __launch_bounds__(128) k_sell(int rows, int nslices, const int32_t* __restrict__ rp,
+                                              const int32_t* __restrict__ sptr, const int32_t* __restrict__ sci,
+                                              const TV* __restrict__ sv, const float* __restrict__ dinv,
+                                              const float* __restrict__ x, const float* __restrict__ b,
+                                              float* __restrict__ y, float omega) {
+  const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (sl >= nslices) return;  // uniform across the warp
+  sell_slice<N, TV, JACOBI, false>(sl, rows, rp, sptr, sci, sv, dinv, x, b, y, omega);
 }
 
 // ---- thread-per-block-row layout (smap = 1) ---------------------------------
@@ -436,7 +455,7 @@ __global__ void __launch_bounds__(128, TPR_MINB) k_tpr(int rows, int nslices, co
     float tt = 0.f;
 #pragma unroll
     for (int c = 0; c < N; ++c) tt = fmaf(__ldg(dinv + (o + r) * N + c), res[c], tt);
-    y[o + r] = xo + omega * tt;
+    y[o + r] = fmaf(omega, tt, xo);
   }
 }
 
@@ -461,32 +480,59 @@ __global__ void __launch_bounds__(128) k_jacobi(int rows, const int32_t* __restr
   }
 }
 
-// y = omega D^-1 b (first sweep from a zero guess)
+// y = omega D^-1 b (first sweep from a zero guess), element t = (i, r)
+template <int N, class AT, class TD, class TC, bool COH>
+__device__ __forceinline__ void jacobi0_elem(size_t t, const TD* __restrict__ dinv, const TC* b, TC* y, AT omega) {
+  const size_t i = t / N;
+  const int r = (int)(t - i * N);
+  AT acc = 0;
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    AT bc;
+    if constexpr (COH) bc = (AT)__ldcg(b + i * N + c);
+    else bc = (AT)b[i * N + c];
+    acc = fma((AT)dinv[(i * N + r) * N + c], bc, acc);
+  }
+  y[t] = (TC)(omega * acc);
+}
+
 template <int N, class AT, class TD, class TC>
 __global__ void k_jacobi0(int rows, const TD* __restrict__ dinv, const TC* __restrict__ b, TC* __restrict__ y,
                           AT omega) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= (size_t)rows * N) return;
-  const size_t i = t / N;
-  const int r = (int)(t - i * N);
-  AT acc = 0;
-#pragma unroll
-  for (int c = 0; c < N; ++c) acc = fma((AT)dinv[(i * N + r) * N + c], (AT)b[i * N + c], acc);
-  y[t] = (TC)(omega * acc);
+  jacobi0_elem<N, AT, TD, TC, false>(t, dinv, b, y, omega);
 }
 
 // Tentative transfers: restriction b_c[I] = sum of r over I's members
 // (ascending), prolongation-correction x[i] += x_c[agg[i]].
+template <int N, class AT, class TC, bool COH>
+__device__ __forceinline__ void restrict_elem(size_t t, const int32_t* __restrict__ mptr,
+                                              const int32_t* __restrict__ mem, const TC* r, TC* bc) {
+  const size_t I = t / N;
+  const int c = (int)(t - I * N);
+  AT acc = 0;
+  for (int q = mptr[I]; q < mptr[I + 1]; ++q) {
+    if constexpr (COH) acc += (AT)__ldcg(r + (size_t)mem[q] * N + c);
+    else acc += (AT)r[(size_t)mem[q] * N + c];
+  }
+  bc[t] = (TC)acc;
+}
+
 template <int N, class AT, class TC>
 __global__ void k_restrict_tent(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
                                 const TC* __restrict__ r, TC* __restrict__ bc) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= (size_t)nagg * N) return;
-  const size_t I = t / N;
-  const int c = (int)(t - I * N);
-  AT acc = 0;
-  for (int q = mptr[I]; q < mptr[I + 1]; ++q) acc += (AT)r[(size_t)mem[q] * N + c];
-  bc[t] = (TC)acc;
+  restrict_elem<N, AT, TC, false>(t, mptr, mem, r, bc);
+}
+
+template <int N, class TC, bool COH>
+__device__ __forceinline__ void prolong_elem(size_t t, const int32_t* __restrict__ agg, const TC* xc, TC* x) {
+  const size_t i = t / N;
+  const int c = (int)(t - i * N);
+  if constexpr (COH) x[t] = __ldcg(x + t) + __ldcg(xc + (size_t)agg[i] * N + c);
+  else x[t] = x[t] + xc[(size_t)agg[i] * N + c];
 }
 
 template <int N, class TC>
@@ -494,23 +540,31 @@ __global__ void k_prolong_tent(int rows, const int32_t* __restrict__ agg, const 
                                TC* __restrict__ x) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= (size_t)rows * N) return;
-  const size_t i = t / N;
-  const int c = (int)(t - i * N);
-  x[t] = x[t] + xc[(size_t)agg[i] * N + c];
+  prolong_elem<N, TC, false>(t, agg, xc, x);
 }
 
 // Coarsest level: x = Ainv b with the dense FP64 inverse, warp per row.
+template <class TC, bool COH>
+__device__ __forceinline__ void gemv_row(int row, int Nc, const double* __restrict__ inv, const TC* b, TC* x) {
+  const int lane = threadIdx.x & 31;
+  double acc = 0.0;
+  for (int c = lane; c < Nc; c += 32) {
+    double bc;
+    if constexpr (COH) bc = (double)__ldcg(b + c);
+    else bc = (double)b[c];
+    acc = fma(inv[(size_t)row * Nc + c], bc, acc);
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+  if (lane == 0) x[row] = (TC)acc;
+}
+
 template <class TC>
 __global__ void k_coarse_gemv(int Nc, const double* __restrict__ inv, const TC* __restrict__ b,
                               TC* __restrict__ x) {
   const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
   if (row >= Nc) return;
-  double acc = 0.0;
-  for (int c = lane; c < Nc; c += 32) acc = fma(inv[(size_t)row * Nc + c], (double)b[c], acc);
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
-  if (lane == 0) x[row] = (TC)acc;
+  gemv_row<TC, false>(row, Nc, inv, b, x);
 }
 
 template <class TI, class TO>
@@ -528,6 +582,69 @@ unsigned rows_grid(int rows, int n) {
   const int rpw = 32 / n;
   const size_t warps = ((size_t)rows + rpw - 1) / rpw;
   return grid_for(warps * 32, 128);
+}
+
+// ---- coarse tail: the V-cycle below a size threshold in one cluster launch ----
+// The levels from lv[tail_level] down are small enough that a launch per
+// sweep, residual and transfer is mostly launch latency. Their part of the
+// cycle runs instead as one launch of a thread-block cluster (8 or 16 SMs):
+// a list of phases, the same operations in the same order as the kernel by
+// kernel cycle launches (Cycle::run), with a cluster barrier between phases.
+// Every element is computed by the same device function as in the separate
+// kernels, so the results are identical bit for bit; vectors written by
+// earlier phases are read through L2 (ld.global.cg), which the cluster
+// barrier's release / acquire makes coherent across the cluster's SMs.
+namespace cg = cooperative_groups;
+
+constexpr int TAIL_THREADS = 512;
+
+template <int N, class TV>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail(const TailPhase* __restrict__ ph, int nph,
+                                                      const TailLevel* __restrict__ lvl, float* const* __restrict__ vec,
+                                                      const float* root_b, float* root_x, const double* __restrict__ cinv,
+                                                      int cN, float omega) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int nthr = (int)(cl.num_blocks() * blockDim.x);
+  const int g = (int)(cl.block_rank() * blockDim.x + threadIdx.x);
+  const int gw = g >> 5, nw = nthr >> 5;
+  auto V = [&](int id) -> float* {
+    return id < 0 ? nullptr : id == 0 ? const_cast<float*>(root_b) : id == 1 ? root_x : vec[id];
+  };
+  for (int p = 0; p < nph; ++p) {
+    const TailPhase f = ph[p];
+    const TailLevel& L = lvl[f.level];
+    const float* a = V(f.ia);
+    const float* b = V(f.ib);
+    float* y = V(f.iy);
+    switch (f.op) {
+      case T_JAC0:
+        for (size_t t = g; t < (size_t)L.rows * N; t += nthr)
+          jacobi0_elem<N, float, float, float, true>(t, L.dinv, b, y, omega);
+        break;
+      case T_SWEEP:
+        for (int sl = gw; sl < L.nslices; sl += nw)
+          sell_slice<N, TV, true, true>(sl, L.rows, L.rp, L.sptr, L.sci, (const TV*)L.sv, L.dinv, a, b, y, omega);
+        break;
+      case T_RESID:
+        for (int sl = gw; sl < L.nslices; sl += nw)
+          sell_slice<N, TV, false, true>(sl, L.rows, L.rp, L.sptr, L.sci, (const TV*)L.sv, nullptr, a, b, y, 0.f);
+        break;
+      case T_RESTRICT:
+        for (size_t t = g; t < (size_t)L.nagg * N; t += nthr)
+          restrict_elem<N, float, float, true>(t, L.mptr, L.mem, a, y);
+        break;
+      case T_PROLONG:
+        for (size_t t = g; t < (size_t)L.rows * N; t += nthr) prolong_elem<N, float, true>(t, L.agg, a, y);
+        break;
+      case T_GEMV:
+        for (int row = gw; row < cN; row += nw) gemv_row<float, true>(row, cN, cinv, b, y);
+        break;
+      default:  // T_ZERO
+        for (size_t t = g; t < (size_t)L.rows * N; t += nthr) y[t] = 0.f;
+        break;
+    }
+    cl.sync();
+  }
 }
 
 }  // namespace
@@ -731,8 +848,35 @@ struct Cycle {
                (k_jacobi0<N, AT, TD, TC>), grid_for((size_t)rows * N, 256), 256, 0, rows, dinv(L), b, x, (AT)1);
     return BCS_OK;
   }
+  // the levels from s->tail_level down as one cluster launch
+  template <int N>
+  bcs_status tail(const float* b, float* x) {
+    const TailPlan& T = s->tail;
+    cudaLaunchConfig_t lc{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = T.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.gridDim = dim3(T.cluster);
+    lc.blockDim = dim3(TAIL_THREADS);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = s->stream;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    const TailPhase* ph = (const TailPhase*)T.buf.p;
+    const TailLevel* lvl = (const TailLevel*)(T.buf.p + T.level_off);
+    float* const* vec = (float* const*)(T.buf.p + T.vec_off);
+    s->pre(K_SWEEP);
+    BCS_CU(s, cudaLaunchKernelEx(&lc, k_tail<N, TV>, ph, T.nph, lvl, vec, b, x, (const double*)s->cinv.p, s->cN,
+                                 (float)s->setup_cfg.jacobi_omega));
+    return s->post(K_SWEEP, "k_tail", T.bytes, T.flops);
+  }
+
   template <int N>
   bcs_status run(int l, const TC* b, TC* x) {
+    if constexpr (std::is_same<TC, float>::value)
+      if (l == s->tail_level) return tail<N>((const float*)b, (float*)x);
     Level& L = s->lv[l];
     const int nu1 = s->setup_cfg.nu1, nu2 = s->setup_cfg.nu2;
     TC* tmp = (TC*)L.vt.p;
@@ -977,8 +1121,9 @@ bcs_status choose_layout(Solver* s, Level& L, int prec, int* map) {
 
 // Layout of level L's sliced copy: kept, forced by the configuration, or
 // picked by the autotuner (which builds and times both).
-bcs_status slice_map(Solver* s, Level& L, int prec, int* map) {
+bcs_status slice_map(Solver* s, Level& L, int prec, bool tail, int* map) {
   *map = L.smap;
+  if (tail) *map = 0;  // the coarse-tail kernel walks the lane-per-row layout
   if (*map < 0) {
     if (s->setup_cfg.slice_layout >= 0) *map = s->setup_cfg.slice_layout;
     else BCS_OKR(choose_layout(s, L, prec, map));
@@ -988,6 +1133,166 @@ bcs_status slice_map(Solver* s, Level& L, int prec, int* map) {
 
 // Cycle vectors and storage copies of the hierarchy in the configured
 // precision (after every setup / resetup).
+// ---- coarse-tail plan ----------------------------------------------------------
+namespace {
+
+// The phases Cycle::run would launch for the levels from lt down, in order,
+// with the same buffer choices (vector ids: 0 / 1 the tail's b / x; per tail
+// level 2 + 4 (l - lt) + {vb, vx, vr, vt}).
+struct TailGen {
+  Solver* s;
+  int lt;
+  std::vector<TailPhase> ph;
+  double bytes = 0.0, flops = 0.0;
+  int id(int l, int k) const { return 2 + 4 * (l - lt) + k; }
+  void push(int op, int l, int ia, int ib, int iy) { ph.push_back(TailPhase{op, l - lt, ia, ib, iy}); }
+  void account(int op, const Level& L) {
+    const double n = s->n, nn = n * n, rows = L.A.rows, nnz = L.A.nnz;
+    const double vb = s->setup_cfg.precision == BCS_PREC_FP32 ? 4.0 : 2.0;
+    switch (op) {
+      case T_SWEEP: bytes += nnz * (nn * vb + 4) + 4 * (rows + 1) + rows * n * (n * 4 + 12); flops += 2 * (nnz + rows) * nn; break;
+      case T_RESID: bytes += nnz * (nn * vb + 4) + 4 * (rows + 1) + rows * n * 12; flops += 2 * nnz * nn; break;
+      case T_JAC0: bytes += rows * n * (n * 4 + 8); flops += 2 * rows * nn; break;
+      case T_RESTRICT: bytes += (rows + L.nagg) * n * 4 + 4 * rows; break;
+      case T_PROLONG: bytes += rows * n * 12 + 4 * rows; break;
+      case T_GEMV: bytes += 8.0 * s->cN * s->cN; flops += 2.0 * s->cN * s->cN; break;
+      default: bytes += rows * n * 4; break;
+    }
+  }
+  void op(int o, int l, int ia, int ib, int iy) {
+    push(o, l, ia, ib, iy);
+    account(o, s->lv[l]);
+  }
+  void gen(int l, int b, int x) {
+    const Level& L = s->lv[l];
+    const bcs_config& c = s->setup_cfg;
+    if (L.coarse_kind == 0) {
+      op(T_GEMV, l, -1, b, x);
+      return;
+    }
+    const int tmp = id(l, 3);
+    if (L.coarse_kind == 1) {  // Cycle::sweeps_from_zero
+      const int count = c.coarse_sweeps;
+      int cur = ((count - 1) % 2 == 0) ? x : tmp, alt = cur == x ? tmp : x;
+      op(T_JAC0, l, -1, b, cur);
+      for (int k = 1; k < count; ++k) {
+        op(T_SWEEP, l, cur, b, alt);
+        std::swap(cur, alt);
+      }
+      return;
+    }
+    const int swaps = (c.nu1 > 1 ? c.nu1 - 1 : 0) + c.nu2;
+    int cur = swaps % 2 == 0 ? x : tmp, alt = cur == x ? tmp : x;
+    if (c.nu1 >= 1) {
+      op(T_JAC0, l, -1, b, cur);
+      for (int k = 1; k < c.nu1; ++k) {
+        op(T_SWEEP, l, cur, b, alt);
+        std::swap(cur, alt);
+      }
+    } else {
+      op(T_ZERO, l, -1, -1, cur);
+    }
+    const int r = id(l, 2);
+    op(T_RESID, l, cur, b, r);
+    op(T_RESTRICT, l, r, -1, id(l + 1, 0));
+    gen(l + 1, id(l + 1, 0), id(l + 1, 1));
+    op(T_PROLONG, l, id(l + 1, 1), -1, cur);
+    for (int k = 0; k < c.nu2; ++k) {
+      op(T_SWEEP, l, cur, b, alt);
+      std::swap(cur, alt);
+    }
+  }
+};
+
+// Largest cluster (16, else 8 SMs) that can be resident for the tail kernel.
+template <int N, class TV>
+bcs_status tail_cluster(Solver* s, int* cluster) {
+  *cluster = 0;
+  for (int cs : {16, 8}) {
+    if (cs > 8 &&
+        cudaFuncSetAttribute(k_tail<N, TV>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t lc{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.gridDim = dim3(cs);
+    lc.blockDim = dim3(TAIL_THREADS);
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k_tail<N, TV>, &lc) == cudaSuccess && nc >= 1) {
+      *cluster = cs;
+      return BCS_OK;
+    }
+    (void)cudaGetLastError();
+  }
+  return BCS_OK;
+}
+
+}  // namespace
+
+// Phase list, level table and vector table of the coarse tail, in one device
+// buffer; the tail is switched off when no cluster of 8 fits.
+bcs_status build_tail(Solver* s) {
+  const int lt = s->tail_level, nl = (int)s->lv.size();
+  int cluster = 0;
+  BCS_OKR(with_n(s->n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    return s->setup_cfg.precision == BCS_PREC_FP32 ? tail_cluster<N, float>(s, &cluster)
+                                                   : tail_cluster<N, bf16>(s, &cluster);
+  }));
+  if (cluster == 0) {
+    s->tail_level = -1;
+    return BCS_OK;
+  }
+  TailGen gen{s, lt};
+  gen.gen(lt, 0, 1);
+  std::vector<TailLevel> lvl(nl - lt);
+  std::vector<float*> vec(2 + 4 * (nl - lt), nullptr);
+  for (int l = lt; l < nl; ++l) {
+    const Level& L = s->lv[l];
+    TailLevel& t = lvl[l - lt];
+    t.rows = L.A.rows;
+    t.nslices = L.nslices;
+    t.nagg = L.nagg;
+    t.pad = 0;
+    t.rp = L.A.rp.p;
+    t.sptr = L.sptr.p;
+    t.sci = L.sci.p;
+    t.mptr = L.mptr.p;
+    t.mem = L.mem.p;
+    t.agg = L.agg.p;
+    t.sv = s->setup_cfg.precision == BCS_PREC_FP32 ? (const void*)L.s32.p : (const void*)L.s16.p;
+    t.dinv = L.dinv32.p;
+    vec[2 + 4 * (l - lt) + 0] = (float*)L.vb.p;
+    vec[2 + 4 * (l - lt) + 1] = (float*)L.vx.p;
+    vec[2 + 4 * (l - lt) + 2] = (float*)L.vr.p;
+    vec[2 + 4 * (l - lt) + 3] = (float*)L.vt.p;
+  }
+  TailPlan& T = s->tail;
+  const size_t a = gen.ph.size() * sizeof(TailPhase);
+  T.level_off = (a + 255) / 256 * 256;
+  T.vec_off = T.level_off + (lvl.size() * sizeof(TailLevel) + 255) / 256 * 256;
+  const size_t total = T.vec_off + vec.size() * sizeof(float*);
+  std::vector<char> host(total, 0);
+  std::memcpy(host.data(), gen.ph.data(), a);
+  std::memcpy(host.data() + T.level_off, lvl.data(), lvl.size() * sizeof(TailLevel));
+  std::memcpy(host.data() + T.vec_off, vec.data(), vec.size() * sizeof(float*));
+  BCS_ALLOC(s, T.buf, total);
+  BCS_CU(s, cudaMemcpyAsync(T.buf.p, host.data(), total, cudaMemcpyHostToDevice, s->stream));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));  // the host staging goes out of scope
+  T.nph = (int)gen.ph.size();
+  T.cluster = cluster;
+  T.bytes = gen.bytes;
+  T.flops = gen.flops;
+  return BCS_OK;
+}
+
 bcs_status cycle_prepare(Solver* s) {
   s->drop_graph();
   const int prec = s->setup_cfg.precision;
@@ -995,6 +1300,19 @@ bcs_status cycle_prepare(Solver* s) {
   const int n = s->n, nn = n * n;
   const bool sliced = prec != BCS_PREC_FP64 && (s->setup_cfg.precond == BCS_PC_AMG || s->setup_cfg.precond == BCS_PC_SGS);
   const size_t nl = s->lv.size();
+  s->tail_level = -1;
+  s->tail.nph = 0;
+  if (sliced && s->setup_cfg.precond == BCS_PC_AMG && s->setup_cfg.pmode == BCS_P_TENTATIVE &&
+      s->setup_cfg.tail_rows > 0 && s->n <= 8) {
+    bool dilu = false;
+    for (const Level& L : s->lv) dilu |= L.ncol > 0;
+    if (!dilu)
+      for (size_t l = 0; l < nl; ++l)
+        if (s->lv[l].A.rows <= s->setup_cfg.tail_rows) {
+          s->tail_level = (int)l;
+          break;
+        }
+  }
   // slice structures of every level first; their step counts are read back
   // together in one round trip
   DBuf<int32_t> steps;
@@ -1013,7 +1331,7 @@ bcs_status cycle_prepare(Solver* s) {
     BCS_ALLOC(s, L.dinv32, (size_t)L.A.rows * nn);
     BCS_OKR(cast_vec<double, float>(s, L.dinv.p, L.dinv32.p, (size_t)L.A.rows * nn));
     int map = 0;
-    BCS_OKR(slice_map(s, L, prec, &map));
+    BCS_OKR(slice_map(s, L, prec, s->tail_level >= 0 && (int)l >= s->tail_level, &map));
     bool need = false;
     BCS_OKR(layout_structure(s, L, map, steps.p + l, &need));
     needed[l] = need;
@@ -1043,6 +1361,7 @@ bcs_status cycle_prepare(Solver* s) {
       BCS_OKR(cast_vec<double, bf16>(s, L.R.v.p, L.R16.p, (size_t)L.R.nnz * nn));
     }
   }
+  if (s->tail_level >= 0) BCS_OKR(build_tail(s));
   return BCS_OK;
 }
 

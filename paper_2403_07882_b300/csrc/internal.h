@@ -159,6 +159,28 @@ struct Level {
   DBuf<char> vd;             // DILU correction vector (cycle precision)
 };
 
+// Coarse tail of the V-cycle (the levels below a size threshold) run as one
+// thread-block-cluster launch: a list of phases over a table of levels and a
+// table of vectors (ids 0 and 1: the tail's own right-hand side and
+// solution, passed at launch).
+enum TailOp { T_JAC0 = 0, T_SWEEP, T_RESID, T_RESTRICT, T_PROLONG, T_GEMV, T_ZERO };
+struct TailPhase {
+  int op, level;   // level: index into the tail's level table
+  int ia, ib, iy;  // vector ids: input x (or r, x_c), right-hand side b, output
+};
+struct TailLevel {
+  int rows, nslices, nagg, pad;
+  const int32_t *rp, *sptr, *sci, *mptr, *mem, *agg;
+  const void* sv;       // sliced values (lane-per-row layout), FP32 or BF16
+  const float* dinv;    // FP32 block inverses
+};
+struct TailPlan {
+  int nph = 0, cluster = 0;
+  size_t level_off = 0, vec_off = 0;
+  double bytes = 0.0, flops = 0.0;
+  DBuf<char> buf;  // phases | levels | vector pointers
+};
+
 // FGMRES restart cycle kept on the device (restart length m <= KS_MAXM): the
 // Arnoldi step index, the rotated Hessenberg matrix, the Givens rotations,
 // the rotated right-hand side g and the stop decision, so that a cycle runs
@@ -241,6 +263,8 @@ struct Solver {
   // V-cycle captured as a CUDA graph (FP32 / BF16 cycle): input lv[0].vb,
   // output lv[0].vx; dropped at every setup / resetup and on destroy
   cudaGraphExec_t cyc_exec = nullptr;
+  int tail_level = -1;             // first level of the coarse tail (-1: none)
+  TailPlan tail;
   cudaStream_t gstream = nullptr;  // private stream the graph is captured on
   long long cyc_kind_launches[BCS_NUM_KERNEL_KINDS] = {};
   double cyc_kind_bytes[BCS_NUM_KERNEL_KINDS] = {}, cyc_kind_flops[BCS_NUM_KERNEL_KINDS] = {};
