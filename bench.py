@@ -146,11 +146,13 @@ def peaks():
 
 
 def kernel_source_digest(path, func):
-    """SHA-256 of the text of __global__ function `func` in `path` (from its
-    definition line to the first line that closes it at column 0)."""
+    """SHA-256 of the text of the __global__ or __device__ function `func` in
+    `path` (from its definition line to the first line that closes it at
+    column 0)."""
     import hashlib
     lines = open(path).read().splitlines()
-    start = next(i for i, l in enumerate(lines) if "__global__" in l and (" " + func + "(") in l)
+    start = next(i for i, l in enumerate(lines)
+                 if ("__global__" in l or "__device__" in l) and (" " + func + "(") in l)
     end = next(i for i in range(start, len(lines)) if lines[i] == "}")
     return hashlib.sha256("\n".join(lines[start:end + 1]).encode()).hexdigest()
 
