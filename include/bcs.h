@@ -411,6 +411,27 @@ BCS_API bcs_status bcs_ldu_structure_noalloc(int32_t n_cells, int32_t n_faces, c
                                              int32_t* pos_diag, int32_t* pos_up, int32_t* pos_lo,
                                              void* stream, char* err, size_t errlen);
 
+/* Solve `count` systems together (1 <= count <= BCS_BATCH_MAX): solvers[i]
+ * with b[i][C_i][n] and x[i][C_i][n] (x[i] holds x0 on entry, the solution on
+ * return), all arrays in `mem` (BCS_MEM_HOST or BCS_MEM_DEVICE). The systems
+ * may differ in size and hierarchy depth; their FGMRES iterations run in
+ * lockstep, every step's kernels covering all systems at once (one launch
+ * per V-cycle phase and level for the whole batch), each system stopping on
+ * its own test. Every system's iterates, x and result equal those of
+ * bcs_solve on it alone, bit for bit. The paper has no counterpart (its
+ * linear systems are solved one by one); batching serves many small
+ * independent cases. Requires, for every solver: values set (else
+ * BCS_ESTATE), the same block size, FGMRES, an FP32 or BF16 aggregation-AMG
+ * cycle with block Jacobi and tentative prolongation, the same nu1, nu2,
+ * jacobi_omega, coarse_sweeps and restart, no internal renumbering, all on
+ * the current device (else BCS_EINVAL, message on solvers[0]). The work runs
+ * on solvers[0]'s stream after every solver's stream is synchronised; the
+ * call returns when it is complete. res[i] receives system i's result; the
+ * return value is BCS_OK, or the first non-OK status among the systems. */
+#define BCS_BATCH_MAX 64
+BCS_API bcs_status bcs_solve_batch(bcs_solver* const* solvers, int count, const double* const* b, double* const* x,
+                                   int mem, bcs_result* res);
+
 /* Message for the last failed call on s (never NULL). */
 BCS_API const char* bcs_last_error(const bcs_solver* s);
 

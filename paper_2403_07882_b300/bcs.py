@@ -114,6 +114,8 @@ def lib():
             "bcs_assemble_density": (ct.c_int, [_vp] + [_vp] * 4 + [ct.POINTER(bcs_flow_params)] + [_vp] * 3
                                      + [ct.c_int]),
             "bcs_solve": (ct.c_int, [_vp, _vp, _vp, ct.c_int, ct.POINTER(bcs_result)]),
+            "bcs_solve_batch": (ct.c_int, [ct.POINTER(_vp), ct.c_int, ct.POINTER(_vp), ct.POINTER(_vp), ct.c_int,
+                                           ct.POINTER(bcs_result)]),
             "bcs_spmv": (ct.c_int, [_vp, _vp, _vp, ct.c_int]),
             "bcs_precond_apply": (ct.c_int, [_vp, _vp, _vp, ct.c_int]),
             "bcs_get_bsr": (ct.c_int, [_vp] + [_vp] * 6),
@@ -153,7 +155,7 @@ def exported_names():
     return ["bcs_config_default", "bcs_create", "bcs_destroy", "bcs_set_config", "bcs_set_structure",
             "bcs_set_values", "bcs_invalidate_hierarchy", "bcs_flow_params_default", "bcs_assemble_density",
             "bcs_pack_vector", "bcs_unpack_vector", "bcs_pack_coefficients", "bcs_get_permutation",
-            "bcs_solve", "bcs_spmv", "bcs_precond_apply",
+            "bcs_solve", "bcs_solve_batch", "bcs_spmv", "bcs_precond_apply",
             "bcs_get_bsr", "bcs_num_levels", "bcs_get_level_info", "bcs_get_level", "bcs_get_prolongation",
             "bcs_get_coarse_inverse", "bcs_get_dilu", "bcs_get_stats", "bcs_reset_stats", "bcs_get_kernel_times", "bcs_kernel_kind_name",
             "bcs_last_error", "bcs_device_bytes", "bcs_ldu_structure_noalloc", "bcs_server_create",
@@ -383,6 +385,35 @@ def bcs_solve(h, b, x, check=False):
     if st in (BCS_EINVAL, BCS_ENOMEM, BCS_ECUDA, BCS_ESTATE) or (check and st != BCS_OK):
         _check(st, h)
     return st, res.as_dict()
+
+
+def bcs_solve_batch(handles, bs, xs):
+    """Solve len(handles) systems together (in place into xs[i]); returns
+    (status, [result dict per system])."""
+    k = len(handles)
+    if not (len(bs) == len(xs) == k):
+        raise ValueError("one right-hand side and one solution per solver")
+    specs = []
+    for h, b, x in zip(handles, bs, xs):
+        n, C, F = _solver_dims(h)
+        specs += [(b, "float64", _cnt(C, n)), (x, "float64", _cnt(C, n))]
+    ptrs, mem = _marshal(*specs)
+    hs = (_vp * k)(*[h.value if isinstance(h, ct.c_void_p) else h for h in handles])
+    pb = (_vp * k)(*ptrs[0::2])
+    px = (_vp * k)(*ptrs[1::2])
+    res = (bcs_result * k)()
+    st = lib().bcs_solve_batch(hs, k, pb, px, mem, res)
+    if st in (BCS_EINVAL, BCS_ENOMEM, BCS_ECUDA, BCS_ESTATE):
+        _check(st, handles[0])
+    return st, [r.as_dict() for r in res]
+
+
+def solve_batch(solvers, bs, xs=None):
+    """Solver objects' systems solved together: (xs, status, results)."""
+    if xs is None:
+        xs = [np.zeros_like(b) if isinstance(b, np.ndarray) else b.new_zeros(b.shape) for b in bs]
+    st, res = bcs_solve_batch([s.h for s in solvers], bs, xs)
+    return xs, st, res
 
 
 def bcs_spmv(h, x, y):

@@ -537,6 +537,71 @@ bcs_status bcs_invalidate_hierarchy(bcs_solver* h) {
   return BCS_OK;
 }
 
+bcs_status bcs_solve_batch(bcs_solver* const* solvers, int count, const double* const* b, double* const* x, int mem,
+                           bcs_result* res) {
+  NvtxRange nvtx_("bcs_solve_batch");
+  if (!solvers || !b || !x || !res || count < 1 || count > BCS_BATCH_MAX) return BCS_EINVAL;
+  if (mem != BCS_MEM_HOST && mem != BCS_MEM_DEVICE) return BCS_EINVAL;
+  std::vector<Solver*> ss(count);
+  for (int i = 0; i < count; ++i) {
+    if (!solvers[i] || !b[i] || !x[i]) return BCS_EINVAL;
+    ss[i] = &solvers[i]->impl;
+    for (int k = 0; k < i; ++k)
+      if (ss[k] == ss[i]) return ss[0]->fail(BCS_EINVAL, "batched solve: a solver appears twice");
+  }
+  Solver* s0 = ss[0];
+  const bcs_config& c0 = s0->setup_cfg;
+  for (int i = 0; i < count; ++i) {
+    Solver* s = ss[i];
+    const bcs_config& c = s->setup_cfg;
+    if (!s->have_hierarchy) return s0->fail(BCS_ESTATE, "batched solve: a solver has no values yet");
+    if (!same_hierarchy_options(s->cfg, s->setup_cfg))
+      return s0->fail(BCS_ESTATE, "batched solve: options changed since a solver's last set_values");
+    if (s->n != s0->n || s->reordered || s->cfg.solver != BCS_FGMRES || c.precond != BCS_PC_AMG ||
+        c.smoother != BCS_SMOOTH_JACOBI || c.pmode != BCS_P_TENTATIVE ||
+        (c.precision != BCS_PREC_FP32 && c.precision != BCS_PREC_BF16) || c.precision != c0.precision ||
+        c.nu1 != c0.nu1 || c.nu2 != c0.nu2 || c.jacobi_omega != c0.jacobi_omega ||
+        c.coarse_sweeps != c0.coarse_sweeps || s->cfg.restart != s0->cfg.restart || s->cfg.restart > KS_MAXM ||
+        (int)s->lv.size() > BATCH_MAX_LEVELS)
+      return s0->fail(BCS_EINVAL,
+                      "batched solve: the solvers need the same block size, FGMRES, an FP32 or BF16 aggregation "
+                      "AMG cycle with block Jacobi and tentative prolongation, the same smoothing options and "
+                      "restart length, and no internal renumbering");
+    if (s->cfg.profile && (s->cfg.profile_kinds == 0 || (s->cfg.profile_kinds & ~((1 << K_SETUP_AGG) |
+                                                                                   (1 << K_SETUP_GAL) |
+                                                                                   (1 << K_SETUP_INV) |
+                                                                                   (1 << K_CONVERT) |
+                                                                                   (1 << K_ASSEMBLE)))))
+      return s0->fail(BCS_EINVAL, "batched solve: per-kernel events of the solve kinds cannot be taken in it");
+    BCS_CU(s0, cudaStreamSynchronize(s->stream));
+  }
+  std::vector<const double*> bd(count);
+  std::vector<double*> xd(count);
+  for (int i = 0; i < count; ++i) {
+    bd[i] = b[i];
+    xd[i] = x[i];
+    if (mem == BCS_MEM_HOST) {
+      Solver* s = ss[i];
+      const size_t N = (size_t)s->C * s->n;
+      BCS_ALLOC(s, s->kb, N);
+      BCS_ALLOC(s, s->kx, N);
+      BCS_CU(s, cudaMemcpyAsync(s->kb.p, b[i], N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+      BCS_CU(s, cudaMemcpyAsync(s->kx.p, x[i], N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+      BCS_CU(s, cudaStreamSynchronize(s->stream));
+      bd[i] = s->kb.p;
+      xd[i] = s->kx.p;
+    }
+  }
+  BCS_OKR(solve_batch(ss.data(), count, bd.data(), xd.data(), res));
+  BCS_CU(s0, cudaStreamSynchronize(s0->stream));
+  bcs_status worst = BCS_OK;
+  for (int i = 0; i < count; ++i) {
+    if (mem == BCS_MEM_HOST) BCS_OKR(to_host(ss[i], x[i], xd[i], (size_t)ss[i]->C * ss[i]->n * sizeof(double)));
+    if (res[i].status != BCS_OK && worst == BCS_OK) worst = (bcs_status)res[i].status;
+  }
+  return worst;
+}
+
 bcs_status bcs_solve(bcs_solver* h, const double* b, double* x, int mem, bcs_result* res) {
   NvtxRange nvtx_("bcs_solve");
   if (!h) return BCS_EINVAL;

@@ -234,9 +234,8 @@ __global__ void k_ks_store_z(const TZ* __restrict__ z, TZ* __restrict__ Z, const
 // h_{j+1,j} <= 1e-14 ||A z_j|| (happy breakdown: no v_{j+1}), the rotated
 // residual |g_{j+1}| <= tol ||b|| or the iteration limit, the end of the
 // cycle. Sets the loop condition of the graph's WHILE node.
-__global__ void k_ks_givens(KrylovState* __restrict__ ks, const double* __restrict__ scal, int slot_a, int slot_b,
-                            int slot_n, cudaGraphConditionalHandle cond, int use_cond) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ int givens_step(KrylovState* __restrict__ ks, const double* __restrict__ scal, int slot_a, int slot_b,
+                           int slot_n) {
   const int j = ks->j, m = ks->m;
   double* H = ks->H;
   const double wn0 = __dsqrt_rn(scal[slot_a + j + 1]);
@@ -282,6 +281,13 @@ __global__ void k_ks_givens(KrylovState* __restrict__ ks, const double* __restri
   }
   ks->stop = stop;
   ks->j = j + 1;
+  return stop;
+}
+
+__global__ void k_ks_givens(KrylovState* __restrict__ ks, const double* __restrict__ scal, int slot_a, int slot_b,
+                            int slot_n, cudaGraphConditionalHandle cond, int use_cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int stop = givens_step(ks, scal, slot_a, slot_b, slot_n);
   if (use_cond) cudaGraphSetConditional(cond, stop == KS_RUN ? 1u : 0u);
 }
 
@@ -327,6 +333,183 @@ __global__ void k_ks_export(const KrylovState* __restrict__ ks, double* __restri
   scal[0] = (double)ks->iters;
   scal[1] = (double)ks->jend;
   scal[2] = (double)ks->stop;
+}
+
+// ---- batched steps: blockIdx.z selects the case ------------------------------
+// Each case's arithmetic is the single-system kernels' (the same device
+// functions, grids of the same shape per case), so a batched solve gives
+// every case the bits it gets alone. A case takes part in a step when its
+// restart cycle was running at the step's start (live, set by
+// kb_step_begin); the finishing kernels serve the cases of the current
+// restart round.
+__global__ void kb_step_begin_k(const BCase* __restrict__ cases, int count) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < count) *cases[c].live = cases[c].ks->stop == KS_RUN;
+}
+
+__global__ void kb_take_vj_k(const BCase* __restrict__ cases) {
+  const BCase& c = cases[blockIdx.z];
+  if (!*c.live) return;
+  const double* v = c.V + (size_t)c.ks->j * c.N;
+  float* out = c.lv[0].vb;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < c.N; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)v[i];
+}
+
+__global__ void kb_store_z_k(const BCase* __restrict__ cases) {
+  const BCase& c = cases[blockIdx.z];
+  if (!*c.live) return;
+  const float* z = c.lv[0].vx;
+  float* zj = c.Z + (size_t)c.ks->j * c.N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < c.N; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = z[i];
+    zj[i] = v;
+    c.kt[i] = (double)v;
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) kb_multidot_k(const BCase* __restrict__ cases, int with_w) {
+  const BCase& c = cases[blockIdx.z];
+  if (!*c.live) return;
+  const int nv = c.ks->j + 1, k = nv + with_w;
+  const int q0 = blockIdx.y * MD_CHUNK, cnt = min(MD_CHUNK, k - q0);
+  switch (cnt) {
+    case 8: multidot_body<8>(c.V, c.N, nv, q0, c.w, c.N, c.red); break;
+    case 7: multidot_body<7>(c.V, c.N, nv, q0, c.w, c.N, c.red); break;
+    case 6: multidot_body<6>(c.V, c.N, nv, q0, c.w, c.N, c.red); break;
+    case 5: multidot_body<5>(c.V, c.N, nv, q0, c.w, c.N, c.red); break;
+    case 4: multidot_body<4>(c.V, c.N, nv, q0, c.w, c.N, c.red); break;
+    case 3: multidot_body<3>(c.V, c.N, nv, q0, c.w, c.N, c.red); break;
+    case 2: multidot_body<2>(c.V, c.N, nv, q0, c.w, c.N, c.red); break;
+    case 1: multidot_body<1>(c.V, c.N, nv, q0, c.w, c.N, c.red); break;
+    default: break;
+  }
+}
+
+// the partials of vectors q < nq (nq: j + 1 + extra when per_step, else 1)
+// to scal[slot + q]; the case takes part when live (per_step) or in the round
+__global__ void __launch_bounds__(RED_THREADS) kb_reduce_k(const BCase* __restrict__ cases, int slot, int extra,
+                                                          int per_step) {
+  const BCase& c = cases[blockIdx.z];
+  if (per_step ? !*c.live : !*c.round) return;
+  const int q = blockIdx.x;
+  if (q >= (per_step ? c.ks->j + 1 + extra : 1)) return;
+  __shared__ double sm[RED_THREADS / 32];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < RED_BLOCKS; b += RED_THREADS) v += c.red[(size_t)q * RED_BLOCKS + b];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int wv = 0; wv < RED_THREADS / 32; ++wv) t += sm[wv];
+    c.scal[slot + q] = t;
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) kb_gs_update_k(const BCase* __restrict__ cases, int hslot, int norm) {
+  const BCase& c = cases[blockIdx.z];
+  if (!*c.live) return;
+  const int k = c.ks->j + 1;
+  const double* h = c.scal + hslot;
+  double acc = 0.0;
+  const size_t stride = (size_t)RED_BLOCKS * RED_THREADS;
+  for (size_t i = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; i < c.N; i += stride) {
+    double t = c.w[i];
+    for (int q = 0; q < k; ++q) t = fma(-__ldg(h + q), __ldg(c.V + (size_t)q * c.N + i), t);
+    c.w[i] = t;
+    acc = fma(t, t, acc);
+  }
+  if (!norm) return;
+  __shared__ double sm[RED_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+  if (lane == 0) sm[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int wv = 0; wv < RED_THREADS / 32; ++wv) v += sm[wv];
+    c.red[blockIdx.x] = v;
+  }
+}
+
+// Givens update and stop test of every live case; the loop continues while
+// one of them still runs.
+__global__ void kb_givens_k(const BCase* __restrict__ cases, int count, cudaGraphConditionalHandle cond) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < count; c += blockDim.x) {
+    const BCase& bc = cases[c];
+    if (!*bc.live) continue;
+    if (givens_step(bc.ks, bc.scal, SLOT_A, SLOT_B, SLOT_N) == KS_RUN) atomicOr(&any, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
+}
+
+__global__ void kb_scale_next_k(const BCase* __restrict__ cases) {
+  const BCase& c = cases[blockIdx.z];
+  if (!*c.live) return;
+  const int stop = c.ks->stop;
+  if (stop == KS_HAPPY || stop == KS_BREAKDOWN) return;
+  const double a = c.ks->rhn;
+  double* v = c.V + (size_t)c.ks->j * c.N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < c.N; i += (size_t)gridDim.x * blockDim.x)
+    v[i] = a * c.w[i];
+}
+
+// back substitution (one thread per case), then x += Z y
+__global__ void kb_backsolve_k(const BCase* __restrict__ cases, int count) {
+  const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ci >= count || !*cases[ci].round) return;
+  KrylovState* ks = cases[ci].ks;
+  if (ks->stop == KS_BREAKDOWN) return;
+  const int jend = ks->jend, m = ks->m;
+  const double* H = ks->H;
+  for (int i = jend - 1; i >= 0; --i) {
+    double t = ks->g[i];
+    for (int k = i + 1; k < jend; ++k) t = __dsub_rn(t, __dmul_rn(H[(size_t)i * m + k], ks->y[k]));
+    ks->y[i] = __ddiv_rn(t, H[(size_t)i * m + i]);
+  }
+}
+
+__global__ void kb_combine_k(const BCase* __restrict__ cases) {
+  const BCase& c = cases[blockIdx.z];
+  if (!*c.round) return;
+  const int k = c.ks->stop == KS_BREAKDOWN ? 0 : c.ks->jend;
+  const double* y = c.ks->y;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < c.N; i += (size_t)gridDim.x * blockDim.x) {
+    double t = c.x[i];
+    for (int q = 0; q < k; ++q) t = fma(y[q], (double)c.Z[(size_t)q * c.N + i], t);
+    c.x[i] = t;
+  }
+}
+
+// partials of ||r||^2 (k_multidot<1>'s order and tree) and the cycle outcome
+__global__ void __launch_bounds__(RED_THREADS) kb_norm_r_k(const BCase* __restrict__ cases) {
+  const BCase& c = cases[blockIdx.z];
+  if (!*c.round) return;
+  multidot_body<1>(c.r, c.N, 1 << 30, 0, c.r, c.N, c.red);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c.scal[SLOT_S] = (double)c.ks->iters;
+    c.scal[SLOT_S + 1] = (double)c.ks->jend;
+    c.scal[SLOT_S + 2] = (double)c.ks->stop;
+  }
+}
+
+// every case's ||r||^2 and cycle outcome into one array (one read for all)
+__global__ void kb_gather_out_k(const BCase* __restrict__ cases, int count, double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= count) return;
+  const double* sc = cases[c].scal;
+  out[4 * c] = sc[SLOT_N];
+  out[4 * c + 1] = sc[SLOT_S];
+  out[4 * c + 2] = sc[SLOT_S + 1];
+  out[4 * c + 3] = sc[SLOT_S + 2];
 }
 
 unsigned vgrid(size_t N) {
@@ -500,5 +683,65 @@ bcs_status bicg_p_update(Solver* s, double beta, double omega, const double* r, 
   return BCS_OK;
 }
 
+
+
+// grid of the element-wise batched kernels: the largest case's
+unsigned bgrid(size_t maxN) { return vgrid(maxN); }
+
+bcs_status kb_step_begin(Solver* s, const BCase* cases, int count) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_step_begin_k, grid_for(count, 64), 64, 0, cases, count);
+  return BCS_OK;
+}
+
+bcs_status kb_take_vj(Solver* s, const BCase* cases, int count, size_t maxN) {
+  BCS_LAUNCH(s, K_CAST, 12.0 * maxN * count, 0, kb_take_vj_k, dim3(bgrid(maxN), 1, count), 256, 0, cases);
+  return BCS_OK;
+}
+
+bcs_status kb_store_z(Solver* s, const BCase* cases, int count, size_t maxN) {
+  BCS_LAUNCH(s, K_CAST, 16.0 * maxN * count, 0, kb_store_z_k, dim3(bgrid(maxN), 1, count), 256, 0, cases);
+  return BCS_OK;
+}
+
+bcs_status kb_multidot(Solver* s, const BCase* cases, int count, bool with_w, int kmax, int slot) {
+  const unsigned chunks = (unsigned)((kmax + MD_CHUNK - 1) / MD_CHUNK);
+  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_multidot_k, dim3(RED_BLOCKS, chunks, count), RED_THREADS, 0, cases, with_w ? 1 : 0);
+  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_reduce_k, dim3(kmax, 1, count), RED_THREADS, 0, cases, slot, with_w ? 1 : 0, 1);
+  return BCS_OK;
+}
+
+bcs_status kb_gs_update(Solver* s, const BCase* cases, int count, int hslot, int nslot) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_gs_update_k, dim3(RED_BLOCKS, 1, count), RED_THREADS, 0, cases, hslot,
+             nslot >= 0 ? 1 : 0);
+  if (nslot >= 0) BCS_LAUNCH(s, K_BLAS, 0, 0, kb_reduce_k, dim3(1, 1, count), RED_THREADS, 0, cases, nslot, 0, 1);
+  return BCS_OK;
+}
+
+bcs_status kb_givens(Solver* s, const BCase* cases, int count, cudaGraphConditionalHandle cond) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_givens_k, 1, 64, 0, cases, count, cond);
+  return BCS_OK;
+}
+
+bcs_status kb_scale_next(Solver* s, const BCase* cases, int count, size_t maxN) {
+  BCS_LAUNCH(s, K_BLAS, 16.0 * maxN * count, 0, kb_scale_next_k, dim3(bgrid(maxN), 1, count), 256, 0, cases);
+  return BCS_OK;
+}
+
+bcs_status kb_finish(Solver* s, const BCase* cases, int count, size_t maxN) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_backsolve_k, grid_for(count, 32), 32, 0, cases, count);
+  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_combine_k, dim3(bgrid(maxN), 1, count), 256, 0, cases);
+  return BCS_OK;
+}
+
+bcs_status kb_norm_r(Solver* s, const BCase* cases, int count) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_norm_r_k, dim3(RED_BLOCKS, 1, count), RED_THREADS, 0, cases);
+  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_reduce_k, dim3(1, 1, count), RED_THREADS, 0, cases, SLOT_N, 0, 0);
+  return BCS_OK;
+}
+
+bcs_status kb_gather_out(Solver* s, const BCase* cases, int count, double* out) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_gather_out_k, grid_for(count, 64), 64, 0, cases, count, out);
+  return BCS_OK;
+}
 
 }  // namespace bcs

@@ -65,17 +65,24 @@ __device__ __forceinline__ AT row_dot(const int32_t* __restrict__ rp, const int3
 
 // y = A x (M_SPMV), y += A x (M_ADD), y = b - A x (M_RESID).
 template <int N, class AT, class TV, class TX, class TY, int MODE>
+__device__ __forceinline__ void rows_eval(int i, int r, const int32_t* __restrict__ rp,
+                                          const int32_t* __restrict__ ci, const TV* __restrict__ val,
+                                          const TX* __restrict__ x, TY* __restrict__ y, const TY* __restrict__ b) {
+  const AT acc = row_dot<N, AT>(rp, ci, val, x, i, r);
+  const size_t o = (size_t)i * N + r;
+  if (MODE == M_SPMV) y[o] = (TY)acc;
+  else if (MODE == M_ADD) y[o] = (TY)((AT)y[o] + acc);
+  else y[o] = (TY)((AT)b[o] - acc);
+}
+
+template <int N, class AT, class TV, class TX, class TY, int MODE>
 __global__ void __launch_bounds__(128) k_rows(int rows, const int32_t* __restrict__ rp,
                                               const int32_t* __restrict__ ci, const TV* __restrict__ val,
                                               const TX* __restrict__ x, TY* __restrict__ y,
                                               const TY* __restrict__ b) {
   RowMap<N> m(rows);
   if (!m.active) return;
-  const AT acc = row_dot<N, AT>(rp, ci, val, x, m.i, m.r);
-  const size_t o = (size_t)m.i * N + m.r;
-  if (MODE == M_SPMV) y[o] = (TY)acc;
-  else if (MODE == M_ADD) y[o] = (TY)((AT)y[o] + acc);
-  else y[o] = (TY)((AT)b[o] - acc);
+  rows_eval<N, AT, TV, TX, TY, MODE>(m.i, m.r, rp, ci, val, x, y, b);
 }
 
 // ---- multicolour DILU sweeps (one launch per colour) -------------------------
@@ -396,15 +403,13 @@ __global__ void k_tpr_fill(int rows, int nslices, const int32_t* __restrict__ rp
 // ascending; the epilogue in column order), so both layouts give identical
 // results.
 template <int N, class TV, bool JACOBI>
-__global__ void __launch_bounds__(128, TPR_MINB) k_tpr(int rows, int nslices, const int32_t* __restrict__ rp,
+__device__ __forceinline__ void tpr_slice(int sl, int rows, const int32_t* __restrict__ rp,
                                              const int32_t* __restrict__ srow, const int32_t* __restrict__ sptr,
                                              const int32_t* __restrict__ sci, const TV* __restrict__ sv,
                                              const float* __restrict__ dinv, const float* __restrict__ x,
                                              const float* __restrict__ b, float* __restrict__ y, float omega) {
   constexpr int NN = N * N, TILE = NN * 32;
   const int lane = threadIdx.x & 31;
-  const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  if (sl >= nslices) return;
   const int pos = sl * 32 + lane;
   if (pos >= rows) return;
   const int i = __ldg(srow + pos);
@@ -457,6 +462,17 @@ __global__ void __launch_bounds__(128, TPR_MINB) k_tpr(int rows, int nslices, co
     for (int c = 0; c < N; ++c) tt = fmaf(__ldg(dinv + (o + r) * N + c), res[c], tt);
     y[o + r] = fmaf(omega, tt, xo);
   }
+}
+
+template <int N, class TV, bool JACOBI>
+__global__ void __launch_bounds__(128, TPR_MINB) k_tpr(int rows, int nslices, const int32_t* __restrict__ rp,
+                                             const int32_t* __restrict__ srow, const int32_t* __restrict__ sptr,
+                                             const int32_t* __restrict__ sci, const TV* __restrict__ sv,
+                                             const float* __restrict__ dinv, const float* __restrict__ x,
+                                             const float* __restrict__ b, float* __restrict__ y, float omega) {
+  const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (sl >= nslices) return;
+  tpr_slice<N, TV, JACOBI>(sl, rows, rp, srow, sptr, sci, sv, dinv, x, b, y, omega);
 }
 
 // y = x + omega D^-1 (b - A x)
@@ -645,6 +661,99 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const TailPhase* __restri
     }
     cl.sync();
   }
+}
+
+// ---- batched V-cycle: blockIdx.z selects the case ------------------------------
+// One launch per phase of each level covers every case that has that level
+// (and whose FGMRES step is live); each element is computed by the device
+// function of the single-system kernel in the level's own layout, so every
+// case gets the bits of its own cycle. Vector roles: 0 vb, 1 vx, 2 vr, 3 vt.
+__device__ __forceinline__ const BLevel* b_level(const BCase& c, int level, int coarse) {
+  if (level >= c.n_levels || !*c.live) return nullptr;
+  const BLevel* L = &c.lv[level];
+  if (coarse ? L->coarse_kind != 1 : L->coarse_kind >= 0) return nullptr;
+  return L;
+}
+
+__device__ __forceinline__ float* b_vec(const BLevel& L, int role) {
+  return role == 0 ? L.vb : role == 1 ? L.vx : role == 2 ? L.vr : L.vt;
+}
+
+template <int N, class TV, bool JACOBI>
+__global__ void __launch_bounds__(128) kb_sweep_k(const BCase* __restrict__ cases, int level, int coarse, int ix,
+                                                  int iy, float omega) {
+  const BLevel* L = b_level(cases[blockIdx.z], level, coarse);
+  if (!L) return;
+  const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (sl >= L->nslices) return;
+  const float* x = b_vec(*L, ix);
+  float* y = b_vec(*L, iy);
+  if (L->smap == 1)
+    tpr_slice<N, TV, JACOBI>(sl, L->rows, L->rp, L->srow, L->sptr, L->sci, (const TV*)L->sv, L->dinv, x, L->vb, y,
+                             omega);
+  else
+    sell_slice<N, TV, JACOBI, false>(sl, L->rows, L->rp, L->sptr, L->sci, (const TV*)L->sv, L->dinv, x, L->vb, y,
+                                     omega);
+}
+
+template <int N>
+__global__ void kb_jac0_k(const BCase* __restrict__ cases, int level, int coarse, int iy, float omega) {
+  const BLevel* L = b_level(cases[blockIdx.z], level, coarse);
+  if (!L) return;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t < (size_t)L->rows * N) jacobi0_elem<N, float, float, float, false>(t, L->dinv, L->vb, b_vec(*L, iy), omega);
+}
+
+template <int N>
+__global__ void kb_zero_k(const BCase* __restrict__ cases, int level, int iy) {
+  const BLevel* L = b_level(cases[blockIdx.z], level, 0);
+  if (!L) return;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t < (size_t)L->rows * N) b_vec(*L, iy)[t] = 0.f;
+}
+
+template <int N>
+__global__ void kb_restrict_k(const BCase* __restrict__ cases, int level) {
+  const BCase& c = cases[blockIdx.z];
+  const BLevel* L = b_level(c, level, 0);
+  if (!L) return;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t < (size_t)L->nagg * N) restrict_elem<N, float, float, false>(t, L->mptr, L->mem, L->vr, c.lv[level + 1].vb);
+}
+
+template <int N>
+__global__ void kb_prolong_k(const BCase* __restrict__ cases, int level, int iy) {
+  const BCase& c = cases[blockIdx.z];
+  const BLevel* L = b_level(c, level, 0);
+  if (!L) return;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t < (size_t)L->rows * N) prolong_elem<N, float, false>(t, L->agg, c.lv[level + 1].vx, b_vec(*L, iy));
+}
+
+__global__ void kb_gemv_k(const BCase* __restrict__ cases) {
+  const BCase& c = cases[blockIdx.z];
+  if (!*c.live) return;
+  const BLevel& L = c.lv[c.n_levels - 1];
+  if (L.coarse_kind != 0) return;
+  const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (row < c.cN) gemv_row<float, false>(row, c.cN, c.cinv, L.vb, L.vx);
+}
+
+// w = A kt (live cases) / r = b - A x (cases of the round), FP64
+template <int N>
+__global__ void __launch_bounds__(128) kb_spmv_w_k(const BCase* __restrict__ cases) {
+  const BCase& c = cases[blockIdx.z];
+  if (!*c.live) return;
+  RowMap<N> m(c.rows);
+  if (m.active) rows_eval<N, double, double, double, double, M_SPMV>(m.i, m.r, c.rp, c.ci, c.val, c.kt, c.w, nullptr);
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) kb_resid_r_k(const BCase* __restrict__ cases) {
+  const BCase& c = cases[blockIdx.z];
+  if (!*c.round) return;
+  RowMap<N> m(c.rows);
+  if (m.active) rows_eval<N, double, double, double, double, M_RESID>(m.i, m.r, c.rp, c.ci, c.val, c.x, c.r, c.b);
 }
 
 }  // namespace
@@ -1499,6 +1608,102 @@ bcs_status jacobi_apply(Solver* s, const double* v, double* z) {
     const int rows = L0.A.rows;
     BCS_LAUNCH(s, K_SWEEP, (double)rows * N * (N * 8 + 16), 2.0 * rows * N * N, (k_jacobi0<N, double, double, double>),
                grid_for((size_t)rows * N, 256), 256, 0, rows, L0.dinv.p, v, z, 1.0);
+    return BCS_OK;
+  });
+}
+
+
+// ---- batched V-cycle and products (host side) ----------------------------------
+namespace {
+
+template <int N, class TV>
+bcs_status kb_cycle_t(Solver* s, const BCase* cases, const std::vector<BCase>& host, int count) {
+  const bcs_config& c = s->setup_cfg;
+  const float om = (float)c.jacobi_omega;
+  int lmax = 0;
+  for (const BCase& h : host) lmax = std::max(lmax, h.n_levels);
+  // largest work of level l over the cases
+  auto most = [&](int l, auto f) {
+    size_t m = 0;
+    for (const BCase& h : host)
+      if (l < h.n_levels) m = std::max<size_t>(m, f(h.lv[l]));
+    return m;
+  };
+  auto slices = [&](int l) { return grid_for(most(l, [](const BLevel& L) { return (size_t)L.nslices; }) * 32, 128); };
+  auto elems = [&](int l) { return grid_for(most(l, [](const BLevel& L) { return (size_t)L.rows * N; }), 256); };
+  const dim3 z1(1, 1, count);
+  auto grid = [&](unsigned g) { return dim3(g, 1, count); };
+  const int swaps = (c.nu1 > 1 ? c.nu1 - 1 : 0) + c.nu2;
+  const int cur0 = swaps % 2 == 0 ? 1 : 3, alt0 = cur0 == 1 ? 3 : 1;
+  int cur_down = cur0, alt_down = alt0;
+  for (int k = 1; k < c.nu1; ++k) std::swap(cur_down, alt_down);
+  // down: pre-smoothing, residual, restriction
+  for (int l = 0; l + 1 < lmax; ++l) {
+    int cur = cur0, alt = alt0;
+    if (c.nu1 >= 1) {
+      BCS_LAUNCH(s, K_SWEEP, 0, 0, (kb_jac0_k<N>), grid(elems(l)), 256, 0, cases, l, 0, cur, om);
+      for (int k = 1; k < c.nu1; ++k) {
+        BCS_LAUNCH(s, K_SWEEP, 0, 0, (kb_sweep_k<N, TV, true>), grid(slices(l)), 128, 0, cases, l, 0, cur, alt, om);
+        std::swap(cur, alt);
+      }
+    } else {
+      BCS_LAUNCH(s, K_SWEEP, 0, 0, (kb_zero_k<N>), grid(elems(l)), 256, 0, cases, l, cur);
+    }
+    BCS_LAUNCH(s, K_RESID, 0, 0, (kb_sweep_k<N, TV, false>), grid(slices(l)), 128, 0, cases, l, 0, cur, 2, 0.f);
+    const unsigned ga = grid_for(most(l, [](const BLevel& L) { return (size_t)L.nagg * N; }), 256);
+    BCS_LAUNCH(s, K_TRANSFER, 0, 0, (kb_restrict_k<N>), grid(ga), 256, 0, cases, l);
+  }
+  // coarsest levels: dense inverses, or smoother sweeps from zero
+  int cn = 0;
+  for (const BCase& h : host) cn = std::max(cn, h.cN);
+  if (cn > 0) BCS_LAUNCH(s, K_COARSE, 0, 0, kb_gemv_k, grid(grid_for((size_t)cn * 32, 256)), 256, 0, cases);
+  for (int l = 0; l < lmax; ++l) {
+    bool any = false;
+    for (const BCase& h : host) any |= l < h.n_levels && h.lv[l].coarse_kind == 1;
+    if (!any) continue;
+    const int n_sw = c.coarse_sweeps;
+    int cur = ((n_sw - 1) % 2 == 0) ? 1 : 3, alt = cur == 1 ? 3 : 1;
+    BCS_LAUNCH(s, K_SWEEP, 0, 0, (kb_jac0_k<N>), grid(elems(l)), 256, 0, cases, l, 1, cur, om);
+    for (int k = 1; k < n_sw; ++k) {
+      BCS_LAUNCH(s, K_SWEEP, 0, 0, (kb_sweep_k<N, TV, true>), grid(slices(l)), 128, 0, cases, l, 1, cur, alt, om);
+      std::swap(cur, alt);
+    }
+  }
+  // up: prolongation-correction, post-smoothing
+  for (int l = lmax - 2; l >= 0; --l) {
+    int cur = cur_down, alt = alt_down;
+    BCS_LAUNCH(s, K_TRANSFER, 0, 0, (kb_prolong_k<N>), grid(elems(l)), 256, 0, cases, l, cur);
+    for (int k = 0; k < c.nu2; ++k) {
+      BCS_LAUNCH(s, K_SWEEP, 0, 0, (kb_sweep_k<N, TV, true>), grid(slices(l)), 128, 0, cases, l, 0, cur, alt, om);
+      std::swap(cur, alt);
+    }
+  }
+  (void)z1;
+  return BCS_OK;
+}
+
+}  // namespace
+
+bcs_status kb_cycle(Solver* s, const BCase* cases, const std::vector<BCase>& host, int count) {
+  return with_n(s->n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    return s->setup_cfg.precision == BCS_PREC_FP32 ? kb_cycle_t<N, float>(s, cases, host, count)
+                                                   : kb_cycle_t<N, bf16>(s, cases, host, count);
+  });
+}
+
+bcs_status kb_spmv_w(Solver* s, const BCase* cases, int count, int max_rows) {
+  return with_n(s->n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    BCS_LAUNCH(s, K_SPMV64, 0, 0, kb_spmv_w_k<N>, dim3(rows_grid(max_rows, N), 1, count), 128, 0, cases);
+    return BCS_OK;
+  });
+}
+
+bcs_status kb_resid_r(Solver* s, const BCase* cases, int count, int max_rows) {
+  return with_n(s->n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    BCS_LAUNCH(s, K_SPMV64, 0, 0, kb_resid_r_k<N>, dim3(rows_grid(max_rows, N), 1, count), 128, 0, cases);
     return BCS_OK;
   });
 }

@@ -198,6 +198,37 @@ struct KrylovState {
 };
 enum { KS_RUN = 0, KS_CONVERGED = 1, KS_HAPPY = 2, KS_BREAKDOWN = 3, KS_MAXITER = 4, KS_CYCLE_END = 5 };
 
+// Device scalar slots of the Krylov solvers (s->scal): first and second
+// Gram-Schmidt pass, norms, the nonzero flag of x0, a restart cycle's
+// outcome (iterations, steps, stop reason).
+constexpr int SLOT_A = 0, SLOT_B = 72, SLOT_N = 144, SLOT_X = 145, SLOT_S = 146;
+
+// Batched solves: several systems' FGMRES run in lockstep, each step's
+// kernels covering every case (blockIdx.z = case) through these tables.
+constexpr int BATCH_MAX_LEVELS = 20;
+struct BLevel {  // one level of one case's hierarchy (FP32 / BF16 cycle)
+  int rows, nslices, smap, nagg, coarse_kind, pad;
+  const int32_t *rp, *srow, *sptr, *sci, *mptr, *mem, *agg;
+  const void* sv;      // sliced values in the level's layout
+  const float* dinv;   // FP32 block inverses
+  float *vb, *vx, *vr, *vt;
+};
+struct BCase {
+  int n_levels, rows;
+  size_t N;                       // unknowns
+  KrylovState* ks;
+  int* live;                      // this step's participation (set at the step's start)
+  const int* round;               // 1 while the case takes part in the current restart round
+  double *V, *w, *kt, *scal, *red, *x, *r;
+  const double* b;
+  float* Z;
+  const int32_t *rp, *ci;         // fine FP64 matrix
+  const double* val;
+  const double* cinv;
+  int cN, pad;
+  BLevel lv[BATCH_MAX_LEVELS];
+};
+
 struct Timer {
   int kind;
   cudaEvent_t a, b;
@@ -416,6 +447,24 @@ bcs_status ks_givens(Solver* s, KrylovState* ks, int slot_a, int slot_b, int slo
 bcs_status ks_scale_next(Solver* s, const KrylovState* ks, const double* w, double* V, size_t ldv, size_t N);
 bcs_status ks_finish_cycle(Solver* s, KrylovState* ks, const void* Z, bool z_float, double* x, size_t N);
 bcs_status ks_export(Solver* s, const KrylovState* ks, int slot);
+// Batched steps (launched on s's stream; cases is a device table of count
+// entries; kmax bounds the vectors of one multi-dot, rows / N the largest
+// case).
+bcs_status kb_step_begin(Solver* s, const BCase* cases, int count);
+bcs_status kb_take_vj(Solver* s, const BCase* cases, int count, size_t maxN);
+bcs_status kb_store_z(Solver* s, const BCase* cases, int count, size_t maxN);
+bcs_status kb_multidot(Solver* s, const BCase* cases, int count, bool with_w, int kmax, int slot);
+bcs_status kb_gs_update(Solver* s, const BCase* cases, int count, int hslot, int nslot);
+bcs_status kb_givens(Solver* s, const BCase* cases, int count, cudaGraphConditionalHandle cond);
+bcs_status kb_scale_next(Solver* s, const BCase* cases, int count, size_t maxN);
+bcs_status kb_finish(Solver* s, const BCase* cases, int count, size_t maxN);
+bcs_status kb_norm_r(Solver* s, const BCase* cases, int count);
+bcs_status kb_gather_out(Solver* s, const BCase* cases, int count, double* out);
+// cycle.cu: the batched V-cycle (level-0 vb -> vx of every live case) and
+// the FP64 products of the batched step
+bcs_status kb_cycle(Solver* s, const BCase* cases, const std::vector<BCase>& host, int count);
+bcs_status kb_spmv_w(Solver* s, const BCase* cases, int count, int max_rows);
+bcs_status kb_resid_r(Solver* s, const BCase* cases, int count, int max_rows);
 
 // ------------------------------------------------------------------- cycle.cu
 enum Mode { M_SPMV = 0, M_ADD = 1, M_RESID = 2 };
@@ -450,6 +499,9 @@ bcs_status dilu_prepare(Solver* s, Level& L);
 
 // ------------------------------------------------------------------ krylov.cu
 bcs_status solve(Solver* s, const double* b_d, double* x_d, bcs_result* res);
+// FGMRES of count solvers in lockstep (device arrays b[i], x[i]; all work on
+// ss[0]'s stream); res[i] per solver.
+bcs_status solve_batch(Solver* const* ss, int count, const double* const* b, double* const* x, bcs_result* res);
 
 }  // namespace bcs
 

@@ -26,11 +26,6 @@ namespace bcs {
 
 namespace {
 
-constexpr int SLOT_A = 0;     // first Gram-Schmidt pass
-constexpr int SLOT_B = 72;    // second pass
-constexpr int SLOT_N = 144;   // norms
-constexpr int SLOT_X = 145;   // nonzero flag of the initial guess
-constexpr int SLOT_S = 146;   // device cycle: iterations, steps, stop reason
 
 size_t zbytes(const Solver* s) { return cycle_is_float(s) ? sizeof(float) : sizeof(double); }
 
@@ -527,6 +522,248 @@ bcs_status solve(Solver* s, const double* b, double* x, bcs_result* res) {
   if (st == BCS_NOT_CONVERGED) s->err = "maximum iterations reached above the tolerance";
   if (st == BCS_BREAKDOWN) s->err = "Krylov breakdown or non-finite residual";
   return st;
+}
+
+
+// ---- batched FGMRES ------------------------------------------------------------
+// Several systems (uneven sizes, same block size and cycle options) solved
+// in lockstep: each restart round is one launch of a graph whose WHILE body
+// is one Arnoldi step of every live case (batched kernels, blockIdx.z =
+// case), followed by the round's back substitutions, x updates, true
+// residuals and one read of every case's outcome. A case leaves the round
+// when its own stop test fires and the batch when it has converged, broken
+// down or reached maxiter. Each case's arithmetic is the single-system
+// device loop's, so its iterates equal those of solving it alone.
+namespace {
+
+bcs_status capture_batch(Solver* s0, const BCase* cases, const std::vector<BCase>& host, int count, int m,
+                         size_t maxN, int max_rows, cudaGraphExec_t* exec, long long* body_launches) {
+  if (!s0->gstream) BCS_CU(s0, cudaStreamCreateWithFlags(&s0->gstream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  BCS_CU(s0, cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle cond = 0;
+  cudaGraphNode_t node = nullptr;
+  cudaGraphNodeParams prm{};
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = cond;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &prm);
+  }
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(s0->gstream, prm.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return s0->fail(BCS_ECUDA, std::string("batched loop graph: ") + cudaGetErrorString(e));
+  }
+  const long long l0 = s0->launches;
+  const cudaStream_t own = s0->stream;
+  s0->stream = s0->gstream;
+  bcs_status st = kb_step_begin(s0, cases, count);
+  if (st == BCS_OK) st = kb_take_vj(s0, cases, count, maxN);
+  if (st == BCS_OK) st = kb_cycle(s0, cases, host, count);
+  if (st == BCS_OK) st = kb_store_z(s0, cases, count, maxN);
+  if (st == BCS_OK) st = kb_spmv_w(s0, cases, count, max_rows);
+  if (st == BCS_OK) st = kb_multidot(s0, cases, count, true, m + 1, SLOT_A);
+  if (st == BCS_OK) st = kb_gs_update(s0, cases, count, SLOT_A, -1);
+  if (st == BCS_OK) st = kb_multidot(s0, cases, count, false, m, SLOT_B);
+  if (st == BCS_OK) st = kb_gs_update(s0, cases, count, SLOT_B, SLOT_N);
+  if (st == BCS_OK) st = kb_givens(s0, cases, count, cond);
+  if (st == BCS_OK) st = kb_scale_next(s0, cases, count, maxN);
+  s0->stream = own;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(s0->gstream, &captured);
+  *body_launches = s0->launches - l0;
+  s0->launches = l0;
+  if (st != BCS_OK || ce != cudaSuccess) {
+    cudaGraphDestroy(g);
+    if (st != BCS_OK) return st;
+    return s0->fail(BCS_ECUDA, std::string("batched loop capture: ") + cudaGetErrorString(ce));
+  }
+  const cudaError_t ie = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    *exec = nullptr;
+    return s0->fail(BCS_ECUDA, std::string("batched loop instantiate: ") + cudaGetErrorString(ie));
+  }
+  return BCS_OK;
+}
+
+}  // namespace
+
+bcs_status solve_batch(Solver* const* ss, int count, const double* const* b, double* const* x, bcs_result* res) {
+  Solver* s0 = ss[0];
+  const int m = s0->cfg.restart;
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<BCase> host(count);
+  std::vector<double> bnorm(count, 0.0), beta(count, 0.0);
+  std::vector<int> iters(count, 0), active(count, 0);
+  std::vector<bcs_status> status(count, BCS_OK);
+  size_t maxN = 0;
+  int max_rows = 0;
+  for (int i = 0; i < count; ++i) {
+    Solver* s = ss[i];
+    const size_t N = (size_t)s->C * s->n;
+    BCS_ALLOC(s, s->kv, (size_t)(m + 1) * N);
+    BCS_ALLOC(s, s->kz, (size_t)m * N * sizeof(float));
+    BCS_ALLOC(s, s->kr, N);
+    BCS_ALLOC(s, s->kw, N);
+    BCS_ALLOC(s, s->kt, N);
+    BCS_ALLOC(s, s->kst, sizeof(KrylovState));
+    BCS_ALLOC(s, s->red, (size_t)72 * 1184);
+    BCS_OKR(initial_residual(s, b[i], x[i], s->kr.p, N, &bnorm[i], &beta[i]));  // synchronises s's stream
+    res[i] = bcs_result{};
+    res[i].rel_res_initial = res[i].rel_res_final = bnorm[i] > 0.0 ? beta[i] / bnorm[i] : 0.0;
+    res[i].levels = (int)s->lv.size();
+    res[i].setup_ms = s->last_setup_ms;
+    if (bnorm[i] == 0.0) {
+      BCS_CU(s, cudaMemsetAsync(x[i], 0, N * sizeof(double), s->stream));
+      BCS_CU(s, cudaStreamSynchronize(s->stream));
+    } else if (!std::isfinite(beta[i])) {
+      status[i] = BCS_BREAKDOWN;
+    } else if (beta[i] > s->cfg.tol * bnorm[i]) {
+      active[i] = 1;
+    }
+    BCase& h = host[i];
+    std::memset(&h, 0, sizeof(h));
+    h.n_levels = (int)s->lv.size();
+    h.rows = s->C;
+    h.N = N;
+    h.ks = reinterpret_cast<KrylovState*>(s->kst.p);
+    h.V = s->kv.p;
+    h.w = s->kw.p;
+    h.kt = s->kt.p;
+    h.scal = s->scal.p;
+    h.red = s->red.p;
+    h.x = x[i];
+    h.r = s->kr.p;
+    h.b = b[i];
+    h.Z = reinterpret_cast<float*>(s->kz.p);
+    h.rp = s->lv[0].A.rp.p;
+    h.ci = s->lv[0].A.ci.p;
+    h.val = s->lv[0].A.v.p;
+    h.cinv = s->cinv.p;
+    h.cN = s->lv.back().coarse_kind == 0 ? s->cN : 0;
+    for (int l = 0; l < h.n_levels; ++l) {
+      const Level& L = s->lv[l];
+      BLevel& t = h.lv[l];
+      t.rows = L.A.rows;
+      t.nslices = L.nslices;
+      t.smap = L.smap;
+      t.nagg = L.nagg;
+      t.coarse_kind = L.coarse_kind;
+      t.rp = L.A.rp.p;
+      t.srow = L.srow.p;
+      t.sptr = L.sptr.p;
+      t.sci = L.sci.p;
+      t.mptr = L.mptr.p;
+      t.mem = L.mem.p;
+      t.agg = L.agg.p;
+      t.sv = s->setup_cfg.precision == BCS_PREC_FP32 ? (const void*)L.s32.p : (const void*)L.s16.p;
+      t.dinv = L.dinv32.p;
+      t.vb = (float*)L.vb.p;
+      t.vx = (float*)L.vx.p;
+      t.vr = (float*)L.vr.p;
+      t.vt = (float*)L.vt.p;
+    }
+    maxN = std::max(maxN, N);
+    max_rows = std::max(max_rows, s->C);
+  }
+  // device tables: cases | live flags | round flags | outcomes
+  DBuf<char> buf;
+  const size_t off_live = ((size_t)count * sizeof(BCase) + 255) / 256 * 256;
+  const size_t off_round = off_live + ((size_t)count * sizeof(int) + 255) / 256 * 256;
+  const size_t off_out = off_round + ((size_t)count * sizeof(int) + 255) / 256 * 256;
+  BCS_ALLOC(s0, buf, off_out + (size_t)count * 4 * sizeof(double));
+  int* live = reinterpret_cast<int*>(buf.p + off_live);
+  int* round = reinterpret_cast<int*>(buf.p + off_round);
+  double* out = reinterpret_cast<double*>(buf.p + off_out);
+  for (int i = 0; i < count; ++i) {
+    host[i].live = live + i;
+    host[i].round = round + i;
+  }
+  const BCase* cases = reinterpret_cast<const BCase*>(buf.p);
+  BCS_CU(s0, cudaMemcpyAsync(buf.p, host.data(), (size_t)count * sizeof(BCase), cudaMemcpyHostToDevice, s0->stream));
+  BCS_CU(s0, cudaMemsetAsync(live, 0, (size_t)count * sizeof(int), s0->stream));
+  // every case starts stopped; the ones with work are started per round
+  for (int i = 0; i < count; ++i) BCS_CU(s0, cudaMemsetAsync(ss[i]->kst.p, 0xff, sizeof(KrylovState), s0->stream));
+  cudaGraphExec_t exec = nullptr;
+  long long body = 0;
+  std::vector<double> h_out((size_t)count * 4);
+  bcs_status st = BCS_OK;
+  for (;;) {
+    bool any = false;
+    for (int i = 0; i < count; ++i) any |= active[i] != 0;
+    if (!any) break;
+    int prev_iters = 0;
+    for (int i = 0; i < count; ++i) {
+      if (!active[i]) continue;
+      Solver* s = ss[i];
+      const size_t N = host[i].N;
+      st = scale_copy(s0, 1.0 / beta[i], host[i].r, host[i].V, N);
+      if (st == BCS_OK) st = ks_init(s0, host[i].ks, beta[i], bnorm[i], iters[i], m, s->cfg.maxiter, s->cfg.tol);
+      if (st != BCS_OK) break;
+      prev_iters = std::max(prev_iters, iters[i]);
+    }
+    if (st != BCS_OK) break;
+    BCS_CU(s0, cudaMemcpyAsync(round, active.data(), (size_t)count * sizeof(int), cudaMemcpyHostToDevice, s0->stream));
+    if (!exec) {
+      st = capture_batch(s0, cases, host, count, m, maxN, max_rows, &exec, &body);
+      if (st != BCS_OK) break;
+    }
+    if (cudaGraphLaunch(exec, s0->stream) != cudaSuccess) {
+      st = s0->fail(BCS_ECUDA, "batched loop launch failed");
+      break;
+    }
+    st = kb_finish(s0, cases, count, maxN);
+    if (st == BCS_OK) st = kb_resid_r(s0, cases, count, max_rows);
+    if (st == BCS_OK) st = kb_norm_r(s0, cases, count);
+    if (st == BCS_OK) st = kb_gather_out(s0, cases, count, out);
+    if (st != BCS_OK) break;
+    if (cudaMemcpyAsync(h_out.data(), out, h_out.size() * sizeof(double), cudaMemcpyDeviceToHost, s0->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s0->stream) != cudaSuccess) {
+      st = s0->fail(BCS_ECUDA, "batched solve: reading the round's outcome failed");
+      break;
+    }
+    int steps = 0;
+    for (int i = 0; i < count; ++i) {
+      if (!active[i]) continue;
+      Solver* s = ss[i];
+      const int it = (int)h_out[4 * i + 1];
+      steps = std::max(steps, it - iters[i]);
+      iters[i] = it;
+      beta[i] = std::sqrt(h_out[4 * i]);
+      res[i].rel_res_final = beta[i] / bnorm[i];
+      const bool breakdown = (int)h_out[4 * i + 3] == KS_BREAKDOWN;
+      if (breakdown || !std::isfinite(beta[i])) {
+        status[i] = BCS_BREAKDOWN;
+        active[i] = 0;
+      } else if (beta[i] <= s->cfg.tol * bnorm[i]) {
+        status[i] = BCS_OK;
+        active[i] = 0;
+      } else if (iters[i] >= s->cfg.maxiter) {
+        status[i] = BCS_NOT_CONVERGED;
+        active[i] = 0;
+      } else {
+        res[i].restarts++;
+      }
+    }
+    s0->launches += body * steps;
+    (void)prev_iters;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (st != BCS_OK) return st;
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < count; ++i) {
+    res[i].iters = iters[i];
+    res[i].status = status[i];
+    res[i].solve_ms = ms;
+  }
+  return BCS_OK;
 }
 
 }  // namespace bcs
