@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=200.0)
     p.add_argument("--serve-max-cells", type=float, default=3e6)
     p.add_argument("--serve-slots", type=int, default=8)
+    p.add_argument("--serve-batch", type=int, default=1,
+                   help="serving: solve up to this many resident cases' requests together (1: off)")
     p.add_argument("--serve-budget-gb", type=float, default=0.0,
                    help="HBM budget of the server in GB (0: the default, 80 %% of free memory)")
     return p.parse_args()
@@ -780,7 +782,7 @@ def run_serve(args):
     keys = ("diag", "upper", "lower", "b")
     t0 = time.perf_counter()
     budget = int(args.serve_budget_gb * 1e9)
-    with bcs.Server(budget_bytes=budget, slots=args.serve_slots) as srv:
+    with bcs.Server(budget_bytes=budget, slots=args.serve_slots, batch=args.serve_batch) as srv:
         cases, ids, kinds = [], [], []
         for c in range(ncases):
             nx = int(round(cells[c] ** (1.0 / 3.0)))
@@ -852,6 +854,7 @@ def run_serve(args):
                     "mean_ms": float(lat.mean()), "iters_max": int(max(iters)),
                     "evictions": stats["evictions"], "rejected": stats["rejected"],
                     "resident_bytes": stats["resident_bytes"], "budget_bytes": stats["budget_bytes"],
+                    "batches": stats["batches"], "batched_requests": stats["batched_requests"],
                     "gpu_timeline": {"window_ms": stats["window_ms"], "busy_frac": stats["busy_frac"],
                                      "overlap2_frac": stats["overlap_frac"],
                                      "mean_requests_in_flight": stats["mean_in_flight"],
@@ -867,6 +870,7 @@ def run_serve(args):
     print(json.dumps({"impl": "native", "mode": "serve", "cases": ncases,
                       "cells_range": [5e4, max_cells], "cells_mean": float(cells.mean()),
                       "block_sizes": {"5": kinds.count(5), "4": kinds.count(4)}, "slots": args.serve_slots,
+                      "batch": args.serve_batch,
                       "budget": "default (80 % of free memory)" if budget == 0 else f"{args.serve_budget_gb:g} GB",
                       "inputs": "two value sets per case resident in device memory, alternated per request",
                       "setup_s": gen_s, "configured_rate": configured, "closed_loop_capacity": capacity,

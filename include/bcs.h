@@ -341,6 +341,9 @@ BCS_API const char* bcs_kernel_kind_name(int k);
  * evicting least-recently-used idle cases; a case larger than the budget is
  * answered with BCS_REJECTED. Results are deterministic per case, the same
  * alone or in any mix. */
+/* Largest batch of bcs_solve_batch and of a server's batching. */
+#define BCS_BATCH_MAX 64
+
 typedef struct bcs_server bcs_server;
 
 typedef struct bcs_server_stats {
@@ -355,6 +358,7 @@ typedef struct bcs_server_stats {
    * covered by two or more (their kernels in flight together);
    * mean_in_flight: summed interval lengths over the window. */
   double window_ms, busy_frac, overlap_frac, mean_in_flight;
+  long long batches, batched_requests;  /* batched solves run and the requests they served */
 } bcs_server_stats;
 
 /* budget_bytes = 0: 80 % of the device's free memory. slots: 1..64. cfg may
@@ -378,6 +382,14 @@ BCS_API bcs_status bcs_server_submit(bcs_server* srv, int case_id, const double*
  * stays valid). res and latency_ms (submit -> completion) may be NULL. */
 BCS_API bcs_status bcs_server_wait(bcs_server* srv, int64_t ticket, int timeout_ms, bcs_result* res,
                                   double* latency_ms);
+/* Batching (default 1: off): a slot that takes a request of a resident case
+ * also takes the first queued request of up to max_batch - 1 other idle
+ * resident cases with the same block size and memory kind, runs each
+ * case's values-only resetup and solves them together with
+ * bcs_solve_batch (each result equal to the case's solve alone; a batch the
+ * batched solver refuses is solved case by case). 1 <= max_batch <=
+ * BCS_BATCH_MAX, else BCS_EINVAL. */
+BCS_API bcs_status bcs_server_set_batch(bcs_server* srv, int max_batch);
 BCS_API bcs_status bcs_server_get_stats(bcs_server* srv, bcs_server_stats* st);
 BCS_API bcs_status bcs_server_reset_stats(bcs_server* srv);
 
@@ -428,7 +440,6 @@ BCS_API bcs_status bcs_ldu_structure_noalloc(int32_t n_cells, int32_t n_faces, c
  * on solvers[0]'s stream after every solver's stream is synchronised; the
  * call returns when it is complete. res[i] receives system i's result; the
  * return value is BCS_OK, or the first non-OK status among the systems. */
-#define BCS_BATCH_MAX 64
 BCS_API bcs_status bcs_solve_batch(bcs_solver* const* solvers, int count, const double* const* b, double* const* x,
                                    int mem, bcs_result* res);
 

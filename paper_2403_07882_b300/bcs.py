@@ -66,7 +66,7 @@ class bcs_server_stats(ct.Structure):
                 ("resident_bytes", ct.c_size_t), ("budget_bytes", ct.c_size_t), ("resident_cases", ct.c_int),
                 ("p50_ms", ct.c_double), ("p99_ms", ct.c_double), ("mean_ms", ct.c_double),
                 ("window_ms", ct.c_double), ("busy_frac", ct.c_double), ("overlap_frac", ct.c_double),
-                ("mean_in_flight", ct.c_double)]
+                ("mean_in_flight", ct.c_double), ("batches", ct.c_longlong), ("batched_requests", ct.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -141,6 +141,7 @@ def lib():
             "bcs_server_wait": (ct.c_int, [_vp, ct.c_int64, ct.c_int, ct.POINTER(bcs_result),
                                            ct.POINTER(ct.c_double)]),
             "bcs_server_get_stats": (ct.c_int, [_vp, ct.POINTER(bcs_server_stats)]),
+            "bcs_server_set_batch": (ct.c_int, [_vp, ct.c_int]),
             "bcs_server_reset_stats": (ct.c_int, [_vp]),
         }
         for name, (res, args) in sig.items():
@@ -160,7 +161,7 @@ def exported_names():
             "bcs_get_coarse_inverse", "bcs_get_dilu", "bcs_get_stats", "bcs_reset_stats", "bcs_get_kernel_times", "bcs_kernel_kind_name",
             "bcs_last_error", "bcs_device_bytes", "bcs_ldu_structure_noalloc", "bcs_server_create",
             "bcs_server_destroy", "bcs_server_register_case", "bcs_server_submit", "bcs_server_wait",
-            "bcs_server_get_stats", "bcs_server_reset_stats"]
+            "bcs_server_get_stats", "bcs_server_reset_stats", "bcs_server_set_batch"]
 
 
 # ------------------------------------------------------------ marshalling
@@ -790,9 +791,11 @@ def bcs_server_reset_stats(h):
 class Server:
     """Owning wrapper of a serving instance; keeps submitted arrays alive."""
 
-    def __init__(self, budget_bytes=0, slots=4, **cfg):
+    def __init__(self, budget_bytes=0, slots=4, batch=1, **cfg):
         self.h = bcs_server_create(budget_bytes, slots, bcs_config_default(**cfg))
         self._keep = {}
+        if batch != 1:
+            _check(lib().bcs_server_set_batch(self.h, batch))
 
     def close(self):
         if getattr(self, "h", None):

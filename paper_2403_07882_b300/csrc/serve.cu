@@ -70,6 +70,8 @@ struct bcs_server {
   int64_t next_ticket = 1;
   uint64_t clock = 0;
   long long submitted = 0, completed = 0, rejected = 0, evictions = 0, admissions = 0;
+  long long batches = 0, batched = 0;
+  int max_batch = 1;  // > 1: a worker solves up to this many resident cases' requests together
   std::vector<double> latencies;
   std::vector<std::pair<double, double>> spans;  // request intervals on the GPU timeline (ms from t0)
   cudaEvent_t t0 = nullptr;                       // reference of the timeline, recorded at create / reset
@@ -172,6 +174,78 @@ void finish(bcs_server* srv, const Request& r, const bcs_result& res) {
   srv->completed++;
 }
 
+// A batch of requests of distinct resident cases: each case's values-only
+// resetup on its own stream, then one batched solve (the results equal the
+// cases' solves alone bit for bit); requests whose resetup fails are
+// answered on their own, and a batch the batched solver refuses is solved
+// case by case.
+void serve_batch(bcs_server* srv, const std::vector<Request>& reqs) {
+  const int k = (int)reqs.size();
+  std::vector<bcs_status> st(k, BCS_OK);
+  std::vector<bcs_result> res(k);
+  std::vector<bool> timed(k, false);
+  std::vector<bcs_solver*> solvers;
+  std::vector<const double*> bs;
+  std::vector<double*> xs;
+  std::vector<int> idx;
+  for (int i = 0; i < k; ++i) {
+    Case& c = *srv->cases[reqs[i].case_id];
+    timed[i] = cudaEventRecord(c.ev_a, c.stream) == cudaSuccess;
+    st[i] = bcs_set_values(c.solver, reqs[i].diag, reqs[i].upper, reqs[i].lower, reqs[i].mem);
+    if (st[i] == BCS_OK) {
+      solvers.push_back(c.solver);
+      bs.push_back(reqs[i].b);
+      xs.push_back(reqs[i].x);
+      idx.push_back(i);
+    }
+  }
+  if (!solvers.empty()) {
+    std::vector<bcs_result> br(solvers.size());
+    const bcs_status bst = bcs_solve_batch(solvers.data(), (int)solvers.size(), bs.data(), xs.data(),
+                                           reqs[idx[0]].mem, br.data());
+    const bool refused = bst == BCS_EINVAL || bst == BCS_ESTATE || bst == BCS_ECUDA || bst == BCS_ENOMEM;
+    for (size_t q = 0; q < idx.size(); ++q) {
+      const int i = idx[q];
+      Case& c = *srv->cases[reqs[i].case_id];
+      if (refused) st[i] = bcs_solve(c.solver, reqs[i].b, reqs[i].x, reqs[i].mem, &res[i]);
+      else {
+        res[i] = br[q];
+        st[i] = (bcs_status)br[q].status;
+      }
+    }
+    if (!refused) {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      srv->batches++;
+      srv->batched += (long long)idx.size();
+    }
+  }
+  std::lock_guard<std::mutex> lk(srv->mu);
+  for (int i = 0; i < k; ++i) {
+    Case& c = *srv->cases[reqs[i].case_id];
+    res[i].status = st[i];
+    // the batch ran on the first solver's stream: its end closes every span
+    cudaStream_t end_stream = solvers.empty() ? c.stream : srv->cases[reqs[idx[0]].case_id]->stream;
+    if (timed[i] && st[i] != BCS_ECUDA && cudaEventRecord(c.ev_b, end_stream) == cudaSuccess &&
+        cudaEventSynchronize(c.ev_b) == cudaSuccess) {
+      float a = 0.f, b = 0.f;
+      if (cudaEventElapsedTime(&a, srv->t0, c.ev_a) == cudaSuccess &&
+          cudaEventElapsedTime(&b, srv->t0, c.ev_b) == cudaSuccess && b > 0.f)
+        srv->spans.push_back({std::max(0.f, a), b});
+      else
+        (void)cudaGetLastError();
+    }
+    if (st[i] == BCS_ECUDA || st[i] == BCS_ENOMEM || st[i] == BCS_SINGULAR_BLOCK || st[i] == BCS_EINVAL) {
+      srv->resident -= c.bytes;
+      c.bytes = 0;
+      drop_device_state(c);
+    }
+    c.busy = false;
+    finish(srv, reqs[i], res[i]);
+  }
+  srv->done_cv.notify_all();
+  srv->work_cv.notify_all();
+}
+
 void worker(bcs_server* srv) {
   cudaSetDevice(srv->device);
   std::unique_lock<std::mutex> lk(srv->mu);
@@ -211,6 +285,29 @@ void worker(bcs_server* srv) {
     c.busy = true;
     c.last_use = ++srv->clock;
     const bool fresh = c.solver == nullptr;
+    // batching: the first queued request of other idle resident cases with
+    // the same block size and memory kind join this one
+    std::vector<Request> more;
+    if (srv->max_batch > 1 && !fresh) {
+      for (auto q = srv->queue.begin(); q != srv->queue.end() && (int)more.size() + 1 < srv->max_batch;) {
+        Case& o = *srv->cases[q->case_id];
+        if (!o.busy && o.solver && o.n == c.n && q->mem == r.mem) {
+          o.busy = true;
+          o.last_use = ++srv->clock;
+          more.push_back(*q);
+          q = srv->queue.erase(q);
+        } else {
+          ++q;
+        }
+      }
+    }
+    if (!more.empty()) {
+      lk.unlock();
+      more.insert(more.begin(), r);
+      serve_batch(srv, more);
+      lk.lock();
+      continue;
+    }
     lk.unlock();
 
     bcs_result res{};
@@ -373,6 +470,13 @@ BCS_API bcs_status bcs_server_wait(bcs_server* srv, int64_t ticket, int timeout_
   return (bcs_status)d.res.status;
 }
 
+BCS_API bcs_status bcs_server_set_batch(bcs_server* srv, int max_batch) {
+  if (!srv || max_batch < 1 || max_batch > BCS_BATCH_MAX) return BCS_EINVAL;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  srv->max_batch = max_batch;
+  return BCS_OK;
+}
+
 BCS_API bcs_status bcs_server_get_stats(bcs_server* srv, bcs_server_stats* st) {
   if (!srv || !st) return BCS_EINVAL;
   std::lock_guard<std::mutex> lk(srv->mu);
@@ -388,6 +492,8 @@ BCS_API bcs_status bcs_server_get_stats(bcs_server* srv, bcs_server_stats* st) {
   int res_cases = 0;
   for (auto& c : srv->cases) res_cases += c->solver != nullptr;
   st->resident_cases = res_cases;
+  st->batches = srv->batches;
+  st->batched_requests = srv->batched;
   if (!srv->latencies.empty()) {
     std::vector<double> l = srv->latencies;
     std::sort(l.begin(), l.end());
@@ -418,6 +524,7 @@ BCS_API bcs_status bcs_server_reset_stats(bcs_server* srv) {
   srv->latencies.clear();
   srv->spans.clear();
   srv->submitted = srv->completed = srv->rejected = srv->evictions = srv->admissions = 0;
+  srv->batches = srv->batched = 0;
   if (cudaEventRecord(srv->t0, srv->tstream) != cudaSuccess || cudaEventSynchronize(srv->t0) != cudaSuccess)
     return BCS_ECUDA;
   return BCS_OK;

@@ -159,3 +159,41 @@ def test_gpu_timeline_statistics():
             assert st["overlap_frac"] > 0.0 and st["mean_in_flight"] > 1.0
         print(f"slots={slots}: window {st['window_ms']:.1f} ms busy {st['busy_frac']:.3f} "
               f"overlap {st['overlap_frac']:.3f} in flight {st['mean_in_flight']:.2f}")
+
+
+def test_batching_server_results_identical():
+    """With batching on, a slot solves the queued requests of several
+    resident cases of the same block size together (bcs_solve_batch); each
+    result equals the case's result alone, bit for bit, and batches form."""
+    systems = [synth.density(10, seed=1), synth.density(12, 9, 7, seed=3), synth.density(8, seed=7),
+               synth.pressure(8, seed=2), synth.density(11, 10, 6, seed=9)]
+    seqs = sequences(systems)
+    alone = []
+    for c, system in enumerate(systems):
+        with bcs.Server(slots=1) as srv:
+            cid = srv.register(system)
+            # the same history as below: a full setup on the system's own
+            # values, then values-only resetups
+            assert srv.wait(srv.submit(cid, system))[0] == bcs.BCS_OK
+            xs = []
+            for s in seqs[c]:
+                st, res, lat, x = srv.wait(srv.submit(cid, s))
+                assert st == bcs.BCS_OK, res
+                xs.append(x)
+            alone.append(xs)
+    with bcs.Server(slots=1, batch=8) as srv:
+        ids = [srv.register(s) for s in systems]
+        for c in range(len(systems)):          # first admission of every case
+            assert srv.wait(srv.submit(ids[c], systems[c]))[0] == bcs.BCS_OK
+        srv.reset_stats()
+        tickets = []
+        for j in range(3):
+            for c in range(len(systems)):
+                tickets.append((c, j, srv.submit(ids[c], seqs[c][j])))
+        for c, j, t in tickets:
+            st, res, lat, x = srv.wait(t)
+            assert st == bcs.BCS_OK, res
+            assert np.array_equal(x, alone[c][j]), (c, j)
+        stats = srv.stats()
+    assert stats["batches"] >= 1 and stats["batched_requests"] >= 2
+    print(f"batches {stats['batches']} serving {stats['batched_requests']} of 15 requests")
