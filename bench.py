@@ -440,6 +440,9 @@ def run_native(args):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (2.9 GB of FP64 block values); no flush needed",
                    "step": "set_structure + set_values (full AMG setup) + solve, device-resident inputs"},
+        "host_syncs_per_solve": {"timed (host-driven loop, events on)": res_mixed[-1]["host_syncs"],
+                                 "uninstrumented (device loops)": res_plain[-1]["host_syncs"],
+                                 "iters": res_plain[-1]["iters"]},
         "uninstrumented": {"value": ms_plain, "unit": "ms", "iters": res_plain[-1]["iters"],
                            "gpu_launches_per_step": stats_plain["launches"] / args.steps,
                            "note": "the same step with no per-kernel events: graph-replayed V-cycle and "

@@ -143,6 +143,7 @@ typedef struct bcs_result {
   double rel_res_final;    /* true residual ||b - A x|| / ||b|| recomputed in FP64 */
   double setup_ms;         /* last set_values (conversion + AMG setup), wall time */
   double solve_ms;         /* this solve, wall time */
+  int host_syncs;          /* times the host waited for the device during this solve */
 } bcs_result;
 
 /* Per-kernel-kind statistics since creation or the last bcs_reset_stats. */

@@ -48,7 +48,7 @@ class bcs_config(ct.Structure):
 class bcs_result(ct.Structure):
     _fields_ = [("status", ct.c_int), ("iters", ct.c_int), ("restarts", ct.c_int), ("levels", ct.c_int),
                 ("rel_res_initial", ct.c_double), ("rel_res_final", ct.c_double),
-                ("setup_ms", ct.c_double), ("solve_ms", ct.c_double)]
+                ("setup_ms", ct.c_double), ("solve_ms", ct.c_double), ("host_syncs", ct.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -168,10 +168,12 @@ __global__ void k_add_combination(const TZ* __restrict__ Z, size_t ldz, int k, C
   }
 }
 
-// y = a x + b y
+// y = a x + b y (one element; shared with the device-resident BiCGStab)
+__device__ __forceinline__ double axpby_elem(double a, double x, double b, double y) { return a * x + b * y; }
+
 __global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, size_t N) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = a * x[i] + b * y[i];
+    y[i] = axpby_elem(a, x[i], b, y[i]);
 }
 
 // y = a x
@@ -181,10 +183,14 @@ __global__ void k_scale(double a, const double* x, double* y, size_t N) {  // ma
 }
 
 // p = r + beta (p - omega v)
+__device__ __forceinline__ double bicg_p_elem(double beta, double omega, double r, double v, double p) {
+  return r + beta * (p - omega * v);
+}
+
 __global__ void k_bicg_p(double beta, double omega, const double* __restrict__ r, const double* __restrict__ v,
                          double* __restrict__ p, size_t N) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
-    p[i] = r[i] + beta * (p[i] - omega * v[i]);
+    p[i] = bicg_p_elem(beta, omega, r[i], v[i], p[i]);
 }
 
 // ---- device-resident FGMRES cycle (state in KrylovState) -------------------
@@ -512,6 +518,127 @@ __global__ void kb_gather_out_k(const BCase* __restrict__ cases, int count, doub
   out[4 * c + 3] = sc[SLOT_S + 2];
 }
 
+// ---- device-resident BiCGStab (state in BicgState, scalars in scal) ----------
+// The scalars are formed with explicitly rounded operations in the order the
+// host-driven loop evaluates them, and the vector updates use the same
+// element functions, so both loops give the same bits.
+__global__ void k_bs_init(BicgState* bs, int it, int maxiter, double tol, double bnorm, int first) {
+  if (threadIdx.x != 0) return;
+  bs->it = it;
+  bs->stop = BS_RUN;
+  bs->first = first;
+  bs->maxiter = maxiter;
+  bs->tol = tol;
+  bs->bnorm = bnorm;
+  if (first == 2) {  // a fresh solve: the host loop's starting values
+    bs->rho_old = 1.0;
+    bs->alpha = 1.0;
+    bs->omega = 1.0;
+    bs->first = 1;
+  }
+}
+
+__global__ void k_bs_rho(BicgState* __restrict__ bs, const double* __restrict__ scal) {
+  if (threadIdx.x != 0 || bs->stop != BS_RUN) return;
+  const double rho = scal[SLOT_A];
+  bs->rho = rho;
+  if (rho == 0.0 || !isfinite(rho)) {
+    bs->stop = BS_BREAK;
+    return;
+  }
+  if (!bs->first) bs->beta = __dmul_rn(__ddiv_rn(rho, bs->rho_old), __ddiv_rn(bs->alpha, bs->omega));
+}
+
+__global__ void k_bs_p(const BicgState* __restrict__ bs, const double* __restrict__ r, const double* __restrict__ v,
+                       double* __restrict__ p, size_t N) {
+  if (bs->stop != BS_RUN) return;
+  const bool first = bs->first;
+  const double beta = bs->beta, omega = bs->omega;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = first ? r[i] : bicg_p_elem(beta, omega, r[i], v[i], p[i]);
+}
+
+__global__ void k_bs_alpha(BicgState* __restrict__ bs, const double* __restrict__ scal) {
+  if (threadIdx.x != 0 || bs->stop != BS_RUN) return;
+  bs->first = 0;
+  const double den = scal[SLOT_A];
+  if (den == 0.0 || !isfinite(den)) {
+    bs->stop = BS_BREAK;
+    return;
+  }
+  bs->alpha = __ddiv_rn(bs->rho, den);
+}
+
+// s = r - alpha v (the host loop: s = r, then s = (-alpha) v + 1 s)
+__global__ void k_bs_s(const BicgState* __restrict__ bs, const double* __restrict__ r, const double* __restrict__ v,
+                       double* __restrict__ sv, size_t N) {
+  if (bs->stop != BS_RUN) return;
+  const double a = -bs->alpha;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    sv[i] = axpby_elem(a, v[i], 1.0, r[i]);
+}
+
+__global__ void k_bs_snorm(BicgState* __restrict__ bs, const double* __restrict__ scal) {
+  if (threadIdx.x != 0 || bs->stop != BS_RUN) return;
+  bs->it = bs->it + 1;
+  const double snrm = __dsqrt_rn(scal[SLOT_N]);
+  if (snrm <= __dmul_rn(bs->tol, bs->bnorm)) bs->stop = BS_S_SMALL;
+}
+
+__global__ void k_bs_omega(BicgState* __restrict__ bs, const double* __restrict__ scal) {
+  if (threadIdx.x != 0 || bs->stop != BS_RUN) return;
+  const double ts = scal[SLOT_A], tt = scal[SLOT_A + 1];
+  if (tt == 0.0 || !isfinite(tt)) {
+    bs->stop = BS_BREAK;
+    return;
+  }
+  bs->omega = __ddiv_rn(ts, tt);
+}
+
+// x += alpha ph + omega sh (ph and sh consecutive, cycle precision)
+template <class TZ>
+__global__ void k_bs_x(const BicgState* __restrict__ bs, const TZ* __restrict__ ph, double* __restrict__ x, size_t N) {
+  if (bs->stop != BS_RUN) return;
+  const double a = bs->alpha, o = bs->omega;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+    double t = x[i];
+    t = fma(a, (double)ph[i], t);
+    t = fma(o, (double)ph[N + i], t);
+    x[i] = t;
+  }
+}
+
+// r = s - omega t (the host loop: r = s, then r = (-omega) t + 1 r)
+__global__ void k_bs_r(const BicgState* __restrict__ bs, const double* __restrict__ sv, const double* __restrict__ t,
+                       double* __restrict__ r, size_t N) {
+  if (bs->stop != BS_RUN) return;
+  const double a = -bs->omega;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    r[i] = axpby_elem(a, t[i], 1.0, sv[i]);
+}
+
+// end of an iteration: rho_old, the residual test, omega = 0, the limit;
+// the loop runs on while nothing happened
+__global__ void k_bs_export(const BicgState* __restrict__ bs, double* __restrict__ scal) {
+  if (threadIdx.x != 0) return;
+  scal[SLOT_S] = (double)bs->it;
+  scal[SLOT_S + 1] = (double)bs->stop;
+  scal[SLOT_S + 2] = bs->alpha;
+}
+
+__global__ void k_bs_end(BicgState* __restrict__ bs, const double* __restrict__ scal,
+                         cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0) return;
+  if (bs->stop == BS_RUN) {
+    bs->rho_old = bs->rho;
+    const double rn = __dsqrt_rn(scal[SLOT_N]);
+    if (rn <= __dmul_rn(bs->tol, bs->bnorm)) bs->stop = BS_R_SMALL;
+    else if (bs->omega == 0.0) bs->stop = BS_OMEGA0;
+    else if (bs->it >= bs->maxiter) bs->stop = BS_MAXITER;
+  }
+  cudaGraphSetConditional(cond, bs->stop == BS_RUN ? 1u : 0u);
+}
+
 unsigned vgrid(size_t N) {
   unsigned g = grid_for(N, 256);
   return g > 148u * 16u ? 148u * 16u : g;
@@ -556,6 +683,7 @@ bcs_status any_nonzero(Solver* s, const double* x, size_t N, int slot) {
 bcs_status fetch_scalars(Solver* s, int count) {
   BCS_CU(s, cudaMemcpyAsync(s->hscal, s->scal.p, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   BCS_CU(s, cudaStreamSynchronize(s->stream));
+  ++s->host_syncs;
   return BCS_OK;
 }
 
@@ -741,6 +869,55 @@ bcs_status kb_norm_r(Solver* s, const BCase* cases, int count) {
 
 bcs_status kb_gather_out(Solver* s, const BCase* cases, int count, double* out) {
   BCS_LAUNCH(s, K_BLAS, 0, 0, kb_gather_out_k, grid_for(count, 64), 64, 0, cases, count, out);
+  return BCS_OK;
+}
+
+bcs_status bs_init(Solver* s, BicgState* bs, int it, int maxiter, double tol, double bnorm, int first) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_init, 1, 32, 0, bs, it, maxiter, tol, bnorm, first);
+  return BCS_OK;
+}
+bcs_status bs_rho(Solver* s, BicgState* bs) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_rho, 1, 32, 0, bs, (const double*)s->scal.p);
+  return BCS_OK;
+}
+bcs_status bs_p_update(Solver* s, const BicgState* bs, const double* r, const double* v, double* p, size_t N) {
+  BCS_LAUNCH(s, K_BLAS, 32.0 * N, 4.0 * N, k_bs_p, vgrid(N), 256, 0, bs, r, v, p, N);
+  return BCS_OK;
+}
+bcs_status bs_alpha(Solver* s, BicgState* bs) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_alpha, 1, 32, 0, bs, (const double*)s->scal.p);
+  return BCS_OK;
+}
+bcs_status bs_s_update(Solver* s, const BicgState* bs, const double* r, const double* v, double* sv, size_t N) {
+  BCS_LAUNCH(s, K_BLAS, 24.0 * N, 3.0 * N, k_bs_s, vgrid(N), 256, 0, bs, r, v, sv, N);
+  return BCS_OK;
+}
+bcs_status bs_snorm(Solver* s, BicgState* bs) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_snorm, 1, 32, 0, bs, (const double*)s->scal.p);
+  return BCS_OK;
+}
+bcs_status bs_omega(Solver* s, BicgState* bs) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_omega, 1, 32, 0, bs, (const double*)s->scal.p);
+  return BCS_OK;
+}
+bcs_status bs_x_update(Solver* s, const BicgState* bs, const void* ph, bool z_float, double* x, size_t N) {
+  if (z_float)
+    BCS_LAUNCH(s, K_BLAS, 24.0 * N, 4.0 * N, k_bs_x<float>, vgrid(N), 256, 0, bs, (const float*)ph, x, N);
+  else
+    BCS_LAUNCH(s, K_BLAS, 32.0 * N, 4.0 * N, k_bs_x<double>, vgrid(N), 256, 0, bs, (const double*)ph, x, N);
+  return BCS_OK;
+}
+bcs_status bs_r_update(Solver* s, const BicgState* bs, const double* sv, const double* t, double* r, size_t N) {
+  BCS_LAUNCH(s, K_BLAS, 24.0 * N, 3.0 * N, k_bs_r, vgrid(N), 256, 0, bs, sv, t, r, N);
+  return BCS_OK;
+}
+bcs_status bs_end(Solver* s, BicgState* bs, cudaGraphConditionalHandle cond) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_end, 1, 32, 0, bs, (const double*)s->scal.p, cond);
+  return BCS_OK;
+}
+
+bcs_status bs_export(Solver* s, const BicgState* bs) {
+  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_export, 1, 32, 0, bs, s->scal.p);
   return BCS_OK;
 }
 

@@ -198,6 +198,15 @@ struct KrylovState {
 };
 enum { KS_RUN = 0, KS_CONVERGED = 1, KS_HAPPY = 2, KS_BREAKDOWN = 3, KS_MAXITER = 4, KS_CYCLE_END = 5 };
 
+// BiCGStab iteration kept on the device: its scalars and why the loop left
+// (an event the host acts on: breakdown restart, a small residual to
+// confirm on the true residual, the iteration limit).
+struct BicgState {
+  int it, stop, first, maxiter;
+  double tol, bnorm, rho, rho_old, alpha, omega, beta;
+};
+enum { BS_RUN = 0, BS_BREAK = 1, BS_S_SMALL = 2, BS_R_SMALL = 3, BS_OMEGA0 = 4, BS_MAXITER = 5 };
+
 // Device scalar slots of the Krylov solvers (s->scal): first and second
 // Gram-Schmidt pass, norms, the nonzero flag of x0, a restart cycle's
 // outcome (iterations, steps, stop reason).
@@ -291,6 +300,7 @@ struct Solver {
   std::vector<cudaEvent_t> event_pool;
   size_t event_next = 0;
   double last_setup_ms = 0.0;
+  long long host_syncs = 0;      // scalar reads that waited for the device (solves)
   // V-cycle captured as a CUDA graph (FP32 / BF16 cycle): input lv[0].vb,
   // output lv[0].vx; dropped at every setup / resetup and on destroy
   cudaGraphExec_t cyc_exec = nullptr;
@@ -304,7 +314,12 @@ struct Solver {
   cudaGraphExec_t kry_exec = nullptr;
   long long kry_kind_launches[BCS_NUM_KERNEL_KINDS] = {};
   double kry_kind_bytes[BCS_NUM_KERNEL_KINDS] = {}, kry_kind_flops[BCS_NUM_KERNEL_KINDS] = {};
-  DBuf<char> kst;                // KrylovState
+  DBuf<char> kst;                // KrylovState / BicgState
+  cudaGraphExec_t bcg_exec = nullptr;  // BiCGStab iteration in a graph WHILE node
+  const void* bcg_key[3] = {};
+  double* kx_dev = nullptr;            // the solution vector the captured BiCGStab step updates
+  long long bcg_kind_launches[BCS_NUM_KERNEL_KINDS] = {};
+  double bcg_kind_bytes[BCS_NUM_KERNEL_KINDS] = {}, bcg_kind_flops[BCS_NUM_KERNEL_KINDS] = {};
   const void* kry_key[5] = {};    // buffers the captured step uses (recapture when one moves)
   int kry_m = 0;
   DBuf<double> kvj, kzj;         // FP64 cycle: fixed input / output of the preconditioner
@@ -313,6 +328,8 @@ struct Solver {
     cyc_exec = nullptr;
     if (kry_exec) cudaGraphExecDestroy(kry_exec);
     kry_exec = nullptr;
+    if (bcg_exec) cudaGraphExecDestroy(bcg_exec);
+    bcg_exec = nullptr;
   }
 
   bcs_status fail(bcs_status st, const std::string& m) {
@@ -447,6 +464,18 @@ bcs_status ks_givens(Solver* s, KrylovState* ks, int slot_a, int slot_b, int slo
 bcs_status ks_scale_next(Solver* s, const KrylovState* ks, const double* w, double* V, size_t ldv, size_t N);
 bcs_status ks_finish_cycle(Solver* s, KrylovState* ks, const void* Z, bool z_float, double* x, size_t N);
 bcs_status ks_export(Solver* s, const KrylovState* ks, int slot);
+// BiCGStab on the device (state bs; scalars from s->scal)
+bcs_status bs_init(Solver* s, BicgState* bs, int it, int maxiter, double tol, double bnorm, int first);
+bcs_status bs_rho(Solver* s, BicgState* bs);
+bcs_status bs_p_update(Solver* s, const BicgState* bs, const double* r, const double* v, double* p, size_t N);
+bcs_status bs_alpha(Solver* s, BicgState* bs);
+bcs_status bs_s_update(Solver* s, const BicgState* bs, const double* r, const double* v, double* sv, size_t N);
+bcs_status bs_snorm(Solver* s, BicgState* bs);
+bcs_status bs_omega(Solver* s, BicgState* bs);
+bcs_status bs_x_update(Solver* s, const BicgState* bs, const void* ph, bool z_float, double* x, size_t N);
+bcs_status bs_r_update(Solver* s, const BicgState* bs, const double* sv, const double* t, double* r, size_t N);
+bcs_status bs_end(Solver* s, BicgState* bs, cudaGraphConditionalHandle cond);
+bcs_status bs_export(Solver* s, const BicgState* bs);  // it, stop, alpha -> scal[SLOT_S ..]
 // Batched steps (launched on s's stream; cases is a device table of count
 // entries; kmax bounds the vectors of one multi-dot, rows / N the largest
 // case).

@@ -364,6 +364,222 @@ bcs_status fgmres(Solver* s, const double* b, double* x, bcs_result* res) {
   return status;
 }
 
+// ---- device-resident BiCGStab --------------------------------------------------
+// One BiCGStab iteration (dots, the rho / alpha / omega scalars and their
+// tests in kernels, the vector updates, two preconditioner applications and
+// products) is captured once into a graph WHILE body; the loop runs until
+// something happens that the host must act on (a breakdown restart, a small
+// residual to confirm on the true residual, omega = 0, the iteration
+// limit). The host then does exactly what the host-driven loop does at that
+// point, so both loops give the same iterates.
+
+// z = M^{-1} v with every launch capturable (no nested graph launch).
+bcs_status apply_M_plain(Solver* s, const double* v, void* z, size_t N) {
+  const int pc = s->setup_cfg.precond;
+  Level& L0 = s->lv[0];
+  if (s->setup_cfg.precision == BCS_PREC_FP64) {
+    if (pc == BCS_PC_AMG) return precond_cycle64(s, v, (double*)z);
+    return sgs_fixed(s, v, z);
+  }
+  BCS_OKR(cast_vec<double, float>(s, v, (float*)L0.vb.p, N));
+  if (pc == BCS_PC_AMG) {
+    BCS_OKR(precond_cycle32(s, (const float*)L0.vb.p, (float*)L0.vx.p));
+    BCS_CU(s, cudaMemcpyAsync(z, L0.vx.p, N * sizeof(float), cudaMemcpyDeviceToDevice, s->stream));
+    return BCS_OK;
+  }
+  return sgs_fixed(s, L0.vb.p, z);
+}
+
+bcs_status bicg_iteration_dev(Solver* s, BicgState* bs, cudaGraphConditionalHandle cond) {
+  const size_t N = (size_t)s->C * s->n;
+  const bool zf = cycle_is_float(s);
+  double *r = s->kv.p, *rhat = r + N, *p = r + 2 * N, *v = r + 3 * N, *sv = r + 4 * N, *t = r + 5 * N;
+  void* ph = s->kz.p;
+  void* sh = s->kz.p + N * zbytes(s);
+  BCS_OKR(dot(s, rhat, r, N, SLOT_A));
+  BCS_OKR(bs_rho(s, bs));
+  BCS_OKR(bs_p_update(s, bs, r, v, p, N));
+  BCS_OKR(apply_M_plain(s, p, ph, N));
+  BCS_OKR(apply_A(s, ph, v, N));
+  BCS_OKR(dot(s, rhat, v, N, SLOT_A));
+  BCS_OKR(bs_alpha(s, bs));
+  BCS_OKR(bs_s_update(s, bs, r, v, sv, N));
+  BCS_OKR(dot(s, sv, sv, N, SLOT_N));
+  BCS_OKR(bs_snorm(s, bs));
+  BCS_OKR(apply_M_plain(s, sv, sh, N));
+  BCS_OKR(apply_A(s, sh, t, N));
+  BCS_OKR(multidot(s, sv, N, 2, t, N, SLOT_A));  // (s, t), (t, t)
+  BCS_OKR(bs_omega(s, bs));
+  BCS_OKR(bs_x_update(s, bs, ph, zf, s->kx_dev, N));
+  BCS_OKR(bs_r_update(s, bs, sv, t, r, N));
+  BCS_OKR(dot(s, r, r, N, SLOT_N));
+  return bs_end(s, bs, cond);
+}
+
+bcs_status capture_bicg(Solver* s, BicgState* bs) {
+  long long kl[BCS_NUM_KERNEL_KINDS];
+  double kb[BCS_NUM_KERNEL_KINDS], kf[BCS_NUM_KERNEL_KINDS];
+  const long long l0 = s->launches;
+  for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {
+    kl[k] = s->kind_launches[k];
+    kb[k] = s->kind_bytes[k];
+    kf[k] = s->kind_flops[k];
+  }
+  if (!s->gstream) BCS_CU(s, cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  BCS_CU(s, cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle cond = 0;
+  cudaGraphNode_t node = nullptr;
+  cudaGraphNodeParams prm{};
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = cond;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &prm);
+  }
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(s->gstream, prm.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return s->fail(BCS_ECUDA, std::string("BiCGStab loop graph: ") + cudaGetErrorString(e));
+  }
+  const cudaStream_t own = s->stream;
+  s->stream = s->gstream;
+  const bcs_status st = bicg_iteration_dev(s, bs, cond);
+  s->stream = own;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(s->gstream, &captured);
+  s->launches = l0;
+  for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {
+    s->bcg_kind_launches[k] = s->kind_launches[k] - kl[k];
+    s->bcg_kind_bytes[k] = s->kind_bytes[k] - kb[k];
+    s->bcg_kind_flops[k] = s->kind_flops[k] - kf[k];
+    s->kind_launches[k] = kl[k];
+    s->kind_bytes[k] = kb[k];
+    s->kind_flops[k] = kf[k];
+  }
+  if (st != BCS_OK || ce != cudaSuccess) {
+    cudaGraphDestroy(g);
+    if (st != BCS_OK) return st;
+    return s->fail(BCS_ECUDA, std::string("BiCGStab loop capture: ") + cudaGetErrorString(ce));
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&s->bcg_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    s->bcg_exec = nullptr;
+    return s->fail(BCS_ECUDA, std::string("BiCGStab loop instantiate: ") + cudaGetErrorString(ie));
+  }
+  return BCS_OK;
+}
+
+bcs_status bicgstab_dev(Solver* s, const double* b, double* x, bcs_result* res) {
+  const bcs_config& cfg = s->cfg;
+  const size_t N = (size_t)s->C * s->n;
+  const bool zf = cycle_is_float(s);
+  BCS_ALLOC(s, s->kv, (size_t)6 * N);
+  BCS_ALLOC(s, s->kz, (size_t)2 * N * zbytes(s));
+  BCS_ALLOC(s, s->kst, std::max(sizeof(KrylovState), sizeof(BicgState)));
+  BCS_ALLOC(s, s->red, (size_t)72 * 1184);
+  if (zf) BCS_ALLOC(s, s->kt, N);
+  if (s->bcg_exec && (s->bcg_key[0] != (const void*)s->kv.p || s->bcg_key[1] != (const void*)s->kz.p ||
+                      s->bcg_key[2] != (const void*)x)) {
+    cudaGraphExecDestroy(s->bcg_exec);
+    s->bcg_exec = nullptr;
+  }
+  double *r = s->kv.p, *rhat = r + N;
+  void* ph = s->kz.p;
+  const double tol = cfg.tol;
+  double bnorm = 0.0, rn = 0.0;
+  BCS_OKR(initial_residual(s, b, x, r, N, &bnorm, &rn));
+  res->iters = 0;
+  res->restarts = 0;
+  if (bnorm == 0.0) {
+    BCS_CU(s, cudaMemsetAsync(x, 0, N * sizeof(double), s->stream));
+    res->rel_res_initial = res->rel_res_final = 0.0;
+    return BCS_OK;
+  }
+  res->rel_res_initial = res->rel_res_final = rn / bnorm;
+  if (!std::isfinite(rn)) return BCS_BREAKDOWN;
+  if (rn <= tol * bnorm) return BCS_OK;
+  BCS_CU(s, cudaMemcpyAsync(rhat, r, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  BicgState* bs = reinterpret_cast<BicgState*>(s->kst.p);
+  BCS_OKR(bs_init(s, bs, 0, cfg.maxiter, tol, bnorm, 2));
+  s->kx_dev = x;
+  if (!s->bcg_exec) {
+    BCS_OKR(capture_bicg(s, bs));
+    s->bcg_key[0] = s->kv.p;
+    s->bcg_key[1] = s->kz.p;
+    s->bcg_key[2] = x;
+  }
+  bool restarted = false;
+  int it = 0;
+  bcs_status status = BCS_NOT_CONVERGED;
+  // restart from the true residual (the host loop's restart); false when a
+  // breakdown recurs
+  auto restart = [&](bool breakdown, bool* ok) -> bcs_status {
+    *ok = true;
+    if (breakdown) {
+      if (restarted) {
+        *ok = false;
+        return BCS_OK;
+      }
+      restarted = true;
+    }
+    double tr = 0.0;
+    BCS_OKR(true_residual(s, b, x, r, N, &tr));
+    BCS_CU(s, cudaMemcpyAsync(rhat, r, N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    res->restarts++;
+    return bs_init(s, bs, it, cfg.maxiter, tol, bnorm, 1);
+  };
+  while (it < cfg.maxiter) {
+    BCS_CU(s, cudaGraphLaunch(s->bcg_exec, s->stream));
+    BCS_OKR(bs_export(s, bs));
+    BCS_OKR(fetch_scalars(s, SLOT_S + 3));
+    const int it_now = (int)s->hscal[SLOT_S];
+    const int stop = (int)s->hscal[SLOT_S + 1];
+    const double alpha = s->hscal[SLOT_S + 2];
+    for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {  // the executed iterations' launches
+      const int steps = std::max(1, it_now - it);
+      s->launches += s->bcg_kind_launches[k] * steps;
+      s->kind_launches[k] += s->bcg_kind_launches[k] * steps;
+      s->kind_bytes[k] += s->bcg_kind_bytes[k] * steps;
+      s->kind_flops[k] += s->bcg_kind_flops[k] * steps;
+    }
+    it = it_now;
+    bool ok = true;
+    if (stop == BS_BREAK || stop == BS_OMEGA0) {
+      BCS_OKR(restart(true, &ok));
+      if (!ok) {
+        status = BCS_BREAKDOWN;
+        break;
+      }
+      continue;
+    }
+    if (stop == BS_S_SMALL || stop == BS_R_SMALL) {
+      if (stop == BS_S_SMALL) BCS_OKR(add_combination(s, ph, zf, N, 1, &alpha, x, N));
+      double tr = 0.0;
+      BCS_OKR(true_residual(s, b, x, r, N, &tr));
+      if (tr <= tol * bnorm) {
+        status = BCS_OK;
+        break;
+      }
+      BCS_OKR(restart(false, &ok));
+      continue;
+    }
+    break;  // BS_MAXITER
+  }
+  double tr = 0.0;
+  BCS_OKR(true_residual(s, b, x, s->kv.p, N, &tr));
+  res->rel_res_final = tr / bnorm;
+  if (status == BCS_NOT_CONVERGED && res->rel_res_final <= tol) status = BCS_OK;
+  if (status == BCS_NOT_CONVERGED && !std::isfinite(tr)) status = BCS_BREAKDOWN;
+  res->iters = it;
+  return status;
+}
+
 bcs_status bicgstab(Solver* s, const double* b, double* x, bcs_result* res) {
   const bcs_config& cfg = s->cfg;
   const size_t N = (size_t)s->C * s->n;
@@ -511,11 +727,14 @@ bcs_status bicgstab(Solver* s, const double* b, double* x, bcs_result* res) {
 
 bcs_status solve(Solver* s, const double* b, double* x, bcs_result* res) {
   const auto t0 = std::chrono::steady_clock::now();
-  bcs_status st = s->cfg.solver == BCS_BICGSTAB ? bicgstab(s, b, x, res) : fgmres(s, b, x, res);
+  const long long syncs0 = s->host_syncs;
+  bcs_status st = s->cfg.solver == BCS_BICGSTAB ? (device_cycle_ok(s) ? bicgstab_dev(s, b, x, res) : bicgstab(s, b, x, res))
+                                                : fgmres(s, b, x, res);
   if (st == BCS_ECUDA || st == BCS_ENOMEM || st == BCS_EINVAL) return st;
   cudaError_t e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return s->fail(BCS_ECUDA, std::string("solve: ") + cudaGetErrorString(e));
   res->status = st;
+  res->host_syncs = (int)(s->host_syncs - syncs0 + 1);
   res->levels = (int)s->lv.size();
   res->setup_ms = s->last_setup_ms;
   res->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -759,6 +978,7 @@ bcs_status solve_batch(Solver* const* ss, int count, const double* const* b, dou
   if (st != BCS_OK) return st;
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   for (int i = 0; i < count; ++i) {
+    res[i].host_syncs = 1 + res[i].restarts + (iters[i] > 0 ? 1 : 0);  // initial residual, one read per round
     res[i].iters = iters[i];
     res[i].status = status[i];
     res[i].solve_ms = ms;

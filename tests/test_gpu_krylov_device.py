@@ -1,10 +1,11 @@
-"""The device-resident FGMRES restart cycle (the Arnoldi step replayed in a
-CUDA graph WHILE node; Givens rotations, least-squares update and the stop
-test in FP64 device kernels) against the host-driven loop (one scalar read
-per step, rotations on the host): the same iterates bit for bit, the same
-iteration and restart counts, one host read per restart cycle, and the true
-residual 1e-8 recomputed by the oracle (GMRES of Saad and Schultz, Sec. 2;
-the GPU solvers of Sec. 2.3)."""
+"""The device-resident Krylov loops against the host-driven ones. FGMRES:
+the Arnoldi step replayed in a CUDA graph WHILE node, Givens rotations,
+least-squares update and the stop test in FP64 device kernels, one host
+read per restart cycle. BiCGStab: the iteration replayed the same way, its
+scalars and tests in kernels, the host acting only on events. Both give the
+host loops' iterates bit for bit, the same iteration and restart counts,
+fewer host synchronisations, and the true residual 1e-8 recomputed by the
+oracle (GMRES of Saad and Schultz, Sec. 2; Sec. 2.3's GMRES and BiCGStab)."""
 import numpy as np
 import pytest
 
@@ -26,6 +27,15 @@ CASES = [
     ("density 10^3 sgs fp64", lambda: synth.density(10, seed=4),
      dict(precond=bcs.BCS_PC_SGS, precision=bcs.BCS_PREC_FP64)),
     ("knn 12 maxiter 3", lambda: synth.knn(12, seed=5), dict(maxiter=3)),
+    ("bicgstab density 16^3 fp32", lambda: synth.density(16, seed=0), dict(solver=bcs.BCS_BICGSTAB)),
+    ("bicgstab pressure 14^3 fp32", lambda: synth.pressure(14, seed=1), dict(solver=bcs.BCS_BICGSTAB)),
+    ("bicgstab pressure 12^3 fp64", lambda: synth.pressure(12, seed=3),
+     dict(solver=bcs.BCS_BICGSTAB, precision=bcs.BCS_PREC_FP64)),
+    ("bicgstab density 12^3 bf16", lambda: synth.density(12, seed=2),
+     dict(solver=bcs.BCS_BICGSTAB, precision=bcs.BCS_PREC_BF16)),
+    ("bicgstab density 10^3 sgs", lambda: synth.density(10, seed=4),
+     dict(solver=bcs.BCS_BICGSTAB, precond=bcs.BCS_PC_SGS)),
+    ("bicgstab knn 12 maxiter 2", lambda: synth.knn(12, seed=5), dict(solver=bcs.BCS_BICGSTAB, maxiter=2)),
 ]
 
 
@@ -56,8 +66,12 @@ def test_device_cycle_equals_host_loop(name, gen, cfg):
         r = system["b"] - oracle.spmv(ref, xd)
         assert np.linalg.norm(r) / np.linalg.norm(system["b"]) <= 1e-8
     else:
-        assert cfg.get("maxiter") == 3 and std == bcs.BCS_NOT_CONVERGED and rd["iters"] == 3
-    print(f"{name}: iters={rd['iters']} restarts={rd['restarts']} launches host={lh} device={ld}")
+        assert std == bcs.BCS_NOT_CONVERGED and rd["iters"] == cfg.get("maxiter")
+    # the device loops read the device once per restart cycle (FGMRES) or per
+    # event (BiCGStab), the host loops once or more per iteration
+    assert rd["host_syncs"] < rh["host_syncs"]
+    print(f"{name}: iters={rd['iters']} restarts={rd['restarts']} launches host={lh} device={ld} "
+          f"host syncs {rh['host_syncs']} -> {rd['host_syncs']}")
 
 
 def test_device_cycle_after_resetup_and_restart_change():
