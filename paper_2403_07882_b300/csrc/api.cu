@@ -263,6 +263,12 @@ bcs_status bcs_destroy(bcs_solver* h) {
     cudaStreamSynchronize(s->cstream);
     cudaStreamDestroy(s->cstream);
   }
+  if (s->sstream) {
+    cudaStreamSynchronize(s->sstream);
+    cudaStreamDestroy(s->sstream);
+  }
+  for (cudaEvent_t e : s->sev)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : s->copy_events) cudaEventDestroy(e);
   for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
   if (s->hscal) cudaFreeHost(s->hscal);

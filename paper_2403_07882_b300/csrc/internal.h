@@ -275,6 +275,8 @@ struct Solver {
   DBuf<double> nrm0;
   bool nrm0_fresh = false;
   cudaStream_t cstream = nullptr;          // host -> device copies of the values in pieces
+  cudaStream_t sstream = nullptr;          // setup work beside the aggregation (block inverses)
+  cudaEvent_t sev[2] = {};
   std::vector<cudaEvent_t> copy_events;     // one per piece
   DBuf<int32_t> stage_o, stage_n;
   // hierarchy

@@ -922,14 +922,14 @@ bcs_status aggregate_level(Solver* s, Level& L, const double* norms) {
   return BCS_OK;
 }
 
-bcs_status block_inverses(Solver* s, Level& L, bool full) {
+bcs_status block_inverses(Solver* s, Level& L, bool full, bool allocated = false) {
   const int rows = L.A.rows, n = s->n;
   if (full || !L.dpos.p) {
-    BCS_ALLOC(s, L.dpos, rows);
+    if (!allocated) BCS_ALLOC(s, L.dpos, rows);
     BCS_LAUNCH(s, K_SETUP_INV, 0, 0, k_diag_pos, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, L.A.ci.p,
                L.dpos.p, s->flag.p);
   }
-  BCS_ALLOC(s, L.dinv, (size_t)rows * n * n);
+  if (!allocated) BCS_ALLOC(s, L.dinv, (size_t)rows * n * n);
   return with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
     BCS_LAUNCH(s, K_SETUP_INV, 16.0 * rows * N * N, 4.0 * rows * N * N * N, k_block_inverse<N>,
@@ -1128,9 +1128,34 @@ bcs_status amg_setup_levels(Solver* s, bool full) {
   // behind (no index depends on them), so the flags are read once, at the
   // end; the multicolour factorisations read them per level.
   const bool dilu = cfg.precond == BCS_PC_SGS || (cfg.precond == BCS_PC_AMG && cfg.smoother != BCS_SMOOTH_JACOBI);
+  // At a full block-Jacobi setup a level's block inverses (FP64-bound) do
+  // not depend on its aggregation (latency-bound small kernels): they run on
+  // a second stream beside it and are joined before anything reads them
+  // (the FP32 copies, smoothed prolongation, the flags at the end).
+  const bool side = full && !dilu && cfg.pmode == BCS_P_TENTATIVE;
+  if (side && !s->sstream) BCS_CU(s, cudaStreamCreateWithFlags(&s->sstream, cudaStreamNonBlocking));
+  if (side && !s->sev[0]) {
+    BCS_CU(s, cudaEventCreateWithFlags(&s->sev[0], cudaEventDisableTiming));
+    BCS_CU(s, cudaEventCreateWithFlags(&s->sev[1], cudaEventDisableTiming));
+  }
+  bool forked = false;
   for (int l = 0;; ++l) {
     Level& L = s->lv[l];
-    BCS_OKR(block_inverses(s, L, full));
+    if (side) {
+      // buffers first, stream-ordered on the solver's stream
+      BCS_ALLOC(s, L.dpos, L.A.rows);
+      BCS_ALLOC(s, L.dinv, (size_t)L.A.rows * s->n * s->n);
+      BCS_CU(s, cudaEventRecord(s->sev[0], s->stream));
+      BCS_CU(s, cudaStreamWaitEvent(s->sstream, s->sev[0], 0));
+      const cudaStream_t own = s->stream;
+      s->stream = s->sstream;
+      const bcs_status st_inv = block_inverses(s, L, full, true);
+      s->stream = own;
+      BCS_OKR(st_inv);
+      forked = true;
+    } else {
+      BCS_OKR(block_inverses(s, L, full));
+    }
     if (dilu) {
       bool singular = false;
       BCS_OKR(check_flags(s, &singular));
@@ -1169,6 +1194,10 @@ bcs_status amg_setup_levels(Solver* s, bool full) {
     }
     L.coarse_kind = -1;
     BCS_OKR(build_transfer(s, l, full));
+  }
+  if (forked) {  // join the second stream
+    BCS_CU(s, cudaEventRecord(s->sev[1], s->sstream));
+    BCS_CU(s, cudaStreamWaitEvent(s->stream, s->sev[1], 0));
   }
   int32_t h = 0;
   BCS_OKR(read_int(s, s->flag.p, &h));
