@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=200.0)
     p.add_argument("--serve-max-cells", type=float, default=3e6)
     p.add_argument("--serve-slots", type=int, default=8)
+    p.add_argument("--serve-solver", default="fgmres", choices=["fgmres", "bicgstab"],
+                   help="serving: Krylov solver of every case")
     p.add_argument("--serve-batch", type=int, default=1,
                    help="serving: solve up to this many resident cases' requests together (1: off)")
     p.add_argument("--serve-budget-gb", type=float, default=0.0,
@@ -785,7 +787,8 @@ def run_serve(args):
     keys = ("diag", "upper", "lower", "b")
     t0 = time.perf_counter()
     budget = int(args.serve_budget_gb * 1e9)
-    with bcs.Server(budget_bytes=budget, slots=args.serve_slots, batch=args.serve_batch) as srv:
+    solver = bcs.BCS_BICGSTAB if args.serve_solver == "bicgstab" else bcs.BCS_FGMRES
+    with bcs.Server(budget_bytes=budget, slots=args.serve_slots, batch=args.serve_batch, solver=solver) as srv:
         cases, ids, kinds = [], [], []
         for c in range(ncases):
             nx = int(round(cells[c] ** (1.0 / 3.0)))
@@ -873,7 +876,7 @@ def run_serve(args):
     print(json.dumps({"impl": "native", "mode": "serve", "cases": ncases,
                       "cells_range": [5e4, max_cells], "cells_mean": float(cells.mean()),
                       "block_sizes": {"5": kinds.count(5), "4": kinds.count(4)}, "slots": args.serve_slots,
-                      "batch": args.serve_batch,
+                      "batch": args.serve_batch, "solver": args.serve_solver,
                       "budget": "default (80 % of free memory)" if budget == 0 else f"{args.serve_budget_gb:g} GB",
                       "inputs": "two value sets per case resident in device memory, alternated per request",
                       "setup_s": gen_s, "configured_rate": configured, "closed_loop_capacity": capacity,
