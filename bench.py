@@ -149,6 +149,29 @@ def peaks():
         return 6400.0, "fallback"
 
 
+SETUP_KINDS = ("setup_aggregation", "setup_galerkin", "setup_inverse", "scan_sort", "cast")
+CYCLE_KINDS = ("jacobi_sweep", "residual", "transfer", "coarse_solve")
+
+
+def level_table(solver):
+    """Per hierarchy level of one profiled step: its size, the CUDA-event
+    time of its setup work (aggregation of its rows, the Galerkin product
+    forming the next level, its block inverses, sorts and FP32 copies) and
+    of its V-cycle kernels with their algorithmic GB/s."""
+    out = []
+    for l, t in enumerate(solver.level_times()):
+        info = solver.level_info(l)
+        row = {"level": l, "rows": info["rows"], "nnz": info["nnz"],
+               "setup_ms": round(sum(t[k]["ms"] for k in SETUP_KINDS if k in t), 4)}
+        for k in CYCLE_KINDS:
+            if k in t:
+                v = t[k]
+                row[k] = {"ms": round(v["ms"], 4), "launches": v["launches"],
+                          "GBps": round(v["bytes"] / (v["ms"] * 1e6), 1) if v["ms"] > 0 else None}
+        out.append(row)
+    return out
+
+
 def kernel_source_digest(path, func):
     """SHA-256 of the text of the __global__ or __device__ function `func` in
     `path` (from its definition line to the first line that closes it at
@@ -364,6 +387,7 @@ def run_native(args):
         step(sp, d, x)
         ktimes = sp.kernel_times()
         kinds = sp.stats()["kinds"]
+        per_level = level_table(sp)
     top_name = max(ktimes.items(), key=lambda kv: kv[1]["ms"])[0]
     live_kinds = 1 << ktimes[top_name]["kind"]
     with ClockSampler(local) as clk:
@@ -465,6 +489,7 @@ def run_native(args):
         "resetup_ms": resetup_ms,
         "roofline": roofline,
         "kernel_breakdown": breakdown,
+        "per_level": per_level,
         "kernels": {k: {"ms_per_step": round(v["ms"], 4), "launches_per_step": v["launches"],
                         "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else None}
                     for k, v in sorted(ktimes.items(), key=lambda kv: -kv[1]["ms"])[:40]},

@@ -327,6 +327,16 @@ BCS_API bcs_status bcs_reset_stats(bcs_solver* s);
  * "name<TAB>launches<TAB>ms<TAB>algorithmic bytes<TAB>kind", written to buf
  * (NUL terminated); BCS_EINVAL when it does not fit in len bytes. */
 BCS_API bcs_status bcs_get_kernel_times(bcs_solver* s, char* buf, size_t len);
+/* Per-level totals of the timed launches (cfg.profile = 1) since the last
+ * bcs_reset_stats: launches[k], ms[k] (CUDA-event time) and bytes[k]
+ * (algorithmic bytes) of kernel kind k on hierarchy level `level`, for
+ * k < BCS_NUM_KERNEL_KINDS (caller-owned host arrays of that length). A
+ * launch belongs to the level whose matrix it reads or builds: setup work of
+ * level l (its block inverses, the aggregation of its rows, the Galerkin
+ * product that forms level l + 1), its FP32 / BF16 copies, and its sweeps,
+ * residuals and transfers in the V-cycle. Zeros for a level with no timed
+ * launch; BCS_EINVAL for level outside [0, 64). */
+BCS_API bcs_status bcs_get_level_times(bcs_solver* s, int level, long long* launches, double* ms, double* bytes);
 /* Name of kernel kind k (0 <= k < BCS_NUM_KERNEL_KINDS), "" if unused. */
 BCS_API const char* bcs_kernel_kind_name(int k);
 

@@ -129,6 +129,7 @@ def lib():
             "bcs_reset_stats": (ct.c_int, [_vp]),
             "bcs_get_kernel_times": (ct.c_int, [_vp, ct.c_char_p, ct.c_size_t]),
             "bcs_kernel_kind_name": (ct.c_char_p, [ct.c_int]),
+            "bcs_get_level_times": (ct.c_int, [_vp, ct.c_int, _vp, _vp, _vp]),
             "bcs_last_error": (ct.c_char_p, [_vp]),
             "bcs_device_bytes": (ct.c_size_t, [_vp]),
             "bcs_ldu_structure_noalloc": (ct.c_int, [ct.c_int32, ct.c_int32] + [_vp] * 8 + [ct.c_char_p, ct.c_size_t]),
@@ -159,7 +160,7 @@ def exported_names():
             "bcs_solve", "bcs_solve_batch", "bcs_spmv", "bcs_precond_apply",
             "bcs_get_bsr", "bcs_num_levels", "bcs_get_level_info", "bcs_get_level", "bcs_get_prolongation",
             "bcs_get_coarse_inverse", "bcs_get_dilu", "bcs_get_stats", "bcs_reset_stats", "bcs_get_kernel_times", "bcs_kernel_kind_name",
-            "bcs_last_error", "bcs_device_bytes", "bcs_ldu_structure_noalloc", "bcs_server_create",
+            "bcs_get_level_times", "bcs_last_error", "bcs_device_bytes", "bcs_ldu_structure_noalloc", "bcs_server_create",
             "bcs_server_destroy", "bcs_server_register_case", "bcs_server_submit", "bcs_server_wait",
             "bcs_server_get_stats", "bcs_server_reset_stats", "bcs_server_set_batch"]
 
@@ -512,6 +513,17 @@ def bcs_get_kernel_times(h):
     return out
 
 
+def bcs_get_level_times(h, level):
+    """{kind name: dict(launches, ms, bytes)} of the timed launches on one
+    hierarchy level (profile = 1); kinds without a launch are left out."""
+    n = (ct.c_longlong * NUM_KERNEL_KINDS)()
+    ms = (ct.c_double * NUM_KERNEL_KINDS)()
+    b = (ct.c_double * NUM_KERNEL_KINDS)()
+    _check(lib().bcs_get_level_times(h, int(level), ct.cast(n, _vp), ct.cast(ms, _vp), ct.cast(b, _vp)), h)
+    return {bcs_kernel_kind_name(k): dict(launches=n[k], ms=ms[k], bytes=b[k])
+            for k in range(NUM_KERNEL_KINDS) if n[k] > 0}
+
+
 def bcs_reset_stats(h):
     return _check(lib().bcs_reset_stats(h), h)
 
@@ -728,6 +740,10 @@ class Solver:
 
     def kernel_times(self):
         return bcs_get_kernel_times(self.h)
+
+    def level_times(self):
+        """[per level {kind name: dict(launches, ms, bytes)}] (profile = 1)."""
+        return [bcs_get_level_times(self.h, l) for l in range(self.levels)]
 
 
 # ---------------------------------------------------------------- serving

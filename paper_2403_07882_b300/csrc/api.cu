@@ -56,7 +56,7 @@ void Solver::pre(int kind) {
       event_pool.push_back(e);
     }
   }
-  Timer t{kind, event_pool[event_next], event_pool[event_next + 1], nullptr, 0.0};
+  Timer t{kind, event_pool[event_next], event_pool[event_next + 1], nullptr, 0.0, cur_level};
   event_next += 2;
   cudaEventRecord(t.a, stream);
   timers.push_back(t);
@@ -84,6 +84,13 @@ void Solver::flush_timers() {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
       kind_ms[t.kind] += ms;
+      if (t.level >= 0 && t.level < LEVEL_TIMES_MAX) {
+        if ((int)level_times.size() <= t.level) level_times.resize(t.level + 1);
+        LevelTime& lt = level_times[t.level];
+        lt.launches[t.kind]++;
+        lt.ms[t.kind] += ms;
+        lt.bytes[t.kind] += t.bytes;
+      }
       if (t.what) {
         NamedTime& nt = named[t.what];
         nt.launches++;
@@ -837,12 +844,27 @@ bcs_status bcs_reset_stats(bcs_solver* h) {
   Solver* s = &h->impl;
   s->flush_timers();
   s->named.clear();
+  s->level_times.clear();
   s->launches = 0;
   for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {
     s->kind_launches[k] = 0;
     s->kind_ms[k] = 0.0;
     s->kind_bytes[k] = 0.0;
     s->kind_flops[k] = 0.0;
+  }
+  return BCS_OK;
+}
+
+bcs_status bcs_get_level_times(bcs_solver* h, int level, long long* launches, double* ms, double* bytes) {
+  if (!h || !launches || !ms || !bytes || level < 0 || level >= LEVEL_TIMES_MAX) return BCS_EINVAL;
+  Solver* s = &h->impl;
+  s->flush_timers();
+  const LevelTime none{};
+  const LevelTime& lt = level < (int)s->level_times.size() ? s->level_times[level] : none;
+  for (int k = 0; k < BCS_NUM_KERNEL_KINDS; ++k) {
+    launches[k] = lt.launches[k];
+    ms[k] = lt.ms[k];
+    bytes[k] = lt.bytes[k];
   }
   return BCS_OK;
 }

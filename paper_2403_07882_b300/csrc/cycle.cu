@@ -984,6 +984,7 @@ struct Cycle {
 
   template <int N>
   bcs_status run(int l, const TC* b, TC* x) {
+    LevelScope level_scope(s, l);
     if constexpr (std::is_same<TC, float>::value)
       if (l == s->tail_level) return tail<N>((const float*)b, (float*)x);
     Level& L = s->lv[l];
@@ -1429,6 +1430,7 @@ bcs_status cycle_prepare(Solver* s) {
   std::vector<char> needed(nl, 0);
   for (size_t l = 0; l < nl; ++l) {
     Level& L = s->lv[l];
+    LevelScope level_scope(s, (int)l);
     const size_t N = (size_t)L.A.rows * n;
     BCS_ALLOC(s, L.vx, N * vsz);
     BCS_ALLOC(s, L.vb, N * vsz);
@@ -1454,6 +1456,7 @@ bcs_status cycle_prepare(Solver* s) {
   }
   for (size_t l = 0; l < nl && sliced; ++l) {
     Level& L = s->lv[l];
+    LevelScope level_scope(s, (int)l);
     BCS_OKR(layout_values(s, L, prec));
     const bool smoothed = L.coarse_kind < 0 && s->setup_cfg.pmode == BCS_P_SMOOTHED;
     if (prec == BCS_PREC_FP32) {

@@ -243,6 +243,15 @@ struct Timer {
   cudaEvent_t a, b;
   const char* what;
   double bytes;
+  int level;  // hierarchy level the launch works on (-1: none)
+};
+
+// Per-level totals of the timed launches (profile = 1), by kernel kind.
+constexpr int LEVEL_TIMES_MAX = 64;
+struct LevelTime {
+  long long launches[BCS_NUM_KERNEL_KINDS] = {};
+  double ms[BCS_NUM_KERNEL_KINDS] = {};
+  double bytes[BCS_NUM_KERNEL_KINDS] = {};
 };
 
 struct NamedTime {
@@ -299,6 +308,11 @@ struct Solver {
   double kind_ms[BCS_NUM_KERNEL_KINDS] = {};
   std::vector<Timer> timers;
   std::map<std::string, NamedTime> named;  // per kernel name (profile = 1)
+  // Level the launches being issued work on (set by the setup's level loop,
+  // the FP32 copies and the V-cycle; -1 outside them) and the per-level
+  // totals of the timed launches.
+  int cur_level = -1;
+  std::vector<LevelTime> level_times;
   std::vector<cudaEvent_t> event_pool;
   size_t event_next = 0;
   double last_setup_ms = 0.0;
@@ -341,6 +355,15 @@ struct Solver {
   void pre(int kind);
   bcs_status post(int kind, const char* what, double bytes, double flops);
   void flush_timers();
+};
+
+// Sets s->cur_level for the lifetime of the guard and restores the previous
+// value after it.
+struct LevelScope {
+  Solver* s;
+  int prev;
+  LevelScope(Solver* s_, int l) : s(s_), prev(s_->cur_level) { s->cur_level = l; }
+  ~LevelScope() { s->cur_level = prev; }
 };
 
 #define BCS_CU(S, call)                                                                \

@@ -628,13 +628,16 @@ __global__ void k_gauss_jordan(int N, double* __restrict__ M, double* __restrict
           p = red_i[w];
         }
       s_p = p;
-      used[p] = 1;
-      if (blockIdx.x == 0) prow_out[k] = p;
+      if (p != INT_MAX) {
+        used[p] = 1;
+        if (blockIdx.x == 0) prow_out[k] = p;
+      }
     }
     __syncthreads();
     const int p = s_p;
-    const double* prow = M + (size_t)p * W;
-    const double piv = prow[k];
+    // no pivot candidate (a column of NaNs) or a zero pivot: singular
+    const double piv = p == INT_MAX ? 0.0 : M[(size_t)p * W + k];
+    const double* prow = M + (size_t)(p == INT_MAX ? 0 : p) * W;
     if (piv == 0.0) {
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 16);
       return;  // every block sees the same pivot and leaves before the next barrier
@@ -656,6 +659,80 @@ __global__ void k_gauss_jordan(int N, double* __restrict__ M, double* __restrict
     }
     grid.sync();
   }
+}
+
+// The same Gauss-Jordan for small N on one block with [A | I] in shared
+// memory: the same pivot choice and the same operation on every element as
+// k_gauss_jordan (one warp per row, the block's barrier per pivot step);
+// the reduced [A | I] and the pivot rows are written back for k_gj_finish.
+constexpr int GJ_SMEM_THREADS = 512;
+
+__global__ void __launch_bounds__(GJ_SMEM_THREADS) k_gauss_jordan_smem(int N, double* __restrict__ M,
+                                                                       int32_t* __restrict__ prow_out,
+                                                                       int32_t* __restrict__ err) {
+  extern __shared__ double sm[];  // N x 2N, then N used flags
+  unsigned char* used = reinterpret_cast<unsigned char*>(sm + 2 * (size_t)N * N);
+  __shared__ int s_p;
+  __shared__ double s_rpiv;
+  const int W = 2 * N;
+  for (int t = threadIdx.x; t < N * W; t += blockDim.x) sm[t] = M[t];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) used[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = 0; k < N; ++k) {
+    if (warp == 0) {
+      // largest |M[i][k]| over the unused rows, the lowest i on ties: the
+      // bit patterns of non-negative doubles order like their values, so
+      // integer compares pick the same row as floating-point ones (NaN,
+      // which no floating-point compare picks, is skipped)
+      long long bk = -1;
+      int bi = INT_MAX;
+      for (int i = lane; i < N; i += 32) {
+        const double v = sm[i * W + k];
+        if (used[i] || isnan(v)) continue;
+        const long long key = __double_as_longlong(v) & 0x7fffffffffffffffll;
+        if (key > bk || (key == bk && i < bi)) {
+          bk = key;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        const long long ok = __shfl_down_sync(0xffffffffu, bk, d);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, d);
+        if (ok > bk || (ok == bk && oi < bi)) {
+          bk = ok;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        s_p = bi;
+        if (bi != INT_MAX) {
+          used[bi] = 1;
+          prow_out[k] = bi;
+          const double piv = sm[bi * W + k];
+          s_rpiv = piv == 0.0 ? 0.0 : 1.0 / piv;
+        }
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p == INT_MAX || sm[p * W + k] == 0.0) {
+      if (threadIdx.x == 0) atomicOr(err, 16);
+      return;
+    }
+    const double* prow = sm + p * W;
+    const double rpiv = s_rpiv;
+    for (int i = warp; i < N; i += nw) {
+      if (i == p) continue;
+      double* row = sm + i * W;
+      const double l = row[k] * rpiv;
+      __syncwarp();  // every lane has read row[k] before lane 0 rewrites it
+      for (int j = k + lane; j < W; j += 32) row[j] = fma(-l, prow[j], row[j]);
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < N * W; t += blockDim.x) M[t] = sm[t];
 }
 
 __global__ void k_gj_finish(int N, const double* __restrict__ M, const int32_t* __restrict__ prow,
@@ -938,6 +1015,10 @@ bcs_status block_inverses(Solver* s, Level& L, bool full, bool allocated = false
   });
 }
 
+// Dense coarse inverses of at most this many unknowns run on one block in
+// shared memory (16 N^2 bytes: 147 KB at 96).
+constexpr int GJ_SMEM_MAX_N = 96;
+
 bcs_status coarse_inverse(Solver* s, Level& L) {
   const int N = L.A.rows * s->n;
   s->cN = N;
@@ -949,24 +1030,33 @@ bcs_status coarse_inverse(Solver* s, Level& L) {
   BCS_ALLOC(s, s->cinv, (size_t)N * N);
   BCS_LAUNCH(s, K_SETUP_INV, 0, 0, k_dense_from_bsr, grid_for(L.A.rows, 64), 64, 0, L.A.rows, s->n, L.A.rp.p,
              L.A.ci.p, L.A.v.p, M.p, N);
-  int dev = 0, sms = 0, per_sm = 0;
-  BCS_CU(s, cudaGetDevice(&dev));
-  BCS_CU(s, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int threads = 256;
-  const size_t smem = (size_t)N;
-  BCS_CU(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gauss_jordan, threads, smem));
-  if (per_sm < 1) return s->fail(BCS_ECUDA, "coarse inverse kernel cannot be resident");
-  int blocks = sms * per_sm;
-  if (blocks > N) blocks = N;
-  int Nn = N;
-  double* Mp = M.p;
-  double* cb = colbuf.p;
-  int32_t* pr = prow.p;
-  int32_t* fl = s->flag.p;
-  void* args[] = {&Nn, &Mp, &cb, &pr, &fl};
-  s->pre(K_SETUP_INV);
-  BCS_CU(s, cudaLaunchCooperativeKernel((void*)k_gauss_jordan, blocks, threads, args, smem, s->stream));
-  BCS_OKR(s->post(K_SETUP_INV, "k_gauss_jordan", 24.0 * N * N * N, 3.0 * N * N * N));
+  if (N <= GJ_SMEM_MAX_N) {
+    // [A | I] fits one block's shared memory: no grid-wide barriers, no L2
+    // round trip per pivot step
+    const size_t smem = 16 * (size_t)N * N + N;
+    BCS_CU(s, cudaFuncSetAttribute(k_gauss_jordan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BCS_LAUNCH(s, K_SETUP_INV, 24.0 * N * N * N, 3.0 * N * N * N, k_gauss_jordan_smem, 1, GJ_SMEM_THREADS, smem, N,
+               M.p, prow.p, s->flag.p);
+  } else {
+    int dev = 0, sms = 0, per_sm = 0;
+    BCS_CU(s, cudaGetDevice(&dev));
+    BCS_CU(s, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = 256;
+    const size_t smem = (size_t)N;
+    BCS_CU(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gauss_jordan, threads, smem));
+    if (per_sm < 1) return s->fail(BCS_ECUDA, "coarse inverse kernel cannot be resident");
+    int blocks = sms * per_sm;
+    if (blocks > N) blocks = N;
+    int Nn = N;
+    double* Mp = M.p;
+    double* cb = colbuf.p;
+    int32_t* pr = prow.p;
+    int32_t* fl = s->flag.p;
+    void* args[] = {&Nn, &Mp, &cb, &pr, &fl};
+    s->pre(K_SETUP_INV);
+    BCS_CU(s, cudaLaunchCooperativeKernel((void*)k_gauss_jordan, blocks, threads, args, smem, s->stream));
+    BCS_OKR(s->post(K_SETUP_INV, "k_gauss_jordan", 24.0 * N * N * N, 3.0 * N * N * N));
+  }
   BCS_LAUNCH(s, K_SETUP_INV, 0, 0, k_gj_finish, grid_for((size_t)N * N, 256), 256, 0, N, M.p, prow.p,
              s->cinv.p);
   return BCS_OK;
@@ -1141,6 +1231,7 @@ bcs_status amg_setup_levels(Solver* s, bool full) {
   bool forked = false;
   for (int l = 0;; ++l) {
     Level& L = s->lv[l];
+    LevelScope level_scope(s, l);
     if (side) {
       // buffers first, stream-ordered on the solver's stream
       BCS_ALLOC(s, L.dpos, L.A.rows);

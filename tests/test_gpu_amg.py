@@ -19,6 +19,9 @@ CASES = [
     ("pressure 9^3 smoothed", lambda: synth.pressure(9, seed=2), dict(pmode=0)),
     ("random n=3 one pass", lambda: synth.random_graph(300, 900, 3, seed=5), dict(agg_passes=1, coarse_size=8)),
     ("random n=2 three passes", lambda: synth.random_graph(400, 1000, 2, seed=6), dict(agg_passes=3, coarse_size=4)),
+    # coarsest level of 81 rows x 4 = 324 unknowns (above 96): the dense inverse
+    # runs on a cooperative grid (the cases above take the shared-memory form)
+    ("pressure 12^3 large dense coarse", lambda: synth.pressure(12, seed=1), dict(coarse_size=200)),
 ]
 
 
