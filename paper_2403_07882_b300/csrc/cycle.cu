@@ -86,36 +86,42 @@ __global__ void __launch_bounds__(128) k_rows(int rows, const int32_t* __restric
 }
 
 // ---- multicolour DILU sweeps (one launch per colour) -------------------------
-// Rows of colour c (list rows_c), lane (w, r) = scalar row r of the w-th row.
+// Rows of colour c (slots t0 .. t0 + cnt of the colour lists crow), lane
+// (w, r) = scalar row r of the w-th row.
 // Forward:  y_i = E_i^{-1} (r_i - sum_{colour(j) < c} A_ij y_j).
 // Backward: d_i = y_i - E_i^{-1} sum_{colour(j) > c} A_ij d_j;  x_i += d_i.
-// One row of a colour's sweep: lane (rw, r) of a row group; every lane of the
-// warp calls it (shuffles), active says whether the lane has a row. Vectors
-// the sweeps write (r, y, d, x) are read with ordinary loads.
-template <int N, class AT, class TV, class TD, class TC, bool FWD>
-__device__ __forceinline__ void dilu_row(bool active, int i, int rw, int r, int c, const int32_t* __restrict__ colour,
-                                         const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                         const TV* __restrict__ val, const TD* __restrict__ einv, const TC* rv, TC* y,
-                                         TC* d, TC* x) {
+// The blocks come from the row's split lists (lower part forward, upper part
+// backward, each in column order: the same fma sequence as a walk over the
+// whole row that skips the other blocks, without reading their colours).
+// GATHER: val is the BSR array, indexed through dsrc (FP64 cycle); else val
+// holds the split blocks in split order. One row of a colour's sweep: lane
+// (rw, r) of a row group; every lane of the warp calls it (shuffles), active
+// says whether the lane has a row. Vectors the sweeps write (r, y, d, x) are
+// read with ordinary loads.
+template <int N, class AT, class TV, class TD, class TC, bool FWD, bool GATHER>
+__device__ __forceinline__ void dilu_row(bool active, int i, int t, int rw, int r, const int32_t* __restrict__ dptr,
+                                         const int32_t* __restrict__ dmid, const int32_t* __restrict__ dsrc,
+                                         const int32_t* __restrict__ dci, const TV* __restrict__ val,
+                                         const TD* __restrict__ einv, const TC* rv, TC* y, TC* d, TC* x) {
   AT acc = 0;
   if (active) {
-    const int kb = __ldg(rp + i), ke = __ldg(rp + i + 1);
-    for (int k = kb; k < ke; ++k) {
-      const int j = __ldg(ci + k);
-      const int cj = __ldg(colour + j);
-      if (FWD ? cj >= c : cj <= c) continue;
-      const TV* a = val + (size_t)k * (N * N) + r * N;
+    const int qb = FWD ? __ldg(dptr + t) : __ldg(dmid + t);
+    const int qe = FWD ? __ldg(dmid + t) : __ldg(dptr + t + 1);
+    for (int q = qb; q < qe; ++q) {
+      const int j = __ldg(dci + q);
+      const size_t blk = GATHER ? (size_t)__ldg(dsrc + q) : (size_t)q;
+      const TV* a = val + blk * (N * N) + r * N;
       const TC* v = (FWD ? y : d) + (size_t)j * N;
 #pragma unroll
       for (int cc = 0; cc < N; ++cc) acc = fma(lda<AT>(a + cc), (AT)v[cc], acc);
     }
   }
   const size_t o = (size_t)i * N + r;
-  const AT t = active ? (FWD ? (AT)rv[o] - acc : acc) : (AT)0;
+  const AT u = active ? (FWD ? (AT)rv[o] - acc : acc) : (AT)0;
   AT s = 0;
 #pragma unroll
   for (int cc = 0; cc < N; ++cc) {
-    const AT tc = __shfl_sync(0xffffffffu, t, (rw * N + cc) & 31);
+    const AT tc = __shfl_sync(0xffffffffu, u, (rw * N + cc) & 31);
     if (active) s = fma(lda<AT>(einv + o * N + cc), tc, s);
   }
   if (!active) return;
@@ -128,16 +134,19 @@ __device__ __forceinline__ void dilu_row(bool active, int i, int rw, int r, int 
   }
 }
 
-template <int N, class AT, class TV, class TD, class TC, bool FWD>
-__global__ void __launch_bounds__(128) k_dilu_sweep(int cnt, const int32_t* __restrict__ rows_c, int c,
-                                                    const int32_t* __restrict__ colour,
-                                                    const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                                    const TV* __restrict__ val, const TD* __restrict__ einv,
-                                                    const TC* __restrict__ r, TC* __restrict__ y,
-                                                    TC* __restrict__ d, TC* __restrict__ x) {
+template <int N, class AT, class TV, class TD, class TC, bool FWD, bool GATHER>
+__global__ void __launch_bounds__(128) k_dilu_sweep(int cnt, int t0, const int32_t* __restrict__ crow,
+                                                    const int32_t* __restrict__ dptr,
+                                                    const int32_t* __restrict__ dmid,
+                                                    const int32_t* __restrict__ dsrc,
+                                                    const int32_t* __restrict__ dci, const TV* __restrict__ val,
+                                                    const TD* __restrict__ einv, const TC* __restrict__ r,
+                                                    TC* __restrict__ y, TC* __restrict__ d, TC* __restrict__ x) {
   RowMap<N> m(cnt);
-  const int i = m.active ? __ldg(rows_c + m.i) : 0;
-  dilu_row<N, AT, TV, TD, TC, FWD>(m.active, i, m.rw, m.r, c, colour, rp, ci, val, einv, r, y, d, x);
+  const int t = t0 + (m.active ? m.i : 0);
+  const int i = m.active ? __ldg(crow + t) : 0;
+  dilu_row<N, AT, TV, TD, TC, FWD, GATHER>(m.active, i, t, m.rw, m.r, dptr, dmid, dsrc, dci, val, einv, r, y, d,
+                                           x);
 }
 
 // ---- sliced (SELL) copy for the FP32 / BF16 cycle ---------------------------
@@ -883,19 +892,20 @@ struct Cycle {
     TC* y = (TC*)L.vt.p;
     TC* d = (TC*)L.vd.p;
     BCS_OKR(resid<N>(L, x, b, r));
+    constexpr bool G = std::is_same<TV, double>::value;  // FP64: the BSR values through dsrc
     const double per_row = (double)N * N * sizeof(TV) + N * N * sizeof(TD) + 3.0 * N * sizeof(TC);
     for (int c = 0; c < L.ncol; ++c) {
       const int b0 = L.cstart[c], m = L.cstart[c + 1] - b0;
       if (m > 0)
-        BCS_LAUNCH(s, K_SWEEP, per_row * m, 2.0 * m * N * N, (k_dilu_sweep<N, AT, TV, TD, TC, true>),
-                   rows_grid(m, N), 128, 0, m, L.crow.p + b0, c, L.colour.p, L.A.rp.p, L.A.ci.p, dmat(L),
+        BCS_LAUNCH(s, K_SWEEP, per_row * m, 2.0 * m * N * N, (k_dilu_sweep<N, AT, TV, TD, TC, true, G>),
+                   rows_grid(m, N), 128, 0, m, b0, L.crow.p, L.dptr.p, L.dmid.p, L.dsrc.p, L.dci.p, dmat(L),
                    deinv(L), r, y, d, x);
     }
     for (int c = L.ncol - 1; c >= 0; --c) {
       const int b0 = L.cstart[c], m = L.cstart[c + 1] - b0;
       if (m > 0)
-        BCS_LAUNCH(s, K_SWEEP, per_row * m, 2.0 * m * N * N, (k_dilu_sweep<N, AT, TV, TD, TC, false>),
-                   rows_grid(m, N), 128, 0, m, L.crow.p + b0, c, L.colour.p, L.A.rp.p, L.A.ci.p, dmat(L),
+        BCS_LAUNCH(s, K_SWEEP, per_row * m, 2.0 * m * N * N, (k_dilu_sweep<N, AT, TV, TD, TC, false, G>),
+                   rows_grid(m, N), 128, 0, m, b0, L.crow.p, L.dptr.p, L.dmid.p, L.dsrc.p, L.dci.p, dmat(L),
                    deinv(L), r, y, d, x);
     }
     return BCS_OK;

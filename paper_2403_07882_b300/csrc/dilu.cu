@@ -107,6 +107,65 @@ __global__ void k_colour_place(int rows, const int32_t* __restrict__ colour, con
   if (i < rows) crow[start[c] + base[c] + rank] = i;
 }
 
+// Split lists in colour-list order: slot t holds row crow[t], so the rows
+// one colour's sweep walks have their lists side by side.
+// Off-diagonal blocks of the slot's row whose column has another colour (the
+// blocks the sweeps use; a valid colouring leaves only the diagonal out).
+__global__ void k_dilu_split_count(int rows, const int32_t* __restrict__ crow, const int32_t* __restrict__ rp,
+                                   const int32_t* __restrict__ ci, const int32_t* __restrict__ colour,
+                                   int32_t* __restrict__ cnt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows) return;
+  const int i = crow[t], c = colour[i];
+  int m = 0;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) m += colour[ci[k]] != c;
+  cnt[t] = m;
+}
+
+// The slot's lower part then its upper part, each in column order.
+__global__ void k_dilu_split_fill(int rows, const int32_t* __restrict__ crow, const int32_t* __restrict__ rp,
+                                  const int32_t* __restrict__ ci, const int32_t* __restrict__ colour,
+                                  const int32_t* __restrict__ dptr, int32_t* __restrict__ dmid,
+                                  int32_t* __restrict__ dsrc, int32_t* __restrict__ dci) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows) return;
+  const int i = crow[t], c = colour[i];
+  int o = dptr[t];
+  for (int k = rp[i]; k < rp[i + 1]; ++k) {
+    const int j = ci[k];
+    if (colour[j] < c) {
+      dsrc[o] = k;
+      dci[o] = j;
+      ++o;
+    }
+  }
+  dmid[t] = o;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) {
+    const int j = ci[k];
+    if (colour[j] > c) {
+      dsrc[o] = k;
+      dci[o] = j;
+      ++o;
+    }
+  }
+}
+
+// Values of the split blocks in the cycle precision: out[q] = A[dsrc[q]]
+// for q < *total (one thread per entry).
+template <int NN, class TO>
+__global__ void k_dilu_split_values(long long bound, const int32_t* __restrict__ total,
+                                    const int32_t* __restrict__ dsrc, const double* __restrict__ val,
+                                    TO* __restrict__ out) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= bound) return;
+  const long long q = t / NN;
+  if (q >= *total) return;
+  const int e = (int)(t - q * NN);
+  const double v = val[(size_t)__ldg(dsrc + q) * NN + e];
+  if constexpr (std::is_same<TO, bf16>::value) out[t] = __double2bfloat16(v);
+  else out[t] = (TO)v;
+}
+
 __device__ __forceinline__ int find_pos(const int32_t* __restrict__ ci, int b, int e, int col) {
   while (b < e) {
     const int m = (b + e) >> 1;
@@ -277,6 +336,18 @@ bcs_status dilu_setup(Solver* s, Level& L, bool full, bool sgs) {
     BCS_ALLOC(s, L.crow, rows);
     BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_colour_place, grid_for(rows, 256), 256, 0, rows, L.colour.p, start.p,
                cursor.p, L.crow.p);
+    // the sweeps' split rows (sized by the nonzero count, an upper bound)
+    BCS_ALLOC(s, L.dptr, rows + 1);
+    BCS_ALLOC(s, L.dmid, rows);
+    BCS_ALLOC(s, L.dsrc, L.A.nnz);
+    BCS_ALLOC(s, L.dci, L.A.nnz);
+    DBuf<int32_t> dcnt;
+    BCS_ALLOC(s, dcnt, rows);
+    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_dilu_split_count, grid_for(rows, 256), 256, 0, rows, L.crow.p, L.A.rp.p,
+               L.A.ci.p, L.colour.p, dcnt.p);
+    BCS_OKR(exclusive_scan(s, dcnt.p, L.dptr.p, rows));
+    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_dilu_split_fill, grid_for(rows, 256), 256, 0, rows, L.crow.p, L.A.rp.p,
+               L.A.ci.p, L.colour.p, L.dptr.p, L.dmid.p, L.dsrc.p, L.dci.p);
     // the host vector L.cstart is read by this copy: finish it before return
     BCS_CU(s, cudaStreamSynchronize(s->stream));
     L.ncol = ncol;
@@ -319,12 +390,21 @@ bcs_status dilu_prepare(Solver* s, Level& L) {
   const size_t nn = (size_t)s->n * s->n;
   BCS_ALLOC(s, L.einv32, (size_t)L.A.rows * nn);
   BCS_OKR(cast_vec<double, float>(s, L.einv.p, L.einv32.p, (size_t)L.A.rows * nn));
-  if (s->setup_cfg.precision == BCS_PREC_BF16) {
-    BCS_ALLOC(s, L.a16, (size_t)L.A.nnz * nn);
-    return cast_vec<double, bf16>(s, L.A.v.p, L.a16.p, (size_t)L.A.nnz * nn);
-  }
-  BCS_ALLOC(s, L.a32, (size_t)L.A.nnz * nn);
-  return cast_vec<double, float>(s, L.A.v.p, L.a32.p, (size_t)L.A.nnz * nn);
+  const long long bound = (long long)L.A.nnz * (long long)nn;
+  const bool b16 = s->setup_cfg.precision == BCS_PREC_BF16;
+  if (b16) BCS_ALLOC(s, L.a16, (size_t)bound);
+  else BCS_ALLOC(s, L.a32, (size_t)bound);
+  return with_n(s->n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    const unsigned g = grid_for((size_t)bound, 256);
+    if (b16)
+      BCS_LAUNCH(s, K_CAST, 10.0 * bound, 0, (k_dilu_split_values<N * N, bf16>), g, 256, 0, bound,
+                 L.dptr.p + L.A.rows, L.dsrc.p, L.A.v.p, L.a16.p);
+    else
+      BCS_LAUNCH(s, K_CAST, 12.0 * bound, 0, (k_dilu_split_values<N * N, float>), g, 256, 0, bound,
+                 L.dptr.p + L.A.rows, L.dsrc.p, L.A.v.p, L.a32.p);
+    return BCS_OK;
+  });
 }
 
 }  // namespace bcs

@@ -154,8 +154,14 @@ struct Level {
   DBuf<int32_t> crow;        // rows grouped by colour: cstart[c] .. cstart[c+1]
   std::vector<int> cstart;
   DBuf<double> einv;         // E_i^{-1}, FP64
-  DBuf<float> einv32, a32;   // FP32 copies for the FP32 / BF16 cycle (a32: BSR values)
-  DBuf<bf16> a16;            // BF16 BSR values for the BF16 cycle
+  // each row's off-diagonal blocks split for the sweeps: the lower part
+  // (colour(j) < colour(i)) then the upper part (colour(j) > colour(i)),
+  // each in column order, stored in colour-list order: the row at crow[t]
+  // at [dptr[t], dptr[t+1]), lower part ending at dmid[t]; dsrc: BSR
+  // position, dci: column (built with the colouring)
+  DBuf<int32_t> dptr, dmid, dsrc, dci;
+  DBuf<float> einv32, a32;   // FP32 copies for the FP32 / BF16 cycle (a32: split-order values)
+  DBuf<bf16> a16;            // BF16 split-order values for the BF16 cycle
   DBuf<char> vd;             // DILU correction vector (cycle precision)
 };
 
