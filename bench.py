@@ -60,6 +60,10 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=200.0)
     p.add_argument("--serve-max-cells", type=float, default=3e6)
     p.add_argument("--serve-slots", type=int, default=8)
+    p.add_argument("--serve-oracle", type=int, default=64,
+                   help="serving: requests of the smaller cases solved in one mix and checked against the oracle")
+    p.add_argument("--serve-oracle-max-cells", type=float, default=2e5,
+                   help="serving: largest case the oracle parity subset draws from")
     p.add_argument("--serve-solver", default="fgmres", choices=["fgmres", "bicgstab"],
                    help="serving: Krylov solver of every case")
     p.add_argument("--serve-batch", type=int, default=1,
@@ -231,6 +235,40 @@ def oracle_run(system, omp=False):
     finally:
         oracle.use_openmp(False)
     return {"setup_ms": (t1 - t0) * 1e3, "solve_ms": (t2 - t1) * 1e3, "total_ms": (t2 - t0) * 1e3}, x, res
+
+
+def oracle_leg(system, cfg_kw, omp=False, spmv_reps=10, resetup=True):
+    """The oracle's own times on one system (host cores; omp: the OpenMP
+    build of the same source): FP64 SpMV (median of spmv_reps calls), full
+    AMG setup, values-only resetup with the same values, and the solve to
+    1e-8 from x0 = 0 with the given configuration. Returns (times, x)."""
+    import oracle
+    oracle.use_openmp(omp)
+    try:
+        ref = oracle.ldu_to_bsr(system)
+        xv = np.random.default_rng(0).uniform(-1, 1, system["b"].shape)
+        sp = []
+        for _ in range(spmv_reps):
+            t0 = time.perf_counter()
+            oracle.spmv(ref, xv)
+            sp.append((time.perf_counter() - t0) * 1e3)
+        cfg = oracle.config(**cfg_kw)
+        t0 = time.perf_counter()
+        amg = oracle.Amg(ref, cfg)
+        t1 = time.perf_counter()
+        out = {"spmv_ms": statistics.median(sp), "setup_ms": (t1 - t0) * 1e3}
+        if resetup:
+            t0 = time.perf_counter()
+            amg.resetup(ref["val"])
+            out["resetup_ms"] = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        x, res, _ = oracle.solve(ref, system["b"], cfg=cfg, amg=amg)
+        out["solve_ms"] = (time.perf_counter() - t0) * 1e3
+        out.update(status=res["status"], iters=res["iters"],
+                   rel_res_true=float(np.linalg.norm(system["b"] - oracle.spmv(ref, x)) / np.linalg.norm(system["b"])))
+        return out, x
+    finally:
+        oracle.use_openmp(False)
 
 
 def oracle_sample(side=SAMPLE_SIDE):
@@ -668,6 +706,7 @@ def run_system(args):
     out = []
     C, F = system["n_cells"], system["n_faces"]
     spmv_bytes = 8.0 * n * n * (C + 2 * F) + 4.0 * (C + 2 * F) + 4.0 * (C + 1) + 16.0 * n * C
+    xs = []
     for label, solver, prec, reorder, extra in runs:
         setup, resetup, solve, total, iters, launches, spmv_ms = [], [], [], [], [], [], []
         for rep in range(args.warmup + args.steps):
@@ -691,6 +730,8 @@ def run_system(args):
                 e[4].record()
                 torch.cuda.synchronize()
                 assert st == bcs.BCS_OK, res
+                if rep == args.warmup + args.steps - 1:
+                    xs.append(x.cpu().numpy())
                 if rep >= args.warmup:
                     setup.append(e[0].elapsed_time(e[1]))
                     solve.append(e[1].elapsed_time(e[2]))
@@ -708,9 +749,32 @@ def run_system(args):
                     "time_to_1e-8_ms": statistics.median(total), "setup_ms": statistics.median(setup),
                     "solve_ms": statistics.median(solve), "resetup_ms": statistics.median(resetup),
                     "iters": iters[-1], "launches_per_solve": launches[-1]})
-    print(json.dumps({"impl": "native", "mode": args.workload, "workload": name,
-                      "step": "structure + values + full setup + solve to 1e-8 from x0 = 0", "runs": out}),
-          flush=True)
+    line = {"impl": "native", "mode": args.workload, "workload": name,
+            "step": "structure + values + full setup + solve to 1e-8 from x0 = 0", "runs": out}
+    if not args.no_cpu_baseline:
+        # the oracle on the host cores with the first arm's solver (FP64
+        # throughout): SpMV, full setup, resetup, solve; single-threaded and
+        # the OpenMP build; every GPU arm's solution against the oracle's
+        okw = dict(solver=runs[0][1])
+        t1, x_ref = oracle_leg(system, okw)
+        tn, x_omp = oracle_leg(system, okw, omp=True)
+        import oracle
+        ref = oracle.ldu_to_bsr(system)
+        bn = np.linalg.norm(system["b"])
+        errs = {}
+        for (label, solver, prec, reorder, extra), o, xg in zip(runs, out, xs):
+            key = f"{label} / {o['preconditioner']} / {o['amg_precision']}" + (" / rcm" if reorder else "")
+            errs[key] = {"rel_err_x_vs_oracle": float(np.linalg.norm(xg - x_ref) / np.linalg.norm(x_ref)),
+                         "rel_res_true": float(np.linalg.norm(system["b"] - oracle.spmv(ref, xg)) / bn)}
+        line["cpu_baseline"] = {"kind": "oracle", "unit": "ms", "cores": 1, "host": host_info(),
+                                "value": t1["setup_ms"] + t1["solve_ms"], "solver": runs[0][0],
+                                "sample": "the full system (no sampling): FP64 SpMV (median of 10), AMG setup, "
+                                          "values-only resetup, solve to 1e-8",
+                                "single_thread": t1,
+                                "oracle_omp": dict(cores=host_info()["nproc"], **tn,
+                                                   identical_to_single_thread=bool(np.array_equal(x_ref, x_omp))),
+                                "gpu_error_vs_oracle": errs}
+    print(json.dumps(line), flush=True)
 
 
 def run_knn(args):
@@ -774,6 +838,33 @@ def run_knn(args):
         cmp_[label] = {"setup_ms": setup_ms, "solve_ms": solve_ms, "time_to_1e-8_ms": setup_ms + solve_ms,
                        "iters": it}
     out["smoother_comparison"] = cmp_
+    if not args.no_cpu_baseline:
+        # the oracle on the last system: single-threaded SpMV (median of 3),
+        # then SpMV, full setup, one values-only resetup and the solve with
+        # the OpenMP build (about a minute, some 30 GB of host memory)
+        import oracle
+        ref = oracle.ldu_to_bsr(system)
+        xv = np.random.default_rng(0).uniform(-1, 1, system["b"].shape)
+        sp = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            oracle.spmv(ref, xv)
+            sp.append((time.perf_counter() - t0) * 1e3)
+        del ref
+        tn, x_or = oracle_leg(system, {}, omp=True, spmv_reps=3)
+        with bcs.Solver(5, precision=bcs.BCS_PREC_FP32) as s3:
+            s3.set_structure(system["n_cells"], d["owner"], d["neighbour"])
+            s3.set_values(*vals)
+            x3 = torch.zeros_like(d["b"])
+            _, st, res = s3.solve(d["b"], x3)
+            x3 = x3.cpu().numpy()
+        out["cpu_baseline"] = {"kind": "oracle", "unit": "ms", "host": host_info(),
+                               "sample": "the last system of the sequence (no sampling)",
+                               "single_thread": {"cores": 1, "spmv_ms": statistics.median(sp)},
+                               "oracle_omp": dict(cores=host_info()["nproc"], **tn),
+                               "gpu_error_vs_oracle": {
+                                   "rel_err_x_vs_oracle": float(np.linalg.norm(x3 - x_or) / np.linalg.norm(x_or)),
+                                   "gpu_iters": res["iters"]}}
     print(json.dumps({"impl": "native", "mode": "knn", **out}), flush=True)
 
 
@@ -814,7 +905,7 @@ def run_serve(args):
     budget = int(args.serve_budget_gb * 1e9)
     solver = bcs.BCS_BICGSTAB if args.serve_solver == "bicgstab" else bcs.BCS_FGMRES
     with bcs.Server(budget_bytes=budget, slots=args.serve_slots, batch=args.serve_batch, solver=solver) as srv:
-        cases, ids, kinds = [], [], []
+        cases, ids, kinds, small = [], [], [], {}
         for c in range(ncases):
             nx = int(round(cells[c] ** (1.0 / 3.0)))
             nz = max(1, int(round(cells[c] / (nx * nx))))
@@ -826,6 +917,8 @@ def run_serve(args):
             ids.append(srv.register(sys0))
             cases.append(tuple({k: torch.from_numpy(v[k]).cuda() for k in keys} for v in (sys0, sys1)))
             kinds.append(kind)
+            if sys0["n_cells"] <= args.serve_oracle_max_cells:
+                small[c] = (sys0, sys1)  # host copies for the oracle parity subset
             del sys0, sys1
         torch.cuda.synchronize()
         gen_s = time.perf_counter() - t0
@@ -898,6 +991,9 @@ def run_serve(args):
         below = None
         if args.serve_rate > 0.8 * capacity["solves_per_s"]:
             below = run(0.8 * capacity["solves_per_s"], n_warm + n_req, n_warm, 7)
+        parity = None
+        if args.serve_oracle > 0 and small and not args.no_cpu_baseline:
+            parity = serve_oracle_parity(args, srv, ids, cases, small, solver)
     print(json.dumps({"impl": "native", "mode": "serve", "cases": ncases,
                       "cells_range": [5e4, max_cells], "cells_mean": float(cells.mean()),
                       "block_sizes": {"5": kinds.count(5), "4": kinds.count(4)}, "slots": args.serve_slots,
@@ -905,7 +1001,50 @@ def run_serve(args):
                       "budget": "default (80 % of free memory)" if budget == 0 else f"{args.serve_budget_gb:g} GB",
                       "inputs": "two value sets per case resident in device memory, alternated per request",
                       "setup_s": gen_s, "configured_rate": configured, "closed_loop_capacity": capacity,
-                      "at_80pct_capacity": below}), flush=True)
+                      "at_80pct_capacity": below, "oracle_parity": parity}), flush=True)
+
+
+def serve_oracle_parity(args, srv, ids, cases, small, solver):
+    """Requests of the smaller cases submitted together (in one mix on all
+    slots), each solution checked by the oracle on the host: its true
+    relative residual recomputed with the FP64 SpMV, and its distance to the
+    oracle's own solution of the same system. Repeats of one (case, value
+    set) must return identical solutions."""
+    import oracle
+    from paper_2403_07882_b300 import bcs
+    rng = np.random.default_rng(8)
+    keys = sorted(small)
+    picks = [(int(keys[rng.integers(0, len(keys))]), int(rng.integers(0, 2))) for _ in range(args.serve_oracle)]
+    tickets = [srv.submit(ids[c], cases[c][v]) for c, v in picks]
+    got = {}
+    identical = True
+    for (c, v), t in zip(picks, tickets):
+        st, res, _, x = srv.wait(t)
+        assert st == bcs.BCS_OK, res
+        x = x.cpu().numpy()
+        if (c, v) in got:
+            identical &= bool(np.array_equal(got[(c, v)], x))
+        else:
+            got[(c, v)] = x
+    okw = dict(solver=solver)
+    worst_res, worst_err = 0.0, 0.0
+    t0 = time.perf_counter()
+    oracle.use_openmp(True)
+    try:
+        for (c, v), x in got.items():
+            sysv = small[c][v]
+            ref = oracle.ldu_to_bsr(sysv)
+            xo, ores, _ = oracle.solve(ref, sysv["b"], cfg=oracle.config(**okw))
+            assert ores["status"] == 0, ores
+            bn = np.linalg.norm(sysv["b"])
+            worst_res = max(worst_res, float(np.linalg.norm(sysv["b"] - oracle.spmv(ref, x)) / bn))
+            worst_err = max(worst_err, float(np.linalg.norm(x - xo) / np.linalg.norm(xo)))
+    finally:
+        oracle.use_openmp(False)
+    return {"requests": len(picks), "distinct_systems": len(got), "cases": len(small),
+            "max_cells": args.serve_oracle_max_cells, "repeats_identical": identical,
+            "max_rel_res_true_by_oracle": worst_res, "max_rel_err_x_vs_oracle": worst_err,
+            "oracle_s": time.perf_counter() - t0, "oracle_cores": host_info()["nproc"]}
 
 
 def main():
