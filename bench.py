@@ -45,7 +45,8 @@ def parse():
     p.add_argument("--side", type=int, default=SIDE)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-full", action="store_true",
-                   help="also run the oracle (OpenMP build) on the full-size system once (minutes, ~20 GB host memory)")
+                   help="also run the oracle (OpenMP build, then one core) on the full-size system once "
+                        "(minutes, ~20 GB host memory)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison run")
     p.add_argument("--no-assembly", action="store_true", help="skip the density-based assembly measurement")
@@ -334,6 +335,9 @@ def cpu_baseline_entry(side, dev=None, full=False):
         tf, _, rf = oracle_run(big, omp=True)
         entry["full_size_omp"] = dict(side=side, cores=host["nproc"], iters=rf["iters"],
                                       rel_res_final=rf["rel_res_final"], **tf)
+        ts, _, rs = oracle_run(big)
+        entry["full_size_single_thread"] = dict(side=side, cores=1, iters=rs["iters"],
+                                                rel_res_final=rs["rel_res_final"], **ts)
     if dev is not None:
         entry["gpu_error_vs_oracle"] = {"system": f"density-based {SAMPLE_SIDE}^3, seed 2 (the sample above)",
                                         "arms": gpu_error_arms(system, x_ref, dev)}
