@@ -119,6 +119,13 @@ typedef struct bcs_config {
                               sweep, residual and transfer (identical results); read at each
                               set_values; 0 (default) = off: measured on B300, the graph-replayed
                               separate launches are faster */
+  int dilu_cluster_rows;   /* FP32 / BF16 cycle with the DILU or SGS smoother: on levels of at
+                              most dilu_cluster_rows block rows a smoothing step (residual and
+                              every colour's forward and backward sweep) runs as one launch of a
+                              thread-block cluster with a cluster barrier between colours,
+                              instead of 1 + 2 x colours launches (identical results); read at
+                              each set_values; default 4096 (measured on B300: larger levels run
+                              faster as separate full-GPU launches), 0 = off */
   /* Device memory, read by bcs_create (later changes are ignored): with alloc
      and release both set, every device buffer of the solver comes from
      alloc(bytes, stream, alloc_user) and goes back through release(ptr,

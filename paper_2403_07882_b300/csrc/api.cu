@@ -124,6 +124,7 @@ bcs_status check_config(const bcs_config* c) {
   if (c->cycle_graph < -1 || c->cycle_graph > 1) return BCS_EINVAL;
   if (c->reorder < 0 || c->reorder > 1) return BCS_EINVAL;
   if (c->tail_rows < 0) return BCS_EINVAL;
+  if (c->dilu_cluster_rows < 0) return BCS_EINVAL;
   if ((c->alloc == nullptr) != (c->release == nullptr)) return BCS_EINVAL;
   if (c->slice_layout < -1 || c->slice_layout > 1) return BCS_EINVAL;
   if (c->smoother < BCS_SMOOTH_JACOBI || c->smoother > BCS_SMOOTH_SGS) return BCS_EINVAL;
@@ -212,6 +213,7 @@ bcs_status bcs_config_default(bcs_config* c) {
   c->cycle_graph = -1;
   c->reorder = 0;
   c->tail_rows = 0;
+  c->dilu_cluster_rows = 4096;
   return BCS_OK;
 }
 

@@ -98,7 +98,15 @@ __global__ void __launch_bounds__(128) k_rows(int rows, const int32_t* __restric
 // (rw, r) of a row group; every lane of the warp calls it (shuffles), active
 // says whether the lane has a row. Vectors the sweeps write (r, y, d, x) are
 // read with ordinary loads.
-template <int N, class AT, class TV, class TD, class TC, bool FWD, bool GATHER>
+// COH: the vectors are read through L2 (ld.global.cg), for the one-launch
+// step in which other blocks of the cluster wrote them in earlier phases.
+template <bool COH, class T>
+__device__ __forceinline__ T ldw(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+
+template <int N, class AT, class TV, class TD, class TC, bool FWD, bool GATHER, bool COH = false>
 __device__ __forceinline__ void dilu_row(bool active, int i, int t, int rw, int r, const int32_t* __restrict__ dptr,
                                          const int32_t* __restrict__ dmid, const int32_t* __restrict__ dsrc,
                                          const int32_t* __restrict__ dci, const TV* __restrict__ val,
@@ -113,11 +121,11 @@ __device__ __forceinline__ void dilu_row(bool active, int i, int t, int rw, int 
       const TV* a = val + blk * (N * N) + r * N;
       const TC* v = (FWD ? y : d) + (size_t)j * N;
 #pragma unroll
-      for (int cc = 0; cc < N; ++cc) acc = fma(lda<AT>(a + cc), (AT)v[cc], acc);
+      for (int cc = 0; cc < N; ++cc) acc = fma(lda<AT>(a + cc), (AT)ldw<COH>(v + cc), acc);
     }
   }
   const size_t o = (size_t)i * N + r;
-  const AT u = active ? (FWD ? (AT)rv[o] - acc : acc) : (AT)0;
+  const AT u = active ? (FWD ? (AT)ldw<COH>(rv + o) - acc : acc) : (AT)0;
   AT s = 0;
 #pragma unroll
   for (int cc = 0; cc < N; ++cc) {
@@ -128,9 +136,9 @@ __device__ __forceinline__ void dilu_row(bool active, int i, int t, int rw, int 
   if (FWD) {
     y[o] = (TC)s;
   } else {
-    const AT dv = (AT)y[o] - s;
+    const AT dv = (AT)ldw<COH>(y + o) - s;
     d[o] = (TC)dv;
-    x[o] = (TC)((AT)x[o] + dv);
+    x[o] = (TC)((AT)ldw<COH>(x + o) + dv);
   }
 }
 
@@ -672,6 +680,67 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const TailPhase* __restri
   }
 }
 
+// ---- one-launch DILU smoothing step for small levels --------------------------
+// A level below a size threshold runs a whole DILU / SGS step as one launch
+// of a thread-block cluster: the residual r = b - A x (when the level has the
+// lane-per-row layout; otherwise it is launched before), then the forward
+// sweep colour by colour and the backward sweep in reverse colour order, with
+// a cluster barrier between phases. Each row is computed by the same device
+// functions as the per-colour launches (identical results); vectors written
+// by earlier phases are read through L2, which the barrier's release /
+// acquire makes coherent across the cluster's SMs.
+constexpr int DC_THREADS = 512;
+
+struct DiluClusterArgs {
+  int rows, nslices, ncol;
+  const int32_t *rp, *sptr, *sci;  // lane-per-row sliced copy (the residual)
+  const void* sv;
+  const int32_t *cstart, *crow, *dptr, *dmid, *dci;
+  const void* dval;  // split-order values
+  const float* einv;
+  const float* b;
+  float *x, *r, *y, *d;
+};
+
+template <int N, class TV, bool RESID>
+__global__ void __launch_bounds__(DC_THREADS) k_dilu_cluster(const DiluClusterArgs A) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int g = (int)(cl.block_rank() * blockDim.x + threadIdx.x);
+  const int gw = g >> 5, nw = (int)(cl.num_blocks() * blockDim.x) >> 5;
+  constexpr int RPW = 32 / N;
+  const int lane = threadIdx.x & 31, rw = lane / N, r = lane - rw * N;
+  if constexpr (RESID) {
+    for (int sl = gw; sl < A.nslices; sl += nw)
+      sell_slice<N, TV, false, true>(sl, A.rows, A.rp, A.sptr, A.sci, (const TV*)A.sv, nullptr, A.x, A.b, A.r, 0.f);
+    cl.sync();
+  }
+  const TV* dv = (const TV*)A.dval;
+  for (int c = 0; c < A.ncol; ++c) {
+    const int t0 = __ldg(A.cstart + c), cnt = __ldg(A.cstart + c + 1) - t0;
+    for (int base = gw * RPW; base < cnt; base += nw * RPW) {  // uniform across the warp
+      const int mi = base + rw;
+      const bool active = rw < RPW && mi < cnt;
+      const int t = t0 + (active ? mi : 0);
+      const int i = active ? __ldg(A.crow + t) : 0;
+      dilu_row<N, float, TV, float, float, true, false, true>(active, i, t, rw, r, A.dptr, A.dmid, nullptr, A.dci,
+                                                               dv, A.einv, A.r, A.y, A.d, A.x);
+    }
+    cl.sync();
+  }
+  for (int c = A.ncol - 1; c >= 0; --c) {
+    const int t0 = __ldg(A.cstart + c), cnt = __ldg(A.cstart + c + 1) - t0;
+    for (int base = gw * RPW; base < cnt; base += nw * RPW) {
+      const int mi = base + rw;
+      const bool active = rw < RPW && mi < cnt;
+      const int t = t0 + (active ? mi : 0);
+      const int i = active ? __ldg(A.crow + t) : 0;
+      dilu_row<N, float, TV, float, float, false, false, true>(active, i, t, rw, r, A.dptr, A.dmid, nullptr, A.dci,
+                                                                dv, A.einv, A.r, A.y, A.d, A.x);
+    }
+    if (c > 0) cl.sync();
+  }
+}
+
 // ---- batched V-cycle: blockIdx.z selects the case ------------------------------
 // One launch per phase of each level covers every case that has that level
 // (and whose FGMRES step is live); each element is computed by the device
@@ -891,6 +960,37 @@ struct Cycle {
     TC* r = (TC*)L.vr.p;
     TC* y = (TC*)L.vt.p;
     TC* d = (TC*)L.vd.p;
+    if constexpr (std::is_same<TC, float>::value) {
+      if (L.dcl > 0) {
+        // the whole step as one cluster launch (the residual inside it when
+        // the level has the lane-per-row layout)
+        const bool inner = L.smap == 0;
+        if (!inner) BCS_OKR(resid<N>(L, x, b, r));
+        const DiluClusterArgs A{L.A.rows, L.nslices, L.ncol, L.A.rp.p, L.sptr.p, L.sci.p, smat(L),
+                                L.cstart_d.p, L.crow.p, L.dptr.p, L.dmid.p, L.dci.p, dmat(L), deinv(L),
+                                (const float*)b, (float*)x, (float*)r, (float*)y, (float*)d};
+        cudaLaunchConfig_t lc{};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = L.dcl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.gridDim = dim3(L.dcl);
+        lc.blockDim = dim3(DC_THREADS);
+        lc.dynamicSmemBytes = 0;
+        lc.stream = s->stream;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        const double per_row = (double)N * N * sizeof(TV) + N * N * sizeof(TD) + 3.0 * N * sizeof(TC);
+        const double rbytes = (double)L.A.nnz * (N * N * sizeof(TV) + 4) + 4.0 * (L.A.rows + 1) +
+                              (double)L.A.rows * N * 3 * sizeof(TC);
+        s->pre(K_SWEEP);
+        if (inner) BCS_CU(s, cudaLaunchKernelEx(&lc, k_dilu_cluster<N, TV, true>, A));
+        else BCS_CU(s, cudaLaunchKernelEx(&lc, k_dilu_cluster<N, TV, false>, A));
+        return s->post(K_SWEEP, "k_dilu_cluster", 2.0 * per_row * L.A.rows + (inner ? rbytes : 0.0),
+                       2.0 * (L.A.nnz + 2.0 * L.A.rows) * N * N);
+      }
+    }
     BCS_OKR(resid<N>(L, x, b, r));
     constexpr bool G = std::is_same<TV, double>::value;  // FP64: the BSR values through dsrc
     const double per_row = (double)N * N * sizeof(TV) + N * N * sizeof(TD) + 3.0 * N * sizeof(TC);
@@ -1251,6 +1351,40 @@ bcs_status slice_map(Solver* s, Level& L, int prec, bool tail, int* map) {
   return BCS_OK;
 }
 
+// Blocks of the one-launch DILU step's cluster on this device: 16 (a
+// non-portable size) when a cluster that large can be resident, else 8, else
+// 0 (per-colour launches).
+template <int N, class TV>
+int dilu_cluster_blocks() {
+  for (int cs : {16, 8}) {
+    if (cs > 8 &&
+        (cudaFuncSetAttribute(k_dilu_cluster<N, TV, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+             cudaSuccess ||
+         cudaFuncSetAttribute(k_dilu_cluster<N, TV, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+             cudaSuccess)) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t lc{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.gridDim = dim3(cs);
+    lc.blockDim = dim3(DC_THREADS);
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int n1 = 0, n2 = 0;
+    if (cudaOccupancyMaxActiveClusters(&n1, k_dilu_cluster<N, TV, true>, &lc) == cudaSuccess &&
+        cudaOccupancyMaxActiveClusters(&n2, k_dilu_cluster<N, TV, false>, &lc) == cudaSuccess && n1 >= 1 &&
+        n2 >= 1)
+      return cs;
+    (void)cudaGetLastError();
+  }
+  return 0;
+}
+
 // Cycle vectors and storage copies of the hierarchy in the configured
 // precision (after every setup / resetup).
 // ---- coarse-tail plan ----------------------------------------------------------
@@ -1438,6 +1572,7 @@ bcs_status cycle_prepare(Solver* s) {
   DBuf<int32_t> steps;
   BCS_ALLOC(s, steps, nl);
   std::vector<char> needed(nl, 0);
+  int dcl_blocks = -1;  // cluster size of the one-launch DILU step, looked up once
   for (size_t l = 0; l < nl; ++l) {
     Level& L = s->lv[l];
     LevelScope level_scope(s, (int)l);
@@ -1447,8 +1582,18 @@ bcs_status cycle_prepare(Solver* s) {
     BCS_ALLOC(s, L.vr, N * vsz);
     BCS_ALLOC(s, L.vt, N * vsz);
     if (L.ncol > 0) BCS_ALLOC(s, L.vd, N * vsz);
+    L.dcl = 0;
     if (!sliced) continue;
     BCS_OKR(dilu_prepare(s, L));
+    if (L.ncol > 0 && L.A.rows <= s->setup_cfg.dilu_cluster_rows) {
+      if (dcl_blocks < 0)
+        BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
+          constexpr int NB = decltype(NC)::value;
+          dcl_blocks = prec == BCS_PREC_FP32 ? dilu_cluster_blocks<NB, float>() : dilu_cluster_blocks<NB, bf16>();
+          return BCS_OK;
+        }));
+      L.dcl = dcl_blocks;
+    }
     BCS_ALLOC(s, L.dinv32, (size_t)L.A.rows * nn);
     BCS_OKR(cast_vec<double, float>(s, L.dinv.p, L.dinv32.p, (size_t)L.A.rows * nn));
     int map = 0;

@@ -315,7 +315,8 @@ bcs_status dilu_setup(Solver* s, Level& L, bool full, bool sgs) {
     if (h[1] & 32) return BCS_OK;  // more than 128 colours: this level keeps block Jacobi
     if (cin != L.colour.p) L.colour = std::move(other);
     // colour lists
-    DBuf<int32_t> cnt, start, cursor;
+    DBuf<int32_t> cnt, cursor;
+    DBuf<int32_t>& start = L.cstart_d;
     BCS_ALLOC(s, cnt, DILU_MAX_COLOURS);
     BCS_ALLOC(s, start, DILU_MAX_COLOURS + 1);
     BCS_ALLOC(s, cursor, DILU_MAX_COLOURS);

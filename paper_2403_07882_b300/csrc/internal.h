@@ -153,6 +153,8 @@ struct Level {
   DBuf<int32_t> colour;      // colour of each row
   DBuf<int32_t> crow;        // rows grouped by colour: cstart[c] .. cstart[c+1]
   std::vector<int> cstart;
+  DBuf<int32_t> cstart_d;    // cstart on the device
+  int dcl = 0;               // FP32 / BF16 cycle: blocks of the one-launch DILU step's cluster (0: per colour)
   DBuf<double> einv;         // E_i^{-1}, FP64
   // each row's off-diagonal blocks split for the sweeps: the lower part
   // (colour(j) < colour(i)) then the upper part (colour(j) > colour(i)),

@@ -98,3 +98,37 @@ def test_dilu_graph_cycle_identical():
             vt = torch.from_numpy(v).to(DEV)
             out[graph] = (s.precond(vt).cpu().numpy(), s.precond(vt).cpu().numpy())
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[1][0], out[1][1])
+
+
+CLUSTER_CASES = [
+    ("density 16^3 DILU fp32", lambda: synth.density(16, seed=0), dict(smoother=DILU)),
+    ("density 16^3 DILU bf16", lambda: synth.density(16, seed=0), dict(smoother=DILU, precision=bcs.BCS_PREC_BF16)),
+    ("pressure 20^3 DILU, tpr layout", lambda: synth.pressure(20, seed=2), dict(smoother=DILU, slice_layout=1)),
+    ("knn 14 DILU", lambda: synth.knn(14, seed=3), dict(smoother=DILU)),
+    ("density 12^3 SGS smoother", lambda: synth.density(12, seed=4), dict(smoother=bcs.BCS_SMOOTH_SGS)),
+    ("density 12^3 SGS preconditioner", lambda: synth.density(12, seed=4),
+     dict(precond=bcs.BCS_PC_SGS, maxiter=5000)),
+]
+
+
+@pytest.mark.parametrize("name,gen,kw", CLUSTER_CASES, ids=[c[0] for c in CLUSTER_CASES])
+def test_dilu_cluster_step_identical(name, gen, kw):
+    """Levels below dilu_cluster_rows run a DILU / SGS step (residual and
+    every colour of both sweeps) as one thread-block-cluster launch: the same
+    solve as with one launch per colour (dilu_cluster_rows = 0), bit for
+    bit, with and without the graph-replayed cycle."""
+    system = gen()
+    b = torch.from_numpy(system["b"]).to(DEV)
+    out = {}
+    for rows, graph in ((0, 1), (1 << 30, 1), (1 << 30, 0)):
+        with bcs.Solver(system["n"], dilu_cluster_rows=rows, cycle_graph=graph, **kw) as s:
+            s.load(system, device=DEV)
+            x, st, res = s.solve(b)
+            assert st == bcs.BCS_OK, res
+            out[(rows, graph)] = (x.cpu().numpy(), res["iters"], s.stats()["kinds"]["jacobi_sweep"]["launches"])
+    ref = out[(0, 1)]
+    for key, (x, it, n) in out.items():
+        assert it == ref[1], key
+        assert np.array_equal(x, ref[0]), key
+        if key[0]:
+            assert 0 < n < ref[2], (key, n, ref[2])  # one launch per step instead of 2 x colours
