@@ -126,6 +126,12 @@ typedef struct bcs_config {
                               instead of 1 + 2 x colours launches (identical results); read at
                               each set_values; default 4096 (measured on B300: larger levels run
                               faster as separate full-GPU launches), 0 = off */
+  int dependent_launch;    /* 1 (default): the V-cycle's kernels are launched as programmatic
+                              dependent launches (each may be scheduled while the kernel before
+                              it finishes, and waits for that kernel's results before touching
+                              any data), which hides part of the launch gap between the many
+                              short kernels of the coarse levels; 0: ordinary launches.
+                              Identical results either way */
   /* Device memory, read by bcs_create (later changes are ignored): with alloc
      and release both set, every device buffer of the solver comes from
      alloc(bytes, stream, alloc_user) and goes back through release(ptr,

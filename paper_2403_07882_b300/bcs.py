@@ -41,7 +41,7 @@ class bcs_config(ct.Structure):
         ("p_omega", ct.c_double), ("coarse_dense_max", ct.c_int), ("coarse_sweeps", ct.c_int),
         ("precision", ct.c_int), ("smoother", ct.c_int), ("profile", ct.c_int), ("profile_kinds", ct.c_int),
         ("slice_layout", ct.c_int), ("cycle_graph", ct.c_int), ("reorder", ct.c_int), ("tail_rows", ct.c_int),
-        ("dilu_cluster_rows", ct.c_int), ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_user", ct.c_void_p),
+        ("dilu_cluster_rows", ct.c_int), ("dependent_launch", ct.c_int), ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_user", ct.c_void_p),
     ]
 
 

@@ -125,6 +125,7 @@ bcs_status check_config(const bcs_config* c) {
   if (c->reorder < 0 || c->reorder > 1) return BCS_EINVAL;
   if (c->tail_rows < 0) return BCS_EINVAL;
   if (c->dilu_cluster_rows < 0) return BCS_EINVAL;
+  if (c->dependent_launch < 0 || c->dependent_launch > 1) return BCS_EINVAL;
   if ((c->alloc == nullptr) != (c->release == nullptr)) return BCS_EINVAL;
   if (c->slice_layout < -1 || c->slice_layout > 1) return BCS_EINVAL;
   if (c->smoother < BCS_SMOOTH_JACOBI || c->smoother > BCS_SMOOTH_SGS) return BCS_EINVAL;
@@ -214,6 +215,7 @@ bcs_status bcs_config_default(bcs_config* c) {
   c->reorder = 0;
   c->tail_rows = 0;
   c->dilu_cluster_rows = 4096;
+  c->dependent_launch = 1;
   return BCS_OK;
 }
 

@@ -56,6 +56,7 @@ template <int K>
 __global__ void __launch_bounds__(RED_THREADS) k_multidot(const double* __restrict__ V, size_t ldv, int q_base,
                                                           const double* __restrict__ w, size_t N,
                                                           double* __restrict__ partial) {
+  dep_enter();
   multidot_body<K>(V, ldv, 1 << 30, q_base + blockIdx.y * K, w, N, partial);
 }
 
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_multidot_ks(const double* __res
                                                              const KrylovState* __restrict__ ks, int with_w,
                                                              const double* __restrict__ w, size_t N,
                                                              double* __restrict__ partial) {
+  dep_enter();
   const int nv = ks->j + 1, k = nv + with_w;
   const int q0 = blockIdx.y * MD_CHUNK, cnt = min(MD_CHUNK, k - q0);
   switch (cnt) {
@@ -87,6 +89,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_multidot_ks(const double* __res
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_partials(const double* __restrict__ partial,
                                                                  double* __restrict__ out,
                                                                  const KrylovState* __restrict__ ks, int extra) {
+  dep_enter();
   __shared__ double sm[RED_THREADS / 32];
   const int q = blockIdx.x;
   if (ks && q >= ks->j + 1 + extra) return;
@@ -106,6 +109,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_partials(const double* _
 
 // *flag = 1.0 if some x[i] != 0 (flag cleared to 0.0 beforehand).
 __global__ void k_any_nonzero(const double* __restrict__ x, size_t N, double* __restrict__ flag) {
+  dep_enter();
   bool nz = false;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
     nz |= x[i] != 0.0;
@@ -115,6 +119,7 @@ __global__ void k_any_nonzero(const double* __restrict__ x, size_t N, double* __
 // w[i] -= sum_q h[q] V[q][i]
 __global__ void k_gs_update(const double* __restrict__ V, size_t ldv, int k, const double* __restrict__ h,
                             double* __restrict__ w, size_t N) {
+  dep_enter();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     double t = w[i];
     for (int q = 0; q < k; ++q) t = fma(-__ldg(h + q), __ldg(V + (size_t)q * ldv + i), t);
@@ -130,6 +135,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gs_update_norm(const double* __
                                                                 const KrylovState* __restrict__ ks,
                                                                 const double* __restrict__ h, double* __restrict__ w,
                                                                 size_t N, double* __restrict__ partial) {
+  dep_enter();
   const int k = ks ? ks->j + 1 : k_host;
   double acc = 0.0;
   const size_t stride = (size_t)RED_BLOCKS * RED_THREADS;
@@ -161,6 +167,7 @@ struct Coefs {
 template <class TZ>
 __global__ void k_add_combination(const TZ* __restrict__ Z, size_t ldz, int k, Coefs y, double* __restrict__ x,
                                   size_t N) {
+  dep_enter();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     double t = x[i];
     for (int q = 0; q < k; ++q) t = fma(y.c[q], (double)Z[(size_t)q * ldz + i], t);
@@ -172,12 +179,14 @@ __global__ void k_add_combination(const TZ* __restrict__ Z, size_t ldz, int k, C
 __device__ __forceinline__ double axpby_elem(double a, double x, double b, double y) { return a * x + b * y; }
 
 __global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, size_t N) {
+  dep_enter();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
     y[i] = axpby_elem(a, x[i], b, y[i]);
 }
 
 // y = a x
-__global__ void k_scale(double a, const double* x, double* y, size_t N) {  // may run in place
+__global__ void k_scale(double a, const double* x, double* y, size_t N) {
+  dep_enter();  // may run in place
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
     y[i] = a * x[i];
 }
@@ -189,6 +198,7 @@ __device__ __forceinline__ double bicg_p_elem(double beta, double omega, double 
 
 __global__ void k_bicg_p(double beta, double omega, const double* __restrict__ r, const double* __restrict__ v,
                          double* __restrict__ p, size_t N) {
+  dep_enter();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
     p[i] = bicg_p_elem(beta, omega, r[i], v[i], p[i]);
 }
@@ -198,6 +208,7 @@ __global__ void k_bicg_p(double beta, double omega, const double* __restrict__ r
 // with explicitly rounded FP64 operations (no fused multiply-add), as the
 // host compiler evaluates them, so both paths give the same bits.
 __global__ void k_ks_init(KrylovState* ks, double beta, double bnorm, int iters, int m, int maxiter, double tol) {
+  dep_enter();
   const int t = threadIdx.x;
   for (int i = t; i <= m; i += blockDim.x) ks->g[i] = i == 0 ? beta : 0.0;
   if (t == 0) {
@@ -217,6 +228,7 @@ __global__ void k_ks_init(KrylovState* ks, double beta, double bnorm, int iters,
 template <class TO>
 __global__ void k_ks_take_vj(const double* __restrict__ V, size_t ldv, const KrylovState* __restrict__ ks,
                              TO* __restrict__ out, size_t N) {
+  dep_enter();
   const double* v = V + (size_t)ks->j * ldv;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
     out[i] = (TO)v[i];
@@ -226,6 +238,7 @@ __global__ void k_ks_take_vj(const double* __restrict__ V, size_t ldv, const Kry
 template <class TZ>
 __global__ void k_ks_store_z(const TZ* __restrict__ z, TZ* __restrict__ Z, const KrylovState* __restrict__ ks,
                              double* __restrict__ widen, size_t N) {
+  dep_enter();
   TZ* zj = Z + (size_t)ks->j * N;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     const TZ v = z[i];
@@ -292,6 +305,7 @@ __device__ int givens_step(KrylovState* __restrict__ ks, const double* __restric
 
 __global__ void k_ks_givens(KrylovState* __restrict__ ks, const double* __restrict__ scal, int slot_a, int slot_b,
                             int slot_n, cudaGraphConditionalHandle cond, int use_cond) {
+  dep_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int stop = givens_step(ks, scal, slot_a, slot_b, slot_n);
   if (use_cond) cudaGraphSetConditional(cond, stop == KS_RUN ? 1u : 0u);
@@ -300,6 +314,7 @@ __global__ void k_ks_givens(KrylovState* __restrict__ ks, const double* __restri
 // V_{j+1} = w / h_{j+1,j} unless the step broke down (j already advanced)
 __global__ void k_ks_scale_next(const KrylovState* __restrict__ ks, const double* __restrict__ w,
                                 double* __restrict__ V, size_t ldv, size_t N) {
+  dep_enter();
   const int stop = ks->stop;
   if (stop == KS_HAPPY || stop == KS_BREAKDOWN) return;
   const double a = ks->rhn;
@@ -310,6 +325,7 @@ __global__ void k_ks_scale_next(const KrylovState* __restrict__ ks, const double
 
 // y = R^{-1} g over the cycle's jend steps (back substitution)
 __global__ void k_ks_backsolve(KrylovState* __restrict__ ks) {
+  dep_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (ks->stop == KS_BREAKDOWN) return;
   const int jend = ks->jend, m = ks->m;
@@ -325,6 +341,7 @@ __global__ void k_ks_backsolve(KrylovState* __restrict__ ks) {
 template <class TZ>
 __global__ void k_ks_combine(const TZ* __restrict__ Z, size_t ldz, const KrylovState* __restrict__ ks,
                              double* __restrict__ x, size_t N) {
+  dep_enter();
   const int k = ks->stop == KS_BREAKDOWN ? 0 : ks->jend;
   const double* y = ks->y;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
@@ -335,6 +352,7 @@ __global__ void k_ks_combine(const TZ* __restrict__ Z, size_t ldz, const KrylovS
 }
 
 __global__ void k_ks_export(const KrylovState* __restrict__ ks, double* __restrict__ scal) {
+  dep_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   scal[0] = (double)ks->iters;
   scal[1] = (double)ks->jend;
@@ -523,6 +541,7 @@ __global__ void kb_gather_out_k(const BCase* __restrict__ cases, int count, doub
 // host-driven loop evaluates them, and the vector updates use the same
 // element functions, so both loops give the same bits.
 __global__ void k_bs_init(BicgState* bs, int it, int maxiter, double tol, double bnorm, int first) {
+  dep_enter();
   if (threadIdx.x != 0) return;
   bs->it = it;
   bs->stop = BS_RUN;
@@ -539,6 +558,7 @@ __global__ void k_bs_init(BicgState* bs, int it, int maxiter, double tol, double
 }
 
 __global__ void k_bs_rho(BicgState* __restrict__ bs, const double* __restrict__ scal) {
+  dep_enter();
   if (threadIdx.x != 0 || bs->stop != BS_RUN) return;
   const double rho = scal[SLOT_A];
   bs->rho = rho;
@@ -551,6 +571,7 @@ __global__ void k_bs_rho(BicgState* __restrict__ bs, const double* __restrict__ 
 
 __global__ void k_bs_p(const BicgState* __restrict__ bs, const double* __restrict__ r, const double* __restrict__ v,
                        double* __restrict__ p, size_t N) {
+  dep_enter();
   if (bs->stop != BS_RUN) return;
   const bool first = bs->first;
   const double beta = bs->beta, omega = bs->omega;
@@ -559,6 +580,7 @@ __global__ void k_bs_p(const BicgState* __restrict__ bs, const double* __restric
 }
 
 __global__ void k_bs_alpha(BicgState* __restrict__ bs, const double* __restrict__ scal) {
+  dep_enter();
   if (threadIdx.x != 0 || bs->stop != BS_RUN) return;
   bs->first = 0;
   const double den = scal[SLOT_A];
@@ -572,6 +594,7 @@ __global__ void k_bs_alpha(BicgState* __restrict__ bs, const double* __restrict_
 // s = r - alpha v (the host loop: s = r, then s = (-alpha) v + 1 s)
 __global__ void k_bs_s(const BicgState* __restrict__ bs, const double* __restrict__ r, const double* __restrict__ v,
                        double* __restrict__ sv, size_t N) {
+  dep_enter();
   if (bs->stop != BS_RUN) return;
   const double a = -bs->alpha;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
@@ -579,6 +602,7 @@ __global__ void k_bs_s(const BicgState* __restrict__ bs, const double* __restric
 }
 
 __global__ void k_bs_snorm(BicgState* __restrict__ bs, const double* __restrict__ scal) {
+  dep_enter();
   if (threadIdx.x != 0 || bs->stop != BS_RUN) return;
   bs->it = bs->it + 1;
   const double snrm = __dsqrt_rn(scal[SLOT_N]);
@@ -586,6 +610,7 @@ __global__ void k_bs_snorm(BicgState* __restrict__ bs, const double* __restrict_
 }
 
 __global__ void k_bs_omega(BicgState* __restrict__ bs, const double* __restrict__ scal) {
+  dep_enter();
   if (threadIdx.x != 0 || bs->stop != BS_RUN) return;
   const double ts = scal[SLOT_A], tt = scal[SLOT_A + 1];
   if (tt == 0.0 || !isfinite(tt)) {
@@ -598,6 +623,7 @@ __global__ void k_bs_omega(BicgState* __restrict__ bs, const double* __restrict_
 // x += alpha ph + omega sh (ph and sh consecutive, cycle precision)
 template <class TZ>
 __global__ void k_bs_x(const BicgState* __restrict__ bs, const TZ* __restrict__ ph, double* __restrict__ x, size_t N) {
+  dep_enter();
   if (bs->stop != BS_RUN) return;
   const double a = bs->alpha, o = bs->omega;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
@@ -611,6 +637,7 @@ __global__ void k_bs_x(const BicgState* __restrict__ bs, const TZ* __restrict__ 
 // r = s - omega t (the host loop: r = s, then r = (-omega) t + 1 r)
 __global__ void k_bs_r(const BicgState* __restrict__ bs, const double* __restrict__ sv, const double* __restrict__ t,
                        double* __restrict__ r, size_t N) {
+  dep_enter();
   if (bs->stop != BS_RUN) return;
   const double a = -bs->omega;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
@@ -620,6 +647,7 @@ __global__ void k_bs_r(const BicgState* __restrict__ bs, const double* __restric
 // end of an iteration: rho_old, the residual test, omega = 0, the limit;
 // the loop runs on while nothing happened
 __global__ void k_bs_export(const BicgState* __restrict__ bs, double* __restrict__ scal) {
+  dep_enter();
   if (threadIdx.x != 0) return;
   scal[SLOT_S] = (double)bs->it;
   scal[SLOT_S + 1] = (double)bs->stop;
@@ -628,6 +656,7 @@ __global__ void k_bs_export(const BicgState* __restrict__ bs, double* __restrict
 
 __global__ void k_bs_end(BicgState* __restrict__ bs, const double* __restrict__ scal,
                          cudaGraphConditionalHandle cond) {
+  dep_enter();
   if (threadIdx.x != 0) return;
   if (bs->stop == BS_RUN) {
     bs->rho_old = bs->rho;
@@ -652,20 +681,20 @@ bcs_status multidot(Solver* s, const double* V, size_t ldv, int k, const double*
   if (k > 72) return s->fail(BCS_EINVAL, "too many vectors in one multidot");
   const int full = k / MD_CHUNK, rem = k % MD_CHUNK;
   if (full > 0)
-    BCS_LAUNCH(s, K_BLAS, 8.0 * N * (full * MD_CHUNK + full), 2.0 * N * full * MD_CHUNK, k_multidot<MD_CHUNK>,
+    BCS_LAUNCH_DEP(s, K_BLAS, 8.0 * N * (full * MD_CHUNK + full), 2.0 * N * full * MD_CHUNK, k_multidot<MD_CHUNK>,
                dim3(RED_BLOCKS, full), RED_THREADS, 0, V, ldv, 0, w, N, s->red.p);
   const int qb = full * MD_CHUNK;
   switch (rem) {
 #define BCS_MD_TAIL(R)                                                                                   \
   case R:                                                                                                \
-    BCS_LAUNCH(s, K_BLAS, 8.0 * N * (R + 1), 2.0 * N * R, k_multidot<R>, dim3(RED_BLOCKS, 1), RED_THREADS, 0, \
+    BCS_LAUNCH_DEP(s, K_BLAS, 8.0 * N * (R + 1), 2.0 * N * R, k_multidot<R>, dim3(RED_BLOCKS, 1), RED_THREADS, 0, \
                V, ldv, qb, w, N, s->red.p);                                                              \
     break;
     BCS_MD_TAIL(1) BCS_MD_TAIL(2) BCS_MD_TAIL(3) BCS_MD_TAIL(4) BCS_MD_TAIL(5) BCS_MD_TAIL(6) BCS_MD_TAIL(7)
 #undef BCS_MD_TAIL
     default: break;
   }
-  BCS_LAUNCH(s, K_BLAS, 8.0 * k * RED_BLOCKS, 0, k_reduce_partials, k, RED_THREADS, 0, s->red.p, s->scal.p + slot,
+  BCS_LAUNCH_DEP(s, K_BLAS, 8.0 * k * RED_BLOCKS, 0, k_reduce_partials, k, RED_THREADS, 0, s->red.p, s->scal.p + slot,
              (const KrylovState*)nullptr, 0);
   return BCS_OK;
 }
@@ -676,7 +705,7 @@ bcs_status dot(Solver* s, const double* x, const double* y, size_t N, int slot) 
 
 bcs_status any_nonzero(Solver* s, const double* x, size_t N, int slot) {
   BCS_CU(s, cudaMemsetAsync(s->scal.p + slot, 0, sizeof(double), s->stream));
-  BCS_LAUNCH(s, K_BLAS, 8.0 * N, 0, k_any_nonzero, RED_BLOCKS, RED_THREADS, 0, x, N, s->scal.p + slot);
+  BCS_LAUNCH_DEP(s, K_BLAS, 8.0 * N, 0, k_any_nonzero, RED_BLOCKS, RED_THREADS, 0, x, N, s->scal.p + slot);
   return BCS_OK;
 }
 
@@ -688,41 +717,41 @@ bcs_status fetch_scalars(Solver* s, int count) {
 }
 
 bcs_status gs_update(Solver* s, const double* V, size_t ldv, int k, const double* hdev, double* w, size_t N) {
-  BCS_LAUNCH(s, K_BLAS, 8.0 * N * (k + 2), 2.0 * N * k, k_gs_update, vgrid(N), 256, 0, V, ldv, k, hdev, w, N);
+  BCS_LAUNCH_DEP(s, K_BLAS, 8.0 * N * (k + 2), 2.0 * N * k, k_gs_update, vgrid(N), 256, 0, V, ldv, k, hdev, w, N);
   return BCS_OK;
 }
 
 bcs_status gs_update_norm(Solver* s, const double* V, size_t ldv, int k, const double* hdev, double* w, size_t N,
                           int slot) {
   BCS_ALLOC(s, s->red, (size_t)72 * RED_BLOCKS);
-  BCS_LAUNCH(s, K_BLAS, 8.0 * N * (k + 2), 2.0 * N * (k + 1), k_gs_update_norm, RED_BLOCKS, RED_THREADS, 0, V, ldv, k,
+  BCS_LAUNCH_DEP(s, K_BLAS, 8.0 * N * (k + 2), 2.0 * N * (k + 1), k_gs_update_norm, RED_BLOCKS, RED_THREADS, 0, V, ldv, k,
              (const KrylovState*)nullptr, hdev, w, N, s->red.p);
-  BCS_LAUNCH(s, K_BLAS, 8.0 * RED_BLOCKS, 0, k_reduce_partials, 1, RED_THREADS, 0, s->red.p, s->scal.p + slot,
+  BCS_LAUNCH_DEP(s, K_BLAS, 8.0 * RED_BLOCKS, 0, k_reduce_partials, 1, RED_THREADS, 0, s->red.p, s->scal.p + slot,
              (const KrylovState*)nullptr, 0);
   return BCS_OK;
 }
 
 bcs_status ks_init(Solver* s, KrylovState* ks, double beta, double bnorm, int iters, int m, int maxiter, double tol) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, k_ks_init, 1, 128, 0, ks, beta, bnorm, iters, m, maxiter, tol);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, k_ks_init, 1, 128, 0, ks, beta, bnorm, iters, m, maxiter, tol);
   return BCS_OK;
 }
 
 bcs_status ks_take_vj(Solver* s, const double* V, size_t ldv, const KrylovState* ks, void* out, bool to_float,
                       size_t N) {
   if (to_float)
-    BCS_LAUNCH(s, K_CAST, 12.0 * N, 0, k_ks_take_vj<float>, vgrid(N), 256, 0, V, ldv, ks, (float*)out, N);
+    BCS_LAUNCH_DEP(s, K_CAST, 12.0 * N, 0, k_ks_take_vj<float>, vgrid(N), 256, 0, V, ldv, ks, (float*)out, N);
   else
-    BCS_LAUNCH(s, K_BLAS, 16.0 * N, 0, k_ks_take_vj<double>, vgrid(N), 256, 0, V, ldv, ks, (double*)out, N);
+    BCS_LAUNCH_DEP(s, K_BLAS, 16.0 * N, 0, k_ks_take_vj<double>, vgrid(N), 256, 0, V, ldv, ks, (double*)out, N);
   return BCS_OK;
 }
 
 bcs_status ks_store_z(Solver* s, const void* zsrc, bool z_float, void* Z, const KrylovState* ks, double* widen,
                       size_t N) {
   if (z_float)
-    BCS_LAUNCH(s, K_CAST, (12.0 + (widen ? 8.0 : 0.0)) * N, 0, k_ks_store_z<float>, vgrid(N), 256, 0,
+    BCS_LAUNCH_DEP(s, K_CAST, (12.0 + (widen ? 8.0 : 0.0)) * N, 0, k_ks_store_z<float>, vgrid(N), 256, 0,
                (const float*)zsrc, (float*)Z, ks, widen, N);
   else
-    BCS_LAUNCH(s, K_BLAS, (16.0 + (widen ? 8.0 : 0.0)) * N, 0, k_ks_store_z<double>, vgrid(N), 256, 0,
+    BCS_LAUNCH_DEP(s, K_BLAS, (16.0 + (widen ? 8.0 : 0.0)) * N, 0, k_ks_store_z<double>, vgrid(N), 256, 0,
                (const double*)zsrc, (double*)Z, ks, widen, N);
   return BCS_OK;
 }
@@ -735,9 +764,9 @@ bcs_status ks_multidot(Solver* s, const double* V, size_t ldv, const KrylovState
   if (kmax > 72) return s->fail(BCS_EINVAL, "too many vectors in one multidot");
   BCS_ALLOC(s, s->red, (size_t)72 * RED_BLOCKS);
   const unsigned chunks = (unsigned)((kmax + MD_CHUNK - 1) / MD_CHUNK);
-  BCS_LAUNCH(s, K_BLAS, 8.0 * N * (kmax + 1), 2.0 * N * kmax, k_multidot_ks, dim3(RED_BLOCKS, chunks), RED_THREADS, 0,
+  BCS_LAUNCH_DEP(s, K_BLAS, 8.0 * N * (kmax + 1), 2.0 * N * kmax, k_multidot_ks, dim3(RED_BLOCKS, chunks), RED_THREADS, 0,
              V, ldv, ks, with_w ? 1 : 0, w, N, s->red.p);
-  BCS_LAUNCH(s, K_BLAS, 8.0 * kmax * RED_BLOCKS, 0, k_reduce_partials, kmax, RED_THREADS, 0, s->red.p,
+  BCS_LAUNCH_DEP(s, K_BLAS, 8.0 * kmax * RED_BLOCKS, 0, k_reduce_partials, kmax, RED_THREADS, 0, s->red.p,
              s->scal.p + slot, ks, with_w ? 1 : 0);
   return BCS_OK;
 }
@@ -746,38 +775,38 @@ bcs_status ks_gs_update(Solver* s, const double* V, size_t ldv, const KrylovStat
                         size_t N, int norm_slot) {
   const int kmax = s->cfg.restart;
   BCS_ALLOC(s, s->red, (size_t)72 * RED_BLOCKS);
-  BCS_LAUNCH(s, K_BLAS, 8.0 * N * (kmax + 2), 2.0 * N * kmax, k_gs_update_norm, RED_BLOCKS, RED_THREADS, 0, V, ldv, 0,
+  BCS_LAUNCH_DEP(s, K_BLAS, 8.0 * N * (kmax + 2), 2.0 * N * kmax, k_gs_update_norm, RED_BLOCKS, RED_THREADS, 0, V, ldv, 0,
              ks, hdev, w, N, norm_slot >= 0 ? s->red.p : nullptr);
   if (norm_slot >= 0)
-    BCS_LAUNCH(s, K_BLAS, 8.0 * RED_BLOCKS, 0, k_reduce_partials, 1, RED_THREADS, 0, s->red.p,
+    BCS_LAUNCH_DEP(s, K_BLAS, 8.0 * RED_BLOCKS, 0, k_reduce_partials, 1, RED_THREADS, 0, s->red.p,
                s->scal.p + norm_slot, (const KrylovState*)nullptr, 0);
   return BCS_OK;
 }
 
 bcs_status ks_givens(Solver* s, KrylovState* ks, int slot_a, int slot_b, int slot_n, cudaGraphConditionalHandle cond) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, k_ks_givens, 1, 32, 0, ks, (const double*)s->scal.p, slot_a, slot_b, slot_n, cond, 1);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, k_ks_givens, 1, 32, 0, ks, (const double*)s->scal.p, slot_a, slot_b, slot_n, cond, 1);
   return BCS_OK;
 }
 
 bcs_status ks_scale_next(Solver* s, const KrylovState* ks, const double* w, double* V, size_t ldv, size_t N) {
-  BCS_LAUNCH(s, K_BLAS, 16.0 * N, 1.0 * N, k_ks_scale_next, vgrid(N), 256, 0, ks, w, V, ldv, N);
+  BCS_LAUNCH_DEP(s, K_BLAS, 16.0 * N, 1.0 * N, k_ks_scale_next, vgrid(N), 256, 0, ks, w, V, ldv, N);
   return BCS_OK;
 }
 
 bcs_status ks_finish_cycle(Solver* s, KrylovState* ks, const void* Z, bool z_float, double* x, size_t N) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, k_ks_backsolve, 1, 32, 0, ks);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, k_ks_backsolve, 1, 32, 0, ks);
   const double k = s->cfg.restart;
   if (z_float)
-    BCS_LAUNCH(s, K_BLAS, (4.0 * k + 16.0) * N, 2.0 * N * k, k_ks_combine<float>, vgrid(N), 256, 0, (const float*)Z,
+    BCS_LAUNCH_DEP(s, K_BLAS, (4.0 * k + 16.0) * N, 2.0 * N * k, k_ks_combine<float>, vgrid(N), 256, 0, (const float*)Z,
                N, (const KrylovState*)ks, x, N);
   else
-    BCS_LAUNCH(s, K_BLAS, (8.0 * k + 16.0) * N, 2.0 * N * k, k_ks_combine<double>, vgrid(N), 256, 0,
+    BCS_LAUNCH_DEP(s, K_BLAS, (8.0 * k + 16.0) * N, 2.0 * N * k, k_ks_combine<double>, vgrid(N), 256, 0,
                (const double*)Z, N, (const KrylovState*)ks, x, N);
   return BCS_OK;
 }
 
 bcs_status ks_export(Solver* s, const KrylovState* ks, int slot) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, k_ks_export, 1, 32, 0, ks, s->scal.p + slot);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, k_ks_export, 1, 32, 0, ks, s->scal.p + slot);
   return BCS_OK;
 }
 
@@ -787,27 +816,27 @@ bcs_status add_combination(Solver* s, const void* Z, bool z_float, size_t ldz, i
   Coefs c{};
   for (int q = 0; q < k; ++q) c.c[q] = y[q];
   if (z_float)
-    BCS_LAUNCH(s, K_BLAS, (4.0 * k + 16.0) * N, 2.0 * N * k, k_add_combination<float>, vgrid(N), 256, 0,
+    BCS_LAUNCH_DEP(s, K_BLAS, (4.0 * k + 16.0) * N, 2.0 * N * k, k_add_combination<float>, vgrid(N), 256, 0,
                (const float*)Z, ldz, k, c, x, N);
   else
-    BCS_LAUNCH(s, K_BLAS, (8.0 * k + 16.0) * N, 2.0 * N * k, k_add_combination<double>, vgrid(N), 256, 0,
+    BCS_LAUNCH_DEP(s, K_BLAS, (8.0 * k + 16.0) * N, 2.0 * N * k, k_add_combination<double>, vgrid(N), 256, 0,
                (const double*)Z, ldz, k, c, x, N);
   return BCS_OK;
 }
 
 bcs_status axpby(Solver* s, double a, const double* x, double b, double* y, size_t N) {
-  BCS_LAUNCH(s, K_BLAS, 24.0 * N, 3.0 * N, k_axpby, vgrid(N), 256, 0, a, x, b, y, N);
+  BCS_LAUNCH_DEP(s, K_BLAS, 24.0 * N, 3.0 * N, k_axpby, vgrid(N), 256, 0, a, x, b, y, N);
   return BCS_OK;
 }
 
 bcs_status scale_copy(Solver* s, double a, const double* x, double* y, size_t N) {
-  BCS_LAUNCH(s, K_BLAS, 16.0 * N, 1.0 * N, k_scale, vgrid(N), 256, 0, a, x, y, N);
+  BCS_LAUNCH_DEP(s, K_BLAS, 16.0 * N, 1.0 * N, k_scale, vgrid(N), 256, 0, a, x, y, N);
   return BCS_OK;
 }
 
 bcs_status bicg_p_update(Solver* s, double beta, double omega, const double* r, const double* v, double* p,
                          size_t N) {
-  BCS_LAUNCH(s, K_BLAS, 32.0 * N, 4.0 * N, k_bicg_p, vgrid(N), 256, 0, beta, omega, r, v, p, N);
+  BCS_LAUNCH_DEP(s, K_BLAS, 32.0 * N, 4.0 * N, k_bicg_p, vgrid(N), 256, 0, beta, omega, r, v, p, N);
   return BCS_OK;
 }
 
@@ -873,51 +902,51 @@ bcs_status kb_gather_out(Solver* s, const BCase* cases, int count, double* out) 
 }
 
 bcs_status bs_init(Solver* s, BicgState* bs, int it, int maxiter, double tol, double bnorm, int first) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_init, 1, 32, 0, bs, it, maxiter, tol, bnorm, first);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, k_bs_init, 1, 32, 0, bs, it, maxiter, tol, bnorm, first);
   return BCS_OK;
 }
 bcs_status bs_rho(Solver* s, BicgState* bs) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_rho, 1, 32, 0, bs, (const double*)s->scal.p);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, k_bs_rho, 1, 32, 0, bs, (const double*)s->scal.p);
   return BCS_OK;
 }
 bcs_status bs_p_update(Solver* s, const BicgState* bs, const double* r, const double* v, double* p, size_t N) {
-  BCS_LAUNCH(s, K_BLAS, 32.0 * N, 4.0 * N, k_bs_p, vgrid(N), 256, 0, bs, r, v, p, N);
+  BCS_LAUNCH_DEP(s, K_BLAS, 32.0 * N, 4.0 * N, k_bs_p, vgrid(N), 256, 0, bs, r, v, p, N);
   return BCS_OK;
 }
 bcs_status bs_alpha(Solver* s, BicgState* bs) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_alpha, 1, 32, 0, bs, (const double*)s->scal.p);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, k_bs_alpha, 1, 32, 0, bs, (const double*)s->scal.p);
   return BCS_OK;
 }
 bcs_status bs_s_update(Solver* s, const BicgState* bs, const double* r, const double* v, double* sv, size_t N) {
-  BCS_LAUNCH(s, K_BLAS, 24.0 * N, 3.0 * N, k_bs_s, vgrid(N), 256, 0, bs, r, v, sv, N);
+  BCS_LAUNCH_DEP(s, K_BLAS, 24.0 * N, 3.0 * N, k_bs_s, vgrid(N), 256, 0, bs, r, v, sv, N);
   return BCS_OK;
 }
 bcs_status bs_snorm(Solver* s, BicgState* bs) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_snorm, 1, 32, 0, bs, (const double*)s->scal.p);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, k_bs_snorm, 1, 32, 0, bs, (const double*)s->scal.p);
   return BCS_OK;
 }
 bcs_status bs_omega(Solver* s, BicgState* bs) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_omega, 1, 32, 0, bs, (const double*)s->scal.p);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, k_bs_omega, 1, 32, 0, bs, (const double*)s->scal.p);
   return BCS_OK;
 }
 bcs_status bs_x_update(Solver* s, const BicgState* bs, const void* ph, bool z_float, double* x, size_t N) {
   if (z_float)
-    BCS_LAUNCH(s, K_BLAS, 24.0 * N, 4.0 * N, k_bs_x<float>, vgrid(N), 256, 0, bs, (const float*)ph, x, N);
+    BCS_LAUNCH_DEP(s, K_BLAS, 24.0 * N, 4.0 * N, k_bs_x<float>, vgrid(N), 256, 0, bs, (const float*)ph, x, N);
   else
-    BCS_LAUNCH(s, K_BLAS, 32.0 * N, 4.0 * N, k_bs_x<double>, vgrid(N), 256, 0, bs, (const double*)ph, x, N);
+    BCS_LAUNCH_DEP(s, K_BLAS, 32.0 * N, 4.0 * N, k_bs_x<double>, vgrid(N), 256, 0, bs, (const double*)ph, x, N);
   return BCS_OK;
 }
 bcs_status bs_r_update(Solver* s, const BicgState* bs, const double* sv, const double* t, double* r, size_t N) {
-  BCS_LAUNCH(s, K_BLAS, 24.0 * N, 3.0 * N, k_bs_r, vgrid(N), 256, 0, bs, sv, t, r, N);
+  BCS_LAUNCH_DEP(s, K_BLAS, 24.0 * N, 3.0 * N, k_bs_r, vgrid(N), 256, 0, bs, sv, t, r, N);
   return BCS_OK;
 }
 bcs_status bs_end(Solver* s, BicgState* bs, cudaGraphConditionalHandle cond) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_end, 1, 32, 0, bs, (const double*)s->scal.p, cond);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, k_bs_end, 1, 32, 0, bs, (const double*)s->scal.p, cond);
   return BCS_OK;
 }
 
 bcs_status bs_export(Solver* s, const BicgState* bs) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, k_bs_export, 1, 32, 0, bs, s->scal.p);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, k_bs_export, 1, 32, 0, bs, s->scal.p);
   return BCS_OK;
 }
 

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(128) k_rows(int rows, const int32_t* __restric
                                               const int32_t* __restrict__ ci, const TV* __restrict__ val,
                                               const TX* __restrict__ x, TY* __restrict__ y,
                                               const TY* __restrict__ b) {
+  dep_enter();
   RowMap<N> m(rows);
   if (!m.active) return;
   rows_eval<N, AT, TV, TX, TY, MODE>(m.i, m.r, rp, ci, val, x, y, b);
@@ -150,6 +151,7 @@ __global__ void __launch_bounds__(128) k_dilu_sweep(int cnt, int t0, const int32
                                                     const int32_t* __restrict__ dci, const TV* __restrict__ val,
                                                     const TD* __restrict__ einv, const TC* __restrict__ r,
                                                     TC* __restrict__ y, TC* __restrict__ d, TC* __restrict__ x) {
+  dep_enter();
   RowMap<N> m(cnt);
   const int t = t0 + (m.active ? m.i : 0);
   const int i = m.active ? __ldg(crow + t) : 0;
@@ -294,6 +296,7 @@ __global__ void __launch_bounds__(128) k_sell(int rows, int nslices, const int32
                                               const TV* __restrict__ sv, const float* __restrict__ dinv,
                                               const float* __restrict__ x, const float* __restrict__ b,
                                               float* __restrict__ y, float omega) {
+  dep_enter();
   const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (sl >= nslices) return;  // uniform across the warp
   sell_slice<N, TV, JACOBI, false>(sl, rows, rp, sptr, sci, sv, dinv, x, b, y, omega);
@@ -487,6 +490,7 @@ __global__ void __launch_bounds__(128, TPR_MINB) k_tpr(int rows, int nslices, co
                                              const int32_t* __restrict__ sci, const TV* __restrict__ sv,
                                              const float* __restrict__ dinv, const float* __restrict__ x,
                                              const float* __restrict__ b, float* __restrict__ y, float omega) {
+  dep_enter();
   const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (sl >= nslices) return;
   tpr_slice<N, TV, JACOBI>(sl, rows, rp, srow, sptr, sci, sv, dinv, x, b, y, omega);
@@ -498,6 +502,7 @@ __global__ void __launch_bounds__(128) k_jacobi(int rows, const int32_t* __restr
                                                 const int32_t* __restrict__ ci, const TV* __restrict__ val,
                                                 const TD* __restrict__ dinv, const TC* __restrict__ x,
                                                 const TC* __restrict__ b, TC* __restrict__ y, AT omega) {
+  dep_enter();
   RowMap<N> m(rows);
   AT res = 0;
   if (m.active) res = (AT)b[(size_t)m.i * N + m.r] - row_dot<N, AT>(rp, ci, val, x, m.i, m.r);
@@ -532,6 +537,7 @@ __device__ __forceinline__ void jacobi0_elem(size_t t, const TD* __restrict__ di
 template <int N, class AT, class TD, class TC>
 __global__ void k_jacobi0(int rows, const TD* __restrict__ dinv, const TC* __restrict__ b, TC* __restrict__ y,
                           AT omega) {
+  dep_enter();
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= (size_t)rows * N) return;
   jacobi0_elem<N, AT, TD, TC, false>(t, dinv, b, y, omega);
@@ -555,6 +561,7 @@ __device__ __forceinline__ void restrict_elem(size_t t, const int32_t* __restric
 template <int N, class AT, class TC>
 __global__ void k_restrict_tent(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
                                 const TC* __restrict__ r, TC* __restrict__ bc) {
+  dep_enter();
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= (size_t)nagg * N) return;
   restrict_elem<N, AT, TC, false>(t, mptr, mem, r, bc);
@@ -571,6 +578,7 @@ __device__ __forceinline__ void prolong_elem(size_t t, const int32_t* __restrict
 template <int N, class TC>
 __global__ void k_prolong_tent(int rows, const int32_t* __restrict__ agg, const TC* __restrict__ xc,
                                TC* __restrict__ x) {
+  dep_enter();
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= (size_t)rows * N) return;
   prolong_elem<N, TC, false>(t, agg, xc, x);
@@ -595,6 +603,7 @@ __device__ __forceinline__ void gemv_row(int row, int Nc, const double* __restri
 template <class TC>
 __global__ void k_coarse_gemv(int Nc, const double* __restrict__ inv, const TC* __restrict__ b,
                               TC* __restrict__ x) {
+  dep_enter();
   const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (row >= Nc) return;
   gemv_row<TC, false>(row, Nc, inv, b, x);
@@ -602,11 +611,13 @@ __global__ void k_coarse_gemv(int Nc, const double* __restrict__ inv, const TC* 
 
 template <class TI, class TO>
 __global__ void k_cast(size_t n, const TI* __restrict__ in, TO* __restrict__ out) {
+  dep_enter();
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
     out[t] = (TO)in[t];
 }
 
 __global__ void k_cast_bf16(size_t n, const double* __restrict__ in, bf16* __restrict__ out) {
+  dep_enter();
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
     out[t] = __double2bfloat16(in[t]);
 }
@@ -841,9 +852,9 @@ bcs_status cast_vec(Solver* s, const TI* in, TO* out, size_t N) {
   unsigned g = grid_for(N, 256);
   if (g > 148u * 16u) g = 148u * 16u;
   if constexpr (std::is_same<TO, bf16>::value) {
-    BCS_LAUNCH(s, K_CAST, (double)N * (sizeof(TI) + sizeof(TO)), 0, k_cast_bf16, g, 256, 0, N, in, out);
+    BCS_LAUNCH_DEP(s, K_CAST, (double)N * (sizeof(TI) + sizeof(TO)), 0, k_cast_bf16, g, 256, 0, N, in, out);
   } else {
-    BCS_LAUNCH(s, K_CAST, (double)N * (sizeof(TI) + sizeof(TO)), 0, (k_cast<TI, TO>), g, 256, 0, N, in, out);
+    BCS_LAUNCH_DEP(s, K_CAST, (double)N * (sizeof(TI) + sizeof(TO)), 0, (k_cast<TI, TO>), g, 256, 0, N, in, out);
   }
   return BCS_OK;
 }
@@ -869,17 +880,17 @@ bcs_status spmv64(Solver* s, const Bsr& A, const void* x, bool x_is_float, doubl
     const unsigned g = rows_grid(rows, N);
     if (x_is_float) {
       if (b)
-        BCS_LAUNCH(s, kind, bytes, flops, (k_rows<N, double, double, float, double, M_RESID>), g, 128, 0, rows,
+        BCS_LAUNCH_DEP(s, kind, bytes, flops, (k_rows<N, double, double, float, double, M_RESID>), g, 128, 0, rows,
                    A.rp.p, A.ci.p, A.v.p, (const float*)x, y, b);
       else
-        BCS_LAUNCH(s, kind, bytes, flops, (k_rows<N, double, double, float, double, M_SPMV>), g, 128, 0, rows,
+        BCS_LAUNCH_DEP(s, kind, bytes, flops, (k_rows<N, double, double, float, double, M_SPMV>), g, 128, 0, rows,
                    A.rp.p, A.ci.p, A.v.p, (const float*)x, y, b);
     } else {
       if (b)
-        BCS_LAUNCH(s, kind, bytes, flops, (k_rows<N, double, double, double, double, M_RESID>), g, 128, 0, rows,
+        BCS_LAUNCH_DEP(s, kind, bytes, flops, (k_rows<N, double, double, double, double, M_RESID>), g, 128, 0, rows,
                    A.rp.p, A.ci.p, A.v.p, (const double*)x, y, b);
       else
-        BCS_LAUNCH(s, kind, bytes, flops, (k_rows<N, double, double, double, double, M_SPMV>), g, 128, 0, rows,
+        BCS_LAUNCH_DEP(s, kind, bytes, flops, (k_rows<N, double, double, double, double, M_SPMV>), g, 128, 0, rows,
                    A.rp.p, A.ci.p, A.v.p, (const double*)x, y, b);
     }
     return BCS_OK;
@@ -904,7 +915,7 @@ struct Cycle {
   bcs_status sweep0(const Level& L, const TC* b, TC* y) {
     const int rows = L.A.rows;
     const AT om = (AT)s->setup_cfg.jacobi_omega;
-    BCS_LAUNCH(s, K_SWEEP, (double)rows * N * (N * sizeof(TD) + 2 * sizeof(TC)), 2.0 * rows * N * N,
+    BCS_LAUNCH_DEP(s, K_SWEEP, (double)rows * N * (N * sizeof(TD) + 2 * sizeof(TC)), 2.0 * rows * N * N,
                (k_jacobi0<N, AT, TD, TC>), grid_for((size_t)rows * N, 256), 256, 0, rows, dinv(L), b, y, om);
     return BCS_OK;
   }
@@ -916,16 +927,16 @@ struct Cycle {
                          (double)rows * N * (N * sizeof(TD) + 3 * sizeof(TC));
     if constexpr (std::is_same<TC, float>::value) {
       if (L.smap == 1)
-        BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_tpr<N, TV, true>),
+        BCS_LAUNCH_DEP(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_tpr<N, TV, true>),
                    grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.srow.p, L.sptr.p,
                    L.sci.p,
                    smat(L), dinv(L), x, b, y, om);
       else
-        BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_sell<N, TV, true>),
+        BCS_LAUNCH_DEP(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_sell<N, TV, true>),
                    grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.sptr.p, L.sci.p,
                    smat(L), dinv(L), x, b, y, om);
     } else {
-      BCS_LAUNCH(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_jacobi<N, AT, TV, TD, TC>),
+      BCS_LAUNCH_DEP(s, K_SWEEP, bytes, 2.0 * (L.A.nnz + rows) * N * N, (k_jacobi<N, AT, TV, TD, TC>),
                  rows_grid(rows, N), 128, 0, rows, L.A.rp.p, L.A.ci.p, mat(L), dinv(L), x, b, y, om);
     }
     return BCS_OK;
@@ -937,16 +948,16 @@ struct Cycle {
                          (double)rows * N * 3 * sizeof(TC);
     if constexpr (std::is_same<TC, float>::value) {
       if (L.smap == 1)
-        BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_tpr<N, TV, false>),
+        BCS_LAUNCH_DEP(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_tpr<N, TV, false>),
                    grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.srow.p, L.sptr.p,
                    L.sci.p,
                    smat(L), (const float*)nullptr, x, b, r, 0.f);
       else
-        BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_sell<N, TV, false>),
+        BCS_LAUNCH_DEP(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_sell<N, TV, false>),
                    grid_for((size_t)L.nslices * 32, 128), 128, 0, rows, L.nslices, L.A.rp.p, L.sptr.p, L.sci.p,
                    smat(L), (const float*)nullptr, x, b, r, 0.f);
     } else {
-      BCS_LAUNCH(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_rows<N, AT, TV, TC, TC, M_RESID>),
+      BCS_LAUNCH_DEP(s, K_RESID, bytes, 2.0 * L.A.nnz * N * N, (k_rows<N, AT, TV, TC, TC, M_RESID>),
                  rows_grid(rows, N), 128, 0, rows, L.A.rp.p, L.A.ci.p, mat(L), x, r, b);
     }
     return BCS_OK;
@@ -997,14 +1008,14 @@ struct Cycle {
     for (int c = 0; c < L.ncol; ++c) {
       const int b0 = L.cstart[c], m = L.cstart[c + 1] - b0;
       if (m > 0)
-        BCS_LAUNCH(s, K_SWEEP, per_row * m, 2.0 * m * N * N, (k_dilu_sweep<N, AT, TV, TD, TC, true, G>),
+        BCS_LAUNCH_DEP(s, K_SWEEP, per_row * m, 2.0 * m * N * N, (k_dilu_sweep<N, AT, TV, TD, TC, true, G>),
                    rows_grid(m, N), 128, 0, m, b0, L.crow.p, L.dptr.p, L.dmid.p, L.dsrc.p, L.dci.p, dmat(L),
                    deinv(L), r, y, d, x);
     }
     for (int c = L.ncol - 1; c >= 0; --c) {
       const int b0 = L.cstart[c], m = L.cstart[c + 1] - b0;
       if (m > 0)
-        BCS_LAUNCH(s, K_SWEEP, per_row * m, 2.0 * m * N * N, (k_dilu_sweep<N, AT, TV, TD, TC, false, G>),
+        BCS_LAUNCH_DEP(s, K_SWEEP, per_row * m, 2.0 * m * N * N, (k_dilu_sweep<N, AT, TV, TD, TC, false, G>),
                    rows_grid(m, N), 128, 0, m, b0, L.crow.p, L.dptr.p, L.dmid.p, L.dsrc.p, L.dci.p, dmat(L),
                    deinv(L), r, y, d, x);
     }
@@ -1014,12 +1025,12 @@ struct Cycle {
   template <int N>
   bcs_status restrict_(const Level& L, const TC* r, TC* bc) {
     if (s->setup_cfg.pmode == BCS_P_TENTATIVE) {
-      BCS_LAUNCH(s, K_TRANSFER, (double)(L.A.rows + L.nagg) * N * sizeof(TC) + 4.0 * L.A.rows, 0,
+      BCS_LAUNCH_DEP(s, K_TRANSFER, (double)(L.A.rows + L.nagg) * N * sizeof(TC) + 4.0 * L.A.rows, 0,
                  (k_restrict_tent<N, AT, TC>), grid_for((size_t)L.nagg * N, 256), 256, 0, L.nagg, L.mptr.p,
                  L.mem.p, r, bc);
     } else {
       const Bsr& R = L.R;
-      BCS_LAUNCH(s, K_TRANSFER, (double)R.nnz * (N * N * sizeof(TV) + 4), 2.0 * R.nnz * N * N,
+      BCS_LAUNCH_DEP(s, K_TRANSFER, (double)R.nnz * (N * N * sizeof(TV) + 4), 2.0 * R.nnz * N * N,
                  (k_rows<N, AT, TV, TC, TC, M_SPMV>), rows_grid(R.rows, N), 128, 0, R.rows, R.rp.p, R.ci.p,
                  rmat(L), r, bc, (const TC*)nullptr);
     }
@@ -1028,11 +1039,11 @@ struct Cycle {
   template <int N>
   bcs_status prolong(const Level& L, const TC* xc, TC* x) {
     if (s->setup_cfg.pmode == BCS_P_TENTATIVE) {
-      BCS_LAUNCH(s, K_TRANSFER, (double)L.A.rows * N * 3 * sizeof(TC) + 4.0 * L.A.rows, 0,
+      BCS_LAUNCH_DEP(s, K_TRANSFER, (double)L.A.rows * N * 3 * sizeof(TC) + 4.0 * L.A.rows, 0,
                  (k_prolong_tent<N, TC>), grid_for((size_t)L.A.rows * N, 256), 256, 0, L.A.rows, L.agg.p, xc, x);
     } else {
       const Bsr& P = L.P;
-      BCS_LAUNCH(s, K_TRANSFER, (double)P.nnz * (N * N * sizeof(TV) + 4), 2.0 * P.nnz * N * N,
+      BCS_LAUNCH_DEP(s, K_TRANSFER, (double)P.nnz * (N * N * sizeof(TV) + 4), 2.0 * P.nnz * N * N,
                  (k_rows<N, AT, TV, TC, TC, M_ADD>), rows_grid(P.rows, N), 128, 0, P.rows, P.rp.p, P.ci.p,
                  pmat(L), xc, x, (const TC*)nullptr);
     }
@@ -1063,7 +1074,7 @@ struct Cycle {
       BCS_CU(s, cudaMemsetAsync(x, 0, (size_t)rows * N * sizeof(TC), s->stream));
       return dilu_step<N>(L, x, b);
     }
-    BCS_LAUNCH(s, K_SWEEP, (double)rows * N * (N * sizeof(TD) + 2 * sizeof(TC)), 2.0 * rows * N * N,
+    BCS_LAUNCH_DEP(s, K_SWEEP, (double)rows * N * (N * sizeof(TD) + 2 * sizeof(TC)), 2.0 * rows * N * N,
                (k_jacobi0<N, AT, TD, TC>), grid_for((size_t)rows * N, 256), 256, 0, rows, dinv(L), b, x, (AT)1);
     return BCS_OK;
   }
@@ -1101,7 +1112,7 @@ struct Cycle {
     const int nu1 = s->setup_cfg.nu1, nu2 = s->setup_cfg.nu2;
     TC* tmp = (TC*)L.vt.p;
     if (L.coarse_kind == 0) {
-      BCS_LAUNCH(s, K_COARSE, 8.0 * s->cN * s->cN, 2.0 * s->cN * s->cN, k_coarse_gemv<TC>,
+      BCS_LAUNCH_DEP(s, K_COARSE, 8.0 * s->cN * s->cN, 2.0 * s->cN * s->cN, k_coarse_gemv<TC>,
                  grid_for((size_t)s->cN * 32, 256), 256, 0, s->cN, s->cinv.p, b, x);
       return BCS_OK;
     }

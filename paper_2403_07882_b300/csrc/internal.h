@@ -391,6 +391,38 @@ struct LevelScope {
       return (S)->fail(BCS_ENOMEM, std::string("device allocation failed: ") + #buf);   \
   } while (0)
 
+// Programmatic dependent launch (sm_90 and later). A kernel launched with
+// BCS_LAUNCH_DEP may be scheduled while its predecessor in the stream is
+// still finishing; it calls dep_enter() first, which waits for that grid to
+// complete with its memory visible before the kernel reads or writes any
+// data, then lets the kernel's own successor begin launching. Launched
+// without the attribute, both instructions return at once.
+__device__ __forceinline__ void dep_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// BCS_LAUNCH with the programmatic-serialization attribute (when
+// cfg.dependent_launch is set); the kernel must begin with dep_enter().
+#define BCS_LAUNCH_DEP(S, KIND, BYTES, FLOPS, kernel, grid, block, smem, ...)                       \
+  do {                                                                                              \
+    (S)->pre(KIND);                                                                                 \
+    cudaLaunchConfig_t lc_{};                                                                       \
+    cudaLaunchAttribute at_[1];                                                                     \
+    at_[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;                                 \
+    at_[0].val.programmaticStreamSerializationAllowed = 1;                                          \
+    lc_.gridDim = dim3(grid);                                                                       \
+    lc_.blockDim = dim3(block);                                                                     \
+    lc_.dynamicSmemBytes = (smem);                                                                  \
+    lc_.stream = (S)->stream;                                                                       \
+    lc_.attrs = at_;                                                                                \
+    lc_.numAttrs = (S)->cfg.dependent_launch ? 1 : 0;                                               \
+    const cudaError_t le_ = cudaLaunchKernelEx(&lc_, kernel, __VA_ARGS__);                          \
+    if (le_ != cudaSuccess) return (S)->fail(BCS_ECUDA, std::string(#kernel) + ": " + cudaGetErrorString(le_)); \
+    bcs_status st_ = (S)->post(KIND, #kernel, (BYTES), (FLOPS));                                    \
+    if (st_ != BCS_OK) return st_;                                                                  \
+  } while (0)
+
 // Launch kernel<<<grid, block, smem, s->stream>>>(args...) with bookkeeping.
 #define BCS_LAUNCH(S, KIND, BYTES, FLOPS, kernel, grid, block, smem, ...)  \
   do {                                                                    \

@@ -188,3 +188,21 @@ def test_coarse_smoother_sweeps_solve(solver, precision):
     assert true_rel(ref, system["b"], x) <= 1e-8
     if precision == bcs.BCS_PREC_FP64:
         assert abs(res["iters"] - ores["iters"]) <= 1, (res["iters"], ores["iters"])
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(precision=bcs.BCS_PREC_FP64), dict(precision=bcs.BCS_PREC_BF16),
+                                dict(smoother=bcs.BCS_SMOOTH_DILU), dict(solver=bcs.BCS_BICGSTAB),
+                                dict(pmode=bcs.BCS_P_SMOOTHED), dict(cycle_graph=0)],
+                         ids=["fp32", "fp64", "bf16", "dilu", "bicgstab", "smoothed-P", "no-graph"])
+def test_dependent_launch_identical(kw):
+    """The V-cycle's kernels as programmatic dependent launches (each may be
+    scheduled while its predecessor finishes and waits for its results):
+    the same solve, bit for bit, as with ordinary launches."""
+    system = synth.pressure(14, seed=3)
+    out = []
+    for dep in (0, 1):
+        x, st, res = gpu_solve(system, dependent_launch=dep, **kw)
+        assert st == bcs.BCS_OK, res
+        out.append((x, res["iters"]))
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
