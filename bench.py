@@ -189,6 +189,17 @@ def kernel_source_digest(path, func):
     return hashlib.sha256("\n".join(lines[start:end + 1]).encode()).hexdigest()
 
 
+def entry_digest(e):
+    """Digest of a profiles/traffic.json entry's kernel: its device-function
+    body ("function") and, when named, the __global__ wrapper that launches
+    it ("wrapper"), concatenated."""
+    d = kernel_source_digest(os.path.join(ROOT, e["source"]), e["function"])
+    if e.get("wrapper"):
+        import hashlib
+        d = hashlib.sha256((d + kernel_source_digest(os.path.join(ROOT, e["source"]), e["wrapper"])).encode()).hexdigest()
+    return d
+
+
 def measured_traffic(kernel, bytes_per_launch):
     """DRAM bytes per launch of `kernel`, from the committed ncu summary
     (profiles/traffic.json: DRAM bytes over algorithmic bytes of a captured
@@ -198,7 +209,7 @@ def measured_traffic(kernel, bytes_per_launch):
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             entries = json.load(f)
         e = entries[kernel]
-        if kernel_source_digest(os.path.join(ROOT, e["source"]), e["function"]) != e["sha256"]:
+        if entry_digest(e) != e["sha256"]:
             return None
     except (OSError, ValueError, KeyError, StopIteration):
         return None

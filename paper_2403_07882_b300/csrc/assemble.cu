@@ -38,6 +38,7 @@ constexpr int AS_NN = 25;
 // the cells are renumbered); flag bit 1 for rho <= 0 or p <= 0 (or NaN)
 __global__ void k_cell_prims(int C, const double* __restrict__ Q, const int32_t* __restrict__ perm, double gamma,
                              double* __restrict__ prim, int32_t* __restrict__ flag) {
+  dep_enter();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   const double* q = Q + (size_t)(perm ? perm[c] : c) * 5;
@@ -101,6 +102,7 @@ __global__ void k_face_lambda(int F, const int32_t* __restrict__ pos_up, const i
                               const double* __restrict__ normal, const double* __restrict__ area,
                               const double* __restrict__ dist, double gamma, double visc, double* __restrict__ lam,
                               int32_t* __restrict__ flag) {
+  dep_enter();
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= F) return;
   const double* a = prim + (size_t)__ldg(ci + __ldg(pos_lo + f)) * 5;
@@ -133,6 +135,7 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assemble_cells(
     const double* __restrict__ area, const double* __restrict__ normal, const double* __restrict__ lam, double gamma,
     double inv_cfl, double* __restrict__ diag, double* __restrict__ upper, double* __restrict__ lower,
     double* __restrict__ val) {
+  dep_enter();
   __shared__ double stage_s[AS_WARPS][32 * AS_NN];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* stage = stage_s[warp];
@@ -216,21 +219,21 @@ bcs_status assemble_density(Solver* s, const double* Q, const double* area, cons
   BCS_ALLOC(s, prim, (size_t)C * 5);
   BCS_CU(s, cudaMemsetAsync(s->flag.p, 0, sizeof(int32_t), s->stream));
   const double visc = (prm.gamma > 4.0 / 3.0 ? prm.gamma : 4.0 / 3.0) * prm.mu / prm.prandtl;
-  BCS_LAUNCH(s, K_ASSEMBLE, 80.0 * C, 0, k_cell_prims, grid_for(C, 256), 256, 0, C, Q,
+  BCS_LAUNCH_DEP(s, K_ASSEMBLE, 80.0 * C, 0, k_cell_prims, grid_for(C, 256), 256, 0, C, Q,
              s->reordered ? (const int32_t*)s->perm.p : nullptr, prm.gamma, prim.p, s->flag.p);
   if (F > 0)
-    BCS_LAUNCH(s, K_ASSEMBLE, 104.0 * F, 0, k_face_lambda, grid_for(F, 256), 256, 0, F, s->pos_up.p, s->pos_lo.p,
+    BCS_LAUNCH_DEP(s, K_ASSEMBLE, 104.0 * F, 0, k_face_lambda, grid_for(F, 256), 256, 0, F, s->pos_up.p, s->pos_lo.p,
                A.ci.p, prim.p, normal, area, dist, prm.gamma, visc, lam.p, s->flag.p);
   // prim, per face side area + normal + lambda + LDU code, blocks written
   const double bytes = 40.0 * C + 44.0 * 2 * F + 200.0 * (C + 2.0 * F);
   const double flops = 2 * F * 55.0 + C * 60.0;
   const unsigned grid = grid_for(C, AS_WARPS * 32);
   if (bsr)
-    BCS_LAUNCH(s, K_ASSEMBLE, bytes, flops, k_assemble_cells<true>, grid, AS_WARPS * 32, 0, C, A.rp.p, s->src.p,
+    BCS_LAUNCH_DEP(s, K_ASSEMBLE, bytes, flops, k_assemble_cells<true>, grid, AS_WARPS * 32, 0, C, A.rp.p, s->src.p,
                s->pos_up.p, s->pos_lo.p, prim.p, area, normal, lam.p, prm.gamma, 1.0 / prm.cfl,
                nullptr, nullptr, nullptr, s->lv[0].A.v.p);
   else
-    BCS_LAUNCH(s, K_ASSEMBLE, bytes, flops, k_assemble_cells<false>, grid, AS_WARPS * 32, 0, C, A.rp.p, s->src.p,
+    BCS_LAUNCH_DEP(s, K_ASSEMBLE, bytes, flops, k_assemble_cells<false>, grid, AS_WARPS * 32, 0, C, A.rp.p, s->src.p,
                s->pos_up.p, s->pos_lo.p, prim.p, area, normal, lam.p, prm.gamma, 1.0 / prm.cfl, diag,
                upper, lower, nullptr);
   int32_t h = 0;

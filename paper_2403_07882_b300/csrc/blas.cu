@@ -367,11 +367,13 @@ __global__ void k_ks_export(const KrylovState* __restrict__ ks, double* __restri
 // kb_step_begin); the finishing kernels serve the cases of the current
 // restart round.
 __global__ void kb_step_begin_k(const BCase* __restrict__ cases, int count) {
+  dep_enter();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < count) *cases[c].live = cases[c].ks->stop == KS_RUN;
 }
 
 __global__ void kb_take_vj_k(const BCase* __restrict__ cases) {
+  dep_enter();
   const BCase& c = cases[blockIdx.z];
   if (!*c.live) return;
   const double* v = c.V + (size_t)c.ks->j * c.N;
@@ -381,6 +383,7 @@ __global__ void kb_take_vj_k(const BCase* __restrict__ cases) {
 }
 
 __global__ void kb_store_z_k(const BCase* __restrict__ cases) {
+  dep_enter();
   const BCase& c = cases[blockIdx.z];
   if (!*c.live) return;
   const float* z = c.lv[0].vx;
@@ -393,6 +396,7 @@ __global__ void kb_store_z_k(const BCase* __restrict__ cases) {
 }
 
 __global__ void __launch_bounds__(RED_THREADS) kb_multidot_k(const BCase* __restrict__ cases, int with_w) {
+  dep_enter();
   const BCase& c = cases[blockIdx.z];
   if (!*c.live) return;
   const int nv = c.ks->j + 1, k = nv + with_w;
@@ -414,6 +418,7 @@ __global__ void __launch_bounds__(RED_THREADS) kb_multidot_k(const BCase* __rest
 // to scal[slot + q]; the case takes part when live (per_step) or in the round
 __global__ void __launch_bounds__(RED_THREADS) kb_reduce_k(const BCase* __restrict__ cases, int slot, int extra,
                                                           int per_step) {
+  dep_enter();
   const BCase& c = cases[blockIdx.z];
   if (per_step ? !*c.live : !*c.round) return;
   const int q = blockIdx.x;
@@ -434,6 +439,7 @@ __global__ void __launch_bounds__(RED_THREADS) kb_reduce_k(const BCase* __restri
 }
 
 __global__ void __launch_bounds__(RED_THREADS) kb_gs_update_k(const BCase* __restrict__ cases, int hslot, int norm) {
+  dep_enter();
   const BCase& c = cases[blockIdx.z];
   if (!*c.live) return;
   const int k = c.ks->j + 1;
@@ -463,6 +469,7 @@ __global__ void __launch_bounds__(RED_THREADS) kb_gs_update_k(const BCase* __res
 // Givens update and stop test of every live case; the loop continues while
 // one of them still runs.
 __global__ void kb_givens_k(const BCase* __restrict__ cases, int count, cudaGraphConditionalHandle cond) {
+  dep_enter();
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
@@ -476,6 +483,7 @@ __global__ void kb_givens_k(const BCase* __restrict__ cases, int count, cudaGrap
 }
 
 __global__ void kb_scale_next_k(const BCase* __restrict__ cases) {
+  dep_enter();
   const BCase& c = cases[blockIdx.z];
   if (!*c.live) return;
   const int stop = c.ks->stop;
@@ -488,6 +496,7 @@ __global__ void kb_scale_next_k(const BCase* __restrict__ cases) {
 
 // back substitution (one thread per case), then x += Z y
 __global__ void kb_backsolve_k(const BCase* __restrict__ cases, int count) {
+  dep_enter();
   const int ci = blockIdx.x * blockDim.x + threadIdx.x;
   if (ci >= count || !*cases[ci].round) return;
   KrylovState* ks = cases[ci].ks;
@@ -502,6 +511,7 @@ __global__ void kb_backsolve_k(const BCase* __restrict__ cases, int count) {
 }
 
 __global__ void kb_combine_k(const BCase* __restrict__ cases) {
+  dep_enter();
   const BCase& c = cases[blockIdx.z];
   if (!*c.round) return;
   const int k = c.ks->stop == KS_BREAKDOWN ? 0 : c.ks->jend;
@@ -515,6 +525,7 @@ __global__ void kb_combine_k(const BCase* __restrict__ cases) {
 
 // partials of ||r||^2 (k_multidot<1>'s order and tree) and the cycle outcome
 __global__ void __launch_bounds__(RED_THREADS) kb_norm_r_k(const BCase* __restrict__ cases) {
+  dep_enter();
   const BCase& c = cases[blockIdx.z];
   if (!*c.round) return;
   multidot_body<1>(c.r, c.N, 1 << 30, 0, c.r, c.N, c.red);
@@ -527,6 +538,7 @@ __global__ void __launch_bounds__(RED_THREADS) kb_norm_r_k(const BCase* __restri
 
 // every case's ||r||^2 and cycle outcome into one array (one read for all)
 __global__ void kb_gather_out_k(const BCase* __restrict__ cases, int count, double* __restrict__ out) {
+  dep_enter();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= count) return;
   const double* sc = cases[c].scal;
@@ -846,58 +858,58 @@ bcs_status bicg_p_update(Solver* s, double beta, double omega, const double* r, 
 unsigned bgrid(size_t maxN) { return vgrid(maxN); }
 
 bcs_status kb_step_begin(Solver* s, const BCase* cases, int count) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_step_begin_k, grid_for(count, 64), 64, 0, cases, count);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, kb_step_begin_k, grid_for(count, 64), 64, 0, cases, count);
   return BCS_OK;
 }
 
 bcs_status kb_take_vj(Solver* s, const BCase* cases, int count, size_t maxN) {
-  BCS_LAUNCH(s, K_CAST, 12.0 * maxN * count, 0, kb_take_vj_k, dim3(bgrid(maxN), 1, count), 256, 0, cases);
+  BCS_LAUNCH_DEP(s, K_CAST, 12.0 * maxN * count, 0, kb_take_vj_k, dim3(bgrid(maxN), 1, count), 256, 0, cases);
   return BCS_OK;
 }
 
 bcs_status kb_store_z(Solver* s, const BCase* cases, int count, size_t maxN) {
-  BCS_LAUNCH(s, K_CAST, 16.0 * maxN * count, 0, kb_store_z_k, dim3(bgrid(maxN), 1, count), 256, 0, cases);
+  BCS_LAUNCH_DEP(s, K_CAST, 16.0 * maxN * count, 0, kb_store_z_k, dim3(bgrid(maxN), 1, count), 256, 0, cases);
   return BCS_OK;
 }
 
 bcs_status kb_multidot(Solver* s, const BCase* cases, int count, bool with_w, int kmax, int slot) {
   const unsigned chunks = (unsigned)((kmax + MD_CHUNK - 1) / MD_CHUNK);
-  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_multidot_k, dim3(RED_BLOCKS, chunks, count), RED_THREADS, 0, cases, with_w ? 1 : 0);
-  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_reduce_k, dim3(kmax, 1, count), RED_THREADS, 0, cases, slot, with_w ? 1 : 0, 1);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, kb_multidot_k, dim3(RED_BLOCKS, chunks, count), RED_THREADS, 0, cases, with_w ? 1 : 0);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, kb_reduce_k, dim3(kmax, 1, count), RED_THREADS, 0, cases, slot, with_w ? 1 : 0, 1);
   return BCS_OK;
 }
 
 bcs_status kb_gs_update(Solver* s, const BCase* cases, int count, int hslot, int nslot) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_gs_update_k, dim3(RED_BLOCKS, 1, count), RED_THREADS, 0, cases, hslot,
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, kb_gs_update_k, dim3(RED_BLOCKS, 1, count), RED_THREADS, 0, cases, hslot,
              nslot >= 0 ? 1 : 0);
-  if (nslot >= 0) BCS_LAUNCH(s, K_BLAS, 0, 0, kb_reduce_k, dim3(1, 1, count), RED_THREADS, 0, cases, nslot, 0, 1);
+  if (nslot >= 0) BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, kb_reduce_k, dim3(1, 1, count), RED_THREADS, 0, cases, nslot, 0, 1);
   return BCS_OK;
 }
 
 bcs_status kb_givens(Solver* s, const BCase* cases, int count, cudaGraphConditionalHandle cond) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_givens_k, 1, 64, 0, cases, count, cond);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, kb_givens_k, 1, 64, 0, cases, count, cond);
   return BCS_OK;
 }
 
 bcs_status kb_scale_next(Solver* s, const BCase* cases, int count, size_t maxN) {
-  BCS_LAUNCH(s, K_BLAS, 16.0 * maxN * count, 0, kb_scale_next_k, dim3(bgrid(maxN), 1, count), 256, 0, cases);
+  BCS_LAUNCH_DEP(s, K_BLAS, 16.0 * maxN * count, 0, kb_scale_next_k, dim3(bgrid(maxN), 1, count), 256, 0, cases);
   return BCS_OK;
 }
 
 bcs_status kb_finish(Solver* s, const BCase* cases, int count, size_t maxN) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_backsolve_k, grid_for(count, 32), 32, 0, cases, count);
-  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_combine_k, dim3(bgrid(maxN), 1, count), 256, 0, cases);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, kb_backsolve_k, grid_for(count, 32), 32, 0, cases, count);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, kb_combine_k, dim3(bgrid(maxN), 1, count), 256, 0, cases);
   return BCS_OK;
 }
 
 bcs_status kb_norm_r(Solver* s, const BCase* cases, int count) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_norm_r_k, dim3(RED_BLOCKS, 1, count), RED_THREADS, 0, cases);
-  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_reduce_k, dim3(1, 1, count), RED_THREADS, 0, cases, SLOT_N, 0, 0);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, kb_norm_r_k, dim3(RED_BLOCKS, 1, count), RED_THREADS, 0, cases);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, kb_reduce_k, dim3(1, 1, count), RED_THREADS, 0, cases, SLOT_N, 0, 0);
   return BCS_OK;
 }
 
 bcs_status kb_gather_out(Solver* s, const BCase* cases, int count, double* out) {
-  BCS_LAUNCH(s, K_BLAS, 0, 0, kb_gather_out_k, grid_for(count, 64), 64, 0, cases, count, out);
+  BCS_LAUNCH_DEP(s, K_BLAS, 0, 0, kb_gather_out_k, grid_for(count, 64), 64, 0, cases, count, out);
   return BCS_OK;
 }
 

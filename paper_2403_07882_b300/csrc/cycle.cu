@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(128) k_dilu_sweep(int cnt, int t0, const int32
 // of its row's x block and the row's lanes exchange them by shuffle.
 __global__ void k_slice_len(int rows, int rpw, int nslices, const int32_t* __restrict__ rp,
                             const int32_t* __restrict__ order, int32_t* __restrict__ slen) {
+  dep_enter();
   const int sl = blockIdx.x * blockDim.x + threadIdx.x;
   if (sl >= nslices) return;
   int m = 0;
@@ -189,6 +190,7 @@ template <int N, class TV>
 __global__ void k_slice_fill(int rows, int nslices, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                              const double* __restrict__ val, const int32_t* __restrict__ sptr, int32_t* __restrict__ sci,
                              TV* __restrict__ sv) {
+  dep_enter();
   constexpr int NN = N * N, RPW = 32 / N, TILE = NN * RPW;
   const int lane = threadIdx.x & 31;
   const int w = lane / N, r = lane - w * N;
@@ -367,6 +369,7 @@ constexpr int SORT_WIN = 256;
 
 __global__ void __launch_bounds__(SORT_WIN) k_window_order(int rows, const int32_t* __restrict__ rp,
                                                           int32_t* __restrict__ srow) {
+  dep_enter();
   __shared__ int len[SORT_WIN];
   const int w0 = blockIdx.x * SORT_WIN, i = w0 + threadIdx.x;
   const int cnt = min(SORT_WIN, rows - w0);
@@ -386,6 +389,7 @@ template <int N, class TV>
 __global__ void k_tpr_fill(int rows, int nslices, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const double* __restrict__ val, const int32_t* __restrict__ srow,
                            const int32_t* __restrict__ sptr, int32_t* __restrict__ sci, TV* __restrict__ sv) {
+  dep_enter();
   constexpr int NN = N * N;
   using T = TprTile<NN, TV>;
   const int lane = threadIdx.x & 31;
@@ -647,6 +651,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail(const TailPhase* __restri
                                                       const TailLevel* __restrict__ lvl, float* const* __restrict__ vec,
                                                       const float* root_b, float* root_x, const double* __restrict__ cinv,
                                                       int cN, float omega) {
+  dep_enter();
   cg::cluster_group cl = cg::this_cluster();
   const int nthr = (int)(cl.num_blocks() * blockDim.x);
   const int g = (int)(cl.block_rank() * blockDim.x + threadIdx.x);
@@ -715,6 +720,7 @@ struct DiluClusterArgs {
 
 template <int N, class TV, bool RESID>
 __global__ void __launch_bounds__(DC_THREADS) k_dilu_cluster(const DiluClusterArgs A) {
+  dep_enter();
   cg::cluster_group cl = cg::this_cluster();
   const int g = (int)(cl.block_rank() * blockDim.x + threadIdx.x);
   const int gw = g >> 5, nw = (int)(cl.num_blocks() * blockDim.x) >> 5;
@@ -771,6 +777,7 @@ __device__ __forceinline__ float* b_vec(const BLevel& L, int role) {
 template <int N, class TV, bool JACOBI>
 __global__ void __launch_bounds__(128) kb_sweep_k(const BCase* __restrict__ cases, int level, int coarse, int ix,
                                                   int iy, float omega) {
+  dep_enter();
   const BLevel* L = b_level(cases[blockIdx.z], level, coarse);
   if (!L) return;
   const int sl = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
@@ -787,6 +794,7 @@ __global__ void __launch_bounds__(128) kb_sweep_k(const BCase* __restrict__ case
 
 template <int N>
 __global__ void kb_jac0_k(const BCase* __restrict__ cases, int level, int coarse, int iy, float omega) {
+  dep_enter();
   const BLevel* L = b_level(cases[blockIdx.z], level, coarse);
   if (!L) return;
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -795,6 +803,7 @@ __global__ void kb_jac0_k(const BCase* __restrict__ cases, int level, int coarse
 
 template <int N>
 __global__ void kb_zero_k(const BCase* __restrict__ cases, int level, int iy) {
+  dep_enter();
   const BLevel* L = b_level(cases[blockIdx.z], level, 0);
   if (!L) return;
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -803,6 +812,7 @@ __global__ void kb_zero_k(const BCase* __restrict__ cases, int level, int iy) {
 
 template <int N>
 __global__ void kb_restrict_k(const BCase* __restrict__ cases, int level) {
+  dep_enter();
   const BCase& c = cases[blockIdx.z];
   const BLevel* L = b_level(c, level, 0);
   if (!L) return;
@@ -812,6 +822,7 @@ __global__ void kb_restrict_k(const BCase* __restrict__ cases, int level) {
 
 template <int N>
 __global__ void kb_prolong_k(const BCase* __restrict__ cases, int level, int iy) {
+  dep_enter();
   const BCase& c = cases[blockIdx.z];
   const BLevel* L = b_level(c, level, 0);
   if (!L) return;
@@ -820,6 +831,7 @@ __global__ void kb_prolong_k(const BCase* __restrict__ cases, int level, int iy)
 }
 
 __global__ void kb_gemv_k(const BCase* __restrict__ cases) {
+  dep_enter();
   const BCase& c = cases[blockIdx.z];
   if (!*c.live) return;
   const BLevel& L = c.lv[c.n_levels - 1];
@@ -831,6 +843,7 @@ __global__ void kb_gemv_k(const BCase* __restrict__ cases) {
 // w = A kt (live cases) / r = b - A x (cases of the round), FP64
 template <int N>
 __global__ void __launch_bounds__(128) kb_spmv_w_k(const BCase* __restrict__ cases) {
+  dep_enter();
   const BCase& c = cases[blockIdx.z];
   if (!*c.live) return;
   RowMap<N> m(c.rows);
@@ -839,6 +852,7 @@ __global__ void __launch_bounds__(128) kb_spmv_w_k(const BCase* __restrict__ cas
 
 template <int N>
 __global__ void __launch_bounds__(128) kb_resid_r_k(const BCase* __restrict__ cases) {
+  dep_enter();
   const BCase& c = cases[blockIdx.z];
   if (!*c.round) return;
   RowMap<N> m(c.rows);
@@ -1212,9 +1226,9 @@ bcs_status layout_structure(Solver* s, Level& L, int map, int32_t* steps_dev, bo
   BCS_ALLOC(s, L.sptr, ns + 1);
   if (map == 1) {
     BCS_ALLOC(s, L.srow, rows);
-    BCS_LAUNCH(s, K_CAST, 0, 0, k_window_order, grid_for(rows, SORT_WIN), SORT_WIN, 0, rows, L.A.rp.p, L.srow.p);
+    BCS_LAUNCH_DEP(s, K_CAST, 0, 0, k_window_order, grid_for(rows, SORT_WIN), SORT_WIN, 0, rows, L.A.rp.p, L.srow.p);
   }
-  BCS_LAUNCH(s, K_CAST, 0, 0, k_slice_len, grid_for(ns, 256), 256, 0, rows, rpw, ns, L.A.rp.p, L.srow.p, slen.p);
+  BCS_LAUNCH_DEP(s, K_CAST, 0, 0, k_slice_len, grid_for(ns, 256), 256, 0, rows, rpw, ns, L.A.rp.p, L.srow.p, slen.p);
   BCS_OKR(exclusive_scan(s, slen.p, L.sptr.p, ns));
   BCS_CU(s, cudaMemcpyAsync(steps_dev, L.sptr.p + ns, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->stream));
   L.nslices = ns;
@@ -1234,18 +1248,18 @@ bcs_status layout_values(Solver* s, Level& L, int prec) {
     if (prec == BCS_PREC_FP32) {
       BCS_ALLOC(s, L.s32, nv);
       if (map == 1)
-        BCS_LAUNCH(s, K_CAST, bytes, 0, (k_tpr_fill<N, float>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
+        BCS_LAUNCH_DEP(s, K_CAST, bytes, 0, (k_tpr_fill<N, float>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
                    L.A.v.p, L.srow.p, L.sptr.p, L.sci.p, L.s32.p);
       else
-        BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, float>), g, 128, 0, rows, L.nslices, L.A.rp.p,
+        BCS_LAUNCH_DEP(s, K_CAST, bytes, 0, (k_slice_fill<N, float>), g, 128, 0, rows, L.nslices, L.A.rp.p,
                    L.A.ci.p, L.A.v.p, L.sptr.p, L.sci.p, L.s32.p);
     } else {
       BCS_ALLOC(s, L.s16, nv);
       if (map == 1)
-        BCS_LAUNCH(s, K_CAST, bytes, 0, (k_tpr_fill<N, bf16>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
+        BCS_LAUNCH_DEP(s, K_CAST, bytes, 0, (k_tpr_fill<N, bf16>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
                    L.A.v.p, L.srow.p, L.sptr.p, L.sci.p, L.s16.p);
       else
-        BCS_LAUNCH(s, K_CAST, bytes, 0, (k_slice_fill<N, bf16>), g, 128, 0, rows, L.nslices, L.A.rp.p,
+        BCS_LAUNCH_DEP(s, K_CAST, bytes, 0, (k_slice_fill<N, bf16>), g, 128, 0, rows, L.nslices, L.A.rp.p,
                    L.A.ci.p, L.A.v.p, L.sptr.p, L.sci.p, L.s16.p);
     }
     return BCS_OK;
@@ -1775,7 +1789,7 @@ bcs_status jacobi_apply(Solver* s, const double* v, double* z) {
   return with_n(s->n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
     const int rows = L0.A.rows;
-    BCS_LAUNCH(s, K_SWEEP, (double)rows * N * (N * 8 + 16), 2.0 * rows * N * N, (k_jacobi0<N, double, double, double>),
+    BCS_LAUNCH_DEP(s, K_SWEEP, (double)rows * N * (N * 8 + 16), 2.0 * rows * N * N, (k_jacobi0<N, double, double, double>),
                grid_for((size_t)rows * N, 256), 256, 0, rows, L0.dinv.p, v, z, 1.0);
     return BCS_OK;
   });
@@ -1810,40 +1824,40 @@ bcs_status kb_cycle_t(Solver* s, const BCase* cases, const std::vector<BCase>& h
   for (int l = 0; l + 1 < lmax; ++l) {
     int cur = cur0, alt = alt0;
     if (c.nu1 >= 1) {
-      BCS_LAUNCH(s, K_SWEEP, 0, 0, (kb_jac0_k<N>), grid(elems(l)), 256, 0, cases, l, 0, cur, om);
+      BCS_LAUNCH_DEP(s, K_SWEEP, 0, 0, (kb_jac0_k<N>), grid(elems(l)), 256, 0, cases, l, 0, cur, om);
       for (int k = 1; k < c.nu1; ++k) {
-        BCS_LAUNCH(s, K_SWEEP, 0, 0, (kb_sweep_k<N, TV, true>), grid(slices(l)), 128, 0, cases, l, 0, cur, alt, om);
+        BCS_LAUNCH_DEP(s, K_SWEEP, 0, 0, (kb_sweep_k<N, TV, true>), grid(slices(l)), 128, 0, cases, l, 0, cur, alt, om);
         std::swap(cur, alt);
       }
     } else {
-      BCS_LAUNCH(s, K_SWEEP, 0, 0, (kb_zero_k<N>), grid(elems(l)), 256, 0, cases, l, cur);
+      BCS_LAUNCH_DEP(s, K_SWEEP, 0, 0, (kb_zero_k<N>), grid(elems(l)), 256, 0, cases, l, cur);
     }
-    BCS_LAUNCH(s, K_RESID, 0, 0, (kb_sweep_k<N, TV, false>), grid(slices(l)), 128, 0, cases, l, 0, cur, 2, 0.f);
+    BCS_LAUNCH_DEP(s, K_RESID, 0, 0, (kb_sweep_k<N, TV, false>), grid(slices(l)), 128, 0, cases, l, 0, cur, 2, 0.f);
     const unsigned ga = grid_for(most(l, [](const BLevel& L) { return (size_t)L.nagg * N; }), 256);
-    BCS_LAUNCH(s, K_TRANSFER, 0, 0, (kb_restrict_k<N>), grid(ga), 256, 0, cases, l);
+    BCS_LAUNCH_DEP(s, K_TRANSFER, 0, 0, (kb_restrict_k<N>), grid(ga), 256, 0, cases, l);
   }
   // coarsest levels: dense inverses, or smoother sweeps from zero
   int cn = 0;
   for (const BCase& h : host) cn = std::max(cn, h.cN);
-  if (cn > 0) BCS_LAUNCH(s, K_COARSE, 0, 0, kb_gemv_k, grid(grid_for((size_t)cn * 32, 256)), 256, 0, cases);
+  if (cn > 0) BCS_LAUNCH_DEP(s, K_COARSE, 0, 0, kb_gemv_k, grid(grid_for((size_t)cn * 32, 256)), 256, 0, cases);
   for (int l = 0; l < lmax; ++l) {
     bool any = false;
     for (const BCase& h : host) any |= l < h.n_levels && h.lv[l].coarse_kind == 1;
     if (!any) continue;
     const int n_sw = c.coarse_sweeps;
     int cur = ((n_sw - 1) % 2 == 0) ? 1 : 3, alt = cur == 1 ? 3 : 1;
-    BCS_LAUNCH(s, K_SWEEP, 0, 0, (kb_jac0_k<N>), grid(elems(l)), 256, 0, cases, l, 1, cur, om);
+    BCS_LAUNCH_DEP(s, K_SWEEP, 0, 0, (kb_jac0_k<N>), grid(elems(l)), 256, 0, cases, l, 1, cur, om);
     for (int k = 1; k < n_sw; ++k) {
-      BCS_LAUNCH(s, K_SWEEP, 0, 0, (kb_sweep_k<N, TV, true>), grid(slices(l)), 128, 0, cases, l, 1, cur, alt, om);
+      BCS_LAUNCH_DEP(s, K_SWEEP, 0, 0, (kb_sweep_k<N, TV, true>), grid(slices(l)), 128, 0, cases, l, 1, cur, alt, om);
       std::swap(cur, alt);
     }
   }
   // up: prolongation-correction, post-smoothing
   for (int l = lmax - 2; l >= 0; --l) {
     int cur = cur_down, alt = alt_down;
-    BCS_LAUNCH(s, K_TRANSFER, 0, 0, (kb_prolong_k<N>), grid(elems(l)), 256, 0, cases, l, cur);
+    BCS_LAUNCH_DEP(s, K_TRANSFER, 0, 0, (kb_prolong_k<N>), grid(elems(l)), 256, 0, cases, l, cur);
     for (int k = 0; k < c.nu2; ++k) {
-      BCS_LAUNCH(s, K_SWEEP, 0, 0, (kb_sweep_k<N, TV, true>), grid(slices(l)), 128, 0, cases, l, 0, cur, alt, om);
+      BCS_LAUNCH_DEP(s, K_SWEEP, 0, 0, (kb_sweep_k<N, TV, true>), grid(slices(l)), 128, 0, cases, l, 0, cur, alt, om);
       std::swap(cur, alt);
     }
   }
@@ -1864,7 +1878,7 @@ bcs_status kb_cycle(Solver* s, const BCase* cases, const std::vector<BCase>& hos
 bcs_status kb_spmv_w(Solver* s, const BCase* cases, int count, int max_rows) {
   return with_n(s->n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    BCS_LAUNCH(s, K_SPMV64, 0, 0, kb_spmv_w_k<N>, dim3(rows_grid(max_rows, N), 1, count), 128, 0, cases);
+    BCS_LAUNCH_DEP(s, K_SPMV64, 0, 0, kb_spmv_w_k<N>, dim3(rows_grid(max_rows, N), 1, count), 128, 0, cases);
     return BCS_OK;
   });
 }
@@ -1872,7 +1886,7 @@ bcs_status kb_spmv_w(Solver* s, const BCase* cases, int count, int max_rows) {
 bcs_status kb_resid_r(Solver* s, const BCase* cases, int count, int max_rows) {
   return with_n(s->n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    BCS_LAUNCH(s, K_SPMV64, 0, 0, kb_resid_r_k<N>, dim3(rows_grid(max_rows, N), 1, count), 128, 0, cases);
+    BCS_LAUNCH_DEP(s, K_SPMV64, 0, 0, kb_resid_r_k<N>, dim3(rows_grid(max_rows, N), 1, count), 128, 0, cases);
     return BCS_OK;
   });
 }

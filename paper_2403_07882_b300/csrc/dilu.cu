@@ -45,6 +45,7 @@ __device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
 __global__ void k_jp_round(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const int32_t* __restrict__ cin, int32_t* __restrict__ cout, int32_t* __restrict__ left,
                            int32_t* __restrict__ err) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   int uncoloured = 0;
   if (i < rows) {
@@ -82,6 +83,7 @@ __global__ void k_jp_round(int rows, const int32_t* __restrict__ rp, const int32
 // Per-colour row counts (block-local histogram, one atomic per colour and
 // block). blockDim >= DILU_MAX_COLOURS.
 __global__ void k_colour_count(int rows, const int32_t* __restrict__ colour, int32_t* __restrict__ cnt) {
+  dep_enter();
   __shared__ int32_t hist[DILU_MAX_COLOURS];
   const int t = threadIdx.x, i = blockIdx.x * blockDim.x + t;
   if (t < DILU_MAX_COLOURS) hist[t] = 0;
@@ -95,6 +97,7 @@ __global__ void k_colour_count(int rows, const int32_t* __restrict__ colour, int
 // order inside a colour does not matter (its rows are independent).
 __global__ void k_colour_place(int rows, const int32_t* __restrict__ colour, const int32_t* __restrict__ start,
                                int32_t* __restrict__ cursor, int32_t* __restrict__ crow) {
+  dep_enter();
   __shared__ int32_t hist[DILU_MAX_COLOURS], base[DILU_MAX_COLOURS];
   const int t = threadIdx.x, i = blockIdx.x * blockDim.x + t;
   if (t < DILU_MAX_COLOURS) hist[t] = 0;
@@ -114,6 +117,7 @@ __global__ void k_colour_place(int rows, const int32_t* __restrict__ colour, con
 __global__ void k_dilu_split_count(int rows, const int32_t* __restrict__ crow, const int32_t* __restrict__ rp,
                                    const int32_t* __restrict__ ci, const int32_t* __restrict__ colour,
                                    int32_t* __restrict__ cnt) {
+  dep_enter();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= rows) return;
   const int i = crow[t], c = colour[i];
@@ -127,6 +131,7 @@ __global__ void k_dilu_split_fill(int rows, const int32_t* __restrict__ crow, co
                                   const int32_t* __restrict__ ci, const int32_t* __restrict__ colour,
                                   const int32_t* __restrict__ dptr, int32_t* __restrict__ dmid,
                                   int32_t* __restrict__ dsrc, int32_t* __restrict__ dci) {
+  dep_enter();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= rows) return;
   const int i = crow[t], c = colour[i];
@@ -156,6 +161,7 @@ template <int NN, class TO>
 __global__ void k_dilu_split_values(long long bound, const int32_t* __restrict__ total,
                                     const int32_t* __restrict__ dsrc, const double* __restrict__ val,
                                     TO* __restrict__ out) {
+  dep_enter();
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= bound) return;
   const long long q = t / NN;
@@ -188,6 +194,7 @@ __global__ void __launch_bounds__(128) k_dilu_schur(int cnt, const int32_t* __re
                                                     const int32_t* __restrict__ ci, const double* __restrict__ val,
                                                     const int32_t* __restrict__ dpos, const double* __restrict__ einv,
                                                     double* __restrict__ E, int32_t* __restrict__ err) {
+  dep_enter();
   constexpr int NN = N * N;
   if constexpr (NN <= 32) {
     const int lane = threadIdx.x & 31;
@@ -269,6 +276,7 @@ template <int N>
 __global__ void __launch_bounds__(64) k_dilu_invert(int cnt, const int32_t* __restrict__ rows_c,
                                                     const double* __restrict__ E, double* __restrict__ einv,
                                                     int32_t* __restrict__ err) {
+  dep_enter();
   constexpr int NN = N * N;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= cnt) return;
@@ -304,7 +312,7 @@ bcs_status dilu_setup(Solver* s, Level& L, bool full, bool sgs) {
     for (int round = 0; h[0] > 0 && !(h[1] & 32); ++round) {
       if (round > rows + 4) return s->fail(BCS_EINVAL, "colouring did not finish");
       BCS_CU(s, cudaMemsetAsync(aux.p, 0, sizeof(int32_t), s->stream));
-      BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_jp_round, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, L.A.ci.p, cin,
+      BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_jp_round, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, L.A.ci.p, cin,
                  cout, aux.p, aux.p + 1);
       std::swap(cin, cout);
       if (round % 4 == 3) {
@@ -322,7 +330,7 @@ bcs_status dilu_setup(Solver* s, Level& L, bool full, bool sgs) {
     BCS_ALLOC(s, cursor, DILU_MAX_COLOURS);
     BCS_CU(s, cudaMemsetAsync(cnt.p, 0, DILU_MAX_COLOURS * sizeof(int32_t), s->stream));
     BCS_CU(s, cudaMemsetAsync(cursor.p, 0, DILU_MAX_COLOURS * sizeof(int32_t), s->stream));
-    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_colour_count, grid_for(rows, 256), 256, 0, rows, L.colour.p, cnt.p);
+    BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_colour_count, grid_for(rows, 256), 256, 0, rows, L.colour.p, cnt.p);
     std::vector<int32_t> hc(DILU_MAX_COLOURS);
     BCS_CU(s, cudaMemcpyAsync(hc.data(), cnt.p, DILU_MAX_COLOURS * sizeof(int32_t), cudaMemcpyDeviceToHost,
                               s->stream));
@@ -335,7 +343,7 @@ bcs_status dilu_setup(Solver* s, Level& L, bool full, bool sgs) {
     BCS_CU(s, cudaMemcpyAsync(start.p, L.cstart.data(), (ncol + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
                               s->stream));
     BCS_ALLOC(s, L.crow, rows);
-    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_colour_place, grid_for(rows, 256), 256, 0, rows, L.colour.p, start.p,
+    BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_colour_place, grid_for(rows, 256), 256, 0, rows, L.colour.p, start.p,
                cursor.p, L.crow.p);
     // the sweeps' split rows (sized by the nonzero count, an upper bound)
     BCS_ALLOC(s, L.dptr, rows + 1);
@@ -344,10 +352,10 @@ bcs_status dilu_setup(Solver* s, Level& L, bool full, bool sgs) {
     BCS_ALLOC(s, L.dci, L.A.nnz);
     DBuf<int32_t> dcnt;
     BCS_ALLOC(s, dcnt, rows);
-    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_dilu_split_count, grid_for(rows, 256), 256, 0, rows, L.crow.p, L.A.rp.p,
+    BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_dilu_split_count, grid_for(rows, 256), 256, 0, rows, L.crow.p, L.A.rp.p,
                L.A.ci.p, L.colour.p, dcnt.p);
     BCS_OKR(exclusive_scan(s, dcnt.p, L.dptr.p, rows));
-    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_dilu_split_fill, grid_for(rows, 256), 256, 0, rows, L.crow.p, L.A.rp.p,
+    BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_dilu_split_fill, grid_for(rows, 256), 256, 0, rows, L.crow.p, L.A.rp.p,
                L.A.ci.p, L.colour.p, L.dptr.p, L.dmid.p, L.dsrc.p, L.dci.p);
     // the host vector L.cstart is read by this copy: finish it before return
     BCS_CU(s, cudaStreamSynchronize(s->stream));
@@ -371,9 +379,9 @@ bcs_status dilu_setup(Solver* s, Level& L, bool full, bool sgs) {
       const int b = L.cstart[c], m = L.cstart[c + 1] - b;
       if (m <= 0) continue;
       const unsigned gs = N * N <= 32 ? grid_for((size_t)m * 32, 128) : grid_for(m, 128);
-      BCS_LAUNCH(s, K_SETUP_INV, 8.0 * m * N * N * 4, 4.0 * m * N * N * N * 3, k_dilu_schur<N>, gs, 128, 0, m,
+      BCS_LAUNCH_DEP(s, K_SETUP_INV, 8.0 * m * N * N * 4, 4.0 * m * N * N * N * 3, k_dilu_schur<N>, gs, 128, 0, m,
                  L.crow.p + b, c, L.colour.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.dpos.p, L.einv.p, E.p, s->flag.p);
-      BCS_LAUNCH(s, K_SETUP_INV, 16.0 * m * N * N, 4.0 * m * N * N * N, k_dilu_invert<N>, grid_for(m, 64), 64, 0,
+      BCS_LAUNCH_DEP(s, K_SETUP_INV, 16.0 * m * N * N, 4.0 * m * N * N * N, k_dilu_invert<N>, grid_for(m, 64), 64, 0,
                  m, L.crow.p + b, E.p, L.einv.p, s->flag.p);
     }
     return BCS_OK;
@@ -399,10 +407,10 @@ bcs_status dilu_prepare(Solver* s, Level& L) {
     constexpr int N = decltype(NC)::value;
     const unsigned g = grid_for((size_t)bound, 256);
     if (b16)
-      BCS_LAUNCH(s, K_CAST, 10.0 * bound, 0, (k_dilu_split_values<N * N, bf16>), g, 256, 0, bound,
+      BCS_LAUNCH_DEP(s, K_CAST, 10.0 * bound, 0, (k_dilu_split_values<N * N, bf16>), g, 256, 0, bound,
                  L.dptr.p + L.A.rows, L.dsrc.p, L.A.v.p, L.a16.p);
     else
-      BCS_LAUNCH(s, K_CAST, 12.0 * bound, 0, (k_dilu_split_values<N * N, float>), g, 256, 0, bound,
+      BCS_LAUNCH_DEP(s, K_CAST, 12.0 * bound, 0, (k_dilu_split_values<N * N, float>), g, 256, 0, bound,
                  L.dptr.p + L.A.rows, L.dsrc.p, L.A.v.p, L.a32.p);
     return BCS_OK;
   });

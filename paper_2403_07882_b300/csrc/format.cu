@@ -20,6 +20,7 @@ namespace {
 __global__ void k_check_count(int C, int F, const int32_t* __restrict__ owner,
                               const int32_t* __restrict__ nb, int32_t* __restrict__ cnt,
                               int32_t* __restrict__ err) {
+  dep_enter();
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= F) return;
   const int o = owner[f], m = nb[f];
@@ -32,6 +33,7 @@ __global__ void k_check_count(int C, int F, const int32_t* __restrict__ owner,
 }
 
 __global__ void k_fill_ones(int32_t* __restrict__ a, int n) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = 1;
 }
@@ -39,6 +41,7 @@ __global__ void k_fill_ones(int32_t* __restrict__ a, int n) {
 // Diagonal first in every row, then faces through a per-row cursor.
 __global__ void k_place_diag(int C, const int32_t* __restrict__ rp, int32_t* __restrict__ col,
                              int32_t* __restrict__ src, int32_t* __restrict__ cursor) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= C) return;
   col[rp[i]] = i;
@@ -49,6 +52,7 @@ __global__ void k_place_diag(int C, const int32_t* __restrict__ rp, int32_t* __r
 __global__ void k_place_faces(int F, const int32_t* __restrict__ owner, const int32_t* __restrict__ nb,
                               const int32_t* __restrict__ rp, int32_t* __restrict__ col,
                               int32_t* __restrict__ src, int32_t* __restrict__ cursor) {
+  dep_enter();
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= F) return;
   const int o = owner[f], m = nb[f];
@@ -66,6 +70,7 @@ __global__ void k_sort_rows(int C, const int32_t* __restrict__ rp, int32_t* __re
                             int32_t* __restrict__ src, int32_t* __restrict__ pos_diag,
                             int32_t* __restrict__ pos_up, int32_t* __restrict__ pos_lo,
                             int32_t* __restrict__ err) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   // longest row -> err[2] (one atomic per warp)
   const int m = __reduce_max_sync(0xffffffffu, i < C ? rp[i + 1] - rp[i] : 0);
@@ -100,6 +105,7 @@ template <int NN>
 __global__ void k_gather_values(size_t total, const int32_t* __restrict__ src,
                                 const double* __restrict__ diag, const double* __restrict__ upper,
                                 const double* __restrict__ lower, double* __restrict__ val) {
+  dep_enter();
   const size_t S = (size_t)gridDim.x * blockDim.x;
   for (size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t0 < total; t0 += GV_U * S) {
     const double* a[GV_U];
@@ -145,6 +151,7 @@ __global__ void __launch_bounds__(GnShape<NN>::WARPS * 32) k_gather_norms(int nn
                                                                          const double* __restrict__ lower,
                                                                          double* __restrict__ val,
                                                                          double* __restrict__ nrm) {
+  dep_enter();
   using G = GnShape<NN>;
   __shared__ double tile[G::WARPS][32 * G::NNP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -202,6 +209,7 @@ __global__ void __launch_bounds__(GnShape<NN>::WARPS * 32) k_scatter_blocks(int 
                                                                            const int32_t* __restrict__ pos,
                                                                            double* __restrict__ val,
                                                                            double* __restrict__ nrm) {
+  dep_enter();
   using G = GnShape<NN>;
   __shared__ double tile[G::WARPS][32 * G::NNP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -253,9 +261,9 @@ bcs_status build_structure(Solver* s, const int32_t* owner, const int32_t* nb) {
   BCS_ALLOC(s, s->pos_up, F > 0 ? F : 1);
   BCS_ALLOC(s, s->pos_lo, F > 0 ? F : 1);
   BCS_CU(s, cudaMemsetAsync(s->flag.p, 0, 4 * sizeof(int32_t), s->stream));
-  BCS_LAUNCH(s, K_CONVERT, 4.0 * C, 0, k_fill_ones, grid_for(C, 256), 256, 0, cnt.p, C);
+  BCS_LAUNCH_DEP(s, K_CONVERT, 4.0 * C, 0, k_fill_ones, grid_for(C, 256), 256, 0, cnt.p, C);
   if (F > 0)
-    BCS_LAUNCH(s, K_CONVERT, 8.0 * F, 0, k_check_count, grid_for(F, 256), 256, 0, C, F, owner, nb, cnt.p,
+    BCS_LAUNCH_DEP(s, K_CONVERT, 8.0 * F, 0, k_check_count, grid_for(F, 256), 256, 0, C, F, owner, nb, cnt.p,
                s->flag.p);
   // Reject bad ids before any kernel indexes rows with them.
   int32_t h = 0;
@@ -263,12 +271,12 @@ bcs_status build_structure(Solver* s, const int32_t* owner, const int32_t* nb) {
   BCS_CU(s, cudaStreamSynchronize(s->stream));
   if (h & 1) return s->fail(BCS_EINVAL, "face addressing: cell id out of range or owner == neighbour");
   BCS_OKR(exclusive_scan(s, cnt.p, A.rp.p, C));
-  BCS_LAUNCH(s, K_CONVERT, 12.0 * C, 0, k_place_diag, grid_for(C, 256), 256, 0, C, A.rp.p, A.ci.p, s->src.p,
+  BCS_LAUNCH_DEP(s, K_CONVERT, 12.0 * C, 0, k_place_diag, grid_for(C, 256), 256, 0, C, A.rp.p, A.ci.p, s->src.p,
              cursor.p);
   if (F > 0)
-    BCS_LAUNCH(s, K_CONVERT, 24.0 * F, 0, k_place_faces, grid_for(F, 256), 256, 0, F, owner, nb, A.rp.p,
+    BCS_LAUNCH_DEP(s, K_CONVERT, 24.0 * F, 0, k_place_faces, grid_for(F, 256), 256, 0, F, owner, nb, A.rp.p,
                A.ci.p, s->src.p, cursor.p);
-  BCS_LAUNCH(s, K_CONVERT, 16.0 * nnz, 0, k_sort_rows, grid_for(C, 128), 128, 0, C, A.rp.p, A.ci.p,
+  BCS_LAUNCH_DEP(s, K_CONVERT, 16.0 * nnz, 0, k_sort_rows, grid_for(C, 128), 128, 0, C, A.rp.p, A.ci.p,
              s->src.p, s->pos_diag.p, s->pos_up.p, s->pos_lo.p, s->flag.p);
   int32_t hf[3] = {0, 0, 0};
   BCS_CU(s, cudaMemcpyAsync(hf, s->flag.p, sizeof(hf), cudaMemcpyDeviceToHost, s->stream));
@@ -291,7 +299,7 @@ bcs_status permute_values(Solver* s, const double* diag, const double* upper, co
     BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
       constexpr int N = decltype(NC)::value;
       using G = GnShape<N * N>;
-      BCS_LAUNCH(s, K_CONVERT, bytes + 8.0 * A.nnz, 2.0 * total, k_gather_norms<N * N>,
+      BCS_LAUNCH_DEP(s, K_CONVERT, bytes + 8.0 * A.nnz, 2.0 * total, k_gather_norms<N * N>,
                  grid_for((size_t)A.nnz, G::WARPS * 32), G::WARPS * 32, 0, A.nnz, s->src.p, diag, upper, lower,
                  A.v.p, s->nrm0.p);
       return BCS_OK;
@@ -303,7 +311,7 @@ bcs_status permute_values(Solver* s, const double* diag, const double* upper, co
     constexpr int N = decltype(NC)::value;
     unsigned grid = grid_for(total, 256);
     if (grid > 148u * 32u) grid = 148u * 32u;
-    BCS_LAUNCH(s, K_CONVERT, bytes, 0, k_gather_values<N * N>, grid, 256, 0, total, s->src.p, diag, upper,
+    BCS_LAUNCH_DEP(s, K_CONVERT, bytes, 0, k_gather_values<N * N>, grid, 256, 0, total, s->src.p, diag, upper,
                lower, A.v.p);
     return BCS_OK;
   });
@@ -369,7 +377,7 @@ bcs_status upload_values(Solver* s, const double* diag, const double* upper, con
       BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
         constexpr int N = decltype(NC)::value;
         using G = GnShape<N * N>;
-        BCS_LAUNCH(s, K_CONVERT, 16.0 * cnt * N * N + 4.0 * cnt + (norms ? 8.0 * cnt : 0.0),
+        BCS_LAUNCH_DEP(s, K_CONVERT, 16.0 * cnt * N * N + 4.0 * cnt + (norms ? 8.0 * cnt : 0.0),
                    norms ? 2.0 * cnt * N * N : 0.0, k_scatter_blocks<N * N>, grid_for(cnt, G::WARPS * 32),
                    G::WARPS * 32, 0, cnt, pt.dev + off, pt.pos + b, A.v.p, norms ? s->nrm0.p : nullptr);
         return BCS_OK;

@@ -40,6 +40,7 @@ struct VecTable {
 template <int N, bool PACK>
 __global__ void k_pack_vector(size_t total, FieldMap m, VecTable t, const double* __restrict__ vin,
                               double* __restrict__ vout) {
+  dep_enter();
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= total) return;
   const size_t c = i / N;
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(PK_WARPS * 32) k_pack_coefficients(int C, int 
                                                                      double* __restrict__ upper,
                                                                      double* __restrict__ lower,
                                                                      double* __restrict__ val) {
+  dep_enter();
   constexpr int NN = N * N, PK_TILE = pk_tile<N>();
   __shared__ double tile_s[PK_WARPS][PK_TILE * NN];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -154,7 +156,7 @@ bcs_status pack_vector(Solver* s, int nfields, const int* ncomp, const double* c
   const size_t total = (size_t)s->C * s->n;
   return with_n(s->n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    BCS_LAUNCH(s, K_CONVERT, 16.0 * total, 0, (k_pack_vector<N, true>), grid_for(total, 256), 256, 0, total, m, t,
+    BCS_LAUNCH_DEP(s, K_CONVERT, 16.0 * total, 0, (k_pack_vector<N, true>), grid_for(total, 256), 256, 0, total, m, t,
                (const double*)nullptr, out);
     return BCS_OK;
   });
@@ -167,7 +169,7 @@ bcs_status unpack_vector(Solver* s, int nfields, const int* ncomp, const double*
   const size_t total = (size_t)s->C * s->n;
   return with_n(s->n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    BCS_LAUNCH(s, K_CONVERT, 16.0 * total, 0, (k_pack_vector<N, false>), grid_for(total, 256), 256, 0, total, m,
+    BCS_LAUNCH_DEP(s, K_CONVERT, 16.0 * total, 0, (k_pack_vector<N, false>), grid_for(total, 256), 256, 0, total, m,
                t, in, (double*)nullptr);
     return BCS_OK;
   });
@@ -190,11 +192,11 @@ bcs_status pack_coefficients(Solver* s, int nfields, const int* ncomp, const dou
     const size_t tiles = ((size_t)C + T - 1) / T + 2 * (((size_t)F + T - 1) / T);
     const unsigned grid = grid_for(tiles, PK_WARPS);
     if (bsr)
-      BCS_LAUNCH(s, K_CONVERT, 16.0 * total + 4.0 * (C + 2.0 * F), 0, (k_pack_coefficients<N, true>), grid,
+      BCS_LAUNCH_DEP(s, K_CONVERT, 16.0 * total + 4.0 * (C + 2.0 * F), 0, (k_pack_coefficients<N, true>), grid,
                  PK_WARPS * 32, 0, C, F, m, t, s->pos_diag.p, s->pos_up.p, s->pos_lo.p, nullptr, nullptr, nullptr,
                  val);
     else
-      BCS_LAUNCH(s, K_CONVERT, 16.0 * total, 0, (k_pack_coefficients<N, false>), grid, PK_WARPS * 32, 0, C, F, m,
+      BCS_LAUNCH_DEP(s, K_CONVERT, 16.0 * total, 0, (k_pack_coefficients<N, false>), grid, PK_WARPS * 32, 0, C, F, m,
                  t, nullptr, nullptr, nullptr, diag, upper, lower, nullptr);
     return BCS_OK;
   });

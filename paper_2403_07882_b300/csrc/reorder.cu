@@ -28,6 +28,7 @@ __device__ __forceinline__ int degree(const int32_t* __restrict__ rp, int v) { r
 __global__ void k_cm_discover(int s0, int m, const int32_t* __restrict__ order, const int32_t* __restrict__ rp,
                               const int32_t* __restrict__ ci, int32_t* __restrict__ lvl, int next,
                               int32_t* __restrict__ par, int32_t* __restrict__ nxt, int32_t* __restrict__ nn) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   const int u = order[s0 + i];
@@ -48,6 +49,7 @@ __global__ void k_cm_discover(int s0, int m, const int32_t* __restrict__ order, 
 
 __global__ void k_cm_count(int nn, int s0, const int32_t* __restrict__ nxt, const int32_t* __restrict__ par,
                            int32_t* __restrict__ cnt) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nn) atomicAdd(cnt + (par[nxt[i]] - s0), 1);
 }
@@ -55,6 +57,7 @@ __global__ void k_cm_count(int nn, int s0, const int32_t* __restrict__ nxt, cons
 __global__ void k_cm_place(int nn, int s0, const int32_t* __restrict__ nxt, const int32_t* __restrict__ par,
                            const int32_t* __restrict__ seg, int32_t* __restrict__ cur, const int32_t* __restrict__ rp,
                            uint64_t* __restrict__ keys) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nn) return;
   const int v = nxt[i], q = par[v] - s0;
@@ -63,6 +66,7 @@ __global__ void k_cm_place(int nn, int s0, const int32_t* __restrict__ nxt, cons
 }
 
 __global__ void k_cm_emit(int nn, int e0, const uint64_t* __restrict__ keys, int32_t* __restrict__ order) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nn) order[e0 + i] = (int32_t)(uint32_t)keys[i];
 }
@@ -73,6 +77,7 @@ __global__ void k_bfs_step(int m, const int32_t* __restrict__ cur, const int32_t
                            const int32_t* __restrict__ ci, const int32_t* __restrict__ lvl, int32_t* __restrict__ mark,
                            int gen, int32_t* __restrict__ nxt, int32_t* __restrict__ nn,
                            unsigned long long* __restrict__ minkey) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   const int u = cur[i];
@@ -85,12 +90,14 @@ __global__ void k_bfs_step(int m, const int32_t* __restrict__ cur, const int32_t
 }
 
 __global__ void k_first_unvisited(int C, int from, const int32_t* __restrict__ lvl, int32_t* __restrict__ first) {
+  dep_enter();
   const int i = from + blockIdx.x * blockDim.x + threadIdx.x;
   if (i < C && lvl[i] == -1) atomicMin(first, i);
 }
 
 __global__ void k_reverse(int C, const int32_t* __restrict__ order, int32_t* __restrict__ perm,
                           int32_t* __restrict__ inv) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= C) return;
   const int old = order[C - 1 - i];
@@ -99,6 +106,7 @@ __global__ void k_reverse(int C, const int32_t* __restrict__ order, int32_t* __r
 }
 
 __global__ void k_start(int r, int pos, int32_t* __restrict__ order, int32_t* __restrict__ lvl, int tag) {
+  dep_enter();
   order[pos] = r;
   lvl[r] = tag;
 }
@@ -146,7 +154,7 @@ bcs_status rcm_order(Solver* s, const Bsr& A, int32_t* perm, int32_t* inv) {
       ++*nlev;
       BCS_CU(s, cudaMemsetAsync(sc.p, 0, sizeof(int32_t), s->stream));
       BCS_CU(s, cudaMemsetAsync(mk.p, 0xff, sizeof(unsigned long long), s->stream));
-      BCS_LAUNCH(s, K_MISC, 0, 0, k_bfs_step, grid_for(m, 256), 256, 0, m, a, A.rp.p, A.ci.p, lvl.p, mark.p, gen, b,
+      BCS_LAUNCH_DEP(s, K_MISC, 0, 0, k_bfs_step, grid_for(m, 256), 256, 0, m, a, A.rp.p, A.ci.p, lvl.p, mark.p, gen, b,
                  sc.p, mk.p);
       Hv h{};
       BCS_CU(s, cudaMemcpyAsync(&h.nn, sc.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
@@ -164,7 +172,7 @@ bcs_status rcm_order(Solver* s, const Bsr& A, int32_t* perm, int32_t* inv) {
     // the component's smallest cell
     int32_t first = INT_MAX;
     BCS_CU(s, cudaMemcpyAsync(sc.p + 1, &first, sizeof(int32_t), cudaMemcpyHostToDevice, s->stream));
-    BCS_LAUNCH(s, K_MISC, 0, 0, k_first_unvisited, grid_for(C - from, 256), 256, 0, C, from, lvl.p, sc.p + 1);
+    BCS_LAUNCH_DEP(s, K_MISC, 0, 0, k_first_unvisited, grid_for(C - from, 256), 256, 0, C, from, lvl.p, sc.p + 1);
     BCS_CU(s, cudaMemcpyAsync(&first, sc.p + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
     BCS_CU(s, cudaStreamSynchronize(s->stream));
     if (first == INT_MAX) return s->fail(BCS_EINVAL, "reordering lost a cell");
@@ -181,13 +189,13 @@ bcs_status rcm_order(Solver* s, const Bsr& A, int32_t* perm, int32_t* inv) {
       x = x2;
     }
     // Cuthill-McKee from r, one level at a time
-    BCS_LAUNCH(s, K_MISC, 0, 0, k_start, 1, 1, 0, r, placed, order.p, lvl.p, ++tag);
+    BCS_LAUNCH_DEP(s, K_MISC, 0, 0, k_start, 1, 1, 0, r, placed, order.p, lvl.p, ++tag);
     int s0 = placed, m = 1;
     placed += 1;
     for (;;) {
       const int next = ++tag;
       BCS_CU(s, cudaMemsetAsync(sc.p, 0, sizeof(int32_t), s->stream));
-      BCS_LAUNCH(s, K_MISC, 0, 0, k_cm_discover, grid_for(m, 256), 256, 0, s0, m, order.p, A.rp.p, A.ci.p, lvl.p,
+      BCS_LAUNCH_DEP(s, K_MISC, 0, 0, k_cm_discover, grid_for(m, 256), 256, 0, s0, m, order.p, A.rp.p, A.ci.p, lvl.p,
                  next, par.p, nxt.p, sc.p);
       int32_t nn = 0;
       BCS_CU(s, cudaMemcpyAsync(&nn, sc.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
@@ -195,18 +203,18 @@ bcs_status rcm_order(Solver* s, const Bsr& A, int32_t* perm, int32_t* inv) {
       if (nn == 0) break;
       BCS_CU(s, cudaMemsetAsync(cnt.p, 0, m * sizeof(int32_t), s->stream));
       BCS_CU(s, cudaMemsetAsync(cur.p, 0, m * sizeof(int32_t), s->stream));
-      BCS_LAUNCH(s, K_MISC, 0, 0, k_cm_count, grid_for(nn, 256), 256, 0, nn, s0, nxt.p, par.p, cnt.p);
+      BCS_LAUNCH_DEP(s, K_MISC, 0, 0, k_cm_count, grid_for(nn, 256), 256, 0, nn, s0, nxt.p, par.p, cnt.p);
       BCS_OKR(exclusive_scan(s, cnt.p, seg.p, m));
-      BCS_LAUNCH(s, K_MISC, 0, 0, k_cm_place, grid_for(nn, 256), 256, 0, nn, s0, nxt.p, par.p, seg.p, cur.p,
+      BCS_LAUNCH_DEP(s, K_MISC, 0, 0, k_cm_place, grid_for(nn, 256), 256, 0, nn, s0, nxt.p, par.p, seg.p, cur.p,
                  A.rp.p, keys.p);
       BCS_OKR(segmented_sort64(s, seg.p, keys.p, m, maxdeg));
-      BCS_LAUNCH(s, K_MISC, 0, 0, k_cm_emit, grid_for(nn, 256), 256, 0, nn, s0 + m, keys.p, order.p);
+      BCS_LAUNCH_DEP(s, K_MISC, 0, 0, k_cm_emit, grid_for(nn, 256), 256, 0, nn, s0 + m, keys.p, order.p);
       s0 += m;
       m = nn;
       placed += nn;
     }
   }
-  BCS_LAUNCH(s, K_MISC, 0, 0, k_reverse, grid_for(C, 256), 256, 0, C, order.p, perm, inv);
+  BCS_LAUNCH_DEP(s, K_MISC, 0, 0, k_reverse, grid_for(C, 256), 256, 0, C, order.p, perm, inv);
   return BCS_OK;
 }
 
@@ -218,6 +226,7 @@ namespace {
 
 __global__ void k_relabel(int F, const int32_t* __restrict__ inv, const int32_t* __restrict__ o,
                           const int32_t* __restrict__ nb, int32_t* __restrict__ o2, int32_t* __restrict__ nb2) {
+  dep_enter();
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= F) return;
   o2[f] = inv[o[f]];
@@ -229,6 +238,7 @@ __global__ void k_relabel(int F, const int32_t* __restrict__ inv, const int32_t*
 // indexed by the caller's cell.
 __global__ void k_user_diag(int C, const int32_t* __restrict__ perm, const int32_t* __restrict__ pd_new,
                             int32_t* __restrict__ pd_user, int32_t* __restrict__ src) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= C) return;
   const int p = pd_new[i];
@@ -239,6 +249,7 @@ __global__ void k_user_diag(int C, const int32_t* __restrict__ perm, const int32
 template <bool GATHER>
 __global__ void k_permute_vec(size_t total, int n, const int32_t* __restrict__ perm, const double* __restrict__ in,
                               double* __restrict__ out) {
+  dep_enter();
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= total) return;
   const size_t i = t / n;
@@ -254,14 +265,14 @@ __global__ void k_permute_vec(size_t total, int n, const int32_t* __restrict__ p
 
 bcs_status relabel_faces(Solver* s, const int32_t* o, const int32_t* nb, int32_t* o2, int32_t* nb2) {
   if (s->F > 0)
-    BCS_LAUNCH(s, K_CONVERT, 16.0 * s->F, 0, k_relabel, grid_for(s->F, 256), 256, 0, s->F, s->inv.p, o, nb, o2, nb2);
+    BCS_LAUNCH_DEP(s, K_CONVERT, 16.0 * s->F, 0, k_relabel, grid_for(s->F, 256), 256, 0, s->F, s->inv.p, o, nb, o2, nb2);
   return BCS_OK;
 }
 
 bcs_status user_diag_maps(Solver* s) {
   DBuf<int32_t> pd;
   BCS_ALLOC(s, pd, s->C);
-  BCS_LAUNCH(s, K_CONVERT, 16.0 * s->C, 0, k_user_diag, grid_for(s->C, 256), 256, 0, s->C, s->perm.p,
+  BCS_LAUNCH_DEP(s, K_CONVERT, 16.0 * s->C, 0, k_user_diag, grid_for(s->C, 256), 256, 0, s->C, s->perm.p,
              s->pos_diag.p, pd.p, s->src.p);
   s->pos_diag = std::move(pd);
   return BCS_OK;
@@ -269,14 +280,14 @@ bcs_status user_diag_maps(Solver* s) {
 
 bcs_status to_internal(Solver* s, const double* user, double* internal) {
   const size_t total = (size_t)s->C * s->n;
-  BCS_LAUNCH(s, K_CONVERT, 16.0 * total, 0, k_permute_vec<true>, grid_for(total, 256), 256, 0, total, s->n,
+  BCS_LAUNCH_DEP(s, K_CONVERT, 16.0 * total, 0, k_permute_vec<true>, grid_for(total, 256), 256, 0, total, s->n,
              s->perm.p, user, internal);
   return BCS_OK;
 }
 
 bcs_status to_user(Solver* s, const double* internal, double* user) {
   const size_t total = (size_t)s->C * s->n;
-  BCS_LAUNCH(s, K_CONVERT, 16.0 * total, 0, k_permute_vec<false>, grid_for(total, 256), 256, 0, total, s->n,
+  BCS_LAUNCH_DEP(s, K_CONVERT, 16.0 * total, 0, k_permute_vec<false>, grid_for(total, 256), 256, 0, total, s->n,
              s->perm.p, internal, user);
   return BCS_OK;
 }

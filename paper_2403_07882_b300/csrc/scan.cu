@@ -16,6 +16,7 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 // Block-local exclusive scan of one tile; writes the tile total.
 __global__ void k_scan_tile(const int32_t* __restrict__ in, int32_t* __restrict__ out,
                             int32_t* __restrict__ tile_sum, int n) {
+  dep_enter();
   __shared__ int32_t warp_tot[SCAN_THREADS / 32];
   const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
   int32_t v[SCAN_ITEMS];
@@ -58,6 +59,7 @@ __global__ void k_scan_tile(const int32_t* __restrict__ in, int32_t* __restrict_
 
 // out[i] += tile_off[i / SCAN_TILE]; thread n writes the grand total.
 __global__ void k_scan_add(int32_t* __restrict__ out, const int32_t* __restrict__ tile_off, int n, int tiles) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] += tile_off[i / SCAN_TILE];
   else if (i == n) out[n] = tile_off[tiles];
@@ -75,6 +77,7 @@ __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 
 __global__ void __launch_bounds__(SMALL_THREADS) k_scan_small(const int32_t* __restrict__ in,
                                                              int32_t* __restrict__ out, int n) {
+  dep_enter();
   __shared__ int32_t buf[SMALL_SCAN_MAX + SMALL_SCAN_MAX / 32];
   __shared__ int32_t warp_tot[SMALL_THREADS / 32];
 #pragma unroll
@@ -137,16 +140,16 @@ bcs_status exclusive_scan(Solver* s, const int32_t* in, int32_t* out, int n) {
     return BCS_OK;
   }
   if (n <= SMALL_SCAN_MAX) {
-    BCS_LAUNCH(s, K_MISC, 8.0 * n, 0, k_scan_small, 1, SMALL_THREADS, 0, in, out, n);
+    BCS_LAUNCH_DEP(s, K_MISC, 8.0 * n, 0, k_scan_small, 1, SMALL_THREADS, 0, in, out, n);
     return BCS_OK;
   }
   const int tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   DBuf<int32_t> sums, offs;
   BCS_ALLOC(s, sums, tiles);
   BCS_ALLOC(s, offs, tiles + 1);
-  BCS_LAUNCH(s, K_MISC, 8.0 * n, 0, k_scan_tile, tiles, SCAN_THREADS, 0, in, out, sums.p, n);
+  BCS_LAUNCH_DEP(s, K_MISC, 8.0 * n, 0, k_scan_tile, tiles, SCAN_THREADS, 0, in, out, sums.p, n);
   BCS_OKR(exclusive_scan(s, sums.p, offs.p, tiles));
-  BCS_LAUNCH(s, K_MISC, 8.0 * n, 0, k_scan_add, grid_for((size_t)n + 1, 256), 256, 0, out, offs.p, n, tiles);
+  BCS_LAUNCH_DEP(s, K_MISC, 8.0 * n, 0, k_scan_add, grid_for((size_t)n + 1, 256), 256, 0, out, offs.p, n, tiles);
   return BCS_OK;
 }
 
@@ -173,6 +176,7 @@ __global__ void k_seg_sort_warp(const int32_t* __restrict__ seg_ptr, T* __restri
                                 int32_t* __restrict__ count, const int32_t* __restrict__ list,
                                 const int32_t* __restrict__ n_list, int32_t* __restrict__ long_rows,
                                 int32_t* __restrict__ n_long) {
+  dep_enter();
   __shared__ T sm[WARPS_PER_BLOCK][WARP_SEG_MAX];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nl = *n_list;
@@ -260,6 +264,7 @@ __global__ void k_seg_sort_warp(const int32_t* __restrict__ seg_ptr, T* __restri
 template <class T, bool UNIQUE>
 __global__ void k_seg_sort_block(const int32_t* __restrict__ seg_ptr, T* __restrict__ keys,
                                  int32_t* __restrict__ count, const int32_t* __restrict__ long_rows) {
+  dep_enter();
   extern __shared__ __align__(16) unsigned char dyn[];
   T* a = reinterpret_cast<T*>(dyn);
   __shared__ int32_t wsum[32];
@@ -314,6 +319,7 @@ template <int M, class T, bool UNIQUE>
 __global__ void k_seg_sort_thread(const int32_t* __restrict__ seg_ptr, T* __restrict__ keys,
                                   int32_t* __restrict__ count, int rows, int32_t* __restrict__ defer,
                                   int32_t* __restrict__ n_defer) {
+  dep_enter();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   const int b = seg_ptr[r], len = seg_ptr[r + 1] - b;
@@ -351,12 +357,12 @@ bcs_status seg_sort(Solver* s, const int32_t* seg_ptr, T* keys, int32_t* count, 
   if (max_len > BLOCK_SEG_MAX)
     return s->fail(BCS_EINVAL, "a sparsity-pattern row has more than 16384 candidate entries");
   if (max_len <= 16) {
-    BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_thread<16, T, UNIQUE>), grid_for(rows, 128), 128, 0, seg_ptr, keys,
+    BCS_LAUNCH_DEP(s, K_MISC, 0, 0, (k_seg_sort_thread<16, T, UNIQUE>), grid_for(rows, 128), 128, 0, seg_ptr, keys,
                count, rows, (int32_t*)nullptr, (int32_t*)nullptr);
     return BCS_OK;
   }
   if (max_len <= 32) {
-    BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_thread<32, T, UNIQUE>), grid_for(rows, 128), 128, 0, seg_ptr, keys,
+    BCS_LAUNCH_DEP(s, K_MISC, 0, 0, (k_seg_sort_thread<32, T, UNIQUE>), grid_for(rows, 128), 128, 0, seg_ptr, keys,
                count, rows, (int32_t*)nullptr, (int32_t*)nullptr);
     return BCS_OK;
   }
@@ -367,10 +373,10 @@ bcs_status seg_sort(Solver* s, const int32_t* seg_ptr, T* keys, int32_t* count, 
   BCS_ALLOC(s, long_rows, rows);
   BCS_ALLOC(s, aux, 2);
   BCS_CU(s, cudaMemsetAsync(aux.p, 0, 2 * sizeof(int32_t), s->stream));
-  BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_thread<32, T, UNIQUE>), grid_for(rows, 128), 128, 0, seg_ptr, keys, count,
+  BCS_LAUNCH_DEP(s, K_MISC, 0, 0, (k_seg_sort_thread<32, T, UNIQUE>), grid_for(rows, 128), 128, 0, seg_ptr, keys, count,
              rows, mid_rows.p, aux.p);
   const unsigned gw = std::min<unsigned>(grid_for(rows, WARPS_PER_BLOCK), 2048u);
-  BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_warp<T, UNIQUE>), gw, 32 * WARPS_PER_BLOCK, 0, seg_ptr, keys, count,
+  BCS_LAUNCH_DEP(s, K_MISC, 0, 0, (k_seg_sort_warp<T, UNIQUE>), gw, 32 * WARPS_PER_BLOCK, 0, seg_ptr, keys, count,
              mid_rows.p, aux.p, long_rows.p, aux.p + 1);
   if (max_len > WARP_SEG_MAX) {
     int32_t h = 0;
@@ -382,7 +388,7 @@ bcs_status seg_sort(Solver* s, const int32_t* seg_ptr, T* keys, int32_t* count, 
       const size_t smem = (size_t)S * sizeof(T);
       BCS_CU(s, cudaFuncSetAttribute(k_seg_sort_block<T, UNIQUE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-      BCS_LAUNCH(s, K_MISC, 0, 0, (k_seg_sort_block<T, UNIQUE>), h, 512, smem, seg_ptr, keys, count, long_rows.p);
+      BCS_LAUNCH_DEP(s, K_MISC, 0, 0, (k_seg_sort_block<T, UNIQUE>), h, 512, smem, seg_ptr, keys, count, long_rows.p);
     }
   }
   return BCS_OK;

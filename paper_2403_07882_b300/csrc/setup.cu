@@ -46,6 +46,7 @@ __device__ __forceinline__ int find_col(const int32_t* __restrict__ ci, int b, i
 
 __global__ void k_diag_pos(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            int32_t* __restrict__ dpos, int32_t* __restrict__ err) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const int p = find_col(ci, rp[i], rp[i + 1], i);
@@ -57,6 +58,7 @@ template <int N>
 __global__ void __launch_bounds__(64) k_block_inverse(int rows, const int32_t* __restrict__ dpos,
                                                       const double* __restrict__ val, double* __restrict__ dinv,
                                                       int32_t* __restrict__ err) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const int dp = dpos[i];
@@ -72,6 +74,7 @@ __global__ void __launch_bounds__(64) k_block_inverse(int rows, const int32_t* _
 
 template <int NN>
 __global__ void k_block_norms(int nnz, const double* __restrict__ val, double* __restrict__ nrm) {
+  dep_enter();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nnz) return;
   const double* a = val + (size_t)k * NN;
@@ -82,6 +85,7 @@ __global__ void k_block_norms(int nnz, const double* __restrict__ val, double* _
 }
 
 __global__ void k_row_index(int rows, const int32_t* __restrict__ rp, int32_t* __restrict__ ridx) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   for (int k = rp[i]; k < rp[i + 1]; ++k) ridx[k] = i;
@@ -90,6 +94,7 @@ __global__ void k_row_index(int rows, const int32_t* __restrict__ rp, int32_t* _
 __global__ void k_weights(int nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                           const int32_t* __restrict__ ridx, const int32_t* __restrict__ dpos,
                           const double* __restrict__ nrm, double* __restrict__ w) {
+  dep_enter();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nnz) return;
   const int i = ridx[k], j = ci[k];
@@ -108,6 +113,7 @@ __global__ void k_weights(int nnz, const int32_t* __restrict__ rp, const int32_t
 __global__ void k_choose(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const double* __restrict__ w, const int32_t* __restrict__ mate,
                          int32_t* __restrict__ choice) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   int best = -1;
@@ -126,6 +132,7 @@ __global__ void k_choose(int rows, const int32_t* __restrict__ rp, const int32_t
 }
 
 __global__ void k_pair(int rows, const int32_t* __restrict__ choice, int32_t* __restrict__ mate) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const int c = choice[i];
@@ -135,6 +142,7 @@ __global__ void k_pair(int rows, const int32_t* __restrict__ choice, int32_t* __
 __global__ void k_root(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                        const double* __restrict__ w, const int32_t* __restrict__ mate,
                        int32_t* __restrict__ root, int32_t* __restrict__ amin) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   int r;
@@ -159,27 +167,32 @@ __global__ void k_root(int rows, const int32_t* __restrict__ rp, const int32_t* 
 
 __global__ void k_is_min(int rows, const int32_t* __restrict__ root, const int32_t* __restrict__ amin,
                          int32_t* __restrict__ flag) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < rows) flag[i] = amin[root[i]] == i ? 1 : 0;
 }
 
 __global__ void k_assign(int rows, const int32_t* __restrict__ root, const int32_t* __restrict__ amin,
                          const int32_t* __restrict__ id, int32_t* __restrict__ agg) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < rows) agg[i] = id[amin[root[i]]];
 }
 
 __global__ void k_compose(int rows, const int32_t* __restrict__ a2, int32_t* __restrict__ agg) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < rows) agg[i] = a2[agg[i]];
 }
 
 __global__ void k_fill_int(int32_t* __restrict__ a, int n, int v) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = v;
 }
 
 __global__ void k_count_by(int m, const int32_t* __restrict__ key, int32_t* __restrict__ cnt) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m) atomicAdd(&cnt[key[i]], 1);
 }
@@ -188,6 +201,7 @@ __global__ void k_count_by(int m, const int32_t* __restrict__ key, int32_t* __re
 __global__ void k_place_by(int m, const int32_t* __restrict__ key, const int32_t* __restrict__ val,
                            const int32_t* __restrict__ ptr, int32_t* __restrict__ cursor,
                            int32_t* __restrict__ out) {
+  dep_enter();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < m) out[ptr[key[q]] + atomicAdd(&cursor[key[q]], 1)] = val ? val[q] : q;
 }
@@ -195,6 +209,7 @@ __global__ void k_place_by(int m, const int32_t* __restrict__ key, const int32_t
 // Block-reduced maximum: one atomic per block (an atomic per element on one
 // address serialises millions of updates).
 __global__ void k_max_int(int n, const int32_t* __restrict__ a, int32_t* __restrict__ out) {
+  dep_enter();
   __shared__ int32_t wm[32];
   int v = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v = max(v, a[i]);
@@ -211,6 +226,7 @@ __global__ void k_max_int(int n, const int32_t* __restrict__ a, int32_t* __restr
 
 __global__ void k_compact(int rows, const int32_t* __restrict__ cptr, const int32_t* __restrict__ cand,
                           const int32_t* __restrict__ rp, int32_t* __restrict__ ci) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const int b = cptr[i], o = rp[i], len = rp[i + 1] - rp[i];
@@ -229,6 +245,7 @@ __global__ void k_compact(int rows, const int32_t* __restrict__ cptr, const int3
 __global__ void k_cand_count_tent(int nagg, const int32_t* __restrict__ mptr, const int32_t* __restrict__ mem,
                                   const int32_t* __restrict__ rp, int32_t* __restrict__ cnt, int32_t* __restrict__ moff,
                                   int32_t* __restrict__ mx) {
+  dep_enter();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   int c = 0;
   if (I < nagg)
@@ -249,6 +266,7 @@ __global__ void k_cand_count_tent(int nagg, const int32_t* __restrict__ mptr, co
 __global__ void k_cand_pack_tent(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                  const int32_t* __restrict__ agg, const int32_t* __restrict__ cptr,
                                  const int32_t* __restrict__ moff, uint64_t* __restrict__ cand) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const long long o = (long long)cptr[agg[i]] + moff[i] - rp[i];
@@ -286,6 +304,7 @@ constexpr int RC_BLOCKS = 148 * 8;
 __global__ void __launch_bounds__(256) k_runs_count(int rows, const int32_t* __restrict__ seg,
                                                     const uint64_t* __restrict__ cand, int32_t* __restrict__ cnt,
                                                     int32_t* __restrict__ mx) {
+  dep_enter();
   __shared__ int wm[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int best = 0;
@@ -316,6 +335,7 @@ constexpr int32_t TS_FIRST = INT32_MIN;
 
 __global__ void k_runs_emit(int rows, const int32_t* __restrict__ seg, const uint64_t* __restrict__ cand,
                             const int32_t* __restrict__ rp, int32_t* __restrict__ col, int32_t* __restrict__ sk) {
+  dep_enter();
   const int I = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (I >= rows) return;
   const int lane = threadIdx.x & 31;
@@ -365,6 +385,7 @@ __global__ void __launch_bounds__(TS_WARPS * 32) k_tent_sum(int nagg, const int3
                                                            const int32_t* __restrict__ sk,
                                                            const int32_t* __restrict__ crp,
                                                            const double* __restrict__ src, double* __restrict__ out) {
+  dep_enter();
   using S = TentShape<NN>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / S::W, e0 = lane - g * S::W;
@@ -425,6 +446,7 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
 template <int N>
 __global__ void k_rho(int rows, const int32_t* __restrict__ rp, const double* __restrict__ val,
                       const double* __restrict__ dinv, double* __restrict__ rho) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const double* D = dinv + (size_t)i * N * N;
@@ -447,12 +469,14 @@ __global__ void k_rho(int rows, const int32_t* __restrict__ rp, const double* __
 }
 
 __global__ void k_cand_count_p(int rows, const int32_t* __restrict__ rp, int32_t* __restrict__ cnt) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < rows) cnt[i] = rp[i + 1] - rp[i];
 }
 
 __global__ void k_cand_fill_p(int rows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                               const int32_t* __restrict__ agg, int32_t* __restrict__ cand) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   for (int k = rp[i]; k < rp[i + 1]; ++k) cand[k] = agg[ci[k]];
@@ -465,6 +489,7 @@ __global__ void k_p_values(int pnnz, const int32_t* __restrict__ prow, const int
                            const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const double* __restrict__ val, const double* __restrict__ dinv,
                            const int32_t* __restrict__ agg, double omega, double* __restrict__ pv) {
+  dep_enter();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= pnnz) return;
   const int i = prow[q], J = pci[q];
@@ -494,6 +519,7 @@ template <int N>
 __global__ void k_transpose_values(int rnnz, const int32_t* __restrict__ rrow, const int32_t* __restrict__ rci,
                                    const int32_t* __restrict__ prp, const int32_t* __restrict__ pci,
                                    const double* __restrict__ pv, double* __restrict__ rv) {
+  dep_enter();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= rnnz) return;
   const int J = rrow[q], i = rci[q];
@@ -507,6 +533,7 @@ __global__ void k_transpose_values(int rnnz, const int32_t* __restrict__ rrow, c
 // General block SpGEMM C = A B.
 __global__ void k_cand_count_gemm(int rows, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
                                   const int32_t* __restrict__ brp, int32_t* __restrict__ cnt) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   int c = 0;
@@ -517,6 +544,7 @@ __global__ void k_cand_count_gemm(int rows, const int32_t* __restrict__ arp, con
 __global__ void k_cand_fill_gemm(int rows, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
                                  const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
                                  const int32_t* __restrict__ cptr, int32_t* __restrict__ cand) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   int o = cptr[i];
@@ -534,6 +562,7 @@ __global__ void k_gemm_values(int cnnz, const int32_t* __restrict__ crow, const 
                               const double* __restrict__ av, const int32_t* __restrict__ brp,
                               const int32_t* __restrict__ bci, const double* __restrict__ bv,
                               double* __restrict__ cv) {
+  dep_enter();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= cnnz) return;
   const int i = crow[q], J = cci[q];
@@ -561,6 +590,7 @@ __global__ void k_gemm_values(int cnnz, const int32_t* __restrict__ crow, const 
 // ------------------------------------------------------------ coarse inverse
 __global__ void k_dense_from_bsr(int rows, int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                  const double* __restrict__ val, double* __restrict__ M, int N) {
+  dep_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const size_t W = 2 * (size_t)N;
@@ -582,6 +612,7 @@ __global__ void k_dense_from_bsr(int rows, int n, const int32_t* __restrict__ rp
 // k+1 in colbuf[(k + 1) & 1]; the pivot row is only read in step k.
 __global__ void k_gauss_jordan(int N, double* __restrict__ M, double* __restrict__ colbuf,
                                int32_t* __restrict__ prow_out, int32_t* __restrict__ err) {
+  dep_enter();
   cg::grid_group grid = cg::this_grid();
   extern __shared__ unsigned char used[];  // N flags
   __shared__ double red_v[32];
@@ -670,6 +701,7 @@ constexpr int GJ_SMEM_THREADS = 512;
 __global__ void __launch_bounds__(GJ_SMEM_THREADS) k_gauss_jordan_smem(int N, double* __restrict__ M,
                                                                        int32_t* __restrict__ prow_out,
                                                                        int32_t* __restrict__ err) {
+  dep_enter();
   extern __shared__ double sm[];  // N x 2N, then N used flags
   unsigned char* used = reinterpret_cast<unsigned char*>(sm + 2 * (size_t)N * N);
   __shared__ int s_p;
@@ -737,6 +769,7 @@ __global__ void __launch_bounds__(GJ_SMEM_THREADS) k_gauss_jordan_smem(int N, do
 
 __global__ void k_gj_finish(int N, const double* __restrict__ M, const int32_t* __restrict__ prow,
                             double* __restrict__ inv) {
+  dep_enter();
   const size_t W = 2 * (size_t)N;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)N * N;
        t += (size_t)gridDim.x * blockDim.x) {
@@ -761,7 +794,7 @@ bcs_status max_of(Solver* s, const int32_t* a, int n, int32_t* out) {
   DBuf<int32_t> m;
   BCS_ALLOC(s, m, 1);
   BCS_CU(s, cudaMemsetAsync(m.p, 0, sizeof(int32_t), s->stream));
-  if (n > 0) BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_max_int, grid_for(n, 256) < 1024 ? grid_for(n, 256) : 1024, 256, 0, n, a, m.p);
+  if (n > 0) BCS_LAUNCH_DEP(s, K_SETUP_GAL, 0, 0, k_max_int, grid_for(n, 256) < 1024 ? grid_for(n, 256) : 1024, 256, 0, n, a, m.p);
   return read_int(s, m.p, out);
 }
 
@@ -771,7 +804,7 @@ bcs_status total_and_max(Solver* s, const int32_t* d_total, const int32_t* a, in
   BCS_ALLOC(s, m, 2);
   BCS_CU(s, cudaMemsetAsync(m.p, 0, 2 * sizeof(int32_t), s->stream));
   if (n > 0)
-    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_max_int, grid_for(n, 256) < 1024 ? grid_for(n, 256) : 1024, 256, 0, n, a,
+    BCS_LAUNCH_DEP(s, K_SETUP_GAL, 0, 0, k_max_int, grid_for(n, 256) < 1024 ? grid_for(n, 256) : 1024, 256, 0, n, a,
                m.p + 1);
   BCS_CU(s, cudaMemcpyAsync(m.p, d_total, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->stream));
   BCS_CU(s, cudaMemcpyAsync(h, m.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
@@ -802,10 +835,10 @@ bcs_status pattern_from_candidates(Solver* s, int rows, DBuf<int32_t>& cnt, Fill
   out.nnz = nnz;
   out.maxrow = tm[1];
   BCS_ALLOC(s, out.ci, nnz > 0 ? nnz : 1);
-  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_compact, grid_for(rows, 256), 256, 0, rows, cptr.p, cand.p, out.rp.p,
+  BCS_LAUNCH_DEP(s, K_SETUP_GAL, 0, 0, k_compact, grid_for(rows, 256), 256, 0, rows, cptr.p, cand.p, out.rp.p,
              out.ci.p);
   BCS_ALLOC(s, crow, nnz > 0 ? nnz : 1);
-  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_row_index, grid_for(rows, 256), 256, 0, rows, out.rp.p, crow.p);
+  BCS_LAUNCH_DEP(s, K_SETUP_GAL, 0, 0, k_row_index, grid_for(rows, 256), 256, 0, rows, out.rp.p, crow.p);
   return BCS_OK;
 }
 
@@ -833,27 +866,27 @@ bcs_status match_pass(Solver* s, const Bsr& A, DBuf<int32_t>& agg, int* nagg, DB
   if (!norms) {
     BCS_OKR(with_n(s->n, [&](auto NC) -> bcs_status {
       constexpr int N = decltype(NC)::value;
-      BCS_LAUNCH(s, K_SETUP_AGG, 8.0 * nnz * (N * N + 1), 2.0 * nnz * N * N, k_block_norms<N * N>, gn, 256, 0, nnz,
+      BCS_LAUNCH_DEP(s, K_SETUP_AGG, 8.0 * nnz * (N * N + 1), 2.0 * nnz * N * N, k_block_norms<N * N>, gn, 256, 0, nnz,
                  A.v.p, nrm.p);
       return BCS_OK;
     }));
   }
-  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_row_index, gr, 256, 0, rows, A.rp.p, ridx.p);
-  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_diag_pos, gr, 256, 0, rows, A.rp.p, A.ci.p, dpos.p, s->flag.p);
-  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_weights, gn, 256, 0, nnz, A.rp.p, A.ci.p, ridx.p, dpos.p,
+  BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_row_index, gr, 256, 0, rows, A.rp.p, ridx.p);
+  BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_diag_pos, gr, 256, 0, rows, A.rp.p, A.ci.p, dpos.p, s->flag.p);
+  BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_weights, gn, 256, 0, nnz, A.rp.p, A.ci.p, ridx.p, dpos.p,
              norms ? norms : nrm.p, w.p);
-  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_fill_int, gr, 256, 0, mate.p, rows, -1);
+  BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_fill_int, gr, 256, 0, mate.p, rows, -1);
   // A round that pairs nobody leaves the state unchanged, so running every
   // round equals stopping at the first idle one.
   for (int round = 0; round < s->setup_cfg.matching_rounds; ++round) {
-    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_choose, gr, 256, 0, rows, A.rp.p, A.ci.p, w.p, mate.p, choice.p);
-    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_pair, gr, 256, 0, rows, choice.p, mate.p);
+    BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_choose, gr, 256, 0, rows, A.rp.p, A.ci.p, w.p, mate.p, choice.p);
+    BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_pair, gr, 256, 0, rows, choice.p, mate.p);
   }
-  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_fill_int, gr, 256, 0, amin.p, rows, INT_MAX);
-  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_root, gr, 256, 0, rows, A.rp.p, A.ci.p, w.p, mate.p, root.p, amin.p);
-  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_is_min, gr, 256, 0, rows, root.p, amin.p, flag.p);
+  BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_fill_int, gr, 256, 0, amin.p, rows, INT_MAX);
+  BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_root, gr, 256, 0, rows, A.rp.p, A.ci.p, w.p, mate.p, root.p, amin.p);
+  BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_is_min, gr, 256, 0, rows, root.p, amin.p, flag.p);
   BCS_OKR(exclusive_scan(s, flag.p, id.p, rows));
-  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_assign, gr, 256, 0, rows, root.p, amin.p, id.p, agg.p);
+  BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_assign, gr, 256, 0, rows, root.p, amin.p, id.p, agg.p);
   // member counts (aggregate ids are < rows) and their maximum, read with
   // the aggregate count in one round trip
   BCS_ALLOC(s, cnt, rows);
@@ -861,8 +894,8 @@ bcs_status match_pass(Solver* s, const Bsr& A, DBuf<int32_t>& agg, int* nagg, DB
   BCS_ALLOC(s, hv, 2);
   BCS_CU(s, cudaMemsetAsync(cnt.p, 0, (size_t)rows * sizeof(int32_t), s->stream));
   BCS_CU(s, cudaMemsetAsync(hv.p, 0, 2 * sizeof(int32_t), s->stream));
-  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_count_by, gr, 256, 0, rows, agg.p, cnt.p);
-  BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_max_int, gr < 1024 ? gr : 1024, 256, 0, rows, cnt.p, hv.p + 1);
+  BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_count_by, gr, 256, 0, rows, agg.p, cnt.p);
+  BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_max_int, gr < 1024 ? gr : 1024, 256, 0, rows, cnt.p, hv.p + 1);
   BCS_CU(s, cudaMemcpyAsync(hv.p, id.p + rows, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->stream));
   int32_t h[2] = {0, 0};
   BCS_CU(s, cudaMemcpyAsync(h, hv.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
@@ -883,7 +916,7 @@ bcs_status members(Solver* s, int rows, int nagg, const int32_t* agg, int32_t* c
   BCS_CU(s, cudaMemsetAsync(cursor.p, 0, nagg * sizeof(int32_t), s->stream));
   if (mx > 4096) BCS_OKR(max_of(s, cnt, nagg, &mx));  // a loose bound: the sort wants the real length
   BCS_OKR(exclusive_scan(s, cnt, mptr.p, nagg));
-  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_place_by, grid_for(rows, 256), 256, 0, rows, agg, (const int32_t*)nullptr,
+  BCS_LAUNCH_DEP(s, K_SETUP_GAL, 0, 0, k_place_by, grid_for(rows, 256), 256, 0, rows, agg, (const int32_t*)nullptr,
              mptr.p, cursor.p, mem.p);
   // members are distinct: sort/unique keeps the counts and sorts each list
   return segmented_sort_unique(s, mptr.p, mem.p, cnt, nagg, mx);
@@ -904,7 +937,7 @@ bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, c
   BCS_ALLOC(s, hv, 4);
   BCS_ALLOC(s, moff, A.rows);
   BCS_CU(s, cudaMemsetAsync(hv.p, 0, 4 * sizeof(int32_t), s->stream));
-  BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p, cnt.p,
+  BCS_LAUNCH_DEP(s, K_SETUP_GAL, 0, 0, k_cand_count_tent, grid_for(nagg, 256), 256, 0, nagg, mptr, mem, A.rp.p, cnt.p,
              moff.p, hv.p + 1);
   BCS_OKR(exclusive_scan(s, cnt.p, plan.seg.p, nagg));
   int32_t h[2] = {0, 0};
@@ -919,10 +952,10 @@ bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, c
   DBuf<uint64_t> cand;
   BCS_ALLOC(s, cand, A.nnz);
   BCS_ALLOC(s, plan.sk, A.nnz);
-  BCS_LAUNCH(s, K_SETUP_GAL, 16.0 * A.nnz, 0, k_cand_pack_tent, grid_for(A.rows, 256), 256, 0, A.rows, A.rp.p,
+  BCS_LAUNCH_DEP(s, K_SETUP_GAL, 16.0 * A.nnz, 0, k_cand_pack_tent, grid_for(A.rows, 256), 256, 0, A.rows, A.rp.p,
              A.ci.p, agg, plan.seg.p, moff.p, cand.p);
   BCS_OKR(segmented_sort64(s, plan.seg.p, cand.p, nagg, max_c));
-  BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_runs_count, std::min<unsigned>(grid_for(nagg, 8), RC_BLOCKS), 256,
+  BCS_LAUNCH_DEP(s, K_SETUP_GAL, 12.0 * A.nnz, 0, k_runs_count, std::min<unsigned>(grid_for(nagg, 8), RC_BLOCKS), 256,
              0, nagg, plan.seg.p, cand.p,
              cnt.p, hv.p + 3);
   BCS_ALLOC(s, Ac.rp, nagg + 1);
@@ -934,7 +967,7 @@ bcs_status tent_pattern(Solver* s, const Bsr& A, int nagg, const int32_t* agg, c
   Ac.nnz = h[0];
   Ac.maxrow = h[1];
   BCS_ALLOC(s, Ac.ci, Ac.nnz);
-  BCS_LAUNCH(s, K_SETUP_GAL, 12.0 * A.nnz + 4.0 * Ac.nnz, 0, k_runs_emit, grid_for((size_t)nagg * 32, 256), 256, 0,
+  BCS_LAUNCH_DEP(s, K_SETUP_GAL, 12.0 * A.nnz + 4.0 * Ac.nnz, 0, k_runs_emit, grid_for((size_t)nagg * 32, 256), 256, 0,
              nagg, plan.seg.p, cand.p, Ac.rp.p, Ac.ci.p, plan.sk.p);
   return BCS_OK;
 }
@@ -948,7 +981,7 @@ bcs_status tent_values(Solver* s, const Bsr& A, const TentPlan& plan, Bsr& Ac) {
     if ((size_t)Ac.nnz * N * N >= (1ull << 31)) return s->fail(BCS_EINVAL, "Galerkin product too large");
     const int nagg = Ac.rows;
     const unsigned grid = grid_for(nagg, TS_WARPS * S::G);
-    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + Ac.nnz) * N * N + 4.0 * A.nnz + 4.0 * (nagg + 1) * 2,
+    BCS_LAUNCH_DEP(s, K_SETUP_GAL, 8.0 * (A.nnz + Ac.nnz) * N * N + 4.0 * A.nnz + 4.0 * (nagg + 1) * 2,
                1.0 * (A.nnz - Ac.nnz) * N * N, k_tent_sum<N * N>, grid, TS_WARPS * 32, 0, nagg, plan.seg.p,
                plan.sk.p, Ac.rp.p, A.v.p, Ac.v.p);
     return BCS_OK;
@@ -979,7 +1012,7 @@ bcs_status aggregate_level(Solver* s, Level& L, const double* norms) {
     // an aggregate of aggregates has at most the product of the largest
     // sizes (an upper bound is all the sorts need)
     maxmem = (int)std::min<long long>((long long)maxmem * mm2, L.A.rows);
-    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_compose, grid_for(L.A.rows, 256), 256, 0, L.A.rows, a2.p, L.agg.p);
+    BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_compose, grid_for(L.A.rows, 256), 256, 0, L.A.rows, a2.p, L.agg.p);
     cur_agg = std::move(a2);
     const bool stalled = n2 == nagg;
     nagg = n2;
@@ -992,7 +1025,7 @@ bcs_status aggregate_level(Solver* s, Level& L, const double* norms) {
   // the graph was coarsened in between; maxmem is then an upper bound)
   if (cur != &L.A) {
     BCS_CU(s, cudaMemsetAsync(cnt.p, 0, (size_t)nagg * sizeof(int32_t), s->stream));
-    BCS_LAUNCH(s, K_SETUP_AGG, 0, 0, k_count_by, grid_for(L.A.rows, 256), 256, 0, L.A.rows, L.agg.p, cnt.p);
+    BCS_LAUNCH_DEP(s, K_SETUP_AGG, 0, 0, k_count_by, grid_for(L.A.rows, 256), 256, 0, L.A.rows, L.agg.p, cnt.p);
   }
   L.cnt = std::move(cnt);
   L.maxmem = maxmem;
@@ -1003,13 +1036,13 @@ bcs_status block_inverses(Solver* s, Level& L, bool full, bool allocated = false
   const int rows = L.A.rows, n = s->n;
   if (full || !L.dpos.p) {
     if (!allocated) BCS_ALLOC(s, L.dpos, rows);
-    BCS_LAUNCH(s, K_SETUP_INV, 0, 0, k_diag_pos, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, L.A.ci.p,
+    BCS_LAUNCH_DEP(s, K_SETUP_INV, 0, 0, k_diag_pos, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, L.A.ci.p,
                L.dpos.p, s->flag.p);
   }
   if (!allocated) BCS_ALLOC(s, L.dinv, (size_t)rows * n * n);
   return with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    BCS_LAUNCH(s, K_SETUP_INV, 16.0 * rows * N * N, 4.0 * rows * N * N * N, k_block_inverse<N>,
+    BCS_LAUNCH_DEP(s, K_SETUP_INV, 16.0 * rows * N * N, 4.0 * rows * N * N * N, k_block_inverse<N>,
                grid_for(rows, 64), 64, 0, rows, L.dpos.p, L.A.v.p, L.dinv.p, s->flag.p);
     return BCS_OK;
   });
@@ -1028,14 +1061,14 @@ bcs_status coarse_inverse(Solver* s, Level& L) {
   BCS_ALLOC(s, colbuf, 2 * (size_t)N);
   BCS_ALLOC(s, prow, N);
   BCS_ALLOC(s, s->cinv, (size_t)N * N);
-  BCS_LAUNCH(s, K_SETUP_INV, 0, 0, k_dense_from_bsr, grid_for(L.A.rows, 64), 64, 0, L.A.rows, s->n, L.A.rp.p,
+  BCS_LAUNCH_DEP(s, K_SETUP_INV, 0, 0, k_dense_from_bsr, grid_for(L.A.rows, 64), 64, 0, L.A.rows, s->n, L.A.rp.p,
              L.A.ci.p, L.A.v.p, M.p, N);
   if (N <= GJ_SMEM_MAX_N) {
     // [A | I] fits one block's shared memory: no grid-wide barriers, no L2
     // round trip per pivot step
     const size_t smem = 16 * (size_t)N * N + N;
     BCS_CU(s, cudaFuncSetAttribute(k_gauss_jordan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    BCS_LAUNCH(s, K_SETUP_INV, 24.0 * N * N * N, 3.0 * N * N * N, k_gauss_jordan_smem, 1, GJ_SMEM_THREADS, smem, N,
+    BCS_LAUNCH_DEP(s, K_SETUP_INV, 24.0 * N * N * N, 3.0 * N * N * N, k_gauss_jordan_smem, 1, GJ_SMEM_THREADS, smem, N,
                M.p, prow.p, s->flag.p);
   } else {
     int dev = 0, sms = 0, per_sm = 0;
@@ -1057,7 +1090,7 @@ bcs_status coarse_inverse(Solver* s, Level& L) {
     BCS_CU(s, cudaLaunchCooperativeKernel((void*)k_gauss_jordan, blocks, threads, args, smem, s->stream));
     BCS_OKR(s->post(K_SETUP_INV, "k_gauss_jordan", 24.0 * N * N * N, 3.0 * N * N * N));
   }
-  BCS_LAUNCH(s, K_SETUP_INV, 0, 0, k_gj_finish, grid_for((size_t)N * N, 256), 256, 0, N, M.p, prow.p,
+  BCS_LAUNCH_DEP(s, K_SETUP_INV, 0, 0, k_gj_finish, grid_for((size_t)N * N, 256), 256, 0, N, M.p, prow.p,
              s->cinv.p);
   return BCS_OK;
 }
@@ -1078,21 +1111,21 @@ bcs_status transpose_P(Solver* s, Level& L, bool full) {
     BCS_ALLOC(s, R.ci, R.nnz);
     BCS_CU(s, cudaMemsetAsync(rcnt.p, 0, L.nagg * sizeof(int32_t), s->stream));
     BCS_CU(s, cudaMemsetAsync(cursor.p, 0, L.nagg * sizeof(int32_t), s->stream));
-    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_count_by, grid_for(P.nnz, 256), 256, 0, P.nnz, P.ci.p, rcnt.p);
+    BCS_LAUNCH_DEP(s, K_SETUP_GAL, 0, 0, k_count_by, grid_for(P.nnz, 256), 256, 0, P.nnz, P.ci.p, rcnt.p);
     BCS_OKR(exclusive_scan(s, rcnt.p, R.rp.p, L.nagg));
-    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_place_by, grid_for(P.nnz, 256), 256, 0, P.nnz, P.ci.p, L.Prow.p, R.rp.p,
+    BCS_LAUNCH_DEP(s, K_SETUP_GAL, 0, 0, k_place_by, grid_for(P.nnz, 256), 256, 0, P.nnz, P.ci.p, L.Prow.p, R.rp.p,
                cursor.p, R.ci.p);
     int32_t mx = 0;
     BCS_OKR(max_of(s, rcnt.p, L.nagg, &mx));
     BCS_OKR(segmented_sort_unique(s, R.rp.p, R.ci.p, rcnt.p, L.nagg, mx));
     BCS_ALLOC(s, L.Rrow, R.nnz);
-    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_row_index, grid_for(L.nagg, 256), 256, 0, L.nagg, R.rp.p, L.Rrow.p);
+    BCS_LAUNCH_DEP(s, K_SETUP_GAL, 0, 0, k_row_index, grid_for(L.nagg, 256), 256, 0, L.nagg, R.rp.p, L.Rrow.p);
   }
   const int n = s->n;
   BCS_ALLOC(s, R.v, (size_t)R.nnz * n * n);
   return with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    BCS_LAUNCH(s, K_SETUP_GAL, 16.0 * R.nnz * N * N, 0, k_transpose_values<N>, grid_for(R.nnz, 128), 128, 0,
+    BCS_LAUNCH_DEP(s, K_SETUP_GAL, 16.0 * R.nnz * N * N, 0, k_transpose_values<N>, grid_for(R.nnz, 128), 128, 0,
                R.nnz, L.Rrow.p, R.ci.p, P.rp.p, P.ci.p, P.v.p, R.v.p);
     return BCS_OK;
   });
@@ -1106,7 +1139,7 @@ bcs_status smoothed_prolongation(Solver* s, Level& L, bool full) {
   BCS_CU(s, cudaMemsetAsync(rho.p, 0, sizeof(double), s->stream));
   BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * L.A.nnz * N * N, 2.0 * L.A.nnz * N * N * N, k_rho<N>, grid_for(rows, 128),
+    BCS_LAUNCH_DEP(s, K_SETUP_GAL, 8.0 * L.A.nnz * N * N, 2.0 * L.A.nnz * N * N * N, k_rho<N>, grid_for(rows, 128),
                128, 0, rows, L.A.rp.p, L.A.v.p, L.dinv.p, rho.p);
     return BCS_OK;
   }));
@@ -1117,10 +1150,10 @@ bcs_status smoothed_prolongation(Solver* s, Level& L, bool full) {
   if (full) {
     DBuf<int32_t> cnt;
     BCS_ALLOC(s, cnt, rows);
-    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_p, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, cnt.p);
+    BCS_LAUNCH_DEP(s, K_SETUP_GAL, 0, 0, k_cand_count_p, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, cnt.p);
     auto fill = [&](const int32_t*, int32_t* cand) -> bcs_status {
       // candidate segments coincide with A's rows
-      BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_fill_p, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, L.A.ci.p,
+      BCS_LAUNCH_DEP(s, K_SETUP_GAL, 0, 0, k_cand_fill_p, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, L.A.ci.p,
                  L.agg.p, cand);
       return BCS_OK;
     };
@@ -1131,7 +1164,7 @@ bcs_status smoothed_prolongation(Solver* s, Level& L, bool full) {
   const double om = L.omega_p;
   BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (L.A.nnz + L.P.nnz) * N * N, 2.0 * L.P.nnz * N * N * N, k_p_values<N>,
+    BCS_LAUNCH_DEP(s, K_SETUP_GAL, 8.0 * (L.A.nnz + L.P.nnz) * N * N, 2.0 * L.P.nnz * N * N * N, k_p_values<N>,
                grid_for(L.P.nnz, 128), 128, 0, L.P.nnz, L.Prow.p, L.P.ci.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.dinv.p,
                L.agg.p, om, L.P.v.p);
     return BCS_OK;
@@ -1145,10 +1178,10 @@ bcs_status spgemm(Solver* s, const Bsr& A, const Bsr& B, Bsr& Cm, DBuf<int32_t>&
   if (full) {
     DBuf<int32_t> cnt;
     BCS_ALLOC(s, cnt, rows);
-    BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_count_gemm, grid_for(rows, 256), 256, 0, rows, A.rp.p, A.ci.p, B.rp.p,
+    BCS_LAUNCH_DEP(s, K_SETUP_GAL, 0, 0, k_cand_count_gemm, grid_for(rows, 256), 256, 0, rows, A.rp.p, A.ci.p, B.rp.p,
                cnt.p);
     auto fill = [&](const int32_t* cptr, int32_t* cand) -> bcs_status {
-      BCS_LAUNCH(s, K_SETUP_GAL, 0, 0, k_cand_fill_gemm, grid_for(rows, 256), 256, 0, rows, A.rp.p, A.ci.p,
+      BCS_LAUNCH_DEP(s, K_SETUP_GAL, 0, 0, k_cand_fill_gemm, grid_for(rows, 256), 256, 0, rows, A.rp.p, A.ci.p,
                  B.rp.p, B.ci.p, cptr, cand);
       return BCS_OK;
     };
@@ -1158,7 +1191,7 @@ bcs_status spgemm(Solver* s, const Bsr& A, const Bsr& B, Bsr& Cm, DBuf<int32_t>&
   BCS_ALLOC(s, Cm.v, (size_t)Cm.nnz * n * n);
   return with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    BCS_LAUNCH(s, K_SETUP_GAL, 8.0 * (A.nnz + Cm.nnz) * N * N, 0, k_gemm_values<N>, grid_for(Cm.nnz, 64), 64, 0,
+    BCS_LAUNCH_DEP(s, K_SETUP_GAL, 8.0 * (A.nnz + Cm.nnz) * N * N, 0, k_gemm_values<N>, grid_for(Cm.nnz, 64), 64, 0,
                Cm.nnz, crow.p, Cm.ci.p, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, Cm.v.p);
     return BCS_OK;
   });

@@ -1,6 +1,6 @@
 """The committed ncu summaries stay in step with the kernels: every entry
-of profiles/traffic.json names an existing kernel whose source text still
-hashes to the captured digest (a changed kernel must be profiled again
+of profiles/traffic.json names an existing kernel whose source text (device
+body and launching wrapper) still hashes to the captured digest (a changed kernel must be profiled again
 before its DRAM traffic is reported), and every summary gives the command
 that produced it."""
 import glob
@@ -16,8 +16,7 @@ def test_traffic_entries_match_current_kernels():
     entries = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     assert entries
     for name, e in entries.items():
-        digest = bench.kernel_source_digest(os.path.join(ROOT, e["source"]), e["function"])
-        assert digest == e["sha256"], f"{name}: kernel changed since its ncu capture"
+        assert bench.entry_digest(e) == e["sha256"], f"{name}: kernel changed since its ncu capture"
         assert 0.5 < e["dram_over_algorithmic"] < 2.0
         assert bench.measured_traffic(name, 1.0e9) == e["dram_over_algorithmic"] * 1.0e9
 
