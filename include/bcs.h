@@ -132,6 +132,9 @@ typedef struct bcs_config {
                               any data), which hides part of the launch gap between the many
                               short kernels of the coarse levels; 0: ordinary launches.
                               Identical results either way */
+  int x0_zero;             /* 1: bcs_solve / bcs_solve_batch ignore the values x holds on entry
+                              and start from x = 0 (with host memory x is then only written,
+                              not copied to the device); 0 (default): x holds the initial guess */
   /* Device memory, read by bcs_create (later changes are ignored): with alloc
      and release both set, every device buffer of the solver comes from
      alloc(bytes, stream, alloc_user) and goes back through release(ptr,
@@ -416,6 +419,11 @@ BCS_API bcs_status bcs_server_wait(bcs_server* srv, int64_t ticket, int timeout_
 BCS_API bcs_status bcs_server_set_batch(bcs_server* srv, int max_batch);
 BCS_API bcs_status bcs_server_get_stats(bcs_server* srv, bcs_server_stats* st);
 BCS_API bcs_status bcs_server_reset_stats(bcs_server* srv);
+/* The message of the most recent request that failed with BCS_ECUDA,
+ * BCS_ENOMEM, BCS_SINGULAR_BLOCK or BCS_EINVAL (the case's device state is
+ * dropped after such a failure, its solver's message with it), NUL
+ * terminated and truncated to len bytes; "" when none failed. */
+BCS_API bcs_status bcs_server_last_error(bcs_server* srv, char* buf, size_t len);
 
 /* Allocation-free block-CSR structure build (the paper has no counterpart).
  * For callers that cannot let a library allocate device memory: programs that

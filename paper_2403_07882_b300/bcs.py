@@ -41,7 +41,8 @@ class bcs_config(ct.Structure):
         ("p_omega", ct.c_double), ("coarse_dense_max", ct.c_int), ("coarse_sweeps", ct.c_int),
         ("precision", ct.c_int), ("smoother", ct.c_int), ("profile", ct.c_int), ("profile_kinds", ct.c_int),
         ("slice_layout", ct.c_int), ("cycle_graph", ct.c_int), ("reorder", ct.c_int), ("tail_rows", ct.c_int),
-        ("dilu_cluster_rows", ct.c_int), ("dependent_launch", ct.c_int), ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_user", ct.c_void_p),
+        ("dilu_cluster_rows", ct.c_int), ("dependent_launch", ct.c_int), ("x0_zero", ct.c_int),
+        ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_user", ct.c_void_p),
     ]
 
 
@@ -144,6 +145,7 @@ def lib():
             "bcs_server_get_stats": (ct.c_int, [_vp, ct.POINTER(bcs_server_stats)]),
             "bcs_server_set_batch": (ct.c_int, [_vp, ct.c_int]),
             "bcs_server_reset_stats": (ct.c_int, [_vp]),
+            "bcs_server_last_error": (ct.c_int, [_vp, ct.c_char_p, ct.c_size_t]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -162,7 +164,8 @@ def exported_names():
             "bcs_get_coarse_inverse", "bcs_get_dilu", "bcs_get_stats", "bcs_reset_stats", "bcs_get_kernel_times", "bcs_kernel_kind_name",
             "bcs_get_level_times", "bcs_last_error", "bcs_device_bytes", "bcs_ldu_structure_noalloc", "bcs_server_create",
             "bcs_server_destroy", "bcs_server_register_case", "bcs_server_submit", "bcs_server_wait",
-            "bcs_server_get_stats", "bcs_server_reset_stats", "bcs_server_set_batch"]
+            "bcs_server_get_stats", "bcs_server_reset_stats", "bcs_server_set_batch",
+            "bcs_server_last_error"]
 
 
 # ------------------------------------------------------------ marshalling
@@ -840,8 +843,14 @@ class Server:
             arrs = [np.ascontiguousarray(a, np.float64) for a in arrs]
             if x is None:
                 x = np.zeros_like(arrs[3])
-        elif x is None:
-            x = arrs[3].new_zeros(arrs[3].shape)
+        else:
+            if x is None:
+                x = arrs[3].new_zeros(arrs[3].shape)
+            # the request runs on the case's own stream, which does not wait
+            # for the caller's: the arrays (and the zeros just queued) must be
+            # complete when the request is submitted
+            import torch
+            torch.cuda.current_stream(arrs[3].device).synchronize()
         t = bcs_server_submit(self.h, case_id, *arrs, x)
         self._keep[t] = (arrs, x)
         return t
@@ -858,3 +867,9 @@ class Server:
 
     def stats(self):
         return bcs_server_get_stats(self.h)
+
+    def last_error(self):
+        """Message of the most recent failed request ("" when none failed)."""
+        buf = ct.create_string_buffer(1024)
+        lib().bcs_server_last_error(self.h, buf, len(buf))
+        return buf.value.decode()

@@ -126,6 +126,7 @@ bcs_status check_config(const bcs_config* c) {
   if (c->tail_rows < 0) return BCS_EINVAL;
   if (c->dilu_cluster_rows < 0) return BCS_EINVAL;
   if (c->dependent_launch < 0 || c->dependent_launch > 1) return BCS_EINVAL;
+  if (c->x0_zero < 0 || c->x0_zero > 1) return BCS_EINVAL;
   if ((c->alloc == nullptr) != (c->release == nullptr)) return BCS_EINVAL;
   if (c->slice_layout < -1 || c->slice_layout > 1) return BCS_EINVAL;
   if (c->smoother < BCS_SMOOTH_JACOBI || c->smoother > BCS_SMOOTH_SGS) return BCS_EINVAL;
@@ -175,7 +176,9 @@ bcs_status values_changed(Solver* s, std::chrono::steady_clock::time_point t0) {
   if (full) s->setup_cfg = s->cfg;
   s->have_hierarchy = false;
   BCS_OKR(amg_setup(s, full));
-  BCS_OKR(cycle_prepare(s));
+  // a values-only resetup rewrites every buffer in place (same sizes, same
+  // addresses), so the captured cycle and Krylov graphs stay valid
+  BCS_OKR(cycle_prepare(s, !full));
   BCS_CU(s, cudaStreamSynchronize(s->stream));
   s->have_hierarchy = true;
   s->last_setup_ms = ms_since(t0);
@@ -216,6 +219,7 @@ bcs_status bcs_config_default(bcs_config* c) {
   c->tail_rows = 0;
   c->dilu_cluster_rows = 4096;
   c->dependent_launch = 1;
+  c->x0_zero = 0;
   return BCS_OK;
 }
 
@@ -603,10 +607,16 @@ bcs_status bcs_solve_batch(bcs_solver* const* solvers, int count, const double* 
       BCS_ALLOC(s, s->kb, N);
       BCS_ALLOC(s, s->kx, N);
       BCS_CU(s, cudaMemcpyAsync(s->kb.p, b[i], N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-      BCS_CU(s, cudaMemcpyAsync(s->kx.p, x[i], N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+      if (!s->cfg.x0_zero)
+        BCS_CU(s, cudaMemcpyAsync(s->kx.p, x[i], N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
       BCS_CU(s, cudaStreamSynchronize(s->stream));
       bd[i] = s->kb.p;
       xd[i] = s->kx.p;
+    }
+    if (ss[i]->cfg.x0_zero) {
+      Solver* s = ss[i];
+      BCS_CU(s, cudaMemsetAsync(xd[i], 0, (size_t)s->C * s->n * sizeof(double), s->stream));
+      BCS_CU(s, cudaStreamSynchronize(s->stream));
     }
   }
   BCS_OKR(solve_batch(ss.data(), count, bd.data(), xd.data(), res));
@@ -637,10 +647,12 @@ bcs_status bcs_solve(bcs_solver* h, const double* b, double* x, int mem, bcs_res
     BCS_ALLOC(s, s->kb, N);
     BCS_ALLOC(s, s->kx, N);
     BCS_CU(s, cudaMemcpyAsync(s->kb.p, b, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    BCS_CU(s, cudaMemcpyAsync(s->kx.p, x, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    if (!s->cfg.x0_zero)
+      BCS_CU(s, cudaMemcpyAsync(s->kx.p, x, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     bd = s->kb.p;
     xd = s->kx.p;
   }
+  if (s->cfg.x0_zero) BCS_CU(s, cudaMemsetAsync(xd, 0, N * sizeof(double), s->stream));
   double* xu = xd;  // x in the caller's numbering on the device
   if (s->reordered) {
     BCS_ALLOC(s, s->rb, N);

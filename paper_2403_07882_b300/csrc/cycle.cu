@@ -1572,8 +1572,8 @@ bcs_status build_tail(Solver* s) {
   return BCS_OK;
 }
 
-bcs_status cycle_prepare(Solver* s) {
-  s->drop_graph();
+bcs_status cycle_prepare(Solver* s, bool keep_graphs) {
+  if (!keep_graphs) s->drop_graph();
   const int prec = s->setup_cfg.precision;
   const size_t vsz = prec == BCS_PREC_FP64 ? sizeof(double) : sizeof(float);
   const int n = s->n, nn = n * n;

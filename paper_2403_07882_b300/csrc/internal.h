@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <utility>
@@ -402,8 +403,35 @@ __device__ __forceinline__ void dep_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// The dynamic shared-memory limit of a kernel is state of the process, not
+// of a launch: raising it to the device's opt-in maximum (less the kernel's
+// static shared memory) once, thread-safe,
+// lets every launch ask for what it needs without racing other threads that
+// set the limit for their own launches.
+template <auto kernel>
+cudaError_t allow_max_dynamic_smem() {
+  static std::once_flag once;  // one per kernel
+  static cudaError_t result = cudaSuccess;
+  std::call_once(once, [&] {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    result = cudaGetDevice(&dev);
+    if (result == cudaSuccess) result = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (result == cudaSuccess) result = cudaFuncGetAttributes(&fa, kernel);
+    // the limit covers the dynamic part; the kernel's static shared memory
+    // counts against the same per-block maximum
+    if (result == cudaSuccess)
+      result = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin - (int)fa.sharedSizeBytes);
+    if (result != cudaSuccess) (void)cudaGetLastError();
+  });
+  return result;
+}
+
 // BCS_LAUNCH with the programmatic-serialization attribute (when
-// cfg.dependent_launch is set); the kernel must begin with dep_enter().
+// cfg.dependent_launch is set); the kernel must begin with dep_enter(). A
+// failed launch clears the thread's last-error state, so that no later
+// launch reports it as its own.
 #define BCS_LAUNCH_DEP(S, KIND, BYTES, FLOPS, kernel, grid, block, smem, ...)                       \
   do {                                                                                              \
     (S)->pre(KIND);                                                                                 \
@@ -418,7 +446,10 @@ __device__ __forceinline__ void dep_enter() {
     lc_.attrs = at_;                                                                                \
     lc_.numAttrs = (S)->cfg.dependent_launch ? 1 : 0;                                               \
     const cudaError_t le_ = cudaLaunchKernelEx(&lc_, kernel, __VA_ARGS__);                          \
-    if (le_ != cudaSuccess) return (S)->fail(BCS_ECUDA, std::string(#kernel) + ": " + cudaGetErrorString(le_)); \
+    if (le_ != cudaSuccess) {                                                                       \
+      (void)cudaGetLastError();                                                                     \
+      return (S)->fail(BCS_ECUDA, std::string(#kernel) + ": " + cudaGetErrorString(le_));           \
+    }                                                                                               \
     bcs_status st_ = (S)->post(KIND, #kernel, (BYTES), (FLOPS));                                    \
     if (st_ != BCS_OK) return st_;                                                                  \
   } while (0)
@@ -565,7 +596,9 @@ enum Mode { M_SPMV = 0, M_ADD = 1, M_RESID = 2 };
 // y = A x (b == nullptr) or y = b - A x with the FP64 matrix; x double or float.
 bcs_status spmv64(Solver* s, const Bsr& A, const void* x, bool x_is_float, double* y,
                   const double* b, int kind);
-bcs_status cycle_prepare(Solver* s);
+// keep_graphs: a values-only resetup (every buffer kept in place), so the
+// captured graphs stay valid; otherwise they are dropped.
+bcs_status cycle_prepare(Solver* s, bool keep_graphs = false);
 bcs_status precond_apply(Solver* s, const double* v, void* z);  // z in cycle precision
 bcs_status jacobi_apply(Solver* s, const double* v, double* z);
 bcs_status sgs_apply(Solver* s, const double* v, void* z);  // z in cycle precision

@@ -386,8 +386,8 @@ bcs_status seg_sort(Solver* s, const int32_t* seg_ptr, T* keys, int32_t* count, 
       int S = 32;
       while (S < max_len) S <<= 1;
       const size_t smem = (size_t)S * sizeof(T);
-      BCS_CU(s, cudaFuncSetAttribute(k_seg_sort_block<T, UNIQUE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+      constexpr auto kseg = k_seg_sort_block<T, UNIQUE>;
+      BCS_CU(s, allow_max_dynamic_smem<kseg>());
       BCS_LAUNCH_DEP(s, K_MISC, 0, 0, (k_seg_sort_block<T, UNIQUE>), h, 512, smem, seg_ptr, keys, count, long_rows.p);
     }
   }

@@ -18,6 +18,7 @@
 #include <condition_variable>
 #include <deque>
 #include <memory>
+#include <cstdio>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -78,6 +79,7 @@ struct bcs_server {
   cudaStream_t tstream = nullptr;
   std::vector<std::thread> workers;
   int device = 0;
+  std::string last_error;  // message of the most recent failed request (guarded by mu)
 };
 
 namespace {
@@ -235,6 +237,7 @@ void serve_batch(bcs_server* srv, const std::vector<Request>& reqs) {
         (void)cudaGetLastError();
     }
     if (st[i] == BCS_ECUDA || st[i] == BCS_ENOMEM || st[i] == BCS_SINGULAR_BLOCK || st[i] == BCS_EINVAL) {
+      srv->last_error = c.solver ? bcs_last_error(c.solver) : "solver creation failed";
       srv->resident -= c.bytes;
       c.bytes = 0;
       drop_device_state(c);
@@ -338,6 +341,7 @@ void worker(bcs_server* srv) {
         (void)cudaGetLastError();
     }
     if (st == BCS_ECUDA || st == BCS_ENOMEM || st == BCS_SINGULAR_BLOCK || st == BCS_EINVAL) {
+      srv->last_error = c.solver ? bcs_last_error(c.solver) : "solver creation failed";
       // drop the case's device state; a later request rebuilds it
       srv->resident -= c.bytes;
       c.bytes = 0;
@@ -515,6 +519,13 @@ BCS_API bcs_status bcs_server_get_stats(bcs_server* srv, bcs_server_stats* st) {
     st->overlap_frac = two / (hi - lo);
     st->mean_in_flight = sum / (hi - lo);
   }
+  return BCS_OK;
+}
+
+BCS_API bcs_status bcs_server_last_error(bcs_server* srv, char* buf, size_t len) {
+  if (!srv || !buf || !len) return BCS_EINVAL;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  std::snprintf(buf, len, "%s", srv->last_error.c_str());
   return BCS_OK;
 }
 

@@ -1067,7 +1067,7 @@ bcs_status coarse_inverse(Solver* s, Level& L) {
     // [A | I] fits one block's shared memory: no grid-wide barriers, no L2
     // round trip per pivot step
     const size_t smem = 16 * (size_t)N * N + N;
-    BCS_CU(s, cudaFuncSetAttribute(k_gauss_jordan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BCS_CU(s, allow_max_dynamic_smem<k_gauss_jordan_smem>());
     BCS_LAUNCH_DEP(s, K_SETUP_INV, 24.0 * N * N * N, 3.0 * N * N * N, k_gauss_jordan_smem, 1, GJ_SMEM_THREADS, smem, N,
                M.p, prow.p, s->flag.p);
   } else {

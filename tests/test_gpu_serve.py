@@ -197,3 +197,24 @@ def test_batching_server_results_identical():
         stats = srv.stats()
     assert stats["batches"] >= 1 and stats["batched_requests"] >= 2
     print(f"batches {stats['batches']} serving {stats['batched_requests']} of 15 requests")
+
+
+def test_failed_request_reports_its_error():
+    """A request whose matrix cannot be set up (a zero diagonal block) is
+    answered BCS_SINGULAR_BLOCK and leaves its message with the server; the
+    case serves the next, valid request."""
+    system = synth.density(6, seed=3)
+    bad = dict(system)
+    bad["diag"] = system["diag"].copy()
+    bad["diag"][7] = 0.0
+    bad["upper"] = system["upper"].copy()
+    bad["lower"] = system["lower"].copy()
+    with bcs.Server(slots=1) as srv:
+        assert srv.last_error() == ""
+        cid = srv.register(system)
+        st, res, _, _ = srv.wait(srv.submit(cid, bad))
+        assert st == bcs.BCS_SINGULAR_BLOCK, res
+        assert "singular" in srv.last_error()
+        st, res, _, x = srv.wait(srv.submit(cid, system))
+        assert st == bcs.BCS_OK, res
+        assert true_rel(system, x) <= 1e-8

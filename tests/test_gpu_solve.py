@@ -206,3 +206,52 @@ def test_dependent_launch_identical(kw):
         out.append((x, res["iters"]))
     assert out[0][1] == out[1][1]
     assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_x0_zero_ignores_x():
+    """cfg.x0_zero: the solve starts from x = 0 whatever x holds on entry,
+    for device and host memory and in a batched solve: the same result as a
+    solve from an explicit zero vector."""
+    system = synth.density(10, seed=6)
+    junk = np.random.default_rng(5).standard_normal(system["b"].shape) * 1e3
+    ref, st, res_ref = gpu_solve(system)
+    assert st == bcs.BCS_OK
+    for device in (True, False):
+        x, st, res = gpu_solve(system, x0=junk, device=device, x0_zero=1)
+        assert st == bcs.BCS_OK and res["iters"] == res_ref["iters"]
+        assert np.array_equal(x, ref)
+    with bcs.Solver(5, x0_zero=1) as s1, bcs.Solver(5, x0_zero=1) as s2:
+        for s in (s1, s2):
+            s.load(system, device=DEV)
+        bs = [torch.from_numpy(system["b"]).to(DEV) for _ in range(2)]
+        xs = [torch.from_numpy(junk).to(DEV) for _ in range(2)]
+        xs, st, res = bcs.solve_batch([s1, s2], bs, xs)
+        assert st == bcs.BCS_OK
+        for x, r in zip(xs, res):
+            assert r["status"] == bcs.BCS_OK and r["iters"] == res_ref["iters"]
+            assert np.array_equal(x.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("solver", [bcs.BCS_FGMRES, bcs.BCS_BICGSTAB])
+def test_resetup_keeps_graphs_identical(solver):
+    """Values-only resetups rewrite the hierarchy in place, so the captured
+    cycle and Krylov graphs are replayed across them: every solve of a
+    resetup sequence equals the one of a solver without graphs bit for bit."""
+    system = synth.pressure(12, seed=4)
+    rng = [np.random.default_rng(17), np.random.default_rng(17)]
+    out = {}
+    for graph in (0, 1):
+        xs = []
+        sysg = system
+        with bcs.Solver(4, solver=solver, cycle_graph=graph) as s:
+            s.load(sysg, device=DEV)
+            b = torch.from_numpy(sysg["b"]).to(DEV)
+            for it in range(4):
+                x, st, res = s.solve(b)
+                assert st == bcs.BCS_OK
+                xs.append((x.cpu().numpy(), res["iters"]))
+                sysg = synth.perturb(sysg, rng[graph], 0.05)
+                s.set_values(*(torch.from_numpy(sysg[k]).to(DEV) for k in ("diag", "upper", "lower")))
+        out[graph] = xs
+    for (x0, i0), (x1, i1) in zip(out[0], out[1]):
+        assert i0 == i1 and np.array_equal(x0, x1)
