@@ -375,11 +375,15 @@ struct LevelScope {
   ~LevelScope() { s->cur_level = prev; }
 };
 
-#define BCS_CU(S, call)                                                                \
-  do {                                                                                 \
-    cudaError_t e_ = (call);                                                           \
-    if (e_ != cudaSuccess)                                                             \
-      return (S)->fail(BCS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+// A failed call also clears the thread's last-error state, so that no later
+// launch check reports it as its own.
+#define BCS_CU(S, call)                                                                  \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      (void)cudaGetLastError();                                                          \
+      return (S)->fail(BCS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+    }                                                                                    \
   } while (0)
 #define BCS_OKR(...)                \
   do {                              \
