@@ -1251,11 +1251,12 @@ bcs_status amg_setup_levels(Solver* s, bool full) {
   // behind (no index depends on them), so the flags are read once, at the
   // end; the multicolour factorisations read them per level.
   const bool dilu = cfg.precond == BCS_PC_SGS || (cfg.precond == BCS_PC_AMG && cfg.smoother != BCS_SMOOTH_JACOBI);
-  // At a full block-Jacobi setup a level's block inverses (FP64-bound) do
-  // not depend on its aggregation (latency-bound small kernels): they run on
-  // a second stream beside it and are joined before anything reads them
-  // (the FP32 copies, smoothed prolongation, the flags at the end).
-  const bool side = full && !dilu && cfg.pmode == BCS_P_TENTATIVE;
+  // With block Jacobi a level's block inverses (FP64-bound) do not depend on
+  // its aggregation (latency-bound small kernels) or, at a values-only
+  // resetup, on its Galerkin product: they run on a second stream beside
+  // them and are joined before anything reads them (the FP32 copies,
+  // smoothed prolongation, the flags at the end).
+  const bool side = !dilu && cfg.pmode == BCS_P_TENTATIVE;
   if (side && !s->sstream) BCS_CU(s, cudaStreamCreateWithFlags(&s->sstream, cudaStreamNonBlocking));
   if (side && !s->sev[0]) {
     BCS_CU(s, cudaEventCreateWithFlags(&s->sev[0], cudaEventDisableTiming));
