@@ -789,7 +789,12 @@ bcs_status bcs_get_level(bcs_solver* h, int l, int32_t* rp, int32_t* col, double
   BCS_OKR(to_host(s, col, L.A.ci.p, (size_t)L.A.nnz * sizeof(int32_t)));
   BCS_OKR(to_host(s, val, L.A.v.p, (size_t)L.A.nnz * nn * sizeof(double)));
   if (agg && L.coarse_kind < 0) BCS_OKR(to_host(s, agg, L.agg.p, (size_t)L.A.rows * sizeof(int32_t)));
-  BCS_OKR(to_host(s, dinv, L.dinv.p, (size_t)L.A.rows * nn * sizeof(double)));
+  if (dinv) {
+    DBuf<double> tmp;
+    const double* d64 = nullptr;
+    BCS_OKR(level_dinv64(s, l, &d64, tmp));
+    BCS_OKR(to_host(s, dinv, d64, (size_t)L.A.rows * nn * sizeof(double)));
+  }
   return BCS_OK;
 }
 

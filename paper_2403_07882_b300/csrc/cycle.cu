@@ -1620,7 +1620,7 @@ bcs_status cycle_prepare(Solver* s, bool keep_graphs) {
       L.dcl = dcl_blocks;
     }
     BCS_ALLOC(s, L.dinv32, (size_t)L.A.rows * nn);
-    BCS_OKR(cast_vec<double, float>(s, L.dinv.p, L.dinv32.p, (size_t)L.A.rows * nn));
+    if (L.dinv64) BCS_OKR(cast_vec<double, float>(s, L.dinv.p, L.dinv32.p, (size_t)L.A.rows * nn));
     int map = 0;
     BCS_OKR(slice_map(s, L, prec, s->tail_level >= 0 && (int)l >= s->tail_level, &map));
     bool need = false;

@@ -121,8 +121,11 @@ struct TentPlan {
 struct Level {
   Bsr A;                     // FP64 operator of this level
   DBuf<int32_t> dpos;        // diagonal block position per row
-  DBuf<double> dinv;         // FP64 diagonal block inverses
+  DBuf<double> dinv;         // FP64 diagonal block inverses (when dinv64)
   DBuf<float> dinv32;        // FP32 block inverses for the FP32 / BF16 cycle
+  // dinv holds this setup's FP64 inverses; false when the setup inverted the
+  // blocks in FP32 straight into dinv32 (FP32 / BF16 block-Jacobi cycle)
+  bool dinv64 = true;
   // transfer to level l+1 (absent at the coarsest level)
   int nagg = 0;
   DBuf<int32_t> agg;         // aggregate of each row
@@ -603,6 +606,12 @@ bcs_status spmv64(Solver* s, const Bsr& A, const void* x, bool x_is_float, doubl
 // keep_graphs: a values-only resetup (every buffer kept in place), so the
 // captured graphs stay valid; otherwise they are dropped.
 bcs_status cycle_prepare(Solver* s, bool keep_graphs = false);
+// The blocks' FP64 inverses of level l into out (computed on demand when the
+// setup inverted them in FP32 only).
+bcs_status level_dinv64(Solver* s, int l, const double** out, DBuf<double>& tmp);
+// Whether the setup inverts the diagonal blocks in FP32 only (FP32 / BF16
+// cycle with AMG, block Jacobi and tentative P: nothing reads FP64 inverses).
+bool fp32_inverses(const Solver* s);
 bcs_status precond_apply(Solver* s, const double* v, void* z);  // z in cycle precision
 bcs_status jacobi_apply(Solver* s, const double* v, double* z);
 bcs_status sgs_apply(Solver* s, const double* v, void* z);  // z in cycle precision

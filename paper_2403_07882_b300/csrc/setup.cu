@@ -54,6 +54,27 @@ __global__ void k_diag_pos(int rows, const int32_t* __restrict__ rp, const int32
   if (p < 0) atomicOr(err, 4);
 }
 
+// The FP32 / BF16 block-Jacobi cycle's inverses computed in FP32 (the FP32
+// pipe is many times the FP64 one): each diagonal block rounded to FP32 and
+// inverted by the same Gauss-Jordan in FP32 arithmetic.
+template <int N>
+__global__ void __launch_bounds__(64) k_block_inverse32(int rows, const int32_t* __restrict__ dpos,
+                                                        const double* __restrict__ val, float* __restrict__ dinv,
+                                                        int32_t* __restrict__ err) {
+  dep_enter();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const int dp = dpos[i];
+  if (dp < 0) return;
+  BlockGJ<N, float> g;
+  const double* a = val + (size_t)dp * N * N;
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+#pragma unroll
+    for (int c = 0; c < N; ++c) g.M[r][c] = (float)a[r * N + c];
+  if (!gj_finish<N>(g, dinv + (size_t)i * N * N)) atomicOr(err, 8);
+}
+
 template <int N>
 __global__ void __launch_bounds__(64) k_block_inverse(int rows, const int32_t* __restrict__ dpos,
                                                       const double* __restrict__ val, double* __restrict__ dinv,
@@ -1032,6 +1053,8 @@ bcs_status aggregate_level(Solver* s, Level& L, const double* norms) {
   return BCS_OK;
 }
 
+// Block inverses of level L: FP64 into L.dinv, or (fp32_inverses) FP32
+// straight into L.dinv32. allocated: the output (and dpos) exist already.
 bcs_status block_inverses(Solver* s, Level& L, bool full, bool allocated = false) {
   const int rows = L.A.rows, n = s->n;
   if (full || !L.dpos.p) {
@@ -1039,11 +1062,20 @@ bcs_status block_inverses(Solver* s, Level& L, bool full, bool allocated = false
     BCS_LAUNCH_DEP(s, K_SETUP_INV, 0, 0, k_diag_pos, grid_for(rows, 256), 256, 0, rows, L.A.rp.p, L.A.ci.p,
                L.dpos.p, s->flag.p);
   }
-  if (!allocated) BCS_ALLOC(s, L.dinv, (size_t)rows * n * n);
+  const bool f32 = fp32_inverses(s);
+  L.dinv64 = !f32;
+  if (!allocated) {
+    if (f32) BCS_ALLOC(s, L.dinv32, (size_t)rows * n * n);
+    else BCS_ALLOC(s, L.dinv, (size_t)rows * n * n);
+  }
   return with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
-    BCS_LAUNCH_DEP(s, K_SETUP_INV, 16.0 * rows * N * N, 4.0 * rows * N * N * N, k_block_inverse<N>,
-               grid_for(rows, 64), 64, 0, rows, L.dpos.p, L.A.v.p, L.dinv.p, s->flag.p);
+    if (f32)
+      BCS_LAUNCH_DEP(s, K_SETUP_INV, 12.0 * rows * N * N, 4.0 * rows * N * N * N, k_block_inverse32<N>,
+                     grid_for(rows, 64), 64, 0, rows, L.dpos.p, L.A.v.p, L.dinv32.p, s->flag.p);
+    else
+      BCS_LAUNCH_DEP(s, K_SETUP_INV, 16.0 * rows * N * N, 4.0 * rows * N * N * N, k_block_inverse<N>,
+                     grid_for(rows, 64), 64, 0, rows, L.dpos.p, L.A.v.p, L.dinv.p, s->flag.p);
     return BCS_OK;
   });
 }
@@ -1231,6 +1263,30 @@ bcs_status build_transfer(Solver* s, int l, bool full) {
 
 bcs_status amg_setup_levels(Solver* s, bool full);
 
+bool fp32_inverses(const Solver* s) {
+  const bcs_config& c = s->setup_cfg;
+  return c.precision != BCS_PREC_FP64 && c.precond == BCS_PC_AMG && c.smoother == BCS_SMOOTH_JACOBI &&
+         c.pmode == BCS_P_TENTATIVE;
+}
+
+bcs_status level_dinv64(Solver* s, int l, const double** out, DBuf<double>& tmp) {
+  Level& L = s->lv[l];
+  if (L.dinv64) {
+    *out = L.dinv.p;
+    return BCS_OK;
+  }
+  const int rows = L.A.rows, n = s->n;
+  BCS_ALLOC(s, tmp, (size_t)rows * n * n);
+  BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    BCS_LAUNCH_DEP(s, K_SETUP_INV, 16.0 * rows * N * N, 4.0 * rows * N * N * N, k_block_inverse<N>,
+                   grid_for(rows, 64), 64, 0, rows, L.dpos.p, L.A.v.p, tmp.p, s->flag.p);
+    return BCS_OK;
+  }));
+  *out = tmp.p;
+  return BCS_OK;
+}
+
 bcs_status amg_setup(Solver* s, bool full) {
   const bcs_status st = amg_setup_levels(s, full);
   s->nrm0_fresh = false;  // the norms belong to these values only
@@ -1269,7 +1325,8 @@ bcs_status amg_setup_levels(Solver* s, bool full) {
     if (side) {
       // buffers first, stream-ordered on the solver's stream
       BCS_ALLOC(s, L.dpos, L.A.rows);
-      BCS_ALLOC(s, L.dinv, (size_t)L.A.rows * s->n * s->n);
+      if (fp32_inverses(s)) BCS_ALLOC(s, L.dinv32, (size_t)L.A.rows * s->n * s->n);
+      else BCS_ALLOC(s, L.dinv, (size_t)L.A.rows * s->n * s->n);
       BCS_CU(s, cudaEventRecord(s->sev[0], s->stream));
       BCS_CU(s, cudaStreamWaitEvent(s->sstream, s->sev[0], 0));
       const cudaStream_t own = s->stream;
