@@ -826,7 +826,12 @@ bcs_status bcs_get_dilu(bcs_solver* h, int level, int* ncolours, int32_t* colour
   *ncolours = L.ncol > 0 ? L.ncol : -1;
   if (L.ncol <= 0) return BCS_OK;
   if (colour) BCS_OKR(to_host(s, colour, L.colour.p, (size_t)L.A.rows * sizeof(int32_t)));
-  if (einv) BCS_OKR(to_host(s, einv, L.einv.p, (size_t)L.A.rows * s->n * s->n * sizeof(double)));
+  if (einv) {
+    DBuf<double> tmp;
+    const double* e64 = nullptr;
+    BCS_OKR(dilu_einv64(s, level, &e64, tmp));
+    BCS_OKR(to_host(s, einv, e64, (size_t)L.A.rows * s->n * s->n * sizeof(double)));
+  }
   return BCS_OK;
 }
 

@@ -188,12 +188,16 @@ __device__ __forceinline__ int find_pos(const int32_t* __restrict__ ci, int b, i
 // earlier neighbour j it forms W[r][cc] = (A_ij E_j^{-1})[r][cc] and, from
 // its row's W by shuffles, Z[r][cc] = (W A_ji)[r][cc], each the fma chain of
 // the definition. Larger blocks: one thread per row, W one row at a time.
-template <int N>
+// T: the arithmetic (double: the factor the oracle reproduces; float: the
+// FP32 / BF16 cycle's factor); TA: the type of the blocks read (the FP64
+// values, or for T = float an FP32 copy rounded once, so that no conversion
+// from FP64 runs per use on the FP64 pipe).
+template <int N, class T, class TA>
 __global__ void __launch_bounds__(128) k_dilu_schur(int cnt, const int32_t* __restrict__ rows_c, int c,
                                                     const int32_t* __restrict__ colour, const int32_t* __restrict__ rp,
-                                                    const int32_t* __restrict__ ci, const double* __restrict__ val,
-                                                    const int32_t* __restrict__ dpos, const double* __restrict__ einv,
-                                                    double* __restrict__ E, int32_t* __restrict__ err) {
+                                                    const int32_t* __restrict__ ci, const TA* __restrict__ val,
+                                                    const int32_t* __restrict__ dpos, const T* __restrict__ einv,
+                                                    T* __restrict__ E, int32_t* __restrict__ err) {
   dep_enter();
   constexpr int NN = N * N;
   if constexpr (NN <= 32) {
@@ -203,7 +207,7 @@ __global__ void __launch_bounds__(128) k_dilu_schur(int cnt, const int32_t* __re
     const int i = rows_c[q];
     const bool act = lane < NN;
     const int r = act ? lane / N : 0, cc = act ? lane - (lane / N) * N : 0;
-    double m = act ? val[(size_t)dpos[i] * NN + lane] : 0.0;
+    T m = act ? (T)val[(size_t)dpos[i] * NN + lane] : (T)0;
     for (int k = rp[i]; k < rp[i + 1]; ++k) {
       const int j = ci[k];
       if (colour[j] >= c) continue;
@@ -212,17 +216,17 @@ __global__ void __launch_bounds__(128) k_dilu_schur(int cnt, const int32_t* __re
         if (lane == 0) atomicOr(err, 128);  // structurally unsymmetric pattern
         return;
       }
-      const double* aij = val + (size_t)k * NN;
-      const double* ej = einv + (size_t)j * NN;
-      const double* aji = val + (size_t)kt * NN;
-      double w = 0.0;
+      const TA* aij = val + (size_t)k * NN;
+      const T* ej = einv + (size_t)j * NN;
+      const TA* aji = val + (size_t)kt * NN;
+      T w = 0;
 #pragma unroll
-      for (int mm = 0; mm < N; ++mm) w = fma(aij[r * N + mm], ej[mm * N + cc], w);
-      double z = 0.0;
+      for (int mm = 0; mm < N; ++mm) w = fma((T)aij[r * N + mm], ej[mm * N + cc], w);
+      T z = 0;
 #pragma unroll
       for (int mm = 0; mm < N; ++mm) {
-        const double wm = __shfl_sync(0xffffffffu, w, (r * N + mm) & 31);
-        z = fma(wm, aji[mm * N + cc], z);
+        const T wm = __shfl_sync(0xffffffffu, w, (r * N + mm) & 31);
+        z = fma(wm, (T)aji[mm * N + cc], z);
       }
       m = m - z;
     }
@@ -231,10 +235,10 @@ __global__ void __launch_bounds__(128) k_dilu_schur(int cnt, const int32_t* __re
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= cnt) return;
     const int i = rows_c[q];
-    double M[NN];
-    const double* d = val + (size_t)dpos[i] * NN;
+    T M[NN];
+    const TA* d = val + (size_t)dpos[i] * NN;
 #pragma unroll
-    for (int e = 0; e < NN; ++e) M[e] = d[e];
+    for (int e = 0; e < NN; ++e) M[e] = (T)d[e];
     for (int k = rp[i]; k < rp[i + 1]; ++k) {
       const int j = ci[k];
       if (colour[j] >= c) continue;
@@ -243,50 +247,92 @@ __global__ void __launch_bounds__(128) k_dilu_schur(int cnt, const int32_t* __re
         atomicOr(err, 128);
         return;
       }
-      const double* aij = val + (size_t)k * NN;
-      const double* ej = einv + (size_t)j * NN;
-      const double* aji = val + (size_t)kt * NN;
+      const TA* aij = val + (size_t)k * NN;
+      const T* ej = einv + (size_t)j * NN;
+      const TA* aji = val + (size_t)kt * NN;
 #pragma unroll
       for (int r = 0; r < N; ++r) {
-        double w[N];
+        T w[N];
 #pragma unroll
         for (int cc = 0; cc < N; ++cc) {
-          double acc = 0.0;
+          T acc = 0;
 #pragma unroll
-          for (int mm = 0; mm < N; ++mm) acc = fma(aij[r * N + mm], ej[mm * N + cc], acc);
+          for (int mm = 0; mm < N; ++mm) acc = fma((T)aij[r * N + mm], ej[mm * N + cc], acc);
           w[cc] = acc;
         }
 #pragma unroll
         for (int cc = 0; cc < N; ++cc) {
-          double z = 0.0;
+          T z = 0;
 #pragma unroll
-          for (int mm = 0; mm < N; ++mm) z = fma(w[mm], aji[mm * N + cc], z);
+          for (int mm = 0; mm < N; ++mm) z = fma(w[mm], (T)aji[mm * N + cc], z);
           M[r * N + cc] = M[r * N + cc] - z;
         }
       }
     }
-    double* o = E + (size_t)q * NN;
+    T* o = E + (size_t)q * NN;
 #pragma unroll
     for (int e = 0; e < NN; ++e) o[e] = M[e];
   }
 }
 
 // E_i^{-1} for the rows of colour c from E (one thread per row).
-template <int N>
+template <int N, class T>
 __global__ void __launch_bounds__(64) k_dilu_invert(int cnt, const int32_t* __restrict__ rows_c,
-                                                    const double* __restrict__ E, double* __restrict__ einv,
+                                                    const T* __restrict__ E, T* __restrict__ einv,
                                                     int32_t* __restrict__ err) {
   dep_enter();
   constexpr int NN = N * N;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= cnt) return;
-  BlockGJ<N> g;
-  const double* a = E + (size_t)q * NN;
+  BlockGJ<N, T> g;
+  const T* a = E + (size_t)q * NN;
 #pragma unroll
   for (int r = 0; r < N; ++r)
 #pragma unroll
     for (int cc = 0; cc < N; ++cc) g.M[r][cc] = a[r * N + cc];
   if (!gj_finish<N>(g, einv + (size_t)rows_c[q] * NN)) atomicOr(err, 64);
+}
+
+// The DILU factor of level L colour by colour (E_i from the Schur sums over
+// earlier colours, then E_i^{-1}) into einv, in arithmetic T; reads the
+// status flags once at the end.
+template <class T>
+bcs_status dilu_factor(Solver* s, const Level& L, T* einv) {
+  const int n = s->n;
+  int maxc = 0;
+  for (int c = 0; c < L.ncol; ++c) maxc = std::max(maxc, L.cstart[c + 1] - L.cstart[c]);
+  DBuf<T> E;
+  BCS_ALLOC(s, E, (size_t)maxc * n * n);
+  // the blocks in the arithmetic's type (an FP32 copy for T = float)
+  DBuf<T> a_copy;
+  const T* va = nullptr;
+  if constexpr (std::is_same<T, double>::value) {
+    va = L.A.v.p;
+  } else {
+    BCS_ALLOC(s, a_copy, (size_t)L.A.nnz * n * n);
+    BCS_OKR(cast_vec<double, T>(s, L.A.v.p, a_copy.p, (size_t)L.A.nnz * n * n));
+    va = a_copy.p;
+  }
+  BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
+    constexpr int N = decltype(NC)::value;
+    for (int c = 0; c < L.ncol; ++c) {
+      const int b = L.cstart[c], m = L.cstart[c + 1] - b;
+      if (m <= 0) continue;
+      const unsigned gs = N * N <= 32 ? grid_for((size_t)m * 32, 128) : grid_for(m, 128);
+      BCS_LAUNCH_DEP(s, K_SETUP_INV, sizeof(T) * m * N * N * 4.0, 4.0 * m * N * N * N * 3, (k_dilu_schur<N, T, T>),
+                     gs, 128, 0, m, L.crow.p + b, c, L.colour.p, L.A.rp.p, L.A.ci.p, va, L.dpos.p, einv, E.p,
+                     s->flag.p);
+      BCS_LAUNCH_DEP(s, K_SETUP_INV, 2.0 * sizeof(T) * m * N * N, 4.0 * m * N * N * N, (k_dilu_invert<N, T>),
+                     grid_for(m, 64), 64, 0, m, L.crow.p + b, E.p, einv, s->flag.p);
+    }
+    return BCS_OK;
+  }));
+  int32_t h = 0;
+  BCS_CU(s, cudaMemcpyAsync(&h, s->flag.p, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+  BCS_CU(s, cudaStreamSynchronize(s->stream));
+  if (h & 128) return s->fail(BCS_EINVAL, "DILU needs a structurally symmetric pattern");
+  if (h & 64) return s->fail(BCS_SINGULAR_BLOCK, "singular DILU diagonal block");
+  return BCS_OK;
 }
 
 }  // namespace
@@ -362,35 +408,32 @@ bcs_status dilu_setup(Solver* s, Level& L, bool full, bool sgs) {
     L.ncol = ncol;
   }
   if (L.ncol <= 0) return BCS_OK;
-  BCS_ALLOC(s, L.einv, (size_t)rows * n * n);
+  L.einv64 = true;
+  if (sgs || s->setup_cfg.precision == BCS_PREC_FP64) BCS_ALLOC(s, L.einv, (size_t)rows * n * n);
   if (sgs) {
     // symmetric Gauss-Seidel: E = D, so E^-1 is the block-Jacobi inverse
     BCS_CU(s, cudaMemcpyAsync(L.einv.p, L.dinv.p, (size_t)rows * n * n * sizeof(double), cudaMemcpyDeviceToDevice,
                               s->stream));
     return BCS_OK;
   }
-  int maxc = 0;
-  for (int c = 0; c < L.ncol; ++c) maxc = std::max(maxc, L.cstart[c + 1] - L.cstart[c]);
-  DBuf<double> E;
-  BCS_ALLOC(s, E, (size_t)maxc * n * n);
-  BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
-    constexpr int N = decltype(NC)::value;
-    for (int c = 0; c < L.ncol; ++c) {
-      const int b = L.cstart[c], m = L.cstart[c + 1] - b;
-      if (m <= 0) continue;
-      const unsigned gs = N * N <= 32 ? grid_for((size_t)m * 32, 128) : grid_for(m, 128);
-      BCS_LAUNCH_DEP(s, K_SETUP_INV, 8.0 * m * N * N * 4, 4.0 * m * N * N * N * 3, k_dilu_schur<N>, gs, 128, 0, m,
-                 L.crow.p + b, c, L.colour.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.dpos.p, L.einv.p, E.p, s->flag.p);
-      BCS_LAUNCH_DEP(s, K_SETUP_INV, 16.0 * m * N * N, 4.0 * m * N * N * N, k_dilu_invert<N>, grid_for(m, 64), 64, 0,
-                 m, L.crow.p + b, E.p, L.einv.p, s->flag.p);
-    }
+  if (s->setup_cfg.precision != BCS_PREC_FP64) {
+    // the FP32 / BF16 cycle's factor, computed in FP32 straight into einv32
+    L.einv64 = false;
+    BCS_ALLOC(s, L.einv32, (size_t)rows * n * n);
+    return dilu_factor<float>(s, L, L.einv32.p);
+  }
+  return dilu_factor<double>(s, L, L.einv.p);
+}
+
+bcs_status dilu_einv64(Solver* s, int l, const double** out, DBuf<double>& tmp) {
+  Level& L = s->lv[l];
+  if (L.einv64) {
+    *out = L.einv.p;
     return BCS_OK;
-  }));
-  int32_t h = 0;
-  BCS_CU(s, cudaMemcpyAsync(&h, s->flag.p, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
-  BCS_CU(s, cudaStreamSynchronize(s->stream));
-  if (h & 128) return s->fail(BCS_EINVAL, "DILU needs a structurally symmetric pattern");
-  if (h & 64) return s->fail(BCS_SINGULAR_BLOCK, "singular DILU diagonal block");
+  }
+  BCS_ALLOC(s, tmp, (size_t)L.A.rows * s->n * s->n);
+  BCS_OKR(dilu_factor<double>(s, L, tmp.p));
+  *out = tmp.p;
   return BCS_OK;
 }
 
@@ -398,7 +441,7 @@ bcs_status dilu_prepare(Solver* s, Level& L) {
   if (L.ncol <= 0) return BCS_OK;
   const size_t nn = (size_t)s->n * s->n;
   BCS_ALLOC(s, L.einv32, (size_t)L.A.rows * nn);
-  BCS_OKR(cast_vec<double, float>(s, L.einv.p, L.einv32.p, (size_t)L.A.rows * nn));
+  if (L.einv64) BCS_OKR(cast_vec<double, float>(s, L.einv.p, L.einv32.p, (size_t)L.A.rows * nn));
   const long long bound = (long long)L.A.nnz * (long long)nn;
   const bool b16 = s->setup_cfg.precision == BCS_PREC_BF16;
   if (b16) BCS_ALLOC(s, L.a16, (size_t)bound);

@@ -159,7 +159,10 @@ struct Level {
   std::vector<int> cstart;
   DBuf<int32_t> cstart_d;    // cstart on the device
   int dcl = 0;               // FP32 / BF16 cycle: blocks of the one-launch DILU step's cluster (0: per colour)
-  DBuf<double> einv;         // E_i^{-1}, FP64
+  DBuf<double> einv;         // E_i^{-1}, FP64 (when einv64)
+  // einv holds this setup's FP64 factor; false when the DILU factor of the
+  // FP32 / BF16 cycle was computed in FP32 straight into einv32
+  bool einv64 = true;
   // each row's off-diagonal blocks split for the sweeps: the lower part
   // (colour(j) < colour(i)) then the upper part (colour(j) > colour(i)),
   // each in column order, stored in colour-list order: the row at crow[t]
@@ -612,6 +615,9 @@ bcs_status level_dinv64(Solver* s, int l, const double** out, DBuf<double>& tmp)
 // Whether the setup inverts the diagonal blocks in FP32 only (FP32 / BF16
 // cycle with AMG, block Jacobi and tentative P: nothing reads FP64 inverses).
 bool fp32_inverses(const Solver* s);
+// The DILU factor's FP64 inverses E_i^{-1} of level l into out (computed on
+// demand when the setup built the FP32 factor only).
+bcs_status dilu_einv64(Solver* s, int l, const double** out, DBuf<double>& tmp);
 bcs_status precond_apply(Solver* s, const double* v, void* z);  // z in cycle precision
 bcs_status jacobi_apply(Solver* s, const double* v, double* z);
 bcs_status sgs_apply(Solver* s, const double* v, void* z);  // z in cycle precision
