@@ -409,13 +409,22 @@ bcs_status dilu_setup(Solver* s, Level& L, bool full, bool sgs) {
   }
   if (L.ncol <= 0) return BCS_OK;
   L.einv64 = true;
-  if (sgs || s->setup_cfg.precision == BCS_PREC_FP64) BCS_ALLOC(s, L.einv, (size_t)rows * n * n);
   if (sgs) {
-    // symmetric Gauss-Seidel: E = D, so E^-1 is the block-Jacobi inverse
+    // symmetric Gauss-Seidel: E = D, so E^-1 is the block-Jacobi inverse (the
+    // FP32 one when the setup inverted the blocks in FP32 only)
+    if (!L.dinv64) {
+      L.einv64 = false;
+      BCS_ALLOC(s, L.einv32, (size_t)rows * n * n);
+      BCS_CU(s, cudaMemcpyAsync(L.einv32.p, L.dinv32.p, (size_t)rows * n * n * sizeof(float),
+                                cudaMemcpyDeviceToDevice, s->stream));
+      return BCS_OK;
+    }
+    BCS_ALLOC(s, L.einv, (size_t)rows * n * n);
     BCS_CU(s, cudaMemcpyAsync(L.einv.p, L.dinv.p, (size_t)rows * n * n * sizeof(double), cudaMemcpyDeviceToDevice,
                               s->stream));
     return BCS_OK;
   }
+  if (s->setup_cfg.precision == BCS_PREC_FP64) BCS_ALLOC(s, L.einv, (size_t)rows * n * n);
   if (s->setup_cfg.precision != BCS_PREC_FP64) {
     // the FP32 / BF16 cycle's factor, computed in FP32 straight into einv32
     L.einv64 = false;
@@ -431,6 +440,8 @@ bcs_status dilu_einv64(Solver* s, int l, const double** out, DBuf<double>& tmp) 
     *out = L.einv.p;
     return BCS_OK;
   }
+  const bcs_config& c = s->setup_cfg;
+  if (c.precond == BCS_PC_SGS || c.smoother == BCS_SMOOTH_SGS) return level_dinv64(s, l, out, tmp);  // E = D
   BCS_ALLOC(s, tmp, (size_t)L.A.rows * s->n * s->n);
   BCS_OKR(dilu_factor<double>(s, L, tmp.p));
   *out = tmp.p;

@@ -612,8 +612,8 @@ bcs_status cycle_prepare(Solver* s, bool keep_graphs = false);
 // The blocks' FP64 inverses of level l into out (computed on demand when the
 // setup inverted them in FP32 only).
 bcs_status level_dinv64(Solver* s, int l, const double** out, DBuf<double>& tmp);
-// Whether the setup inverts the diagonal blocks in FP32 only (FP32 / BF16
-// cycle with AMG, block Jacobi and tentative P: nothing reads FP64 inverses).
+// Whether the setup inverts the diagonal blocks in FP32 only (an FP32 / BF16
+// cycle whose configuration reads no FP64 inverses).
 bool fp32_inverses(const Solver* s);
 // The DILU factor's FP64 inverses E_i^{-1} of level l into out (computed on
 // demand when the setup built the FP32 factor only).

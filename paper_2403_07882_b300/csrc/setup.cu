@@ -1265,8 +1265,10 @@ bcs_status amg_setup_levels(Solver* s, bool full);
 
 bool fp32_inverses(const Solver* s) {
   const bcs_config& c = s->setup_cfg;
-  return c.precision != BCS_PREC_FP64 && c.precond == BCS_PC_AMG && c.smoother == BCS_SMOOTH_JACOBI &&
-         c.pmode == BCS_P_TENTATIVE;
+  // FP64 inverses are read by the FP64 cycle, the block-Jacobi
+  // preconditioner (applied in FP64) and smoothed P's damping estimate
+  return c.precision != BCS_PREC_FP64 && c.precond != BCS_PC_JACOBI &&
+         !(c.precond == BCS_PC_AMG && c.pmode == BCS_P_SMOOTHED);
 }
 
 bcs_status level_dinv64(Solver* s, int l, const double** out, DBuf<double>& tmp) {
