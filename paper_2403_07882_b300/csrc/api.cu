@@ -171,6 +171,10 @@ bcs_status to_host(Solver* s, void* dst, const void* src, size_t bytes) {
 
 // After new fine values: full AMG setup, or values-only resetup.
 bcs_status values_changed(Solver* s, std::chrono::steady_clock::time_point t0) {
+  struct DirectCopyDone {  // a gather's sliced copy belongs to these values only
+    Solver* s;
+    ~DirectCopyDone() { s->v0_direct = -1; }
+  } done{s};
   s->have_values = true;
   const bool full = !s->have_hierarchy;
   if (full) s->setup_cfg = s->cfg;

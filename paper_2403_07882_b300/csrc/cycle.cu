@@ -316,16 +316,7 @@ __global__ void __launch_bounds__(128) k_sell(int rows, int nslices, const int32
 // SORT_WIN consecutive rows, longest first (ties by row index), so the rows
 // of a slice have similar lengths and little padding (coarse levels mix rows
 // of 7 to 30 blocks).
-template <int NN, class TV>
-struct TprTile {
-  static constexpr int G = 16 / (int)sizeof(TV);  // entries per 16-byte group
-  static constexpr int NG = NN / G;               // full groups
-  static constexpr int R = NN - NG * G;           // remaining entries
-  static constexpr int TILE = NN * 32;
-  __host__ __device__ static constexpr int off(int e, int w) {
-    return e < NG * G ? (e / G) * G * 32 + w * G + e % G : NG * G * 32 + (e - NG * G) * 32 + w;
-  }
-};
+// (TprTile, in internal.h, gives these offsets.)
 
 // resident blocks of 128 threads per SM the sweep is compiled for (caps its
 // registers at 64)
@@ -388,7 +379,8 @@ __global__ void __launch_bounds__(SORT_WIN) k_window_order(int rows, const int32
 template <int N, class TV>
 __global__ void k_tpr_fill(int rows, int nslices, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const double* __restrict__ val, const int32_t* __restrict__ srow,
-                           const int32_t* __restrict__ sptr, int32_t* __restrict__ sci, TV* __restrict__ sv) {
+                           const int32_t* __restrict__ sptr, int32_t* __restrict__ sci, TV* __restrict__ sv,
+                           int32_t* __restrict__ tpos) {
   dep_enter();
   constexpr int NN = N * N;
   using T = TprTile<NN, TV>;
@@ -419,6 +411,7 @@ __global__ void k_tpr_fill(int rows, int nslices, const int32_t* __restrict__ rp
       else tile[T::NG * T::G * 32 + r * 32 + lane] = (TV)a[T::NG * T::G + r];
     }
     sci[(size_t)(t0 + k) * 32 + lane] = ci[p0 + k];
+    if (tpos) tpos[p0 + k] = (t0 + k) * 32 + lane;  // the slot of block-CSR position p0 + k
   }
 }
 
@@ -1216,6 +1209,8 @@ bcs_status layout_structure(Solver* s, Level& L, int map, int32_t* steps_dev, bo
   const int n = s->n, rows = L.A.rows, rpw = map == 1 ? 32 : 32 / n;
   *needed = L.nslices == 0 || L.smap != map;
   if (!*needed) return BCS_OK;
+  if (!s->lv.empty() && &L == &s->lv[0]) s->v0_direct = -1;  // a copy in the old layout
+  L.tpos.release();
   L.sci.release();
   L.s32.release();
   L.s16.release();
@@ -1239,8 +1234,20 @@ bcs_status layout_structure(Solver* s, Level& L, int map, int32_t* steps_dev, bo
 // Values of level L's sliced copy (its structure in place, nsteps known).
 bcs_status layout_values(Solver* s, Level& L, int prec) {
   const int n = s->n, rows = L.A.rows, map = L.smap, rpw = map == 1 ? 32 : 32 / n;
+  if (&L == &s->lv[0] && s->v0_direct >= 0) {
+    const bool written = s->v0_direct == prec && map == 1 && L.tpos.p && L.sci.p;
+    s->v0_direct = -1;
+    if (written) return BCS_OK;  // the value gather wrote this copy
+  }
   if (!L.sci.p) BCS_ALLOC(s, L.sci, (size_t)L.nsteps * rpw);
   const size_t nv = (size_t)L.nsteps * rpw * n * n;
+  // the fine level's first fill in layout 1 also records the slot map
+  // (slots in int32)
+  int32_t* tpos = nullptr;
+  if (map == 1 && &L == &s->lv[0] && !L.tpos.p && (size_t)L.nsteps * 32 <= (size_t)INT32_MAX) {
+    BCS_ALLOC(s, L.tpos, L.A.nnz > 0 ? L.A.nnz : 1);
+    tpos = L.tpos.p;
+  }
   return with_n(n, [&](auto NC) -> bcs_status {
     constexpr int N = decltype(NC)::value;
     const unsigned g = grid_for((size_t)L.nslices * 32, 128);
@@ -1249,7 +1256,7 @@ bcs_status layout_values(Solver* s, Level& L, int prec) {
       BCS_ALLOC(s, L.s32, nv);
       if (map == 1)
         BCS_LAUNCH_DEP(s, K_CAST, bytes, 0, (k_tpr_fill<N, float>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
-                   L.A.v.p, L.srow.p, L.sptr.p, L.sci.p, L.s32.p);
+                   L.A.v.p, L.srow.p, L.sptr.p, L.sci.p, L.s32.p, tpos);
       else
         BCS_LAUNCH_DEP(s, K_CAST, bytes, 0, (k_slice_fill<N, float>), g, 128, 0, rows, L.nslices, L.A.rp.p,
                    L.A.ci.p, L.A.v.p, L.sptr.p, L.sci.p, L.s32.p);
@@ -1257,7 +1264,7 @@ bcs_status layout_values(Solver* s, Level& L, int prec) {
       BCS_ALLOC(s, L.s16, nv);
       if (map == 1)
         BCS_LAUNCH_DEP(s, K_CAST, bytes, 0, (k_tpr_fill<N, bf16>), g, 128, 0, rows, L.nslices, L.A.rp.p, L.A.ci.p,
-                   L.A.v.p, L.srow.p, L.sptr.p, L.sci.p, L.s16.p);
+                   L.A.v.p, L.srow.p, L.sptr.p, L.sci.p, L.s16.p, tpos);
       else
         BCS_LAUNCH_DEP(s, K_CAST, bytes, 0, (k_slice_fill<N, bf16>), g, 128, 0, rows, L.nslices, L.A.rp.p,
                    L.A.ci.p, L.A.v.p, L.sptr.p, L.sci.p, L.s16.p);
@@ -1654,6 +1661,29 @@ bcs_status cycle_prepare(Solver* s, bool keep_graphs) {
     }
   }
   if (s->tail_level >= 0) BCS_OKR(build_tail(s));
+  return BCS_OK;
+}
+
+namespace {
+bool sliced_cycle(const bcs_config& c) {
+  return c.precision != BCS_PREC_FP64 && (c.precond == BCS_PC_AMG || c.precond == BCS_PC_SGS);
+}
+}  // namespace
+
+bcs_status fine_slice_target(Solver* s, SliceTarget* t) {
+  *t = SliceTarget{};
+  if (s->lv.empty()) return BCS_OK;
+  // the configuration the next setup takes: the new one for a full setup
+  const bcs_config& c = s->have_hierarchy ? s->setup_cfg : s->cfg;
+  Level& L = s->lv[0];
+  if (!sliced_cycle(c) || L.smap != 1 || !L.tpos.p || !L.sci.p || L.nslices == 0) return BCS_OK;
+  if (c.slice_layout == 0 || (c.tail_rows > 0 && L.A.rows <= c.tail_rows)) return BCS_OK;
+  const size_t nv = (size_t)L.nsteps * 32 * s->n * s->n;
+  if (c.precision == BCS_PREC_FP32 && L.s32.p && L.s32.n == nv) t->s32 = L.s32.p;
+  else if (c.precision == BCS_PREC_BF16 && L.s16.p && L.s16.n == nv) t->s16 = L.s16.p;
+  else return BCS_OK;
+  t->tpos = L.tpos.p;
+  t->prec = c.precision;
   return BCS_OK;
 }
 

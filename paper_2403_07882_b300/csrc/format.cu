@@ -144,13 +144,51 @@ struct GnShape {
   static constexpr int LPB = NN < 32 ? NN : 32;  // lanes loading one block
 };
 
+// One block (n*n doubles, row-major, in shared memory) into its slot of the
+// fine level's thread-per-row sliced copy (s32 or s16, the other null):
+// slice lane slot % 32 of step tile slot / 32, each entry rounded to the
+// cycle precision as k_tpr_fill rounds it (round to nearest).
+template <int NN>
+__device__ __forceinline__ void store_slot(const double* blk, int slot, float* s32, bf16* s16) {
+  const int w = slot & 31;
+  const size_t t = (size_t)(slot >> 5);
+  if (s32) {
+    using T = TprTile<NN, float>;
+    float* tile = s32 + t * T::TILE;
+#pragma unroll
+    for (int g = 0; g < T::NG; ++g) {
+      alignas(16) float v[T::G];
+#pragma unroll
+      for (int q = 0; q < T::G; ++q) v[q] = (float)blk[g * T::G + q];
+      *reinterpret_cast<uint4*>(tile + g * T::G * 32 + w * T::G) = *reinterpret_cast<const uint4*>(v);
+    }
+#pragma unroll
+    for (int r = 0; r < T::R; ++r) tile[T::NG * T::G * 32 + r * 32 + w] = (float)blk[T::NG * T::G + r];
+  } else {
+    using T = TprTile<NN, bf16>;
+    bf16* tile = s16 + t * T::TILE;
+#pragma unroll
+    for (int g = 0; g < T::NG; ++g) {
+      alignas(16) bf16 v[T::G];
+#pragma unroll
+      for (int q = 0; q < T::G; ++q) v[q] = __double2bfloat16(blk[g * T::G + q]);
+      *reinterpret_cast<uint4*>(tile + g * T::G * 32 + w * T::G) = *reinterpret_cast<const uint4*>(v);
+    }
+#pragma unroll
+    for (int r = 0; r < T::R; ++r) tile[T::NG * T::G * 32 + r * 32 + w] = __double2bfloat16(blk[T::NG * T::G + r]);
+  }
+}
+
 template <int NN>
 __global__ void __launch_bounds__(GnShape<NN>::WARPS * 32) k_gather_norms(int nnz, const int32_t* __restrict__ src,
                                                                          const double* __restrict__ diag,
                                                                          const double* __restrict__ upper,
                                                                          const double* __restrict__ lower,
                                                                          double* __restrict__ val,
-                                                                         double* __restrict__ nrm) {
+                                                                         double* __restrict__ nrm,
+                                                                         const int32_t* __restrict__ tpos,
+                                                                         float* __restrict__ s32,
+                                                                         bf16* __restrict__ s16) {
   dep_enter();
   using G = GnShape<NN>;
   __shared__ double tile[G::WARPS][32 * G::NNP];
@@ -187,13 +225,16 @@ __global__ void __launch_bounds__(GnShape<NN>::WARPS * 32) k_gather_norms(int nn
   }
   __syncwarp();
   if (lane < cnt) {
-    double acc = 0.0;
+    if (nrm) {
+      double acc = 0.0;
 #pragma unroll
-    for (int e = 0; e < NN; ++e) {
-      const double v = tl[lane * G::NNP + e];
-      acc = fma(v, v, acc);
+      for (int e = 0; e < NN; ++e) {
+        const double v = tl[lane * G::NNP + e];
+        acc = fma(v, v, acc);
+      }
+      nrm[p0 + lane] = sqrt(acc);
     }
-    nrm[p0 + lane] = sqrt(acc);
+    if (tpos) store_slot<NN>(tl + lane * G::NNP, __ldg(tpos + p0 + lane), s32, s16);
   }
   double* out = val + (size_t)p0 * NN;
   for (int q = lane; q < cnt * NN; q += 32) out[q] = tl[(q / NN) * G::NNP + q % NN];
@@ -208,7 +249,10 @@ template <int NN>
 __global__ void __launch_bounds__(GnShape<NN>::WARPS * 32) k_scatter_blocks(int count, const double* __restrict__ src,
                                                                            const int32_t* __restrict__ pos,
                                                                            double* __restrict__ val,
-                                                                           double* __restrict__ nrm) {
+                                                                           double* __restrict__ nrm,
+                                                                           const int32_t* __restrict__ tpos,
+                                                                           float* __restrict__ s32,
+                                                                           bf16* __restrict__ s16) {
   dep_enter();
   using G = GnShape<NN>;
   __shared__ double tile[G::WARPS][32 * G::NNP];
@@ -221,14 +265,17 @@ __global__ void __launch_bounds__(GnShape<NN>::WARPS * 32) k_scatter_blocks(int 
   for (int q = lane; q < cnt * NN; q += 32) tl[(q / NN) * G::NNP + q % NN] = __ldg(in + q);
   const int my = lane < cnt ? __ldg(pos + b0 + lane) : 0;
   __syncwarp();
-  if (nrm && lane < cnt) {
-    double acc = 0.0;
+  if (lane < cnt) {
+    if (nrm) {
+      double acc = 0.0;
 #pragma unroll
-    for (int e = 0; e < NN; ++e) {
-      const double v = tl[lane * G::NNP + e];
-      acc = fma(v, v, acc);
+      for (int e = 0; e < NN; ++e) {
+        const double v = tl[lane * G::NNP + e];
+        acc = fma(v, v, acc);
+      }
+      nrm[my] = sqrt(acc);
     }
-    nrm[my] = sqrt(acc);
+    if (tpos) store_slot<NN>(tl + lane * G::NNP, __ldg(tpos + my), s32, s16);
   }
   for (int b = 0; b < cnt; ++b) {
     const int p = __shfl_sync(0xffffffffu, my, b);
@@ -293,18 +340,26 @@ bcs_status permute_values(Solver* s, const double* diag, const double* upper, co
   const size_t total = (size_t)A.nnz * nn;
   const double bytes = 16.0 * total + 4.0 * A.nnz;
   s->nrm0_fresh = false;
-  if (!s->have_hierarchy) {
-    // a full setup follows: its first matching pass takes these norms
-    BCS_ALLOC(s, s->nrm0, A.nnz);
+  s->v0_direct = -1;
+  // the fine level's sliced copy written here too when its layout is known
+  SliceTarget sl;
+  BCS_OKR(fine_slice_target(s, &sl));
+  const double slice_bytes = sl.tpos ? 4.0 * A.nnz + (double)total * (sl.s32 ? 4 : 2) : 0.0;
+  const bool norms = !s->have_hierarchy;
+  if (norms || sl.tpos) {
+    // the tile gather: with the block norms when a full setup follows (its
+    // first matching pass takes them), with the sliced copy when known
+    if (norms) BCS_ALLOC(s, s->nrm0, A.nnz);
     BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
       constexpr int N = decltype(NC)::value;
       using G = GnShape<N * N>;
-      BCS_LAUNCH_DEP(s, K_CONVERT, bytes + 8.0 * A.nnz, 2.0 * total, k_gather_norms<N * N>,
-                 grid_for((size_t)A.nnz, G::WARPS * 32), G::WARPS * 32, 0, A.nnz, s->src.p, diag, upper, lower,
-                 A.v.p, s->nrm0.p);
+      BCS_LAUNCH_DEP(s, K_CONVERT, bytes + (norms ? 8.0 * A.nnz : 0.0) + slice_bytes, norms ? 2.0 * total : 0.0,
+                 k_gather_norms<N * N>, grid_for((size_t)A.nnz, G::WARPS * 32), G::WARPS * 32, 0, A.nnz,
+                 s->src.p, diag, upper, lower, A.v.p, norms ? s->nrm0.p : nullptr, sl.tpos, sl.s32, sl.s16);
       return BCS_OK;
     }));
-    s->nrm0_fresh = true;
+    s->nrm0_fresh = norms;
+    s->v0_direct = sl.prec;
     return BCS_OK;
   }
   return with_n(n, [&](auto NC) -> bcs_status {
@@ -336,6 +391,9 @@ bcs_status upload_values(Solver* s, const double* diag, const double* upper, con
   }
   const bool norms = !s->have_hierarchy;
   s->nrm0_fresh = false;
+  s->v0_direct = -1;
+  SliceTarget sl;
+  BCS_OKR(fine_slice_target(s, &sl));
   if (norms) BCS_ALLOC(s, s->nrm0, A.nnz);
   if (!s->cstream) BCS_CU(s, cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking));
   struct Part {
@@ -377,14 +435,18 @@ bcs_status upload_values(Solver* s, const double* diag, const double* upper, con
       BCS_OKR(with_n(n, [&](auto NC) -> bcs_status {
         constexpr int N = decltype(NC)::value;
         using G = GnShape<N * N>;
-        BCS_LAUNCH_DEP(s, K_CONVERT, 16.0 * cnt * N * N + 4.0 * cnt + (norms ? 8.0 * cnt : 0.0),
+        BCS_LAUNCH_DEP(s, K_CONVERT,
+                   16.0 * cnt * N * N + 4.0 * cnt + (norms ? 8.0 * cnt : 0.0) +
+                       (sl.tpos ? 4.0 * cnt + (double)cnt * N * N * (sl.s32 ? 4 : 2) : 0.0),
                    norms ? 2.0 * cnt * N * N : 0.0, k_scatter_blocks<N * N>, grid_for(cnt, G::WARPS * 32),
-                   G::WARPS * 32, 0, cnt, pt.dev + off, pt.pos + b, A.v.p, norms ? s->nrm0.p : nullptr);
+                   G::WARPS * 32, 0, cnt, pt.dev + off, pt.pos + b, A.v.p, norms ? s->nrm0.p : nullptr, sl.tpos,
+                   sl.s32, sl.s16);
         return BCS_OK;
       }));
     }
   }
   s->nrm0_fresh = norms;
+  s->v0_direct = sl.prec;
   return BCS_OK;
 }
 

@@ -101,6 +101,21 @@ struct DBuf {
   }
 };
 
+// Step tile of the thread-per-block-row sliced layout (layout 1, cycle.cu):
+// 32 block rows' n*n entries; entry e of slice lane w sits in 16-byte groups
+// of G consecutive entries (group g of lane w at g * G * 32 + w * G), the
+// n*n mod G remaining entries element-major after the groups.
+template <int NN, class TV>
+struct TprTile {
+  static constexpr int G = 16 / (int)sizeof(TV);  // entries per 16-byte group
+  static constexpr int NG = NN / G;               // full groups
+  static constexpr int R = NN - NG * G;           // remaining entries
+  static constexpr int TILE = NN * 32;
+  __host__ __device__ static constexpr int off(int e, int w) {
+    return e < NG * G ? (e / G) * G * 32 + w * G + e % G : NG * G * 32 + (e - NG * G) * 32 + w;
+  }
+};
+
 // ----------------------------------------------------------- data structures
 // Block-CSR matrix on the device; values FP64 (setup precision).
 struct Bsr {
@@ -149,6 +164,10 @@ struct Level {
   int nslices = 0, nsteps = 0;
   DBuf<int32_t> sptr, sci;
   DBuf<int32_t> srow;        // layout 1: block row at each slice position
+  // layout 1 of the fine level: the slot (step * 32 + slice lane) of every
+  // block-CSR position, recorded by the first fill; through it the value
+  // gather of a later upload writes the sliced copy itself
+  DBuf<int32_t> tpos;
   DBuf<float> s32;
   DBuf<bf16> s16;
   DBuf<char> vx, vb, vr, vt; // V-cycle vectors (cycle precision)
@@ -298,6 +317,10 @@ struct Solver {
   // when a full setup follows (fresh: they belong to the current values)
   DBuf<double> nrm0;
   bool nrm0_fresh = false;
+  // precision of the fine level's sliced copy when the value gather wrote
+  // it through lv[0].tpos (the copy then skips its fill), else -1; set by
+  // the gather, cleared when the new values have been set up
+  int v0_direct = -1;
   cudaStream_t cstream = nullptr;          // host -> device copies of the values in pieces
   cudaStream_t sstream = nullptr;          // setup work beside the aggregation (block inverses)
   cudaEvent_t sev[2] = {};
@@ -609,6 +632,22 @@ bcs_status spmv64(Solver* s, const Bsr& A, const void* x, bool x_is_float, doubl
 // keep_graphs: a values-only resetup (every buffer kept in place), so the
 // captured graphs stay valid; otherwise they are dropped.
 bcs_status cycle_prepare(Solver* s, bool keep_graphs = false);
+// Where the value gather writes the fine level's sliced copy: the slot map
+// and the buffer of the precision the next setup uses (one of s32, s16
+// set), or all null when it cannot: no slot map yet (the first setup of a
+// structure fills the copy and records it), another layout or precision,
+// an unsliced cycle. The buffer is never allocated here: allocated before
+// a full setup (which then runs with it held), the copy made every later
+// full setup of a 2.1 M block-row structure about 3 ms slower with the
+// same kernel times (measured; the cause was not isolated), so a new
+// structure's first setup fills the copy after the hierarchy is built.
+struct SliceTarget {
+  const int32_t* tpos = nullptr;
+  float* s32 = nullptr;
+  bf16* s16 = nullptr;
+  int prec = -1;
+};
+bcs_status fine_slice_target(Solver* s, SliceTarget* t);
 // The blocks' FP64 inverses of level l into out (computed on demand when the
 // setup inverted them in FP32 only).
 bcs_status level_dinv64(Solver* s, int l, const double** out, DBuf<double>& tmp);

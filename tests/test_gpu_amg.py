@@ -172,6 +172,48 @@ def test_slice_layouts_identical(gen, precision):
     assert np.linalg.norm(outs[0] - z_ref) <= tol * np.linalg.norm(z_ref)
 
 
+def tpr_fill_launches(s):
+    return sum(t["launches"] for name, t in s.kernel_times().items() if name.startswith("(k_tpr_fill"))
+
+
+@pytest.mark.parametrize("precision", [bcs.BCS_PREC_FP32, bcs.BCS_PREC_BF16])
+@pytest.mark.parametrize("host", [False, True], ids=["device-values", "host-values"])
+@pytest.mark.parametrize("cfg", [dict(), dict(smoother=bcs.BCS_SMOOTH_DILU), dict(precond=bcs.BCS_PC_SGS)],
+                         ids=["amg-jacobi", "amg-dilu", "sgs"])
+def test_gather_writes_fine_sliced_copy(precision, host, cfg):
+    """The first setup of a structure fills the fine level's thread-per-row
+    FP32 / BF16 copy and records each block's slot; at every values-only
+    resetup the value gather writes the copy through those slots and the
+    fill kernel skips that level. Same values give the same preconditioner
+    bits; new values give those of the lane-per-row layout filled from the
+    block-CSR values (bit for bit with block Jacobi, whose layouts share one
+    fma order; within the storage precision with DILU / SGS sweeps)."""
+    system = synth.density(20, seed=1)
+    v = torch.from_numpy(np.random.default_rng(12).standard_normal(system["b"].shape)).to(DEV)
+    dev = {k: torch.from_numpy(system[k]).to(DEV) for k in ("owner", "neighbour", "diag", "upper", "lower")}
+    vals1 = [system[k] if host else dev[k] for k in ("diag", "upper", "lower")]
+    vals2 = [vals1[0], 0.8 * vals1[1], 0.7 * vals1[2]]
+    z, fills = {}, []
+    for layout in (1, 0):
+        with bcs.Solver(5, precision=precision, slice_layout=layout, profile=1, **cfg) as s:
+            s.set_structure(system["n_cells"], dev["owner"], dev["neighbour"])
+            for phase, vals in (("setup", vals1), ("resetup-same", vals1), ("resetup-new", vals2)):
+                s.reset_stats()
+                s.set_values(*vals)
+                if layout == 1:
+                    fills.append(tpr_fill_launches(s))
+                z[layout, phase] = s.precond(v).cpu().numpy()
+    assert fills[0] >= 1 and fills[1] == fills[2] == fills[0] - 1, fills
+    assert np.array_equal(z[1, "resetup-same"], z[1, "setup"])
+    new, ref = z[1, "resetup-new"], z[0, "resetup-new"]
+    assert np.linalg.norm(new - z[1, "setup"]) > 1e-2 * np.linalg.norm(ref)  # the values did change
+    if not cfg:
+        assert np.array_equal(new, ref)
+    else:
+        tol = 1e-5 if precision == bcs.BCS_PREC_FP32 else 2e-2
+        assert np.linalg.norm(new - ref) <= tol * np.linalg.norm(ref)
+
+
 @pytest.mark.parametrize("precision", [bcs.BCS_PREC_FP32, bcs.BCS_PREC_BF16])
 def test_graph_cycle_identical(precision):
     """The V-cycle replayed as a CUDA graph gives the same bits as the same
