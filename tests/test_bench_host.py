@@ -1,10 +1,40 @@
 """Host-side logic of bench.py and the flow-state generator, without a GPU:
 the clock summary (median SM clock, throttle reasons) from nvidia-smi CSV
-lines, and the physical validity of synth.flow's states and geometry."""
+lines, the reference arm's JSON line (the oracle timed on the host cores),
+and the physical validity of synth.flow's states and geometry."""
+import json
+import os
+import subprocess
+import sys
+
 import numpy as np
 
 import bench
 from paper_2403_07882_b300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` runs the oracle (one step: a full solve of
+    the 64^3 sample) and prints exactly one JSON line with the launch
+    contract's keys, on the native arm's metric and workload."""
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["config"]["workload"] == bench.WORKLOAD
+    assert d["unit"] == "ms" and d["higher_is_better"] is False and d["n_gpus"] == 1
+    assert d["steps"] == 1 and d["warmup"] == 0 and d["value"] > 0 and d["vs_baseline"] is None
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
 def test_clock_summary_from_csv_lines():
