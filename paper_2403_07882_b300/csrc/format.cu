@@ -134,7 +134,9 @@ __global__ void k_gather_values(size_t total, const int32_t* __restrict__ src,
 // each source block (n*n contiguous doubles) is loaded by n*n lanes into a
 // tile in shared memory (rows padded to an odd length: conflict-free), lane
 // b then sums the squares of block b, and the tile is stored to the
-// positions as one contiguous run.
+// positions as one contiguous run. At a values-only resetup (nrm null) the
+// kernel gathers without the norms and, given the fine level's slot map,
+// lane b also stores block b into the fine level's thread-per-row copy.
 constexpr int GN_U = 8;
 
 template <int NN>
